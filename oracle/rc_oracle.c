@@ -1,0 +1,650 @@
+/* rc_oracle.c - plain FP64 CPU oracle of one particle region-competition iteration
+ * with particle-approximated Sobolev gradients (arXiv:1403.0240).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the product path. Slow on purpose: every
+ * step follows the paper (or the reading stated where the paper is silent) in the
+ * plainest form, in ascending particle-key order (pixel index, then candidate
+ * label). Build with -ffp-contract=off so that no multiply-add is fused.
+ *
+ * Readings where the paper is silent (the optimizer's details are deferred to
+ * Cardinale et al. 2012, which is not available):
+ *  - A particle is a pair (pixel x, candidate label c) where L(x) != c and some
+ *    connectivity-neighbour of x has label c: particles sit on both sides of the
+ *    contour (Fig. 1, "Discrete particle approximation").
+ *  - Piecewise-constant data term: sum of squared deviations from the region means
+ *    (theta_i = region mean, Methods "Bayesian image models"); the energy change of
+ *    one flip is the exact single-pixel SSE change.
+ *  - Piecewise-smooth data term: local means over a ball of radius R.
+ *  - Length prior: number of connectivity-adjacent pixel pairs with different labels.
+ *  - Eq. 6 sets use the strict cutoff d < E/2, are normalised by their counts, and an
+ *    empty set contributes 0; every q uses its pre-update energy difference.
+ *  - Ranking before the moves ("The Region Competition (RC) algorithm"): per pixel
+ *    the smallest (g, c) is its candidate if g < 0; candidates that keep every
+ *    foreground region's topology (simple points) are accepted greedily in
+ *    ascending (g, pixel) order, skipping any within Chebyshev distance 1 of an
+ *    accepted pixel.
+ *  - Oscillation fallback (Eq. 6 discussion): switch to L2 for good once the
+ *    accepted-move count has not reached a new minimum for osc_window iterations;
+ *    an L2 iteration with no accepted move means convergence.
+ */
+#include "rc_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Eq. 5: K(r) = (1/E) (1 + ((|r|/E)^2 - |r|/E + 1/6) / (2 eps)), |r| <= E/2 */
+double orc_kernel_eq5(double r, double E, double eps)
+{
+    double x = fabs(r) / E;
+    double num = x * x - x + 1.0 / 6.0;
+    return (1.0 / E) * (1.0 + num / (2.0 * eps));
+}
+
+/* ------------------------------------------------------------------ */
+static double pix(const orc_params* p, const void* I, int64_t i)
+{
+    if (p->dtype == 0) return (double)((const float*)I)[i];
+    return (double)((const uint16_t*)I)[i];
+}
+
+static void coords(const orc_params* p, int64_t i, int64_t* z, int64_t* y, int64_t* x)
+{
+    *x = i % p->W;
+    *y = (i / p->W) % p->H;
+    *z = i / (p->W * p->H);
+}
+
+static int inside(const orc_params* p, int64_t z, int64_t y, int64_t x)
+{
+    return z >= 0 && z < p->D && y >= 0 && y < p->H && x >= 0 && x < p->W;
+}
+
+/* connectivity neighbours: 4 in 2D, 6 in 3D */
+static int nbr_offsets(const orc_params* p, int off[6][3])
+{
+    int k = 0;
+    if (p->ndim == 3) {
+        off[k][0] = -1; off[k][1] = 0; off[k][2] = 0; k++;
+        off[k][0] = 1;  off[k][1] = 0; off[k][2] = 0; k++;
+    }
+    off[k][0] = 0; off[k][1] = -1; off[k][2] = 0; k++;
+    off[k][0] = 0; off[k][1] = 1;  off[k][2] = 0; k++;
+    off[k][0] = 0; off[k][1] = 0;  off[k][2] = -1; k++;
+    off[k][0] = 0; off[k][1] = 0;  off[k][2] = 1; k++;
+    return k;
+}
+
+/* ------------------------------------------------------------------ */
+/* Particles: every (x, c) with c != L(x) the label of a connectivity neighbour. */
+int64_t orc_extract(const orc_params* p, const int32_t* L,
+                    uint32_t* idx, int32_t* l, int32_t* c, int64_t cap)
+{
+    int off[6][3];
+    int nn = nbr_offsets(p, off);
+    int64_t npix = p->D * p->H * p->W;
+    int64_t count = 0;
+    for (int64_t i = 0; i < npix; i++) {
+        int64_t z, y, x;
+        coords(p, i, &z, &y, &x);
+        int32_t own = L[i];
+        int32_t labs[6];
+        int nl = 0;
+        for (int k = 0; k < nn; k++) {
+            int64_t zz = z + off[k][0], yy = y + off[k][1], xx = x + off[k][2];
+            if (!inside(p, zz, yy, xx)) continue;
+            int32_t m = L[(zz * p->H + yy) * p->W + xx];
+            if (m == own) continue;
+            int seen = 0;
+            for (int j = 0; j < nl; j++) if (labs[j] == m) seen = 1;
+            if (!seen) labs[nl++] = m;
+        }
+        /* ascending candidate label */
+        for (int a = 1; a < nl; a++)
+            for (int b = a; b > 0 && labs[b - 1] > labs[b]; b--) {
+                int32_t t = labs[b]; labs[b] = labs[b - 1]; labs[b - 1] = t;
+            }
+        for (int j = 0; j < nl; j++) {
+            if (count < cap) {
+                idx[count] = (uint32_t)i;
+                l[count] = own;
+                c[count] = labs[j];
+            }
+            count++;
+        }
+    }
+    return count;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact summation: a big fixed-point integer with least significant bit 2^-300,
+ * 32 value bits per limb; positive and negative parts kept apart, rounded once
+ * to the nearest double (ties to even). */
+#define ACC_LIMBS 24
+#define ACC_LSB (-300)
+
+typedef struct { uint64_t pos[ACC_LIMBS], neg[ACC_LIMBS]; int64_t adds; } bigacc;
+
+static void acc_norm(uint64_t* a)
+{
+    uint64_t carry = 0;
+    for (int k = 0; k < ACC_LIMBS; k++) {
+        uint64_t t = a[k] + carry;
+        a[k] = t & 0xFFFFFFFFull;
+        carry = t >> 32;
+    }
+}
+
+/* add m * 2^(s + ACC_LSB), m < 2^49, s >= 0 */
+static void acc_add(bigacc* A, int neg, uint64_t m, int s)
+{
+    uint64_t* a = neg ? A->neg : A->pos;
+    int k = s / 32, r = s % 32;
+    /* m * 2^r has at most 81 bits: bits 0-31, 32-63 and 64-95 go to limbs k, k+1, k+2 */
+    uint64_t lo = (m << r) & 0xFFFFFFFFull;
+    uint64_t mid, hi;
+    if (r == 0) {
+        mid = (m >> 32) & 0xFFFFFFFFull;
+        hi = 0;
+    } else {
+        mid = (m >> (32 - r)) & 0xFFFFFFFFull;
+        hi = m >> (64 - r);
+    }
+    a[k] += lo;
+    if (k + 1 < ACC_LIMBS) a[k + 1] += mid;
+    if (k + 2 < ACC_LIMBS) a[k + 2] += hi;
+    if (++A->adds >= (1 << 24)) { acc_norm(A->pos); acc_norm(A->neg); A->adds = 0; }
+}
+
+static void acc_add_f32(bigacc* A, float f, int squares)
+{
+    uint32_t bits;
+    memcpy(&bits, &f, 4);
+    int sign = (int)(bits >> 31);
+    int eb = (int)((bits >> 23) & 0xFF);
+    uint64_t m = bits & 0x7FFFFFu;
+    if (eb == 0) eb = 1; else m |= 0x800000u;   /* subnormals share the smallest scale */
+    if (m == 0) return;
+    /* |f| = m * 2^(eb - 150) */
+    if (!squares) acc_add(A, sign, m, eb - 150 - ACC_LSB);
+    else acc_add(A, 0, m * m, 2 * (eb - 150) - ACC_LSB);
+}
+
+static void acc_add_int(bigacc* A, uint64_t m)
+{
+    if (m) acc_add(A, 0, m, -ACC_LSB);
+}
+
+static int big_cmp(const uint64_t* a, const uint64_t* b)
+{
+    for (int k = ACC_LIMBS - 1; k >= 0; k--) {
+        if (a[k] != b[k]) return a[k] > b[k] ? 1 : -1;
+    }
+    return 0;
+}
+
+static void big_sub(uint64_t* r, const uint64_t* a, const uint64_t* b)  /* r = a - b, a >= b */
+{
+    int64_t borrow = 0;
+    for (int k = 0; k < ACC_LIMBS; k++) {
+        int64_t t = (int64_t)a[k] - (int64_t)b[k] - borrow;
+        borrow = t < 0;
+        if (t < 0) t += (int64_t)1 << 32;
+        r[k] = (uint64_t)t;
+    }
+}
+
+static int big_bit(const uint64_t* a, int b) { return (int)((a[b / 32] >> (b % 32)) & 1u); }
+
+static double acc_round(bigacc* A)
+{
+    acc_norm(A->pos);
+    acc_norm(A->neg);
+    uint64_t mag[ACC_LIMBS];
+    int sign = 0;
+    int cmp = big_cmp(A->pos, A->neg);
+    if (cmp == 0) return 0.0;
+    if (cmp > 0) big_sub(mag, A->pos, A->neg);
+    else { big_sub(mag, A->neg, A->pos); sign = 1; }
+    int h = -1;
+    for (int b = ACC_LIMBS * 32 - 1; b >= 0; b--) if (big_bit(mag, b)) { h = b; break; }
+    uint64_t mant = 0;
+    int shift = 0;
+    if (h <= 52) {
+        for (int b = h; b >= 0; b--) mant = (mant << 1) | (uint64_t)big_bit(mag, b);
+    } else {
+        shift = h - 52;
+        for (int b = h; b >= shift; b--) mant = (mant << 1) | (uint64_t)big_bit(mag, b);
+        int round = big_bit(mag, shift - 1);
+        int sticky = 0;
+        for (int b = shift - 2; b >= 0; b--) if (big_bit(mag, b)) { sticky = 1; break; }
+        if (round && (sticky || (mant & 1u))) {
+            mant++;
+            if (mant == (1ull << 53)) { mant >>= 1; shift++; }
+        }
+    }
+    double v = ldexp((double)mant, shift + ACC_LSB);
+    return sign ? -v : v;
+}
+
+double orc_exact_sum_f32(const float* v, int64_t n, int squares)
+{
+    bigacc A;
+    memset(&A, 0, sizeof A);
+    for (int64_t i = 0; i < n; i++) acc_add_f32(&A, v[i], squares);
+    return acc_round(&A);
+}
+
+/* Region statistics: n_i = |Omega_i|, S_i = sum I, Q_i = sum I^2, each exact and
+ * rounded once (theta_i = S_i / n_i is the region mean, Methods). */
+void orc_stats(const orc_params* p, const void* I, const int32_t* L,
+               int64_t* n, double* S, double* Q)
+{
+    int M = p->nlabels;
+    bigacc* AS = (bigacc*)calloc((size_t)M, sizeof(bigacc));
+    bigacc* AQ = (bigacc*)calloc((size_t)M, sizeof(bigacc));
+    int64_t npix = p->D * p->H * p->W;
+    for (int m = 0; m < M; m++) n[m] = 0;
+    for (int64_t i = 0; i < npix; i++) {
+        int32_t m = L[i];
+        n[m]++;
+        if (p->dtype == 0) {
+            float f = ((const float*)I)[i];
+            acc_add_f32(&AS[m], f, 0);
+            acc_add_f32(&AQ[m], f, 1);
+        } else {
+            uint64_t u = ((const uint16_t*)I)[i];
+            acc_add_int(&AS[m], u);
+            acc_add_int(&AQ[m], u * u);
+        }
+    }
+    for (int m = 0; m < M; m++) {
+        S[m] = acc_round(&AS[m]);
+        Q[m] = acc_round(&AQ[m]);
+    }
+    free(AS);
+    free(AQ);
+}
+
+/* ------------------------------------------------------------------ */
+/* Length prior: change of the number of connectivity-adjacent pixel pairs with
+ * different labels when x goes from l to c (neighbours outside the image absent). */
+int64_t orc_delta_perimeter(const orc_params* p, const int32_t* L, uint32_t xi, int32_t l, int32_t c)
+{
+    int off[6][3];
+    int nn = nbr_offsets(p, off);
+    int64_t z, y, x;
+    coords(p, xi, &z, &y, &x);
+    int64_t d = 0;
+    for (int k = 0; k < nn; k++) {
+        int64_t zz = z + off[k][0], yy = y + off[k][1], xx = x + off[k][2];
+        if (!inside(p, zz, yy, xx)) continue;
+        int32_t m = L[(zz * p->H + yy) * p->W + xx];
+        d += (int64_t)(m != c) - (int64_t)(m != l);
+    }
+    return d;
+}
+
+/* Energy difference of moving particle (x: l -> c), data term + lambda * length. */
+void orc_energy(const orc_params* p, const void* I, const int32_t* L,
+                const int64_t* n, const double* S, int64_t N,
+                const uint32_t* idx, const int32_t* l, const int32_t* c, double* dE)
+{
+    int Ri = (int)floor(p->ps_radius);
+    double R2 = p->ps_radius * p->ps_radius;
+    for (int64_t k = 0; k < N; k++) {
+        uint32_t xi = idx[k];
+        int32_t lp = l[k], cp = c[k];
+        double v = pix(p, I, xi);
+        double data;
+        if (p->model == 0) {
+            /* Piecewise constant: exact SSE change of moving v from region l to c. */
+            double mc = S[cp] / (double)n[cp];
+            double ml = S[lp] / (double)n[lp];
+            double a = v - mc;
+            double b = v - ml;
+            double t1 = ((double)n[cp] / ((double)n[cp] + 1.0)) * (a * a);
+            double t2 = 0.0;
+            if (n[lp] > 1) t2 = ((double)n[lp] / ((double)n[lp] - 1.0)) * (b * b);
+            data = t1 - t2;
+        } else {
+            /* Piecewise smooth: local means over the ball of radius R, row-major order. */
+            int64_t z, y, x;
+            coords(p, xi, &z, &y, &x);
+            double sc = 0.0, sl = 0.0;
+            int64_t cc = 0, cl = 0;
+            int Rz = p->ndim == 3 ? Ri : 0;
+            for (int dz = -Rz; dz <= Rz; dz++)
+                for (int dy = -Ri; dy <= Ri; dy++)
+                    for (int dx = -Ri; dx <= Ri; dx++) {
+                        int64_t d2 = (int64_t)dz * dz + (int64_t)dy * dy + (int64_t)dx * dx;
+                        if (!((double)d2 <= R2)) continue;
+                        int64_t zz = z + dz, yy = y + dy, xx = x + dx;
+                        if (!inside(p, zz, yy, xx)) continue;
+                        int64_t j = (zz * p->H + yy) * p->W + xx;
+                        int32_t m = L[j];
+                        if (m == cp) { sc = sc + pix(p, I, j); cc++; }
+                        else if (m == lp) { sl = sl + pix(p, I, j); cl++; }
+                    }
+            double muc = sc / (double)cc;
+            double mul = sl / (double)cl;
+            double a = v - muc;
+            double b = v - mul;
+            data = a * a - b * b;
+        }
+        int64_t dP = orc_delta_perimeter(p, L, xi, lp, cp);
+        dE[k] = data + p->lambda * (double)dP;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 6 on particles, neighbours found with a cell list of edge ceil(E/2). */
+static int cmp_i64(const void* a, const void* b)
+{
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+void orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int32_t* l,
+                 const int32_t* c, const double* dE, int all_pairs,
+                 double* g, double* A, double* B, int32_t* nQ, int32_t* nQp)
+{
+    double rc = p->cutoff;
+    double r2 = rc * rc;
+    double E = 2.0 * rc;
+    double eps = 1.0 / 24.0;
+    int64_t s = (int64_t)ceil(rc);
+    if (s < 1) s = 1;
+    int64_t ncx = (p->W + s - 1) / s, ncy = (p->H + s - 1) / s, ncz = (p->D + s - 1) / s;
+    int64_t ncell = ncx * ncy * ncz;
+    int64_t* cz = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    int64_t* cy = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    int64_t* cx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    int64_t* cstart = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    int64_t* fill = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+    int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    for (int64_t k = 0; k < N; k++) {
+        coords(p, idx[k], &cz[k], &cy[k], &cx[k]);
+        int64_t cell = ((cz[k] / s) * ncy + cy[k] / s) * ncx + cx[k] / s;
+        cstart[cell + 1]++;
+    }
+    for (int64_t q = 0; q < ncell; q++) cstart[q + 1] += cstart[q];
+    for (int64_t k = 0; k < N; k++) {
+        int64_t cell = ((cz[k] / s) * ncy + cy[k] / s) * ncx + cx[k] / s;
+        order[cstart[cell] + fill[cell]++] = k;
+    }
+    for (int64_t k = 0; k < N; k++) {
+        int64_t nlist = 0;
+        if (all_pairs) {
+            for (int64_t q = 0; q < N; q++) list[nlist++] = q;
+        } else {
+            int64_t kz = cz[k] / s, ky = cy[k] / s, kx = cx[k] / s;
+            for (int64_t dz = -1; dz <= 1; dz++)
+                for (int64_t dy = -1; dy <= 1; dy++)
+                    for (int64_t dx = -1; dx <= 1; dx++) {
+                        int64_t zz = kz + dz, yy = ky + dy, xx = kx + dx;
+                        if (zz < 0 || zz >= ncz || yy < 0 || yy >= ncy || xx < 0 || xx >= ncx) continue;
+                        int64_t cell = (zz * ncy + yy) * ncx + xx;
+                        for (int64_t j = cstart[cell]; j < cstart[cell + 1]; j++) list[nlist++] = order[j];
+                    }
+            qsort(list, (size_t)nlist, sizeof(int64_t), cmp_i64);   /* ascending particle key */
+        }
+        double As = 0.0, Bs = 0.0;
+        int32_t na = 0, nb = 0;
+        for (int64_t t = 0; t < nlist; t++) {
+            int64_t q = list[t];
+            int64_t ddz = cz[q] - cz[k], ddy = cy[q] - cy[k], ddx = cx[q] - cx[k];
+            int64_t d2 = ddz * ddz + ddy * ddy + ddx * ddx;
+            if (!((double)d2 < r2)) continue;
+            double K = orc_kernel_eq5(sqrt((double)d2), E, eps);
+            if (l[q] == l[k]) { As = As + K * dE[q]; na++; }
+            if (c[q] == l[k]) { Bs = Bs + K * dE[q]; nb++; }
+        }
+        double a = na ? As / (double)na : 0.0;
+        double b = nb ? Bs / (double)nb : 0.0;
+        g[k] = a - b;
+        if (A) A[k] = a;
+        if (B) B[k] = b;
+        if (nQ) nQ[k] = na;
+        if (nQp) nQp[k] = nb;
+    }
+    free(cz); free(cy); free(cx); free(cstart); free(order); free(fill); free(list);
+}
+
+/* ------------------------------------------------------------------ */
+/* Simple points by topological numbers (Bertrand & Malandain 1994).
+ * 2D, foreground 4 / background 8: T4 = number of 4-components of X in the
+ * 8-neighbourhood that contain a 4-neighbour of x; T8 = number of 8-components of
+ * the complement in the 8-neighbourhood. 3D, foreground 6 / background 26: T6 =
+ * number of 6-components of X in the 18-neighbourhood containing a 6-neighbour of
+ * x; T26 = number of 26-components of the complement in the 26-neighbourhood.
+ * x is simple iff both numbers are 1. Components are found by breadth-first
+ * search over the window cells. */
+static int count_components(int ncell, const int* member, const int (*pos)[3],
+                            int adjacency, const int* must_touch)
+{
+    int label[27];
+    int queue[27];
+    for (int i = 0; i < ncell; i++) label[i] = -1;
+    int ncomp = 0, counted = 0;
+    for (int s0 = 0; s0 < ncell; s0++) {
+        if (!member[s0] || label[s0] >= 0) continue;
+        int head = 0, tail = 0, touches = 0;
+        queue[tail++] = s0;
+        label[s0] = ncomp;
+        while (head < tail) {
+            int u = queue[head++];
+            if (must_touch && must_touch[u]) touches = 1;
+            for (int v = 0; v < ncell; v++) {
+                if (!member[v] || label[v] >= 0) continue;
+                int dz = abs(pos[u][0] - pos[v][0]), dy = abs(pos[u][1] - pos[v][1]), dx = abs(pos[u][2] - pos[v][2]);
+                int l1 = dz + dy + dx, linf = dz > dy ? (dz > dx ? dz : dx) : (dy > dx ? dy : dx);
+                int adj = adjacency == 6 || adjacency == 4 ? (l1 == 1) : (linf == 1);
+                if (adj) { label[v] = ncomp; queue[tail++] = v; }
+            }
+        }
+        ncomp++;
+        if (!must_touch || touches) counted++;
+    }
+    return counted;
+}
+
+int orc_simple_2d(const uint8_t* nb9)
+{
+    int pos[8][3], fg[8], bg[8], touch[8];
+    int k = 0;
+    for (int dy = -1; dy <= 1; dy++)
+        for (int dx = -1; dx <= 1; dx++) {
+            if (dy == 0 && dx == 0) continue;
+            pos[k][0] = 0; pos[k][1] = dy; pos[k][2] = dx;
+            int in = nb9[(dy + 1) * 3 + (dx + 1)] != 0;
+            fg[k] = in;
+            bg[k] = !in;
+            touch[k] = (abs(dy) + abs(dx)) == 1;
+            k++;
+        }
+    int t4 = count_components(8, fg, (const int (*)[3])pos, 4, touch);
+    int t8 = count_components(8, bg, (const int (*)[3])pos, 8, NULL);
+    return t4 == 1 && t8 == 1;
+}
+
+int orc_simple_3d(const uint8_t* nb27)
+{
+    int pos[26][3], fg18[26], bg[26], touch[26];
+    int k = 0;
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                if (dz == 0 && dy == 0 && dx == 0) continue;
+                pos[k][0] = dz; pos[k][1] = dy; pos[k][2] = dx;
+                int in = nb27[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] != 0;
+                int l1 = abs(dz) + abs(dy) + abs(dx);
+                fg18[k] = in && l1 <= 2;
+                bg[k] = !in;
+                touch[k] = l1 == 1;
+                k++;
+            }
+    int t6 = count_components(26, fg18, (const int (*)[3])pos, 6, touch);
+    int t26 = count_components(26, bg, (const int (*)[3])pos, 26, NULL);
+    return t6 == 1 && t26 == 1;
+}
+
+static int simple_for_label(const orc_params* p, const int32_t* L, uint32_t xi, int32_t lab)
+{
+    int64_t z, y, x;
+    coords(p, xi, &z, &y, &x);
+    uint8_t nb[27];
+    int k = 0;
+    int rz = p->ndim == 3 ? 1 : 0;
+    for (int dz = -rz; dz <= rz; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int64_t zz = z + dz, yy = y + dy, xx = x + dx;
+                int in = 0;
+                if (inside(p, zz, yy, xx)) in = L[(zz * p->H + yy) * p->W + xx] == lab;
+                nb[k++] = (uint8_t)in;
+            }
+    return p->ndim == 3 ? orc_simple_3d(nb) : orc_simple_2d(nb);
+}
+
+/* Topological control: foreground regions stay connected sets without new or lost
+ * holes; removal from l (l != 0) and addition to c (c != 0) must both be simple. */
+int orc_admissible(const orc_params* p, const int32_t* L, uint32_t xi, int32_t l, int32_t c)
+{
+    if (l != 0 && !simple_for_label(p, L, xi, l)) return 0;
+    if (c != 0 && !simple_for_label(p, L, xi, c)) return 0;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+typedef struct { double g; uint32_t idx; int32_t c; } cand_t;
+
+static int cmp_cand(const void* a, const void* b)
+{
+    const cand_t* x = (const cand_t*)a;
+    const cand_t* y = (const cand_t*)b;
+    if (x->g < y->g) return -1;
+    if (x->g > y->g) return 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+int64_t orc_select(const orc_params* p, const int32_t* L, int64_t N,
+                   const uint32_t* idx, const int32_t* l, const int32_t* c, const double* g,
+                   uint32_t* acc_idx, int32_t* acc_c, int64_t* n_candidates)
+{
+    cand_t* cand = (cand_t*)malloc(sizeof(cand_t) * (size_t)(N > 0 ? N : 1));
+    int64_t nc = 0;
+    int64_t k = 0;
+    while (k < N) {
+        int64_t e = k;
+        while (e < N && idx[e] == idx[k]) e++;
+        int64_t best = k;
+        for (int64_t j = k + 1; j < e; j++)
+            if (g[j] < g[best] || (g[j] == g[best] && c[j] < c[best])) best = j;
+        if (g[best] < 0.0 && orc_admissible(p, L, idx[best], l[best], c[best])) {
+            cand[nc].g = g[best];
+            cand[nc].idx = idx[best];
+            cand[nc].c = c[best];
+            nc++;
+        }
+        k = e;
+    }
+    if (n_candidates) *n_candidates = nc;
+    qsort(cand, (size_t)nc, sizeof(cand_t), cmp_cand);
+    int64_t npix = p->D * p->H * p->W;
+    uint8_t* taken = (uint8_t*)calloc((size_t)npix, 1);
+    int64_t na = 0;
+    int rz = p->ndim == 3 ? 1 : 0;
+    for (int64_t t = 0; t < nc; t++) {
+        int64_t z, y, x;
+        coords(p, cand[t].idx, &z, &y, &x);
+        int blocked = 0;
+        for (int dz = -rz; dz <= rz && !blocked; dz++)
+            for (int dy = -1; dy <= 1 && !blocked; dy++)
+                for (int dx = -1; dx <= 1 && !blocked; dx++) {
+                    int64_t zz = z + dz, yy = y + dy, xx = x + dx;
+                    if (inside(p, zz, yy, xx) && taken[(zz * p->H + yy) * p->W + xx]) blocked = 1;
+                }
+        if (blocked) continue;
+        taken[cand[t].idx] = 1;
+        if (acc_idx) acc_idx[na] = cand[t].idx;
+        if (acc_c) acc_c[na] = cand[t].c;
+        na++;
+    }
+    free(taken);
+    free(cand);
+    return na;
+}
+
+/* ------------------------------------------------------------------ */
+void orc_state_init(const orc_params* p, orc_state* st)
+{
+    st->mode = p->gradient == 0 ? 0 : 1;
+    st->converged = 0;
+    st->t = 0;
+    st->best_A = -1;
+    st->t_best = 0;
+}
+
+int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
+                orc_status* status, int64_t cap,
+                uint32_t* d_idx, int32_t* d_l, int32_t* d_c, double* d_dE, double* d_g)
+{
+    memset(status, 0, sizeof *status);
+    status->mode_used = st->mode;
+    if (st->converged) { status->converged = 1; st->t++; return 0; }
+    int M = p->nlabels;
+    int64_t npix = p->D * p->H * p->W;
+    int64_t* n = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
+    double* S = (double*)malloc(sizeof(double) * (size_t)M);
+    double* Q = (double*)malloc(sizeof(double) * (size_t)M);
+    orc_stats(p, I, L, n, S, Q);
+    int64_t N = orc_extract(p, L, NULL, NULL, NULL, 0);
+    size_t NN = (size_t)(N > 0 ? N : 1);
+    uint32_t* idx = (uint32_t*)malloc(sizeof(uint32_t) * NN);
+    int32_t* l = (int32_t*)malloc(sizeof(int32_t) * NN);
+    int32_t* c = (int32_t*)malloc(sizeof(int32_t) * NN);
+    double* dE = (double*)malloc(sizeof(double) * NN);
+    double* g = (double*)malloc(sizeof(double) * NN);
+    double* A = (double*)malloc(sizeof(double) * NN);
+    double* B = (double*)malloc(sizeof(double) * NN);
+    orc_extract(p, L, idx, l, c, N);
+    orc_energy(p, I, L, n, S, N, idx, l, c, dE);
+    if (st->mode == 0) {
+        orc_sobolev(p, N, idx, l, c, dE, 0, g, A, B, NULL, NULL);
+        for (int64_t k = 0; k < N; k++)
+            if (A[k] != 0.0 && B[k] != 0.0 && ((A[k] > 0.0) == (B[k] > 0.0))) status->n_osc++;
+    } else {
+        for (int64_t k = 0; k < N; k++) g[k] = dE[k];
+    }
+    uint32_t* acc_idx = (uint32_t*)malloc(sizeof(uint32_t) * NN);
+    int32_t* acc_c = (int32_t*)malloc(sizeof(int32_t) * NN);
+    int64_t ncand = 0;
+    int64_t na = orc_select(p, L, N, idx, l, c, g, acc_idx, acc_c, &ncand);
+    for (int64_t t = 0; t < na; t++) L[acc_idx[t]] = acc_c[t];
+    (void)npix;
+    status->n_particles = N;
+    status->n_candidates = ncand;
+    status->n_accepted = na;
+    if (d_idx || d_l || d_c || d_dE || d_g) {
+        for (int64_t k = 0; k < N && k < cap; k++) {
+            if (d_idx) d_idx[k] = idx[k];
+            if (d_l) d_l[k] = l[k];
+            if (d_c) d_c[k] = c[k];
+            if (d_dE) d_dE[k] = dE[k];
+            if (d_g) d_g[k] = g[k];
+        }
+    }
+    /* oscillation fallback and convergence */
+    if (st->best_A < 0 || na < st->best_A) { st->best_A = na; st->t_best = st->t; }
+    if (st->mode == 0 && p->osc_window > 0 && st->t - st->t_best >= p->osc_window) st->mode = 1;
+    if (status->mode_used == 1 && na == 0) st->converged = 1;
+    status->converged = st->converged;
+    st->t++;
+    free(n); free(S); free(Q); free(idx); free(l); free(c); free(dE); free(g); free(A); free(B);
+    free(acc_idx); free(acc_c);
+    return 0;
+}

@@ -1,0 +1,109 @@
+/* rc_oracle.h - CPU oracle for particle region competition with Sobolev gradients.
+ *
+ * TEST INFRASTRUCTURE ONLY. This plain, slow, single-threaded FP64 implementation
+ * of one iteration of the method of Sbalzarini, Schneider & Cardinale, "Particle
+ * methods enable fast and simple approximation of Sobolev gradients in image
+ * segmentation" (arXiv:1403.0240) exists to check the CUDA path. Only the tests,
+ * the smoke check and the benchmark's CPU-baseline leg may load it. It shares no
+ * code, header, table or constant with the CUDA library.
+ *
+ * Parity status of each function (what pins it, in tests/test_oracle_*.py):
+ *   orc_kernel_eq5      - Eq. 5; pinned by the closed form at eps = 1/24, the
+ *                         Figure 2 axis ticks, the vanishing at r = +-E/2, unit mass.
+ *   orc_extract         - particles on both sides of the contour (Fig. 1); pinned
+ *                         by the 64x64 square count (252 inner + 256 outer) and a
+ *                         numpy brute-force neighbour scan.
+ *   orc_stats           - exact region sums rounded once; pinned by math.fsum,
+ *                         fractions.Fraction and the partition invariants.
+ *   orc_energy (PC)     - exact single-flip SSE change; pinned by a brute-force
+ *                         recompute of the total SSE before and after the flip.
+ *   orc_energy (PS)     - local-mean difference; pinned by scipy.ndimage
+ *                         convolutions and by the R -> infinity limit.
+ *   orc_energy (length) - pinned by a brute-force recount of the perimeter.
+ *   orc_sobolev         - Eq. 6 with a cell list; pinned by all-pairs brute force,
+ *                         the degenerate cutoff, and a hand-computed straight line.
+ *   orc_simple_2d/3d    - topological numbers; pinned by Yokoi's formula (2D) and
+ *                         global component / Euler-characteristic counts (2D, 3D).
+ *   orc_select          - ranked greedy selection; pinned by an independent
+ *                         local-minimum-rounds evaluation and permutation tests.
+ *   orc_iterate         - composition of the above; pinned by the partition and
+ *                         connectivity invariants after every iteration.
+ */
+#ifndef RC_ORACLE_H
+#define RC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t ndim;        /* 2 | 3 */
+    int32_t dtype;       /* 0 = float32 image, 1 = uint16 image */
+    int64_t D, H, W;     /* D = 1 in 2D; row-major, x fastest */
+    int32_t model;       /* 0 = piecewise constant, 1 = piecewise smooth */
+    int32_t conn;        /* foreground connectivity: 4 (2D) | 6 (3D) */
+    double lambda;       /* length weight (Eq. 10) */
+    double cutoff;       /* interaction cutoff E/2 in pixels */
+    double ps_radius;    /* local-mean radius R (piecewise smooth) */
+    int32_t gradient;    /* 0 = Sobolev (Eq. 6), 1 = L2 */
+    int32_t osc_window;  /* iterations without a new minimum of accepted moves before switching to L2; 0 = never */
+    int32_t nlabels;     /* M: labels are 0..M-1 */
+    int32_t pad_;
+} orc_params;
+
+typedef struct {
+    int32_t mode;        /* 0 = Sobolev, 1 = L2 */
+    int32_t converged;
+    int64_t t;           /* iterations done */
+    int64_t best_A;      /* smallest accepted-move count so far, -1 before the first iteration */
+    int64_t t_best;      /* first iteration at which best_A was reached */
+} orc_state;
+
+typedef struct {
+    int64_t n_particles;
+    int64_t n_candidates;
+    int64_t n_accepted;
+    int64_t n_osc;       /* particles whose two Eq. 6 terms are non-zero with equal sign */
+    int32_t mode_used;
+    int32_t converged;
+} orc_status;
+
+double  orc_kernel_eq5(double r, double E, double eps);
+
+int64_t orc_extract(const orc_params* p, const int32_t* L,
+                    uint32_t* idx, int32_t* l, int32_t* c, int64_t cap);
+
+double  orc_exact_sum_f32(const float* v, int64_t n, int squares);
+
+void    orc_stats(const orc_params* p, const void* I, const int32_t* L,
+                  int64_t* n, double* S, double* Q);
+
+void    orc_energy(const orc_params* p, const void* I, const int32_t* L,
+                   const int64_t* n, const double* S, int64_t N,
+                   const uint32_t* idx, const int32_t* l, const int32_t* c, double* dE);
+
+int64_t orc_delta_perimeter(const orc_params* p, const int32_t* L, uint32_t x, int32_t l, int32_t c);
+
+void    orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int32_t* l,
+                    const int32_t* c, const double* dE, int all_pairs,
+                    double* g, double* A, double* B, int32_t* nQ, int32_t* nQp);
+
+int     orc_simple_2d(const uint8_t* nb9);
+int     orc_simple_3d(const uint8_t* nb27);
+int     orc_admissible(const orc_params* p, const int32_t* L, uint32_t x, int32_t l, int32_t c);
+
+int64_t orc_select(const orc_params* p, const int32_t* L, int64_t N,
+                   const uint32_t* idx, const int32_t* l, const int32_t* c, const double* g,
+                   uint32_t* acc_idx, int32_t* acc_c, int64_t* n_candidates);
+
+void    orc_state_init(const orc_params* p, orc_state* st);
+
+int     orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
+                    orc_status* status, int64_t cap,
+                    uint32_t* d_idx, int32_t* d_l, int32_t* d_c, double* d_dE, double* d_g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
