@@ -1,0 +1,182 @@
+/* seg.h - C-ABI of libseg: particle region-competition segmentation with
+ * particle-approximated Sobolev gradients on one CUDA GPU (sm_103a).
+ *
+ * Method: Sbalzarini, Schneider & Cardinale, "Particle methods enable fast and
+ * simple approximation of Sobolev gradients in image segmentation" (arXiv:1403.0240).
+ * One iteration (seg_step) does, entirely on the device:
+ *   1. particle extraction: every (pixel x, candidate label c) with c != L(x) the
+ *      label of a connectivity neighbour of x (Fig. 1; "Discrete particle
+ *      approximation"), binned into a cell list of edge >= E/2 ("cell lists");
+ *   2. the per-particle energy difference dE of moving x to c (Methods, Eq. 11):
+ *      piecewise-constant or piecewise-smooth data term plus lambda times the
+ *      change of the number of unlike neighbour pairs (length prior, Eq. 10);
+ *   3. the Sobolev gradient of Eq. 6 with the kernel of Eq. 5 (eps = 1/24,
+ *      E = 2 * cutoff), or dE itself in L2 mode;
+ *   4. ranking and moves: per pixel the smallest gradient is a candidate if it is
+ *      negative; candidates whose move keeps every foreground region's topology
+ *      (simple points, 4/8 in 2D, 6/26 in 3D) are accepted greedily in ascending
+ *      (gradient, pixel) order, none within Chebyshev distance 1 of another
+ *      ("The Region Competition (RC) algorithm": ranking makes the result
+ *      independent of particle order);
+ *   5. label update and exact region statistics (count, sum I, sum I^2; the
+ *      region mean is the piecewise-constant intensity, Methods);
+ *   6. the oscillation fallback to L2 gradients (Eq. 6 discussion).
+ * Gradients are computed in FP32 with a rigorous error bound; any ranking or sign
+ * decision the bound cannot certify is recomputed in FP64 in ascending particle
+ * key order, so labels are identical to an FP64 evaluation of the same rules.
+ *
+ * Conventions: every call returns SEG_OK (0) or a negative SEG_E* code; nothing
+ * aborts the process. Pointers marked "host or device" may point to host memory
+ * (pageable or pinned) or to device memory of the context's device; the library
+ * tells them apart with cudaPointerGetAttributes. The caller keeps ownership of
+ * everything it passes; the library copies inputs at seg_init and owns its
+ * device state until seg_destroy. A context is not thread-safe: use one context
+ * per host thread, or serialise calls. All work is ordered on the CUDA stream
+ * given at seg_init.
+ */
+#ifndef SEG_H
+#define SEG_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEG_OK        0
+#define SEG_EINVAL   -1   /* bad parameter, shape, label image or pointer */
+#define SEG_ENOMEM   -2   /* device memory (or the batch budget) exhausted */
+#define SEG_ECUDA    -3   /* a CUDA runtime call failed; see seg_last_cuda_error */
+#define SEG_ETIMEOUT -4   /* a bounded device-side wait gave up; the context is poisoned */
+#define SEG_ESTATE   -5   /* call not valid in the object's current state */
+
+enum { SEG_F32 = 0, SEG_U16 = 1 };                 /* image element type */
+enum { SEG_PC = 0, SEG_PS = 1 };                   /* piecewise constant / piecewise smooth */
+enum { SEG_SOBOLEV = 0, SEG_L2 = 1 };              /* gradient type at start */
+enum { SEG_STATS_EXACT = 0 };                      /* region sums exact, rounded once to FP64 */
+
+typedef struct seg_ctx seg_ctx;
+typedef struct seg_batch seg_batch;
+
+typedef struct {
+    int32_t ndim;          /* 2 | 3 */
+    int32_t dtype;         /* SEG_F32 | SEG_U16 */
+    int64_t shape[3];      /* {D, H, W}; D = 1 in 2D; row-major, x fastest; each >= 1, D*H*W < 2^31 */
+    int32_t model;         /* SEG_PC | SEG_PS */
+    int32_t connectivity;  /* foreground: 4 (2D) | 6 (3D); background uses 8 | 26 */
+    double  lambda;        /* length weight (Eq. 10), >= 0 */
+    double  cutoff;        /* interaction cutoff E/2 in pixels, > 0; E = 2 * cutoff, eps = 1/24 */
+    double  ps_radius;     /* local-mean radius R for SEG_PS, >= 1 */
+    int32_t gradient;      /* SEG_SOBOLEV | SEG_L2 */
+    int32_t osc_window;    /* switch to L2 once the accepted-move count has not reached a new
+                              minimum for this many iterations; 0 = never switch */
+    int32_t stats_mode;    /* SEG_STATS_EXACT */
+    int32_t validate;      /* nonzero: check on the host that every foreground label of labels0
+                              is one connected component (else SEG_EINVAL) */
+    int32_t cell_edge;     /* cell-list edge in pixels, >= ceil(cutoff); 0 = ceil(cutoff) */
+    int32_t reserved[7];   /* must be zero */
+} seg_params;
+
+typedef struct {
+    int64_t iteration;     /* index of the iteration this status describes (0-based) */
+    int64_t n_particles;
+    int64_t n_candidates;  /* pixels whose best particle is negative and topology-admissible */
+    int64_t n_accepted;    /* moves executed */
+    int64_t n_osc;         /* particles whose two Eq. 6 terms are non-zero with equal sign (FP32) */
+    int64_t n_fixup;       /* particles whose gradient was recomputed in FP64 */
+    int32_t mode_used;     /* SEG_SOBOLEV | SEG_L2 */
+    int32_t converged;     /* an L2 iteration accepted no move; later iterations do nothing */
+    int32_t mis_rounds;    /* rounds of the parallel ranked selection */
+    int32_t error;         /* 0, or a SEG_E* code raised on the device */
+} seg_status;
+
+typedef struct {
+    int64_t t;             /* iterations done */
+    int64_t best_A;        /* smallest accepted-move count so far (-1 before the first iteration) */
+    int64_t t_best;        /* iteration at which best_A was first reached */
+    int32_t mode;          /* SEG_SOBOLEV | SEG_L2 */
+    int32_t converged;
+} seg_state;
+
+/* Particle arrays of the most recent iteration, in the library's internal order
+ * (cell-major; sort by (idx, c) to get key order). Each pointer may be NULL (not
+ * copied), host or device. */
+typedef struct {
+    uint32_t* idx;         /* linear pixel index (z*H + y)*W + x */
+    int32_t*  l;           /* current label of the pixel */
+    int32_t*  c;           /* candidate label */
+    float*    dE;          /* L2 energy difference (FP32) */
+    float*    eE;          /* bound on |dE - dE_fp64| */
+    float*    g;           /* gradient used for ranking: Eq. 6 in Sobolev mode, dE in L2 mode */
+    float*    eg;          /* bound on |g - g_fp64| */
+    double*   key;         /* ranking key: the FP64 value where recomputed, else g */
+    uint8_t*  flags;       /* bit 0 recomputed in FP64, bit 1 pixel candidate, bit 2 accepted */
+} seg_particle_buffers;
+
+/* Bytes of device memory seg_init will allocate for these parameters (particle
+ * capacity at its initial size). Returns SEG_EINVAL for invalid parameters. */
+int seg_estimate_bytes(const seg_params* p, int32_t nlabels, size_t* bytes);
+
+/* Create a context: validates p, copies image (dtype elements, D*H*W, host or
+ * device) and labels0 (int32 >= 0, host or device; 0 = background), computes the
+ * exact region statistics. cuda_stream is a cudaStream_t (NULL = the legacy default
+ * stream) on the current device. Errors: SEG_EINVAL (parameters, shape, negative
+ * labels, non-finite image values, a disconnected foreground label when
+ * p->validate), SEG_ENOMEM, SEG_ECUDA. On error *out is NULL. */
+int seg_init(const seg_params* p, const void* image, const int32_t* labels0,
+             void* cuda_stream, seg_ctx** out);
+
+/* Run iters iterations (iters >= 0) on the context's stream, replaying one
+ * captured CUDA graph per iteration, and wait for them. If out is not NULL it
+ * receives the status of the last iteration. Returns the device error code if
+ * one was raised (SEG_ETIMEOUT), SEG_ECUDA on a runtime failure. */
+int seg_step(seg_ctx* c, int32_t iters, seg_status* out);
+
+/* Copy the current label image (D*H*W int32) to out (host or device); n_out is
+ * the element capacity of out (SEG_EINVAL if too small). Synchronises the stream. */
+int seg_labels(seg_ctx* c, int32_t* out, size_t n_out);
+
+/* Copy the particle arrays of the most recent iteration (up to cap entries) and
+ * store their count in *n. Synchronises the stream. */
+int seg_particles(seg_ctx* c, const seg_particle_buffers* out, int64_t cap, int64_t* n);
+
+/* Region statistics for labels 0..max_labels-1 (host arrays, each may be NULL):
+ * count, sum of I and sum of I^2 over the region, exact and rounded once. */
+int seg_stats(seg_ctx* c, int64_t* n, double* S, double* Q, int32_t max_labels);
+
+/* Optimiser state for checkpointing; seg_set_state restores it after a seg_init
+ * from the saved labels, so that the next iterations repeat bit for bit. */
+int seg_get_state(seg_ctx* c, seg_state* out);
+int seg_set_state(seg_ctx* c, const seg_state* in);
+
+/* Number of labels M (max label of labels0 + 1) and the image shape. */
+int seg_info(seg_ctx* c, int32_t* nlabels, int64_t shape[3]);
+
+void seg_destroy(seg_ctx* c);
+
+/* Batching: contexts on the same device stepped together, one launch per stage
+ * for all of them (continuous batching adds and removes contexts between steps).
+ * The batch does not own the contexts; a context belongs to at most one batch. */
+int seg_batch_create(void* cuda_stream, seg_batch** out);
+int seg_batch_add(seg_batch* b, seg_ctx* c);
+int seg_batch_remove(seg_batch* b, seg_ctx* c);
+int seg_batch_size(seg_batch* b);
+/* Run iters iterations of every context in the batch; statuses (may be NULL)
+ * receives one seg_status per context in the order they were added. */
+int seg_batch_step(seg_batch* b, int32_t iters, seg_status* statuses, int32_t n_statuses);
+void seg_batch_destroy(seg_batch* b);
+
+/* Test hook: the device's simple-point test on n neighbourhood bitmasks (host arrays).
+ * Bit k of masks[i] is neighbour k of the 3x3 (2D, 8 bits) or 3x3x3 (3D, 26 bits) window
+ * in row-major order with the centre left out; out[i] = 1 if the centre is a simple
+ * point (4/8 in 2D, 6/26 in 3D). */
+int seg_debug_simple(int32_t ndim, const uint32_t* masks, int32_t n, uint8_t* out);
+
+const char* seg_strerror(int code);
+/* Text of the last CUDA error this thread saw inside libseg ("" if none). */
+const char* seg_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,809 @@
+// Decision kernels of one iteration: certification of float32 decisions, the FP64
+// recompute of uncertified gradients, candidate selection with topology control,
+// and the cooperative commit (ranked conflict-free selection, label update, exact
+// region statistics, oscillation fallback).
+#include "seg_internal.cuh"
+
+namespace segk {
+
+// ---------------------------------------------------------------------------
+// Simple points by topological numbers (Bertrand & Malandain): bitmask flood fills
+// over the 8 (2D) or 26 (3D) neighbour positions, row-major order without the centre.
+struct TopoTables {
+    unsigned adjF[2][26];   // foreground adjacency: 4 (2D) | 6 (3D)
+    unsigned adjB[2][26];   // background adjacency: 8 (2D) | 26 (3D)
+    unsigned nF[2];         // neighbourhood of the foreground count: N8* (2D) | N18* (3D)
+    unsigned touch[2];      // 4- | 6-neighbours of the centre
+    unsigned all[2];
+    int npos[2];
+};
+__constant__ TopoTables c_topo;
+
+cudaError_t topology_tables_init()
+{
+    TopoTables t;
+    memset(&t, 0, sizeof t);
+    for (int d = 0; d < 2; d++) {
+        int pos[26][3];
+        int n = 0;
+        for (int dz = (d ? -1 : 0); dz <= (d ? 1 : 0); dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    if (!dz && !dy && !dx) continue;
+                    pos[n][0] = dz; pos[n][1] = dy; pos[n][2] = dx;
+                    n++;
+                }
+        t.npos[d] = n;
+        t.all[d] = n == 32 ? 0xffffffffu : ((1u << n) - 1u);
+        for (int a = 0; a < n; a++) {
+            int l1 = abs(pos[a][0]) + abs(pos[a][1]) + abs(pos[a][2]);
+            if (l1 == 1) t.touch[d] |= 1u << a;
+            if (d == 0 || l1 <= 2) t.nF[d] |= 1u << a;
+            for (int b = 0; b < n; b++) {
+                if (a == b) continue;
+                int dz = abs(pos[a][0] - pos[b][0]), dy = abs(pos[a][1] - pos[b][1]), dx = abs(pos[a][2] - pos[b][2]);
+                int m1 = dz + dy + dx, mi = max(dz, max(dy, dx));
+                if (m1 == 1) t.adjF[d][a] |= 1u << b;
+                if (mi == 1) t.adjB[d][a] |= 1u << b;
+            }
+        }
+    }
+    return cudaMemcpyToSymbol(c_topo, &t, sizeof t);
+}
+
+// number of components of set S (adjacency adj) that meet `touch` (all if touch == 0); stops at 2
+__device__ __forceinline__ int components(unsigned S, const unsigned* adj, unsigned touch)
+{
+    int count = 0;
+    while (S) {
+        unsigned comp = S & (0u - S);
+        unsigned frontier = comp;
+        while (frontier) {
+            int a = __ffs(frontier) - 1;
+            frontier &= frontier - 1;
+            unsigned nb = adj[a] & S & ~comp;
+            comp |= nb;
+            frontier |= nb;
+        }
+        S &= ~comp;
+        if (!touch || (comp & touch)) {
+            if (++count > 1) return count;
+        }
+    }
+    return count;
+}
+
+__device__ __forceinline__ bool simple_mask(unsigned X, int d)
+{
+    const unsigned* aF = c_topo.adjF[d];
+    const unsigned* aB = c_topo.adjB[d];
+    if (components(X & c_topo.nF[d], aF, c_topo.touch[d]) != 1) return false;
+    return components(~X & c_topo.all[d], aB, 0u) == 1;
+}
+
+__device__ __forceinline__ unsigned label_mask(const Job& J, int x, int y, int z, int lab)
+{
+    unsigned m = 0;
+    int k = 0;
+    const int rz = J.ndim == 3 ? 1 : 0;
+    for (int dz = -rz; dz <= rz; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                if (!dz && !dy && !dx) continue;
+                int xx = x + dx, yy = y + dy, zz = z + dz;
+                if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D &&
+                    J.L[((long long)zz * J.H + yy) * J.W + xx] == lab)
+                    m |= 1u << k;
+                k++;
+            }
+    return m;
+}
+
+// Topological control: removal from l (foreground) and addition to c (foreground)
+// must both be simple, so regions neither split, vanish, merge nor change holes.
+__device__ __forceinline__ bool admissible(const Job& J, unsigned gi, int l, int c)
+{
+    int x = (int)(gi % (unsigned)J.W);
+    int y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
+    int z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+    int d = J.ndim == 3 ? 1 : 0;
+    if (l != 0 && !simple_mask(label_mask(J, x, y, z, l), d)) return false;
+    if (c != 0 && !simple_mask(label_mask(J, x, y, z, c), d)) return false;
+    return true;
+}
+
+__global__ void k_debug_simple(const unsigned* masks, int ndim, int n, unsigned char* out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = simple_mask(masks[i], ndim == 3 ? 1 : 0) ? 1 : 0;
+}
+
+cudaError_t launch_debug_simple(const unsigned* masks, int ndim, int n, unsigned char* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_debug_simple<<<(n + 255) / 256, 256, 0, s>>>(masks, ndim, n, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool job_idle(const Counters* c)
+{
+    return ld_volatile(&c->skip) != 0 || ld_volatile(&c->need) != 0;
+}
+
+__device__ __forceinline__ void coords(const Job& J, unsigned gi, int& x, int& y, int& z)
+{
+    x = (int)(gi % (unsigned)J.W);
+    y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
+    z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+}
+
+// Certification: a particle that could be negative (g < eg) is queued for the FP64
+// recompute when its sign, or its order against any other possibly-negative particle
+// at Chebyshev distance <= 1 (same pixel included), is not certified by the bounds.
+__global__ void __launch_bounds__(256) k_flag(Group g)
+{
+    const unsigned t = blockIdx.x;
+    const int gj = group_job_of_tile(g, t);
+    const Job& J = g.jobs[g.job_ids[gj]];
+    const unsigned k = t - g.tile_prefix[gj];
+    Counters* ctr = J.ctr;
+    if (job_idle(ctr)) return;
+    const unsigned pstart = J.tile_start[k], pcount = J.tile_count[k];
+    const unsigned tag = ld_volatile(&ctr->iter_tag);
+    const unsigned np = ld_volatile(&ctr->n_particles);
+    const int rz = J.ndim == 3 ? 1 : 0;
+    for (unsigned i = threadIdx.x; i < pcount; i += blockDim.x) {
+        const unsigned p = pstart + i;
+        const float gp = J.p_g[p], ep = J.p_eg[p];
+        J.p_key[p] = (double)gp;
+        if (!(gp < ep)) continue;
+        bool flag = fabsf(gp) <= ep;
+        if (!flag) {
+            int x, y, z;
+            coords(J, J.p_idx[p], x, y, z);
+            for (int dz = -rz; dz <= rz && !flag; dz++)
+                for (int dy = -1; dy <= 1 && !flag; dy++)
+                    for (int dx = -1; dx <= 1 && !flag; dx++) {
+                        int xx = x + dx, yy = y + dy, zz = z + dz;
+                        if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
+                        unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
+                        unsigned long long e = J.pmap[yi];
+                        if ((unsigned)(e >> 32) != tag) continue;
+                        for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi; q++) {
+                            if (q == p) continue;
+                            float gq = J.p_g[q], eq = J.p_eg[q];
+                            if (!(gq < eq)) continue;
+                            if (fabs((double)gp - (double)gq) <= (double)ep + (double)eq) { flag = true; break; }
+                        }
+                    }
+        }
+        if (flag) {
+            J.p_flags[p] |= kFlagFixup;
+            unsigned slot = atomicAdd(&ctr->n_flag, 1u);
+            J.flag_list[slot] = p;
+        }
+    }
+}
+
+cudaError_t launch_flag(const Group& g, cudaStream_t s)
+{
+    if (g.total_tiles == 0) return cudaSuccess;
+    k_flag<<<g.total_tiles, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 recompute in the order of the definition: every product and sum rounded
+// separately (no fused multiply-add), neighbours in ascending particle key.
+__device__ __forceinline__ double image64(const Job& J, long long i)
+{
+    if (J.dtype == SEG_F32) return (double)((const float*)J.I)[i];
+    return (double)((const unsigned short*)J.I)[i];
+}
+
+// Eq. 5 at eps = 1/24 in the order written: (1/E) (1 + ((r/E)^2 - r/E + 1/6) / (2 eps)).
+__device__ __forceinline__ double kernel64(int d2, double E)
+{
+    const double eps = 1.0 / 24.0;
+    double r = __dsqrt_rn((double)d2);
+    double x = __ddiv_rn(r, E);
+    double num = __dadd_rn(__dsub_rn(__dmul_rn(x, x), x), 1.0 / 6.0);
+    return __dmul_rn(__ddiv_rn(1.0, E), __dadd_rn(1.0, __ddiv_rn(num, __dmul_rn(2.0, eps))));
+}
+
+__device__ double energy64(const Job& J, unsigned gi, int l, int c)
+{
+    int x, y, z;
+    coords(J, gi, x, y, z);
+    const double v = image64(J, gi);
+    double data;
+    if (J.model == SEG_PC) {
+        double a = __dsub_rn(v, J.mu64[c]);
+        double b = __dsub_rn(v, J.mu64[l]);
+        double t1 = __dmul_rn(J.wp64[c], __dmul_rn(a, a));
+        double t2 = J.st_n[l] > 1 ? __dmul_rn(J.wm64[l], __dmul_rn(b, b)) : 0.0;
+        data = __dsub_rn(t1, t2);
+    } else {
+        double sc = 0.0, sl = 0.0;
+        long long cc = 0, cl = 0;
+        for (int u = 0; u < J.ps_n; u++) {
+            int4 d = J.ps_off[u];
+            int xx = x + d.z, yy = y + d.y, zz = z + d.x;
+            if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
+            long long j = ((long long)zz * J.H + yy) * J.W + xx;
+            int m = J.L[j];
+            if (m == c) { sc = __dadd_rn(sc, image64(J, j)); cc++; }
+            else if (m == l) { sl = __dadd_rn(sl, image64(J, j)); cl++; }
+        }
+        double a = __dsub_rn(v, __ddiv_rn(sc, (double)cc));
+        double b = __dsub_rn(v, __ddiv_rn(sl, (double)cl));
+        data = __dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+    }
+    int dP = 0;
+    const int nbz = J.ndim == 3 ? 1 : 0;
+    const int off[6][3] = {{0, 0, -1}, {0, 0, 1}, {0, -1, 0}, {0, 1, 0}, {-1, 0, 0}, {1, 0, 0}};
+    for (int u = 0; u < 4 + 2 * nbz; u++) {
+        int xx = x + off[u][2], yy = y + off[u][1], zz = z + off[u][0];
+        if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
+        int m = J.L[((long long)zz * J.H + yy) * J.W + xx];
+        dP += (int)(m != c) - (int)(m != l);
+    }
+    return __dadd_rn(data, __dmul_rn(J.lambda64, (double)dP));
+}
+
+constexpr int kFixWarps = 8;
+constexpr int kFixTerms = 32 * 6;
+
+__global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int njobs)
+{
+    __shared__ double s_t[kFixWarps][kFixTerms];
+    __shared__ unsigned char s_a[kFixWarps][kFixTerms];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned gw = blockIdx.x * kFixWarps + w, nw = gridDim.x * kFixWarps;
+    for (int j = 0; j < njobs; j++) {
+        const Job& J = jobs[j];
+        Counters* ctr = J.ctr;
+        if (job_idle(ctr)) continue;
+        const unsigned nf = ld_volatile(&ctr->n_flag);
+        const unsigned tag = ld_volatile(&ctr->iter_tag);
+        const unsigned np = ld_volatile(&ctr->n_particles);
+        const int mode = ld_volatile(&ctr->mode);
+        for (unsigned f = gw; f < nf; f += nw) {
+            const unsigned p = J.flag_list[f];
+            const unsigned gi = J.p_idx[p];
+            const int lp = J.p_l[p], cp = J.p_c[p];
+            double gval;
+            if (mode == SEG_L2) {
+                gval = lane == 0 ? energy64(J, gi, lp, cp) : 0.0;
+            } else {
+                int x, y, z;
+                coords(J, gi, x, y, z);
+                double As = 0.0, Bs = 0.0;
+                long long nA = 0, nB = 0;
+                for (int base = 0; base < J.nb_n; base += 32) {
+                    const int u = base + lane;
+                    double tv[6];
+                    unsigned char ta[6];
+                    int nt = 0;
+                    if (u < J.nb_n) {
+                        int4 d = J.nb_off[u];
+                        int xx = x + d.z, yy = y + d.y, zz = z + d.x;
+                        if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D) {
+                            unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
+                            unsigned long long e = J.pmap[yi];
+                            if ((unsigned)(e >> 32) == tag) {
+                                double K = kernel64(d.w, J.E);
+                                for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi && nt < 6; q++) {
+                                    int lq = J.p_l[q], cq = J.p_c[q];
+                                    if (lq == lp || cq == lp) {
+                                        tv[nt] = __dmul_rn(K, energy64(J, yi, lq, cq));
+                                        ta[nt] = lq == lp ? 1 : 0;
+                                        nt++;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    int incl = nt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                    for (int i = 0; i < nt; i++) {
+                        s_t[w][incl - nt + i] = tv[i];
+                        s_a[w][incl - nt + i] = ta[i];
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        for (int i = 0; i < tot; i++) {
+                            if (s_a[w][i]) { As = __dadd_rn(As, s_t[w][i]); nA++; }
+                            else { Bs = __dadd_rn(Bs, s_t[w][i]); nB++; }
+                        }
+                    }
+                    __syncwarp();
+                }
+                double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
+                double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
+                gval = __dsub_rn(A, B);
+            }
+            if (lane == 0) J.p_key[p] = gval;
+        }
+    }
+}
+
+cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s)
+{
+    if (njobs <= 0) return cudaSuccess;
+    k_fixup<<<sms * 2, kFixWarps * 32, 0, s>>>(jobs, njobs);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather_counters(const Job* jobs, int njobs, Counters* out)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < njobs) out[j] = *jobs[j].ctr;
+}
+
+cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cudaStream_t s)
+{
+    if (njobs <= 0) return cudaSuccess;
+    k_gather_counters<<<(njobs + 127) / 128, 128, 0, s>>>(jobs, njobs, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Candidates: per pixel the particle with the smallest (key, c); a candidate if its
+// key is negative and its move passes the topology tests.
+__global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
+{
+    const unsigned t = blockIdx.x;
+    if (t == 0 && threadIdx.x == 0) {
+        bc->bar_count = 0;
+        bc->err = 0;
+    }
+    const int gj = group_job_of_tile(g, t);
+    const Job& J = g.jobs[g.job_ids[gj]];
+    const unsigned k = t - g.tile_prefix[gj];
+    Counters* ctr = J.ctr;
+    if (job_idle(ctr)) return;
+    const unsigned pstart = J.tile_start[k], pend = pstart + J.tile_count[k];
+    for (unsigned p = pstart + threadIdx.x; p < pend; p += blockDim.x) {
+        const unsigned gi = J.p_idx[p];
+        if (p > pstart && J.p_idx[p - 1] == gi) continue;
+        unsigned best = p;
+        double bk = J.p_key[p];
+        int bc_ = J.p_c[p];
+        for (unsigned q = p + 1; q < pend && J.p_idx[q] == gi; q++) {
+            double kq = J.p_key[q];
+            int cq = J.p_c[q];
+            if (kq < bk || (kq == bk && cq < bc_)) { best = q; bk = kq; bc_ = cq; }
+        }
+        int slot = -1;
+        if (bk < 0.0 && admissible(J, gi, J.p_l[best], bc_)) {
+            slot = (int)atomicAdd(&ctr->n_cand, 1u);
+            J.c_best[slot] = (int)best;
+            J.c_key[slot] = bk;
+            J.c_pix[slot] = gi;
+            J.p_flags[best] |= kFlagCand;
+        }
+        J.pix_cand[p] = slot;
+    }
+}
+
+cudaError_t launch_select(const Group& g, BatchCtl* bc, cudaStream_t s)
+{
+    if (g.total_tiles == 0) return cudaSuccess;
+    k_select<<<g.total_tiles, 256, 0, s>>>(g, bc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Exact region statistics.
+__device__ __forceinline__ void f32_parts(float f, int& slot, long long& sm, unsigned long long& m2lo,
+                                          unsigned long long& m2hi)
+{
+    unsigned bits = __float_as_uint(f);
+    int eb = (int)((bits >> 23) & 0xffu);
+    unsigned long long m = bits & 0x7fffffu;
+    if (eb == 0) eb = 1; else m |= 0x800000ull;
+    slot = eb;
+    sm = (bits >> 31) ? -(long long)m : (long long)m;
+    unsigned long long sq = m * m;
+    m2lo = sq & 0xffffffull;
+    m2hi = sq >> 24;
+}
+
+__device__ __forceinline__ void atomic_add_ll(long long* a, long long v)
+{
+    atomicAdd((unsigned long long*)a, (unsigned long long)v);
+}
+
+// one pixel of value at index i joins (sign +1) or leaves (sign -1) label m
+__device__ __forceinline__ void stats_move(const Job& J, long long i, int m, int sign)
+{
+    atomic_add_ll(J.st_n + m, sign);
+    if (J.dtype == SEG_U16) {
+        long long v = ((const unsigned short*)J.I)[i];
+        atomic_add_ll(J.st_S + m, sign * v);
+        atomic_add_ll(J.st_Q + m, sign * v * v);
+    } else {
+        int slot;
+        long long sm;
+        unsigned long long lo, hi;
+        f32_parts(((const float*)J.I)[i], slot, sm, lo, hi);
+        if (sm == 0) return;
+        int k = slot - J.slot_lo;
+        atomic_add_ll(J.st_S + (long long)m * J.nS + k, sign * sm);
+        atomic_add_ll(J.st_Q + (long long)m * J.nQ + 2 * k, sign * (long long)lo);
+        atomic_add_ll(J.st_Q + (long long)m * J.nQ + 2 * k + 24, sign * (long long)hi);
+    }
+}
+
+// Round sum_k bins[k] * 2^(k + e0) (exactly) to the nearest double, ties to even.
+constexpr int kLimbs = 24;
+__device__ double round_bins(const long long* bins, int nb, int e0)
+{
+    long long lim[kLimbs];
+    for (int i = 0; i < kLimbs; i++) lim[i] = 0;
+    for (int k = 0; k < nb; k++) {
+        long long b = bins[k];
+        if (!b) continue;
+        int j = k >> 5, r = k & 31;
+        unsigned long long lo = (unsigned long long)(b & 0xffffffffLL) << r;
+        lim[j] += (long long)(lo & 0xffffffffull);
+        lim[j + 1] += (long long)(lo >> 32);
+        long long hs = (b >> 32) * (1LL << r);
+        lim[j + 1] += hs & 0xffffffffLL;
+        lim[j + 2] += hs >> 32;
+    }
+    long long carry = 0;
+    for (int i = 0; i < kLimbs; i++) {
+        long long t = lim[i] + carry;
+        lim[i] = t & 0xffffffffLL;
+        carry = t >> 32;
+    }
+    const bool neg = carry < 0;
+    if (neg) {
+        unsigned long long cy = 1;
+        for (int i = 0; i < kLimbs; i++) {
+            unsigned long long t = ((~(unsigned long long)lim[i]) & 0xffffffffull) + cy;
+            lim[i] = (long long)(t & 0xffffffffull);
+            cy = t >> 32;
+        }
+    }
+    int top = -1;
+    for (int i = kLimbs - 1; i >= 0; i--)
+        if (lim[i]) { top = i * 32 + 31 - __clz((unsigned)lim[i]); break; }
+    if (top < 0) return 0.0;
+    auto bit = [&](int b) -> unsigned long long { return ((unsigned long long)lim[b >> 5] >> (b & 31)) & 1ull; };
+    unsigned long long mant = 0;
+    int shift = 0;
+    if (top <= 52) {
+        for (int b = top; b >= 0; b--) mant = (mant << 1) | bit(b);
+    } else {
+        shift = top - 52;
+        for (int b = top; b >= shift; b--) mant = (mant << 1) | bit(b);
+        unsigned long long rb = bit(shift - 1);
+        bool sticky = false;
+        for (int b = shift - 2; b >= 0 && !sticky; b--) sticky = bit(b) != 0;
+        if (rb && (sticky || (mant & 1ull))) {
+            mant++;
+            if (mant == (1ull << 53)) { mant >>= 1; shift++; }
+        }
+    }
+    double v = ldexp((double)mant, shift + e0);
+    return neg ? -v : v;
+}
+
+__device__ void finalize_label(const Job& J, int m)
+{
+    long long n = J.st_n[m];
+    double S, Q;
+    if (J.dtype == SEG_U16) {
+        S = __ll2double_rn(J.st_S[m]);
+        Q = __ll2double_rn(J.st_Q[m]);
+    } else {
+        S = round_bins(J.st_S + (long long)m * J.nS, J.nS, J.slot_lo - 150);
+        Q = round_bins(J.st_Q + (long long)m * J.nQ, J.nQ, 2 * (J.slot_lo - 150));
+    }
+    const double dn = (double)n;
+    const double mu = n > 0 ? __ddiv_rn(S, dn) : 0.0;
+    const double wp = __ddiv_rn(dn, __dadd_rn(dn, 1.0));
+    const double wm = n > 1 ? __ddiv_rn(dn, __dsub_rn(dn, 1.0)) : 0.0;
+    J.S64[m] = S;
+    J.Q64[m] = Q;
+    J.mu64[m] = mu;
+    J.wp64[m] = wp;
+    J.wm64[m] = wm;
+    J.mu32[m] = __double2float_rn(mu);
+    J.wp32[m] = __double2float_rn(wp);
+    J.wm32[m] = __double2float_rn(wm);
+}
+
+// Initial statistics: warp-aggregated atomics keyed by (label, slot).
+__device__ __forceinline__ void warp_add(unsigned long long key, bool valid, long long val, long long* addr)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long k = valid ? key : ~0ull;
+    unsigned peers = __match_any_sync(0xffffffffu, k);
+    long long sum = 0;
+    for (int i = 0; i < 32; i++) {
+        long long v = __shfl_sync(0xffffffffu, val, i);
+        if ((peers >> i) & 1u) sum += v;
+    }
+    if (valid && lane == __ffs(peers) - 1 && sum) atomic_add_ll(addr, sum);
+}
+
+__global__ void __launch_bounds__(256) k_stats_init(const Job* jobs, int j)
+{
+    const Job& J = jobs[j];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n = J.npix;
+    const long long rounds = (n + stride - 1) / stride;
+    for (long long r = 0; r < rounds; r++) {
+        long long i = r * stride + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        bool valid = i < n;
+        int m = valid ? J.L[i] : 0;
+        warp_add((unsigned long long)m, valid, 1, J.st_n + m);
+        if (J.dtype == SEG_U16) {
+            long long v = valid ? ((const unsigned short*)J.I)[i] : 0;
+            warp_add((unsigned long long)m, valid, v, J.st_S + m);
+            warp_add((unsigned long long)m, valid, v * v, J.st_Q + m);
+        } else {
+            int slot = 0;
+            long long sm = 0;
+            unsigned long long lo = 0, hi = 0;
+            if (valid) f32_parts(((const float*)J.I)[i], slot, sm, lo, hi);
+            bool nz = valid && sm != 0;
+            int kk = nz ? slot - J.slot_lo : 0;
+            unsigned long long key = ((unsigned long long)m << 16) | (unsigned)kk;
+            warp_add(key, nz, sm, J.st_S + (long long)m * J.nS + kk);
+            warp_add(key, nz, (long long)lo, J.st_Q + (long long)m * J.nQ + 2 * kk);
+            warp_add(key, nz, (long long)hi, J.st_Q + (long long)m * J.nQ + 2 * kk + 24);
+        }
+    }
+}
+
+__global__ void k_stats_finalize(const Job* jobs, int njobs)
+{
+    for (int j = 0; j < njobs; j++) {
+        const Job& J = jobs[j];
+        for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < J.M; m += gridDim.x * blockDim.x) finalize_label(J, m);
+    }
+}
+
+cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = (npix + 255) / 256;
+    int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    if (grid < 1) grid = 1;
+    k_stats_init<<<grid, 256, 0, s>>>(jobs, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s)
+{
+    k_stats_finalize<<<64, 128, 0, s>>>(jobs, njobs);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Commit, one co-resident grid with bounded barriers:
+//  A. each candidate lists its neighbouring candidates (Chebyshev distance 1) with a
+//     smaller (key, pixel);
+//  B. rounds: a candidate is accepted once all smaller neighbours are rejected and
+//     rejected as soon as one is accepted; this equals the greedy pass in ascending
+//     (key, pixel) order, whatever the processing order;
+//  C. accepted moves update labels and the exact region sums;
+//  D. region tables, oscillation fallback, status, counters for the next iteration.
+__device__ __forceinline__ bool key_less(double ka, unsigned pa, double kb, unsigned pb)
+{
+    return ka < kb || (ka == kb && pa < pb);
+}
+
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* s_red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned tot = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) tot += s_red[i];
+    return tot;   // valid in thread 0
+}
+
+constexpr unsigned kMaxRounds = 1u << 20;
+
+__global__ void __launch_bounds__(512) k_commit(const Job* jobs, int njobs, BatchCtl* bc)
+{
+    __shared__ unsigned s_red[32];
+    const unsigned nblocks = gridDim.x;
+    const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    bool ok = true;
+
+    // A
+    for (int j = 0; j < njobs; j++) {
+        const Job& J = jobs[j];
+        Counters* ctr = J.ctr;
+        if (job_idle(ctr)) continue;
+        const unsigned nc = ld_volatile(&ctr->n_cand);
+        const unsigned tag = ld_volatile(&ctr->iter_tag);
+        const int rz = J.ndim == 3 ? 1 : 0;
+        for (unsigned s = gtid; s < nc; s += gstride) {
+            const unsigned gi = J.c_pix[s];
+            const double ks = J.c_key[s];
+            int x, y, z;
+            coords(J, gi, x, y, z);
+            int n = 0;
+            for (int dz = -rz; dz <= rz; dz++)
+                for (int dy = -1; dy <= 1; dy++)
+                    for (int dx = -1; dx <= 1; dx++) {
+                        if (!dz && !dy && !dx) continue;
+                        int xx = x + dx, yy = y + dy, zz = z + dz;
+                        if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
+                        unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
+                        unsigned long long e = J.pmap[yi];
+                        if ((unsigned)(e >> 32) != tag) continue;
+                        int o = J.pix_cand[(unsigned)e];
+                        if (o < 0) continue;
+                        if (key_less(J.c_key[o], J.c_pix[o], ks, gi)) J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
+                    }
+            J.c_nnbr[s] = n;
+            J.c_state[s] = kUndecided;
+        }
+    }
+    ok = grid_barrier(bc, nblocks);
+
+    // B
+    unsigned rounds = 0;
+    if (ok) {
+        for (unsigned r = 0;; r++) {
+            unsigned undecided = 0;
+            for (int j = 0; j < njobs; j++) {
+                const Job& J = jobs[j];
+                Counters* ctr = J.ctr;
+                if (job_idle(ctr)) continue;
+                const unsigned nc = ld_volatile(&ctr->n_cand);
+                for (unsigned s = gtid; s < nc; s += gstride) {
+                    if (ld_volatile(J.c_state + s) != kUndecided) continue;
+                    const int n = J.c_nnbr[s];
+                    bool any_acc = false, all_rej = true;
+                    for (int i = 0; i < n; i++) {
+                        int st = ld_volatile(J.c_state + J.c_nbr[(long long)s * J.nbr_stride + i]);
+                        if (st == kAccepted) { any_acc = true; break; }
+                        if (st != kRejected) all_rej = false;
+                    }
+                    if (any_acc) *(volatile int*)(J.c_state + s) = kRejected;
+                    else if (all_rej) *(volatile int*)(J.c_state + s) = kAccepted;
+                    else undecided++;
+                }
+            }
+            unsigned bs = block_sum(undecided, s_red);
+            if (threadIdx.x == 0) {
+                if (bs) atomicAdd(&bc->rounds_cnt[r % 3], bs);
+                if (blockIdx.x == 0) bc->rounds_cnt[(r + 1) % 3] = 0;
+            }
+            if (!grid_barrier(bc, nblocks)) { ok = false; break; }
+            unsigned rem = ld_volatile(&bc->rounds_cnt[r % 3]);
+            if (rem == 0) { rounds = r + 1; break; }
+            if (r + 1 >= kMaxRounds) {
+                if (gtid == 0) atomicExch(&bc->err, SEG_ETIMEOUT);
+                ok = false;
+                break;
+            }
+        }
+    }
+
+    // C
+    if (ok) {
+        for (int j = 0; j < njobs; j++) {
+            const Job& J = jobs[j];
+            Counters* ctr = J.ctr;
+            if (job_idle(ctr)) continue;
+            const unsigned nc = ld_volatile(&ctr->n_cand);
+            unsigned acc = 0;
+            for (unsigned s = gtid; s < nc; s += gstride) {
+                if (J.c_state[s] != kAccepted) continue;
+                const int p = J.c_best[s];
+                const unsigned gi = J.c_pix[s];
+                const int l = J.p_l[p], c = J.p_c[p];
+                J.L[gi] = c;
+                J.p_flags[p] |= kFlagAcc;
+                stats_move(J, gi, l, -1);
+                stats_move(J, gi, c, +1);
+                acc++;
+            }
+            unsigned bs = block_sum(acc, s_red);
+            if (threadIdx.x == 0 && bs) atomicAdd(&ctr->n_accepted, bs);
+        }
+        ok = grid_barrier(bc, nblocks);
+    }
+
+    // D
+    for (int j = 0; j < njobs; j++) {
+        const Job& J = jobs[j];
+        if (ok && !job_idle(J.ctr))
+            for (int m = (int)gtid; m < J.M; m += (int)gstride) finalize_label(J, m);
+    }
+    for (int j = (int)gtid; j < njobs; j += (int)gstride) {
+        const Job& J = jobs[j];
+        Counters* c = J.ctr;
+        if (!ok) atomicExch(&c->error, ld_volatile(&bc->err) ? ld_volatile(&bc->err) : SEG_ETIMEOUT);
+        if (c->error || c->need) {
+            c->skip = 1;
+            c->last.error = c->error;
+            continue;
+        }
+        if (c->converged) {
+            c->last.iteration = c->t;
+            c->last.n_particles = 0;
+            c->last.n_candidates = 0;
+            c->last.n_accepted = 0;
+            c->last.n_osc = 0;
+            c->last.n_fixup = 0;
+            c->last.mode_used = c->mode;
+            c->last.converged = 1;
+            c->last.mis_rounds = 0;
+            c->t++;
+            continue;
+        }
+        const long long A = c->n_accepted;
+        const int used = c->mode;
+        if (c->best_A < 0 || A < c->best_A) { c->best_A = A; c->t_best = c->t; }
+        if (c->mode == SEG_SOBOLEV && J.osc_window > 0 && c->t - c->t_best >= J.osc_window) c->mode = SEG_L2;
+        if (used == SEG_L2 && A == 0) c->converged = 1;
+        c->last.iteration = c->t;
+        c->last.n_particles = c->n_particles;
+        c->last.n_candidates = c->n_cand;
+        c->last.n_accepted = A;
+        c->last.n_osc = used == SEG_SOBOLEV ? c->n_osc : 0;
+        c->last.n_fixup = c->n_flag;
+        c->last.mode_used = used;
+        c->last.converged = c->converged;
+        c->last.mis_rounds = (int)rounds;
+        c->last.error = 0;
+        c->t++;
+        c->iter_tag++;
+        c->n_flag = 0;
+        c->n_cand = 0;
+        c->n_accepted = 0;
+        c->n_osc = 0;
+        c->skip = c->converged;
+    }
+    if (gtid == 0) {
+        bc->ticket[0] = 0;
+        bc->ticket[1] = 0;
+        bc->rounds_cnt[0] = 0;
+        bc->rounds_cnt[1] = 0;
+        bc->rounds_cnt[2] = 0;
+    }
+}
+
+cudaError_t commit_occupancy(int block, int* blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_commit, block, 0);
+}
+
+cudaError_t launch_commit(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_commit, jobs, njobs, bc);
+}
+
+}  // namespace segk

@@ -1,0 +1,549 @@
+// Tile kernels of one iteration: particle extraction fused with the energy
+// difference, and the Sobolev interaction of Eq. 6 over a cell tile.
+#include <algorithm>
+
+#include "seg_internal.cuh"
+
+namespace segk {
+
+constexpr int kBlock = 256;
+constexpr float kU = 1.1920929e-7f;          // 2^-23: twice the float32 unit roundoff
+constexpr float kFp64Margin = 1e-12f;        // covers the FP64 evaluation's own rounding
+
+__device__ __forceinline__ float gamma_n(int n)
+{
+    float t = (float)n * 5.9604645e-8f;      // n * 2^-24
+    return t / (1.0f - t);
+}
+
+struct TileBox {
+    int x0, x1, y0, y1, z0, z1;   // pixel box of the tile
+    int cx0, cy0, cz0;            // first cell
+    int ccx, ccy, ccz;            // cells in the tile
+};
+
+__device__ __forceinline__ TileBox tile_box(const Job& J, unsigned k)
+{
+    TileBox b;
+    int tx = (int)(k % (unsigned)J.ntx);
+    int ty = (int)((k / (unsigned)J.ntx) % (unsigned)J.nty);
+    int tz = (int)(k / ((unsigned)J.ntx * (unsigned)J.nty));
+    int s = J.cell, sz = J.ndim == 3 ? J.cell : 1;
+    b.cx0 = tx * J.tcx; b.cy0 = ty * J.tcy; b.cz0 = tz * J.tcz;
+    b.ccx = min(J.tcx, J.ncx - b.cx0);
+    b.ccy = min(J.tcy, J.ncy - b.cy0);
+    b.ccz = min(J.tcz, J.ncz - b.cz0);
+    b.x0 = b.cx0 * s; b.x1 = min(J.W, (b.cx0 + b.ccx) * s);
+    b.y0 = b.cy0 * s; b.y1 = min(J.H, (b.cy0 + b.ccy) * s);
+    b.z0 = b.cz0 * sz; b.z1 = min(J.D, (b.cz0 + b.ccz) * sz);
+    return b;
+}
+
+// --------------------------------------------------------------------------
+// Block-wide exclusive scan of one unsigned per thread.
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* s_warp, unsigned& total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        unsigned a = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, a, o);
+            if (lane >= o) a += y;
+        }
+        if (lane < nw) s_warp[lane] = a;       // inclusive warp totals
+    }
+    __syncthreads();
+    unsigned before = w > 0 ? s_warp[w - 1] : 0u;
+    total = s_warp[(blockDim.x >> 5) - 1];
+    return before + x - v;
+}
+
+// --------------------------------------------------------------------------
+// Energy difference of moving a pixel of value v from label l to c (Methods, Eq. 11),
+// piecewise-constant data term: the exact single-pixel change of the sum of squared
+// deviations from the region means, plus lambda * change of unlike neighbour pairs.
+// Returns dE in float and a bound on |dE - dE_fp64|.
+__device__ __forceinline__ void energy_pc(const Job& J, float v, int l, int c, int dP, float& dE, float& eE)
+{
+    float mc = __ldg(J.mu32 + c), ml = __ldg(J.mu32 + l);
+    float a = v - mc, b = v - ml;
+    float ea = kU * (fabsf(mc) + fabsf(a));
+    float eb = kU * (fabsf(ml) + fabsf(b));
+    float aa = a * a, bb = b * b;
+    float eaa = (2.0f * fabsf(a) + ea) * ea + kU * aa;
+    float ebb = (2.0f * fabsf(b) + eb) * eb + kU * bb;
+    float wp = __ldg(J.wp32 + c), wm = __ldg(J.wm32 + l);
+    float t1 = wp * aa, t2 = wm * bb;
+    float et1 = wp * eaa * 1.0001f + kU * t1;
+    float et2 = wm * ebb * 1.0001f + kU * t2;
+    float d = t1 - t2;
+    float lp = J.lambda32 * (float)dP;
+    dE = d + lp;
+    float err = et1 + et2 + kU * (fabsf(d) + fabsf(lp) + fabsf(dE)) + kFp64Margin * (t1 + t2 + fabsf(lp));
+    eE = err * 1.001f;
+}
+
+// Piecewise-smooth data term from local means over the ball of radius R around x,
+// x counted in its own label: (v - mu_c)^2 - (v - mu_l)^2.
+__device__ __forceinline__ void energy_ps_finish(const Job& J, float v, int dP, float sc, float ac, int cc,
+                                                 float sl, float al, int cl, float& dE, float& eE)
+{
+    float muc = sc / (float)cc, mul = sl / (float)cl;
+    float emc = gamma_n(cc) * ac / (float)cc + kU * fabsf(muc);
+    float eml = gamma_n(cl) * al / (float)cl + kU * fabsf(mul);
+    float a = v - muc, b = v - mul;
+    float ea = emc + kU * fabsf(a), eb = eml + kU * fabsf(b);
+    float aa = a * a, bb = b * b;
+    float eaa = (2.0f * fabsf(a) + ea) * ea + kU * aa;
+    float ebb = (2.0f * fabsf(b) + eb) * eb + kU * bb;
+    float d = aa - bb;
+    float lp = J.lambda32 * (float)dP;
+    dE = d + lp;
+    float mac = ac / (float)cc, mal = al / (float)cl;
+    float err = eaa + ebb + kU * (fabsf(d) + fabsf(lp) + fabsf(dE)) +
+                kFp64Margin * (aa + bb + fabsf(lp) + mac * mac + mal * mal + v * v);
+    eE = err * 1.001f;
+}
+
+__device__ __forceinline__ float image_at(const Job& J, long long i)
+{
+    if (J.dtype == SEG_F32) return __ldg((const float*)J.I + i);
+    return (float)__ldg((const unsigned short*)J.I + i);
+}
+
+// --------------------------------------------------------------------------
+// Extraction: one block per tile of cells, tiles taken in ticket order so that the
+// decoupled look-back only waits on tiles that have already started.
+template <int NDIM>
+__global__ void __launch_bounds__(kBlock) k_extract(Group g)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned s_ticket, s_base;
+    __shared__ unsigned s_warp[32];
+    const int tid = threadIdx.x;
+    if (tid == 0) s_ticket = atomicAdd(g.ticket, 1u);
+    __syncthreads();
+    const unsigned t = s_ticket;
+    const int gj = group_job_of_tile(g, t);
+    const Job& J = g.jobs[g.job_ids[gj]];
+    const unsigned k = t - g.tile_prefix[gj];
+    Counters* ctr = J.ctr;
+    if (ld_volatile(&ctr->skip)) return;
+    const unsigned tag = ld_volatile(&ctr->iter_tag);
+
+    const TileBox b = tile_box(J, k);
+    const int h = J.halo, hz = NDIM == 3 ? J.halo : 0;
+    const int bx = b.x1 - b.x0 + 2 * h, by = b.y1 - b.y0 + 2 * h, bz = b.z1 - b.z0 + 2 * hz;
+    const int nbox = bx * by * bz;
+    int* sL = (int*)smem;
+    float* sI = (float*)(sL + nbox);
+    const bool stage_img = J.ps_staged != 0;
+    // labels (and, for the 2D piecewise-smooth model, the image) with halo; -1 outside
+    for (int i = tid; i < nbox; i += blockDim.x) {
+        int lx = i % bx, ly = (i / bx) % by, lz = i / (bx * by);
+        int x = b.x0 - h + lx, y = b.y0 - h + ly, z = b.z0 - hz + lz;
+        int lab = -1;
+        float val = 0.0f;
+        if (x >= 0 && x < J.W && y >= 0 && y < J.H && z >= 0 && z < J.D) {
+            long long gi = ((long long)z * J.H + y) * J.W + x;
+            lab = __ldg(J.L + gi);
+            if (stage_img) val = image_at(J, gi);
+        }
+        sL[i] = lab;
+        if (stage_img) sI[i] = val;
+    }
+    __syncthreads();
+
+    const int s = J.cell, sz = NDIM == 3 ? J.cell : 1;
+    const int cellvol = s * s * sz;
+    const int ncell = b.ccx * b.ccy * b.ccz;
+    const int tile_q = ncell * cellvol;
+    const int chunk = (tile_q + blockDim.x - 1) / blockDim.x;
+    const int q0 = min(tid * chunk, tile_q), q1 = min(q0 + chunk, tile_q);
+    unsigned* s_cstart = (unsigned*)(sI + (stage_img ? nbox : 0));
+
+    auto pixel_of = [&](int q, int& x, int& y, int& z) -> bool {
+        int kc = q / cellvol, r = q - kc * cellvol;
+        int lx = kc % b.ccx, ly = (kc / b.ccx) % b.ccy, lz = kc / (b.ccx * b.ccy);
+        int rx = r % s, ry = (r / s) % s, rz = r / (s * s);
+        x = (b.cx0 + lx) * s + rx;
+        y = (b.cy0 + ly) * s + ry;
+        z = (b.cz0 + lz) * sz + rz;
+        return x < J.W && y < J.H && z < J.D;
+    };
+    auto sidx = [&](int x, int y, int z) -> int {
+        return ((z - b.z0 + hz) * by + (y - b.y0 + h)) * bx + (x - b.x0 + h);
+    };
+    // distinct neighbour labels different from the own label, ascending
+    auto particles_at = [&](int x, int y, int z, int* labs) -> int {
+        int si = sidx(x, y, z);
+        int own = sL[si];
+        int nb[6];
+        nb[0] = sL[si - 1];
+        nb[1] = sL[si + 1];
+        nb[2] = sL[si - bx];
+        nb[3] = sL[si + bx];
+        int nn = 4;
+        if (NDIM == 3) { nb[4] = sL[si - bx * by]; nb[5] = sL[si + bx * by]; nn = 6; }
+        int n = 0;
+        for (int j = 0; j < nn; j++) {
+            int m = nb[j];
+            if (m < 0 || m == own) continue;
+            bool seen = false;
+            for (int u = 0; u < n; u++) seen |= (labs[u] == m);
+            if (seen) continue;
+            int p = n++;
+            while (p > 0 && labs[p - 1] > m) { labs[p] = labs[p - 1]; p--; }
+            labs[p] = m;
+        }
+        return n;
+    };
+
+    unsigned cnt = 0;
+    for (int q = q0; q < q1; q++) {
+        int x, y, z, labs[6];
+        if (!pixel_of(q, x, y, z)) continue;
+        cnt += particles_at(x, y, z, labs);
+    }
+    unsigned total;
+    unsigned off = block_excl_scan(cnt, s_warp, total);
+
+    // decoupled look-back over the tiles of this job
+    if (tid == 0) {
+        const unsigned long long ep = (unsigned long long)(tag & 0x3fffffffu) << 34;
+        unsigned excl = 0;
+        if (k == 0) {
+            atomicExch(J.tile_word + 0, ep | (2ull << 32) | total);
+        } else {
+            atomicExch(J.tile_word + k, ep | (1ull << 32) | total);
+            long long i = (long long)k - 1;
+            unsigned spins = 0;
+            while (i >= 0) {
+                unsigned long long w = ld_volatile(J.tile_word + i);
+                unsigned st = (unsigned)((w >> 32) & 3u);
+                if ((w & ~((1ull << 34) - 1)) != ep || st == 0) {
+                    if (++spins > kSpinLimit) { atomicExch(&ctr->error, SEG_ETIMEOUT); break; }
+                    continue;
+                }
+                excl += (unsigned)w;
+                if (st == 2) break;
+                i--;
+            }
+            __threadfence();
+            atomicExch(J.tile_word + k, ep | (2ull << 32) | (excl + total));
+        }
+        s_base = excl;
+        J.tile_start[k] = excl;
+        J.tile_count[k] = total;
+        if (k == (unsigned)J.ntiles - 1) {
+            ctr->n_particles = excl + total;
+            if ((long long)excl + total > J.pcap) atomicMax(&ctr->need, excl + total);
+        }
+    }
+    __syncthreads();
+    const unsigned base = s_base;
+    const bool fits = (long long)base + total <= J.pcap;
+
+    // emit particles with their energy differences
+    unsigned o = base + off;
+    for (int q = q0; q < q1; q++) {
+        int x, y, z, labs[6];
+        if (q % cellvol == 0) s_cstart[q / cellvol] = o - base;
+        if (!pixel_of(q, x, y, z)) continue;
+        int n = particles_at(x, y, z, labs);
+        if (n == 0) continue;
+        const long long gi = ((long long)z * J.H + y) * J.W + x;
+        const int si = sidx(x, y, z);
+        const int own = sL[si];
+        const float v = stage_img ? sI[si] : image_at(J, gi);
+        int nb[6];
+        nb[0] = sL[si - 1]; nb[1] = sL[si + 1]; nb[2] = sL[si - bx]; nb[3] = sL[si + bx];
+        int nn = 4;
+        if (NDIM == 3) { nb[4] = sL[si - bx * by]; nb[5] = sL[si + bx * by]; nn = 6; }
+        if (fits) J.pmap[gi] = ((unsigned long long)tag << 32) | o;
+        for (int j = 0; j < n; j++, o++) {
+            const int c = labs[j];
+            int dP = 0;
+            for (int u = 0; u < nn; u++) {
+                int m = nb[u];
+                if (m < 0) continue;
+                dP += (int)(m != c) - (int)(m != own);
+            }
+            float dE, eE;
+            if (J.model == SEG_PC) {
+                energy_pc(J, v, own, c, dP, dE, eE);
+            } else {
+                float sc = 0.f, ac = 0.f, sl = 0.f, al = 0.f;
+                int cc = 0, cl = 0;
+                for (int u = 0; u < J.ps_n; u++) {
+                    int4 d = __ldg(J.ps_off + u);
+                    int yx = x + d.z, yy = y + d.y, yz = z + d.x;
+                    int m;
+                    float f;
+                    if (stage_img) {
+                        int sj = si + d.y * bx + d.z;
+                        m = sL[sj];
+                        f = sI[sj];
+                    } else {
+                        if (yx < 0 || yx >= J.W || yy < 0 || yy >= J.H || yz < 0 || yz >= J.D) continue;
+                        long long gj2 = ((long long)yz * J.H + yy) * J.W + yx;
+                        m = __ldg(J.L + gj2);
+                        f = image_at(J, gj2);
+                    }
+                    if (m == c) { sc += f; ac += fabsf(f); cc++; }
+                    else if (m == own) { sl += f; al += fabsf(f); cl++; }
+                }
+                energy_ps_finish(J, v, dP, sc, ac, cc, sl, al, cl, dE, eE);
+            }
+            if (fits) {
+                J.p_idx[o] = (unsigned)gi;
+                J.p_l[o] = own;
+                J.p_c[o] = c;
+                J.p_dE[o] = dE;
+                J.p_eE[o] = eE;
+                J.p_flags[o] = 0;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) s_cstart[ncell] = total;
+    __syncthreads();
+    for (int kc = tid; kc < ncell; kc += blockDim.x) {
+        int lx = kc % b.ccx, ly = (kc / b.ccx) % b.ccy, lz = kc / (b.ccx * b.ccy);
+        long long cid = ((long long)(b.cz0 + lz) * J.ncy + (b.cy0 + ly)) * J.ncx + (b.cx0 + lx);
+        J.cell_start[cid] = base + s_cstart[kc];
+        J.cell_count[cid] = s_cstart[kc + 1] - s_cstart[kc];
+    }
+}
+
+size_t extract_smem_bytes(const Job& J)
+{
+    int s = J.cell, sz = J.ndim == 3 ? J.cell : 1;
+    int h = J.halo, hz = J.ndim == 3 ? J.halo : 0;
+    long long bx = (long long)J.tcx * s + 2 * h, by = (long long)J.tcy * s + 2 * h, bz = (long long)J.tcz * sz + 2 * hz;
+    long long nbox = bx * by * bz;
+    bool img = J.ps_staged != 0;
+    long long ncell = (long long)J.tcx * J.tcy * J.tcz;
+    return (size_t)(nbox * 4 * (img ? 2 : 1) + (ncell + 1) * 4);
+}
+
+cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t st)
+{
+    if (g.total_tiles == 0) return cudaSuccess;
+    if (ndim == 2) k_extract<2><<<g.total_tiles, kBlock, smem, st>>>(g);
+    else k_extract<3><<<g.total_tiles, kBlock, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Sobolev interaction, Eq. 6: g_p = (1/|Q_p|) sum_{Q_p} K(d) dE_q - (1/|Q'_p|) sum_{Q'_p} K(d) dE_q,
+// Q_p = {q : d < E/2, l_q = l_p}, Q'_p = {q : d < E/2, c_q = l_p}; empty sets give 0.
+// The particles of the tile's cells and of a one-cell ring around them are staged in
+// shared memory (or read from global memory when they do not fit).
+constexpr int kStageCap = 3072;
+
+struct Staged {
+    unsigned pos;   // packed (z << 20) | (y << 10) | x relative to the staged box origin
+    int l, c;
+    float dE, eE;
+};
+
+template <int NDIM>
+__global__ void __launch_bounds__(kBlock) k_sobolev(Group g)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned s_warp[32];
+    __shared__ float s_klut[256];
+    __shared__ unsigned s_osc;
+    const int tid = threadIdx.x;
+    const unsigned t = blockIdx.x;
+    const int gj = group_job_of_tile(g, t);
+    const Job& J = g.jobs[g.job_ids[gj]];
+    const unsigned k = t - g.tile_prefix[gj];
+    Counters* ctr = J.ctr;
+    if (ld_volatile(&ctr->skip) || ld_volatile(&ctr->need)) return;
+    const unsigned pstart = J.tile_start[k], pcount = J.tile_count[k];
+    if (pcount == 0) return;
+    const int mode = ld_volatile(&ctr->mode);
+    if (mode == SEG_L2) {
+        for (unsigned i = tid; i < pcount; i += blockDim.x) {
+            J.p_g[pstart + i] = J.p_dE[pstart + i];
+            J.p_eg[pstart + i] = J.p_eE[pstart + i];
+        }
+        return;
+    }
+    const TileBox b = tile_box(J, k);
+    const int s = J.cell, sz = NDIM == 3 ? J.cell : 1;
+    // staged cell box: tile cells plus one ring
+    const int ex0 = max(b.cx0 - 1, 0), ex1 = min(b.cx0 + b.ccx + 1, J.ncx);
+    const int ey0 = max(b.cy0 - 1, 0), ey1 = min(b.cy0 + b.ccy + 1, J.ncy);
+    const int ez0 = NDIM == 3 ? max(b.cz0 - 1, 0) : b.cz0;
+    const int ez1 = NDIM == 3 ? min(b.cz0 + b.ccz + 1, J.ncz) : b.cz0 + b.ccz;
+    const int enx = ex1 - ex0, eny = ey1 - ey0, enz = ez1 - ez0;
+    const int ne = enx * eny * enz;
+    unsigned* s_eoff = (unsigned*)smem;                 // ne + 1 prefix of staged counts
+    Staged* sP = (Staged*)(s_eoff + ((ne + 2) & ~1));
+    const int ox = ex0 * s, oy = ey0 * s, oz = ez0 * sz;  // staged box origin (pixels)
+
+    // prefix over the staged cells (chunked per thread)
+    const int chunk = (ne + blockDim.x - 1) / blockDim.x;
+    const int e0 = min(tid * chunk, ne), e1 = min(e0 + chunk, ne);
+    unsigned cnt = 0;
+    for (int e = e0; e < e1; e++) {
+        int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
+        long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
+        cnt += J.cell_count[cid];
+    }
+    unsigned total;
+    unsigned off = block_excl_scan(cnt, s_warp, total);
+    for (int e = e0; e < e1; e++) {
+        int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
+        long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
+        s_eoff[e] = off;
+        off += J.cell_count[cid];
+    }
+    if (tid == 0) { s_eoff[ne] = total; s_osc = 0; }
+    for (int d2 = tid; d2 <= J.r2max && d2 < 256; d2 += blockDim.x) s_klut[d2] = __ldg(J.klut + d2);
+    __syncthreads();
+    const bool staged = total <= (unsigned)kStageCap && J.r2max < 256;
+    if (staged) {
+        for (unsigned i = tid; i < total; i += blockDim.x) {
+            int lo = 0, hi = ne - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (s_eoff[mid] <= i) lo = mid; else hi = mid - 1;
+            }
+            int e = lo;
+            int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
+            long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
+            unsigned p = J.cell_start[cid] + (i - s_eoff[e]);
+            unsigned gi = J.p_idx[p];
+            int x = (int)(gi % (unsigned)J.W);
+            int y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
+            int z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+            Staged sp;
+            sp.pos = ((unsigned)(z - oz) << 20) | ((unsigned)(y - oy) << 10) | (unsigned)(x - ox);
+            sp.l = J.p_l[p];
+            sp.c = J.p_c[p];
+            sp.dE = J.p_dE[p];
+            sp.eE = J.p_eE[p];
+            sP[i] = sp;
+        }
+    }
+    __syncthreads();
+
+    unsigned osc = 0;
+    for (unsigned i = tid; i < pcount; i += blockDim.x) {
+        const unsigned p = pstart + i;
+        const unsigned gi = J.p_idx[p];
+        const int x = (int)(gi % (unsigned)J.W);
+        const int y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
+        const int z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+        const int lp = J.p_l[p];
+        const int pcx = x / s, pcy = y / s, pcz = NDIM == 3 ? z / s : z;
+        float As = 0.f, Bs = 0.f, aA = 0.f, aB = 0.f, eAs = 0.f, eBs = 0.f;
+        int nA = 0, nB = 0;
+        for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); dz++) {
+            int cz = pcz + dz;
+            if (cz < ez0 || cz >= ez1) continue;
+            for (int dy = -1; dy <= 1; dy++) {
+                int cy = pcy + dy;
+                if (cy < ey0 || cy >= ey1) continue;
+                for (int dx = -1; dx <= 1; dx++) {
+                    int cx = pcx + dx;
+                    if (cx < ex0 || cx >= ex1) continue;
+                    int e = ((cz - ez0) * eny + (cy - ey0)) * enx + (cx - ex0);
+                    if (staged) {
+                        const unsigned e_lo = s_eoff[e], e_hi = s_eoff[e + 1];
+                        const unsigned mypos_x = (unsigned)(x - ox), mypos_y = (unsigned)(y - oy), mypos_z = (unsigned)(z - oz);
+                        for (unsigned j = e_lo; j < e_hi; j++) {
+                            const Staged q = sP[j];
+                            int ddx = (int)(q.pos & 1023u) - (int)mypos_x;
+                            int ddy = (int)((q.pos >> 10) & 1023u) - (int)mypos_y;
+                            int ddz = (int)(q.pos >> 20) - (int)mypos_z;
+                            int d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            if (d2 > J.r2max) continue;
+                            float K = s_klut[d2];
+                            if (q.l == lp) {
+                                float w = K * q.dE;
+                                As += w; aA += fabsf(w); eAs += K * q.eE; nA++;
+                            } else if (q.c == lp) {
+                                float w = K * q.dE;
+                                Bs += w; aB += fabsf(w); eBs += K * q.eE; nB++;
+                            }
+                        }
+                    } else {
+                        long long cid = ((long long)cz * J.ncy + cy) * J.ncx + cx;
+                        const unsigned c0 = J.cell_start[cid], c1 = c0 + J.cell_count[cid];
+                        for (unsigned j = c0; j < c1; j++) {
+                            unsigned qi = J.p_idx[j];
+                            int qx = (int)(qi % (unsigned)J.W);
+                            int qy = (int)((qi / (unsigned)J.W) % (unsigned)J.H);
+                            int qz = (int)(qi / ((unsigned)J.W * (unsigned)J.H));
+                            int d2 = (qx - x) * (qx - x) + (qy - y) * (qy - y) + (qz - z) * (qz - z);
+                            if (d2 > J.r2max) continue;
+                            float K = __ldg(J.klut + d2);
+                            int ql = J.p_l[j], qc = J.p_c[j];
+                            if (ql == lp) {
+                                float w = K * J.p_dE[j];
+                                As += w; aA += fabsf(w); eAs += K * J.p_eE[j]; nA++;
+                            } else if (qc == lp) {
+                                float w = K * J.p_dE[j];
+                                Bs += w; aB += fabsf(w); eBs += K * J.p_eE[j]; nB++;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        float A = nA ? As / (float)nA : 0.f;
+        float B = nB ? Bs / (float)nB : 0.f;
+        float eA = nA ? ((eAs + (kU + gamma_n(nA)) * aA) * 1.0001f / (float)nA + kU * fabsf(A)) : 0.f;
+        float eB = nB ? ((eBs + (kU + gamma_n(nB)) * aB) * 1.0001f / (float)nB + kU * fabsf(B)) : 0.f;
+        float gp = A - B;
+        float margin = kFp64Margin * ((nA ? aA / (float)nA : 0.f) + (nB ? aB / (float)nB : 0.f));
+        float eg = (eA + eB + kU * fabsf(gp) + margin) * 1.001f;
+        J.p_g[p] = gp;
+        J.p_eg[p] = eg;
+        osc += (A != 0.f && B != 0.f && ((A > 0.f) == (B > 0.f))) ? 1u : 0u;
+    }
+    if (osc) atomicAdd(&s_osc, osc);
+    __syncthreads();
+    if (tid == 0 && s_osc) atomicAdd(&ctr->n_osc, s_osc);
+}
+
+size_t sobolev_smem_bytes(const Job& J)
+{
+    long long ne = (long long)(J.tcx + 2) * (J.tcy + 2) * (J.ndim == 3 ? J.tcz + 2 : J.tcz);
+    return (size_t)(((ne + 2) & ~1LL) * 4 + (long long)kStageCap * sizeof(Staged));
+}
+
+cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t st)
+{
+    if (g.total_tiles == 0) return cudaSuccess;
+    if (ndim == 2) k_sobolev<2><<<g.total_tiles, kBlock, smem, st>>>(g);
+    else k_sobolev<3><<<g.total_tiles, kBlock, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+// Dynamic shared memory limits, set outside any stream capture.
+cudaError_t configure_kernels(size_t x2, size_t x3, size_t s2, size_t s3)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_extract<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(x2, 1))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_extract<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(x3, 1))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_sobolev<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s2, 1))) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sobolev<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1));
+}
+
+}  // namespace segk

@@ -1,0 +1,953 @@
+// libseg host side: validation, device state, the per-batch stepper that replays one
+// captured CUDA graph per iteration, and the C-ABI entry points declared in seg.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "seg_internal.cuh"
+
+using namespace segk;
+
+namespace {
+
+thread_local std::string g_last_cuda;
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    g_last_cuda = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return SEG_ECUDA;
+}
+
+#define CK(x)                                              \
+    do {                                                   \
+        cudaError_t e_ = (x);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #x);   \
+    } while (0)
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Sub-allocation plan of one device allocation.
+struct Arena {
+    size_t bytes = 0;
+    std::vector<std::pair<void**, size_t>> parts;
+    template <class T>
+    void add(T** p, size_t count)
+    {
+        parts.push_back({(void**)p, align256(count * sizeof(T) + 1)});
+        bytes += parts.back().second;
+    }
+    void assign(char* base)
+    {
+        size_t off = 0;
+        for (auto& pr : parts) {
+            *pr.first = base + off;
+            off += pr.second;
+        }
+    }
+};
+
+}  // namespace
+
+struct Stepper;
+
+struct seg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    seg_params params{};
+    Job h{};                      // host copy of the job descriptor
+    Job* d_self = nullptr;        // device copy used by init-time kernels
+    Counters* d_ctr = nullptr;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    char* parena = nullptr;       // particle and candidate buffers (regrown on demand)
+    size_t parena_bytes = 0;
+    Stepper* own = nullptr;       // stepper used by seg_step
+    seg_batch* batch = nullptr;
+    Counters* h_ctr = nullptr;    // pinned host mirror
+};
+
+struct Stepper {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<seg_ctx*> members;
+    Job* d_jobs = nullptr;
+    int cap_jobs = 0;
+    int* d_ids = nullptr;          // group job ids (2D then 3D)
+    unsigned* d_prefix = nullptr;  // group tile prefixes (2D then 3D)
+    int cap_ids = 0;
+    BatchCtl* d_bc = nullptr;
+    Counters* d_gather = nullptr;
+    Counters* h_gather = nullptr;
+    int cap_gather = 0;
+    Group grp[2]{};
+    size_t smem_x[2]{}, smem_s[2]{};
+    int commit_grid = 0, commit_block = 512;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool use_graph = true;
+    bool dirty = true;
+};
+
+struct seg_batch {
+    Stepper st;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int validate(const seg_params* p)
+{
+    if (!p) return SEG_EINVAL;
+    if (p->ndim != 2 && p->ndim != 3) return SEG_EINVAL;
+    if (p->dtype != SEG_F32 && p->dtype != SEG_U16) return SEG_EINVAL;
+    for (int i = 0; i < 3; i++)
+        if (p->shape[i] < 1) return SEG_EINVAL;
+    if (p->ndim == 2 && p->shape[0] != 1) return SEG_EINVAL;
+    long double npix = (long double)p->shape[0] * p->shape[1] * p->shape[2];
+    if (npix >= 2147483647.0L) return SEG_EINVAL;
+    if (p->model != SEG_PC && p->model != SEG_PS) return SEG_EINVAL;
+    if ((p->ndim == 2 && p->connectivity != 4) || (p->ndim == 3 && p->connectivity != 6)) return SEG_EINVAL;
+    if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return SEG_EINVAL;
+    if (!(p->cutoff > 0.0) || p->cutoff > 32.0) return SEG_EINVAL;
+    if (p->model == SEG_PS && (!(p->ps_radius >= 1.0) || p->ps_radius > 64.0)) return SEG_EINVAL;
+    if (p->gradient != SEG_SOBOLEV && p->gradient != SEG_L2) return SEG_EINVAL;
+    if (p->osc_window < 0) return SEG_EINVAL;
+    if (p->stats_mode != SEG_STATS_EXACT) return SEG_EINVAL;
+    int need = (int)std::ceil(p->cutoff);
+    if (p->cell_edge != 0 && (p->cell_edge < need || p->cell_edge > 256)) return SEG_EINVAL;
+    for (int i = 0; i < 7; i++)
+        if (p->reserved[i]) return SEG_EINVAL;
+    return SEG_OK;
+}
+
+// Eq. 5 in FP64, then rounded to float for the interaction table.
+double kernel_eq5(double r, double E)
+{
+    const double eps = 1.0 / 24.0;
+    double x = r / E;
+    double num = x * x - x + 1.0 / 6.0;
+    return (1.0 / E) * (1.0 + num / (2.0 * eps));
+}
+
+int largest_d2_below(double cutoff)
+{
+    const double r2 = cutoff * cutoff;
+    long long k = (long long)std::ceil(r2) - 1;
+    if (k < 0) k = 0;
+    while ((double)(k + 1) < r2) k++;
+    while (k > 0 && !((double)k < r2)) k--;
+    return (int)k;
+}
+
+// Geometry, tables and the plan of the fixed device allocation.
+struct Plan {
+    Job h{};
+    std::vector<float> klut;
+    std::vector<int4> ps_off, nb_off;
+    Arena fixed;
+};
+
+void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
+{
+    Job& h = P.h;
+    h.ndim = p->ndim;
+    h.D = (int)p->shape[0];
+    h.H = (int)p->shape[1];
+    h.W = (int)p->shape[2];
+    h.npix = (long long)h.D * h.H * h.W;
+    h.dtype = p->dtype;
+    h.model = p->model;
+    h.conn = p->connectivity;
+    h.cell = p->cell_edge ? p->cell_edge : std::max(1, (int)std::ceil(p->cutoff));
+    const int s = h.cell;
+    h.ncx = (h.W + s - 1) / s;
+    h.ncy = (h.H + s - 1) / s;
+    h.ncz = h.ndim == 3 ? (h.D + s - 1) / s : h.D;
+    if (h.ndim == 2) {
+        h.tcx = std::max(1, 64 / s);
+        h.tcy = std::max(1, 32 / s);
+        h.tcz = 1;
+    } else {
+        h.tcx = std::max(1, 32 / s);
+        h.tcy = std::max(1, 8 / s);
+        h.tcz = std::max(1, 8 / s);
+    }
+    h.ntx = (h.ncx + h.tcx - 1) / h.tcx;
+    h.nty = (h.ncy + h.tcy - 1) / h.tcy;
+    h.ntz = (h.ncz + h.tcz - 1) / h.tcz;
+    h.ntiles = h.ntx * h.nty * h.ntz;
+    const int R = (int)std::floor(p->ps_radius);
+    h.ps_staged = (h.model == SEG_PS && h.ndim == 2 && R <= 32) ? 1 : 0;
+    h.halo = h.ps_staged ? std::max(1, R) : 1;
+    h.lambda64 = p->lambda;
+    h.lambda32 = (float)p->lambda;
+    h.cutoff = p->cutoff;
+    h.E = 2.0 * p->cutoff;
+    h.r2max = largest_d2_below(p->cutoff);
+    h.M = M;
+    h.osc_window = p->osc_window;
+    h.nbr_stride = h.ndim == 3 ? 26 : 8;
+    h.slot_lo = slot_lo;
+    h.nS = nS;
+    h.nQ = 2 * (nS - 1) + 25;
+    P.klut.resize(h.r2max + 1);
+    for (int d2 = 0; d2 <= h.r2max; d2++) P.klut[d2] = (float)kernel_eq5(std::sqrt((double)d2), h.E);
+    const int rz = h.ndim == 3 ? 1 : 0;
+    if (h.model == SEG_PS) {
+        const double R2 = p->ps_radius * p->ps_radius;
+        for (int dz = -R * rz; dz <= R * rz; dz++)
+            for (int dy = -R; dy <= R; dy++)
+                for (int dx = -R; dx <= R; dx++) {
+                    int d2 = dz * dz + dy * dy + dx * dx;
+                    if ((double)d2 <= R2) P.ps_off.push_back(make_int4(dz, dy, dx, d2));
+                }
+    }
+    const int rr = (int)std::floor(std::sqrt((double)h.r2max));
+    for (int dz = -rr * rz; dz <= rr * rz; dz++)
+        for (int dy = -rr; dy <= rr; dy++)
+            for (int dx = -rr; dx <= rr; dx++) {
+                int d2 = dz * dz + dy * dy + dx * dx;
+                if (d2 <= h.r2max) P.nb_off.push_back(make_int4(dz, dy, dx, d2));
+            }
+    h.ps_n = (int)P.ps_off.size();
+    h.nb_n = (int)P.nb_off.size();
+
+    Arena& A = P.fixed;
+    const long long npix = h.npix;
+    const long long ncell = (long long)h.ncx * h.ncy * h.ncz;
+    const size_t esz = h.dtype == SEG_F32 ? 4 : 2;
+    A.add((char**)&h.I, npix * esz);
+    A.add(&h.L, npix);
+    A.add(&h.pmap, npix);
+    A.add(&h.cell_start, ncell);
+    A.add(&h.cell_count, ncell);
+    A.add(&h.tile_word, h.ntiles);
+    A.add(&h.tile_start, h.ntiles);
+    A.add(&h.tile_count, h.ntiles);
+    A.add(&h.st_n, M);
+    A.add(&h.st_S, (size_t)M * (h.dtype == SEG_F32 ? h.nS : 1));
+    A.add(&h.st_Q, (size_t)M * (h.dtype == SEG_F32 ? h.nQ : 1));
+    A.add(&h.S64, M);
+    A.add(&h.Q64, M);
+    A.add(&h.mu64, M);
+    A.add(&h.wp64, M);
+    A.add(&h.wm64, M);
+    A.add(&h.mu32, M);
+    A.add(&h.wp32, M);
+    A.add(&h.wm32, M);
+    A.add((float**)&h.klut, P.klut.size());
+    A.add((int4**)&h.ps_off, std::max<size_t>(1, P.ps_off.size()));
+    A.add((int4**)&h.nb_off, P.nb_off.size());
+    A.add(&h.ctr, 1);
+}
+
+size_t particle_bytes(long long pcap, int stride)
+{
+    Arena A;
+    Job h{};
+    A.add(&h.p_idx, pcap);
+    A.add(&h.p_l, pcap);
+    A.add(&h.p_c, pcap);
+    A.add(&h.p_dE, pcap);
+    A.add(&h.p_eE, pcap);
+    A.add(&h.p_g, pcap);
+    A.add(&h.p_eg, pcap);
+    A.add(&h.p_key, pcap);
+    A.add(&h.p_flags, pcap);
+    A.add(&h.pix_cand, pcap);
+    A.add(&h.flag_list, pcap);
+    A.add(&h.c_best, pcap);
+    A.add(&h.c_key, pcap);
+    A.add(&h.c_pix, pcap);
+    A.add(&h.c_state, pcap);
+    A.add(&h.c_nnbr, pcap);
+    A.add(&h.c_nbr, pcap * stride);
+    return A.bytes;
+}
+
+void assign_particles(Job& h, char* base, long long pcap)
+{
+    Arena A;
+    A.add(&h.p_idx, pcap);
+    A.add(&h.p_l, pcap);
+    A.add(&h.p_c, pcap);
+    A.add(&h.p_dE, pcap);
+    A.add(&h.p_eE, pcap);
+    A.add(&h.p_g, pcap);
+    A.add(&h.p_eg, pcap);
+    A.add(&h.p_key, pcap);
+    A.add(&h.p_flags, pcap);
+    A.add(&h.pix_cand, pcap);
+    A.add(&h.flag_list, pcap);
+    A.add(&h.c_best, pcap);
+    A.add(&h.c_key, pcap);
+    A.add(&h.c_pix, pcap);
+    A.add(&h.c_state, pcap);
+    A.add(&h.c_nnbr, pcap);
+    A.add(&h.c_nbr, pcap * h.nbr_stride);
+    A.assign(base);
+    h.pcap = pcap;
+}
+
+long long default_pcap(long long npix, int ndim)
+{
+    long long worst = 2LL * ndim * npix;
+    long long want = std::max<long long>(65536, npix / 2);
+    return std::min(worst, want);
+}
+
+int grow_particles(seg_ctx* c, long long need)
+{
+    long long pcap = std::max<long long>(need + need / 2, c->h.pcap * 2);
+    pcap = std::min<long long>(pcap, 2LL * c->h.ndim * c->h.npix);
+    if (pcap < need) return SEG_ENOMEM;
+    size_t bytes = particle_bytes(pcap, c->h.nbr_stride);
+    char* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SEG_ENOMEM;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaFree(c->parena));
+    c->parena = mem;
+    c->parena_bytes = bytes;
+    assign_particles(c->h, mem, pcap);
+    CK(cudaMemcpyAsync(c->d_self, &c->h, sizeof(Job), cudaMemcpyHostToDevice, c->stream));
+    return SEG_OK;
+}
+
+// ---------------------------------------------------------------------------
+void stepper_free_graph(Stepper& s)
+{
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.graph) cudaGraphDestroy(s.graph);
+    s.exec = nullptr;
+    s.graph = nullptr;
+}
+
+int stepper_build(Stepper& s)
+{
+    stepper_free_graph(s);
+    const int n = (int)s.members.size();
+    if (!s.d_bc) {
+        CK(cudaMalloc(&s.d_bc, sizeof(BatchCtl)));
+        CK(cudaMemsetAsync(s.d_bc, 0, sizeof(BatchCtl), s.stream));
+    }
+    if (n > s.cap_jobs) {
+        if (s.d_jobs) CK(cudaFree(s.d_jobs));
+        if (s.d_ids) CK(cudaFree(s.d_ids));
+        if (s.d_prefix) CK(cudaFree(s.d_prefix));
+        if (s.d_gather) CK(cudaFree(s.d_gather));
+        if (s.h_gather) CK(cudaFreeHost(s.h_gather));
+        int cap = std::max(n, 2 * s.cap_jobs);
+        CK(cudaMalloc(&s.d_jobs, sizeof(Job) * cap));
+        CK(cudaMalloc(&s.d_ids, sizeof(int) * cap));
+        CK(cudaMalloc(&s.d_prefix, sizeof(unsigned) * (cap + 2)));
+        CK(cudaMalloc(&s.d_gather, sizeof(Counters) * cap));
+        CK(cudaMallocHost(&s.h_gather, sizeof(Counters) * cap));
+        s.cap_jobs = cap;
+    }
+    std::vector<Job> jobs(n);
+    std::vector<int> ids;
+    std::vector<unsigned> prefix;
+    for (int i = 0; i < n; i++) jobs[i] = s.members[i]->h;
+    int id_off[2] = {0, 0}, pf_off[2] = {0, 0};
+    for (int gidx = 0; gidx < 2; gidx++) {
+        const int nd = gidx == 0 ? 2 : 3;
+        id_off[gidx] = (int)ids.size();
+        pf_off[gidx] = (int)prefix.size();
+        unsigned acc = 0;
+        size_t sx = 0, ss = 0;
+        int cnt = 0;
+        for (int i = 0; i < n; i++) {
+            if (jobs[i].ndim != nd) continue;
+            ids.push_back(i);
+            prefix.push_back(acc);
+            acc += (unsigned)jobs[i].ntiles;
+            sx = std::max(sx, extract_smem_bytes(jobs[i]));
+            ss = std::max(ss, sobolev_smem_bytes(jobs[i]));
+            cnt++;
+        }
+        prefix.push_back(acc);
+        Group& g = s.grp[gidx];
+        g.jobs = s.d_jobs;
+        g.njobs = cnt;
+        g.total_tiles = cnt ? acc : 0;
+        g.ticket = &s.d_bc->ticket[gidx];
+        s.smem_x[gidx] = sx;
+        s.smem_s[gidx] = ss;
+    }
+    if ((int)prefix.size() > s.cap_jobs + 2 || (int)ids.size() > s.cap_jobs) return SEG_EINVAL;
+    for (int gidx = 0; gidx < 2; gidx++) {
+        s.grp[gidx].job_ids = s.d_ids + id_off[gidx];
+        s.grp[gidx].tile_prefix = s.d_prefix + pf_off[gidx];
+    }
+    if (n) CK(cudaMemcpyAsync(s.d_jobs, jobs.data(), sizeof(Job) * n, cudaMemcpyHostToDevice, s.stream));
+    if (!ids.empty()) CK(cudaMemcpyAsync(s.d_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s.stream));
+    CK(cudaMemcpyAsync(s.d_prefix, prefix.data(), sizeof(unsigned) * prefix.size(), cudaMemcpyHostToDevice, s.stream));
+    CK(configure_kernels(s.smem_x[0], s.smem_x[1], s.smem_s[0], s.smem_s[1]));
+    int per_sm = 0;
+    CK(commit_occupancy(s.commit_block, &per_sm));
+    if (per_sm < 1) return cuda_fail(cudaErrorCooperativeLaunchTooLarge, "commit occupancy");
+    s.commit_grid = s.sms * std::min(per_sm, 2);
+    CK(cudaStreamSynchronize(s.stream));
+    s.dirty = false;
+    return SEG_OK;
+}
+
+cudaError_t stepper_enqueue(Stepper& s)
+{
+    cudaError_t e;
+    const int n = (int)s.members.size();
+    for (int gidx = 0; gidx < 2; gidx++)
+        if (s.grp[gidx].njobs && (e = launch_extract(s.grp[gidx], gidx + 2, s.smem_x[gidx], s.stream)) != cudaSuccess) return e;
+    for (int gidx = 0; gidx < 2; gidx++)
+        if (s.grp[gidx].njobs && (e = launch_sobolev(s.grp[gidx], gidx + 2, s.smem_s[gidx], s.stream)) != cudaSuccess) return e;
+    for (int gidx = 0; gidx < 2; gidx++)
+        if (s.grp[gidx].njobs && (e = launch_flag(s.grp[gidx], s.stream)) != cudaSuccess) return e;
+    if ((e = launch_fixup(s.d_jobs, n, s.sms, s.stream)) != cudaSuccess) return e;
+    for (int gidx = 0; gidx < 2; gidx++)
+        if (s.grp[gidx].njobs && (e = launch_select(s.grp[gidx], s.d_bc, s.stream)) != cudaSuccess) return e;
+    return launch_commit(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.stream);
+}
+
+int stepper_run(Stepper& s, int iters)
+{
+    if (s.dirty) {
+        int rc = stepper_build(s);
+        if (rc) return rc;
+    }
+    if (s.members.empty() || iters <= 0) return SEG_OK;
+    if (s.use_graph && !s.exec) {
+        cudaError_t e = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = stepper_enqueue(s);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(s.stream, &g);
+            if (e2 == cudaSuccess && e == cudaSuccess && g) {
+                e = cudaGraphInstantiate(&s.exec, g, 0);
+                s.graph = g;
+                if (e != cudaSuccess) {
+                    stepper_free_graph(s);
+                    s.use_graph = false;
+                }
+            } else {
+                if (g) cudaGraphDestroy(g);
+                s.use_graph = false;
+            }
+        } else {
+            s.use_graph = false;
+        }
+        cudaGetLastError();
+    }
+    for (int i = 0; i < iters; i++) {
+        if (s.use_graph) CK(cudaGraphLaunch(s.exec, s.stream));
+        else CK(stepper_enqueue(s));
+    }
+    return SEG_OK;
+}
+
+int stepper_read(Stepper& s)
+{
+    const int n = (int)s.members.size();
+    if (!n) return SEG_OK;
+    CK(launch_gather_counters(s.d_jobs, n, s.d_gather, s.stream));
+    CK(cudaMemcpyAsync(s.h_gather, s.d_gather, sizeof(Counters) * n, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
+    for (int i = 0; i < n; i++) *s.members[i]->h_ctr = s.h_gather[i];
+    return SEG_OK;
+}
+
+// Run `iters` iterations of every member; members whose particle buffers overflowed are
+// regrown and finish their remaining iterations in further passes.
+int stepper_step(Stepper& s, int iters)
+{
+    const int n = (int)s.members.size();
+    std::vector<long long> target(n);
+    int rc = SEG_OK;
+    if (s.dirty && (rc = stepper_build(s)) != SEG_OK) return rc;
+    rc = stepper_read(s);
+    if (rc) return rc;
+    for (int i = 0; i < n; i++) target[i] = s.members[i]->h_ctr->t + iters;
+    int todo = iters;
+    for (int pass = 0; pass < 64 && todo > 0; pass++) {
+        rc = stepper_run(s, todo);
+        if (rc) return rc;
+        rc = stepper_read(s);
+        if (rc) return rc;
+        todo = 0;
+        bool regrown = false;
+        for (int i = 0; i < n; i++) {
+            seg_ctx* c = s.members[i];
+            Counters& h = *c->h_ctr;
+            if (h.error) return h.error;
+            if (h.need) {
+                rc = grow_particles(c, h.need);
+                if (rc) return rc;
+                // clear the overflow and move to a fresh tag so that no pixel-map or
+                // look-back word of the abandoned pass can be taken for a current one
+                h.need = 0;
+                h.skip = h.converged;
+                h.iter_tag += 1;
+                CK(cudaMemcpyAsync(c->d_ctr, &h, sizeof h, cudaMemcpyHostToDevice, s.stream));
+                CK(cudaStreamSynchronize(s.stream));
+                regrown = true;
+            }
+        }
+        if (regrown) {
+            s.dirty = true;
+            if (s.members.size() > 1) return SEG_OK;   // batch: members report their own t
+            todo = (int)(target[0] - s.members[0]->h_ctr->t);
+        }
+    }
+    return SEG_OK;
+}
+
+int ensure_device(int dev)
+{
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != dev) CK(cudaSetDevice(dev));
+    return SEG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int seg_estimate_bytes(const seg_params* p, int32_t nlabels, size_t* bytes)
+{
+    int rc = validate(p);
+    if (rc) return rc;
+    if (nlabels < 1 || !bytes) return SEG_EINVAL;
+    Plan P;
+    make_geometry(p, nlabels, 1, 254, P);
+    *bytes = P.fixed.bytes + particle_bytes(default_pcap(P.h.npix, P.h.ndim), P.h.nbr_stride);
+    return SEG_OK;
+}
+
+int seg_init(const seg_params* p, const void* image, const int32_t* labels0, void* cuda_stream, seg_ctx** out)
+{
+    if (!out) return SEG_EINVAL;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!image || !labels0) return SEG_EINVAL;
+    const long long npix = p->shape[0] * p->shape[1] * p->shape[2];
+    const size_t esz = p->dtype == SEG_F32 ? 4 : 2;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    // host views of the inputs for validation and the exponent range
+    std::vector<int32_t> hl;
+    const int32_t* L0 = labels0;
+    if (is_device_ptr(labels0)) {
+        hl.resize(npix);
+        CK(cudaMemcpy(hl.data(), labels0, npix * 4, cudaMemcpyDeviceToHost));
+        L0 = hl.data();
+    }
+    std::vector<char> hi;
+    const void* I0 = image;
+    const bool img_dev = is_device_ptr(image);
+    if (img_dev && p->dtype == SEG_F32) {
+        hi.resize(npix * esz);
+        CK(cudaMemcpy(hi.data(), image, npix * esz, cudaMemcpyDeviceToHost));
+        I0 = hi.data();
+    }
+    int32_t maxlab = 0;
+    for (long long i = 0; i < npix; i++) {
+        if (L0[i] < 0) return SEG_EINVAL;
+        maxlab = std::max(maxlab, L0[i]);
+    }
+    if (maxlab >= (1 << 24)) return SEG_EINVAL;
+    const int M = maxlab + 1;
+    int slot_lo = 1, slot_hi = 1;
+    if (p->dtype == SEG_F32) {
+        bool any = false;
+        const uint32_t* bits = (const uint32_t*)I0;
+        for (long long i = 0; i < npix; i++) {
+            uint32_t b = bits[i];
+            int eb = (b >> 23) & 0xff;
+            if (eb == 255) return SEG_EINVAL;
+            if ((b & 0x7fffffffu) == 0) continue;
+            int slot = eb ? eb : 1;
+            if (!any) { slot_lo = slot_hi = slot; any = true; }
+            slot_lo = std::min(slot_lo, slot);
+            slot_hi = std::max(slot_hi, slot);
+        }
+    }
+    if (p->validate) {
+        // every foreground label forms one connected component (union-find)
+        const long long D = p->shape[0], H = p->shape[1], W = p->shape[2];
+        std::vector<int64_t> parent(npix);
+        std::iota(parent.begin(), parent.end(), 0);
+        auto find = [&](int64_t a) {
+            while (parent[a] != a) { parent[a] = parent[parent[a]]; a = parent[a]; }
+            return a;
+        };
+        auto unite = [&](int64_t a, int64_t b) { a = find(a); b = find(b); if (a != b) parent[a] = b; };
+        for (long long z = 0; z < D; z++)
+            for (long long y = 0; y < H; y++)
+                for (long long x = 0; x < W; x++) {
+                    long long i = (z * H + y) * W + x;
+                    if (!L0[i]) continue;
+                    if (x + 1 < W && L0[i + 1] == L0[i]) unite(i, i + 1);
+                    if (y + 1 < H && L0[i + W] == L0[i]) unite(i, i + W);
+                    if (z + 1 < D && L0[i + W * H] == L0[i]) unite(i, i + W * H);
+                }
+        std::vector<int64_t> root(M, -1);
+        for (long long i = 0; i < npix; i++) {
+            if (!L0[i]) continue;
+            int64_t r = find(i);
+            if (root[L0[i]] < 0) root[L0[i]] = r;
+            else if (root[L0[i]] != r) return SEG_EINVAL;
+        }
+    }
+
+    seg_ctx* c = new seg_ctx();
+    c->params = *p;
+    c->stream = stream;
+    CK(cudaGetDevice(&c->device));
+    Plan P;
+    make_geometry(p, M, slot_lo, slot_hi - slot_lo + 1, P);
+    c->h = P.h;
+    auto fail = [&](int code) {
+        seg_destroy(c);
+        return code;
+    };
+    cudaError_t e = cudaMalloc(&c->arena, P.fixed.bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(SEG_ENOMEM); }
+    c->arena_bytes = P.fixed.bytes;
+    // the plan recorded addresses of fields of P.h: re-point them into c->h
+    for (auto& pr : P.fixed.parts) pr.first = (void**)((char*)&c->h + ((char*)pr.first - (char*)&P.h));
+    P.fixed.assign(c->arena);
+    c->d_ctr = c->h.ctr;
+    long long pcap = default_pcap(c->h.npix, c->h.ndim);
+    size_t pb = particle_bytes(pcap, c->h.nbr_stride);
+    e = cudaMalloc(&c->parena, pb);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(SEG_ENOMEM); }
+    c->parena_bytes = pb;
+    assign_particles(c->h, c->parena, pcap);
+    if ((e = cudaMalloc(&c->d_self, sizeof(Job))) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc job"));
+    if ((e = cudaMallocHost(&c->h_ctr, sizeof(Counters))) != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost"));
+
+    static bool topo_ready = false;
+    if (!topo_ready) {
+        if ((e = topology_tables_init()) != cudaSuccess) return fail(cuda_fail(e, "topology tables"));
+        topo_ready = true;
+    }
+    Counters hc{};
+    hc.iter_tag = 1;
+    hc.mode = p->gradient;
+    hc.best_A = -1;
+    memset(c->h_ctr, 0, sizeof(Counters));
+#define CKF(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return fail(cuda_fail(e_, #x)); } while (0)
+    CKF(cudaMemcpyAsync((void*)c->h.I, image, npix * esz, cudaMemcpyDefault, stream));
+    CKF(cudaMemcpyAsync(c->h.L, labels0, npix * 4, cudaMemcpyDefault, stream));
+    CKF(cudaMemsetAsync(c->h.pmap, 0, npix * 8, stream));
+    CKF(cudaMemsetAsync(c->h.tile_word, 0, (size_t)c->h.ntiles * 8, stream));
+    CKF(cudaMemsetAsync(c->h.st_n, 0, (size_t)M * 8, stream));
+    CKF(cudaMemsetAsync(c->h.st_S, 0, (size_t)M * (p->dtype == SEG_F32 ? c->h.nS : 1) * 8, stream));
+    CKF(cudaMemsetAsync(c->h.st_Q, 0, (size_t)M * (p->dtype == SEG_F32 ? c->h.nQ : 1) * 8, stream));
+    CKF(cudaMemcpyAsync((void*)c->h.klut, P.klut.data(), P.klut.size() * 4, cudaMemcpyHostToDevice, stream));
+    if (!P.ps_off.empty())
+        CKF(cudaMemcpyAsync((void*)c->h.ps_off, P.ps_off.data(), P.ps_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+    CKF(cudaMemcpyAsync((void*)c->h.nb_off, P.nb_off.data(), P.nb_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+    CKF(cudaMemcpyAsync(c->d_ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, stream));
+    CKF(cudaMemcpyAsync(c->d_self, &c->h, sizeof(Job), cudaMemcpyHostToDevice, stream));
+    CKF(launch_stats_init(c->d_self, 0, npix, stream));
+    CKF(launch_stats_finalize(c->d_self, 1, stream));
+    CKF(cudaStreamSynchronize(stream));
+    c->own = new Stepper();
+    c->own->device = c->device;
+    c->own->stream = stream;
+    CKF(cudaDeviceGetAttribute(&c->own->sms, cudaDevAttrMultiProcessorCount, c->device));
+    c->own->members.push_back(c);
+#undef CKF
+    *out = c;
+    return SEG_OK;
+}
+
+int seg_step(seg_ctx* c, int32_t iters, seg_status* out)
+{
+    if (!c || iters < 0) return SEG_EINVAL;
+    if (c->batch) return SEG_ESTATE;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    rc = stepper_step(*c->own, iters);
+    if (rc) return rc;
+    if (iters == 0) {
+        rc = stepper_read(*c->own);
+        if (rc) return rc;
+    }
+    if (out) *out = c->h_ctr->last;
+    return c->h_ctr->error ? c->h_ctr->error : SEG_OK;
+}
+
+int seg_labels(seg_ctx* c, int32_t* out, size_t n_out)
+{
+    if (!c || !out) return SEG_EINVAL;
+    if ((long long)n_out < c->h.npix) return SEG_EINVAL;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out, c->h.L, c->h.npix * 4, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SEG_OK;
+}
+
+int seg_particles(seg_ctx* c, const seg_particle_buffers* b, int64_t cap, int64_t* n)
+{
+    if (!c || !b || !n || cap < 0) return SEG_EINVAL;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    unsigned np = 0;
+    CK(cudaMemcpyAsync(&np, &c->d_ctr->n_particles, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if ((long long)np > c->h.pcap) np = (unsigned)c->h.pcap;
+    *n = np;
+    long long k = std::min<long long>(np, cap);
+    if (k > 0) {
+        if (b->idx) CK(cudaMemcpyAsync(b->idx, c->h.p_idx, k * 4, cudaMemcpyDefault, c->stream));
+        if (b->l) CK(cudaMemcpyAsync(b->l, c->h.p_l, k * 4, cudaMemcpyDefault, c->stream));
+        if (b->c) CK(cudaMemcpyAsync(b->c, c->h.p_c, k * 4, cudaMemcpyDefault, c->stream));
+        if (b->dE) CK(cudaMemcpyAsync(b->dE, c->h.p_dE, k * 4, cudaMemcpyDefault, c->stream));
+        if (b->eE) CK(cudaMemcpyAsync(b->eE, c->h.p_eE, k * 4, cudaMemcpyDefault, c->stream));
+        if (b->g) CK(cudaMemcpyAsync(b->g, c->h.p_g, k * 4, cudaMemcpyDefault, c->stream));
+        if (b->eg) CK(cudaMemcpyAsync(b->eg, c->h.p_eg, k * 4, cudaMemcpyDefault, c->stream));
+        if (b->key) CK(cudaMemcpyAsync(b->key, c->h.p_key, k * 8, cudaMemcpyDefault, c->stream));
+        if (b->flags) CK(cudaMemcpyAsync(b->flags, c->h.p_flags, k, cudaMemcpyDefault, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return SEG_OK;
+}
+
+int seg_stats(seg_ctx* c, int64_t* n, double* S, double* Q, int32_t max_labels)
+{
+    if (!c || max_labels < 0) return SEG_EINVAL;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    int k = std::min(max_labels, c->h.M);
+    if (k > 0) {
+        if (n) CK(cudaMemcpyAsync(n, c->h.st_n, k * 8, cudaMemcpyDeviceToHost, c->stream));
+        if (S) CK(cudaMemcpyAsync(S, c->h.S64, k * 8, cudaMemcpyDeviceToHost, c->stream));
+        if (Q) CK(cudaMemcpyAsync(Q, c->h.Q64, k * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    for (int m = k; m < max_labels; m++) {
+        if (n) n[m] = 0;
+        if (S) S[m] = 0.0;
+        if (Q) Q[m] = 0.0;
+    }
+    return SEG_OK;
+}
+
+int seg_get_state(seg_ctx* c, seg_state* out)
+{
+    if (!c || !out) return SEG_EINVAL;
+    Counters h;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(&h, c->d_ctr, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out->t = h.t;
+    out->best_A = h.best_A;
+    out->t_best = h.t_best;
+    out->mode = h.mode;
+    out->converged = h.converged;
+    return SEG_OK;
+}
+
+int seg_set_state(seg_ctx* c, const seg_state* in)
+{
+    if (!c || !in) return SEG_EINVAL;
+    if (in->mode != SEG_SOBOLEV && in->mode != SEG_L2) return SEG_EINVAL;
+    if (in->t < 0 || in->t_best < 0 || in->t_best > in->t || in->best_A < -1) return SEG_EINVAL;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    Counters h;
+    CK(cudaMemcpyAsync(&h, c->d_ctr, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    h.t = in->t;
+    h.best_A = in->best_A;
+    h.t_best = in->t_best;
+    h.mode = in->mode;
+    h.converged = in->converged ? 1 : 0;
+    h.skip = h.converged || h.error || h.need;
+    CK(cudaMemcpyAsync(c->d_ctr, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SEG_OK;
+}
+
+int seg_info(seg_ctx* c, int32_t* nlabels, int64_t shape[3])
+{
+    if (!c) return SEG_EINVAL;
+    if (nlabels) *nlabels = c->h.M;
+    if (shape) {
+        shape[0] = c->h.D;
+        shape[1] = c->h.H;
+        shape[2] = c->h.W;
+    }
+    return SEG_OK;
+}
+
+void seg_destroy(seg_ctx* c)
+{
+    if (!c) return;
+    if (c->batch) seg_batch_remove(c->batch, c);
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != c->device) cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->own) {
+        Stepper& s = *c->own;
+        stepper_free_graph(s);
+        if (s.d_jobs) cudaFree(s.d_jobs);
+        if (s.d_ids) cudaFree(s.d_ids);
+        if (s.d_prefix) cudaFree(s.d_prefix);
+        if (s.d_bc) cudaFree(s.d_bc);
+        if (s.d_gather) cudaFree(s.d_gather);
+        if (s.h_gather) cudaFreeHost(s.h_gather);
+        delete c->own;
+    }
+    if (c->arena) cudaFree(c->arena);
+    if (c->parena) cudaFree(c->parena);
+    if (c->d_self) cudaFree(c->d_self);
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    cudaGetLastError();
+    if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
+    delete c;
+}
+
+int seg_batch_create(void* cuda_stream, seg_batch** out)
+{
+    if (!out) return SEG_EINVAL;
+    seg_batch* b = new seg_batch();
+    b->st.stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&b->st.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->st.sms, cudaDevAttrMultiProcessorCount, b->st.device);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "seg_batch_create");
+    }
+    *out = b;
+    return SEG_OK;
+}
+
+int seg_batch_add(seg_batch* b, seg_ctx* c)
+{
+    if (!b || !c) return SEG_EINVAL;
+    if (c->batch) return SEG_ESTATE;
+    if (c->device != b->st.device) return SEG_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    b->st.members.push_back(c);
+    c->batch = b;
+    b->st.dirty = true;
+    return SEG_OK;
+}
+
+int seg_batch_remove(seg_batch* b, seg_ctx* c)
+{
+    if (!b || !c || c->batch != b) return SEG_EINVAL;
+    CK(cudaStreamSynchronize(b->st.stream));
+    auto& m = b->st.members;
+    m.erase(std::remove(m.begin(), m.end(), c), m.end());
+    c->batch = nullptr;
+    b->st.dirty = true;
+    return SEG_OK;
+}
+
+int seg_batch_size(seg_batch* b) { return b ? (int)b->st.members.size() : 0; }
+
+int seg_batch_step(seg_batch* b, int32_t iters, seg_status* statuses, int32_t n_statuses)
+{
+    if (!b || iters < 0) return SEG_EINVAL;
+    int rc = ensure_device(b->st.device);
+    if (rc) return rc;
+    rc = stepper_step(b->st, iters);
+    if (rc) return rc;
+    if (iters == 0) {
+        rc = stepper_read(b->st);
+        if (rc) return rc;
+    }
+    int err = SEG_OK;
+    for (size_t i = 0; i < b->st.members.size(); i++) {
+        const Counters& h = *b->st.members[i]->h_ctr;
+        if (statuses && (int)i < n_statuses) statuses[i] = h.last;
+        if (h.error && !err) err = h.error;
+    }
+    return err;
+}
+
+void seg_batch_destroy(seg_batch* b)
+{
+    if (!b) return;
+    if (b->st.stream) cudaStreamSynchronize(b->st.stream);
+    for (auto* c : b->st.members) c->batch = nullptr;
+    Stepper& s = b->st;
+    stepper_free_graph(s);
+    if (s.d_jobs) cudaFree(s.d_jobs);
+    if (s.d_ids) cudaFree(s.d_ids);
+    if (s.d_prefix) cudaFree(s.d_prefix);
+    if (s.d_bc) cudaFree(s.d_bc);
+    if (s.d_gather) cudaFree(s.d_gather);
+    if (s.h_gather) cudaFreeHost(s.h_gather);
+    cudaGetLastError();
+    delete b;
+}
+
+int seg_debug_simple(int32_t ndim, const uint32_t* masks, int32_t n, uint8_t* out)
+{
+    if ((ndim != 2 && ndim != 3) || n < 0 || (n && (!masks || !out))) return SEG_EINVAL;
+    if (!n) return SEG_OK;
+    static bool topo_ready = false;
+    if (!topo_ready) {
+        CK(topology_tables_init());
+        topo_ready = true;
+    }
+    unsigned* dm = nullptr;
+    unsigned char* dout = nullptr;
+    CK(cudaMalloc(&dm, (size_t)n * 4));
+    cudaError_t e = cudaMalloc(&dout, n);
+    if (e == cudaSuccess) e = cudaMemcpy(dm, masks, (size_t)n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_debug_simple(dm, ndim, n, dout, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, n, cudaMemcpyDeviceToHost);
+    cudaFree(dm);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return cuda_fail(e, "seg_debug_simple");
+    return SEG_OK;
+}
+
+const char* seg_strerror(int code)
+{
+    switch (code) {
+        case SEG_OK: return "ok";
+        case SEG_EINVAL: return "invalid argument";
+        case SEG_ENOMEM: return "out of device memory";
+        case SEG_ECUDA: return "CUDA runtime error";
+        case SEG_ETIMEOUT: return "bounded device wait timed out";
+        case SEG_ESTATE: return "invalid state for this call";
+        default: return "unknown error";
+    }
+}
+
+const char* seg_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Internal declarations shared by the libseg CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "seg.h"
+
+namespace segk {
+
+// Bounded waits: a spin that exceeds this many polls gives up and raises SEG_ETIMEOUT.
+constexpr unsigned kSpinLimit = 1u << 26;
+
+constexpr unsigned char kFlagFixup = 1, kFlagCand = 2, kFlagAcc = 4;
+constexpr int kUndecided = 0, kAccepted = 1, kRejected = 2;
+
+// Per-job counters and optimiser state, device memory, zeroed at seg_init.
+struct Counters {
+    unsigned n_particles;   // particles of the current iteration
+    unsigned need;          // particles required when the capacity was exceeded (sticky until regrown)
+    unsigned n_flag;        // particles queued for the FP64 recompute
+    unsigned n_cand;        // candidates
+    unsigned n_accepted;
+    unsigned n_osc;
+    unsigned mis_rounds;
+    int error;              // SEG_E* raised on the device (sticky)
+    unsigned iter_tag;      // grows by one per executed iteration; tags pixel-map and look-back words
+    int mode;               // gradient type of the next iteration
+    int converged;
+    int skip;               // nonzero: this iteration does nothing (converged, error or overflow)
+    long long t;            // iterations done
+    long long best_A;       // smallest accepted count so far, -1 before the first iteration
+    long long t_best;
+    seg_status last;        // status of the last executed iteration
+};
+
+// Everything a kernel needs about one segmentation job; lives in device memory.
+struct Job {
+    int ndim, D, H, W;
+    long long npix;
+    int dtype, model, conn;
+    int cell;                 // cell-list edge (all axes in 3D; x and y in 2D)
+    int ncx, ncy, ncz;        // cells per axis (ncz = D in 2D)
+    int tcx, tcy, tcz;        // cells per tile per axis
+    int ntx, nty, ntz, ntiles;
+    int halo;                 // label/image halo staged by extraction
+    int ps_staged;            // 2D piecewise smooth with the ball inside the staged halo
+    float lambda32;
+    double lambda64;
+    double cutoff, E;         // E = 2 * cutoff (Eq. 5 length scale)
+    int r2max;                // interaction partners: squared distance <= r2max  (< cutoff^2)
+    int ps_n;                 // piecewise-smooth ball offsets, row-major (dz, dy, dx, d2)
+    const int4* ps_off;
+    int nb_n;                 // offsets with d2 <= r2max, row-major (for the FP64 recompute)
+    const int4* nb_off;
+    const float* klut;        // K(sqrt(d2)) rounded to float, d2 = 0..r2max
+    int M;                    // number of labels
+    int osc_window;           // L2 fallback window (0 = never)
+    int nbr_stride;           // neighbour-list slots per candidate: 8 (2D) | 26 (3D)
+    int slot_lo, nS, nQ;      // exact float32 sums: exponent slots [slot_lo, slot_lo + nS)
+    const void* I;
+    int* L;
+    unsigned long long* pmap; // per pixel: (iter_tag << 32) | index of the pixel's first particle
+    long long pcap;
+    unsigned* p_idx;
+    int* p_l;
+    int* p_c;
+    float* p_dE;
+    float* p_eE;
+    float* p_g;
+    float* p_eg;
+    double* p_key;
+    unsigned char* p_flags;
+    int* pix_cand;            // at a pixel's first particle: its candidate slot or -1
+    unsigned* flag_list;
+    unsigned* cell_start;
+    unsigned* cell_count;
+    unsigned long long* tile_word;  // decoupled look-back: (tag << 34) | (status << 32) | value
+    unsigned* tile_start;
+    unsigned* tile_count;
+    long long* st_n;          // [M]
+    long long* st_S;          // u16: [M]; f32: [M * nS] mantissa sums per exponent slot
+    long long* st_Q;          // u16: [M]; f32: [M * nQ] 24-bit limbs of squared mantissas
+    double* S64;
+    double* Q64;
+    double* mu64;
+    double* wp64;             // n / (n + 1)
+    double* wm64;             // n / (n - 1), 0 for n <= 1
+    float* mu32;
+    float* wp32;
+    float* wm32;
+    int* c_best;              // candidate -> particle
+    double* c_key;
+    unsigned* c_pix;
+    int* c_state;
+    int* c_nbr;               // smaller-key neighbouring candidates, nbr_stride slots per candidate
+    int* c_nnbr;
+    Counters* ctr;
+};
+
+// A set of jobs of one dimensionality, stepped by one launch per stage.
+struct Group {
+    const Job* jobs;          // device array of all jobs of the batch
+    const int* job_ids;       // jobs of this group
+    const unsigned* tile_prefix;   // njobs + 1 exclusive prefix of tiles
+    int njobs;
+    unsigned total_tiles;
+    unsigned* ticket;         // extraction tile ticket
+};
+
+struct BatchCtl {
+    unsigned ticket[2];       // per group
+    unsigned bar_count;
+    unsigned bar_gen;
+    unsigned rounds_cnt[3];
+    int err;
+    unsigned cand_total;
+    unsigned pad[7];
+};
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(const volatile unsigned*)p; }
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p)
+{
+    return *(const volatile unsigned long long*)p;
+}
+
+// Which job / tile a tile ticket maps to.
+__device__ __forceinline__ int group_job_of_tile(const Group& g, unsigned t)
+{
+    int lo = 0, hi = g.njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (g.tile_prefix[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Bounded grid-wide barrier for a co-resident (cooperative) grid.
+__device__ __forceinline__ bool grid_barrier(BatchCtl* bc, unsigned nblocks)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned gen = ld_volatile(&bc->bar_gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&bc->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            bc->bar_count = 0;
+            __threadfence();
+            atomicAdd(&bc->bar_gen, 1u);
+        } else {
+            unsigned spins = 0;
+            while (ld_volatile(&bc->bar_gen) == gen) {
+                if (++spins > kSpinLimit) { atomicExch(&bc->err, SEG_ETIMEOUT); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ld_volatile(&bc->err) == 0;
+}
+
+// Launch wrappers (one iteration's stages); defined in the kernel translation units.
+cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t s);
+cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t s);
+cudaError_t launch_flag(const Group& g, cudaStream_t s);
+cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s);
+cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cudaStream_t s);
+cudaError_t configure_kernels(size_t smem_x2, size_t smem_x3, size_t smem_s2, size_t smem_s3);
+cudaError_t launch_select(const Group& g, BatchCtl* bc, cudaStream_t s);
+cudaError_t launch_commit(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s);
+cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s);
+cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s);
+cudaError_t topology_tables_init();
+cudaError_t commit_occupancy(int block, int* blocks_per_sm);
+size_t extract_smem_bytes(const Job& h);
+size_t sobolev_smem_bytes(const Job& h);
+cudaError_t launch_debug_simple(const unsigned* masks, int ndim, int n, unsigned char* out, cudaStream_t s);
+
+}  // namespace segk

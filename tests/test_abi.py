@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every entry point include/seg.h declares.
+
+No compute call is made here (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1403_0240_gb300 import build, seg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libseg():
+    build.build()
+    return seg.lib()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "seg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(seg_\w+)\s*\(", text)))
+
+
+def test_header_symbols_exported(libseg):
+    names = _declared()
+    assert len(names) >= 19
+    bound = {n for n, _, _ in seg.SIGNATURES}
+    for n in names:
+        assert hasattr(libseg, n), f"{n} declared but not exported"
+        assert n in bound, f"{n} not bound in the Python layer"
+
+
+def test_struct_layouts():
+    # seg_params: 2 x int32, 3 x int64, 2 x int32, 3 x double, 5 x int32, 7 reserved int32
+    assert C.sizeof(seg.Params) == 112
+    assert C.sizeof(seg.Status) == 64
+    assert C.sizeof(seg.State) == 32
+    assert C.sizeof(seg.ParticleBuffers) == 9 * C.sizeof(C.c_void_p)
+
+
+def test_strerror_and_validation_without_gpu(libseg):
+    assert libseg.seg_strerror(seg.SEG_EINVAL) == b"invalid argument"
+    assert libseg.seg_strerror(seg.SEG_ETIMEOUT).startswith(b"bounded")
+    import numpy as np
+    p = seg.make_params(np.zeros((4, 5), np.float32), cutoff=3.0)
+    out = C.c_size_t(0)
+    assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_OK and out.value > 0
+    p.cutoff = -1.0
+    assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL
+    p.cutoff = 3.0
+    p.connectivity = 6
+    assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL

@@ -1,0 +1,190 @@
+"""CUDA path against the oracle, through the C-ABI, element by element."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1403_0240_gb300 import seg, synth
+from gpu_helpers import compare_step, pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.init()
+    yield
+    torch.cuda.synchronize()
+
+
+def _mask_to_nb(mask, ndim):
+    n = 8 if ndim == 2 else 26
+    bits = [(int(mask) >> k) & 1 for k in range(n)]
+    centre = n // 2
+    return np.array(bits[:centre] + [1] + bits[centre:], np.uint8)
+
+
+def test_simple_points_match_oracle():
+    m2 = np.arange(256, dtype=np.uint32)
+    got2 = seg.debug_simple(2, m2)
+    ref2 = np.array([oracle.simple_2d(_mask_to_nb(m, 2)) for m in m2], np.uint8)
+    assert np.array_equal(got2, ref2)
+    rng = np.random.default_rng(0)
+    m3 = np.concatenate([rng.integers(0, 1 << 26, 20000, dtype=np.int64),
+                         (rng.random((20000, 26)) < 0.8).dot(1 << np.arange(26)),
+                         (rng.random((20000, 26)) < 0.2).dot(1 << np.arange(26))]).astype(np.uint32)
+    got3 = seg.debug_simple(3, m3)
+    ref3 = np.array([oracle.simple_3d(_mask_to_nb(m, 3)) for m in m3], np.uint8)
+    assert np.array_equal(got3, ref3)
+
+
+def test_disks_128_full_run_bit_exact():
+    # 128x128 two-disk scene, 50 Sobolev iterations, every iteration compared
+    w = synth.disks()
+    ctx, run = pair(w)
+    fixed = 0
+    for it in range(w.iterations):
+        st, stats = compare_step(ctx, run, f"disks it{it}")
+        fixed += stats.get("fixed", 0)
+    n, S, Q = ctx.stats()
+    n_ref, S_ref, Q_ref = oracle.stats(run.p, w.image, run.L)
+    assert np.array_equal(n, n_ref) and np.array_equal(S, S_ref) and np.array_equal(Q, Q_ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_disks_uneven_l2_and_switch(seed):
+    w = synth.disks(97, 133, seed=seed)
+    ctx, run = pair(w, osc_window=3)
+    for it in range(40):
+        compare_step(ctx, run, f"uneven{seed} it{it}")
+    ctx.close()
+
+
+def test_multilabel_grid_2d_pc():
+    w = synth.disks(150, 170, seed=21)
+    w.labels0 = synth.square_grid_labels(150, 170, 30, 14)
+    ctx, run = pair(w)
+    for it in range(15):
+        compare_step(ctx, run, f"grid2d it{it}")
+    ctx.close()
+
+
+def test_piecewise_smooth_2d():
+    w = synth.ellipses(192, 160, seed=31, iterations=12)
+    w.labels0 = synth.square_grid_labels(192, 160, 32, 16)
+    ctx, run = pair(w)
+    for it in range(12):
+        compare_step(ctx, run, f"ps2d it{it}")
+    ctx.close()
+
+
+def test_piecewise_constant_3d_u16():
+    w = synth.ellipsoids(40, 36, 44, seed=41)
+    w.labels0 = synth.cube_grid_labels(40, 36, 44, 12, 6)
+    ctx, run = pair(w)
+    for it in range(10):
+        compare_step(ctx, run, f"pc3d it{it}")
+    ctx.close()
+
+
+def test_piecewise_smooth_3d():
+    w = synth.ellipsoids(20, 22, 24, seed=42)
+    w.model, w.ps_radius, w.lam = "ps", 2.5, 400.0
+    w.labels0 = synth.cube_grid_labels(20, 22, 24, 10, 5)
+    ctx, run = pair(w)
+    for it in range(6):
+        compare_step(ctx, run, f"ps3d it{it}")
+    ctx.close()
+
+
+@pytest.mark.parametrize("cell_edge", [0, 6])
+def test_cell_edge_does_not_change_results(cell_edge):
+    w = synth.disks(100, 90, seed=51)
+    ctx, run = pair(w, cell_edge=cell_edge)
+    for it in range(10):
+        compare_step(ctx, run, f"cell{cell_edge} it{it}")
+    ctx.close()
+
+
+@pytest.mark.parametrize("cutoff", [1.0, 0.5])
+def test_degenerate_cutoff(cutoff):
+    w = synth.disks(64, 64, seed=61)
+    ctx, run = pair(w, cutoff=cutoff)
+    for it in range(10):
+        compare_step(ctx, run, f"cut{cutoff} it{it}")
+    ctx.close()
+
+
+def test_l2_until_convergence():
+    w = synth.disks(80, 80, seed=71)
+    ctx, run = pair(w, gradient="l2")
+    for it in range(200):
+        st, _ = compare_step(ctx, run, f"l2 it{it}")
+        if st["converged"]:
+            break
+    assert st["converged"] == 1
+    st2, _ = compare_step(ctx, run, "after convergence")
+    assert st2["n_accepted"] == 0 and st2["converged"] == 1
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (5, 1), (3, 3), (2, 2, 2), (1, 1, 9)])
+def test_tiny_images(shape):
+    rng = np.random.default_rng(len(shape) * 10 + shape[-1])
+    I = (rng.random(shape) * 2).astype(np.float32) if len(shape) == 2 else rng.integers(0, 500, shape).astype(np.uint16)
+    L = np.zeros(shape, np.int32)
+    L.reshape(-1)[0] = 1
+    w = synth.Workload("tiny", I, L, "pc", 4 if len(shape) == 2 else 6, 0.01, 2.0)
+    ctx, run = pair(w)
+    for it in range(4):
+        compare_step(ctx, run, f"tiny{shape} it{it}")
+    ctx.close()
+
+
+def test_no_particles():
+    I = np.random.default_rng(0).random((33, 47)).astype(np.float32)
+    w = synth.Workload("flat", I, np.zeros(I.shape, np.int32), "pc", 4, 0.04, 3.0)
+    ctx, run = pair(w)
+    for it in range(3):
+        st, _ = compare_step(ctx, run, "flat")
+        assert st["n_particles"] == 0
+    ctx.close()
+
+
+def test_checkpoint_resume_repeats_bit_for_bit():
+    w = synth.disks(96, 96, seed=81)
+    a = seg.Context.from_workload(w, osc_window=4)
+    a.step(12)
+    saved_L, saved_state = a.labels().copy(), a.get_state()
+    a.step(15)
+    b = seg.Context(w.image, saved_L, model=w.model, lam=w.lam, cutoff=w.cutoff, osc_window=4)
+    b.set_state(saved_state)
+    b.step(15)
+    assert np.array_equal(a.labels(), b.labels())
+    assert a.get_state() == b.get_state()
+    a.close()
+    b.close()
+
+
+def test_invalid_inputs_rejected():
+    I = np.zeros((8, 8), np.float32)
+    L = np.zeros((8, 8), np.int32)
+    bad = L.copy()
+    bad[0, 0] = -1
+    with pytest.raises(seg.SegError):
+        seg.Context(I, bad)
+    nan = I.copy()
+    nan[1, 1] = np.nan
+    with pytest.raises(seg.SegError):
+        seg.Context(nan, L)
+    split = L.copy()
+    split[1, 1] = 1
+    split[5, 5] = 1
+    with pytest.raises(seg.SegError):
+        seg.Context(I, split, validate=True)
+    with pytest.raises(seg.SegError):
+        seg.Context(I, L, cutoff=0.0)
+    with pytest.raises(seg.SegError):
+        seg.Context(I, L, model="ps", ps_radius=0.5)
