@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Throughput of the particle region-competition iteration with Sobolev gradients.
+
+One step = one iteration of the whole hot path (extraction, energy differences, Eq. 6
+interaction, certified selection, moves, exact statistics) on one job. The default job
+is the 1024x1024 float32 piecewise-smooth ellipse scene (local-mean radius 8, cutoff 5,
+256 square seeds, 200 iterations per job; a fresh job is started, untimed, every 200
+iterations). The metric counts particles processed per second (particle-iterations/s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Under torchrun (N > 1) every rank steps its own independent job (replicas: the method
+has no exchange step), and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Sobolev particle-iterations/s"
+UNIT = "particle-iterations/s"
+STAGES = ("extract", "sobolev", "flag", "fixup", "select", "commit")
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic bytes per unit (one particle, or one accepted move) of each stage: the
+# method's own traffic, band-only (a full-image rescan is implementation overhead).
+#   extract = particle write (idx, l, c: 12 B) + amortised label-band reads (8 B)
+#           + image value (4 B) + energy difference out (4 B)
+#   sobolev = particle in (idx, l, c, dE: 16 B) + gradient out (4 B)
+#   flag, fixup, select = 12 B per particle; commit = 12 B per particle + 24 B per move
+ALG_BYTES = {"extract": (28, 0), "sobolev": (20, 0), "flag": (12, 0), "fixup": (12, 0),
+             "select": (12, 0), "commit": (12, 24)}
+
+
+def workloads():
+    from paper_1403_0240_gb300 import synth
+    return {
+        "ellipses1024": (lambda seed: synth.ellipses(seed=1 + seed),
+                         "2D 1024x1024 float32 piecewise smooth: 40 ellipses, bias field, Poisson noise (20 photons); "
+                         "32x32 squares on a 64 px pitch; local-mean radius 8, cutoff 5, lambda 0.04, 200 iterations"),
+        "disks128": (lambda seed: synth.disks(seed=seed) if seed == 0 else synth.disks(128, 128, seed=seed),
+                     "2D 128x128 float32 piecewise constant: two disks, Gaussian noise 0.3; centred 64x64 square; "
+                     "cutoff 3, lambda 0.04, 50 iterations"),
+        "ellipsoids256": (lambda seed: synth.ellipsoids(seed=2 + seed),
+                          "3D 256^3 uint16 piecewise constant: 200 ellipsoids, blur 1.5, Poisson noise; 16^3 cubes on a "
+                          "32 pitch; cutoff 4, lambda 1600, 100 iterations"),
+    }
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sources_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("k_tile.cu", "k_select.cu", "seg_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1403_0240_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(stage: str, workload: str, units: float):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this launch, or None
+    when the summary is missing, is for another workload, or predates the current kernels."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(stage)
+    if not e or e.get("workload") != workload or e.get("sources") != kernel_sources_digest():
+        return None
+    return float(e["dram_bytes_per_unit"]) * units
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.lines: list[str] = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0:
+            time.sleep(0.02)
+        self.mark = len(self.lines)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r.split(", ") for r in self.lines[max(0, getattr(self, "mark", 0) - 1):] if r]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def allmax(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_sample(w, seconds: float = 12.0, max_iters: int = 400):
+    """The CPU oracle as it stands, single-threaded, on the first iterations of the job."""
+    import oracle
+    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius)
+    run = oracle.Run(p, w.image, w.labels0)
+    t0 = time.perf_counter()
+    parts, its = 0, 0
+    while its < max_iters and (time.perf_counter() - t0) < seconds:
+        s, _ = run.step()
+        parts += s["n_particles"]
+        its += 1
+    dt = time.perf_counter() - t0
+    return parts / dt, its, dt
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the oracle, timed on this host's cores, on the same workload."""
+    if rank != 0:
+        return
+    name = args.workload
+    make, desc = workloads()[name]
+    w = make(0)
+    import oracle
+    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius)
+    run = oracle.Run(p, w.image, w.labels0)
+    for _ in range(args.warmup):
+        run.step()
+    parts, times = 0, []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        s, _ = run.step()
+        times.append(time.perf_counter() - t0)
+        parts += s["n_particles"]
+    total = sum(times)
+    value = parts / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": name, "description": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"iterations {args.warmup}..{args.warmup + args.steps - 1} of one job, "
+                                       "single-threaded FP64 C oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+
+    from paper_1403_0240_gb300 import seg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    name = args.workload
+    make, desc = workloads()[name]
+    w = make(rank)
+    iters_per_job = w.iterations
+    img_d = torch.from_numpy(w.image).to(dev)
+    lab_d = torch.from_numpy(w.labels0).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def new_ctx():
+        c = seg.Context(img_d, lab_d, model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
+                        ps_radius=w.ps_radius, osc_window=0, stream=stream)
+        c.profile(True)
+        return c
+
+    ctx = new_ctx()
+    done_in_job = 0
+    for _ in range(args.warmup):
+        if done_in_job == iters_per_job:
+            ctx.close()
+            ctx, done_in_job = new_ctx(), 0
+        flush.zero_()
+        ctx.step_async(1)
+        done_in_job += 1
+    ctx.poll()
+    torch.cuda.synchronize(dev)
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_ms = {k: 0.0 for k in STAGES}
+    step_parts = []
+    accepted = 0
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    before = ctx.poll()["particles_total"]
+    for k in range(args.steps):
+        if done_in_job == iters_per_job:
+            step_parts_job = ctx.poll()["particles_total"] - before
+            step_parts.append(step_parts_job)
+            ctx.close()
+            ctx, done_in_job = new_ctx(), 0
+            before = 0
+        flush.zero_()
+        ev0[k].record(stream)
+        ctx.step_async(1)
+        ev1[k].record(stream)
+        st = ctx.stage_times()
+        for s_ in STAGES:
+            stage_ms[s_] += st[s_]
+        done_in_job += 1
+        accepted += ctx.poll()["n_accepted"]
+    st_last = ctx.poll()
+    step_parts.append(st_last["particles_total"] - before)
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop() if sampler else None
+    if st_last["error"]:
+        raise RuntimeError(f"device error {st_last['error']}")
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    particles = float(sum(step_parts))
+    t_max = allmax(pg, dev_ms / 1000.0)
+    total_particles = allsum(pg, particles)
+    value = total_particles / t_max
+    ctx.close()
+
+    # end to end through the public API: host (pinned) inputs, a status read every step,
+    # the label image back to the host at the end; one job of K' iterations
+    img_h = torch.from_numpy(w.image).pin_memory()
+    lab_h = torch.from_numpy(w.labels0).pin_memory()
+    out_h = torch.empty(w.labels0.shape, dtype=torch.int32).pin_memory()
+    k_e2e = min(args.steps, iters_per_job)
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    c2 = seg.Context(img_h, lab_h, model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
+                     ps_radius=w.ps_radius, osc_window=0, stream=stream)
+    for _ in range(k_e2e):
+        s2 = c2.step(1)
+    c2.labels(out=out_h)
+    e2e_t = time.perf_counter() - t0
+    barrier(pg)
+    e2e_parts = allsum(pg, float(s2["particles_total"]))
+    e2e_t = allmax(pg, e2e_t)
+    c2.close()
+    in_bytes = w.image.nbytes + w.labels0.nbytes
+    status_bytes = 200     # the per-step counter record read back by seg_step
+    e2e = {"value": e2e_parts / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": int(math.ceil(in_bytes / k_e2e)),
+           "d2h_bytes_per_step": int(math.ceil(w.labels0.nbytes / k_e2e)) + status_bytes,
+           "iterations": k_e2e}
+
+    if rank != 0:
+        return
+    mean_stage = {k: v / args.steps for k, v in stage_ms.items()}
+    dom = max(mean_stage, key=mean_stage.get)
+    mean_parts = particles / args.steps
+    per_p, per_move = ALG_BYTES[dom]
+    alg_bytes = per_p * mean_parts + per_move * (accepted / args.steps)
+    peak, peak_kind = read_peaks()
+    achieved = alg_bytes / (mean_stage[dom] / 1000.0) / 1e9
+    traffic = traffic_from_profile(dom, name, mean_parts)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": mean_stage[dom]}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, its, secs = oracle_sample(w, seconds=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {its} iterations of the same job ({secs:.1f} s), single-threaded FP64 C oracle"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "description": desc, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between timed iterations (256 MiB write)",
+                       "iterations_per_job": iters_per_job, "mean_particles": mean_parts,
+                       "precision": "float32 gradients with certified bounds, FP64 recompute of uncertified "
+                                    "decisions, exact region sums"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            # per step: the six stage kernels of the iteration graph plus the status gather of poll()
+            "gpu_launches": (len(STAGES) + 1) * args.steps, "clocks": clocks,
+            "stages_ms": {k: round(v, 5) for k, v in mean_stage.items()},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ellipses1024", choices=sorted(workloads().keys()))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local, pg = dist_setup() if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0, None)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -87,7 +87,10 @@ typedef struct {
     int32_t mode_used;     /* SEG_SOBOLEV | SEG_L2 */
     int32_t converged;     /* an L2 iteration accepted no move; later iterations do nothing */
     int32_t mis_rounds;    /* rounds of the parallel ranked selection */
-    int32_t error;         /* 0, or a SEG_E* code raised on the device */
+    int32_t error;         /* 0, or a SEG_E* code raised on the device; SEG_ENOMEM: the
+                              particle buffers overflowed and the iteration was not run
+                              (the next seg_step regrows them and runs it) */
+    int64_t particles_total; /* particles summed over all iterations run so far */
 } seg_status;
 
 typedef struct {
@@ -132,6 +135,20 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0,
  * one was raised (SEG_ETIMEOUT), SEG_ECUDA on a runtime failure. */
 int seg_step(seg_ctx* c, int32_t iters, seg_status* out);
 
+/* Enqueue iters iterations on the context's stream and return without waiting
+ * (graph launches only; no host synchronisation, no buffer regrowth). */
+int seg_step_async(seg_ctx* c, int32_t iters);
+
+/* Wait for the context's stream and return the status of the last iteration run. */
+int seg_poll(seg_ctx* c, seg_status* out);
+
+/* Stage timing: when on, the captured iteration graph also records CUDA events
+ * between its stages (extract, sobolev, flag, fixup, select, commit);
+ * seg_stage_times waits for the stream and writes the milliseconds each stage took
+ * in the most recent iteration (n >= 6), returning SEG_ESTATE when timing is off. */
+int seg_profile(seg_ctx* c, int32_t on);
+int seg_stage_times(seg_ctx* c, float* ms, int32_t n);
+
 /* Copy the current label image (D*H*W int32) to out (host or device); n_out is
  * the element capacity of out (SEG_EINVAL if too small). Synchronises the stream. */
 int seg_labels(seg_ctx* c, int32_t* out, size_t n_out);
@@ -164,6 +181,8 @@ int seg_batch_size(seg_batch* b);
 /* Run iters iterations of every context in the batch; statuses (may be NULL)
  * receives one seg_status per context in the order they were added. */
 int seg_batch_step(seg_batch* b, int32_t iters, seg_status* statuses, int32_t n_statuses);
+int seg_batch_step_async(seg_batch* b, int32_t iters);
+int seg_batch_poll(seg_batch* b, seg_status* statuses, int32_t n_statuses);
 void seg_batch_destroy(seg_batch* b);
 
 /* Test hook: the device's simple-point test on n neighbourhood bitmasks (host arrays).

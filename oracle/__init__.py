@@ -55,6 +55,10 @@ class State(C.Structure):
                 ("best_A", C.c_int64), ("t_best", C.c_int64)]
 
 
+class Dump(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("idx", "l", "c", "dE", "g", "dE_scale", "g_scale")]
+
+
 class Status(C.Structure):
     _fields_ = [("n_particles", C.c_int64), ("n_candidates", C.c_int64),
                 ("n_accepted", C.c_int64), ("n_osc", C.c_int64),
@@ -81,11 +85,11 @@ def lib():
             L.orc_stats.restype = None
             L.orc_stats.argtypes = [P(Params), vp, vp, vp, vp, vp]
             L.orc_energy.restype = None
-            L.orc_energy.argtypes = [P(Params), vp, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+            L.orc_energy.argtypes = [P(Params), vp, vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]
             L.orc_delta_perimeter.restype = C.c_int64
             L.orc_delta_perimeter.argtypes = [P(Params), vp, C.c_uint32, C.c_int32, C.c_int32]
             L.orc_sobolev.restype = None
-            L.orc_sobolev.argtypes = [P(Params), C.c_int64, vp, vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
+            L.orc_sobolev.argtypes = [P(Params), C.c_int64, vp, vp, vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
             L.orc_simple_2d.restype = C.c_int
             L.orc_simple_2d.argtypes = [vp]
             L.orc_simple_3d.restype = C.c_int
@@ -97,8 +101,7 @@ def lib():
             L.orc_state_init.restype = None
             L.orc_state_init.argtypes = [P(Params), P(State)]
             L.orc_iterate.restype = C.c_int
-            L.orc_iterate.argtypes = [P(Params), vp, vp, P(State), P(Status), C.c_int64,
-                                      vp, vp, vp, vp, vp]
+            L.orc_iterate.argtypes = [P(Params), vp, vp, P(State), P(Status), C.c_int64, P(Dump)]
             _lib = L
     return _lib
 
@@ -160,7 +163,7 @@ def stats(p: Params, I: np.ndarray, L: np.ndarray):
     return n, S, Q
 
 
-def energy(p: Params, I: np.ndarray, L: np.ndarray, idx, l, c, n=None, S=None) -> np.ndarray:
+def energy(p: Params, I: np.ndarray, L: np.ndarray, idx, l, c, n=None, S=None, with_scale: bool = False):
     I = np.ascontiguousarray(I)
     L = np.ascontiguousarray(L, dtype=np.int32)
     if n is None:
@@ -169,9 +172,11 @@ def energy(p: Params, I: np.ndarray, L: np.ndarray, idx, l, c, n=None, S=None) -
     l = np.ascontiguousarray(l, np.int32)
     c = np.ascontiguousarray(c, np.int32)
     dE = np.zeros(idx.size, np.float64)
+    sc = np.zeros(idx.size, np.float64)
     lib().orc_energy(C.byref(p), _ptr(I), _ptr(L), _ptr(np.ascontiguousarray(n, np.int64)),
-                     _ptr(np.ascontiguousarray(S, np.float64)), idx.size, _ptr(idx), _ptr(l), _ptr(c), _ptr(dE))
-    return dE
+                     _ptr(np.ascontiguousarray(S, np.float64)), idx.size, _ptr(idx), _ptr(l), _ptr(c), _ptr(dE),
+                     _ptr(sc))
+    return (dE, sc) if with_scale else dE
 
 
 def delta_perimeter(p: Params, L: np.ndarray, x: int, l: int, c: int) -> int:
@@ -188,7 +193,7 @@ def sobolev(p: Params, idx, l, c, dE, all_pairs: bool = False):
     g, A, B = (np.zeros(N, np.float64) for _ in range(3))
     nQ, nQp = np.zeros(N, np.int32), np.zeros(N, np.int32)
     lib().orc_sobolev(C.byref(p), N, _ptr(idx), _ptr(l), _ptr(c), _ptr(dE), int(all_pairs),
-                      _ptr(g), _ptr(A), _ptr(B), _ptr(nQ), _ptr(nQp))
+                      _ptr(g), _ptr(A), _ptr(B), _ptr(nQ), _ptr(nQp), None, None)
     return g, A, B, nQ, nQp
 
 
@@ -235,16 +240,18 @@ class Run:
     def step(self, dump: bool = False):
         s = Status()
         if not dump:
-            lib().orc_iterate(C.byref(self.p), _ptr(self.I), _ptr(self.L), C.byref(self.st), C.byref(s), 0,
-                              None, None, None, None, None)
+            lib().orc_iterate(C.byref(self.p), _ptr(self.I), _ptr(self.L), C.byref(self.st), C.byref(s), 0, None)
             return s.as_dict(), None
         L_before = self.L.copy()
         N = lib().orc_extract(C.byref(self.p), _ptr(L_before), None, None, None, 0)
-        idx, l, c = np.zeros(N, np.uint32), np.zeros(N, np.int32), np.zeros(N, np.int32)
-        dE, g = np.zeros(N, np.float64), np.zeros(N, np.float64)
+        out = {"idx": np.zeros(N, np.uint32), "l": np.zeros(N, np.int32), "c": np.zeros(N, np.int32)}
+        for k in ("dE", "g", "dE_scale", "g_scale"):
+            out[k] = np.zeros(N, np.float64)
+        d = Dump(**{k: out[k].ctypes.data_as(C.c_void_p) for k in out})
         lib().orc_iterate(C.byref(self.p), _ptr(self.I), _ptr(self.L), C.byref(self.st), C.byref(s), N,
-                          _ptr(idx), _ptr(l), _ptr(c), _ptr(dE), _ptr(g))
-        return s.as_dict(), {"idx": idx, "l": l, "c": c, "dE": dE, "g": g, "labels_before": L_before}
+                          C.byref(d))
+        out["labels_before"] = L_before
+        return s.as_dict(), out
 
     def state(self) -> dict:
         return {k: int(getattr(self.st, k)) for k, _ in State._fields_}

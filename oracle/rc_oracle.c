@@ -290,7 +290,7 @@ int64_t orc_delta_perimeter(const orc_params* p, const int32_t* L, uint32_t xi, 
 /* Energy difference of moving particle (x: l -> c), data term + lambda * length. */
 void orc_energy(const orc_params* p, const void* I, const int32_t* L,
                 const int64_t* n, const double* S, int64_t N,
-                const uint32_t* idx, const int32_t* l, const int32_t* c, double* dE)
+                const uint32_t* idx, const int32_t* l, const int32_t* c, double* dE, double* scale)
 {
     int Ri = (int)floor(p->ps_radius);
     double R2 = p->ps_radius * p->ps_radius;
@@ -309,11 +309,18 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
             double t2 = 0.0;
             if (n[lp] > 1) t2 = ((double)n[lp] / ((double)n[lp] - 1.0)) * (b * b);
             data = t1 - t2;
+            /* first-order scale: each deviation a = v - mu perturbed by |v| + |mu|, plus the terms */
+            if (scale) {
+                double wc = (double)n[cp] / ((double)n[cp] + 1.0);
+                double wl = n[lp] > 1 ? (double)n[lp] / ((double)n[lp] - 1.0) : 0.0;
+                scale[k] = 2.0 * wc * fabs(a) * (fabs(v) + fabs(mc)) + 2.0 * wl * fabs(b) * (fabs(v) + fabs(ml)) +
+                           fabs(t1) + fabs(t2);
+            }
         } else {
             /* Piecewise smooth: local means over the ball of radius R, row-major order. */
             int64_t z, y, x;
             coords(p, xi, &z, &y, &x);
-            double sc = 0.0, sl = 0.0;
+            double sc = 0.0, sl = 0.0, ac = 0.0, al = 0.0;
             int64_t cc = 0, cl = 0;
             int Rz = p->ndim == 3 ? Ri : 0;
             for (int dz = -Rz; dz <= Rz; dz++)
@@ -325,17 +332,21 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
                         if (!inside(p, zz, yy, xx)) continue;
                         int64_t j = (zz * p->H + yy) * p->W + xx;
                         int32_t m = L[j];
-                        if (m == cp) { sc = sc + pix(p, I, j); cc++; }
-                        else if (m == lp) { sl = sl + pix(p, I, j); cl++; }
+                        if (m == cp) { sc = sc + pix(p, I, j); ac += fabs(pix(p, I, j)); cc++; }
+                        else if (m == lp) { sl = sl + pix(p, I, j); al += fabs(pix(p, I, j)); cl++; }
                     }
             double muc = sc / (double)cc;
             double mul = sl / (double)cl;
             double a = v - muc;
             double b = v - mul;
             data = a * a - b * b;
+            if (scale)
+                scale[k] = 2.0 * fabs(a) * (fabs(v) + ac / (double)cc) + 2.0 * fabs(b) * (fabs(v) + al / (double)cl) +
+                           a * a + b * b;
         }
         int64_t dP = orc_delta_perimeter(p, L, xi, lp, cp);
         dE[k] = data + p->lambda * (double)dP;
+        if (scale) scale[k] += fabs(p->lambda * (double)dP);
     }
 }
 
@@ -349,7 +360,8 @@ static int cmp_i64(const void* a, const void* b)
 
 void orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int32_t* l,
                  const int32_t* c, const double* dE, int all_pairs,
-                 double* g, double* A, double* B, int32_t* nQ, int32_t* nQp)
+                 double* g, double* A, double* B, int32_t* nQ, int32_t* nQp,
+                 const double* dE_scale, double* scale)
 {
     double rc = p->cutoff;
     double r2 = rc * rc;
@@ -392,7 +404,7 @@ void orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int3
                     }
             qsort(list, (size_t)nlist, sizeof(int64_t), cmp_i64);   /* ascending particle key */
         }
-        double As = 0.0, Bs = 0.0;
+        double As = 0.0, Bs = 0.0, Aa = 0.0, Ba = 0.0;
         int32_t na = 0, nb = 0;
         for (int64_t t = 0; t < nlist; t++) {
             int64_t q = list[t];
@@ -400,8 +412,9 @@ void orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int3
             int64_t d2 = ddz * ddz + ddy * ddy + ddx * ddx;
             if (!((double)d2 < r2)) continue;
             double K = orc_kernel_eq5(sqrt((double)d2), E, eps);
-            if (l[q] == l[k]) { As = As + K * dE[q]; na++; }
-            if (c[q] == l[k]) { Bs = Bs + K * dE[q]; nb++; }
+            double sq = dE_scale ? dE_scale[q] : fabs(dE[q]);
+            if (l[q] == l[k]) { As = As + K * dE[q]; Aa += fabs(K) * sq; na++; }
+            if (c[q] == l[k]) { Bs = Bs + K * dE[q]; Ba += fabs(K) * sq; nb++; }
         }
         double a = na ? As / (double)na : 0.0;
         double b = nb ? Bs / (double)nb : 0.0;
@@ -410,6 +423,7 @@ void orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int3
         if (B) B[k] = b;
         if (nQ) nQ[k] = na;
         if (nQp) nQp[k] = nb;
+        if (scale) scale[k] = (na ? Aa / (double)na : 0.0) + (nb ? Ba / (double)nb : 0.0) + fabs(a) + fabs(b);
     }
     free(cz); free(cy); free(cx); free(cstart); free(order); free(fill); free(list);
 }
@@ -590,8 +604,7 @@ void orc_state_init(const orc_params* p, orc_state* st)
 }
 
 int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
-                orc_status* status, int64_t cap,
-                uint32_t* d_idx, int32_t* d_l, int32_t* d_c, double* d_dE, double* d_g)
+                orc_status* status, int64_t cap, const orc_dump* dump)
 {
     memset(status, 0, sizeof *status);
     status->mode_used = st->mode;
@@ -611,14 +624,16 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
     double* g = (double*)malloc(sizeof(double) * NN);
     double* A = (double*)malloc(sizeof(double) * NN);
     double* B = (double*)malloc(sizeof(double) * NN);
+    double* dEs = (double*)malloc(sizeof(double) * NN);
+    double* gs = (double*)malloc(sizeof(double) * NN);
     orc_extract(p, L, idx, l, c, N);
-    orc_energy(p, I, L, n, S, N, idx, l, c, dE);
+    orc_energy(p, I, L, n, S, N, idx, l, c, dE, dEs);
     if (st->mode == 0) {
-        orc_sobolev(p, N, idx, l, c, dE, 0, g, A, B, NULL, NULL);
+        orc_sobolev(p, N, idx, l, c, dE, 0, g, A, B, NULL, NULL, dEs, gs);
         for (int64_t k = 0; k < N; k++)
             if (A[k] != 0.0 && B[k] != 0.0 && ((A[k] > 0.0) == (B[k] > 0.0))) status->n_osc++;
     } else {
-        for (int64_t k = 0; k < N; k++) g[k] = dE[k];
+        for (int64_t k = 0; k < N; k++) { g[k] = dE[k]; gs[k] = dEs[k]; }
     }
     uint32_t* acc_idx = (uint32_t*)malloc(sizeof(uint32_t) * NN);
     int32_t* acc_c = (int32_t*)malloc(sizeof(int32_t) * NN);
@@ -629,13 +644,15 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
     status->n_particles = N;
     status->n_candidates = ncand;
     status->n_accepted = na;
-    if (d_idx || d_l || d_c || d_dE || d_g) {
+    if (dump) {
         for (int64_t k = 0; k < N && k < cap; k++) {
-            if (d_idx) d_idx[k] = idx[k];
-            if (d_l) d_l[k] = l[k];
-            if (d_c) d_c[k] = c[k];
-            if (d_dE) d_dE[k] = dE[k];
-            if (d_g) d_g[k] = g[k];
+            if (dump->idx) dump->idx[k] = idx[k];
+            if (dump->l) dump->l[k] = l[k];
+            if (dump->c) dump->c[k] = c[k];
+            if (dump->dE) dump->dE[k] = dE[k];
+            if (dump->g) dump->g[k] = g[k];
+            if (dump->dE_scale) dump->dE_scale[k] = dEs[k];
+            if (dump->g_scale) dump->g_scale[k] = gs[k];
         }
     }
     /* oscillation fallback and convergence */
@@ -645,6 +662,7 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
     status->converged = st->converged;
     st->t++;
     free(n); free(S); free(Q); free(idx); free(l); free(c); free(dE); free(g); free(A); free(B);
+    free(dEs); free(gs);
     free(acc_idx); free(acc_c);
     return 0;
 }

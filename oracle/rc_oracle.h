@@ -22,8 +22,9 @@
  *   orc_energy (length) - pinned by a brute-force recount of the perimeter.
  *   orc_sobolev         - Eq. 6 with a cell list; pinned by all-pairs brute force,
  *                         the degenerate cutoff, and a hand-computed straight line.
- *   orc_simple_2d/3d    - topological numbers; pinned by Yokoi's formula (2D) and
- *                         global component / Euler-characteristic counts (2D, 3D).
+ *   orc_simple_2d/3d    - topological numbers; pinned by Yokoi's formula and global
+ *                         component counts (2D), and by contractibility of the
+ *                         centre's link in the cubical complex (3D).
  *   orc_select          - ranked greedy selection; pinned by an independent
  *                         local-minimum-rounds evaluation and permutation tests.
  *   orc_iterate         - composition of the above; pinned by the partition and
@@ -79,15 +80,20 @@ double  orc_exact_sum_f32(const float* v, int64_t n, int squares);
 void    orc_stats(const orc_params* p, const void* I, const int32_t* L,
                   int64_t* n, double* S, double* Q);
 
+/* scale (may be NULL): first-order magnitude scale of each dE: every deviation v - mu
+ * weighted by the magnitudes it is formed from (|v| + |mu|), plus its terms */
 void    orc_energy(const orc_params* p, const void* I, const int32_t* L,
                    const int64_t* n, const double* S, int64_t N,
-                   const uint32_t* idx, const int32_t* l, const int32_t* c, double* dE);
+                   const uint32_t* idx, const int32_t* l, const int32_t* c, double* dE, double* scale);
 
 int64_t orc_delta_perimeter(const orc_params* p, const int32_t* L, uint32_t x, int32_t l, int32_t c);
 
+/* scale (may be NULL): sum_Q K s_q / |Q| + sum_Q' K s_q / |Q'| + |A| + |B| of each g, with s_q
+ * the scale of dE_q (dE_scale, or |dE_q| when dE_scale is NULL) */
 void    orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int32_t* l,
                     const int32_t* c, const double* dE, int all_pairs,
-                    double* g, double* A, double* B, int32_t* nQ, int32_t* nQp);
+                    double* g, double* A, double* B, int32_t* nQ, int32_t* nQp,
+                    const double* dE_scale, double* scale);
 
 int     orc_simple_2d(const uint8_t* nb9);
 int     orc_simple_3d(const uint8_t* nb27);
@@ -99,9 +105,19 @@ int64_t orc_select(const orc_params* p, const int32_t* L, int64_t N,
 
 void    orc_state_init(const orc_params* p, orc_state* st);
 
+/* per-particle arrays of one iteration, in key order (each pointer may be NULL) */
+typedef struct {
+    uint32_t* idx;
+    int32_t* l;
+    int32_t* c;
+    double* dE;
+    double* g;
+    double* dE_scale;
+    double* g_scale;
+} orc_dump;
+
 int     orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
-                    orc_status* status, int64_t cap,
-                    uint32_t* d_idx, int32_t* d_l, int32_t* d_c, double* d_dE, double* d_g);
+                    orc_status* status, int64_t cap, const orc_dump* dump);
 
 #ifdef __cplusplus
 }

@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(512) k_commit(const Job* jobs, int njobs, Batc
         if (!ok) atomicExch(&c->error, ld_volatile(&bc->err) ? ld_volatile(&bc->err) : SEG_ETIMEOUT);
         if (c->error || c->need) {
             c->skip = 1;
-            c->last.error = c->error;
+            c->last.error = c->error ? c->error : SEG_ENOMEM;
             continue;
         }
         if (c->converged) {
@@ -751,6 +751,8 @@ __global__ void __launch_bounds__(512) k_commit(const Job* jobs, int njobs, Batc
             c->last.mode_used = c->mode;
             c->last.converged = 1;
             c->last.mis_rounds = 0;
+            c->last.error = 0;
+            c->last.particles_total = c->cum_particles;
             c->t++;
             continue;
         }
@@ -769,6 +771,8 @@ __global__ void __launch_bounds__(512) k_commit(const Job* jobs, int njobs, Batc
         c->last.converged = c->converged;
         c->last.mis_rounds = (int)rounds;
         c->last.error = 0;
+        c->cum_particles += c->n_particles;
+        c->last.particles_total = c->cum_particles;
         c->t++;
         c->iter_tag++;
         c->n_flag = 0;

@@ -75,10 +75,12 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* s_warp
 // Returns dE in float and a bound on |dE - dE_fp64|.
 __device__ __forceinline__ void energy_pc(const Job& J, float v, int l, int c, int dP, float& dE, float& eE)
 {
-    float mc = __ldg(J.mu32 + c), ml = __ldg(J.mu32 + l);
-    float a = v - mc, b = v - ml;
-    float ea = kU * (fabsf(mc) + fabsf(a));
-    float eb = kU * (fabsf(ml) + fabsf(b));
+    // the deviations from the region means in FP64 (exact up to one rounding each),
+    // so that v close to a mean loses no accuracy; everything else in float32
+    float a = __double2float_rn(__dsub_rn((double)v, __ldg(J.mu64 + c)));
+    float b = __double2float_rn(__dsub_rn((double)v, __ldg(J.mu64 + l)));
+    float ea = kU * fabsf(a);
+    float eb = kU * fabsf(b);
     float aa = a * a, bb = b * b;
     float eaa = (2.0f * fabsf(a) + ea) * ea + kU * aa;
     float ebb = (2.0f * fabsf(b) + eb) * eb + kU * bb;
@@ -94,24 +96,24 @@ __device__ __forceinline__ void energy_pc(const Job& J, float v, int l, int c, i
 }
 
 // Piecewise-smooth data term from local means over the ball of radius R around x,
-// x counted in its own label: (v - mu_c)^2 - (v - mu_l)^2.
+// x counted in its own label: (v - mu_c)^2 - (v - mu_l)^2. The ball sums are taken of
+// the shifted values I(y) - v, so a = v - mu_c = -(sum (I - v)) / n_c directly.
+// sc, sl: shifted sums; ac, al: sums of |I(y) - v|.
 __device__ __forceinline__ void energy_ps_finish(const Job& J, float v, int dP, float sc, float ac, int cc,
                                                  float sl, float al, int cl, float& dE, float& eE)
 {
-    float muc = sc / (float)cc, mul = sl / (float)cl;
-    float emc = gamma_n(cc) * ac / (float)cc + kU * fabsf(muc);
-    float eml = gamma_n(cl) * al / (float)cl + kU * fabsf(mul);
-    float a = v - muc, b = v - mul;
-    float ea = emc + kU * fabsf(a), eb = eml + kU * fabsf(b);
+    float a = -sc / (float)cc, b = -sl / (float)cl;
+    float ea = gamma_n(cc + 1) * ac / (float)cc + kU * fabsf(a);
+    float eb = gamma_n(cl + 1) * al / (float)cl + kU * fabsf(b);
     float aa = a * a, bb = b * b;
     float eaa = (2.0f * fabsf(a) + ea) * ea + kU * aa;
     float ebb = (2.0f * fabsf(b) + eb) * eb + kU * bb;
     float d = aa - bb;
     float lp = J.lambda32 * (float)dP;
     dE = d + lp;
-    float mac = ac / (float)cc, mal = al / (float)cl;
+    float mac = ac / (float)cc + fabsf(v), mal = al / (float)cl + fabsf(v);
     float err = eaa + ebb + kU * (fabsf(d) + fabsf(lp) + fabsf(dE)) +
-                kFp64Margin * (aa + bb + fabsf(lp) + mac * mac + mal * mal + v * v);
+                kFp64Margin * (aa + bb + fabsf(lp) + mac * mac + mal * mal);
     eE = err * 1.001f;
 }
 
@@ -300,8 +302,8 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
                         m = __ldg(J.L + gj2);
                         f = image_at(J, gj2);
                     }
-                    if (m == c) { sc += f; ac += fabsf(f); cc++; }
-                    else if (m == own) { sl += f; al += fabsf(f); cl++; }
+                    if (m == c) { float dv = f - v; sc += dv; ac += fabsf(dv); cc++; }
+                    else if (m == own) { float dv = f - v; sl += dv; al += fabsf(dv); cl++; }
                 }
                 energy_ps_finish(J, v, dP, sc, ac, cc, sl, al, cl, dE, eE);
             }

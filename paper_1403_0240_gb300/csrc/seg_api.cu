@@ -94,7 +94,13 @@ struct Stepper {
     cudaGraphExec_t exec = nullptr;
     bool use_graph = true;
     bool dirty = true;
+    bool profile = false;
+    cudaEvent_t ev[7]{};
+    cudaStream_t work = nullptr;   // library stream: graphs are captured and launched here
+    cudaEvent_t fence_in = nullptr, fence_out = nullptr;
 };
+
+constexpr int kStages = 6;
 
 struct seg_batch {
     Stepper st;
@@ -413,20 +419,75 @@ int stepper_build(Stepper& s)
     return SEG_OK;
 }
 
+thread_local bool g_capturing = false;
+
+cudaError_t stage_mark(Stepper& s, int k)
+{
+    if (!s.profile) return cudaSuccess;
+    if (g_capturing) return cudaEventRecordWithFlags(s.ev[k], s.work, cudaEventRecordExternal);
+    return cudaEventRecord(s.ev[k], s.work);
+}
+
 cudaError_t stepper_enqueue(Stepper& s)
 {
     cudaError_t e;
     const int n = (int)s.members.size();
+    if ((e = stage_mark(s, 0)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
-        if (s.grp[gidx].njobs && (e = launch_extract(s.grp[gidx], gidx + 2, s.smem_x[gidx], s.stream)) != cudaSuccess) return e;
+        if (s.grp[gidx].njobs && (e = launch_extract(s.grp[gidx], gidx + 2, s.smem_x[gidx], s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 1)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
-        if (s.grp[gidx].njobs && (e = launch_sobolev(s.grp[gidx], gidx + 2, s.smem_s[gidx], s.stream)) != cudaSuccess) return e;
+        if (s.grp[gidx].njobs && (e = launch_sobolev(s.grp[gidx], gidx + 2, s.smem_s[gidx], s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 2)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
-        if (s.grp[gidx].njobs && (e = launch_flag(s.grp[gidx], s.stream)) != cudaSuccess) return e;
-    if ((e = launch_fixup(s.d_jobs, n, s.sms, s.stream)) != cudaSuccess) return e;
+        if (s.grp[gidx].njobs && (e = launch_flag(s.grp[gidx], s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 3)) != cudaSuccess) return e;
+    if ((e = launch_fixup(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 4)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
-        if (s.grp[gidx].njobs && (e = launch_select(s.grp[gidx], s.d_bc, s.stream)) != cudaSuccess) return e;
-    return launch_commit(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.stream);
+        if (s.grp[gidx].njobs && (e = launch_select(s.grp[gidx], s.d_bc, s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 5)) != cudaSuccess) return e;
+    if ((e = launch_commit(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.work)) != cudaSuccess) return e;
+    return stage_mark(s, 6);
+}
+
+int stepper_set_profile(Stepper& s, bool on)
+{
+    if (on && !s.ev[0])
+        for (int k = 0; k <= kStages; k++) CK(cudaEventCreate(&s.ev[k]));
+    if (s.profile != on) {
+        s.profile = on;
+        stepper_free_graph(s);
+    }
+    return SEG_OK;
+}
+
+int stepper_stage_times(Stepper& s, float* ms, int n)
+{
+    if (!s.profile || !s.ev[0]) return SEG_ESTATE;
+    if (!ms || n < kStages) return SEG_EINVAL;
+    CK(cudaStreamSynchronize(s.stream));
+    if (s.work) CK(cudaStreamSynchronize(s.work));
+    for (int k = 0; k < kStages; k++) CK(cudaEventElapsedTime(&ms[k], s.ev[k], s.ev[k + 1]));
+    return SEG_OK;
+}
+
+void stepper_release(Stepper& s)
+{
+    stepper_free_graph(s);
+    if (s.d_jobs) cudaFree(s.d_jobs);
+    if (s.d_ids) cudaFree(s.d_ids);
+    if (s.d_prefix) cudaFree(s.d_prefix);
+    if (s.d_bc) cudaFree(s.d_bc);
+    if (s.d_gather) cudaFree(s.d_gather);
+    if (s.h_gather) cudaFreeHost(s.h_gather);
+    for (int k = 0; k <= kStages; k++)
+        if (s.ev[k]) cudaEventDestroy(s.ev[k]);
+    if (s.work) cudaStreamSynchronize(s.work);
+    if (s.fence_in) cudaEventDestroy(s.fence_in);
+    if (s.fence_out) cudaEventDestroy(s.fence_out);
+    if (s.work) cudaStreamDestroy(s.work);
+    cudaGetLastError();
 }
 
 int stepper_run(Stepper& s, int iters)
@@ -436,12 +497,19 @@ int stepper_run(Stepper& s, int iters)
         if (rc) return rc;
     }
     if (s.members.empty() || iters <= 0) return SEG_OK;
+    if (!s.work) {
+        CK(cudaStreamCreateWithFlags(&s.work, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&s.fence_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&s.fence_out, cudaEventDisableTiming));
+    }
     if (s.use_graph && !s.exec) {
-        cudaError_t e = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = cudaStreamBeginCapture(s.work, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
+            g_capturing = true;
             cudaError_t e2 = stepper_enqueue(s);
+            g_capturing = false;
             cudaGraph_t g = nullptr;
-            e = cudaStreamEndCapture(s.stream, &g);
+            e = cudaStreamEndCapture(s.work, &g);
             if (e2 == cudaSuccess && e == cudaSuccess && g) {
                 e = cudaGraphInstantiate(&s.exec, g, 0);
                 s.graph = g;
@@ -458,10 +526,16 @@ int stepper_run(Stepper& s, int iters)
         }
         cudaGetLastError();
     }
+    // order the work after everything already queued on the caller's stream, and make
+    // the caller's stream wait for it
+    CK(cudaEventRecord(s.fence_in, s.stream));
+    CK(cudaStreamWaitEvent(s.work, s.fence_in, 0));
     for (int i = 0; i < iters; i++) {
-        if (s.use_graph) CK(cudaGraphLaunch(s.exec, s.stream));
+        if (s.use_graph) CK(cudaGraphLaunch(s.exec, s.work));
         else CK(stepper_enqueue(s));
     }
+    CK(cudaEventRecord(s.fence_out, s.work));
+    CK(cudaStreamWaitEvent(s.stream, s.fence_out, 0));
     return SEG_OK;
 }
 
@@ -488,11 +562,14 @@ int stepper_step(Stepper& s, int iters)
     if (rc) return rc;
     for (int i = 0; i < n; i++) target[i] = s.members[i]->h_ctr->t + iters;
     int todo = iters;
-    for (int pass = 0; pass < 64 && todo > 0; pass++) {
-        rc = stepper_run(s, todo);
-        if (rc) return rc;
-        rc = stepper_read(s);
-        if (rc) return rc;
+    for (int pass = 0; pass < 64; pass++) {
+        if (pass > 0 || todo > 0) {
+            if (todo <= 0) break;
+            rc = stepper_run(s, todo);
+            if (rc) return rc;
+            rc = stepper_read(s);
+            if (rc) return rc;
+        }
         todo = 0;
         bool regrown = false;
         for (int i = 0; i < n; i++) {
@@ -517,6 +594,7 @@ int stepper_step(Stepper& s, int iters)
             if (s.members.size() > 1) return SEG_OK;   // batch: members report their own t
             todo = (int)(target[0] - s.members[0]->h_ctr->t);
         }
+        if (todo <= 0) break;
     }
     return SEG_OK;
 }
@@ -702,6 +780,46 @@ int seg_step(seg_ctx* c, int32_t iters, seg_status* out)
     return c->h_ctr->error ? c->h_ctr->error : SEG_OK;
 }
 
+int seg_step_async(seg_ctx* c, int32_t iters)
+{
+    if (!c || iters < 0) return SEG_EINVAL;
+    if (c->batch) return SEG_ESTATE;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    return stepper_run(*c->own, iters);
+}
+
+int seg_poll(seg_ctx* c, seg_status* out)
+{
+    if (!c) return SEG_EINVAL;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    Stepper& s = c->batch ? c->batch->st : *c->own;
+    if (s.dirty && (rc = stepper_build(s)) != SEG_OK) return rc;
+    rc = stepper_read(s);
+    if (rc) return rc;
+    if (out) *out = c->h_ctr->last;
+    return c->h_ctr->error ? c->h_ctr->error : SEG_OK;
+}
+
+int seg_profile(seg_ctx* c, int32_t on)
+{
+    if (!c) return SEG_EINVAL;
+    if (c->batch) return SEG_ESTATE;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    return stepper_set_profile(*c->own, on != 0);
+}
+
+int seg_stage_times(seg_ctx* c, float* ms, int32_t n)
+{
+    if (!c) return SEG_EINVAL;
+    if (c->batch) return SEG_ESTATE;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    return stepper_stage_times(*c->own, ms, n);
+}
+
 int seg_labels(seg_ctx* c, int32_t* out, size_t n_out)
 {
     if (!c || !out) return SEG_EINVAL;
@@ -817,14 +935,7 @@ void seg_destroy(seg_ctx* c)
     if (cur != c->device) cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->own) {
-        Stepper& s = *c->own;
-        stepper_free_graph(s);
-        if (s.d_jobs) cudaFree(s.d_jobs);
-        if (s.d_ids) cudaFree(s.d_ids);
-        if (s.d_prefix) cudaFree(s.d_prefix);
-        if (s.d_bc) cudaFree(s.d_bc);
-        if (s.d_gather) cudaFree(s.d_gather);
-        if (s.h_gather) cudaFreeHost(s.h_gather);
+        stepper_release(*c->own);
         delete c->own;
     }
     if (c->arena) cudaFree(c->arena);
@@ -896,20 +1007,37 @@ int seg_batch_step(seg_batch* b, int32_t iters, seg_status* statuses, int32_t n_
     return err;
 }
 
+int seg_batch_step_async(seg_batch* b, int32_t iters)
+{
+    if (!b || iters < 0) return SEG_EINVAL;
+    int rc = ensure_device(b->st.device);
+    if (rc) return rc;
+    return stepper_run(b->st, iters);
+}
+
+int seg_batch_poll(seg_batch* b, seg_status* statuses, int32_t n_statuses)
+{
+    if (!b) return SEG_EINVAL;
+    int rc = ensure_device(b->st.device);
+    if (rc) return rc;
+    if (b->st.dirty && (rc = stepper_build(b->st)) != SEG_OK) return rc;
+    rc = stepper_read(b->st);
+    if (rc) return rc;
+    int err = SEG_OK;
+    for (size_t i = 0; i < b->st.members.size(); i++) {
+        const Counters& h = *b->st.members[i]->h_ctr;
+        if (statuses && (int)i < n_statuses) statuses[i] = h.last;
+        if (h.error && !err) err = h.error;
+    }
+    return err;
+}
+
 void seg_batch_destroy(seg_batch* b)
 {
     if (!b) return;
     if (b->st.stream) cudaStreamSynchronize(b->st.stream);
     for (auto* c : b->st.members) c->batch = nullptr;
-    Stepper& s = b->st;
-    stepper_free_graph(s);
-    if (s.d_jobs) cudaFree(s.d_jobs);
-    if (s.d_ids) cudaFree(s.d_ids);
-    if (s.d_prefix) cudaFree(s.d_prefix);
-    if (s.d_bc) cudaFree(s.d_bc);
-    if (s.d_gather) cudaFree(s.d_gather);
-    if (s.h_gather) cudaFreeHost(s.h_gather);
-    cudaGetLastError();
+    stepper_release(b->st);
     delete b;
 }
 

@@ -30,6 +30,7 @@ struct Counters {
     long long t;            // iterations done
     long long best_A;       // smallest accepted count so far, -1 before the first iteration
     long long t_best;
+    long long cum_particles; // particles summed over executed iterations
     seg_status last;        // status of the last executed iteration
 };
 

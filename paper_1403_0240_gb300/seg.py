@@ -33,7 +33,7 @@ class Status(C.Structure):
     _fields_ = [("iteration", C.c_int64), ("n_particles", C.c_int64), ("n_candidates", C.c_int64),
                 ("n_accepted", C.c_int64), ("n_osc", C.c_int64), ("n_fixup", C.c_int64),
                 ("mode_used", C.c_int32), ("converged", C.c_int32), ("mis_rounds", C.c_int32),
-                ("error", C.c_int32)]
+                ("error", C.c_int32), ("particles_total", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -54,6 +54,10 @@ SIGNATURES = [
     ("seg_estimate_bytes", C.c_int, [_P(Params), C.c_int32, _P(C.c_size_t)]),
     ("seg_init", C.c_int, [_P(Params), _V, _V, _V, _P(_V)]),
     ("seg_step", C.c_int, [_V, C.c_int32, _P(Status)]),
+    ("seg_step_async", C.c_int, [_V, C.c_int32]),
+    ("seg_poll", C.c_int, [_V, _P(Status)]),
+    ("seg_profile", C.c_int, [_V, C.c_int32]),
+    ("seg_stage_times", C.c_int, [_V, _P(C.c_float), C.c_int32]),
     ("seg_labels", C.c_int, [_V, _V, C.c_size_t]),
     ("seg_particles", C.c_int, [_V, _P(ParticleBuffers), C.c_int64, _P(C.c_int64)]),
     ("seg_stats", C.c_int, [_V, _V, _V, _V, C.c_int32]),
@@ -66,6 +70,8 @@ SIGNATURES = [
     ("seg_batch_remove", C.c_int, [_V, _V]),
     ("seg_batch_size", C.c_int, [_V]),
     ("seg_batch_step", C.c_int, [_V, C.c_int32, _V, C.c_int32]),
+    ("seg_batch_step_async", C.c_int, [_V, C.c_int32]),
+    ("seg_batch_poll", C.c_int, [_V, _V, C.c_int32]),
     ("seg_batch_destroy", None, [_V]),
     ("seg_debug_simple", C.c_int, [C.c_int32, _V, C.c_int32, _V]),
     ("seg_strerror", C.c_char_p, [C.c_int]),
@@ -208,6 +214,24 @@ class Context:
         _check(lib().seg_step(self.handle, int(iters), C.byref(st)), "seg_step")
         return st.as_dict()
 
+    def step_async(self, iters: int = 1):
+        _check(lib().seg_step_async(self.handle, int(iters)), "seg_step_async")
+
+    def poll(self) -> dict:
+        st = Status()
+        _check(lib().seg_poll(self.handle, C.byref(st)), "seg_poll")
+        return st.as_dict()
+
+    STAGES = ("extract", "sobolev", "flag", "fixup", "select", "commit")
+
+    def profile(self, on: bool = True):
+        _check(lib().seg_profile(self.handle, int(bool(on))), "seg_profile")
+
+    def stage_times(self) -> dict:
+        ms = (C.c_float * len(self.STAGES))()
+        _check(lib().seg_stage_times(self.handle, ms, len(self.STAGES)), "seg_stage_times")
+        return {k: float(ms[i]) for i, k in enumerate(self.STAGES)}
+
     def labels(self, out=None):
         if out is None:
             out = np.empty(self.shape, np.int32)
@@ -286,6 +310,15 @@ class Batch:
         n = len(self.members)
         st = (Status * max(n, 1))()
         _check(lib().seg_batch_step(self._h, int(iters), C.cast(st, C.c_void_p), n), "seg_batch_step")
+        return [st[i].as_dict() for i in range(n)]
+
+    def step_async(self, iters: int = 1):
+        _check(lib().seg_batch_step_async(self._h, int(iters)), "seg_batch_step_async")
+
+    def poll(self) -> list[dict]:
+        n = len(self.members)
+        st = (Status * max(n, 1))()
+        _check(lib().seg_batch_poll(self._h, C.cast(st, C.c_void_p), n), "seg_batch_poll")
         return [st[i].as_dict() for i in range(n)]
 
     def close(self):

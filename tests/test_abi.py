@@ -36,7 +36,7 @@ def test_header_symbols_exported(libseg):
 def test_struct_layouts():
     # seg_params: 2 x int32, 3 x int64, 2 x int32, 3 x double, 5 x int32, 7 reserved int32
     assert C.sizeof(seg.Params) == 112
-    assert C.sizeof(seg.Status) == 64
+    assert C.sizeof(seg.Status) == 72
     assert C.sizeof(seg.State) == 32
     assert C.sizeof(seg.ParticleBuffers) == 9 * C.sizeof(C.c_void_p)
 
