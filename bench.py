@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Sobolev particle-iterations/s"
 UNIT = "particle-iterations/s"
-STAGES = ("extract", "sobolev", "flag", "fixup", "select", "commit")
+STAGES = ("extract", "sobolev", "flag", "fixup", "select", "lists", "rounds", "moves", "finish")
 L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic bytes per unit (one particle, or one accepted move) of each stage: the
@@ -38,9 +38,10 @@ L2_FLUSH_BYTES = 256 << 20
 #   extract = particle write (idx, l, c: 12 B) + amortised label-band reads (8 B)
 #           + image value (4 B) + energy difference out (4 B)
 #   sobolev = particle in (idx, l, c, dE: 16 B) + gradient out (4 B)
-#   flag, fixup, select = 12 B per particle; commit = 12 B per particle + 24 B per move
+#   flag, fixup, select, lists, rounds = 12 B per particle (the survey's a6 figure, split);
+#   moves = 24 B per accepted move (label write and statistics); finish = 12 B per particle
 ALG_BYTES = {"extract": (28, 0), "sobolev": (20, 0), "flag": (12, 0), "fixup": (12, 0),
-             "select": (12, 0), "commit": (12, 24)}
+             "select": (12, 0), "lists": (12, 0), "rounds": (12, 0), "moves": (0, 24), "finish": (12, 0)}
 
 
 def workloads():
@@ -264,7 +265,7 @@ def run_ours(args, world, rank, local, pg):
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stage_ms = {k: 0.0 for k in STAGES}
     step_parts = []
-    accepted = 0
+    accepted = fixups = rounds = 0
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -287,7 +288,10 @@ def run_ours(args, world, rank, local, pg):
         for s_ in STAGES:
             stage_ms[s_] += st[s_]
         done_in_job += 1
-        accepted += ctx.poll()["n_accepted"]
+        sp = ctx.poll()
+        accepted += sp["n_accepted"]
+        fixups += sp["n_fixup"]
+        rounds += sp["mis_rounds"]
     st_last = ctx.poll()
     step_parts.append(st_last["particles_total"] - before)
     torch.cuda.synchronize(dev)
@@ -354,10 +358,12 @@ def run_ours(args, world, rank, local, pg):
             "config": {"workload": name, "description": desc, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed iterations (256 MiB write)",
                        "iterations_per_job": iters_per_job, "mean_particles": mean_parts,
+                       "mean_accepted": accepted / args.steps, "mean_fp64_recomputes": fixups / args.steps,
+                       "mean_selection_rounds": rounds / args.steps,
                        "precision": "float32 gradients with certified bounds, FP64 recompute of uncertified "
                                     "decisions, exact region sums"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            # per step: the six stage kernels of the iteration graph plus the status gather of poll()
+            # per step: the nine stage kernels of the iteration graph plus the status gather of poll()
             "gpu_launches": (len(STAGES) + 1) * args.steps, "clocks": clocks,
             "stages_ms": {k: round(v, 5) for k, v in mean_stage.items()},
             "wall_s": wall}

@@ -143,9 +143,9 @@ int seg_step_async(seg_ctx* c, int32_t iters);
 int seg_poll(seg_ctx* c, seg_status* out);
 
 /* Stage timing: when on, the captured iteration graph also records CUDA events
- * between its stages (extract, sobolev, flag, fixup, select, commit);
- * seg_stage_times waits for the stream and writes the milliseconds each stage took
- * in the most recent iteration (n >= 6), returning SEG_ESTATE when timing is off. */
+ * between its stages (extract, sobolev, flag, fixup, select, lists, rounds, moves,
+ * finish); seg_stage_times waits for the stream and writes the milliseconds each stage
+ * took in the most recent iteration (n >= 9), returning SEG_ESTATE when timing is off. */
 int seg_profile(seg_ctx* c, int32_t on);
 int seg_stage_times(seg_ctx* c, float* ms, int32_t n);
 

@@ -202,17 +202,9 @@ __device__ __forceinline__ double image64(const Job& J, long long i)
     return (double)((const unsigned short*)J.I)[i];
 }
 
-// Eq. 5 at eps = 1/24 in the order written: (1/E) (1 + ((r/E)^2 - r/E + 1/6) / (2 eps)).
-__device__ __forceinline__ double kernel64(int d2, double E)
-{
-    const double eps = 1.0 / 24.0;
-    double r = __dsqrt_rn((double)d2);
-    double x = __ddiv_rn(r, E);
-    double num = __dadd_rn(__dsub_rn(__dmul_rn(x, x), x), 1.0 / 6.0);
-    return __dmul_rn(__ddiv_rn(1.0, E), __dadd_rn(1.0, __ddiv_rn(num, __dmul_rn(2.0, eps))));
-}
-
-__device__ double energy64(const Job& J, unsigned gi, int l, int c)
+// q: index of the particle (gi, l -> c) in the current particle arrays; its exact ball
+// sums are reused when they were stored (piecewise smooth with exact FP64 ball sums).
+__device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
 {
     int x, y, z;
     coords(J, gi, x, y, z);
@@ -227,14 +219,23 @@ __device__ double energy64(const Job& J, unsigned gi, int l, int c)
     } else {
         double sc = 0.0, sl = 0.0;
         long long cc = 0, cl = 0;
-        for (int u = 0; u < J.ps_n; u++) {
-            int4 d = J.ps_off[u];
-            int xx = x + d.z, yy = y + d.y, zz = z + d.x;
-            if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
-            long long j = ((long long)zz * J.H + yy) * J.W + xx;
-            int m = J.L[j];
-            if (m == c) { sc = __dadd_rn(sc, image64(J, j)); cc++; }
-            else if (m == l) { sl = __dadd_rn(sl, image64(J, j)); cl++; }
+        if (J.ps_exact64) {
+            // every partial sum of the row-major FP64 loop is a multiple of 2^e_min below 2^53
+            // units, so that loop is exact and equals the exact integer sum taken by extraction
+            sc = __dmul_rn((double)J.p_qc[q], J.unit64);
+            sl = __dmul_rn((double)J.p_ql[q], J.unit64);
+            cc = J.p_nc[q];
+            cl = J.p_nl[q];
+        } else {
+            for (int u = 0; u < J.ps_n; u++) {
+                int4 d = J.ps_off[u];
+                int xx = x + d.z, yy = y + d.y, zz = z + d.x;
+                if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
+                long long j = ((long long)zz * J.H + yy) * J.W + xx;
+                int m = J.L[j];
+                if (m == c) { sc = __dadd_rn(sc, image64(J, j)); cc++; }
+                else if (m == l) { sl = __dadd_rn(sl, image64(J, j)); cl++; }
+            }
         }
         double a = __dsub_rn(v, __ddiv_rn(sc, (double)cc));
         double b = __dsub_rn(v, __ddiv_rn(sl, (double)cl));
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int n
             const int lp = J.p_l[p], cp = J.p_c[p];
             double gval;
             if (mode == SEG_L2) {
-                gval = lane == 0 ? energy64(J, gi, lp, cp) : 0.0;
+                gval = lane == 0 ? energy64(J, gi, lp, cp, p) : 0.0;
             } else {
                 int x, y, z;
                 coords(J, gi, x, y, z);
@@ -293,11 +294,11 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int n
                             unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
                             unsigned long long e = J.pmap[yi];
                             if ((unsigned)(e >> 32) == tag) {
-                                double K = kernel64(d.w, J.E);
+                                const double K = J.klut64[d.w];
                                 for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi && nt < 6; q++) {
                                     int lq = J.p_l[q], cq = J.p_c[q];
                                     if (lq == lp || cq == lp) {
-                                        tv[nt] = __dmul_rn(K, energy64(J, yi, lq, cq));
+                                        tv[nt] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
                                         ta[nt] = lq == lp ? 1 : 0;
                                         nt++;
                                     }
@@ -620,15 +621,11 @@ __device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* s_red)
 }
 
 constexpr unsigned kMaxRounds = 1u << 20;
+constexpr unsigned kSmallCandidates = 32768;   // at most this many: one block decides alone
 
-__global__ void __launch_bounds__(512) k_commit(const Job* jobs, int njobs, BatchCtl* bc)
+// A: neighbour lists of smaller-key candidates; states reset
+__device__ void commit_lists(const Job* jobs, int njobs, unsigned t0, unsigned stride)
 {
-    __shared__ unsigned s_red[32];
-    const unsigned nblocks = gridDim.x;
-    const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
-    bool ok = true;
-
-    // A
     for (int j = 0; j < njobs; j++) {
         const Job& J = jobs[j];
         Counters* ctr = J.ctr;
@@ -636,7 +633,7 @@ __global__ void __launch_bounds__(512) k_commit(const Job* jobs, int njobs, Batc
         const unsigned nc = ld_volatile(&ctr->n_cand);
         const unsigned tag = ld_volatile(&ctr->iter_tag);
         const int rz = J.ndim == 3 ? 1 : 0;
-        for (unsigned s = gtid; s < nc; s += gstride) {
+        for (unsigned s = t0; s < nc; s += stride) {
             const unsigned gi = J.c_pix[s];
             const double ks = J.c_key[s];
             int x, y, z;
@@ -659,80 +656,69 @@ __global__ void __launch_bounds__(512) k_commit(const Job* jobs, int njobs, Batc
             J.c_state[s] = kUndecided;
         }
     }
-    ok = grid_barrier(bc, nblocks);
+}
 
-    // B
-    unsigned rounds = 0;
-    if (ok) {
-        for (unsigned r = 0;; r++) {
-            unsigned undecided = 0;
-            for (int j = 0; j < njobs; j++) {
-                const Job& J = jobs[j];
-                Counters* ctr = J.ctr;
-                if (job_idle(ctr)) continue;
-                const unsigned nc = ld_volatile(&ctr->n_cand);
-                for (unsigned s = gtid; s < nc; s += gstride) {
-                    if (ld_volatile(J.c_state + s) != kUndecided) continue;
-                    const int n = J.c_nnbr[s];
-                    bool any_acc = false, all_rej = true;
-                    for (int i = 0; i < n; i++) {
-                        int st = ld_volatile(J.c_state + J.c_nbr[(long long)s * J.nbr_stride + i]);
-                        if (st == kAccepted) { any_acc = true; break; }
-                        if (st != kRejected) all_rej = false;
-                    }
-                    if (any_acc) *(volatile int*)(J.c_state + s) = kRejected;
-                    else if (all_rej) *(volatile int*)(J.c_state + s) = kAccepted;
-                    else undecided++;
-                }
+// B: one pass of decisions; returns how many candidates stay undecided
+__device__ unsigned commit_round(const Job* jobs, int njobs, unsigned t0, unsigned stride)
+{
+    unsigned undecided = 0;
+    for (int j = 0; j < njobs; j++) {
+        const Job& J = jobs[j];
+        Counters* ctr = J.ctr;
+        if (job_idle(ctr)) continue;
+        const unsigned nc = ld_volatile(&ctr->n_cand);
+        for (unsigned s = t0; s < nc; s += stride) {
+            if (ld_volatile(J.c_state + s) != kUndecided) continue;
+            const int n = J.c_nnbr[s];
+            bool any_acc = false, all_rej = true;
+            for (int i = 0; i < n; i++) {
+                int st = ld_volatile(J.c_state + J.c_nbr[(long long)s * J.nbr_stride + i]);
+                if (st == kAccepted) { any_acc = true; break; }
+                if (st != kRejected) all_rej = false;
             }
-            unsigned bs = block_sum(undecided, s_red);
-            if (threadIdx.x == 0) {
-                if (bs) atomicAdd(&bc->rounds_cnt[r % 3], bs);
-                if (blockIdx.x == 0) bc->rounds_cnt[(r + 1) % 3] = 0;
-            }
-            if (!grid_barrier(bc, nblocks)) { ok = false; break; }
-            unsigned rem = ld_volatile(&bc->rounds_cnt[r % 3]);
-            if (rem == 0) { rounds = r + 1; break; }
-            if (r + 1 >= kMaxRounds) {
-                if (gtid == 0) atomicExch(&bc->err, SEG_ETIMEOUT);
-                ok = false;
-                break;
-            }
+            if (any_acc) *(volatile int*)(J.c_state + s) = kRejected;
+            else if (all_rej) *(volatile int*)(J.c_state + s) = kAccepted;
+            else undecided++;
         }
     }
+    return undecided;
+}
 
-    // C
-    if (ok) {
-        for (int j = 0; j < njobs; j++) {
-            const Job& J = jobs[j];
-            Counters* ctr = J.ctr;
-            if (job_idle(ctr)) continue;
-            const unsigned nc = ld_volatile(&ctr->n_cand);
-            unsigned acc = 0;
-            for (unsigned s = gtid; s < nc; s += gstride) {
-                if (J.c_state[s] != kAccepted) continue;
-                const int p = J.c_best[s];
-                const unsigned gi = J.c_pix[s];
-                const int l = J.p_l[p], c = J.p_c[p];
-                J.L[gi] = c;
-                J.p_flags[p] |= kFlagAcc;
-                stats_move(J, gi, l, -1);
-                stats_move(J, gi, c, +1);
-                acc++;
-            }
-            unsigned bs = block_sum(acc, s_red);
-            if (threadIdx.x == 0 && bs) atomicAdd(&ctr->n_accepted, bs);
+// C: accepted moves change labels and the exact region sums
+__device__ void commit_moves(const Job* jobs, int njobs, unsigned t0, unsigned stride, unsigned* s_red)
+{
+    for (int j = 0; j < njobs; j++) {
+        const Job& J = jobs[j];
+        Counters* ctr = J.ctr;
+        if (job_idle(ctr)) continue;
+        const unsigned nc = ld_volatile(&ctr->n_cand);
+        unsigned acc = 0;
+        for (unsigned s = t0; s < nc; s += stride) {
+            if (ld_volatile(J.c_state + s) != kAccepted) continue;
+            const int p = J.c_best[s];
+            const unsigned gi = J.c_pix[s];
+            const int l = J.p_l[p], c = J.p_c[p];
+            J.L[gi] = c;
+            J.p_flags[p] |= kFlagAcc;
+            stats_move(J, gi, l, -1);
+            stats_move(J, gi, c, +1);
+            acc++;
         }
-        ok = grid_barrier(bc, nblocks);
+        unsigned bs = block_sum(acc, s_red);
+        if (threadIdx.x == 0 && bs) atomicAdd(&ctr->n_accepted, bs);
     }
+}
 
-    // D
+// D: region tables, oscillation fallback, status and counters for the next iteration
+__device__ void commit_finish(const Job* jobs, int njobs, unsigned t0, unsigned stride, bool ok, unsigned rounds,
+                              BatchCtl* bc)
+{
     for (int j = 0; j < njobs; j++) {
         const Job& J = jobs[j];
         if (ok && !job_idle(J.ctr))
-            for (int m = (int)gtid; m < J.M; m += (int)gstride) finalize_label(J, m);
+            for (int m = (int)t0; m < J.M; m += (int)stride) finalize_label(J, m);
     }
-    for (int j = (int)gtid; j < njobs; j += (int)gstride) {
+    for (int j = (int)t0; j < njobs; j += (int)stride) {
         const Job& J = jobs[j];
         Counters* c = J.ctr;
         if (!ok) atomicExch(&c->error, ld_volatile(&bc->err) ? ld_volatile(&bc->err) : SEG_ETIMEOUT);
@@ -781,7 +767,7 @@ __global__ void __launch_bounds__(512) k_commit(const Job* jobs, int njobs, Batc
         c->n_osc = 0;
         c->skip = c->converged;
     }
-    if (gtid == 0) {
+    if (t0 == 0) {
         bc->ticket[0] = 0;
         bc->ticket[1] = 0;
         bc->rounds_cnt[0] = 0;
@@ -790,12 +776,134 @@ __global__ void __launch_bounds__(512) k_commit(const Job* jobs, int njobs, Batc
     }
 }
 
-cudaError_t commit_occupancy(int block, int* blocks_per_sm)
+// A, as its own grid: neighbour lists and state reset for every candidate of every job
+__global__ void __launch_bounds__(256) k_lists(const Job* jobs, int njobs)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_commit, block, 0);
+    commit_lists(jobs, njobs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-cudaError_t launch_commit(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s)
+// B: the rounds. With few candidates one block runs them on shared-memory states with
+// block barriers; otherwise the whole co-resident grid runs them with bounded grid barriers.
+constexpr int kMaxSmallJobs = 1024;
+
+__global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, BatchCtl* bc)
+{
+    __shared__ unsigned s_red[32];
+    __shared__ unsigned s_total, s_flag;
+    __shared__ unsigned s_base[kMaxSmallJobs + 1];
+    __shared__ unsigned char s_state[kSmallCandidates];
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        const bool small_jobs = njobs <= kMaxSmallJobs;
+        for (int j = 0; j < njobs; j++) {
+            if (small_jobs) s_base[j] = t;
+            if (!job_idle(jobs[j].ctr)) t += ld_volatile(&jobs[j].ctr->n_cand);
+        }
+        if (small_jobs) s_base[njobs] = t;
+        s_total = small_jobs ? t : 0xffffffffu;
+    }
+    __syncthreads();
+    const unsigned total = s_total;
+    if (total <= kSmallCandidates) {
+        if (blockIdx.x != 0) return;
+        volatile unsigned char* st = s_state;
+        for (unsigned i = threadIdx.x; i < total; i += blockDim.x) st[i] = kUndecided;
+        __syncthreads();
+        unsigned rounds = 0;
+        bool ok = true;
+        for (unsigned r = 0;; r++) {
+            unsigned und = 0;
+            for (int j = 0; j < njobs; j++) {
+                const Job& J = jobs[j];
+                if (job_idle(J.ctr)) continue;
+                const unsigned nc = ld_volatile(&J.ctr->n_cand);
+                const unsigned b = s_base[j];
+                for (unsigned s = threadIdx.x; s < nc; s += blockDim.x) {
+                    if (st[b + s] != kUndecided) continue;
+                    const int n = J.c_nnbr[s];
+                    const int* nb = J.c_nbr + (long long)s * J.nbr_stride;
+                    bool any_acc = false, all_rej = true;
+                    for (int i = 0; i < n; i++) {
+                        const unsigned char v = st[b + nb[i]];
+                        if (v == kAccepted) { any_acc = true; break; }
+                        if (v != kRejected) all_rej = false;
+                    }
+                    if (any_acc) st[b + s] = kRejected;
+                    else if (all_rej) st[b + s] = kAccepted;
+                    else und++;
+                }
+            }
+            const unsigned bs = block_sum(und, s_red);
+            if (threadIdx.x == 0) s_flag = bs;
+            __syncthreads();
+            const unsigned rem = s_flag;
+            __syncthreads();
+            if (rem == 0) { rounds = r + 1; break; }
+            if (r + 1 >= kMaxRounds) { ok = false; break; }
+        }
+        for (int j = 0; j < njobs; j++) {
+            const Job& J = jobs[j];
+            if (job_idle(J.ctr)) continue;
+            const unsigned nc = ld_volatile(&J.ctr->n_cand);
+            for (unsigned s = threadIdx.x; s < nc; s += blockDim.x) J.c_state[s] = st[s_base[j] + s];
+        }
+        if (threadIdx.x == 0) {
+            bc->rounds_done = rounds;
+            if (!ok) atomicExch(&bc->err, SEG_ETIMEOUT);
+        }
+        return;
+    }
+
+    const unsigned nblocks = gridDim.x;
+    const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    unsigned rounds = 0;
+    for (unsigned r = 0;; r++) {
+        unsigned undecided = commit_round(jobs, njobs, gtid, gstride);
+        unsigned bs = block_sum(undecided, s_red);
+        if (threadIdx.x == 0) {
+            if (bs) atomicAdd(&bc->rounds_cnt[r % 3], bs);
+            if (blockIdx.x == 0) bc->rounds_cnt[(r + 1) % 3] = 0;
+        }
+        if (!grid_barrier(bc, nblocks)) break;
+        unsigned rem = ld_volatile(&bc->rounds_cnt[r % 3]);
+        if (rem == 0) { rounds = r + 1; break; }
+        if (r + 1 >= kMaxRounds) {
+            if (gtid == 0) atomicExch(&bc->err, SEG_ETIMEOUT);
+            break;
+        }
+    }
+    if (gtid == 0) bc->rounds_done = rounds;
+}
+
+// C, as its own grid
+__global__ void __launch_bounds__(256) k_moves(const Job* jobs, int njobs, const BatchCtl* bc)
+{
+    __shared__ unsigned s_red[32];
+    if (ld_volatile(&bc->err)) return;
+    commit_moves(jobs, njobs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, s_red);
+}
+
+// D, as its own grid
+__global__ void __launch_bounds__(256) k_finish(const Job* jobs, int njobs, BatchCtl* bc)
+{
+    const bool ok = ld_volatile(&bc->err) == 0;
+    commit_finish(jobs, njobs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, ok,
+                  ld_volatile(&bc->rounds_done), bc);
+}
+
+cudaError_t commit_occupancy(int block, int* blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_rounds, block, 0);
+}
+
+cudaError_t launch_lists(const Job* jobs, int njobs, int sms, cudaStream_t s)
+{
+    k_lists<<<sms * 4, 256, 0, s>>>(jobs, njobs);
+    return cudaGetLastError();
+}
+
+// the rounds kernel is cooperative: every block co-resident
+cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -807,7 +915,19 @@ cudaError_t launch_commit(const Job* jobs, int njobs, BatchCtl* bc, int grid, in
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_commit, jobs, njobs, bc);
+    return cudaLaunchKernelEx(&cfg, k_rounds, jobs, njobs, bc);
+}
+
+cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s)
+{
+    k_moves<<<sms * 4, 256, 0, s>>>(jobs, njobs, bc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s)
+{
+    k_finish<<<sms, 256, 0, s>>>(jobs, njobs, bc);
+    return cudaGetLastError();
 }
 
 }  // namespace segk

@@ -117,10 +117,38 @@ __device__ __forceinline__ void energy_ps_finish(const Job& J, float v, int dP, 
     eE = err * 1.001f;
 }
 
+// Same with exact fixed-point ball sums: isc = sum over the c-part of the ball of q(I) - q(v)
+// (exact), so a = v - mu_c = -(isc / n_c) * 2^e_min with two float32 roundings.
+// ac, al: sums of |I| over each part (for the FP64 margin only).
+__device__ __forceinline__ void energy_ps_finish_int(const Job& J, float v, int dP, long long isc, int cc,
+                                                     long long isl, int cl, float& dE, float& eE)
+{
+    float a = -((float)isc / (float)cc) * J.unit32;
+    float b = -((float)isl / (float)cl) * J.unit32;
+    float ea = 1.0001f * kU * fabsf(a), eb = 1.0001f * kU * fabsf(b);
+    float aa = a * a, bb = b * b;
+    float eaa = (2.0f * fabsf(a) + ea) * ea + kU * aa;
+    float ebb = (2.0f * fabsf(b) + eb) * eb + kU * bb;
+    float d = aa - bb;
+    float lp = J.lambda32 * (float)dP;
+    dE = d + lp;
+    float mx = J.maxabs + fabsf(v);
+    float err = eaa + ebb + kU * (fabsf(d) + fabsf(lp) + fabsf(dE)) +
+                kFp64Margin * (aa + bb + fabsf(lp) + 2.0f * mx * mx);
+    eE = err * 1.001f;
+}
+
 __device__ __forceinline__ float image_at(const Job& J, long long i)
 {
     if (J.dtype == SEG_F32) return __ldg((const float*)J.I + i);
     return (float)__ldg((const unsigned short*)J.I + i);
+}
+
+// the image value as an exact fixed-point integer (see fixed_of_f32)
+__device__ __forceinline__ long long image_q(const Job& J, long long i)
+{
+    if (J.dtype == SEG_F32) return fixed_of_f32(__ldg((const float*)J.I + i), J.slot_lo);
+    return (long long)__ldg((const unsigned short*)J.I + i);
 }
 
 // --------------------------------------------------------------------------
@@ -147,22 +175,34 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     const int h = J.halo, hz = NDIM == 3 ? J.halo : 0;
     const int bx = b.x1 - b.x0 + 2 * h, by = b.y1 - b.y0 + 2 * h, bz = b.z1 - b.z0 + 2 * hz;
     const int nbox = bx * by * bz;
-    int* sL = (int*)smem;
-    float* sI = (float*)(sL + nbox);
+    // shared layout: [fixed-point image (int64) | float image] [labels] [cell starts]
     const bool stage_img = J.ps_staged != 0;
+    const bool use_int = J.ps_int != 0;
+    long long* sQ = (long long*)smem;
+    float* sI = (float*)smem;
+    const size_t img_bytes = stage_img ? (size_t)nbox * (use_int ? 8 : 4) : 0;
+    int* sL = (int*)(smem + img_bytes);
+    unsigned* s_cstart = (unsigned*)(sL + nbox);
     // labels (and, for the 2D piecewise-smooth model, the image) with halo; -1 outside
     for (int i = tid; i < nbox; i += blockDim.x) {
         int lx = i % bx, ly = (i / bx) % by, lz = i / (bx * by);
         int x = b.x0 - h + lx, y = b.y0 - h + ly, z = b.z0 - hz + lz;
         int lab = -1;
         float val = 0.0f;
+        long long qval = 0;
         if (x >= 0 && x < J.W && y >= 0 && y < J.H && z >= 0 && z < J.D) {
             long long gi = ((long long)z * J.H + y) * J.W + x;
             lab = __ldg(J.L + gi);
-            if (stage_img) val = image_at(J, gi);
+            if (stage_img) {
+                if (use_int) qval = image_q(J, gi);
+                else val = image_at(J, gi);
+            }
         }
         sL[i] = lab;
-        if (stage_img) sI[i] = val;
+        if (stage_img) {
+            if (use_int) sQ[i] = qval;
+            else sI[i] = val;
+        }
     }
     __syncthreads();
 
@@ -172,7 +212,6 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     const int tile_q = ncell * cellvol;
     const int chunk = (tile_q + blockDim.x - 1) / blockDim.x;
     const int q0 = min(tid * chunk, tile_q), q1 = min(q0 + chunk, tile_q);
-    unsigned* s_cstart = (unsigned*)(sI + (stage_img ? nbox : 0));
 
     auto pixel_of = [&](int q, int& x, int& y, int& z) -> bool {
         int kc = q / cellvol, r = q - kc * cellvol;
@@ -210,6 +249,20 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         }
         return n;
     };
+    // change of the number of unlike neighbour pairs when the pixel goes from own to c
+    auto delta_p = [&](int si, int own, int c) -> int {
+        int nb[6];
+        nb[0] = sL[si - 1]; nb[1] = sL[si + 1]; nb[2] = sL[si - bx]; nb[3] = sL[si + bx];
+        int nn = 4;
+        if (NDIM == 3) { nb[4] = sL[si - bx * by]; nb[5] = sL[si + bx * by]; nn = 6; }
+        int dP = 0;
+        for (int u = 0; u < nn; u++) {
+            int m = nb[u];
+            if (m < 0) continue;
+            dP += (int)(m != c) - (int)(m != own);
+        }
+        return dP;
+    };
 
     unsigned cnt = 0;
     for (int q = q0; q < q1; q++) {
@@ -220,43 +273,62 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     unsigned total;
     unsigned off = block_excl_scan(cnt, s_warp, total);
 
-    // decoupled look-back over the tiles of this job
-    if (tid == 0) {
+    // decoupled look-back over the tiles of this job: warp 0 inspects 32 predecessors per
+    // round trip, nearest first, and stops at the first one that knows its inclusive prefix
+    if (tid < 32) {
+        const int lane = tid;
         const unsigned long long ep = (unsigned long long)(tag & 0x3fffffffu) << 34;
+        const unsigned long long emask = ~((1ull << 34) - 1);
         unsigned excl = 0;
-        if (k == 0) {
-            atomicExch(J.tile_word + 0, ep | (2ull << 32) | total);
-        } else {
-            atomicExch(J.tile_word + k, ep | (1ull << 32) | total);
-            long long i = (long long)k - 1;
+        if (lane == 0) atomicExch(J.tile_word + k, ep | ((k == 0 ? 2ull : 1ull) << 32) | total);
+        if (k > 0) {
+            long long win_end = (long long)k - 1;
             unsigned spins = 0;
-            while (i >= 0) {
-                unsigned long long w = ld_volatile(J.tile_word + i);
-                unsigned st = (unsigned)((w >> 32) & 3u);
-                if ((w & ~((1ull << 34) - 1)) != ep || st == 0) {
-                    if (++spins > kSpinLimit) { atomicExch(&ctr->error, SEG_ETIMEOUT); break; }
+            while (true) {
+                const long long i = win_end - lane;
+                unsigned st = 2, val = 0;          // before tile 0: an inclusive prefix of 0
+                if (i >= 0) {
+                    unsigned long long w = ld_volatile(J.tile_word + i);
+                    st = (w & emask) == ep ? (unsigned)((w >> 32) & 3u) : 0u;
+                    val = (unsigned)w;
+                }
+                const unsigned m2 = __ballot_sync(0xffffffffu, st == 2);
+                const unsigned m0 = __ballot_sync(0xffffffffu, st == 0);
+                const int first2 = m2 ? __ffs(m2) - 1 : 31;
+                const unsigned need = first2 == 31 ? 0xffffffffu : ((2u << first2) - 1u);
+                if (m0 & need) {
+                    if (++spins > kSpinLimit) {
+                        if (lane == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
                     continue;
                 }
-                excl += (unsigned)w;
-                if (st == 2) break;
-                i--;
+                unsigned add = lane <= first2 ? val : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+                excl += add;
+                if (m2) break;
+                win_end -= 32;
             }
             __threadfence();
-            atomicExch(J.tile_word + k, ep | (2ull << 32) | (excl + total));
+            if (lane == 0) atomicExch(J.tile_word + k, ep | (2ull << 32) | (excl + total));
         }
-        s_base = excl;
-        J.tile_start[k] = excl;
-        J.tile_count[k] = total;
-        if (k == (unsigned)J.ntiles - 1) {
-            ctr->n_particles = excl + total;
-            if ((long long)excl + total > J.pcap) atomicMax(&ctr->need, excl + total);
+        if (lane == 0) {
+            s_base = excl;
+            J.tile_start[k] = excl;
+            J.tile_count[k] = total;
+            if (k == (unsigned)J.ntiles - 1) {
+                ctr->n_particles = excl + total;
+                if ((long long)excl + total > J.pcap) atomicMax(&ctr->need, excl + total);
+            }
         }
     }
     __syncthreads();
     const unsigned base = s_base;
     const bool fits = (long long)base + total <= J.pcap;
 
-    // emit particles with their energy differences
+    // emit particles (with their energy differences for the piecewise-constant model)
     unsigned o = base + off;
     for (int q = q0; q < q1; q++) {
         int x, y, z, labs[6];
@@ -267,53 +339,20 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         const long long gi = ((long long)z * J.H + y) * J.W + x;
         const int si = sidx(x, y, z);
         const int own = sL[si];
-        const float v = stage_img ? sI[si] : image_at(J, gi);
-        int nb[6];
-        nb[0] = sL[si - 1]; nb[1] = sL[si + 1]; nb[2] = sL[si - bx]; nb[3] = sL[si + bx];
-        int nn = 4;
-        if (NDIM == 3) { nb[4] = sL[si - bx * by]; nb[5] = sL[si + bx * by]; nn = 6; }
         if (fits) J.pmap[gi] = ((unsigned long long)tag << 32) | o;
+        const float v = J.model == SEG_PC ? image_at(J, gi) : 0.0f;
         for (int j = 0; j < n; j++, o++) {
             const int c = labs[j];
-            int dP = 0;
-            for (int u = 0; u < nn; u++) {
-                int m = nb[u];
-                if (m < 0) continue;
-                dP += (int)(m != c) - (int)(m != own);
-            }
-            float dE, eE;
+            if (!fits) continue;
+            J.p_idx[o] = (unsigned)gi;
+            J.p_l[o] = own;
+            J.p_c[o] = c;
+            J.p_flags[o] = 0;
             if (J.model == SEG_PC) {
-                energy_pc(J, v, own, c, dP, dE, eE);
-            } else {
-                float sc = 0.f, ac = 0.f, sl = 0.f, al = 0.f;
-                int cc = 0, cl = 0;
-                for (int u = 0; u < J.ps_n; u++) {
-                    int4 d = __ldg(J.ps_off + u);
-                    int yx = x + d.z, yy = y + d.y, yz = z + d.x;
-                    int m;
-                    float f;
-                    if (stage_img) {
-                        int sj = si + d.y * bx + d.z;
-                        m = sL[sj];
-                        f = sI[sj];
-                    } else {
-                        if (yx < 0 || yx >= J.W || yy < 0 || yy >= J.H || yz < 0 || yz >= J.D) continue;
-                        long long gj2 = ((long long)yz * J.H + yy) * J.W + yx;
-                        m = __ldg(J.L + gj2);
-                        f = image_at(J, gj2);
-                    }
-                    if (m == c) { float dv = f - v; sc += dv; ac += fabsf(dv); cc++; }
-                    else if (m == own) { float dv = f - v; sl += dv; al += fabsf(dv); cl++; }
-                }
-                energy_ps_finish(J, v, dP, sc, ac, cc, sl, al, cl, dE, eE);
-            }
-            if (fits) {
-                J.p_idx[o] = (unsigned)gi;
-                J.p_l[o] = own;
-                J.p_c[o] = c;
+                float dE, eE;
+                energy_pc(J, v, own, c, delta_p(si, own, c), dE, eE);
                 J.p_dE[o] = dE;
                 J.p_eE[o] = eE;
-                J.p_flags[o] = 0;
             }
         }
     }
@@ -326,6 +365,78 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         J.cell_start[cid] = base + s_cstart[kc];
         J.cell_count[cid] = s_cstart[kc + 1] - s_cstart[kc];
     }
+    if (J.model != SEG_PS || !fits) return;
+
+    // piecewise-smooth energy: one particle per warp, the lanes share the ball offsets
+    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (unsigned o2 = base + warp; o2 < base + total; o2 += nw) {
+        const unsigned gi = J.p_idx[o2];
+        const int own = J.p_l[o2], c = J.p_c[o2];
+        const int x = (int)(gi % (unsigned)J.W);
+        const int y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
+        const int z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+        const int si = sidx(x, y, z);
+        const float v = stage_img && !use_int ? sI[si] : image_at(J, gi);
+        long long qv = 0;
+        if (use_int) qv = stage_img ? sQ[si] : image_q(J, gi);
+        long long isc = 0, isl = 0;
+        float fsc = 0.f, fsl = 0.f, ac = 0.f, al = 0.f;
+        int cc = 0, cl = 0;
+        for (int u = lane; u < J.ps_n; u += 32) {
+            const int4 d = __ldg(J.ps_off + u);
+            int m;
+            float f = 0.f;
+            long long qy = 0;
+            if (stage_img) {
+                const int sj = si + d.y * bx + d.z;
+                m = sL[sj];
+                if (use_int) qy = sQ[sj]; else f = sI[sj];
+            } else {
+                const int yx = x + d.z, yy = y + d.y, yz = z + d.x;
+                if (yx < 0 || yx >= J.W || yy < 0 || yy >= J.H || yz < 0 || yz >= J.D) continue;
+                const long long gj2 = ((long long)yz * J.H + yy) * J.W + yx;
+                m = __ldg(J.L + gj2);
+                if (m != c && m != own) continue;
+                if (use_int) qy = image_q(J, gj2); else f = image_at(J, gj2);
+            }
+            if (m == c) {
+                if (use_int) isc += qy - qv;
+                else { float dv = f - v; fsc += dv; ac += fabsf(dv); }
+                cc++;
+            } else if (m == own) {
+                if (use_int) isl += qy - qv;
+                else { float dv = f - v; fsl += dv; al += fabsf(dv); }
+                cl++;
+            }
+        }
+#pragma unroll
+        for (int w2 = 16; w2 > 0; w2 >>= 1) {
+            isc += __shfl_xor_sync(0xffffffffu, isc, w2);
+            isl += __shfl_xor_sync(0xffffffffu, isl, w2);
+            fsc += __shfl_xor_sync(0xffffffffu, fsc, w2);
+            fsl += __shfl_xor_sync(0xffffffffu, fsl, w2);
+            ac += __shfl_xor_sync(0xffffffffu, ac, w2);
+            al += __shfl_xor_sync(0xffffffffu, al, w2);
+            cc += __shfl_xor_sync(0xffffffffu, cc, w2);
+            cl += __shfl_xor_sync(0xffffffffu, cl, w2);
+        }
+        if (lane == 0) {
+            float dE, eE;
+            const int dP = delta_p(si, own, c);
+            if (use_int) {
+                energy_ps_finish_int(J, v, dP, isc, cc, isl, cl, dE, eE);
+                // keep the exact ball sums for the FP64 recompute
+                J.p_qc[o2] = isc + (long long)cc * qv;
+                J.p_ql[o2] = isl + (long long)cl * qv;
+                J.p_nc[o2] = cc;
+                J.p_nl[o2] = cl;
+            } else {
+                energy_ps_finish(J, v, dP, fsc, ac, cc, fsl, al, cl, dE, eE);
+            }
+            J.p_dE[o2] = dE;
+            J.p_eE[o2] = eE;
+        }
+    }
 }
 
 size_t extract_smem_bytes(const Job& J)
@@ -334,9 +445,9 @@ size_t extract_smem_bytes(const Job& J)
     int h = J.halo, hz = J.ndim == 3 ? J.halo : 0;
     long long bx = (long long)J.tcx * s + 2 * h, by = (long long)J.tcy * s + 2 * h, bz = (long long)J.tcz * sz + 2 * hz;
     long long nbox = bx * by * bz;
-    bool img = J.ps_staged != 0;
+    long long img = J.ps_staged ? (J.ps_int ? 8 : 4) : 0;
     long long ncell = (long long)J.tcx * J.tcy * J.tcz;
-    return (size_t)(nbox * 4 * (img ? 2 : 1) + (ncell + 1) * 4);
+    return (size_t)(nbox * (4 + img) + (ncell + 1) * 4);
 }
 
 cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t st)
@@ -352,7 +463,8 @@ cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t s
 // Q_p = {q : d < E/2, l_q = l_p}, Q'_p = {q : d < E/2, c_q = l_p}; empty sets give 0.
 // The particles of the tile's cells and of a one-cell ring around them are staged in
 // shared memory (or read from global memory when they do not fit).
-constexpr int kStageCap = 3072;
+constexpr int kStageCap2 = 1024;   // staged particles per 2D tile (more: read from global memory)
+constexpr int kStageCap3 = 4096;   // per 3D tile
 
 struct Staged {
     unsigned pos;   // packed (z << 20) | (y << 10) | x relative to the staged box origin
@@ -417,7 +529,7 @@ __global__ void __launch_bounds__(kBlock) k_sobolev(Group g)
     if (tid == 0) { s_eoff[ne] = total; s_osc = 0; }
     for (int d2 = tid; d2 <= J.r2max && d2 < 256; d2 += blockDim.x) s_klut[d2] = __ldg(J.klut + d2);
     __syncthreads();
-    const bool staged = total <= (unsigned)kStageCap && J.r2max < 256;
+    const bool staged = total <= (unsigned)(NDIM == 3 ? kStageCap3 : kStageCap2) && J.r2max < 256;
     if (staged) {
         for (unsigned i = tid; i < total; i += blockDim.x) {
             int lo = 0, hi = ne - 1;
@@ -527,7 +639,7 @@ __global__ void __launch_bounds__(kBlock) k_sobolev(Group g)
 size_t sobolev_smem_bytes(const Job& J)
 {
     long long ne = (long long)(J.tcx + 2) * (J.tcy + 2) * (J.ndim == 3 ? J.tcz + 2 : J.tcz);
-    return (size_t)(((ne + 2) & ~1LL) * 4 + (long long)kStageCap * sizeof(Staged));
+    return (size_t)(((ne + 2) & ~1LL) * 4 + (long long)(J.ndim == 3 ? kStageCap3 : kStageCap2) * sizeof(Staged));
 }
 
 cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t st)

@@ -89,18 +89,18 @@ struct Stepper {
     int cap_gather = 0;
     Group grp[2]{};
     size_t smem_x[2]{}, smem_s[2]{};
-    int commit_grid = 0, commit_block = 512;
+    int commit_grid = 0, commit_block = 1024;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool use_graph = true;
     bool dirty = true;
     bool profile = false;
-    cudaEvent_t ev[7]{};
+    cudaEvent_t ev[10]{};
     cudaStream_t work = nullptr;   // library stream: graphs are captured and launched here
     cudaEvent_t fence_in = nullptr, fence_out = nullptr;
 };
 
-constexpr int kStages = 6;
+constexpr int kStages = 9;
 
 struct seg_batch {
     Stepper st;
@@ -166,6 +166,7 @@ int largest_d2_below(double cutoff)
 struct Plan {
     Job h{};
     std::vector<float> klut;
+    std::vector<double> klut64;
     std::vector<int4> ps_off, nb_off;
     Arena fixed;
 };
@@ -214,7 +215,11 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     h.nS = nS;
     h.nQ = 2 * (nS - 1) + 25;
     P.klut.resize(h.r2max + 1);
-    for (int d2 = 0; d2 <= h.r2max; d2++) P.klut[d2] = (float)kernel_eq5(std::sqrt((double)d2), h.E);
+    P.klut64.resize(h.r2max + 1);
+    for (int d2 = 0; d2 <= h.r2max; d2++) {
+        P.klut64[d2] = kernel_eq5(std::sqrt((double)d2), h.E);
+        P.klut[d2] = (float)P.klut64[d2];
+    }
     const int rz = h.ndim == 3 ? 1 : 0;
     if (h.model == SEG_PS) {
         const double R2 = p->ps_radius * p->ps_radius;
@@ -234,6 +239,18 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
             }
     h.ps_n = (int)P.ps_off.size();
     h.nb_n = (int)P.nb_off.size();
+    // exact ball sums: |q| < 2^(23 + nS) for float32 (2^16 for uint16); a ball sum of ps_n terms
+    // needs log2(ps_n) more bits, a sum of shifted values one more; int64 holds 63 bits and an
+    // FP64 partial sum is exact below 2^53 units
+    int lg = 0;
+    while ((1LL << lg) < (long long)std::max(1, h.ps_n)) lg++;
+    const int qbits = h.dtype == SEG_F32 ? 23 + nS : 16;
+    h.e_min = h.dtype == SEG_F32 ? slot_lo - 150 : 0;
+    const bool unit_ok = h.e_min >= -120 && h.e_min <= 100;
+    h.ps_int = (h.model == SEG_PS && unit_ok && qbits + lg + 1 <= 62) ? 1 : 0;
+    h.ps_exact64 = (h.ps_int && qbits + lg <= 53) ? 1 : 0;
+    h.unit32 = unit_ok ? std::ldexp(1.0f, h.e_min) : 0.0f;
+    h.unit64 = std::ldexp(1.0, h.e_min);
 
     Arena& A = P.fixed;
     const long long npix = h.npix;
@@ -259,6 +276,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     A.add(&h.wp32, M);
     A.add(&h.wm32, M);
     A.add((float**)&h.klut, P.klut.size());
+    A.add((double**)&h.klut64, P.klut64.size());
     A.add((int4**)&h.ps_off, std::max<size_t>(1, P.ps_off.size()));
     A.add((int4**)&h.nb_off, P.nb_off.size());
     A.add(&h.ctr, 1);
@@ -277,6 +295,10 @@ size_t particle_bytes(long long pcap, int stride)
     A.add(&h.p_eg, pcap);
     A.add(&h.p_key, pcap);
     A.add(&h.p_flags, pcap);
+    A.add(&h.p_qc, pcap);
+    A.add(&h.p_ql, pcap);
+    A.add(&h.p_nc, pcap);
+    A.add(&h.p_nl, pcap);
     A.add(&h.pix_cand, pcap);
     A.add(&h.flag_list, pcap);
     A.add(&h.c_best, pcap);
@@ -300,6 +322,10 @@ void assign_particles(Job& h, char* base, long long pcap)
     A.add(&h.p_eg, pcap);
     A.add(&h.p_key, pcap);
     A.add(&h.p_flags, pcap);
+    A.add(&h.p_qc, pcap);
+    A.add(&h.p_ql, pcap);
+    A.add(&h.p_nc, pcap);
+    A.add(&h.p_nl, pcap);
     A.add(&h.pix_cand, pcap);
     A.add(&h.flag_list, pcap);
     A.add(&h.c_best, pcap);
@@ -413,7 +439,7 @@ int stepper_build(Stepper& s)
     int per_sm = 0;
     CK(commit_occupancy(s.commit_block, &per_sm));
     if (per_sm < 1) return cuda_fail(cudaErrorCooperativeLaunchTooLarge, "commit occupancy");
-    s.commit_grid = s.sms * std::min(per_sm, 2);
+    s.commit_grid = s.sms * std::min(per_sm, 1);
     CK(cudaStreamSynchronize(s.stream));
     s.dirty = false;
     return SEG_OK;
@@ -447,8 +473,14 @@ cudaError_t stepper_enqueue(Stepper& s)
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_select(s.grp[gidx], s.d_bc, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 5)) != cudaSuccess) return e;
-    if ((e = launch_commit(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.work)) != cudaSuccess) return e;
-    return stage_mark(s, 6);
+    if ((e = launch_lists(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 6)) != cudaSuccess) return e;
+    if ((e = launch_rounds(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 7)) != cudaSuccess) return e;
+    if ((e = launch_moves(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 8)) != cudaSuccess) return e;
+    if ((e = launch_finish(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
+    return stage_mark(s, 9);
 }
 
 int stepper_set_profile(Stepper& s, bool on)
@@ -658,6 +690,7 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     if (maxlab >= (1 << 24)) return SEG_EINVAL;
     const int M = maxlab + 1;
     int slot_lo = 1, slot_hi = 1;
+    float maxabs = 0.0f;
     if (p->dtype == SEG_F32) {
         bool any = false;
         const uint32_t* bits = (const uint32_t*)I0;
@@ -670,7 +703,12 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
             if (!any) { slot_lo = slot_hi = slot; any = true; }
             slot_lo = std::min(slot_lo, slot);
             slot_hi = std::max(slot_hi, slot);
+            maxabs = std::max(maxabs, std::fabs(((const float*)I0)[i]));
         }
+    } else if (!img_dev) {
+        for (long long i = 0; i < npix; i++) maxabs = std::max(maxabs, (float)((const uint16_t*)I0)[i]);
+    } else {
+        maxabs = 65535.0f;
     }
     if (p->validate) {
         // every foreground label forms one connected component (union-find)
@@ -706,6 +744,7 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     CK(cudaGetDevice(&c->device));
     Plan P;
     make_geometry(p, M, slot_lo, slot_hi - slot_lo + 1, P);
+    P.h.maxabs = maxabs;
     c->h = P.h;
     auto fail = [&](int code) {
         seg_destroy(c);
@@ -746,6 +785,7 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     CKF(cudaMemsetAsync(c->h.st_S, 0, (size_t)M * (p->dtype == SEG_F32 ? c->h.nS : 1) * 8, stream));
     CKF(cudaMemsetAsync(c->h.st_Q, 0, (size_t)M * (p->dtype == SEG_F32 ? c->h.nQ : 1) * 8, stream));
     CKF(cudaMemcpyAsync((void*)c->h.klut, P.klut.data(), P.klut.size() * 4, cudaMemcpyHostToDevice, stream));
+    CKF(cudaMemcpyAsync((void*)c->h.klut64, P.klut64.data(), P.klut64.size() * 8, cudaMemcpyHostToDevice, stream));
     if (!P.ps_off.empty())
         CKF(cudaMemcpyAsync((void*)c->h.ps_off, P.ps_off.data(), P.ps_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
     CKF(cudaMemcpyAsync((void*)c->h.nb_off, P.nb_off.data(), P.nb_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));

@@ -45,6 +45,12 @@ struct Job {
     int ntx, nty, ntz, ntiles;
     int halo;                 // label/image halo staged by extraction
     int ps_staged;            // 2D piecewise smooth with the ball inside the staged halo
+    int ps_int;               // ball sums exact in int64 fixed point (value = q * 2^e_min)
+    int ps_exact64;           // ... and every FP64 partial sum over a ball is exact (order free)
+    int e_min;                // exponent of the fixed-point unit
+    float unit32;             // 2^e_min as a float
+    double unit64;            // 2^e_min as a double
+    float maxabs;             // largest |I| of the image
     float lambda32;
     double lambda64;
     double cutoff, E;         // E = 2 * cutoff (Eq. 5 length scale)
@@ -54,6 +60,7 @@ struct Job {
     int nb_n;                 // offsets with d2 <= r2max, row-major (for the FP64 recompute)
     const int4* nb_off;
     const float* klut;        // K(sqrt(d2)) rounded to float, d2 = 0..r2max
+    const double* klut64;     // K(sqrt(d2)) in FP64, Eq. 5 evaluated in the order written
     int M;                    // number of labels
     int osc_window;           // L2 fallback window (0 = never)
     int nbr_stride;           // neighbour-list slots per candidate: 8 (2D) | 26 (3D)
@@ -71,6 +78,10 @@ struct Job {
     float* p_eg;
     double* p_key;
     unsigned char* p_flags;
+    long long* p_qc;          // piecewise smooth with exact sums: sum of q(I) over the c part of the ball
+    long long* p_ql;          //   ... over the own-label part
+    int* p_nc;                //   pixel counts of the two parts
+    int* p_nl;
     int* pix_cand;            // at a pixel's first particle: its candidate slot or -1
     unsigned* flag_list;
     unsigned* cell_start;
@@ -114,9 +125,22 @@ struct BatchCtl {
     unsigned bar_gen;
     unsigned rounds_cnt[3];
     int err;
-    unsigned cand_total;
+    unsigned rounds_done;     // selection rounds of the last iteration
     unsigned pad[7];
 };
+
+// Image value as an exact fixed-point integer: value = q * 2^e_min. For float32 images
+// q = +-mantissa * 2^(slot - slot_lo); for uint16 images q is the value itself.
+__device__ __forceinline__ long long fixed_of_f32(float f, int slot_lo)
+{
+    unsigned bits = __float_as_uint(f);
+    int eb = (int)((bits >> 23) & 0xffu);
+    unsigned long long m = bits & 0x7fffffu;
+    if (eb == 0) eb = 1; else m |= 0x800000ull;
+    if (m == 0) return 0;
+    long long q = (long long)(m << (eb - slot_lo));
+    return (bits >> 31) ? -q : q;
+}
 
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(const volatile unsigned*)p; }
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
@@ -169,7 +193,10 @@ cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s);
 cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cudaStream_t s);
 cudaError_t configure_kernels(size_t smem_x2, size_t smem_x3, size_t smem_s2, size_t smem_s3);
 cudaError_t launch_select(const Group& g, BatchCtl* bc, cudaStream_t s);
-cudaError_t launch_commit(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s);
+cudaError_t launch_lists(const Job* jobs, int njobs, int sms, cudaStream_t s);
+cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s);
+cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
+cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s);
 cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s);
 cudaError_t topology_tables_init();

@@ -222,7 +222,7 @@ class Context:
         _check(lib().seg_poll(self.handle, C.byref(st)), "seg_poll")
         return st.as_dict()
 
-    STAGES = ("extract", "sobolev", "flag", "fixup", "select", "commit")
+    STAGES = ("extract", "sobolev", "flag", "fixup", "select", "lists", "rounds", "moves", "finish")
 
     def profile(self, on: bool = True):
         _check(lib().seg_profile(self.handle, int(bool(on))), "seg_profile")
