@@ -103,9 +103,8 @@ __device__ __forceinline__ unsigned label_mask(const Job& J, int x, int y, int z
 // must both be simple, so regions neither split, vanish, merge nor change holes.
 __device__ __forceinline__ bool admissible(const Job& J, unsigned gi, int l, int c)
 {
-    int x = (int)(gi % (unsigned)J.W);
-    int y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
-    int z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+    int x, y, z;
+    pix_coords(J, gi, x, y, z);
     int d = J.ndim == 3 ? 1 : 0;
     if (l != 0 && !simple_mask(label_mask(J, x, y, z, l), d)) return false;
     if (c != 0 && !simple_mask(label_mask(J, x, y, z, c), d)) return false;
@@ -133,9 +132,7 @@ __device__ __forceinline__ bool job_idle(const Counters* c)
 
 __device__ __forceinline__ void coords(const Job& J, unsigned gi, int& x, int& y, int& z)
 {
-    x = (int)(gi % (unsigned)J.W);
-    y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
-    z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+    pix_coords(J, gi, x, y, z);
 }
 
 // Certification: a particle that could be negative (g < eg) is queued for the FP64
@@ -448,6 +445,7 @@ constexpr int kLimbs = 24;
 __device__ double round_bins(const long long* bins, int nb, int e0)
 {
     long long lim[kLimbs];
+    const int nl = min(kLimbs, (nb + 63) / 32 + 3);   // bins span nb bits plus 64 of each value
     for (int i = 0; i < kLimbs; i++) lim[i] = 0;
     for (int k = 0; k < nb; k++) {
         long long b = bins[k];
@@ -461,7 +459,7 @@ __device__ double round_bins(const long long* bins, int nb, int e0)
         lim[j + 2] += hs >> 32;
     }
     long long carry = 0;
-    for (int i = 0; i < kLimbs; i++) {
+    for (int i = 0; i < nl; i++) {
         long long t = lim[i] + carry;
         lim[i] = t & 0xffffffffLL;
         carry = t >> 32;
@@ -469,14 +467,14 @@ __device__ double round_bins(const long long* bins, int nb, int e0)
     const bool neg = carry < 0;
     if (neg) {
         unsigned long long cy = 1;
-        for (int i = 0; i < kLimbs; i++) {
+        for (int i = 0; i < nl; i++) {
             unsigned long long t = ((~(unsigned long long)lim[i]) & 0xffffffffull) + cy;
             lim[i] = (long long)(t & 0xffffffffull);
             cy = t >> 32;
         }
     }
     int top = -1;
-    for (int i = kLimbs - 1; i >= 0; i--)
+    for (int i = nl - 1; i >= 0; i--)
         if (lim[i]) { top = i * 32 + 31 - __clz((unsigned)lim[i]); break; }
     if (top < 0) return 0.0;
     auto bit = [&](int b) -> unsigned long long { return ((unsigned long long)lim[b >> 5] >> (b & 31)) & 1ull; };
@@ -713,10 +711,12 @@ __device__ void commit_moves(const Job* jobs, int njobs, unsigned t0, unsigned s
 __device__ void commit_finish(const Job* jobs, int njobs, unsigned t0, unsigned stride, bool ok, unsigned rounds,
                               BatchCtl* bc)
 {
+    // labels go to block-leading threads first, so that their serial work spreads over SMs
+    const unsigned spread = (t0 % blockDim.x) * gridDim.x + t0 / blockDim.x;
     for (int j = 0; j < njobs; j++) {
         const Job& J = jobs[j];
         if (ok && !job_idle(J.ctr))
-            for (int m = (int)t0; m < J.M; m += (int)stride) finalize_label(J, m);
+            for (int m = (int)spread; m < J.M; m += (int)stride) finalize_label(J, m);
     }
     for (int j = (int)t0; j < njobs; j += (int)stride) {
         const Job& J = jobs[j];

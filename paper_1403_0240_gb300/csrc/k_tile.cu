@@ -183,9 +183,13 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     const size_t img_bytes = stage_img ? (size_t)nbox * (use_int ? 8 : 4) : 0;
     int* sL = (int*)(smem + img_bytes);
     unsigned* s_cstart = (unsigned*)(sL + nbox);
-    // labels (and, for the 2D piecewise-smooth model, the image) with halo; -1 outside
-    for (int i = tid; i < nbox; i += blockDim.x) {
-        int lx = i % bx, ly = (i / bx) % by, lz = i / (bx * by);
+    // labels (and, for the 2D piecewise-smooth model, the image) with halo; -1 outside;
+    // one warp per row of the box
+    const int nrows = by * bz;
+    for (int row = tid >> 5; row < nrows; row += blockDim.x >> 5)
+    for (int lx = tid & 31; lx < bx; lx += 32) {
+        const int ly = row % by, lz = row / by;
+        const int i = row * bx + lx;
         int x = b.x0 - h + lx, y = b.y0 - h + ly, z = b.z0 - hz + lz;
         int lab = -1;
         float val = 0.0f;
@@ -213,13 +217,33 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     const int chunk = (tile_q + blockDim.x - 1) / blockDim.x;
     const int q0 = min(tid * chunk, tile_q), q1 = min(q0 + chunk, tile_q);
 
-    auto pixel_of = [&](int q, int& x, int& y, int& z) -> bool {
+    // cell-major walk: (cell lx, ly, lz of the tile; pixel rx, ry, rz of the cell), the
+    // start decoded once per thread, then advanced like an odometer
+    struct Walk { int lx, ly, lz, rx, ry, rz; };
+    auto walk_start = [&](int q) -> Walk {
+        Walk w;
         int kc = q / cellvol, r = q - kc * cellvol;
-        int lx = kc % b.ccx, ly = (kc / b.ccx) % b.ccy, lz = kc / (b.ccx * b.ccy);
-        int rx = r % s, ry = (r / s) % s, rz = r / (s * s);
-        x = (b.cx0 + lx) * s + rx;
-        y = (b.cy0 + ly) * s + ry;
-        z = (b.cz0 + lz) * sz + rz;
+        w.lx = kc % b.ccx; w.ly = (kc / b.ccx) % b.ccy; w.lz = kc / (b.ccx * b.ccy);
+        w.rx = r % s; w.ry = (r / s) % s; w.rz = r / (s * s);
+        return w;
+    };
+    auto walk_next = [&](Walk& w) {
+        if (++w.rx < s) return;
+        w.rx = 0;
+        if (++w.ry < s) return;
+        w.ry = 0;
+        if (++w.rz < sz) return;
+        w.rz = 0;
+        if (++w.lx < b.ccx) return;
+        w.lx = 0;
+        if (++w.ly < b.ccy) return;
+        w.ly = 0;
+        ++w.lz;
+    };
+    auto walk_pixel = [&](const Walk& w, int& x, int& y, int& z) -> bool {
+        x = (b.cx0 + w.lx) * s + w.rx;
+        y = (b.cy0 + w.ly) * s + w.ry;
+        z = (b.cz0 + w.lz) * sz + w.rz;
         return x < J.W && y < J.H && z < J.D;
     };
     auto sidx = [&](int x, int y, int z) -> int {
@@ -265,10 +289,13 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     };
 
     unsigned cnt = 0;
-    for (int q = q0; q < q1; q++) {
-        int x, y, z, labs[6];
-        if (!pixel_of(q, x, y, z)) continue;
-        cnt += particles_at(x, y, z, labs);
+    {
+        Walk w = walk_start(q0);
+        for (int q = q0; q < q1; q++, walk_next(w)) {
+            int x, y, z, labs[6];
+            if (!walk_pixel(w, x, y, z)) continue;
+            cnt += particles_at(x, y, z, labs);
+        }
     }
     unsigned total;
     unsigned off = block_excl_scan(cnt, s_warp, total);
@@ -330,10 +357,11 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
 
     // emit particles (with their energy differences for the piecewise-constant model)
     unsigned o = base + off;
-    for (int q = q0; q < q1; q++) {
+    Walk wk = walk_start(q0);
+    for (int q = q0; q < q1; q++, walk_next(wk)) {
         int x, y, z, labs[6];
-        if (q % cellvol == 0) s_cstart[q / cellvol] = o - base;
-        if (!pixel_of(q, x, y, z)) continue;
+        if (wk.rx == 0 && wk.ry == 0 && wk.rz == 0) s_cstart[(wk.lz * b.ccy + wk.ly) * b.ccx + wk.lx] = o - base;
+        if (!walk_pixel(wk, x, y, z)) continue;
         int n = particles_at(x, y, z, labs);
         if (n == 0) continue;
         const long long gi = ((long long)z * J.H + y) * J.W + x;
@@ -372,9 +400,8 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     for (unsigned o2 = base + warp; o2 < base + total; o2 += nw) {
         const unsigned gi = J.p_idx[o2];
         const int own = J.p_l[o2], c = J.p_c[o2];
-        const int x = (int)(gi % (unsigned)J.W);
-        const int y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
-        const int z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+        int x, y, z;
+        pix_coords(J, gi, x, y, z);
         const int si = sidx(x, y, z);
         const float v = stage_img && !use_int ? sI[si] : image_at(J, gi);
         long long qv = 0;
@@ -542,9 +569,8 @@ __global__ void __launch_bounds__(kBlock) k_sobolev(Group g)
             long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
             unsigned p = J.cell_start[cid] + (i - s_eoff[e]);
             unsigned gi = J.p_idx[p];
-            int x = (int)(gi % (unsigned)J.W);
-            int y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
-            int z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+            int x, y, z;
+            pix_coords(J, gi, x, y, z);
             Staged sp;
             sp.pos = ((unsigned)(z - oz) << 20) | ((unsigned)(y - oy) << 10) | (unsigned)(x - ox);
             sp.l = J.p_l[p];
@@ -560,11 +586,11 @@ __global__ void __launch_bounds__(kBlock) k_sobolev(Group g)
     for (unsigned i = tid; i < pcount; i += blockDim.x) {
         const unsigned p = pstart + i;
         const unsigned gi = J.p_idx[p];
-        const int x = (int)(gi % (unsigned)J.W);
-        const int y = (int)((gi / (unsigned)J.W) % (unsigned)J.H);
-        const int z = (int)(gi / ((unsigned)J.W * (unsigned)J.H));
+        int x, y, z;
+        pix_coords(J, gi, x, y, z);
         const int lp = J.p_l[p];
-        const int pcx = x / s, pcy = y / s, pcz = NDIM == 3 ? z / s : z;
+        const int pcx = (int)fdiv((unsigned)x, J.fd_cell), pcy = (int)fdiv((unsigned)y, J.fd_cell);
+        const int pcz = NDIM == 3 ? (int)fdiv((unsigned)z, J.fd_cell) : z;
         float As = 0.f, Bs = 0.f, aA = 0.f, aB = 0.f, eAs = 0.f, eBs = 0.f;
         int nA = 0, nB = 0;
         for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); dz++) {
@@ -601,9 +627,8 @@ __global__ void __launch_bounds__(kBlock) k_sobolev(Group g)
                         const unsigned c0 = J.cell_start[cid], c1 = c0 + J.cell_count[cid];
                         for (unsigned j = c0; j < c1; j++) {
                             unsigned qi = J.p_idx[j];
-                            int qx = (int)(qi % (unsigned)J.W);
-                            int qy = (int)((qi / (unsigned)J.W) % (unsigned)J.H);
-                            int qz = (int)(qi / ((unsigned)J.W * (unsigned)J.H));
+                            int qx, qy, qz;
+                            pix_coords(J, qi, qx, qy, qz);
                             int d2 = (qx - x) * (qx - x) + (qy - y) * (qy - y) + (qz - z) * (qz - z);
                             if (d2 > J.r2max) continue;
                             float K = __ldg(J.klut + d2);

@@ -179,11 +179,14 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     h.H = (int)p->shape[1];
     h.W = (int)p->shape[2];
     h.npix = (long long)h.D * h.H * h.W;
+    h.fd_W = make_fastdiv((unsigned)h.W);
+    h.fd_HW = make_fastdiv((unsigned)((long long)h.W * h.H));
     h.dtype = p->dtype;
     h.model = p->model;
     h.conn = p->connectivity;
     h.cell = p->cell_edge ? p->cell_edge : std::max(1, (int)std::ceil(p->cutoff));
     const int s = h.cell;
+    h.fd_cell = make_fastdiv((unsigned)s);
     h.ncx = (h.W + s - 1) / s;
     h.ncy = (h.H + s - 1) / s;
     h.ncz = h.ndim == 3 ? (h.D + s - 1) / s : h.D;

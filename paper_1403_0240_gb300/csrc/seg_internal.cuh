@@ -13,6 +13,31 @@ constexpr unsigned kSpinLimit = 1u << 26;
 constexpr unsigned char kFlagFixup = 1, kFlagCand = 2, kFlagAcc = 4;
 constexpr int kUndecided = 0, kAccepted = 1, kRejected = 2;
 
+// Division by an invariant 32-bit divisor with one multiply-high (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", 1994, Fig. 4.1).
+struct FastDiv {
+    unsigned d, m;
+    int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    int l = 0;
+    while ((1ull << l) < d) l++;
+    FastDiv f;
+    f.d = d;
+    f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f)
+{
+    unsigned t = __umulhi(n, f.m);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 // Per-job counters and optimiser state, device memory, zeroed at seg_init.
 struct Counters {
     unsigned n_particles;   // particles of the current iteration
@@ -38,6 +63,7 @@ struct Counters {
 struct Job {
     int ndim, D, H, W;
     long long npix;
+    FastDiv fd_W, fd_HW, fd_cell;   // divide by W, by W*H, by the cell edge
     int dtype, model, conn;
     int cell;                 // cell-list edge (all axes in 3D; x and y in 2D)
     int ncx, ncy, ncz;        // cells per axis (ncz = D in 2D)
@@ -147,6 +173,21 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volati
 __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p)
 {
     return *(const volatile unsigned long long*)p;
+}
+
+// pixel coordinates of a linear index
+__device__ __forceinline__ void pix_coords(const Job& J, unsigned gi, int& x, int& y, int& z)
+{
+    unsigned zy = fdiv(gi, J.fd_W);
+    x = (int)(gi - zy * (unsigned)J.W);
+    if (J.ndim == 3) {
+        unsigned zz = fdiv(gi, J.fd_HW);
+        z = (int)zz;
+        y = (int)(zy - zz * (unsigned)J.H);
+    } else {
+        z = 0;
+        y = (int)zy;
+    }
 }
 
 // Which job / tile a tile ticket maps to.
