@@ -636,20 +636,32 @@ __device__ void commit_lists(const Job* jobs, int njobs, unsigned t0, unsigned s
             const double ks = J.c_key[s];
             int x, y, z;
             coords(J, gi, x, y, z);
-            int n = 0;
+            // three dependent levels (pixel map, candidate slot, key), each level's loads for
+            // all neighbours issued together
+            int slot[26];
+            int nn = 0;
             for (int dz = -rz; dz <= rz; dz++)
                 for (int dy = -1; dy <= 1; dy++)
                     for (int dx = -1; dx <= 1; dx++) {
                         if (!dz && !dy && !dx) continue;
                         int xx = x + dx, yy = y + dy, zz = z + dz;
-                        if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
-                        unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
-                        unsigned long long e = J.pmap[yi];
-                        if ((unsigned)(e >> 32) != tag) continue;
-                        int o = J.pix_cand[(unsigned)e];
-                        if (o < 0) continue;
-                        if (key_less(J.c_key[o], J.c_pix[o], ks, gi)) J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
+                        bool in = xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D;
+                        slot[nn++] = in ? (int)(((long long)zz * J.H + yy) * J.W + xx) : -1;
                     }
+            unsigned long long e[26];
+#pragma unroll
+            for (int i = 0; i < 26; i++)
+                e[i] = (i < nn && slot[i] >= 0) ? J.pmap[(unsigned)slot[i]] : 0ull;
+#pragma unroll
+            for (int i = 0; i < 26; i++)
+                slot[i] = (i < nn && slot[i] >= 0 && (unsigned)(e[i] >> 32) == tag) ? J.pix_cand[(unsigned)e[i]] : -1;
+            int n = 0;
+#pragma unroll
+            for (int i = 0; i < 26; i++) {
+                const int o = slot[i];
+                if (i < nn && o >= 0 && key_less(J.c_key[o], J.c_pix[o], ks, gi))
+                    J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
+            }
             J.c_nnbr[s] = n;
             J.c_state[s] = kUndecided;
         }

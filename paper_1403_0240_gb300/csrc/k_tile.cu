@@ -395,9 +395,17 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     }
     if (J.model != SEG_PS || !fits) return;
 
-    // piecewise-smooth energy: one particle per warp, the lanes share the ball offsets
-    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (unsigned o2 = base + warp; o2 < base + total; o2 += nw) {
+    // piecewise-smooth energy: one particle per thread over the dense range of this tile's
+    // particles, so every thread runs the same ball loop
+    int* s_delta = (int*)(s_cstart + ncell + 1);   // ball offsets as staged-box index deltas
+    if (stage_img) {
+        for (int u = tid; u < J.ps_n; u += blockDim.x) {
+            const int4 d = __ldg(J.ps_off + u);
+            s_delta[u] = d.y * bx + d.z;
+        }
+    }
+    __syncthreads();
+    for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
         const unsigned gi = J.p_idx[o2];
         const int own = J.p_l[o2], c = J.p_c[o2];
         int x, y, z;
@@ -409,60 +417,58 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         long long isc = 0, isl = 0;
         float fsc = 0.f, fsl = 0.f, ac = 0.f, al = 0.f;
         int cc = 0, cl = 0;
-        for (int u = lane; u < J.ps_n; u += 32) {
-            const int4 d = __ldg(J.ps_off + u);
-            int m;
-            float f = 0.f;
-            long long qy = 0;
-            if (stage_img) {
-                const int sj = si + d.y * bx + d.z;
-                m = sL[sj];
-                if (use_int) qy = sQ[sj]; else f = sI[sj];
-            } else {
-                const int yx = x + d.z, yy = y + d.y, yz = z + d.x;
-                if (yx < 0 || yx >= J.W || yy < 0 || yy >= J.H || yz < 0 || yz >= J.D) continue;
-                const long long gj2 = ((long long)yz * J.H + yy) * J.W + yx;
-                m = __ldg(J.L + gj2);
-                if (m != c && m != own) continue;
-                if (use_int) qy = image_q(J, gj2); else f = image_at(J, gj2);
+        if (stage_img && use_int) {
+            for (int u = 0; u < J.ps_n; u++) {
+                const int sj = si + s_delta[u];
+                const int m = sL[sj];
+                if (m == c) { isc += sQ[sj]; cc++; }
+                else if (m == own) { isl += sQ[sj]; cl++; }
             }
-            if (m == c) {
-                if (use_int) isc += qy - qv;
-                else { float dv = f - v; fsc += dv; ac += fabsf(dv); }
-                cc++;
-            } else if (m == own) {
-                if (use_int) isl += qy - qv;
-                else { float dv = f - v; fsl += dv; al += fabsf(dv); }
-                cl++;
+            isc -= (long long)cc * qv;
+            isl -= (long long)cl * qv;
+        } else {
+            for (int u = 0; u < J.ps_n; u++) {
+                int m;
+                float f = 0.f;
+                long long qy = 0;
+                if (stage_img) {
+                    const int sj = si + s_delta[u];
+                    m = sL[sj];
+                    f = sI[sj];
+                } else {
+                    const int4 d = __ldg(J.ps_off + u);
+                    const int yx = x + d.z, yy = y + d.y, yz = z + d.x;
+                    if (yx < 0 || yx >= J.W || yy < 0 || yy >= J.H || yz < 0 || yz >= J.D) continue;
+                    const long long gj2 = ((long long)yz * J.H + yy) * J.W + yx;
+                    m = __ldg(J.L + gj2);
+                    if (m != c && m != own) continue;
+                    if (use_int) qy = image_q(J, gj2); else f = image_at(J, gj2);
+                }
+                if (m == c) {
+                    if (use_int) isc += qy - qv;
+                    else { float dv = f - v; fsc += dv; ac += fabsf(dv); }
+                    cc++;
+                } else if (m == own) {
+                    if (use_int) isl += qy - qv;
+                    else { float dv = f - v; fsl += dv; al += fabsf(dv); }
+                    cl++;
+                }
             }
         }
-#pragma unroll
-        for (int w2 = 16; w2 > 0; w2 >>= 1) {
-            isc += __shfl_xor_sync(0xffffffffu, isc, w2);
-            isl += __shfl_xor_sync(0xffffffffu, isl, w2);
-            fsc += __shfl_xor_sync(0xffffffffu, fsc, w2);
-            fsl += __shfl_xor_sync(0xffffffffu, fsl, w2);
-            ac += __shfl_xor_sync(0xffffffffu, ac, w2);
-            al += __shfl_xor_sync(0xffffffffu, al, w2);
-            cc += __shfl_xor_sync(0xffffffffu, cc, w2);
-            cl += __shfl_xor_sync(0xffffffffu, cl, w2);
+        float dE, eE;
+        const int dP = delta_p(si, own, c);
+        if (use_int) {
+            energy_ps_finish_int(J, v, dP, isc, cc, isl, cl, dE, eE);
+            // keep the exact ball sums for the FP64 recompute
+            J.p_qc[o2] = isc + (long long)cc * qv;
+            J.p_ql[o2] = isl + (long long)cl * qv;
+            J.p_nc[o2] = cc;
+            J.p_nl[o2] = cl;
+        } else {
+            energy_ps_finish(J, v, dP, fsc, ac, cc, fsl, al, cl, dE, eE);
         }
-        if (lane == 0) {
-            float dE, eE;
-            const int dP = delta_p(si, own, c);
-            if (use_int) {
-                energy_ps_finish_int(J, v, dP, isc, cc, isl, cl, dE, eE);
-                // keep the exact ball sums for the FP64 recompute
-                J.p_qc[o2] = isc + (long long)cc * qv;
-                J.p_ql[o2] = isl + (long long)cl * qv;
-                J.p_nc[o2] = cc;
-                J.p_nl[o2] = cl;
-            } else {
-                energy_ps_finish(J, v, dP, fsc, ac, cc, fsl, al, cl, dE, eE);
-            }
-            J.p_dE[o2] = dE;
-            J.p_eE[o2] = eE;
-        }
+        J.p_dE[o2] = dE;
+        J.p_eE[o2] = eE;
     }
 }
 
@@ -474,7 +480,8 @@ size_t extract_smem_bytes(const Job& J)
     long long nbox = bx * by * bz;
     long long img = J.ps_staged ? (J.ps_int ? 8 : 4) : 0;
     long long ncell = (long long)J.tcx * J.tcy * J.tcz;
-    return (size_t)(nbox * (4 + img) + (ncell + 1) * 4);
+    long long deltas = J.ps_staged ? J.ps_n : 0;
+    return (size_t)(nbox * (4 + img) + (ncell + 1) * 4 + deltas * 4);
 }
 
 cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t st)
