@@ -185,6 +185,27 @@ int seg_batch_step_async(seg_batch* b, int32_t iters);
 int seg_batch_poll(seg_batch* b, seg_status* statuses, int32_t n_statuses);
 void seg_batch_destroy(seg_batch* b);
 
+/* Exact region statistics of a label image, allocating no device memory.
+ * The paper has no counterpart: this is for callers that cannot call cudaMalloc, such as
+ * code that manages device memory through a pool of its own (an unplanned cudaMalloc would
+ * bypass the pool's accounting and can fragment or exhaust it) or code that must not risk
+ * the implicit device synchronisation of cudaMalloc/cudaFree. It computes what seg_init
+ * computes and seg_stats returns: per label m < nlabels the pixel count n[m], and the sums
+ * S[m] of I and Q[m] of I^2 over the region, each exact and rounded once to FP64.
+ * image (dtype elements), labels (int32 in 0..nlabels-1), n (int64), S and Q (double) are
+ * caller-owned device buffers of npix and nlabels elements; host pointers give SEG_EINVAL.
+ * Limits: 1 <= nlabels <= 1024 and npix < 2^31, else SEG_EINVAL; a label outside
+ * 0..nlabels-1 gives SEG_EINVAL before anything is summed. Non-finite float values give
+ * meaningless sums but stay in bounds.
+ * The working accumulators live in one fixed device array of about 6.6 MB that every GPU
+ * loading libseg holds until the process exits. The first call on a device looks up that
+ * array's device address (once per device), so make it before any stream capture. All calls
+ * share the array, so calls that overlap on the GPU (other streams, other host threads)
+ * race and give wrong results. Work is ordered on cuda_stream (a cudaStream_t, NULL = the
+ * legacy default stream); the call returns after it has finished. */
+int seg_region_stats_noalloc(int32_t dtype, int64_t npix, const void* image, const int32_t* labels,
+                             int32_t nlabels, int64_t* n, double* S, double* Q, void* cuda_stream);
+
 /* Test hook: the device's simple-point test on n neighbourhood bitmasks (host arrays).
  * Bit k of masks[i] is neighbour k of the 3x3 (2D, 8 bits) or 3x3x3 (3D, 26 bits) window
  * in row-major order with the centre left out; out[i] = 1 if the centre is a simple

@@ -73,6 +73,7 @@ SIGNATURES = [
     ("seg_batch_step_async", C.c_int, [_V, C.c_int32]),
     ("seg_batch_poll", C.c_int, [_V, _V, C.c_int32]),
     ("seg_batch_destroy", None, [_V]),
+    ("seg_region_stats_noalloc", C.c_int, [C.c_int32, C.c_int64, _V, _V, C.c_int32, _V, _V, _V, _V]),
     ("seg_debug_simple", C.c_int, [C.c_int32, _V, C.c_int32, _V]),
     ("seg_strerror", C.c_char_p, [C.c_int]),
     ("seg_last_cuda_error", C.c_char_p, []),
@@ -340,3 +341,26 @@ def debug_simple(ndim: int, masks) -> np.ndarray:
     _check(lib().seg_debug_simple(int(ndim), m.ctypes.data_as(C.c_void_p), m.size,
                                   out.ctypes.data_as(C.c_void_p)), "seg_debug_simple")
     return out
+
+
+def region_stats_noalloc(image, labels, nlabels: int, n=None, S=None, Q=None, stream=None):
+    """Exact region statistics through the allocation-free entry point.
+
+    image and labels are CUDA tensors; n, S, Q (int64 / float64 CUDA tensors of nlabels
+    elements) are allocated here by torch when not given, since the library allocates
+    nothing. Returns (n, S, Q)."""
+    import torch
+    dev = image.device
+    if n is None:
+        n = torch.empty(nlabels, dtype=torch.int64, device=dev)
+    if S is None:
+        S = torch.empty(nlabels, dtype=torch.float64, device=dev)
+    if Q is None:
+        Q = torch.empty(nlabels, dtype=torch.float64, device=dev)
+    ip, _ = _ptr(image)
+    lp, _ = _ptr(labels)
+    _check(lib().seg_region_stats_noalloc(_dtype_code(image), int(image.numel()), ip, lp, int(nlabels),
+                                          C.c_void_p(n.data_ptr()), C.c_void_p(S.data_ptr()),
+                                          C.c_void_p(Q.data_ptr()), _stream_handle(stream)),
+           "seg_region_stats_noalloc")
+    return n, S, Q
