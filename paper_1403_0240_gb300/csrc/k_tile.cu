@@ -249,41 +249,59 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     auto sidx = [&](int x, int y, int z) -> int {
         return ((z - b.z0 + hz) * by + (y - b.y0 + h)) * bx + (x - b.x0 + h);
     };
-    // distinct neighbour labels different from the own label, ascending
-    auto particles_at = [&](int x, int y, int z, int* labs) -> int {
-        int si = sidx(x, y, z);
-        int own = sL[si];
-        int nb[6];
-        nb[0] = sL[si - 1];
-        nb[1] = sL[si + 1];
-        nb[2] = sL[si - bx];
-        nb[3] = sL[si + bx];
-        int nn = 4;
-        if (NDIM == 3) { nb[4] = sL[si - bx * by]; nb[5] = sL[si + bx * by]; nn = 6; }
+    // distinct neighbour labels different from the own label, ascending: the neighbours are
+    // sorted in registers by an odd-even transposition network, then repeats are dropped;
+    // labs[j] is INT_MAX for j >= n
+    constexpr int NN = NDIM == 3 ? 6 : 4;
+    auto particles_at = [&](int x, int y, int z, int (&labs)[NN]) -> int {
+        const int si = sidx(x, y, z);
+        const int own = sL[si];
+        int v[NN];
+        v[0] = sL[si - 1];
+        v[1] = sL[si + 1];
+        v[2] = sL[si - bx];
+        v[3] = sL[si + bx];
+        if (NDIM == 3) { v[NDIM == 3 ? 4 : 0] = sL[si - bx * by]; v[NDIM == 3 ? 5 : 1] = sL[si + bx * by]; }
+#pragma unroll
+        for (int j = 0; j < NN; j++)
+            if (v[j] < 0 || v[j] == own) v[j] = 0x7fffffff;
+#pragma unroll
+        for (int r = 0; r < NN; r++)
+#pragma unroll
+            for (int j = r & 1; j + 1 < NN; j += 2) {
+                const int a = min(v[j], v[j + 1]), b = max(v[j], v[j + 1]);
+                v[j] = a;
+                v[j + 1] = b;
+            }
         int n = 0;
-        for (int j = 0; j < nn; j++) {
-            int m = nb[j];
-            if (m < 0 || m == own) continue;
-            bool seen = false;
-            for (int u = 0; u < n; u++) seen |= (labs[u] == m);
-            if (seen) continue;
-            int p = n++;
-            while (p > 0 && labs[p - 1] > m) { labs[p] = labs[p - 1]; p--; }
-            labs[p] = m;
+#pragma unroll
+        for (int j = 0; j < NN; j++) {
+            const bool keep = v[j] != 0x7fffffff && (j == 0 || v[j] != v[j > 0 ? j - 1 : 0]);
+            labs[j] = 0x7fffffff;
+            if (keep) n++;
+        }
+        // compact the kept values to the front (static indices only)
+        int w = 0;
+#pragma unroll
+        for (int j = 0; j < NN; j++) {
+            const bool keep = v[j] != 0x7fffffff && (j == 0 || v[j] != v[j > 0 ? j - 1 : 0]);
+#pragma unroll
+            for (int t = 0; t < NN; t++)
+                if (keep && t == w) labs[t] = v[j];
+            if (keep) w++;
         }
         return n;
     };
     // change of the number of unlike neighbour pairs when the pixel goes from own to c
     auto delta_p = [&](int si, int own, int c) -> int {
-        int nb[6];
+        int nb[NN];
         nb[0] = sL[si - 1]; nb[1] = sL[si + 1]; nb[2] = sL[si - bx]; nb[3] = sL[si + bx];
-        int nn = 4;
-        if (NDIM == 3) { nb[4] = sL[si - bx * by]; nb[5] = sL[si + bx * by]; nn = 6; }
+        if (NDIM == 3) { nb[NDIM == 3 ? 4 : 0] = sL[si - bx * by]; nb[NDIM == 3 ? 5 : 1] = sL[si + bx * by]; }
         int dP = 0;
-        for (int u = 0; u < nn; u++) {
-            int m = nb[u];
-            if (m < 0) continue;
-            dP += (int)(m != c) - (int)(m != own);
+#pragma unroll
+        for (int u = 0; u < NN; u++) {
+            const int m = nb[u];
+            if (m >= 0) dP += (int)(m != c) - (int)(m != own);
         }
         return dP;
     };
@@ -292,7 +310,7 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     {
         Walk w = walk_start(q0);
         for (int q = q0; q < q1; q++, walk_next(w)) {
-            int x, y, z, labs[6];
+            int x, y, z, labs[NN];
             if (!walk_pixel(w, x, y, z)) continue;
             cnt += particles_at(x, y, z, labs);
         }
@@ -359,7 +377,7 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     unsigned o = base + off;
     Walk wk = walk_start(q0);
     for (int q = q0; q < q1; q++, walk_next(wk)) {
-        int x, y, z, labs[6];
+        int x, y, z, labs[NN];
         if (wk.rx == 0 && wk.ry == 0 && wk.rz == 0) s_cstart[(wk.lz * b.ccy + wk.ly) * b.ccx + wk.lx] = o - base;
         if (!walk_pixel(wk, x, y, z)) continue;
         int n = particles_at(x, y, z, labs);
@@ -369,19 +387,23 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         const int own = sL[si];
         if (fits) J.pmap[gi] = ((unsigned long long)tag << 32) | o;
         const float v = J.model == SEG_PC ? image_at(J, gi) : 0.0f;
-        for (int j = 0; j < n; j++, o++) {
+#pragma unroll
+        for (int j = 0; j < NN; j++) {
+            if (j >= n) break;
             const int c = labs[j];
-            if (!fits) continue;
-            J.p_idx[o] = (unsigned)gi;
-            J.p_l[o] = own;
-            J.p_c[o] = c;
-            J.p_flags[o] = 0;
-            if (J.model == SEG_PC) {
-                float dE, eE;
-                energy_pc(J, v, own, c, delta_p(si, own, c), dE, eE);
-                J.p_dE[o] = dE;
-                J.p_eE[o] = eE;
+            if (fits) {
+                J.p_idx[o] = (unsigned)gi;
+                J.p_l[o] = own;
+                J.p_c[o] = c;
+                J.p_flags[o] = 0;
+                if (J.model == SEG_PC) {
+                    float dE, eE;
+                    energy_pc(J, v, own, c, delta_p(si, own, c), dE, eE);
+                    J.p_dE[o] = dE;
+                    J.p_eE[o] = eE;
+                }
             }
+            o++;
         }
     }
     __syncthreads();
@@ -405,6 +427,63 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         }
     }
     __syncthreads();
+    if (stage_img && use_int) {
+        // a quad of lanes per particle, each lane every fourth ball offset; the loads of an
+        // offset do not depend on the label test, so consecutive offsets overlap
+        const int lane4 = tid & 3;
+        const unsigned nquad = blockDim.x >> 2;
+        for (unsigned lp0 = 0; lp0 < total; lp0 += nquad) {
+            const unsigned lp = lp0 + (tid >> 2);
+            const bool act = lp < total;
+            const unsigned o2 = base + (act ? lp : 0);
+            unsigned gi = 0;
+            int own = -2, c = -2, si = 0;
+            if (act) {
+                gi = J.p_idx[o2];
+                own = J.p_l[o2];
+                c = J.p_c[o2];
+                int x, y, z;
+                pix_coords(J, gi, x, y, z);
+                si = sidx(x, y, z);
+            }
+            long long isc = 0, isl = 0;
+            int cc = 0, cl = 0;
+            if (act) {
+#pragma unroll 4
+                for (int u = lane4; u < J.ps_n; u += 4) {
+                    const int sj = si + s_delta[u];
+                    const int m = sL[sj];
+                    const long long q = sQ[sj];
+                    const bool inc = m == c, inl = m == own;
+                    isc += inc ? q : 0;
+                    isl += inl ? q : 0;
+                    cc += inc;
+                    cl += inl;
+                }
+            }
+#pragma unroll
+            for (int w2 = 1; w2 < 4; w2 <<= 1) {
+                isc += __shfl_xor_sync(0xffffffffu, isc, w2);
+                isl += __shfl_xor_sync(0xffffffffu, isl, w2);
+                cc += __shfl_xor_sync(0xffffffffu, cc, w2);
+                cl += __shfl_xor_sync(0xffffffffu, cl, w2);
+            }
+            if (act && lane4 == 0) {
+                const long long qv = sQ[si];
+                const float v = (float)qv * J.unit32;
+                const long long sc = isc - (long long)cc * qv, sl = isl - (long long)cl * qv;
+                float dE, eE;
+                energy_ps_finish_int(J, v, delta_p(si, own, c), sc, cc, sl, cl, dE, eE);
+                J.p_qc[o2] = isc;
+                J.p_ql[o2] = isl;
+                J.p_nc[o2] = cc;
+                J.p_nl[o2] = cl;
+                J.p_dE[o2] = dE;
+                J.p_eE[o2] = eE;
+            }
+        }
+        return;
+    }
     for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
         const unsigned gi = J.p_idx[o2];
         const int own = J.p_l[o2], c = J.p_c[o2];
@@ -417,42 +496,31 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         long long isc = 0, isl = 0;
         float fsc = 0.f, fsl = 0.f, ac = 0.f, al = 0.f;
         int cc = 0, cl = 0;
-        if (stage_img && use_int) {
-            for (int u = 0; u < J.ps_n; u++) {
+        for (int u = 0; u < J.ps_n; u++) {
+            int m;
+            float f = 0.f;
+            long long qy = 0;
+            if (stage_img) {
                 const int sj = si + s_delta[u];
-                const int m = sL[sj];
-                if (m == c) { isc += sQ[sj]; cc++; }
-                else if (m == own) { isl += sQ[sj]; cl++; }
+                m = sL[sj];
+                f = sI[sj];
+            } else {
+                const int4 d = __ldg(J.ps_off + u);
+                const int yx = x + d.z, yy = y + d.y, yz = z + d.x;
+                if (yx < 0 || yx >= J.W || yy < 0 || yy >= J.H || yz < 0 || yz >= J.D) continue;
+                const long long gj2 = ((long long)yz * J.H + yy) * J.W + yx;
+                m = __ldg(J.L + gj2);
+                if (m != c && m != own) continue;
+                if (use_int) qy = image_q(J, gj2); else f = image_at(J, gj2);
             }
-            isc -= (long long)cc * qv;
-            isl -= (long long)cl * qv;
-        } else {
-            for (int u = 0; u < J.ps_n; u++) {
-                int m;
-                float f = 0.f;
-                long long qy = 0;
-                if (stage_img) {
-                    const int sj = si + s_delta[u];
-                    m = sL[sj];
-                    f = sI[sj];
-                } else {
-                    const int4 d = __ldg(J.ps_off + u);
-                    const int yx = x + d.z, yy = y + d.y, yz = z + d.x;
-                    if (yx < 0 || yx >= J.W || yy < 0 || yy >= J.H || yz < 0 || yz >= J.D) continue;
-                    const long long gj2 = ((long long)yz * J.H + yy) * J.W + yx;
-                    m = __ldg(J.L + gj2);
-                    if (m != c && m != own) continue;
-                    if (use_int) qy = image_q(J, gj2); else f = image_at(J, gj2);
-                }
-                if (m == c) {
-                    if (use_int) isc += qy - qv;
-                    else { float dv = f - v; fsc += dv; ac += fabsf(dv); }
-                    cc++;
-                } else if (m == own) {
-                    if (use_int) isl += qy - qv;
-                    else { float dv = f - v; fsl += dv; al += fabsf(dv); }
-                    cl++;
-                }
+            if (m == c) {
+                if (use_int) isc += qy - qv;
+                else { float dv = f - v; fsc += dv; ac += fabsf(dv); }
+                cc++;
+            } else if (m == own) {
+                if (use_int) isl += qy - qv;
+                else { float dv = f - v; fsl += dv; al += fabsf(dv); }
+                cl++;
             }
         }
         float dE, eE;
