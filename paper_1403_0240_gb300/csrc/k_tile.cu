@@ -152,12 +152,91 @@ __device__ __forceinline__ long long image_q(const Job& J, long long i)
 }
 
 // --------------------------------------------------------------------------
+// Tensor-memory-access copies of a tile box into shared memory, completed on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// wait for phase 0 of bar with a bounded number of polls; false when it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar)
+{
+    for (unsigned spins = 0; spins < kSpinLimit; spins++)
+        if (mbar_try_wait(bar, 0)) return true;
+    return false;
+}
+
+__host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
+
+// Box of a tile as staged in shared memory: origin (ox, oy, oz) and extent (bx, by, bz).
+struct StageBox {
+    int ox, oy, oz, bx, by, bz;
+};
+
+__device__ __forceinline__ StageBox stage_box(const Job& J, const TileBox& b, int h, int hz)
+{
+    StageBox r;
+    const int s = J.cell, sz = J.ndim == 3 ? J.cell : 1;
+    r.oy = b.y0 - h;
+    r.oz = b.z0 - hz;
+    if (J.use_tma) {
+        r.ox = (b.x0 - h) & ~7;
+        r.bx = J.tma_bx;
+        r.by = J.tcy * s + 2 * h;
+        r.bz = J.tcz * sz + 2 * hz;
+    } else {
+        r.ox = b.x0 - h;
+        r.bx = b.x1 - b.x0 + 2 * h;
+        r.by = b.y1 - b.y0 + 2 * h;
+        r.bz = b.z1 - b.z0 + 2 * hz;
+    }
+    return r;
+}
+
+// --------------------------------------------------------------------------
 // Extraction: one block per tile of cells, tiles taken in ticket order so that the
 // decoupled look-back only waits on tiles that have already started.
 template <int NDIM>
 __global__ void __launch_bounds__(kBlock) k_extract(Group g)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned s_ticket, s_base;
     __shared__ unsigned s_warp[32];
     const int tid = threadIdx.x;
@@ -173,24 +252,78 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
 
     const TileBox b = tile_box(J, k);
     const int h = J.halo, hz = NDIM == 3 ? J.halo : 0;
-    const int bx = b.x1 - b.x0 + 2 * h, by = b.y1 - b.y0 + 2 * h, bz = b.z1 - b.z0 + 2 * hz;
+    const StageBox sb = stage_box(J, b, h, hz);
+    const int bx = sb.bx, by = sb.by, bz = sb.bz;
     const int nbox = bx * by * bz;
-    // shared layout: [fixed-point image (int64) | float image] [labels] [cell starts]
+    // shared layout (128-byte aligned regions): [fixed-point image (int64)] [image as stored
+    // (float32 | uint16)] [labels] [cell starts] [ball deltas]
     const bool stage_img = J.ps_staged != 0;
     const bool use_int = J.ps_int != 0;
-    long long* sQ = (long long*)smem;
-    float* sI = (float*)smem;
-    const size_t img_bytes = stage_img ? (size_t)nbox * (use_int ? 8 : 4) : 0;
-    int* sL = (int*)(smem + img_bytes);
-    unsigned* s_cstart = (unsigned*)(sL + nbox);
-    // labels (and, for the 2D piecewise-smooth model, the image) with halo; -1 outside;
-    // one warp per row of the box
-    const int nrows = by * bz;
+    const size_t esz = J.dtype == SEG_F32 ? 4 : 2;
+    const bool q32 = J.ps_q32 != 0;
+    size_t off_b = 0;
+    long long* sQ = (long long*)(smem + off_b);
+    if (stage_img && use_int && !q32) off_b = align128(off_b + (size_t)nbox * 8);
+    unsigned char* sRaw = smem + off_b;
+    float* sI = (float*)sRaw;
+    int* sQ32 = (int*)sRaw;   // int32 fixed point, converted in place over the staged image
+    if (stage_img) off_b = align128(off_b + (size_t)nbox * (q32 ? 4 : esz));
+    int* sL = (int*)(smem + off_b);
+    off_b = align128(off_b + (size_t)nbox * 4);
+    unsigned* s_cstart = (unsigned*)(smem + off_b);
+    __shared__ __align__(8) unsigned long long s_bar;
+    const bool outside_box = sb.ox < 0 || sb.oy < 0 || sb.oz < 0 || sb.ox + bx > J.W || sb.oy + by > J.H ||
+                             sb.oz + bz > J.D;
+    if (J.use_tma) {
+        // one tensor copy per array, completed on one mbarrier; -1 for labels outside the image
+        if (tid == 0) {
+            mbar_init(&s_bar, 1);
+            const unsigned bytes = (unsigned)nbox * 4u + (stage_img ? (unsigned)(nbox * esz) : 0u);
+            mbar_expect_tx(&s_bar, bytes);
+            if (NDIM == 3) {
+                tma_load_3d(sL, J.tmap_L, sb.ox, sb.oy, sb.oz, &s_bar);
+            } else {
+                tma_load_2d(sL, J.tmap_L, sb.ox, sb.oy, &s_bar);
+                if (stage_img) tma_load_2d(sRaw, J.tmap_I, sb.ox, sb.oy, &s_bar);
+            }
+        }
+        __syncthreads();
+        const bool arrived = mbar_wait_bounded(&s_bar);
+        if (__syncthreads_or(!arrived)) {   // the whole block leaves together
+            if (tid == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
+            mbar_wait_bounded(&s_bar);       // a second bounded wait for the copy in flight
+            return;
+        }
+        if (outside_box || stage_img) {
+            for (int row = tid >> 5; row < by * bz; row += blockDim.x >> 5)
+            for (int lx = tid & 31; lx < bx; lx += 32) {
+                const int ly = row % by, lz = row / by;
+                const int i = row * bx + lx;
+                const int x = sb.ox + lx, y = sb.oy + ly, z = sb.oz + lz;
+                const bool in = x >= 0 && x < J.W && y >= 0 && y < J.H && z >= 0 && z < J.D;
+                if (!in) sL[i] = -1;
+                if (stage_img && use_int) {
+                    long long q = 0;
+                    if (in) q = J.dtype == SEG_F32 ? fixed_of_f32(sI[i], J.slot_lo)
+                                                   : (long long)((const unsigned short*)sRaw)[i];
+                    if (q32) {
+                        if (J.dtype == SEG_F32) sQ32[i] = (int)q;   // same element, same size: in place
+                    } else {
+                        sQ[i] = q;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // row-by-row staging when the rows cannot be copied by tensor copies: labels (and, for the
+    // 2D piecewise-smooth model, the image) with halo; -1 outside; one warp per row of the box
+    const int nrows = J.use_tma ? 0 : by * bz;
     for (int row = tid >> 5; row < nrows; row += blockDim.x >> 5)
     for (int lx = tid & 31; lx < bx; lx += 32) {
         const int ly = row % by, lz = row / by;
         const int i = row * bx + lx;
-        int x = b.x0 - h + lx, y = b.y0 - h + ly, z = b.z0 - hz + lz;
+        int x = sb.ox + lx, y = sb.oy + ly, z = sb.oz + lz;
         int lab = -1;
         float val = 0.0f;
         long long qval = 0;
@@ -204,7 +337,8 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         }
         sL[i] = lab;
         if (stage_img) {
-            if (use_int) sQ[i] = qval;
+            if (use_int && q32) sQ32[i] = (int)qval;
+            else if (use_int) sQ[i] = qval;
             else sI[i] = val;
         }
     }
@@ -247,7 +381,7 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         return x < J.W && y < J.H && z < J.D;
     };
     auto sidx = [&](int x, int y, int z) -> int {
-        return ((z - b.z0 + hz) * by + (y - b.y0 + h)) * bx + (x - b.x0 + h);
+        return ((z - sb.oz) * by + (y - sb.oy)) * bx + (x - sb.ox);
     };
     // distinct neighbour labels different from the own label, ascending: the neighbours are
     // sorted in registers by an odd-even transposition network, then repeats are dropped;
@@ -430,58 +564,61 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     if (stage_img && use_int) {
         // a quad of lanes per particle, each lane every fourth ball offset; the loads of an
         // offset do not depend on the label test, so consecutive offsets overlap
-        const int lane4 = tid & 3;
-        const unsigned nquad = blockDim.x >> 2;
-        for (unsigned lp0 = 0; lp0 < total; lp0 += nquad) {
-            const unsigned lp = lp0 + (tid >> 2);
-            const bool act = lp < total;
-            const unsigned o2 = base + (act ? lp : 0);
-            unsigned gi = 0;
-            int own = -2, c = -2, si = 0;
-            if (act) {
-                gi = J.p_idx[o2];
-                own = J.p_l[o2];
-                c = J.p_c[o2];
-                int x, y, z;
-                pix_coords(J, gi, x, y, z);
-                si = sidx(x, y, z);
-            }
-            long long isc = 0, isl = 0;
-            int cc = 0, cl = 0;
-            if (act) {
+        auto quad_pass = [&](const auto* Q) {
+            const int lane4 = tid & 3;
+            const unsigned nquad = blockDim.x >> 2;
+            for (unsigned lp0 = 0; lp0 < total; lp0 += nquad) {
+                const unsigned lp = lp0 + (tid >> 2);
+                const bool act = lp < total;
+                const unsigned o2 = base + (act ? lp : 0);
+                int own = -2, c = -2, si = 0;
+                if (act) {
+                    const unsigned gi = J.p_idx[o2];
+                    own = J.p_l[o2];
+                    c = J.p_c[o2];
+                    int x, y, z;
+                    pix_coords(J, gi, x, y, z);
+                    si = sidx(x, y, z);
+                }
+                long long isc = 0, isl = 0;
+                int cc = 0, cl = 0;
+                if (act) {
 #pragma unroll 4
-                for (int u = lane4; u < J.ps_n; u += 4) {
-                    const int sj = si + s_delta[u];
-                    const int m = sL[sj];
-                    const long long q = sQ[sj];
-                    const bool inc = m == c, inl = m == own;
-                    isc += inc ? q : 0;
-                    isl += inl ? q : 0;
-                    cc += inc;
-                    cl += inl;
+                    for (int u = lane4; u < J.ps_n; u += 4) {
+                        const int sj = si + s_delta[u];
+                        const int m = sL[sj];
+                        const long long q = Q[sj];
+                        const bool inc = m == c, inl = m == own;
+                        isc += inc ? q : 0;
+                        isl += inl ? q : 0;
+                        cc += inc;
+                        cl += inl;
+                    }
+                }
+#pragma unroll
+                for (int w2 = 1; w2 < 4; w2 <<= 1) {
+                    isc += __shfl_xor_sync(0xffffffffu, isc, w2);
+                    isl += __shfl_xor_sync(0xffffffffu, isl, w2);
+                    cc += __shfl_xor_sync(0xffffffffu, cc, w2);
+                    cl += __shfl_xor_sync(0xffffffffu, cl, w2);
+                }
+                if (act && lane4 == 0) {
+                    const long long qv = Q[si];
+                    const float v = (float)qv * J.unit32;
+                    const long long sc = isc - (long long)cc * qv, sl = isl - (long long)cl * qv;
+                    float dE, eE;
+                    energy_ps_finish_int(J, v, delta_p(si, own, c), sc, cc, sl, cl, dE, eE);
+                    J.p_qc[o2] = isc;
+                    J.p_ql[o2] = isl;
+                    J.p_nc[o2] = cc;
+                    J.p_nl[o2] = cl;
+                    J.p_dE[o2] = dE;
+                    J.p_eE[o2] = eE;
                 }
             }
-#pragma unroll
-            for (int w2 = 1; w2 < 4; w2 <<= 1) {
-                isc += __shfl_xor_sync(0xffffffffu, isc, w2);
-                isl += __shfl_xor_sync(0xffffffffu, isl, w2);
-                cc += __shfl_xor_sync(0xffffffffu, cc, w2);
-                cl += __shfl_xor_sync(0xffffffffu, cl, w2);
-            }
-            if (act && lane4 == 0) {
-                const long long qv = sQ[si];
-                const float v = (float)qv * J.unit32;
-                const long long sc = isc - (long long)cc * qv, sl = isl - (long long)cl * qv;
-                float dE, eE;
-                energy_ps_finish_int(J, v, delta_p(si, own, c), sc, cc, sl, cl, dE, eE);
-                J.p_qc[o2] = isc;
-                J.p_ql[o2] = isl;
-                J.p_nc[o2] = cc;
-                J.p_nl[o2] = cl;
-                J.p_dE[o2] = dE;
-                J.p_eE[o2] = eE;
-            }
-        }
+        };
+        if (q32) quad_pass(sQ32);
+        else quad_pass(sQ);
         return;
     }
     for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
@@ -544,12 +681,17 @@ size_t extract_smem_bytes(const Job& J)
 {
     int s = J.cell, sz = J.ndim == 3 ? J.cell : 1;
     int h = J.halo, hz = J.ndim == 3 ? J.halo : 0;
-    long long bx = (long long)J.tcx * s + 2 * h, by = (long long)J.tcy * s + 2 * h, bz = (long long)J.tcz * sz + 2 * hz;
+    long long bx = J.use_tma ? J.tma_bx : (long long)J.tcx * s + 2 * h;
+    long long by = (long long)J.tcy * s + 2 * h, bz = (long long)J.tcz * sz + 2 * hz;
     long long nbox = bx * by * bz;
-    long long img = J.ps_staged ? (J.ps_int ? 8 : 4) : 0;
+    size_t esz = J.dtype == SEG_F32 ? 4 : 2;
+    size_t b = 0;
+    if (J.ps_staged && J.ps_int && !J.ps_q32) b = align128(b + nbox * 8);
+    if (J.ps_staged) b = align128(b + nbox * (J.ps_q32 ? 4 : esz));
+    b = align128(b + nbox * 4);
     long long ncell = (long long)J.tcx * J.tcy * J.tcz;
     long long deltas = J.ps_staged ? J.ps_n : 0;
-    return (size_t)(nbox * (4 + img) + (ncell + 1) * 4 + deltas * 4);
+    return b + (size_t)((ncell + 1) * 4 + deltas * 4) + 128;
 }
 
 cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t st)

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "seg_internal.cuh"
 
 using namespace segk;
@@ -252,6 +254,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     const bool unit_ok = h.e_min >= -120 && h.e_min <= 100;
     h.ps_int = (h.model == SEG_PS && unit_ok && qbits + lg + 1 <= 62) ? 1 : 0;
     h.ps_exact64 = (h.ps_int && qbits + lg <= 53) ? 1 : 0;
+    h.ps_q32 = (h.ps_int && h.dtype == SEG_F32 && qbits <= 31) ? 1 : 0;
     h.unit32 = unit_ok ? std::ldexp(1.0f, h.e_min) : 0.0f;
     h.unit64 = std::ldexp(1.0, h.e_min);
 
@@ -283,6 +286,54 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     A.add((int4**)&h.ps_off, std::max<size_t>(1, P.ps_off.size()));
     A.add((int4**)&h.nb_off, P.nb_off.size());
     A.add(&h.ctr, 1);
+}
+
+// Tensor maps for the extraction tiles: labels (int32) and, when the piecewise-smooth image
+// is staged, the image. Box: tma_bx x (tile rows + 2 halo) [x (tile slices + 2 halo)], from
+// an x coordinate aligned down to 8 elements, so every copy starts on a 16-byte boundary.
+// Row pitches that are not multiples of 16 bytes keep the row-by-row load.
+void setup_tma(Job& h)
+{
+    h.use_tma = 0;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        cudaGetLastError();
+    }
+    if (!encode) return;
+    const int s = h.cell, sz = h.ndim == 3 ? h.cell : 1;
+    const int hz = h.ndim == 3 ? h.halo : 0;
+    const int bx = ((h.tcx * s + 2 * h.halo + 7 + 7) / 8) * 8;
+    const int by = h.tcy * s + 2 * h.halo;
+    const int bz = h.tcz * sz + 2 * hz;
+    if (bx > 256 || by > 256 || bz > 256) return;
+    const size_t esz = h.dtype == SEG_F32 ? 4 : 2;
+    if ((h.W * 4) % 16 != 0) return;
+    if (h.ps_staged && (h.W * esz) % 16 != 0) return;
+    const cuuint32_t rank = h.ndim == 3 ? 3 : 2;
+    cuuint64_t gdim[3] = {(cuuint64_t)h.W, (cuuint64_t)h.H, (cuuint64_t)h.D};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    cuuint32_t estr[3] = {1, 1, 1};
+    cuuint64_t gstr_l[2] = {(cuuint64_t)h.W * 4, (cuuint64_t)h.W * h.H * 4};
+    if (encode((CUtensorMap*)h.tmap_L, CU_TENSOR_MAP_DATA_TYPE_INT32, rank, (void*)h.L, gdim, gstr_l, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return;
+    if (h.ps_staged) {
+        cuuint64_t gstr_i[2] = {(cuuint64_t)h.W * esz, (cuuint64_t)h.W * h.H * esz};
+        if (encode((CUtensorMap*)h.tmap_I, h.dtype == SEG_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                   rank, (void*)h.I, gdim, gstr_i, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+    }
+    h.tma_bx = bx;
+    h.use_tma = 1;
 }
 
 size_t particle_bytes(long long pcap, int stride)
@@ -760,6 +811,7 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     for (auto& pr : P.fixed.parts) pr.first = (void**)((char*)&c->h + ((char*)pr.first - (char*)&P.h));
     P.fixed.assign(c->arena);
     c->d_ctr = c->h.ctr;
+    setup_tma(c->h);
     long long pcap = default_pcap(c->h.npix, c->h.ndim);
     size_t pb = particle_bytes(pcap, c->h.nbr_stride);
     e = cudaMalloc(&c->parena, pb);

@@ -59,8 +59,13 @@ struct Counters {
     seg_status last;        // status of the last executed iteration
 };
 
-// Everything a kernel needs about one segmentation job; lives in device memory.
-struct Job {
+// Everything a kernel needs about one segmentation job; lives in device memory (the
+// tensor maps inside need 64-byte alignment).
+struct alignas(64) Job {
+    unsigned char tmap_L[128];  // TMA tensor map of the label image (when use_tma)
+    unsigned char tmap_I[128];  // ... of the image (2D piecewise smooth with staged image)
+    int use_tma;              // tile boxes arrive by tensor copies
+    int tma_bx;               // box width in elements (multiple of 8) from an x aligned down to 8
     int ndim, D, H, W;
     long long npix;
     FastDiv fd_W, fd_HW, fd_cell;   // divide by W, by W*H, by the cell edge
@@ -73,6 +78,7 @@ struct Job {
     int ps_staged;            // 2D piecewise smooth with the ball inside the staged halo
     int ps_int;               // ball sums exact in int64 fixed point (value = q * 2^e_min)
     int ps_exact64;           // ... and every FP64 partial sum over a ball is exact (order free)
+    int ps_q32;               // fixed-point pixel values fit in int32 (staged as int32)
     int e_min;                // exponent of the fixed-point unit
     float unit32;             // 2^e_min as a float
     double unit64;            // 2^e_min as a double
