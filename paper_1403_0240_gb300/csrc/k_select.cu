@@ -250,6 +250,69 @@ __device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
     return __dadd_rn(data, __dmul_rn(J.lambda64, (double)dP));
 }
 
+// ---------------------------------------------------------------------------
+// Batches: per-job counts (flagged particles, candidates, labels) turned into one
+// flattened index space by a block-parallel exclusive prefix in shared memory; an index is
+// mapped back to its job by binary search. Idle jobs count zero.
+constexpr int kMaxBatchJobs = 2048;
+enum JobCount { kCountFlag = 0, kCountCand = 1, kCountLabels = 2 };
+
+__device__ __forceinline__ unsigned job_count(const Job& J, int kind)
+{
+    if (kind == kCountLabels) return (unsigned)J.M;
+    if (ld_volatile(&J.ctr->skip) || ld_volatile(&J.ctr->need)) return 0;
+    return ld_volatile(kind == kCountFlag ? &J.ctr->n_flag : &J.ctr->n_cand);
+}
+
+// s_pref[0..njobs]: exclusive prefix; returns the total (all threads)
+__device__ unsigned block_job_prefix(const Job* jobs, int njobs, int kind, unsigned* s_pref, unsigned* s_tmp)
+{
+    const int nt = blockDim.x;
+    const int chunk = (njobs + nt - 1) / nt;
+    const int j0 = min((int)threadIdx.x * chunk, njobs), j1 = min(j0 + chunk, njobs);
+    unsigned sum = 0;
+    for (int j = j0; j < j1; j++) sum += job_count(jobs[j], kind);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_tmp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned a = lane < (nt >> 5) ? s_tmp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, a, o);
+            if (lane >= o) a += y;
+        }
+        if (lane < (nt >> 5)) s_tmp[lane] = a;
+    }
+    __syncthreads();
+    unsigned run = (w > 0 ? s_tmp[w - 1] : 0u) + x - sum;
+    for (int j = j0; j < j1; j++) {
+        s_pref[j] = run;
+        run += job_count(jobs[j], kind);
+    }
+    const unsigned total = s_tmp[(nt >> 5) - 1];
+    if (threadIdx.x == 0) s_pref[njobs] = total;
+    __syncthreads();
+    return total;
+}
+
+// the job holding flattened index i (the last job whose prefix is <= i)
+__device__ __forceinline__ int job_of(const unsigned* s_pref, int njobs, unsigned i)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s_pref[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 constexpr int kFixWarps = 8;
 constexpr int kFixTerms = 32 * 6;
 
@@ -257,17 +320,20 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int n
 {
     __shared__ double s_t[kFixWarps][kFixTerms];
     __shared__ unsigned char s_a[kFixWarps][kFixTerms];
+    __shared__ unsigned s_pref[kMaxBatchJobs + 1];
+    __shared__ unsigned s_tmp[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned gw = blockIdx.x * kFixWarps + w, nw = gridDim.x * kFixWarps;
-    for (int j = 0; j < njobs; j++) {
-        const Job& J = jobs[j];
-        Counters* ctr = J.ctr;
-        if (job_idle(ctr)) continue;
-        const unsigned nf = ld_volatile(&ctr->n_flag);
-        const unsigned tag = ld_volatile(&ctr->iter_tag);
-        const unsigned np = ld_volatile(&ctr->n_particles);
-        const int mode = ld_volatile(&ctr->mode);
-        for (unsigned f = gw; f < nf; f += nw) {
+    const unsigned total = block_job_prefix(jobs, njobs, kCountFlag, s_pref, s_tmp);
+    {
+        for (unsigned fi = gw; fi < total; fi += nw) {
+            const int j = job_of(s_pref, njobs, fi);
+            const Job& J = jobs[j];
+            Counters* ctr = J.ctr;
+            const unsigned f = fi - s_pref[j];
+            const unsigned tag = ld_volatile(&ctr->iter_tag);
+            const unsigned np = ld_volatile(&ctr->n_particles);
+            const int mode = ld_volatile(&ctr->mode);
             const unsigned p = J.flag_list[f];
             const unsigned gi = J.p_idx[p];
             const int lp = J.p_l[p], cp = J.p_c[p];
@@ -622,200 +688,144 @@ constexpr unsigned kMaxRounds = 1u << 20;
 constexpr unsigned kSmallCandidates = 32768;   // at most this many: one block decides alone
 
 // A: neighbour lists of smaller-key candidates; states reset
-__device__ void commit_lists(const Job* jobs, int njobs, unsigned t0, unsigned stride)
+__device__ void commit_list_one(const Job& J, unsigned s)
 {
-    for (int j = 0; j < njobs; j++) {
-        const Job& J = jobs[j];
-        Counters* ctr = J.ctr;
-        if (job_idle(ctr)) continue;
-        const unsigned nc = ld_volatile(&ctr->n_cand);
-        const unsigned tag = ld_volatile(&ctr->iter_tag);
-        const int rz = J.ndim == 3 ? 1 : 0;
-        for (unsigned s = t0; s < nc; s += stride) {
-            const unsigned gi = J.c_pix[s];
-            const double ks = J.c_key[s];
-            int x, y, z;
-            coords(J, gi, x, y, z);
-            // three dependent levels (pixel map, candidate slot, key), each level's loads for
-            // all neighbours issued together
-            int slot[26];
-            int nn = 0;
-            for (int dz = -rz; dz <= rz; dz++)
-                for (int dy = -1; dy <= 1; dy++)
-                    for (int dx = -1; dx <= 1; dx++) {
-                        if (!dz && !dy && !dx) continue;
-                        int xx = x + dx, yy = y + dy, zz = z + dz;
-                        bool in = xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D;
-                        slot[nn++] = in ? (int)(((long long)zz * J.H + yy) * J.W + xx) : -1;
-                    }
-            unsigned long long e[26];
-#pragma unroll
-            for (int i = 0; i < 26; i++)
-                e[i] = (i < nn && slot[i] >= 0) ? J.pmap[(unsigned)slot[i]] : 0ull;
-#pragma unroll
-            for (int i = 0; i < 26; i++)
-                slot[i] = (i < nn && slot[i] >= 0 && (unsigned)(e[i] >> 32) == tag) ? J.pix_cand[(unsigned)e[i]] : -1;
-            int n = 0;
-#pragma unroll
-            for (int i = 0; i < 26; i++) {
-                const int o = slot[i];
-                if (i < nn && o >= 0 && key_less(J.c_key[o], J.c_pix[o], ks, gi))
-                    J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
+    const unsigned tag = ld_volatile(&J.ctr->iter_tag);
+    const int rz = J.ndim == 3 ? 1 : 0;
+    const unsigned gi = J.c_pix[s];
+    const double ks = J.c_key[s];
+    int x, y, z;
+    coords(J, gi, x, y, z);
+    // three dependent levels (pixel map, candidate slot, key), each level's loads for all
+    // neighbours issued together
+    int slot[26];
+    int nn = 0;
+    for (int dz = -rz; dz <= rz; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                if (!dz && !dy && !dx) continue;
+                int xx = x + dx, yy = y + dy, zz = z + dz;
+                bool in = xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D;
+                slot[nn++] = in ? (int)(((long long)zz * J.H + yy) * J.W + xx) : -1;
             }
-            J.c_nnbr[s] = n;
-            J.c_state[s] = kUndecided;
-        }
+    unsigned long long e[26];
+#pragma unroll
+    for (int i = 0; i < 26; i++)
+        e[i] = (i < nn && slot[i] >= 0) ? J.pmap[(unsigned)slot[i]] : 0ull;
+#pragma unroll
+    for (int i = 0; i < 26; i++)
+        slot[i] = (i < nn && slot[i] >= 0 && (unsigned)(e[i] >> 32) == tag) ? J.pix_cand[(unsigned)e[i]] : -1;
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < 26; i++) {
+        const int o = slot[i];
+        if (i < nn && o >= 0 && key_less(J.c_key[o], J.c_pix[o], ks, gi))
+            J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
     }
+    J.c_nnbr[s] = n;
+    J.c_state[s] = kUndecided;
 }
 
-// B: one pass of decisions; returns how many candidates stay undecided
-__device__ unsigned commit_round(const Job* jobs, int njobs, unsigned t0, unsigned stride)
+// B: one decision for candidate s of job J on state array st (offset b); returns the new
+// state (kUndecided when it has to wait)
+template <class State>
+__device__ __forceinline__ int commit_decide(const Job& J, unsigned s, State st, unsigned b)
 {
-    unsigned undecided = 0;
-    for (int j = 0; j < njobs; j++) {
-        const Job& J = jobs[j];
-        Counters* ctr = J.ctr;
-        if (job_idle(ctr)) continue;
-        const unsigned nc = ld_volatile(&ctr->n_cand);
-        for (unsigned s = t0; s < nc; s += stride) {
-            if (ld_volatile(J.c_state + s) != kUndecided) continue;
-            const int n = J.c_nnbr[s];
-            bool any_acc = false, all_rej = true;
-            for (int i = 0; i < n; i++) {
-                int st = ld_volatile(J.c_state + J.c_nbr[(long long)s * J.nbr_stride + i]);
-                if (st == kAccepted) { any_acc = true; break; }
-                if (st != kRejected) all_rej = false;
-            }
-            if (any_acc) *(volatile int*)(J.c_state + s) = kRejected;
-            else if (all_rej) *(volatile int*)(J.c_state + s) = kAccepted;
-            else undecided++;
-        }
+    const int n = J.c_nnbr[s];
+    const int* nb = J.c_nbr + (long long)s * J.nbr_stride;
+    bool all_rej = true;
+    for (int i = 0; i < n; i++) {
+        const int v = st[b + nb[i]];
+        if (v == kAccepted) return kRejected;
+        if (v != kRejected) all_rej = false;
     }
-    return undecided;
+    return all_rej ? kAccepted : kUndecided;
 }
 
-// C: accepted moves change labels and the exact region sums
-__device__ void commit_moves(const Job* jobs, int njobs, unsigned t0, unsigned stride, unsigned* s_red)
+// C: one accepted move changes the label and the exact region sums
+__device__ __forceinline__ void commit_move_one(const Job& J, unsigned s)
 {
-    for (int j = 0; j < njobs; j++) {
-        const Job& J = jobs[j];
-        Counters* ctr = J.ctr;
-        if (job_idle(ctr)) continue;
-        const unsigned nc = ld_volatile(&ctr->n_cand);
-        unsigned acc = 0;
-        for (unsigned s = t0; s < nc; s += stride) {
-            if (ld_volatile(J.c_state + s) != kAccepted) continue;
-            const int p = J.c_best[s];
-            const unsigned gi = J.c_pix[s];
-            const int l = J.p_l[p], c = J.p_c[p];
-            J.L[gi] = c;
-            J.p_flags[p] |= kFlagAcc;
-            stats_move(J, gi, l, -1);
-            stats_move(J, gi, c, +1);
-            acc++;
-        }
-        unsigned bs = block_sum(acc, s_red);
-        if (threadIdx.x == 0 && bs) atomicAdd(&ctr->n_accepted, bs);
-    }
+    const int p = J.c_best[s];
+    const unsigned gi = J.c_pix[s];
+    const int l = J.p_l[p], c = J.p_c[p];
+    J.L[gi] = c;
+    J.p_flags[p] |= kFlagAcc;
+    stats_move(J, gi, l, -1);
+    stats_move(J, gi, c, +1);
 }
 
-// D: region tables, oscillation fallback, status and counters for the next iteration
-__device__ void commit_finish(const Job* jobs, int njobs, unsigned t0, unsigned stride, bool ok, unsigned rounds,
-                              BatchCtl* bc)
+// D: per-job oscillation fallback, status and counters for the next iteration
+__device__ void commit_job_status(const Job& J, bool ok, unsigned rounds, int err)
 {
-    // labels go to block-leading threads first, so that their serial work spreads over SMs
-    const unsigned spread = (t0 % blockDim.x) * gridDim.x + t0 / blockDim.x;
-    for (int j = 0; j < njobs; j++) {
-        const Job& J = jobs[j];
-        if (ok && !job_idle(J.ctr))
-            for (int m = (int)spread; m < J.M; m += (int)stride) finalize_label(J, m);
+    Counters* c = J.ctr;
+    if (!ok) atomicExch(&c->error, err ? err : SEG_ETIMEOUT);
+    if (c->error || c->need) {
+        c->skip = 1;
+        c->last.error = c->error ? c->error : SEG_ENOMEM;
+        return;
     }
-    for (int j = (int)t0; j < njobs; j += (int)stride) {
-        const Job& J = jobs[j];
-        Counters* c = J.ctr;
-        if (!ok) atomicExch(&c->error, ld_volatile(&bc->err) ? ld_volatile(&bc->err) : SEG_ETIMEOUT);
-        if (c->error || c->need) {
-            c->skip = 1;
-            c->last.error = c->error ? c->error : SEG_ENOMEM;
-            continue;
-        }
-        if (c->converged) {
-            c->last.iteration = c->t;
-            c->last.n_particles = 0;
-            c->last.n_candidates = 0;
-            c->last.n_accepted = 0;
-            c->last.n_osc = 0;
-            c->last.n_fixup = 0;
-            c->last.mode_used = c->mode;
-            c->last.converged = 1;
-            c->last.mis_rounds = 0;
-            c->last.error = 0;
-            c->last.particles_total = c->cum_particles;
-            c->t++;
-            continue;
-        }
-        const long long A = c->n_accepted;
-        const int used = c->mode;
-        if (c->best_A < 0 || A < c->best_A) { c->best_A = A; c->t_best = c->t; }
-        if (c->mode == SEG_SOBOLEV && J.osc_window > 0 && c->t - c->t_best >= J.osc_window) c->mode = SEG_L2;
-        if (used == SEG_L2 && A == 0) c->converged = 1;
+    if (c->converged) {
         c->last.iteration = c->t;
-        c->last.n_particles = c->n_particles;
-        c->last.n_candidates = c->n_cand;
-        c->last.n_accepted = A;
-        c->last.n_osc = used == SEG_SOBOLEV ? c->n_osc : 0;
-        c->last.n_fixup = c->n_flag;
-        c->last.mode_used = used;
-        c->last.converged = c->converged;
-        c->last.mis_rounds = (int)rounds;
+        c->last.n_particles = 0;
+        c->last.n_candidates = 0;
+        c->last.n_accepted = 0;
+        c->last.n_osc = 0;
+        c->last.n_fixup = 0;
+        c->last.mode_used = c->mode;
+        c->last.converged = 1;
+        c->last.mis_rounds = 0;
         c->last.error = 0;
-        c->cum_particles += c->n_particles;
         c->last.particles_total = c->cum_particles;
         c->t++;
-        c->iter_tag++;
-        c->n_flag = 0;
-        c->n_cand = 0;
-        c->n_accepted = 0;
-        c->n_osc = 0;
-        c->skip = c->converged;
+        return;
     }
-    if (t0 == 0) {
-        bc->ticket[0] = 0;
-        bc->ticket[1] = 0;
-        bc->rounds_cnt[0] = 0;
-        bc->rounds_cnt[1] = 0;
-        bc->rounds_cnt[2] = 0;
-    }
+    const long long A = c->n_accepted;
+    const int used = c->mode;
+    if (c->best_A < 0 || A < c->best_A) { c->best_A = A; c->t_best = c->t; }
+    if (c->mode == SEG_SOBOLEV && J.osc_window > 0 && c->t - c->t_best >= J.osc_window) c->mode = SEG_L2;
+    if (used == SEG_L2 && A == 0) c->converged = 1;
+    c->last.iteration = c->t;
+    c->last.n_particles = c->n_particles;
+    c->last.n_candidates = c->n_cand;
+    c->last.n_accepted = A;
+    c->last.n_osc = used == SEG_SOBOLEV ? c->n_osc : 0;
+    c->last.n_fixup = c->n_flag;
+    c->last.mode_used = used;
+    c->last.converged = c->converged;
+    c->last.mis_rounds = (int)rounds;
+    c->last.error = 0;
+    c->cum_particles += c->n_particles;
+    c->last.particles_total = c->cum_particles;
+    c->t++;
+    c->iter_tag++;
+    c->n_flag = 0;
+    c->n_cand = 0;
+    c->n_accepted = 0;
+    c->n_osc = 0;
+    c->skip = c->converged;
 }
 
-// A, as its own grid: neighbour lists and state reset for every candidate of every job
+// A, as its own grid, over the flattened candidates of all jobs
 __global__ void __launch_bounds__(256) k_lists(const Job* jobs, int njobs)
 {
-    commit_lists(jobs, njobs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    __shared__ unsigned s_pref[kMaxBatchJobs + 1];
+    __shared__ unsigned s_tmp[32];
+    const unsigned total = block_job_prefix(jobs, njobs, kCountCand, s_pref, s_tmp);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int j = job_of(s_pref, njobs, i);
+        commit_list_one(jobs[j], i - s_pref[j]);
+    }
 }
 
 // B: the rounds. With few candidates one block runs them on shared-memory states with
 // block barriers; otherwise the whole co-resident grid runs them with bounded grid barriers.
-constexpr int kMaxSmallJobs = 1024;
-
 __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, BatchCtl* bc)
 {
     __shared__ unsigned s_red[32];
-    __shared__ unsigned s_total, s_flag;
-    __shared__ unsigned s_base[kMaxSmallJobs + 1];
+    __shared__ unsigned s_flag;
+    __shared__ unsigned s_pref[kMaxBatchJobs + 1];
     __shared__ unsigned char s_state[kSmallCandidates];
-    if (threadIdx.x == 0) {
-        unsigned t = 0;
-        const bool small_jobs = njobs <= kMaxSmallJobs;
-        for (int j = 0; j < njobs; j++) {
-            if (small_jobs) s_base[j] = t;
-            if (!job_idle(jobs[j].ctr)) t += ld_volatile(&jobs[j].ctr->n_cand);
-        }
-        if (small_jobs) s_base[njobs] = t;
-        s_total = small_jobs ? t : 0xffffffffu;
-    }
-    __syncthreads();
-    const unsigned total = s_total;
+    const unsigned total = block_job_prefix(jobs, njobs, kCountCand, s_pref, s_red);
     if (total <= kSmallCandidates) {
         if (blockIdx.x != 0) return;
         volatile unsigned char* st = s_state;
@@ -825,25 +835,13 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
         bool ok = true;
         for (unsigned r = 0;; r++) {
             unsigned und = 0;
-            for (int j = 0; j < njobs; j++) {
-                const Job& J = jobs[j];
-                if (job_idle(J.ctr)) continue;
-                const unsigned nc = ld_volatile(&J.ctr->n_cand);
-                const unsigned b = s_base[j];
-                for (unsigned s = threadIdx.x; s < nc; s += blockDim.x) {
-                    if (st[b + s] != kUndecided) continue;
-                    const int n = J.c_nnbr[s];
-                    const int* nb = J.c_nbr + (long long)s * J.nbr_stride;
-                    bool any_acc = false, all_rej = true;
-                    for (int i = 0; i < n; i++) {
-                        const unsigned char v = st[b + nb[i]];
-                        if (v == kAccepted) { any_acc = true; break; }
-                        if (v != kRejected) all_rej = false;
-                    }
-                    if (any_acc) st[b + s] = kRejected;
-                    else if (all_rej) st[b + s] = kAccepted;
-                    else und++;
-                }
+            for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
+                if (st[i] != kUndecided) continue;
+                const int j = job_of(s_pref, njobs, i);
+                const unsigned b = s_pref[j];
+                const int v = commit_decide(jobs[j], i - b, st, b);
+                if (v == kUndecided) und++;
+                else st[i] = (unsigned char)v;
             }
             const unsigned bs = block_sum(und, s_red);
             if (threadIdx.x == 0) s_flag = bs;
@@ -853,11 +851,9 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
             if (rem == 0) { rounds = r + 1; break; }
             if (r + 1 >= kMaxRounds) { ok = false; break; }
         }
-        for (int j = 0; j < njobs; j++) {
-            const Job& J = jobs[j];
-            if (job_idle(J.ctr)) continue;
-            const unsigned nc = ld_volatile(&J.ctr->n_cand);
-            for (unsigned s = threadIdx.x; s < nc; s += blockDim.x) J.c_state[s] = st[s_base[j] + s];
+        for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
+            const int j = job_of(s_pref, njobs, i);
+            jobs[j].c_state[i - s_pref[j]] = st[i];
         }
         if (threadIdx.x == 0) {
             bc->rounds_done = rounds;
@@ -870,7 +866,16 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
     unsigned rounds = 0;
     for (unsigned r = 0;; r++) {
-        unsigned undecided = commit_round(jobs, njobs, gtid, gstride);
+        unsigned undecided = 0;
+        for (unsigned i = gtid; i < total; i += gstride) {
+            const int j = job_of(s_pref, njobs, i);
+            const Job& J = jobs[j];
+            const unsigned s = i - s_pref[j];
+            if (ld_volatile(J.c_state + s) != kUndecided) continue;
+            const int v = commit_decide(J, s, (const volatile int*)J.c_state, 0u);
+            if (v == kUndecided) undecided++;
+            else *(volatile int*)(J.c_state + s) = v;
+        }
         unsigned bs = block_sum(undecided, s_red);
         if (threadIdx.x == 0) {
             if (bs) atomicAdd(&bc->rounds_cnt[r % 3], bs);
@@ -887,20 +892,56 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
     if (gtid == 0) bc->rounds_done = rounds;
 }
 
-// C, as its own grid
+// C, as its own grid: accepted moves; accepted counts aggregated per warp and job
 __global__ void __launch_bounds__(256) k_moves(const Job* jobs, int njobs, const BatchCtl* bc)
 {
-    __shared__ unsigned s_red[32];
+    __shared__ unsigned s_pref[kMaxBatchJobs + 1];
+    __shared__ unsigned s_tmp[32];
     if (ld_volatile(&bc->err)) return;
-    commit_moves(jobs, njobs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, s_red);
+    const unsigned total = block_job_prefix(jobs, njobs, kCountCand, s_pref, s_tmp);
+    const unsigned stride = gridDim.x * blockDim.x;
+    const unsigned rounds = (total + stride - 1) / stride;
+    for (unsigned r = 0; r < rounds; r++) {
+        const unsigned i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        int j = -1;
+        bool acc = false;
+        if (i < total) {
+            j = job_of(s_pref, njobs, i);
+            const unsigned s = i - s_pref[j];
+            if (jobs[j].c_state[s] == kAccepted) {
+                commit_move_one(jobs[j], s);
+                acc = true;
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, acc ? j : -1);
+        if (acc && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&jobs[j].ctr->n_accepted, (unsigned)__popc(peers));
+    }
 }
 
-// D, as its own grid
+// D, as its own grid: exact region tables of every label of every job, then per-job status
 __global__ void __launch_bounds__(256) k_finish(const Job* jobs, int njobs, BatchCtl* bc)
 {
-    const bool ok = ld_volatile(&bc->err) == 0;
-    commit_finish(jobs, njobs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, ok,
-                  ld_volatile(&bc->rounds_done), bc);
+    __shared__ unsigned s_pref[kMaxBatchJobs + 1];
+    __shared__ unsigned s_tmp[32];
+    const int err = ld_volatile(&bc->err);
+    const bool ok = err == 0;
+    const unsigned total = block_job_prefix(jobs, njobs, kCountLabels, s_pref, s_tmp);
+    // labels go to block-leading threads first, so that their serial work spreads over SMs
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned k = threadIdx.x * gridDim.x + blockIdx.x; k < total; k += stride) {
+        const int j = job_of(s_pref, njobs, k);
+        const Job& J = jobs[j];
+        if (ok && !job_idle(J.ctr)) finalize_label(J, (int)(k - s_pref[j]));
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < njobs; j += stride)
+        commit_job_status(jobs[j], ok, ld_volatile(&bc->rounds_done), err);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bc->ticket[0] = 0;
+        bc->ticket[1] = 0;
+        bc->rounds_cnt[0] = 0;
+        bc->rounds_cnt[1] = 0;
+        bc->rounds_cnt[2] = 0;
+    }
 }
 
 cudaError_t commit_occupancy(int block, int* blocks_per_sm)

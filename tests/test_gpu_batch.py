@@ -1,0 +1,108 @@
+"""Batched stepping: each job of a batch gives exactly what it gives alone.
+
+A batch runs one launch per stage for all of its jobs; jobs never share data, so labels,
+statistics and every particle array must be identical (bit for bit) to a solo run of the
+same job. Jobs joining and leaving between steps (continuous batching) must not change
+anything either."""
+import numpy as np
+import pytest
+
+from paper_1403_0240_gb300 import seg, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs():
+    a = synth.disks(128, 128, seed=0)
+    b = synth.disks(97, 151, seed=5)
+    b.labels0 = synth.square_grid_labels(97, 151, 32, 12)
+    c = synth.ellipses(160, 192, seed=7)
+    c.labels0 = synth.square_grid_labels(160, 192, 32, 16)
+    d = synth.ellipsoids(24, 28, 32, seed=8)
+    d.labels0 = synth.cube_grid_labels(24, 28, 32, 12, 6)
+    e = synth.disks(5, 3, seed=9)
+    e.labels0 = np.zeros((5, 3), np.int32)
+    e.labels0[1:3, 1] = 1
+    f = synth.ellipsoids(16, 16, 16, seed=10)
+    return [a, b, c, d, e, f]
+
+
+def _solo(w, iters):
+    ctx = seg.Context.from_workload(w)
+    for _ in range(iters):
+        ctx.step(1)
+    out = {"labels": ctx.labels().copy(), "stats": ctx.stats(), "particles": ctx.particles(),
+           "state": ctx.get_state()}
+    ctx.close()
+    return out
+
+
+def _same(got_ctx, ref):
+    assert np.array_equal(got_ctx.labels(), ref["labels"])
+    n, S, Q = got_ctx.stats()
+    assert np.array_equal(n, ref["stats"][0]) and np.array_equal(S, ref["stats"][1])
+    p = got_ctx.particles()
+    for k in ("idx", "l", "c", "dE", "eE", "g", "eg", "key", "flags"):
+        assert np.array_equal(p[k], ref["particles"][k]), k
+    assert got_ctx.get_state() == ref["state"]
+
+
+def test_batch_equals_solo():
+    jobs = _jobs()
+    iters = 12
+    refs = [_solo(w, iters) for w in jobs]
+    batch = seg.Batch()
+    ctxs = [seg.Context.from_workload(w) for w in jobs]
+    for c in ctxs:
+        batch.add(c)
+    for _ in range(iters):
+        sts = batch.step(1)
+        assert all(s["error"] == 0 for s in sts)
+    for c, r in zip(ctxs, refs):
+        _same(c, r)
+    batch.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_continuous_batching_equals_solo():
+    jobs = _jobs()
+    refs = {i: _solo(w, 10) for i, w in enumerate(jobs)}
+    batch = seg.Batch()
+    ctxs = {}
+    done = {}
+    pending = list(range(len(jobs)))
+    step = 0
+    # admit two jobs at a time, remove a job once it has run 10 iterations
+    while pending or ctxs:
+        while pending and len(ctxs) < 3:
+            i = pending.pop(0)
+            ctxs[i] = seg.Context.from_workload(jobs[i])
+            batch.add(ctxs[i])
+        batch.step(1)
+        step += 1
+        for i in list(ctxs):
+            if ctxs[i].get_state()["t"] == 10:
+                batch.remove(ctxs[i])
+                _same(ctxs[i], refs[i])
+                ctxs[i].close()
+                done[i] = True
+                del ctxs[i]
+    assert len(done) == len(jobs)
+    batch.close()
+
+
+def test_batch_rejects_double_membership():
+    w = _jobs()[0]
+    c = seg.Context.from_workload(w)
+    b1, b2 = seg.Batch(), seg.Batch()
+    b1.add(c)
+    with pytest.raises(seg.SegError):
+        b2.add(c)
+    with pytest.raises(seg.SegError):
+        c.step(1)                         # a context in a batch is stepped by its batch
+    b1.remove(c)
+    c.step(1)
+    b1.close()
+    b2.close()
+    c.close()
