@@ -25,6 +25,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -193,6 +195,164 @@ def oracle_sample(w, seconds: float = 12.0, max_iters: int = 400):
         its += 1
     dt = time.perf_counter() - t0
     return parts / dt, its, dt
+
+
+def run_batch(args, world, rank, local, pg):
+    """512 uneven 2D images (sides 64-512, 1-8 disks): one batch stepped together, against
+    the plain loop that steps each image alone."""
+    import torch
+
+    from paper_1403_0240_gb300 import seg, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    jobs = synth.batch_disks(args.images, seed0=1000 + 100000 * rank, iterations=args.steps)
+    dev_jobs = [(torch.from_numpy(w.image).to(dev), torch.from_numpy(w.labels0).to(dev), w) for w in jobs]
+
+    def contexts(n=None):
+        return [seg.Context(i, l, model=w.model, lam=w.lam, cutoff=w.cutoff, stream=stream)
+                for i, l, w in dev_jobs[:n]]
+
+    # warm-up: graph capture and code paths on a few jobs
+    warm = contexts(8)
+    b = seg.Batch(stream=stream)
+    for c in warm:
+        b.add(c)
+    b.step(args.warmup)
+    b.close()
+    for c in warm:
+        c.step(1)
+        c.close()
+
+    plain_ctx = contexts()
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    t0 = time.perf_counter()
+    plain_parts = 0
+    for c in plain_ctx:
+        plain_parts += c.step(args.steps)["particles_total"]
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter() - t0
+    for c in plain_ctx:
+        c.close()
+
+    batch_ctx = contexts()
+    b = seg.Batch(stream=stream)
+    for c in batch_ctx:
+        b.add(c)
+    b.poll()
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    t0 = time.perf_counter()
+    st = b.step(args.steps)
+    torch.cuda.synchronize(dev)
+    t_batch = time.perf_counter() - t0
+    barrier(pg)
+    batch_parts = sum(x["particles_total"] for x in st)
+    b.close()
+    for c in batch_ctx:
+        c.close()
+    t_b = allmax(pg, t_batch)
+    t_p = allmax(pg, t_plain)
+    parts_b = allsum(pg, float(batch_parts))
+    parts_p = allsum(pg, float(plain_parts))
+    if rank != 0:
+        return
+    value = parts_b / t_b
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t_b / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch512", "description": f"{args.images} 2D float32 disk images, sides U{{64..512}}, "
+                       "1-8 disks, piecewise constant, cutoff 3, one batch stepped together",
+                       "plain_value": parts_p / t_p, "batched_over_plain": (parts_b / t_b) / (parts_p / t_p),
+                       "plain_s": t_p, "batched_s": t_b, "images": args.images,
+                       "timing": "wall clock around whole-batch steps (synchronised)"}}
+    print(json.dumps(line), flush=True)
+
+
+def _pool_workload(kind, side, cache):
+    """Synthetic job images, one per (kind, side rounded to a bucket), reused by arrivals."""
+    from paper_1403_0240_gb300 import synth
+    if kind == "pc3d":
+        side = max(64, min(256, int(round(side / 32.0)) * 32))
+    else:
+        side = max(128, min(1024, int(round(side / 64.0)) * 64))
+    key = (kind, side)
+    if key not in cache:
+        cache[key] = synth.make_job(synth.Arrival(0.0, kind, side, seed=7 * side + len(kind)), iterations=100)
+    return cache[key]
+
+
+def run_served(args, world, rank, local, pg):
+    """Poisson arrivals (200 jobs/s): continuous batching against one job at a time."""
+    import torch
+
+    from paper_1403_0240_gb300 import seg, synth
+    from paper_1403_0240_gb300.serve import Request, SegBackend, Server, latency_summary
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    arrivals = synth.arrival_stream(args.jobs, seed=42 + rank)
+    cache = {}
+    reqs = []
+    for i, a in enumerate(arrivals):
+        w = _pool_workload(a.kind, a.side, cache)
+        reqs.append(Request(i, a.t, w.image, w.labels0, args.job_iters,
+                            dict(model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
+                                 ps_radius=w.ps_radius)))
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(0.6 * free)
+    # warm-up on a few jobs
+    be = SegBackend(stream=torch.cuda.current_stream(dev), init_stream=torch.cuda.Stream(dev), keep_labels=True)
+    srv = Server(be, budget, max_jobs=512, max_iters_per_step=args.iters_per_step)
+    for r in reqs[:4]:
+        srv.submit(Request(r.job_id, 0.0, r.image, r.labels0, 3, r.params))
+    while not srv.idle():
+        srv.step()
+    srv = Server(be, budget, max_jobs=512, max_iters_per_step=args.iters_per_step)
+    barrier(pg)
+    t0 = time.perf_counter()
+    res = srv.run([Request(r.job_id, r.arrival, r.image, r.labels0, r.iterations, r.params) for r in reqs], t0=t0)
+    t_served = max(x.completed for x in res) - t0
+    parts = sum(x.particles for x in res)
+    be.close()
+    served = latency_summary(res)
+    # one job at a time, first come first served, on the first arrivals of the same stream
+    # (virtual clock: start = max(arrival, previous completion); the service time is measured
+    # and covers set-up, the iterations and the label read-back, as a served job's does)
+    done_t, lat, parts_plain, busy = 0.0, [], 0, 0.0
+    n_plain = min(len(reqs), args.plain_jobs)
+    for r in reqs[:n_plain]:
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        c = seg.Context(r.image, r.labels0, **r.params)
+        st = c.step(r.iterations)
+        c.labels()
+        torch.cuda.synchronize(dev)
+        svc = time.perf_counter() - t1
+        c.close()
+        start = max(r.arrival, done_t)
+        done_t = start + svc
+        busy += svc
+        lat.append(done_t - r.arrival)
+        parts_plain += st["particles_total"]
+    if rank != 0:
+        return
+    lat = np.array(lat)
+    line = {"metric": METRIC, "value": parts / t_served, "unit": UNIT, "n_gpus": world, "steps": len(res),
+            "warmup": 4, "ms_per_step": 1000 * t_served / max(1, srv.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served", "jobs": len(res), "arrival_rate_per_s": 200,
+                       "description": "Poisson arrivals, 80% 2D (half piecewise constant disks, half piecewise "
+                                      "smooth ellipses, sides 128-1024), 20% 3D ellipsoids (sides 64-256); "
+                                      f"{args.job_iters} iterations per job; images pooled by size bucket",
+                       "budget_bytes": budget, "served_p50_s": served["p50_s"], "served_p99_s": served["p99_s"],
+                       "served_makespan_s": t_served,
+                       "plain_jobs": n_plain, "plain_value": parts_plain / busy,
+                       "plain_p50_s": float(np.percentile(lat, 50)), "plain_p99_s": float(np.percentile(lat, 99)),
+                       "served_over_plain": (parts / t_served) / (parts_plain / busy)}}
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args, world, rank):
@@ -376,7 +536,12 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ellipses1024", choices=sorted(workloads().keys()))
+    ap.add_argument("--workload", default="ellipses1024", choices=sorted(list(workloads().keys()) + ["batch512", "served"]))
+    ap.add_argument("--images", type=int, default=512, help="batch512: images in the batch")
+    ap.add_argument("--jobs", type=int, default=2000, help="served: jobs in the arrival stream")
+    ap.add_argument("--plain-jobs", type=int, default=400, help="served: jobs replayed one at a time")
+    ap.add_argument("--job-iters", type=int, default=100, help="served: iterations per job")
+    ap.add_argument("--iters-per-step", type=int, default=4, help="served: most iterations per batch step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -387,7 +552,12 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    run_ours(args, world, rank, local, pg)
+    if args.workload == "batch512":
+        run_batch(args, world, rank, local, pg)
+    elif args.workload == "served":
+        run_served(args, world, rank, local, pg)
+    else:
+        run_ours(args, world, rank, local, pg)
     if pg is not None:
         pg.destroy_process_group()
 

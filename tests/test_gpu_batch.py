@@ -106,3 +106,27 @@ def test_batch_rejects_double_membership():
     b1.close()
     b2.close()
     c.close()
+
+
+def test_served_jobs_equal_solo():
+    from paper_1403_0240_gb300.serve import Request, SegBackend, Server
+    jobs = _jobs()
+    iters = [8, 12, 10, 6, 9, 11]
+    refs = [_solo(w, n) for w, n in zip(jobs, iters)]
+
+    def params(w):
+        return dict(model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff, ps_radius=w.ps_radius)
+
+    backend = SegBackend()
+    reqs = [Request(i, 0.0, w.image, w.labels0, n, params(w)) for i, (w, n) in enumerate(zip(jobs, iters))]
+    biggest = max(backend.estimate(r) for r in reqs)
+    srv = Server(backend, budget_bytes=int(2.5 * biggest), max_jobs=4, max_iters_per_step=3)
+    for r in reqs:
+        srv.submit(r)
+    while not srv.idle():
+        srv.step()
+    assert len(srv.results) == len(jobs)
+    for r in srv.results:
+        assert r.iterations == iters[r.job_id]
+        assert np.array_equal(r.labels, refs[r.job_id]["labels"])
+    backend.close()
