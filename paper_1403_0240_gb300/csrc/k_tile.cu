@@ -1,6 +1,7 @@
 // Tile kernels of one iteration: particle extraction fused with the energy
 // difference, and the Sobolev interaction of Eq. 6 over a cell tile.
 #include <algorithm>
+#include <mutex>
 
 #include "seg_internal.cuh"
 
@@ -705,23 +706,76 @@ cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t s
 // --------------------------------------------------------------------------
 // Sobolev interaction, Eq. 6: g_p = (1/|Q_p|) sum_{Q_p} K(d) dE_q - (1/|Q'_p|) sum_{Q'_p} K(d) dE_q,
 // Q_p = {q : d < E/2, l_q = l_p}, Q'_p = {q : d < E/2, c_q = l_p}; empty sets give 0.
-// The particles of the tile's cells and of a one-cell ring around them are staged in
-// shared memory (or read from global memory when they do not fit).
-constexpr int kStageCap2 = 1024;   // staged particles per 2D tile (more: read from global memory)
-constexpr int kStageCap3 = 4096;   // per 3D tile
+//
+// One block per tile. The particles within rr = floor(sqrt(r2max)) pixels of the tile (found
+// through the tile's cells and one ring of cells around them) are staged in shared memory
+// sorted by pixel, with a per-pixel offset table over the staged pixel box. A particle then
+// visits only the rows of its interaction ball: for every (dy, dz) with dy^2 + dz^2 <= r2max
+// the particles of the pixel run [x - rx, x + rx], rx = floor(sqrt(r2max - dy^2 - dz^2)), are
+// one contiguous range of the staged arrays, and every one of them is a partner by
+// construction. Tiles whose box or particle count does not fit read global memory instead.
+constexpr int kRecCap = 2048;      // staged particles per tile
+constexpr int kBoxCap = 16384;     // staged pixel box per tile
+constexpr int kMaxRows = 256;      // (dy, dz) rows of the interaction ball
 
-struct Staged {
-    unsigned pos;   // packed (z << 20) | (y << 10) | x relative to the staged box origin
-    int l, c;
+struct Rec {
     float dE, eE;
+    int l, c;
 };
 
+__host__ __device__ __forceinline__ int isqrt_floor(int v)
+{
+    int r = 0;
+    while ((r + 1) * (r + 1) <= v) r++;
+    return r;
+}
+
+// staged pixel box of a full tile (an upper bound for every tile of the job)
+__host__ __device__ __forceinline__ long long sob_box_cap(const Job& J)
+{
+    const int rr = isqrt_floor(J.r2max);
+    long long bx = (long long)J.tcx * J.cell + 2 * rr, by = (long long)J.tcy * J.cell + 2 * rr;
+    long long bz = J.ndim == 3 ? (long long)J.tcz * J.cell + 2 * rr : 1;
+    return bx * by * bz;
+}
+
+__host__ __device__ __forceinline__ bool sob_can_stage(const Job& J)
+{
+    const int rr = isqrt_floor(J.r2max);
+    const int w = 2 * rr + 1;
+    return J.r2max < 256 && (J.ndim == 3 ? w * w : w) <= kMaxRows && sob_box_cap(J) <= kBoxCap;
+}
+
+__host__ __device__ __forceinline__ long long sob_ring_cells(const Job& J)
+{
+    return (long long)(J.tcx + 2) * (J.tcy + 2) * (J.ndim == 3 ? J.tcz + 2 : J.tcz);
+}
+
+// shared-memory layout: records | x | ring-cell prefix | pixel offsets (u16)
+struct SobLayout {
+    size_t x, eoff, off, total;
+};
+
+__host__ __device__ __forceinline__ SobLayout sob_layout(const Job& J)
+{
+    SobLayout L;
+    const bool st = sob_can_stage(J);
+    const size_t rec = st ? (size_t)kRecCap * sizeof(Rec) : 0;
+    L.x = rec;
+    L.eoff = L.x + (st ? (size_t)kRecCap * 2 : 0);
+    L.off = L.eoff + (size_t)((sob_ring_cells(J) + 4) & ~3LL) * 4;
+    L.total = L.off + (st ? (size_t)((sob_box_cap(J) + 8) & ~7LL) * 2 : 0);
+    return L;
+}
+
 template <int NDIM>
-__global__ void __launch_bounds__(kBlock) k_sobolev(Group g)
+__global__ void __launch_bounds__(kBlock, 3) k_sobolev(Group g)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned s_warp[32];
     __shared__ float s_klut[256];
+    __shared__ int s_rows[kMaxRows];
+    __shared__ int s_nrows;
     __shared__ unsigned s_osc;
     const int tid = threadIdx.x;
     const unsigned t = blockIdx.x;
@@ -741,126 +795,204 @@ __global__ void __launch_bounds__(kBlock) k_sobolev(Group g)
         return;
     }
     const TileBox b = tile_box(J, k);
-    const int s = J.cell, sz = NDIM == 3 ? J.cell : 1;
-    // staged cell box: tile cells plus one ring
+    const int r2max = J.r2max;
+    const int rr = isqrt_floor(r2max);
+    const bool can_stage = sob_can_stage(J);
+    const SobLayout lay = sob_layout(J);
+    Rec* s_rec = (Rec*)smem;
+    unsigned short* s_x = (unsigned short*)(smem + lay.x);
+    unsigned* s_eoff = (unsigned*)(smem + lay.eoff);
+    unsigned short* s_off = (unsigned short*)(smem + lay.off);
+
+    // ring cells: the tile's cells plus one ring
     const int ex0 = max(b.cx0 - 1, 0), ex1 = min(b.cx0 + b.ccx + 1, J.ncx);
     const int ey0 = max(b.cy0 - 1, 0), ey1 = min(b.cy0 + b.ccy + 1, J.ncy);
     const int ez0 = NDIM == 3 ? max(b.cz0 - 1, 0) : b.cz0;
     const int ez1 = NDIM == 3 ? min(b.cz0 + b.ccz + 1, J.ncz) : b.cz0 + b.ccz;
     const int enx = ex1 - ex0, eny = ey1 - ey0, enz = ez1 - ez0;
     const int ne = enx * eny * enz;
-    unsigned* s_eoff = (unsigned*)smem;                 // ne + 1 prefix of staged counts
-    Staged* sP = (Staged*)(s_eoff + ((ne + 2) & ~1));
-    const int ox = ex0 * s, oy = ey0 * s, oz = ez0 * sz;  // staged box origin (pixels)
+    // staged pixel box: the tile's pixels grown by rr, clipped to the image
+    const int bx0 = max(b.x0 - rr, 0), bx1 = min(b.x1 + rr, J.W);
+    const int by0 = max(b.y0 - rr, 0), by1 = min(b.y1 + rr, J.H);
+    const int bz0 = NDIM == 3 ? max(b.z0 - rr, 0) : b.z0;
+    const int bz1 = NDIM == 3 ? min(b.z1 + rr, J.D) : b.z1;
+    const int bnx = bx1 - bx0, bny = by1 - by0, bnz = bz1 - bz0;
+    const int nbox = bnx * bny * bnz;
 
-    // prefix over the staged cells (chunked per thread)
-    const int chunk = (ne + blockDim.x - 1) / blockDim.x;
-    const int e0 = min(tid * chunk, ne), e1 = min(e0 + chunk, ne);
-    unsigned cnt = 0;
-    for (int e = e0; e < e1; e++) {
-        int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
-        long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
-        cnt += J.cell_count[cid];
-    }
-    unsigned total;
-    unsigned off = block_excl_scan(cnt, s_warp, total);
-    for (int e = e0; e < e1; e++) {
-        int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
-        long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
-        s_eoff[e] = off;
-        off += J.cell_count[cid];
-    }
-    if (tid == 0) { s_eoff[ne] = total; s_osc = 0; }
-    for (int d2 = tid; d2 <= J.r2max && d2 < 256; d2 += blockDim.x) s_klut[d2] = __ldg(J.klut + d2);
-    __syncthreads();
-    const bool staged = total <= (unsigned)(NDIM == 3 ? kStageCap3 : kStageCap2) && J.r2max < 256;
-    if (staged) {
-        for (unsigned i = tid; i < total; i += blockDim.x) {
+    if (tid == 0) s_osc = 0;
+    for (int d2 = tid; d2 <= r2max && d2 < 256; d2 += blockDim.x) s_klut[d2] = __ldg(J.klut + d2);
+
+    bool staged = false;
+    if (can_stage) {
+        // rows of the ball, (dz, dy) ascending, compacted in thread order
+        const int w = 2 * rr + 1, nr = NDIM == 3 ? w * w : w;
+        bool ok = false;
+        int packed = 0;
+        if (tid < nr) {
+            const int dy = tid % w - rr, dz = NDIM == 3 ? tid / w - rr : 0;
+            const int dyz2 = dy * dy + dz * dz;
+            ok = dyz2 <= r2max;
+            const int rx = isqrt_floor(r2max - (ok ? dyz2 : 0));
+            packed = rx | ((dy + 128) << 8) | ((dz + 128) << 16) | (dyz2 << 24);
+        }
+        unsigned tot_rows;
+        const unsigned slot = block_excl_scan(ok ? 1u : 0u, s_warp, tot_rows);
+        if (ok) s_rows[slot] = packed;
+        if (tid == 0) s_nrows = (int)tot_rows;
+        // particle counts of the ring cells, and a zeroed pixel table
+        const int chunk = (ne + blockDim.x - 1) / blockDim.x;
+        const int e0 = min(tid * chunk, ne), e1 = min(e0 + chunk, ne);
+        unsigned cnt = 0;
+        for (int e = e0; e < e1; e++) {
+            int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
+            long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
+            cnt += J.cell_count[cid];
+        }
+        unsigned* s_off32 = (unsigned*)s_off;
+        for (int i = tid; i < (nbox + 2) / 2; i += blockDim.x) s_off32[i] = 0u;
+        __syncthreads();                               // s_warp reuse
+        unsigned ring_total;
+        unsigned off = block_excl_scan(cnt, s_warp, ring_total);
+        for (int e = e0; e < e1; e++) {
+            int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
+            long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
+            s_eoff[e] = off;
+            off += J.cell_count[cid];
+        }
+        if (tid == 0) s_eoff[ne] = ring_total;
+        __syncthreads();
+        // pass 1: particles per box pixel
+        for (unsigned i = tid; i < ring_total; i += blockDim.x) {
             int lo = 0, hi = ne - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
                 if (s_eoff[mid] <= i) lo = mid; else hi = mid - 1;
             }
-            int e = lo;
-            int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
-            long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
-            unsigned p = J.cell_start[cid] + (i - s_eoff[e]);
-            unsigned gi = J.p_idx[p];
+            const int e = lo;
+            const int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
+            const long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
+            const unsigned p = J.cell_start[cid] + (i - s_eoff[e]);
             int x, y, z;
-            pix_coords(J, gi, x, y, z);
-            Staged sp;
-            sp.pos = ((unsigned)(z - oz) << 20) | ((unsigned)(y - oy) << 10) | (unsigned)(x - ox);
-            sp.l = J.p_l[p];
-            sp.c = J.p_c[p];
-            sp.dE = J.p_dE[p];
-            sp.eE = J.p_eE[p];
-            sP[i] = sp;
+            pix_coords(J, J.p_idx[p], x, y, z);
+            x -= bx0; y -= by0; z -= bz0;
+            if ((unsigned)x < (unsigned)bnx && (unsigned)y < (unsigned)bny && (unsigned)z < (unsigned)bnz) {
+                const int bp = (z * bny + y) * bnx + x;
+                atomicAdd(&s_off32[bp >> 1], 1u << (16 * (bp & 1)));
+            }
         }
+        __syncthreads();
+        // exclusive prefix over the box pixels (chunk per thread)
+        const int pc = (nbox + blockDim.x - 1) / blockDim.x;
+        const int q0 = min(tid * pc, nbox), q1 = min(q0 + pc, nbox);
+        unsigned sum = 0;
+        for (int q = q0; q < q1; q++) sum += s_off[q];
+        __syncthreads();                               // s_warp reuse
+        unsigned staged_total;
+        unsigned run = block_excl_scan(sum, s_warp, staged_total);
+        for (int q = q0; q < q1; q++) {
+            const unsigned c = s_off[q];
+            s_off[q] = (unsigned short)run;
+            run += c;
+        }
+        if (tid == 0) s_off[nbox] = (unsigned short)min(staged_total, 65535u);
+        staged = staged_total <= (unsigned)kRecCap;
+        __syncthreads();
+        if (staged) {
+            // pass 2: scatter; particles of one pixel are adjacent in their cell, so the rank of
+            // a particle among its pixel's particles is the run of equal indices before it
+            for (unsigned i = tid; i < ring_total; i += blockDim.x) {
+                int lo = 0, hi = ne - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (s_eoff[mid] <= i) lo = mid; else hi = mid - 1;
+                }
+                const int e = lo;
+                const int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
+                const long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
+                const unsigned within = i - s_eoff[e];
+                const unsigned p = J.cell_start[cid] + within;
+                const unsigned gi = J.p_idx[p];
+                int x, y, z;
+                pix_coords(J, gi, x, y, z);
+                x -= bx0; y -= by0; z -= bz0;
+                if ((unsigned)x < (unsigned)bnx && (unsigned)y < (unsigned)bny && (unsigned)z < (unsigned)bnz) {
+                    unsigned rank = 0;
+                    while (rank < within && J.p_idx[p - rank - 1] == gi) rank++;
+                    const int bp = (z * bny + y) * bnx + x;
+                    const unsigned pos = s_off[bp] + rank;
+                    Rec r;
+                    r.dE = J.p_dE[p];
+                    r.eE = J.p_eE[p];
+                    r.l = J.p_l[p];
+                    r.c = J.p_c[p];
+                    s_rec[pos] = r;
+                    s_x[pos] = (unsigned short)x;
+                }
+            }
+        }
+        __syncthreads();
+    } else {
+        __syncthreads();
     }
-    __syncthreads();
 
     unsigned osc = 0;
+    const int nrows = staged ? s_nrows : 0;
     for (unsigned i = tid; i < pcount; i += blockDim.x) {
         const unsigned p = pstart + i;
         const unsigned gi = J.p_idx[p];
         int x, y, z;
         pix_coords(J, gi, x, y, z);
         const int lp = J.p_l[p];
-        const int pcx = (int)fdiv((unsigned)x, J.fd_cell), pcy = (int)fdiv((unsigned)y, J.fd_cell);
-        const int pcz = NDIM == 3 ? (int)fdiv((unsigned)z, J.fd_cell) : z;
         float As = 0.f, Bs = 0.f, aA = 0.f, aB = 0.f, eAs = 0.f, eBs = 0.f;
         int nA = 0, nB = 0;
-        for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); dz++) {
-            int cz = pcz + dz;
-            if (cz < ez0 || cz >= ez1) continue;
-            for (int dy = -1; dy <= 1; dy++) {
-                int cy = pcy + dy;
-                if (cy < ey0 || cy >= ey1) continue;
-                for (int dx = -1; dx <= 1; dx++) {
-                    int cx = pcx + dx;
-                    if (cx < ex0 || cx >= ex1) continue;
-                    int e = ((cz - ez0) * eny + (cy - ey0)) * enx + (cx - ex0);
-                    if (staged) {
-                        const unsigned e_lo = s_eoff[e], e_hi = s_eoff[e + 1];
-                        const unsigned mypos_x = (unsigned)(x - ox), mypos_y = (unsigned)(y - oy), mypos_z = (unsigned)(z - oz);
-                        for (unsigned j = e_lo; j < e_hi; j++) {
-                            const Staged q = sP[j];
-                            int ddx = (int)(q.pos & 1023u) - (int)mypos_x;
-                            int ddy = (int)((q.pos >> 10) & 1023u) - (int)mypos_y;
-                            int ddz = (int)(q.pos >> 20) - (int)mypos_z;
-                            int d2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            if (d2 > J.r2max) continue;
-                            float K = s_klut[d2];
-                            if (q.l == lp) {
-                                float w = K * q.dE;
-                                As += w; aA += fabsf(w); eAs += K * q.eE; nA++;
-                            } else if (q.c == lp) {
-                                float w = K * q.dE;
-                                Bs += w; aB += fabsf(w); eBs += K * q.eE; nB++;
-                            }
-                        }
-                    } else {
-                        long long cid = ((long long)cz * J.ncy + cy) * J.ncx + cx;
+        if (staged) {
+            const int lx = x - bx0, ly = y - by0, lz = z - bz0;
+            for (int r = 0; r < nrows; r++) {
+                const int row = s_rows[r];
+                const int yy = ly + ((row >> 8) & 255) - 128;
+                const int zz = lz + ((row >> 16) & 255) - 128;
+                if ((unsigned)yy >= (unsigned)bny || (unsigned)zz >= (unsigned)bnz) continue;
+                const int rx = row & 255, dyz2 = (int)((unsigned)row >> 24);
+                const int xl = max(lx - rx, 0), xh = min(lx + rx, bnx - 1);
+                const int base = (zz * bny + yy) * bnx;
+                const unsigned j1 = s_off[base + xh + 1];
+                for (unsigned j = s_off[base + xl]; j < j1; j++) {
+                    const int dx = (int)s_x[j] - lx;
+                    const float K = s_klut[dyz2 + dx * dx];
+                    const Rec q = s_rec[j];
+                    if (q.l == lp) {
+                        const float w = K * q.dE;
+                        As += w; aA += fabsf(w); eAs += K * q.eE; nA++;
+                    } else if (q.c == lp) {
+                        const float w = K * q.dE;
+                        Bs += w; aB += fabsf(w); eBs += K * q.eE; nB++;
+                    }
+                }
+            }
+        } else {
+            const int pcx = (int)fdiv((unsigned)x, J.fd_cell), pcy = (int)fdiv((unsigned)y, J.fd_cell);
+            const int pcz = NDIM == 3 ? (int)fdiv((unsigned)z, J.fd_cell) : z;
+            for (int cz = max(pcz - (NDIM == 3), 0); cz <= min(pcz + (NDIM == 3), J.ncz - 1); cz++)
+                for (int cy = max(pcy - 1, 0); cy <= min(pcy + 1, J.ncy - 1); cy++)
+                    for (int cx = max(pcx - 1, 0); cx <= min(pcx + 1, J.ncx - 1); cx++) {
+                        const long long cid = ((long long)cz * J.ncy + cy) * J.ncx + cx;
                         const unsigned c0 = J.cell_start[cid], c1 = c0 + J.cell_count[cid];
                         for (unsigned j = c0; j < c1; j++) {
-                            unsigned qi = J.p_idx[j];
                             int qx, qy, qz;
-                            pix_coords(J, qi, qx, qy, qz);
-                            int d2 = (qx - x) * (qx - x) + (qy - y) * (qy - y) + (qz - z) * (qz - z);
-                            if (d2 > J.r2max) continue;
-                            float K = __ldg(J.klut + d2);
-                            int ql = J.p_l[j], qc = J.p_c[j];
+                            pix_coords(J, J.p_idx[j], qx, qy, qz);
+                            const int d2 = (qx - x) * (qx - x) + (qy - y) * (qy - y) + (qz - z) * (qz - z);
+                            if (d2 > r2max) continue;
+                            const float K = __ldg(J.klut + d2);
+                            const int ql = J.p_l[j], qc = J.p_c[j];
                             if (ql == lp) {
-                                float w = K * J.p_dE[j];
+                                const float w = K * J.p_dE[j];
                                 As += w; aA += fabsf(w); eAs += K * J.p_eE[j]; nA++;
                             } else if (qc == lp) {
-                                float w = K * J.p_dE[j];
+                                const float w = K * J.p_dE[j];
                                 Bs += w; aB += fabsf(w); eBs += K * J.p_eE[j]; nB++;
                             }
                         }
                     }
-                }
-            }
         }
         float A = nA ? As / (float)nA : 0.f;
         float B = nB ? Bs / (float)nB : 0.f;
@@ -880,8 +1012,7 @@ __global__ void __launch_bounds__(kBlock) k_sobolev(Group g)
 
 size_t sobolev_smem_bytes(const Job& J)
 {
-    long long ne = (long long)(J.tcx + 2) * (J.tcy + 2) * (J.ndim == 3 ? J.tcz + 2 : J.tcz);
-    return (size_t)(((ne + 2) & ~1LL) * 4 + (long long)(J.ndim == 3 ? kStageCap3 : kStageCap2) * sizeof(Staged));
+    return sob_layout(J).total;
 }
 
 cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t st)
@@ -892,14 +1023,29 @@ cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t s
     return cudaGetLastError();
 }
 
-// Dynamic shared memory limits, set outside any stream capture.
+// Dynamic shared memory limits, set outside any stream capture. The limits only grow (per
+// device), so that a context built later with smaller tiles does not lower the limit below
+// what the graphs of earlier contexts launch with.
 cudaError_t configure_kernels(size_t x2, size_t x3, size_t s2, size_t s3)
 {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_extract<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(x2, 1))) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_extract<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(x3, 1))) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_sobolev<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s2, 1))) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sobolev<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(s3, 1));
+    static std::mutex mu;
+    static size_t cur[64][4];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    const size_t want[4] = {std::max<size_t>(x2, 1), std::max<size_t>(x3, 1), std::max<size_t>(s2, 1),
+                            std::max<size_t>(s3, 1)};
+    const void* fn[4] = {(const void*)k_extract<2>, (const void*)k_extract<3>, (const void*)k_sobolev<2>,
+                         (const void*)k_sobolev<3>};
+    for (int i = 0; i < 4; i++) {
+        if (want[i] <= cur[dev][i]) continue;
+        if ((e = cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want[i])) != cudaSuccess)
+            return e;
+        cur[dev][i] = want[i];
+    }
+    return cudaSuccess;
 }
 
 }  // namespace segk
