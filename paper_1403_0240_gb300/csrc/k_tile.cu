@@ -708,15 +708,17 @@ cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t s
 // Q_p = {q : d < E/2, l_q = l_p}, Q'_p = {q : d < E/2, c_q = l_p}; empty sets give 0.
 //
 // One block per tile. The particles within rr = floor(sqrt(r2max)) pixels of the tile (found
-// through the tile's cells and one ring of cells around them) are staged in shared memory
-// sorted by pixel, with a per-pixel offset table over the staged pixel box. A particle then
-// visits only the rows of its interaction ball: for every (dy, dz) with dy^2 + dz^2 <= r2max
-// the particles of the pixel run [x - rx, x + rx], rx = floor(sqrt(r2max - dy^2 - dz^2)), are
-// one contiguous range of the staged arrays, and every one of them is a partner by
-// construction. Tiles whose box or particle count does not fit read global memory instead.
+// through the tile's cells and one ring of cells around them, one warp per cell) are staged
+// in shared memory sorted by pixel, with a per-pixel offset table over the box "tile grown
+// by rr" (not clipped to the image: pixels outside hold no particles). A particle then visits
+// only the rows of its interaction ball: for every (dy, dz) with dy^2 + dz^2 <= r2max the
+// particles of the pixel run [x - rx, x + rx], rx = floor(sqrt(r2max - dy^2 - dz^2)), are one
+// contiguous range of the staged arrays, and every one of them is a partner by construction.
+// Tiles whose box or particle count does not fit read global memory instead.
 constexpr int kRecCap = 2048;      // staged particles per tile
 constexpr int kBoxCap = 16384;     // staged pixel box per tile
 constexpr int kMaxRows = 256;      // (dy, dz) rows of the interaction ball
+constexpr int kMaxRing = 4096;     // ring cells per tile
 
 struct Rec {
     float dE, eE;
@@ -739,54 +741,98 @@ __host__ __device__ __forceinline__ long long sob_box_cap(const Job& J)
     return bx * by * bz;
 }
 
-__host__ __device__ __forceinline__ bool sob_can_stage(const Job& J)
-{
-    const int rr = isqrt_floor(J.r2max);
-    const int w = 2 * rr + 1;
-    return J.r2max < 256 && (J.ndim == 3 ? w * w : w) <= kMaxRows && sob_box_cap(J) <= kBoxCap;
-}
-
 __host__ __device__ __forceinline__ long long sob_ring_cells(const Job& J)
 {
     return (long long)(J.tcx + 2) * (J.tcy + 2) * (J.ndim == 3 ? J.tcz + 2 : J.tcz);
 }
 
-// shared-memory layout: records | x | ring-cell prefix | pixel offsets (u16)
+__host__ __device__ __forceinline__ bool sob_can_stage(const Job& J)
+{
+    const int rr = isqrt_floor(J.r2max);
+    const int w = 2 * rr + 1;
+    return J.r2max < 256 && (J.ndim == 3 ? w * w : w) <= kMaxRows && sob_box_cap(J) <= kBoxCap &&
+           sob_ring_cells(J) <= kMaxRing;
+}
+
+// shared-memory layout: records | x | pixel offsets (u16) | ring-cell starts, counts, prefix
 struct SobLayout {
-    size_t x, eoff, off, total;
+    size_t x, off, cs, cn, eoff, total;
 };
 
 __host__ __device__ __forceinline__ SobLayout sob_layout(const Job& J)
 {
     SobLayout L;
     const bool st = sob_can_stage(J);
-    const size_t rec = st ? (size_t)kRecCap * sizeof(Rec) : 0;
-    L.x = rec;
-    L.eoff = L.x + (st ? (size_t)kRecCap * 2 : 0);
-    L.off = L.eoff + (size_t)((sob_ring_cells(J) + 4) & ~3LL) * 4;
-    L.total = L.off + (st ? (size_t)((sob_box_cap(J) + 8) & ~7LL) * 2 : 0);
+    const size_t ring = st ? (size_t)((sob_ring_cells(J) + 4) & ~3LL) * 4 : 0;
+    L.x = st ? (size_t)kRecCap * sizeof(Rec) : 0;
+    L.off = L.x + (st ? (size_t)kRecCap * 2 : 0);
+    L.cs = L.off + (st ? (size_t)((sob_box_cap(J) + 8) & ~7LL) * 2 : 0);
+    L.cn = L.cs + ring;
+    L.eoff = L.cn + ring;
+    L.total = L.eoff + ring;
     return L;
 }
 
+// the ring cell holding ring particle i (the last cell whose prefix is <= i)
+__device__ __forceinline__ int ring_cell_of(const unsigned* s_eoff, int ne, unsigned i)
+{
+    int lo = 0, hi = ne - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_eoff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <int NDIM>
-__global__ void __launch_bounds__(kBlock, 3) k_sobolev(Group g)
+__device__ __forceinline__ void sobolev_sums(const Job& J, int lp, int x, int y, int z, int r2max, float& As, float& Bs,
+                                             float& aA, float& aB, float& eAs, float& eBs, int& nA, int& nB)
+{
+    const int pcx = (int)fdiv((unsigned)x, J.fd_cell), pcy = (int)fdiv((unsigned)y, J.fd_cell);
+    const int pcz = NDIM == 3 ? (int)fdiv((unsigned)z, J.fd_cell) : z;
+    for (int cz = max(pcz - (NDIM == 3), 0); cz <= min(pcz + (NDIM == 3), J.ncz - 1); cz++)
+        for (int cy = max(pcy - 1, 0); cy <= min(pcy + 1, J.ncy - 1); cy++)
+            for (int cx = max(pcx - 1, 0); cx <= min(pcx + 1, J.ncx - 1); cx++) {
+                const long long cid = ((long long)cz * J.ncy + cy) * J.ncx + cx;
+                const unsigned c0 = J.cell_start[cid], c1 = c0 + J.cell_count[cid];
+                for (unsigned j = c0; j < c1; j++) {
+                    int qx, qy, qz;
+                    pix_coords(J, J.p_idx[j], qx, qy, qz);
+                    const int d2 = (qx - x) * (qx - x) + (qy - y) * (qy - y) + (qz - z) * (qz - z);
+                    if (d2 > r2max) continue;
+                    const float K = __ldg(J.klut + d2);
+                    const int ql = J.p_l[j], qc = J.p_c[j];
+                    if (ql == lp) {
+                        const float wq = K * J.p_dE[j];
+                        As += wq; aA += fabsf(wq); eAs += K * J.p_eE[j]; nA++;
+                    } else if (qc == lp) {
+                        const float wq = K * J.p_dE[j];
+                        Bs += wq; aB += fabsf(wq); eBs += K * J.p_eE[j]; nB++;
+                    }
+                }
+            }
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned s_warp[32];
     __shared__ float s_klut[256];
-    __shared__ int s_rows[kMaxRows];
+    __shared__ int s_rdelta[kMaxRows];           // row offset in the pixel box
+    __shared__ unsigned short s_rinfo[kMaxRows]; // rx | dy^2 + dz^2 << 8
     __shared__ int s_nrows;
     __shared__ unsigned s_osc;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const unsigned t = blockIdx.x;
     const int gj = group_job_of_tile(g, t);
     const Job& J = g.jobs[g.job_ids[gj]];
     const unsigned k = t - g.tile_prefix[gj];
     Counters* ctr = J.ctr;
-    if (ld_volatile(&ctr->skip) || ld_volatile(&ctr->need)) return;
+    const unsigned skip = ld_volatile(&ctr->skip) | ld_volatile(&ctr->need);
     const unsigned pstart = J.tile_start[k], pcount = J.tile_count[k];
-    if (pcount == 0) return;
     const int mode = ld_volatile(&ctr->mode);
+    if (skip || pcount == 0) return;
     if (mode == SEG_L2) {
         for (unsigned i = tid; i < pcount; i += blockDim.x) {
             J.p_g[pstart + i] = J.p_dE[pstart + i];
@@ -794,6 +840,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_sobolev(Group g)
         }
         return;
     }
+    // the thread's first own particle, fetched while the neighbourhood is staged
+    const unsigned my_gi = (unsigned)tid < pcount ? J.p_idx[pstart + tid] : 0u;
+    const int my_l = (unsigned)tid < pcount ? J.p_l[pstart + tid] : 0;
     const TileBox b = tile_box(J, k);
     const int r2max = J.r2max;
     const int rr = isqrt_floor(r2max);
@@ -801,209 +850,202 @@ __global__ void __launch_bounds__(kBlock, 3) k_sobolev(Group g)
     const SobLayout lay = sob_layout(J);
     Rec* s_rec = (Rec*)smem;
     unsigned short* s_x = (unsigned short*)(smem + lay.x);
-    unsigned* s_eoff = (unsigned*)(smem + lay.eoff);
     unsigned short* s_off = (unsigned short*)(smem + lay.off);
-
-    // ring cells: the tile's cells plus one ring
-    const int ex0 = max(b.cx0 - 1, 0), ex1 = min(b.cx0 + b.ccx + 1, J.ncx);
-    const int ey0 = max(b.cy0 - 1, 0), ey1 = min(b.cy0 + b.ccy + 1, J.ncy);
-    const int ez0 = NDIM == 3 ? max(b.cz0 - 1, 0) : b.cz0;
-    const int ez1 = NDIM == 3 ? min(b.cz0 + b.ccz + 1, J.ncz) : b.cz0 + b.ccz;
-    const int enx = ex1 - ex0, eny = ey1 - ey0, enz = ez1 - ez0;
-    const int ne = enx * eny * enz;
-    // staged pixel box: the tile's pixels grown by rr, clipped to the image
-    const int bx0 = max(b.x0 - rr, 0), bx1 = min(b.x1 + rr, J.W);
-    const int by0 = max(b.y0 - rr, 0), by1 = min(b.y1 + rr, J.H);
-    const int bz0 = NDIM == 3 ? max(b.z0 - rr, 0) : b.z0;
-    const int bz1 = NDIM == 3 ? min(b.z1 + rr, J.D) : b.z1;
-    const int bnx = bx1 - bx0, bny = by1 - by0, bnz = bz1 - bz0;
-    const int nbox = bnx * bny * bnz;
+    unsigned* s_off32 = (unsigned*)s_off;
+    unsigned* s_cs = (unsigned*)(smem + lay.cs);
+    unsigned* s_cn = (unsigned*)(smem + lay.cn);
+    unsigned* s_eoff = (unsigned*)(smem + lay.eoff);
 
     if (tid == 0) s_osc = 0;
     for (int d2 = tid; d2 <= r2max && d2 < 256; d2 += blockDim.x) s_klut[d2] = __ldg(J.klut + d2);
 
-    bool staged = false;
+    // staged pixel box: an x-slab [sx0, sx1) of the tile grown by rr (2D: z is the tile's single
+    // plane); the whole tile first, halved while its particles do not fit
+    const int by0 = b.y0 - rr, bz0 = NDIM == 3 ? b.z0 - rr : b.z0;
+    const int bny = b.y1 - b.y0 + 2 * rr, bnz = NDIM == 3 ? b.z1 - b.z0 + 2 * rr : 1;
+    int row_dy = 0, row_dz = 0, row_slot = -1;
+    unsigned ring_total = 0;
+    int ne = 0;
     if (can_stage) {
         // rows of the ball, (dz, dy) ascending, compacted in thread order
         const int w = 2 * rr + 1, nr = NDIM == 3 ? w * w : w;
         bool ok = false;
-        int packed = 0;
+        int info = 0;
         if (tid < nr) {
-            const int dy = tid % w - rr, dz = NDIM == 3 ? tid / w - rr : 0;
-            const int dyz2 = dy * dy + dz * dz;
+            row_dy = tid % w - rr;
+            row_dz = NDIM == 3 ? tid / w - rr : 0;
+            const int dyz2 = row_dy * row_dy + row_dz * row_dz;
             ok = dyz2 <= r2max;
-            const int rx = isqrt_floor(r2max - (ok ? dyz2 : 0));
-            packed = rx | ((dy + 128) << 8) | ((dz + 128) << 16) | (dyz2 << 24);
+            info = isqrt_floor(r2max - (ok ? dyz2 : 0)) | (dyz2 << 8);
         }
         unsigned tot_rows;
         const unsigned slot = block_excl_scan(ok ? 1u : 0u, s_warp, tot_rows);
-        if (ok) s_rows[slot] = packed;
+        if (ok) { s_rinfo[slot] = (unsigned short)info; row_slot = (int)slot; }
         if (tid == 0) s_nrows = (int)tot_rows;
-        // particle counts of the ring cells, and a zeroed pixel table
+        // ring cells: the tile's cells plus one ring, clipped to the image; their particle
+        // ranges and an exclusive prefix of their counts (ring index of a cell's first particle)
+        const int ex0 = max(b.cx0 - 1, 0), ex1 = min(b.cx0 + b.ccx + 1, J.ncx);
+        const int ey0 = max(b.cy0 - 1, 0), ey1 = min(b.cy0 + b.ccy + 1, J.ncy);
+        const int ez0 = NDIM == 3 ? max(b.cz0 - 1, 0) : b.cz0;
+        const int ez1 = NDIM == 3 ? min(b.cz0 + b.ccz + 1, J.ncz) : b.cz0 + b.ccz;
+        const int enx = ex1 - ex0, eny = ey1 - ey0;
+        ne = enx * eny * (ez1 - ez0);
         const int chunk = (ne + blockDim.x - 1) / blockDim.x;
         const int e0 = min(tid * chunk, ne), e1 = min(e0 + chunk, ne);
         unsigned cnt = 0;
         for (int e = e0; e < e1; e++) {
-            int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
-            long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
-            cnt += J.cell_count[cid];
-        }
-        unsigned* s_off32 = (unsigned*)s_off;
-        for (int i = tid; i < (nbox + 2) / 2; i += blockDim.x) s_off32[i] = 0u;
-        __syncthreads();                               // s_warp reuse
-        unsigned ring_total;
-        unsigned off = block_excl_scan(cnt, s_warp, ring_total);
-        for (int e = e0; e < e1; e++) {
-            int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
-            long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
-            s_eoff[e] = off;
-            off += J.cell_count[cid];
-        }
-        if (tid == 0) s_eoff[ne] = ring_total;
-        __syncthreads();
-        // pass 1: particles per box pixel
-        for (unsigned i = tid; i < ring_total; i += blockDim.x) {
-            int lo = 0, hi = ne - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_eoff[mid] <= i) lo = mid; else hi = mid - 1;
-            }
-            const int e = lo;
             const int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
             const long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
-            const unsigned p = J.cell_start[cid] + (i - s_eoff[e]);
-            int x, y, z;
-            pix_coords(J, J.p_idx[p], x, y, z);
-            x -= bx0; y -= by0; z -= bz0;
-            if ((unsigned)x < (unsigned)bnx && (unsigned)y < (unsigned)bny && (unsigned)z < (unsigned)bnz) {
-                const int bp = (z * bny + y) * bnx + x;
-                atomicAdd(&s_off32[bp >> 1], 1u << (16 * (bp & 1)));
-            }
+            const unsigned cs = J.cell_start[cid], cn = J.cell_count[cid];
+            s_cs[e] = cs;
+            s_cn[e] = cn;
+            cnt += cn;
         }
-        __syncthreads();
-        // exclusive prefix over the box pixels (chunk per thread)
-        const int pc = (nbox + blockDim.x - 1) / blockDim.x;
-        const int q0 = min(tid * pc, nbox), q1 = min(q0 + pc, nbox);
-        unsigned sum = 0;
-        for (int q = q0; q < q1; q++) sum += s_off[q];
         __syncthreads();                               // s_warp reuse
-        unsigned staged_total;
-        unsigned run = block_excl_scan(sum, s_warp, staged_total);
-        for (int q = q0; q < q1; q++) {
-            const unsigned c = s_off[q];
-            s_off[q] = (unsigned short)run;
-            run += c;
+        unsigned off = block_excl_scan(cnt, s_warp, ring_total);
+        for (int e = e0; e < e1; e++) {
+            s_eoff[e] = off;
+            off += s_cn[e];
         }
-        if (tid == 0) s_off[nbox] = (unsigned short)min(staged_total, 65535u);
-        staged = staged_total <= (unsigned)kRecCap;
-        __syncthreads();
-        if (staged) {
-            // pass 2: scatter; particles of one pixel are adjacent in their cell, so the rank of
-            // a particle among its pixel's particles is the run of equal indices before it
-            for (unsigned i = tid; i < ring_total; i += blockDim.x) {
-                int lo = 0, hi = ne - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (s_eoff[mid] <= i) lo = mid; else hi = mid - 1;
-                }
-                const int e = lo;
-                const int lx = e % enx, ly = (e / enx) % eny, lz = e / (enx * eny);
-                const long long cid = ((long long)(ez0 + lz) * J.ncy + (ey0 + ly)) * J.ncx + (ex0 + lx);
-                const unsigned within = i - s_eoff[e];
-                const unsigned p = J.cell_start[cid] + within;
-                const unsigned gi = J.p_idx[p];
-                int x, y, z;
-                pix_coords(J, gi, x, y, z);
-                x -= bx0; y -= by0; z -= bz0;
-                if ((unsigned)x < (unsigned)bnx && (unsigned)y < (unsigned)bny && (unsigned)z < (unsigned)bnz) {
-                    unsigned rank = 0;
-                    while (rank < within && J.p_idx[p - rank - 1] == gi) rank++;
-                    const int bp = (z * bny + y) * bnx + x;
-                    const unsigned pos = s_off[bp] + rank;
-                    Rec r;
-                    r.dE = J.p_dE[p];
-                    r.eE = J.p_eE[p];
-                    r.l = J.p_l[p];
-                    r.c = J.p_c[p];
-                    s_rec[pos] = r;
-                    s_x[pos] = (unsigned short)x;
-                }
-            }
-        }
-        __syncthreads();
-    } else {
-        __syncthreads();
     }
 
     unsigned osc = 0;
-    const int nrows = staged ? s_nrows : 0;
-    for (unsigned i = tid; i < pcount; i += blockDim.x) {
-        const unsigned p = pstart + i;
-        const unsigned gi = J.p_idx[p];
-        int x, y, z;
-        pix_coords(J, gi, x, y, z);
-        const int lp = J.p_l[p];
-        float As = 0.f, Bs = 0.f, aA = 0.f, aB = 0.f, eAs = 0.f, eBs = 0.f;
-        int nA = 0, nB = 0;
-        if (staged) {
-            const int lx = x - bx0, ly = y - by0, lz = z - bz0;
-            for (int r = 0; r < nrows; r++) {
-                const int row = s_rows[r];
-                const int yy = ly + ((row >> 8) & 255) - 128;
-                const int zz = lz + ((row >> 16) & 255) - 128;
-                if ((unsigned)yy >= (unsigned)bny || (unsigned)zz >= (unsigned)bnz) continue;
-                const int rx = row & 255, dyz2 = (int)((unsigned)row >> 24);
-                const int xl = max(lx - rx, 0), xh = min(lx + rx, bnx - 1);
-                const int base = (zz * bny + yy) * bnx;
-                const unsigned j1 = s_off[base + xh + 1];
-                for (unsigned j = s_off[base + xl]; j < j1; j++) {
-                    const int dx = (int)s_x[j] - lx;
-                    const float K = s_klut[dyz2 + dx * dx];
-                    const Rec q = s_rec[j];
-                    if (q.l == lp) {
-                        const float w = K * q.dE;
-                        As += w; aA += fabsf(w); eAs += K * q.eE; nA++;
-                    } else if (q.c == lp) {
-                        const float w = K * q.dE;
-                        Bs += w; aB += fabsf(w); eBs += K * q.eE; nB++;
+    int sx0 = b.x0, width = b.x1 - b.x0;
+    while (sx0 < b.x1) {                                 // block-uniform
+        const int sx1 = min(sx0 + width, b.x1);
+        const int bx0 = sx0 - rr, bnx = sx1 - sx0 + 2 * rr;
+        const int nbox = bnx * bny * bnz;
+        bool staged = false;
+        if (can_stage) {
+            if (row_slot >= 0) s_rdelta[row_slot] = (row_dz * bny + row_dy) * bnx;
+            for (int i = tid; i < (nbox + 2) / 2; i += blockDim.x) s_off32[i] = 0u;
+            __syncthreads();
+            // pass 1: particles per box pixel, one thread per ring particle
+            for (unsigned i = tid; i < ring_total; i += blockDim.x) {
+                const int e = ring_cell_of(s_eoff, ne, i);
+                int x, y, z;
+                pix_coords(J, J.p_idx[s_cs[e] + (i - s_eoff[e])], x, y, z);
+                x -= bx0; y -= by0; z -= bz0;
+                if ((unsigned)x < (unsigned)bnx && (unsigned)y < (unsigned)bny && (unsigned)z < (unsigned)bnz) {
+                    const int bp = (z * bny + y) * bnx + x;
+                    atomicAdd(&s_off32[bp >> 1], 1u << (16 * (bp & 1)));
+                }
+            }
+            __syncthreads();
+            // exclusive prefix over the box pixels (chunk per thread)
+            const int pc = (nbox + blockDim.x - 1) / blockDim.x;
+            const int q0 = min(tid * pc, nbox), q1 = min(q0 + pc, nbox);
+            unsigned sum = 0;
+            for (int q = q0; q < q1; q++) sum += s_off[q];
+            unsigned staged_total;
+            unsigned run = block_excl_scan(sum, s_warp, staged_total);
+            if (staged_total > (unsigned)kRecCap && sx1 - sx0 > 1) {
+                width = (sx1 - sx0 + 1) / 2;                  // too many: a narrower slab
+                __syncthreads();
+                continue;
+            }
+            for (int q = q0; q < q1; q++) {
+                const unsigned c = s_off[q];
+                s_off[q] = (unsigned short)run;
+                run += c;
+            }
+            if (tid == 0) s_off[nbox] = (unsigned short)min(staged_total, 65535u);
+            staged = staged_total <= (unsigned)kRecCap;
+            __syncthreads();
+            if (staged) {
+                // pass 2: scatter. Particles of one pixel are adjacent in their cell, hence in
+                // ring order; a particle's rank among them is the run of equal pixel indices
+                // before it (found with warp ballots, global loads only across warp chunks).
+                for (unsigned base = 0; base < ring_total; base += blockDim.x) {
+                    const unsigned i = base + tid;
+                    const bool v = i < ring_total;
+                    unsigned p = 0, gi = 0xffffffffu, within = 0;
+                    if (v) {
+                        const int e = ring_cell_of(s_eoff, ne, i);
+                        within = i - s_eoff[e];
+                        p = s_cs[e] + within;
+                        gi = J.p_idx[p];
+                    }
+                    unsigned prev = __shfl_up_sync(0xffffffffu, gi, 1);
+                    if (lane == 0 && v && within > 0) prev = J.p_idx[p - 1];
+                    const bool eq = v && within > 0 && prev == gi;
+                    const unsigned m = __ballot_sync(0xffffffffu, eq);
+                    int x, y, z;
+                    pix_coords(J, v ? gi : 0u, x, y, z);
+                    x -= bx0; y -= by0; z -= bz0;
+                    if (v && (unsigned)x < (unsigned)bnx && (unsigned)y < (unsigned)bny && (unsigned)z < (unsigned)bnz) {
+                        unsigned rank = 0;
+                        if (eq) {
+                            const unsigned zeros = ~m & ((2u << lane) - 1u);   // lanes <= lane not equal
+                            if (zeros) {
+                                rank = (unsigned)lane - (31u - __clz(zeros));
+                            } else {
+                                rank = (unsigned)lane + 1;                   // the run reaches lane 0
+                                while (rank < within && J.p_idx[p - rank - 1] == gi) rank++;
+                            }
+                        }
+                        const unsigned pos = s_off[(z * bny + y) * bnx + x] + rank;
+                        Rec r;
+                        r.dE = J.p_dE[p];
+                        r.eE = J.p_eE[p];
+                        r.l = J.p_l[p];
+                        r.c = J.p_c[p];
+                        s_rec[pos] = r;
+                        s_x[pos] = (unsigned short)x;
                     }
                 }
             }
-        } else {
-            const int pcx = (int)fdiv((unsigned)x, J.fd_cell), pcy = (int)fdiv((unsigned)y, J.fd_cell);
-            const int pcz = NDIM == 3 ? (int)fdiv((unsigned)z, J.fd_cell) : z;
-            for (int cz = max(pcz - (NDIM == 3), 0); cz <= min(pcz + (NDIM == 3), J.ncz - 1); cz++)
-                for (int cy = max(pcy - 1, 0); cy <= min(pcy + 1, J.ncy - 1); cy++)
-                    for (int cx = max(pcx - 1, 0); cx <= min(pcx + 1, J.ncx - 1); cx++) {
-                        const long long cid = ((long long)cz * J.ncy + cy) * J.ncx + cx;
-                        const unsigned c0 = J.cell_start[cid], c1 = c0 + J.cell_count[cid];
-                        for (unsigned j = c0; j < c1; j++) {
-                            int qx, qy, qz;
-                            pix_coords(J, J.p_idx[j], qx, qy, qz);
-                            const int d2 = (qx - x) * (qx - x) + (qy - y) * (qy - y) + (qz - z) * (qz - z);
-                            if (d2 > r2max) continue;
-                            const float K = __ldg(J.klut + d2);
-                            const int ql = J.p_l[j], qc = J.p_c[j];
-                            if (ql == lp) {
-                                const float w = K * J.p_dE[j];
-                                As += w; aA += fabsf(w); eAs += K * J.p_eE[j]; nA++;
-                            } else if (qc == lp) {
-                                const float w = K * J.p_dE[j];
-                                Bs += w; aB += fabsf(w); eBs += K * J.p_eE[j]; nB++;
-                            }
+        }
+        __syncthreads();
+
+        const int nrows = staged ? s_nrows : 0;
+        for (unsigned i = tid; i < pcount; i += blockDim.x) {
+            const unsigned p = pstart + i;
+            const unsigned gi = i == (unsigned)tid ? my_gi : J.p_idx[p];
+            int x, y, z;
+            pix_coords(J, gi, x, y, z);
+            if (x < sx0 || x >= sx1) continue;
+            const int lp = i == (unsigned)tid ? my_l : J.p_l[p];
+            float As = 0.f, Bs = 0.f, aA = 0.f, aB = 0.f, eAs = 0.f, eBs = 0.f;
+            int nA = 0, nB = 0;
+            if (staged) {
+                // the particle lies in the slab, so every row of its ball lies in the box
+                const int lx = x - bx0;
+                const int cbase = ((z - bz0) * bny + (y - by0)) * bnx + lx;
+                for (int r = 0; r < nrows; r++) {
+                    const int info = s_rinfo[r];
+                    const int rx = info & 255, dyz2 = info >> 8;
+                    const int base = cbase + s_rdelta[r];
+                    const unsigned j1 = s_off[base + rx + 1];
+                    for (unsigned j = s_off[base - rx]; j < j1; j++) {
+                        const int dx = (int)s_x[j] - lx;
+                        const float K = s_klut[dyz2 + dx * dx];
+                        const Rec q = s_rec[j];
+                        if (q.l == lp) {
+                            const float wq = K * q.dE;
+                            As += wq; aA += fabsf(wq); eAs += K * q.eE; nA++;
+                        } else if (q.c == lp) {
+                            const float wq = K * q.dE;
+                            Bs += wq; aB += fabsf(wq); eBs += K * q.eE; nB++;
                         }
                     }
+                }
+            } else {
+                sobolev_sums<NDIM>(J, lp, x, y, z, r2max, As, Bs, aA, aB, eAs, eBs, nA, nB);
+            }
+            float A = nA ? As / (float)nA : 0.f;
+            float B = nB ? Bs / (float)nB : 0.f;
+            float eA = nA ? ((eAs + (kU + gamma_n(nA)) * aA) * 1.0001f / (float)nA + kU * fabsf(A)) : 0.f;
+            float eB = nB ? ((eBs + (kU + gamma_n(nB)) * aB) * 1.0001f / (float)nB + kU * fabsf(B)) : 0.f;
+            float gp = A - B;
+            float margin = kFp64Margin * ((nA ? aA / (float)nA : 0.f) + (nB ? aB / (float)nB : 0.f));
+            float eg = (eA + eB + kU * fabsf(gp) + margin) * 1.001f;
+            J.p_g[p] = gp;
+            J.p_eg[p] = eg;
+            osc += (A != 0.f && B != 0.f && ((A > 0.f) == (B > 0.f))) ? 1u : 0u;
         }
-        float A = nA ? As / (float)nA : 0.f;
-        float B = nB ? Bs / (float)nB : 0.f;
-        float eA = nA ? ((eAs + (kU + gamma_n(nA)) * aA) * 1.0001f / (float)nA + kU * fabsf(A)) : 0.f;
-        float eB = nB ? ((eBs + (kU + gamma_n(nB)) * aB) * 1.0001f / (float)nB + kU * fabsf(B)) : 0.f;
-        float gp = A - B;
-        float margin = kFp64Margin * ((nA ? aA / (float)nA : 0.f) + (nB ? aB / (float)nB : 0.f));
-        float eg = (eA + eB + kU * fabsf(gp) + margin) * 1.001f;
-        J.p_g[p] = gp;
-        J.p_eg[p] = eg;
-        osc += (A != 0.f && B != 0.f && ((A > 0.f) == (B > 0.f))) ? 1u : 0u;
+        sx0 = sx1;
+        __syncthreads();                                 // the next slab reuses shared memory
     }
     if (osc) atomicAdd(&s_osc, osc);
     __syncthreads();
