@@ -80,18 +80,21 @@ def kernel_sources_digest() -> str:
 
 
 def traffic_from_profile(stage: str, workload: str, units: float):
-    """DRAM bytes per launch from the committed ncu summary, scaled to this launch, or None
-    when the summary is missing, is for another workload, or predates the current kernels."""
+    """DRAM bytes per launch from the committed ncu summary (bytes per particle of the captured
+    launch, scaled to this launch's particles), or None when there is no capture of this stage on
+    this workload or the kernels changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
         return None
-    e = d.get(stage)
-    if not e or e.get("workload") != workload or e.get("sources") != kernel_sources_digest():
+    if d.get("sources") != kernel_sources_digest():
         return None
-    return float(e["dram_bytes_per_unit"]) * units
+    for e in d.get("entries", []):
+        if e.get("stage") == stage and e.get("workload") == workload:
+            return float(e["dram_bytes_per_unit"]) * units
+    return None
 
 
 class ClockSampler:
@@ -416,6 +419,7 @@ def run_ours(args, world, rank, local, pg):
 
     ctx = new_ctx()
     done_in_job = 0
+    iter_log = open(args.iter_log, "w") if args.iter_log else None
     for _ in range(args.warmup):
         if done_in_job == iters_per_job:
             ctx.close()
@@ -423,6 +427,8 @@ def run_ours(args, world, rank, local, pg):
         flush.zero_()
         ctx.step_async(1)
         done_in_job += 1
+        if iter_log:
+            iter_log.write(json.dumps({"phase": "warmup", **ctx.poll()}) + "\n")
     ctx.poll()
     torch.cuda.synchronize(dev)
 
@@ -454,6 +460,8 @@ def run_ours(args, world, rank, local, pg):
             stage_ms[s_] += st[s_]
         done_in_job += 1
         sp = ctx.poll()
+        if iter_log:
+            iter_log.write(json.dumps({"phase": "timed", **sp}) + "\n")
         accepted += sp["n_accepted"]
         fixups += sp["n_fixup"]
         rounds += sp["mis_rounds"]
@@ -548,6 +556,8 @@ def main():
     ap.add_argument("--iters-per-step", type=int, default=4, help="served: most iterations per batch step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--iter-log", default="", help="write every warm-up and timed iteration's status here "
+                    "(JSON lines), to relate profiler launches to their particle counts")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
