@@ -213,8 +213,23 @@ def run_batch(args, world, rank, local, pg):
     jobs = synth.batch_disks(args.images, seed0=1000 + 100000 * rank, iterations=args.steps)
     dev_jobs = [(torch.from_numpy(w.image).to(dev), torch.from_numpy(w.labels0).to(dev), w) for w in jobs]
 
+    # cell edge and tile shape for the batch, tuned by timing candidate settings on a sample of
+    # the batch stepped together; both the batch and the per-image loop use the tuned settings
+    from paper_1403_0240_gb300 import tune
+    tuned, tune_table = {}, []
+    if not args.no_tune:
+        best, tune_table = tune.autotune_batch(
+            [(i, l, dict(model=w.model, lam=w.lam, cutoff=w.cutoff)) for i, l, w in dev_jobs], iters=5,
+            sample=128, stream=stream)
+        tuned = {"cell_mult": best["cell_multiple"], "tile": best["tile"]}
+
+    def settings(w):
+        if not tuned:
+            return {}
+        return {"cell_edge": tuned["cell_mult"] * max(1, math.ceil(w.cutoff)), "tile": tuned["tile"]}
+
     def contexts(n=None):
-        return [seg.Context(i, l, model=w.model, lam=w.lam, cutoff=w.cutoff, stream=stream)
+        return [seg.Context(i, l, model=w.model, lam=w.lam, cutoff=w.cutoff, stream=stream, **settings(w))
                 for i, l, w in dev_jobs[:n]]
 
     # warm-up: graph capture and code paths on a few jobs
@@ -270,6 +285,7 @@ def run_batch(args, world, rank, local, pg):
                        "1-8 disks, piecewise constant, cutoff 3, one batch stepped together",
                        "plain_value": parts_p / t_p, "batched_over_plain": (parts_b / t_b) / (parts_p / t_p),
                        "plain_s": t_p, "batched_s": t_b, "images": args.images,
+                       "tuned": tuned, "tune_table_s_per_iter": [list(t) for t in tune_table],
                        "timing": "wall clock around whole-batch steps (synchronised)"}}
     print(json.dumps(line), flush=True)
 
@@ -556,6 +572,7 @@ def main():
     ap.add_argument("--iters-per-step", type=int, default=4, help="served: most iterations per batch step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="batch512: default cell edge and tile shape")
     ap.add_argument("--iter-log", default="", help="write every warm-up and timed iteration's status here "
                     "(JSON lines), to relate profiler launches to their particle counts")
     args = ap.parse_args()

@@ -74,7 +74,10 @@ typedef struct {
     int32_t validate;      /* nonzero: check on the host that every foreground label of labels0
                               is one connected component (else SEG_EINVAL) */
     int32_t cell_edge;     /* cell-list edge in pixels, >= ceil(cutoff); 0 = ceil(cutoff) */
-    int32_t reserved[7];   /* must be zero */
+    int32_t tile[3];       /* tile shape in pixels {z, y, x}, each 0 (default) or 1..1024; a tile
+                              is floor(tile / cell_edge) cells (at least one) per axis; z must be
+                              0 or 1 in 2D. Default 8 x 32 x 32 / cell (3D), 32 x 64 / cell (2D) */
+    int32_t reserved[4];   /* must be zero */
 } seg_params;
 
 typedef struct {
@@ -119,6 +122,28 @@ typedef struct {
 /* Bytes of device memory seg_init will allocate for these parameters (particle
  * capacity at its initial size). Returns SEG_EINVAL for invalid parameters. */
 int seg_estimate_bytes(const seg_params* p, int32_t nlabels, size_t* bytes);
+
+/* Autotuning (batched and served workloads): the cell-list edge and the tile shape change only
+ * the speed, never a label, statistic or particle set. seg_autotune times candidates on the
+ * given job: cell edge in {c, 2c} (c = p->cell_edge, or ceil(cutoff) when 0) times tile shapes
+ * {16x16, 32x32, 32x64, 64x64, 64x128} (2D, y x x) or {8x8x8, 8x8x32, 16x16x16, 8x16x32,
+ * 16x16x32} (3D, z x y x x); a candidate whose tiles come out the same in cells as an earlier
+ * one is skipped. Each candidate is a fresh context (seg_init on image and labels0, host or
+ * device pointers) stepped 2 untimed and then `iters` timed iterations (CUDA events on
+ * cuda_stream; no L2 flush); its mean time per iteration is reported. *best receives p with
+ * cell_edge and tile set to the fastest candidate. entries (may be NULL) receive up to
+ * max_entries candidates in the order tried, *n_entries (may be NULL) their number.
+ * Returns SEG_OK when at least one candidate ran, else the first candidate's error. */
+typedef struct {
+    int32_t cell_edge;     /* cell-list edge in pixels */
+    int32_t tile[3];       /* tile shape in pixels {z, y, x} */
+    float   ms_per_iter;   /* mean time of one iteration; -1 when the candidate failed */
+    int32_t status;        /* SEG_OK, or the error seg_init / seg_step returned */
+} seg_tune_entry;
+
+int seg_autotune(const seg_params* p, const void* image, const int32_t* labels0, int32_t iters,
+                 void* cuda_stream, seg_params* best, seg_tune_entry* entries, int32_t max_entries,
+                 int32_t* n_entries);
 
 /* Create a context: validates p, copies image (dtype elements, D*H*W, host or
  * device) and labels0 (int32 >= 0, host or device; 0 = background), computes the

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -140,7 +141,10 @@ int validate(const seg_params* p)
     if (p->stats_mode != SEG_STATS_EXACT) return SEG_EINVAL;
     int need = (int)std::ceil(p->cutoff);
     if (p->cell_edge != 0 && (p->cell_edge < need || p->cell_edge > 256)) return SEG_EINVAL;
-    for (int i = 0; i < 7; i++)
+    for (int i = 0; i < 3; i++)
+        if (p->tile[i] < 0 || p->tile[i] > 1024) return SEG_EINVAL;
+    if (p->ndim == 2 && p->tile[0] > 1) return SEG_EINVAL;
+    for (int i = 0; i < 4; i++)
         if (p->reserved[i]) return SEG_EINVAL;
     return SEG_OK;
 }
@@ -192,15 +196,13 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     h.ncx = (h.W + s - 1) / s;
     h.ncy = (h.H + s - 1) / s;
     h.ncz = h.ndim == 3 ? (h.D + s - 1) / s : h.D;
-    if (h.ndim == 2) {
-        h.tcx = std::max(1, 64 / s);
-        h.tcy = std::max(1, 32 / s);
-        h.tcz = 1;
-    } else {
-        h.tcx = std::max(1, 32 / s);
-        h.tcy = std::max(1, 8 / s);
-        h.tcz = std::max(1, 8 / s);
-    }
+    // tiles: a whole number of cells per axis (default 32 x 64 pixels in 2D, 8 x 8 x 32 in 3D)
+    const int tx = p->tile[2] > 0 ? p->tile[2] : (h.ndim == 2 ? 64 : 32);
+    const int ty = p->tile[1] > 0 ? p->tile[1] : (h.ndim == 2 ? 32 : 8);
+    const int tz = p->tile[0] > 0 ? p->tile[0] : 8;
+    h.tcx = std::max(1, tx / s);
+    h.tcy = std::max(1, ty / s);
+    h.tcz = h.ndim == 2 ? 1 : std::max(1, tz / s);
     h.ntx = (h.ncx + h.tcx - 1) / h.tcx;
     h.nty = (h.ncy + h.tcy - 1) / h.tcy;
     h.ntz = (h.ncz + h.tcz - 1) / h.tcz;
@@ -706,6 +708,76 @@ int seg_estimate_bytes(const seg_params* p, int32_t nlabels, size_t* bytes)
     Plan P;
     make_geometry(p, nlabels, 1, 254, P);
     *bytes = P.fixed.bytes + particle_bytes(default_pcap(P.h.npix, P.h.ndim), P.h.nbr_stride);
+    return SEG_OK;
+}
+
+int seg_autotune(const seg_params* p, const void* image, const int32_t* labels0, int32_t iters, void* cuda_stream,
+                 seg_params* best, seg_tune_entry* entries, int32_t max_entries, int32_t* n_entries)
+{
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!image || !labels0 || !best || iters < 1 || max_entries < 0) return SEG_EINVAL;
+    if (n_entries) *n_entries = 0;
+    const int c0 = p->cell_edge ? p->cell_edge : std::max(1, (int)std::ceil(p->cutoff));
+    static const int t2[5][3] = {{1, 16, 16}, {1, 32, 32}, {1, 32, 64}, {1, 64, 64}, {1, 64, 128}};
+    static const int t3[5][3] = {{8, 8, 8}, {8, 8, 32}, {16, 16, 16}, {8, 16, 32}, {16, 16, 32}};
+    const int (*tiles)[3] = p->ndim == 2 ? t2 : t3;
+    std::vector<std::array<int, 4>> seen;   // (cell, tcz, tcy, tcx) already tried
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "autotune events");
+    }
+    int n = 0, first_err = SEG_OK;
+    float best_ms = -1.0f;
+    for (int ci = 0; ci < 2; ci++) {
+        const int cell = c0 * (ci + 1);
+        if (cell > 256) continue;
+        for (int ti = 0; ti < 5; ti++) {
+            seg_params q = *p;
+            q.cell_edge = cell;
+            q.tile[0] = p->ndim == 2 ? 0 : tiles[ti][0];
+            q.tile[1] = tiles[ti][1];
+            q.tile[2] = tiles[ti][2];
+            std::array<int, 4> key = {cell, p->ndim == 2 ? 1 : std::max(1, q.tile[0] / cell),
+                                      std::max(1, q.tile[1] / cell), std::max(1, q.tile[2] / cell)};
+            if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+            seen.push_back(key);
+            float ms = -1.0f;
+            seg_ctx* c = nullptr;
+            int r = seg_init(&q, image, labels0, cuda_stream, &c);
+            if (r == SEG_OK) r = seg_step(c, 2, nullptr);
+            if (r == SEG_OK) {
+                if (cudaEventRecord(e0, stream) != cudaSuccess) r = SEG_ECUDA;
+                if (r == SEG_OK) r = seg_step_async(c, iters);
+                if (r == SEG_OK && cudaEventRecord(e1, stream) != cudaSuccess) r = SEG_ECUDA;
+                if (r == SEG_OK && cudaEventSynchronize(e1) != cudaSuccess) r = SEG_ECUDA;
+                if (r == SEG_OK) r = seg_poll(c, nullptr);
+                float t = 0.0f;
+                if (r == SEG_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = t / (float)iters;
+                else if (r == SEG_OK) r = SEG_ECUDA;
+            }
+            if (c) seg_destroy(c);
+            if (r != SEG_OK && first_err == SEG_OK) first_err = r;
+            if (r != SEG_OK) ms = -1.0f;
+            if (entries && n < max_entries) {
+                entries[n].cell_edge = cell;
+                for (int i = 0; i < 3; i++) entries[n].tile[i] = q.tile[i];
+                entries[n].ms_per_iter = ms;
+                entries[n].status = r;
+            }
+            n++;
+            if (ms >= 0.0f && (best_ms < 0.0f || ms < best_ms)) {
+                best_ms = ms;
+                *best = q;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_entries) *n_entries = std::min(n, max_entries);
+    if (best_ms < 0.0f) return first_err ? first_err : SEG_EINVAL;
     return SEG_OK;
 }
 

@@ -26,7 +26,13 @@ class Params(C.Structure):
                 ("model", C.c_int32), ("connectivity", C.c_int32),
                 ("lam", C.c_double), ("cutoff", C.c_double), ("ps_radius", C.c_double),
                 ("gradient", C.c_int32), ("osc_window", C.c_int32), ("stats_mode", C.c_int32),
-                ("validate", C.c_int32), ("cell_edge", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("validate", C.c_int32), ("cell_edge", C.c_int32), ("tile", C.c_int32 * 3),
+                ("reserved", C.c_int32 * 4)]
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("cell_edge", C.c_int32), ("tile", C.c_int32 * 3), ("ms_per_iter", C.c_float),
+                ("status", C.c_int32)]
 
 
 class Status(C.Structure):
@@ -52,6 +58,8 @@ class ParticleBuffers(C.Structure):
 _P, _V = C.POINTER, C.c_void_p
 SIGNATURES = [
     ("seg_estimate_bytes", C.c_int, [_P(Params), C.c_int32, _P(C.c_size_t)]),
+    ("seg_autotune", C.c_int, [_P(Params), _V, _V, C.c_int32, _V, _P(Params), _P(TuneEntry), C.c_int32,
+                               _P(C.c_int32)]),
     ("seg_init", C.c_int, [_P(Params), _V, _V, _V, _P(_V)]),
     ("seg_step", C.c_int, [_V, C.c_int32, _P(Status)]),
     ("seg_step_async", C.c_int, [_V, C.c_int32]),
@@ -152,7 +160,7 @@ def _stream_handle(stream):
 
 
 def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_radius=0.0,
-                gradient="sobolev", osc_window=0, validate=False, cell_edge=0) -> Params:
+                gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None) -> Params:
     shape = tuple(int(s) for s in image.shape)
     p = Params()
     p.ndim = len(shape)
@@ -168,7 +176,30 @@ def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_ra
     p.stats_mode = SEG_STATS_EXACT
     p.validate = int(bool(validate))
     p.cell_edge = int(cell_edge)
+    if tile is not None:
+        t = [int(v) for v in tile]
+        t = [0] * (3 - len(t)) + t          # (y, x) in 2D
+        p.tile[0], p.tile[1], p.tile[2] = t
     return p
+
+
+def autotune(image, labels0, iters: int = 10, stream=None, **kw):
+    """Time the cell-edge x tile-shape candidates of seg_autotune on this job; returns
+    (best keyword arguments for Context, [(cell_edge, tile, ms_per_iter, status), ...])."""
+    params = make_params(image, **kw)
+    ip, ikeep = _ptr(image)
+    lp, lkeep = _ptr(labels0 if _is_torch(labels0) else np.asarray(labels0, dtype=np.int32))
+    best = Params()
+    entries = (TuneEntry * 16)()
+    n = C.c_int32(0)
+    _check(lib().seg_autotune(C.byref(params), ip, lp, int(iters), _stream_handle(stream), C.byref(best), entries, 16,
+                              C.byref(n)), "seg_autotune")
+    table = [(int(e.cell_edge), tuple(int(v) for v in e.tile), float(e.ms_per_iter), int(e.status))
+             for e in entries[:n.value]]
+    out = dict(kw)
+    out["cell_edge"] = int(best.cell_edge)
+    out["tile"] = tuple(int(v) for v in best.tile)
+    return out, table
 
 
 def estimate_bytes(params: Params, nlabels: int) -> int:
@@ -181,9 +212,9 @@ class Context:
     """One segmentation job resident on the GPU (seg_init ... seg_destroy)."""
 
     def __init__(self, image, labels0, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_radius=0.0,
-                 gradient="sobolev", osc_window=0, validate=False, cell_edge=0, stream=None):
+                 gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None, stream=None):
         self.params = make_params(image, model, connectivity, lam, cutoff, ps_radius, gradient, osc_window,
-                                  validate, cell_edge)
+                                  validate, cell_edge, tile)
         self.shape = tuple(int(s) for s in image.shape)
         ip, ikeep = _ptr(image)
         lp, lkeep = _ptr(labels0 if _is_torch(labels0) else np.asarray(labels0, dtype=np.int32))

@@ -87,7 +87,7 @@ class SegBackend:
 
 
 def _param_kwargs(req: Request) -> dict:
-    keys = ("model", "connectivity", "lam", "cutoff", "ps_radius", "gradient", "osc_window", "cell_edge")
+    keys = ("model", "connectivity", "lam", "cutoff", "ps_radius", "gradient", "osc_window", "cell_edge", "tile")
     return {k: req.params[k] for k in keys if k in req.params}
 
 

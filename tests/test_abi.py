@@ -34,7 +34,7 @@ def test_header_symbols_exported(libseg):
 
 
 def test_struct_layouts():
-    # seg_params: 2 x int32, 3 x int64, 2 x int32, 3 x double, 5 x int32, 7 reserved int32
+    # seg_params: 2 x int32, 3 x int64, 2 x int32, 3 x double, 5 x int32, 3 x int32 tile, 4 reserved int32
     assert C.sizeof(seg.Params) == 112
     assert C.sizeof(seg.Status) == 72
     assert C.sizeof(seg.State) == 32
@@ -52,4 +52,12 @@ def test_strerror_and_validation_without_gpu(libseg):
     assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL
     p.cutoff = 3.0
     p.connectivity = 6
+    assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL
+    p.connectivity = 4
+    for tile, code in [((0, 16, 16), seg.SEG_OK), ((1, 64, 128), seg.SEG_OK), ((2, 16, 16), seg.SEG_EINVAL),
+                       ((0, -1, 16), seg.SEG_EINVAL), ((0, 16, 1025), seg.SEG_EINVAL)]:
+        p.tile[0], p.tile[1], p.tile[2] = tile
+        assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == code, tile
+    p.tile[0] = p.tile[1] = p.tile[2] = 0
+    p.reserved[3] = 1
     assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL
