@@ -652,6 +652,81 @@ cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream
     return cudaGetLastError();
 }
 
+// One pass over the inputs: label range, float32 exponent range and largest magnitude (or the
+// largest uint16 value), NaN/infinity, and the number of particles of the initial labels
+// (per pixel, the distinct labels among its 4 (2D) or 6 (3D) neighbours that differ from its
+// own). out must hold the identities of the reductions on entry.
+__global__ void k_scan_inputs(const void* I, int dtype, const int* L, int ndim, int D, int H, int W, InputScan* out)
+{
+    const long long npix = (long long)D * H * W;
+    int lmin = 0x7fffffff, lmax = -0x7fffffff - 1, slo = 0x7fffffff, shi = -1, bad = 0;
+    unsigned mabs = 0;
+    unsigned long long parts = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
+        const int l = L[i];
+        lmin = min(lmin, l);
+        lmax = max(lmax, l);
+        if (dtype == SEG_F32) {
+            const unsigned b = ((const unsigned*)I)[i];
+            const int eb = (int)((b >> 23) & 0xffu);
+            if (eb == 255) bad = 1;
+            else if (b & 0x7fffffffu) {
+                const int slot = eb ? eb : 1;
+                slo = min(slo, slot);
+                shi = max(shi, slot);
+                mabs = max(mabs, b & 0x7fffffffu);
+            }
+        } else {
+            mabs = max(mabs, (unsigned)((const unsigned short*)I)[i]);
+        }
+        const long long x = i % W, y = (i / W) % H, z = i / ((long long)W * H);
+        int nb[6];
+        int n = 0;
+        if (x > 0) nb[n++] = L[i - 1];
+        if (x + 1 < W) nb[n++] = L[i + 1];
+        if (y > 0) nb[n++] = L[i - W];
+        if (y + 1 < H) nb[n++] = L[i + W];
+        if (ndim == 3 && z > 0) nb[n++] = L[i - (long long)W * H];
+        if (ndim == 3 && z + 1 < D) nb[n++] = L[i + (long long)W * H];
+        for (int a = 0; a < n; a++) {
+            if (nb[a] == l) continue;
+            bool first = true;
+            for (int b2 = 0; b2 < a; b2++) first &= nb[b2] != nb[a];
+            parts += first ? 1u : 0u;
+        }
+    }
+    lmin = __reduce_min_sync(0xffffffffu, lmin);
+    lmax = __reduce_max_sync(0xffffffffu, lmax);
+    slo = __reduce_min_sync(0xffffffffu, slo);
+    shi = __reduce_max_sync(0xffffffffu, shi);
+    bad = __reduce_or_sync(0xffffffffu, (unsigned)bad);
+    mabs = __reduce_max_sync(0xffffffffu, mabs);
+    for (int o = 16; o > 0; o >>= 1) parts += __shfl_down_sync(0xffffffffu, parts, o);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&out->lab_min, lmin);
+        atomicMax(&out->lab_max, lmax);
+        atomicMin(&out->slot_lo, slo);
+        atomicMax(&out->slot_hi, shi);
+        atomicMax(&out->maxabs, mabs);
+        if (bad) atomicOr(&out->bad, 1);
+        if (parts) atomicAdd(&out->particles, parts);
+    }
+}
+
+cudaError_t launch_scan_inputs(const void* I, int dtype, const int* L, int ndim, int D, int H, int W, InputScan* out,
+                               cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long npix = (long long)D * H * W;
+    long long want = (npix + 255) / 256;
+    int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    if (grid < 1) grid = 1;
+    k_scan_inputs<<<grid, 256, 0, s>>>(I, dtype, L, ndim, D, H, W, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s)
 {
     k_stats_finalize<<<64, 128, 0, s>>>(jobs, njobs);

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -56,6 +57,90 @@ struct Arena {
     }
 };
 
+// Device memory of contexts comes from a library-owned stream-ordered pool per device, so
+// that creating and destroying contexts (served jobs) neither pays for a fresh allocation
+// each time nor synchronises the device; the pool keeps freed memory for reuse and is
+// trimmed once no context holds memory.
+struct DevicePool {
+    cudaMemPool_t pool = nullptr;
+    long long live = 0;
+};
+std::mutex g_pool_mu;
+DevicePool g_pools[64];
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        DevicePool& d = g_pools[dev];
+        if (!d.pool) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if ((e = cudaMemPoolCreate(&d.pool, &props)) != cudaSuccess) return e;
+            unsigned long long keep = ~0ull;
+            cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = d.pool;
+        d.live++;
+    }
+    e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        g_pools[dev].live--;
+    }
+    return e;
+}
+
+void dev_free(void* p, cudaStream_t s)
+{
+    if (!p) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    cudaFreeAsync(p, s);
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    DevicePool& d = g_pools[dev];
+    if (--d.live == 0 && d.pool) {
+        cudaStreamSynchronize(s);
+        cudaMemPoolTrimTo(d.pool, 0);
+    }
+}
+
+// Pinned host mirrors of the per-context counters, handed out from slabs that live as long
+// as the process (a pinned allocation per context would cost more than the context).
+std::mutex g_pin_mu;
+std::vector<Counters*> g_pin_free;
+
+Counters* pinned_counters()
+{
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    if (g_pin_free.empty()) {
+        constexpr int kSlab = 64;
+        Counters* slab = nullptr;
+        if (cudaMallocHost(&slab, sizeof(Counters) * kSlab) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = kSlab - 1; i >= 0; i--) g_pin_free.push_back(slab + i);
+    }
+    Counters* c = g_pin_free.back();
+    g_pin_free.pop_back();
+    return c;
+}
+
+void release_counters(Counters* c)
+{
+    if (!c) return;
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    g_pin_free.push_back(c);
+}
+
 }  // namespace
 
 struct Stepper;
@@ -67,6 +152,7 @@ struct seg_ctx {
     Job h{};                      // host copy of the job descriptor
     Job* d_self = nullptr;        // device copy used by init-time kernels
     Counters* d_ctr = nullptr;
+    char* inputs = nullptr;       // image, labels and the input scan record
     char* arena = nullptr;
     size_t arena_bytes = 0;
     char* parena = nullptr;       // particle and candidate buffers (regrown on demand)
@@ -111,15 +197,6 @@ struct seg_batch {
 
 namespace {
 
-bool is_device_ptr(const void* p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 int validate(const seg_params* p)
 {
@@ -264,8 +341,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     const long long npix = h.npix;
     const long long ncell = (long long)h.ncx * h.ncy * h.ncz;
     const size_t esz = h.dtype == SEG_F32 ? 4 : 2;
-    A.add((char**)&h.I, npix * esz);
-    A.add(&h.L, npix);
+    (void)esz;                     // image and labels live in the context's input buffer
     A.add(&h.pmap, npix);
     A.add(&h.cell_start, ncell);
     A.add(&h.cell_count, ncell);
@@ -401,6 +477,19 @@ long long default_pcap(long long npix, int ndim)
     return std::min(worst, want);
 }
 
+// initial capacity once the initial particle count n0 is known: room for the contour to
+// double (more regrows the buffers between iterations)
+long long initial_pcap(long long npix, int ndim, long long n0)
+{
+    long long worst = 2LL * ndim * npix;
+    return std::min(worst, std::max<long long>(65536, 2 * n0 + 65536));
+}
+
+size_t input_bytes(long long npix, int dtype)
+{
+    return align256(npix * (dtype == SEG_F32 ? 4 : 2) + 1) + align256(npix * 4 + 1) + 256;
+}
+
 int grow_particles(seg_ctx* c, long long need)
 {
     long long pcap = std::max<long long>(need + need / 2, c->h.pcap * 2);
@@ -408,13 +497,13 @@ int grow_particles(seg_ctx* c, long long need)
     if (pcap < need) return SEG_ENOMEM;
     size_t bytes = particle_bytes(pcap, c->h.nbr_stride);
     char* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, bytes);
+    CK(cudaStreamSynchronize(c->stream));
+    cudaError_t e = dev_alloc((void**)&mem, bytes, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return SEG_ENOMEM;
     }
-    CK(cudaStreamSynchronize(c->stream));
-    CK(cudaFree(c->parena));
+    dev_free(c->parena, c->stream);
     c->parena = mem;
     c->parena_bytes = bytes;
     assign_particles(c->h, mem, pcap);
@@ -707,7 +796,8 @@ int seg_estimate_bytes(const seg_params* p, int32_t nlabels, size_t* bytes)
     if (nlabels < 1 || !bytes) return SEG_EINVAL;
     Plan P;
     make_geometry(p, nlabels, 1, 254, P);
-    *bytes = P.fixed.bytes + particle_bytes(default_pcap(P.h.npix, P.h.ndim), P.h.nbr_stride);
+    *bytes = input_bytes(P.h.npix, p->dtype) + P.fixed.bytes +
+             particle_bytes(default_pcap(P.h.npix, P.h.ndim), P.h.nbr_stride);
     return SEG_OK;
 }
 
@@ -792,52 +882,45 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     const size_t esz = p->dtype == SEG_F32 ? 4 : 2;
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
-    // host views of the inputs for validation and the exponent range
-    std::vector<int32_t> hl;
-    const int32_t* L0 = labels0;
-    if (is_device_ptr(labels0)) {
-        hl.resize(npix);
-        CK(cudaMemcpy(hl.data(), labels0, npix * 4, cudaMemcpyDeviceToHost));
-        L0 = hl.data();
-    }
-    std::vector<char> hi;
-    const void* I0 = image;
-    const bool img_dev = is_device_ptr(image);
-    if (img_dev && p->dtype == SEG_F32) {
-        hi.resize(npix * esz);
-        CK(cudaMemcpy(hi.data(), image, npix * esz, cudaMemcpyDeviceToHost));
-        I0 = hi.data();
-    }
-    int32_t maxlab = 0;
-    for (long long i = 0; i < npix; i++) {
-        if (L0[i] < 0) return SEG_EINVAL;
-        maxlab = std::max(maxlab, L0[i]);
-    }
-    if (maxlab >= (1 << 24)) return SEG_EINVAL;
-    const int M = maxlab + 1;
+    seg_ctx* c = new seg_ctx();
+    c->params = *p;
+    c->stream = stream;
+    auto fail = [&](int code) {
+        seg_destroy(c);
+        return code;
+    };
+#define CKF(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return fail(cuda_fail(e_, #x)); } while (0)
+    CKF(cudaGetDevice(&c->device));
+    // inputs on the device, then one scan kernel for what the plan needs to know about them
+    const size_t ib = align256(npix * esz + 1), lb = align256(npix * 4 + 1);
+    cudaError_t e = dev_alloc((void**)&c->inputs, input_bytes(npix, p->dtype), stream);
+    if (e != cudaSuccess) { cudaGetLastError(); c->inputs = nullptr; return fail(SEG_ENOMEM); }
+    void* dI = c->inputs;
+    int32_t* dL = (int32_t*)(c->inputs + ib);
+    InputScan* dscan = (InputScan*)(c->inputs + ib + lb);
+    CKF(cudaMemcpyAsync(dI, image, npix * esz, cudaMemcpyDefault, stream));
+    CKF(cudaMemcpyAsync(dL, labels0, npix * 4, cudaMemcpyDefault, stream));
+    InputScan scan{0x7fffffff, -0x7fffffff - 1, 0x7fffffff, -1, 0u, 0, 0ull};
+    CKF(cudaMemcpyAsync(dscan, &scan, sizeof scan, cudaMemcpyHostToDevice, stream));
+    CKF(launch_scan_inputs(dI, p->dtype, dL, p->ndim, (int)p->shape[0], (int)p->shape[1], (int)p->shape[2], dscan,
+                           stream));
+    CKF(cudaMemcpyAsync(&scan, dscan, sizeof scan, cudaMemcpyDeviceToHost, stream));
+    CKF(cudaStreamSynchronize(stream));
+    if (scan.lab_min < 0 || scan.lab_max >= (1 << 24) || scan.bad) return fail(SEG_EINVAL);
+    const int M = scan.lab_max + 1;
     int slot_lo = 1, slot_hi = 1;
     float maxabs = 0.0f;
     if (p->dtype == SEG_F32) {
-        bool any = false;
-        const uint32_t* bits = (const uint32_t*)I0;
-        for (long long i = 0; i < npix; i++) {
-            uint32_t b = bits[i];
-            int eb = (b >> 23) & 0xff;
-            if (eb == 255) return SEG_EINVAL;
-            if ((b & 0x7fffffffu) == 0) continue;
-            int slot = eb ? eb : 1;
-            if (!any) { slot_lo = slot_hi = slot; any = true; }
-            slot_lo = std::min(slot_lo, slot);
-            slot_hi = std::max(slot_hi, slot);
-            maxabs = std::max(maxabs, std::fabs(((const float*)I0)[i]));
-        }
-    } else if (!img_dev) {
-        for (long long i = 0; i < npix; i++) maxabs = std::max(maxabs, (float)((const uint16_t*)I0)[i]);
+        if (scan.slot_hi >= scan.slot_lo) { slot_lo = scan.slot_lo; slot_hi = scan.slot_hi; }
+        std::memcpy(&maxabs, &scan.maxabs, sizeof maxabs);
     } else {
-        maxabs = 65535.0f;
+        maxabs = (float)scan.maxabs;
     }
     if (p->validate) {
-        // every foreground label forms one connected component (union-find)
+        // every foreground label forms one connected component (union-find on the host)
+        std::vector<int32_t> hl(npix);
+        CKF(cudaMemcpy(hl.data(), dL, npix * 4, cudaMemcpyDeviceToHost));
+        const int32_t* L0 = hl.data();
         const long long D = p->shape[0], H = p->shape[1], W = p->shape[2];
         std::vector<int64_t> parent(npix);
         std::iota(parent.begin(), parent.end(), 0);
@@ -860,52 +943,43 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
             if (!L0[i]) continue;
             int64_t r = find(i);
             if (root[L0[i]] < 0) root[L0[i]] = r;
-            else if (root[L0[i]] != r) return SEG_EINVAL;
+            else if (root[L0[i]] != r) return fail(SEG_EINVAL);
         }
     }
 
-    seg_ctx* c = new seg_ctx();
-    c->params = *p;
-    c->stream = stream;
-    CK(cudaGetDevice(&c->device));
     Plan P;
     make_geometry(p, M, slot_lo, slot_hi - slot_lo + 1, P);
     P.h.maxabs = maxabs;
     c->h = P.h;
-    auto fail = [&](int code) {
-        seg_destroy(c);
-        return code;
-    };
-    cudaError_t e = cudaMalloc(&c->arena, P.fixed.bytes);
-    if (e != cudaSuccess) { cudaGetLastError(); return fail(SEG_ENOMEM); }
+    e = dev_alloc((void**)&c->arena, P.fixed.bytes, stream);
+    if (e != cudaSuccess) { cudaGetLastError(); c->arena = nullptr; return fail(SEG_ENOMEM); }
     c->arena_bytes = P.fixed.bytes;
     // the plan recorded addresses of fields of P.h: re-point them into c->h
     for (auto& pr : P.fixed.parts) pr.first = (void**)((char*)&c->h + ((char*)pr.first - (char*)&P.h));
     P.fixed.assign(c->arena);
+    c->h.I = dI;
+    c->h.L = dL;
     c->d_ctr = c->h.ctr;
     setup_tma(c->h);
-    long long pcap = default_pcap(c->h.npix, c->h.ndim);
+    long long pcap = initial_pcap(c->h.npix, c->h.ndim, (long long)scan.particles);
     size_t pb = particle_bytes(pcap, c->h.nbr_stride);
-    e = cudaMalloc(&c->parena, pb);
-    if (e != cudaSuccess) { cudaGetLastError(); return fail(SEG_ENOMEM); }
+    e = dev_alloc((void**)&c->parena, pb, stream);
+    if (e != cudaSuccess) { cudaGetLastError(); c->parena = nullptr; return fail(SEG_ENOMEM); }
     c->parena_bytes = pb;
     assign_particles(c->h, c->parena, pcap);
-    if ((e = cudaMalloc(&c->d_self, sizeof(Job))) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc job"));
-    if ((e = cudaMallocHost(&c->h_ctr, sizeof(Counters))) != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost"));
+    e = dev_alloc((void**)&c->d_self, sizeof(Job), stream);
+    if (e != cudaSuccess) { c->d_self = nullptr; return fail(cuda_fail(e, "job descriptor")); }
+    if (!(c->h_ctr = pinned_counters())) return fail(cuda_fail(cudaErrorMemoryAllocation, "pinned counters"));
 
-    static bool topo_ready = false;
-    if (!topo_ready) {
-        if ((e = topology_tables_init()) != cudaSuccess) return fail(cuda_fail(e, "topology tables"));
-        topo_ready = true;
-    }
+    static std::once_flag topo_once;
+    static cudaError_t topo_err = cudaSuccess;
+    std::call_once(topo_once, [] { topo_err = topology_tables_init(); });
+    if (topo_err != cudaSuccess) return fail(cuda_fail(topo_err, "topology tables"));
     Counters hc{};
     hc.iter_tag = 1;
     hc.mode = p->gradient;
     hc.best_A = -1;
     memset(c->h_ctr, 0, sizeof(Counters));
-#define CKF(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return fail(cuda_fail(e_, #x)); } while (0)
-    CKF(cudaMemcpyAsync((void*)c->h.I, image, npix * esz, cudaMemcpyDefault, stream));
-    CKF(cudaMemcpyAsync(c->h.L, labels0, npix * 4, cudaMemcpyDefault, stream));
     CKF(cudaMemsetAsync(c->h.pmap, 0, npix * 8, stream));
     CKF(cudaMemsetAsync(c->h.tile_word, 0, (size_t)c->h.ntiles * 8, stream));
     CKF(cudaMemsetAsync(c->h.st_n, 0, (size_t)M * 8, stream));
@@ -1100,15 +1174,16 @@ void seg_destroy(seg_ctx* c)
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != c->device) cudaSetDevice(c->device);
-    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);
     if (c->own) {
         stepper_release(*c->own);
         delete c->own;
     }
-    if (c->arena) cudaFree(c->arena);
-    if (c->parena) cudaFree(c->parena);
-    if (c->d_self) cudaFree(c->d_self);
-    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    dev_free(c->arena, c->stream);
+    dev_free(c->parena, c->stream);
+    dev_free(c->d_self, c->stream);
+    dev_free(c->inputs, c->stream);
+    release_counters(c->h_ctr);
     cudaGetLastError();
     if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
     delete c;

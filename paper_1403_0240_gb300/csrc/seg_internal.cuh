@@ -232,6 +232,15 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl* bc, unsigned nblocks)
     return ld_volatile(&bc->err) == 0;
 }
 
+// What seg_init needs to know about its inputs, found on the device in one pass.
+struct InputScan {
+    int lab_min, lab_max;          // smallest and largest label
+    int slot_lo, slot_hi;          // float32: exponent slots of the non-zero values (slot_hi < slot_lo: none)
+    unsigned maxabs;               // float32: bits of the largest |I|; uint16: the largest value
+    int bad;                       // float32: a NaN or an infinity
+    unsigned long long particles;  // particles of the initial labels (pixel, neighbouring label) pairs
+};
+
 // Launch wrappers (one iteration's stages); defined in the kernel translation units.
 cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t s);
 cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t s);
@@ -245,6 +254,8 @@ cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, in
 cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s);
+cudaError_t launch_scan_inputs(const void* I, int dtype, const int* L, int ndim, int D, int H, int W, InputScan* out,
+                               cudaStream_t s);
 cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s);
 cudaError_t topology_tables_init();
 cudaError_t commit_occupancy(int block, int* blocks_per_sm);

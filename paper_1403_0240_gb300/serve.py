@@ -28,6 +28,7 @@ class Request:
     labels0: np.ndarray
     iterations: int
     params: dict = field(default_factory=dict)   # model, connectivity, lam, cutoff, ps_radius, ...
+    nlabels: int | None = None     # largest initial label + 1 (found from labels0 when None)
 
 
 @dataclass
@@ -59,8 +60,10 @@ class SegBackend:
         self.keep_labels = keep_labels
 
     def estimate(self, req: Request) -> int:
+        if req.nlabels is None:
+            req.nlabels = int(req.labels0.max()) + 1
         p = self.seg.make_params(req.image, **_param_kwargs(req))
-        return self.seg.estimate_bytes(p, int(req.labels0.max()) + 1)
+        return self.seg.estimate_bytes(p, req.nlabels)
 
     def create(self, req: Request):
         return self.seg.Context(req.image, req.labels0, stream=self.init_stream, **_param_kwargs(req))
@@ -105,6 +108,9 @@ class Server:
         self.used = 0
         self.results: list[Result] = []
         self.steps = 0
+        # host seconds spent per phase of step(): setting up admitted jobs, waiting for the batch
+        # step to finish, retiring finished jobs (label read-back), adding joined jobs
+        self.timing = {"admit_s": 0.0, "wait_s": 0.0, "retire_s": 0.0, "join_s": 0.0, "member_steps": 0}
 
     def submit(self, req: Request):
         self.queue.append(req)
@@ -138,8 +144,14 @@ class Server:
         k = self._iters_for(members)
         if k:
             self.backend.step_async(k)
+        t0 = self.clock()
         joined = self._admit()                    # host work overlaps the step in flight
+        t1 = self.clock()
         statuses = self.backend.poll() if k else []
+        t2 = self.clock()
+        self.timing["admit_s"] += t1 - t0
+        self.timing["wait_s"] += t2 - t1
+        self.timing["member_steps"] += len(members)
         for jid, st in zip(members, statuses):
             r = self.resident[jid]
             r["done"] += k
@@ -156,9 +168,13 @@ class Server:
                 del self.resident[jid]
                 self.results.append(Result(jid, r["req"].arrival, r["admitted"], now, r["done"], r["particles"],
                                            r["converged"], labels))
+        t3 = self.clock()
         for jid in joined:                        # membership changes only between steps
             self.backend.add(self.resident[jid]["ctx"])
             self.order.append(jid)
+        t4 = self.clock()
+        self.timing["retire_s"] += t3 - t2
+        self.timing["join_s"] += t4 - t3
         if k:
             self.steps += 1
         return k
