@@ -385,6 +385,76 @@ def run_served(args, world, rank, local, pg):
     print(json.dumps(line), flush=True)
 
 
+def _contour_length(L: np.ndarray) -> int:
+    """Adjacent pixel pairs (4/6-neighbours) with different labels: the length prior's P."""
+    return int(sum(np.count_nonzero(np.diff(L, axis=a)) for a in range(L.ndim)))
+
+
+def _pc_energy(I: np.ndarray, L: np.ndarray, lam: float) -> float:
+    """Piecewise-constant energy: squared deviations from the region means plus lambda * P."""
+    I64 = I.astype(np.float64).ravel()
+    lab = L.ravel()
+    n = np.bincount(lab)
+    S = np.bincount(lab, weights=I64)
+    mu = np.divide(S, n, out=np.zeros_like(S), where=n > 0)
+    return float(np.sum((I64 - mu[lab]) ** 2) + lam * _contour_length(L))
+
+
+def run_convergence(args, world, rank, local, pg):
+    """Iterations to convergence of the L2 flow and of the Sobolev flow with the oscillation
+    switch live, on the 128^2 and 1024^2 workloads (one job at a time, status read every
+    iteration)."""
+    import torch
+
+    from paper_1403_0240_gb300 import seg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    out = []
+    for name in ("disks128", "ellipses1024"):
+        make, _ = workloads()[name]
+        w = make(rank)
+        runs = {}
+        for flow in ("l2", "sobolev"):
+            ctx = seg.Context(torch.from_numpy(w.image).to(dev), torch.from_numpy(w.labels0).to(dev), model=w.model,
+                              connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff, ps_radius=w.ps_radius,
+                              gradient=flow, osc_window=args.osc_window if flow == "sobolev" else 0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            switch, accepted, it = None, [], 0
+            while it < args.max_iters:
+                st = ctx.step(1)
+                it += 1
+                accepted.append(st["n_accepted"])
+                if flow == "sobolev" and switch is None and st["mode_used"] == seg.SEG_L2:
+                    switch = st["iteration"]
+                if st["converged"]:
+                    break
+            torch.cuda.synchronize(dev)
+            secs = time.perf_counter() - t0
+            L = ctx.labels().copy()
+            runs[flow] = {"iterations": it, "converged": bool(st["converged"]), "switch_to_l2_at": switch,
+                          "seconds": round(secs, 4), "particle_iterations": int(st["particles_total"]),
+                          "moves": int(sum(accepted)), "contour_length": _contour_length(L),
+                          "energy": _pc_energy(w.image, L, w.lam) if w.model == "pc" else None, "labels": L}
+            ctx.close()
+        agree = float(np.mean(runs["l2"]["labels"] == runs["sobolev"]["labels"]))
+        for r in runs.values():
+            r.pop("labels")
+        out.append({"workload": name, "l2": runs["l2"], "sobolev": runs["sobolev"],
+                    "final_label_agreement": agree})
+    if rank != 0:
+        return
+    tot_p = sum(r[f]["particle_iterations"] for r in out for f in ("l2", "sobolev"))
+    tot_s = sum(r[f]["seconds"] for r in out for f in ("l2", "sobolev"))
+    line = {"metric": METRIC, "value": tot_p / tot_s, "unit": UNIT, "n_gpus": world, "steps": None,
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "convergence", "osc_window": args.osc_window, "max_iters": args.max_iters,
+                       "timing": "wall clock, status read after every iteration", "runs": out}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     """Reference arm: the oracle, timed on this host's cores, on the same workload."""
     if rank != 0:
@@ -571,7 +641,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ellipses1024", choices=sorted(list(workloads().keys()) + ["batch512", "served"]))
+    ap.add_argument("--workload", default="ellipses1024", choices=sorted(list(workloads().keys()) + ["batch512", "served", "convergence"]))
     ap.add_argument("--images", type=int, default=512, help="batch512: images in the batch")
     ap.add_argument("--jobs", type=int, default=2000, help="served: jobs in the arrival stream")
     ap.add_argument("--job-iters", type=int, default=100, help="served: iterations per job")
@@ -579,6 +649,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batch512: default cell edge and tile shape")
+    ap.add_argument("--osc-window", type=int, default=10, help="convergence: oscillation window of the Sobolev flow")
+    ap.add_argument("--max-iters", type=int, default=3000, help="convergence: iteration cap per run")
     ap.add_argument("--iter-log", default="", help="write every warm-up and timed iteration's status here "
                     "(JSON lines), to relate profiler launches to their particle counts")
     args = ap.parse_args()
@@ -593,6 +665,8 @@ def main():
         run_batch(args, world, rank, local, pg)
     elif args.workload == "served":
         run_served(args, world, rank, local, pg)
+    elif args.workload == "convergence":
+        run_convergence(args, world, rank, local, pg)
     else:
         run_ours(args, world, rank, local, pg)
     if pg is not None:
