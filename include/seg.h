@@ -183,7 +183,9 @@ int seg_labels(seg_ctx* c, int32_t* out, size_t n_out);
 int seg_particles(seg_ctx* c, const seg_particle_buffers* out, int64_t cap, int64_t* n);
 
 /* Region statistics for labels 0..max_labels-1 (host arrays, each may be NULL):
- * count, sum of I and sum of I^2 over the region, exact and rounded once. */
+ * count, sum of I and sum of I^2 over the region, exact and rounded once (the sums of
+ * squares are rounded by this call). Call it between steps: it synchronises the context's
+ * stream, not a batch's step in flight. */
 int seg_stats(seg_ctx* c, int64_t* n, double* S, double* Q, int32_t max_labels);
 
 /* Optimiser state for checkpointing; seg_set_state restores it after a seg_init

@@ -539,21 +539,27 @@ __device__ double round_bins(const long long* bins, int nb, int e0)
             cy = t >> 32;
         }
     }
-    int top = -1;
+    int hl = -1;
     for (int i = nl - 1; i >= 0; i--)
-        if (lim[i]) { top = i * 32 + 31 - __clz((unsigned)lim[i]); break; }
-    if (top < 0) return 0.0;
-    auto bit = [&](int b) -> unsigned long long { return ((unsigned long long)lim[b >> 5] >> (b & 31)) & 1ull; };
-    unsigned long long mant = 0;
+        if (lim[i]) { hl = i; break; }
+    if (hl < 0) return 0.0;
+    const int top = hl * 32 + 31 - __clz((unsigned)lim[hl]);
+    // a 96-bit window of limbs hl-2 .. hl holds the 53 mantissa bits and the rounding bit
+    const int base = (hl - 2) * 32;
+    unsigned __int128 w = ((unsigned __int128)(unsigned long long)lim[hl] << 64) |
+                          ((unsigned __int128)(unsigned long long)(hl >= 1 ? lim[hl - 1] : 0) << 32) |
+                          (unsigned __int128)(unsigned long long)(hl >= 2 ? lim[hl - 2] : 0);
+    unsigned long long mant;
     int shift = 0;
     if (top <= 52) {
-        for (int b = top; b >= 0; b--) mant = (mant << 1) | bit(b);
+        mant = (unsigned long long)(w >> (0 - base));            // base = -64 or -32 here: the whole value
     } else {
         shift = top - 52;
-        for (int b = top; b >= shift; b--) mant = (mant << 1) | bit(b);
-        unsigned long long rb = bit(shift - 1);
-        bool sticky = false;
-        for (int b = shift - 2; b >= 0 && !sticky; b--) sticky = bit(b) != 0;
+        const int r = shift - base;                              // window position of the lowest mantissa bit
+        mant = (unsigned long long)(w >> r) & ((1ull << 53) - 1);
+        const unsigned long long rb = (unsigned long long)(w >> (r - 1)) & 1ull;
+        bool sticky = r >= 2 && (w & (((unsigned __int128)1 << (r - 1)) - 1)) != 0;
+        for (int i = hl - 3; i >= 0 && !sticky; i--) sticky = lim[i] != 0;
         if (rb && (sticky || (mant & 1ull))) {
             mant++;
             if (mant == (1ull << 53)) { mant >>= 1; shift++; }
@@ -563,23 +569,24 @@ __device__ double round_bins(const long long* bins, int nb, int e0)
     return neg ? -v : v;
 }
 
-__device__ void finalize_label(const Job& J, int m)
+// The per-iteration finish needs the means (S); the sums of squares (Q) are only reported,
+// so they are rounded when statistics are read.
+__device__ void finalize_label(const Job& J, int m, bool with_Q)
 {
     long long n = J.st_n[m];
-    double S, Q;
+    double S;
     if (J.dtype == SEG_U16) {
         S = __ll2double_rn(J.st_S[m]);
-        Q = __ll2double_rn(J.st_Q[m]);
+        if (with_Q) J.Q64[m] = __ll2double_rn(J.st_Q[m]);
     } else {
         S = round_bins(J.st_S + (long long)m * J.nS, J.nS, J.slot_lo - 150);
-        Q = round_bins(J.st_Q + (long long)m * J.nQ, J.nQ, 2 * (J.slot_lo - 150));
+        if (with_Q) J.Q64[m] = round_bins(J.st_Q + (long long)m * J.nQ, J.nQ, 2 * (J.slot_lo - 150));
     }
     const double dn = (double)n;
     const double mu = n > 0 ? __ddiv_rn(S, dn) : 0.0;
     const double wp = __ddiv_rn(dn, __dadd_rn(dn, 1.0));
     const double wm = n > 1 ? __ddiv_rn(dn, __dsub_rn(dn, 1.0)) : 0.0;
     J.S64[m] = S;
-    J.Q64[m] = Q;
     J.mu64[m] = mu;
     J.wp64[m] = wp;
     J.wm64[m] = wm;
@@ -636,7 +643,7 @@ __global__ void k_stats_finalize(const Job* jobs, int njobs)
 {
     for (int j = 0; j < njobs; j++) {
         const Job& J = jobs[j];
-        for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < J.M; m += gridDim.x * blockDim.x) finalize_label(J, m);
+        for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < J.M; m += gridDim.x * blockDim.x) finalize_label(J, m, true);
     }
 }
 
@@ -1006,7 +1013,7 @@ __global__ void __launch_bounds__(256) k_finish(const Job* jobs, int njobs, Batc
     for (unsigned k = threadIdx.x * gridDim.x + blockIdx.x; k < total; k += stride) {
         const int j = job_of(s_pref, njobs, k);
         const Job& J = jobs[j];
-        if (ok && !job_idle(J.ctr)) finalize_label(J, (int)(k - s_pref[j]));
+        if (ok && !job_idle(J.ctr)) finalize_label(J, (int)(k - s_pref[j]), false);
     }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < njobs; j += stride)
         commit_job_status(jobs[j], ok, ld_volatile(&bc->rounds_done), err);

@@ -1105,6 +1105,8 @@ int seg_stats(seg_ctx* c, int64_t* n, double* S, double* Q, int32_t max_labels)
     if (rc) return rc;
     int k = std::min(max_labels, c->h.M);
     if (k > 0) {
+        // the sums of squares are rounded from the exact sums here (the iteration needs only S)
+        if (Q) CK(launch_stats_finalize(c->d_self, 1, c->stream));
         if (n) CK(cudaMemcpyAsync(n, c->h.st_n, k * 8, cudaMemcpyDeviceToHost, c->stream));
         if (S) CK(cudaMemcpyAsync(S, c->h.S64, k * 8, cudaMemcpyDeviceToHost, c->stream));
         if (Q) CK(cudaMemcpyAsync(Q, c->h.Q64, k * 8, cudaMemcpyDeviceToHost, c->stream));
