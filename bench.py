@@ -503,9 +503,21 @@ def run_ours(args, world, rank, local, pg):
     lab_d = torch.from_numpy(w.labels0).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    settings = {}
+    if args.tile:
+        settings["tile"] = tuple(int(v) for v in args.tile.split("x"))
+    if args.cell_edge:
+        settings["cell_edge"] = args.cell_edge
+    tune_table = None
+    if args.autotune:
+        best, tune_table = seg.autotune(img_d, lab_d, iters=20, stream=stream, model=w.model,
+                                        connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
+                                        ps_radius=w.ps_radius)
+        settings = {"cell_edge": best["cell_edge"], "tile": best["tile"]}
+
     def new_ctx():
         c = seg.Context(img_d, lab_d, model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
-                        ps_radius=w.ps_radius, osc_window=0, stream=stream)
+                        ps_radius=w.ps_radius, osc_window=0, stream=stream, **settings)
         c.profile(True)
         return c
 
@@ -582,7 +594,7 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     c2 = seg.Context(img_h, lab_h, model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
-                     ps_radius=w.ps_radius, osc_window=0, stream=stream)
+                     ps_radius=w.ps_radius, osc_window=0, stream=stream, **settings)
     for _ in range(k_e2e):
         s2 = c2.step(1)
     c2.labels(out=out_h)
@@ -623,6 +635,8 @@ def run_ours(args, world, rank, local, pg):
             "config": {"workload": name, "description": desc, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed iterations (256 MiB write)",
                        "iterations_per_job": iters_per_job, "mean_particles": mean_parts,
+                       "settings": {k: list(v) if isinstance(v, tuple) else v for k, v in settings.items()} or "default",
+                       "autotune_ms_per_iter": tune_table,
                        "mean_accepted": accepted / args.steps, "mean_fp64_recomputes": fixups / args.steps,
                        "mean_selection_rounds": rounds / args.steps,
                        "precision": "float32 gradients with certified bounds, FP64 recompute of uncertified "
@@ -649,6 +663,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batch512: default cell edge and tile shape")
+    ap.add_argument("--tile", default="", help="tile shape in pixels, e.g. 30x64 (2D: y x x) or 8x8x32")
+    ap.add_argument("--cell-edge", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true", help="time seg_autotune's candidates first and use the fastest")
     ap.add_argument("--osc-window", type=int, default=10, help="convergence: oscillation window of the Sobolev flow")
     ap.add_argument("--max-iters", type=int, default=3000, help="convergence: iteration cap per run")
     ap.add_argument("--iter-log", default="", help="write every warm-up and timed iteration's status here "

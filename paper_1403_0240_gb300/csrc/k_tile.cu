@@ -235,7 +235,7 @@ __device__ __forceinline__ StageBox stage_box(const Job& J, const TileBox& b, in
 // Extraction: one block per tile of cells, tiles taken in ticket order so that the
 // decoupled look-back only waits on tiles that have already started.
 template <int NDIM>
-__global__ void __launch_bounds__(kBlock) k_extract(Group g)
+__global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned s_ticket, s_base;
@@ -272,51 +272,49 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     int* sL = (int*)(smem + off_b);
     off_b = align128(off_b + (size_t)nbox * 4);
     unsigned* s_cstart = (unsigned*)(smem + off_b);
-    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ __align__(8) unsigned long long s_bar, s_bar_img;
+    __shared__ int s_img_fail;
     const bool outside_box = sb.ox < 0 || sb.oy < 0 || sb.oz < 0 || sb.ox + bx > J.W || sb.oy + by > J.H ||
                              sb.oz + bz > J.D;
+    // the image copy (2D piecewise smooth) completes on its own mbarrier: counting and the
+    // look-back need only the labels, so the image arrives while they run
+    const bool img_tma = J.use_tma && stage_img;
+    if (tid == 0) s_img_fail = 0;
     if (J.use_tma) {
-        // one tensor copy per array, completed on one mbarrier; -1 for labels outside the image
+        // one tensor copy per array; -1 for labels outside the image
         if (tid == 0) {
             mbar_init(&s_bar, 1);
-            const unsigned bytes = (unsigned)nbox * 4u + (stage_img ? (unsigned)(nbox * esz) : 0u);
-            mbar_expect_tx(&s_bar, bytes);
+            mbar_expect_tx(&s_bar, (unsigned)nbox * 4u);
+            if (img_tma) {
+                mbar_init(&s_bar_img, 1);
+                mbar_expect_tx(&s_bar_img, (unsigned)(nbox * esz));
+            }
             if (NDIM == 3) {
                 tma_load_3d(sL, J.tmap_L, sb.ox, sb.oy, sb.oz, &s_bar);
             } else {
                 tma_load_2d(sL, J.tmap_L, sb.ox, sb.oy, &s_bar);
-                if (stage_img) tma_load_2d(sRaw, J.tmap_I, sb.ox, sb.oy, &s_bar);
+                if (img_tma) tma_load_2d(sRaw, J.tmap_I, sb.ox, sb.oy, &s_bar_img);
             }
         }
         __syncthreads();
         const bool arrived = mbar_wait_bounded(&s_bar);
         if (__syncthreads_or(!arrived)) {   // the whole block leaves together
             if (tid == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
-            mbar_wait_bounded(&s_bar);       // a second bounded wait for the copy in flight
+            mbar_wait_bounded(&s_bar);       // a second bounded wait for the copies in flight
+            if (img_tma) mbar_wait_bounded(&s_bar_img);
             return;
         }
-        if (outside_box || stage_img) {
+        if (outside_box) {
             for (int row = tid >> 5; row < by * bz; row += blockDim.x >> 5)
             for (int lx = tid & 31; lx < bx; lx += 32) {
                 const int ly = row % by, lz = row / by;
-                const int i = row * bx + lx;
                 const int x = sb.ox + lx, y = sb.oy + ly, z = sb.oz + lz;
-                const bool in = x >= 0 && x < J.W && y >= 0 && y < J.H && z >= 0 && z < J.D;
-                if (!in) sL[i] = -1;
-                if (stage_img && use_int) {
-                    long long q = 0;
-                    if (in) q = J.dtype == SEG_F32 ? fixed_of_f32(sI[i], J.slot_lo)
-                                                   : (long long)((const unsigned short*)sRaw)[i];
-                    if (q32) {
-                        if (J.dtype == SEG_F32) sQ32[i] = (int)q;   // same element, same size: in place
-                    } else {
-                        sQ[i] = q;
-                    }
-                }
+                if (!(x >= 0 && x < J.W && y >= 0 && y < J.H && z >= 0 && z < J.D)) sL[row * bx + lx] = -1;
             }
         }
         __syncthreads();
     }
+
     // row-by-row staging when the rows cannot be copied by tensor copies: labels (and, for the
     // 2D piecewise-smooth model, the image) with halo; -1 outside; one warp per row of the box
     const int nrows = J.use_tma ? 0 : by * bz;
@@ -441,13 +439,17 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         return dP;
     };
 
-    unsigned cnt = 0;
+    // count; a thread whose chunk has at most 32 pixels remembers which of them hold particles
+    unsigned cnt = 0, busy = 0;
+    const bool use_mask = q1 - q0 <= 32;
     {
         Walk w = walk_start(q0);
         for (int q = q0; q < q1; q++, walk_next(w)) {
             int x, y, z, labs[NN];
             if (!walk_pixel(w, x, y, z)) continue;
-            cnt += particles_at(x, y, z, labs);
+            const int n = particles_at(x, y, z, labs);
+            cnt += n;
+            if (n) busy |= 1u << ((q - q0) & 31);
         }
     }
     unsigned total;
@@ -462,34 +464,55 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
         unsigned excl = 0;
         if (lane == 0) atomicExch(J.tile_word + k, ep | ((k == 0 ? 2ull : 1ull) << 32) | total);
         if (k > 0) {
+            // each lane reads 8 consecutive predecessors (lane 0 the nearest), 256 per round
+            // trip. The ready run nearest to the tile is consumed up to the first inclusive
+            // prefix; a predecessor that has published nothing yet stops the run, and the next
+            // round starts there (progress without waiting for the whole window).
+            constexpr int kPer = 8;
             long long win_end = (long long)k - 1;
             unsigned spins = 0;
             while (true) {
-                const long long i = win_end - lane;
-                unsigned st = 2, val = 0;          // before tile 0: an inclusive prefix of 0
-                if (i >= 0) {
-                    unsigned long long w = ld_volatile(J.tile_word + i);
-                    st = (w & emask) == ep ? (unsigned)((w >> 32) & 3u) : 0u;
-                    val = (unsigned)w;
+                unsigned st[kPer], val[kPer];
+#pragma unroll
+                for (int j = 0; j < kPer; j++) {
+                    const long long i = win_end - (long long)lane * kPer - j;
+                    st[j] = 2;                      // before tile 0: an inclusive prefix of 0
+                    val[j] = 0;
+                    if (i >= 0) {
+                        const unsigned long long w = ld_volatile(J.tile_word + i);
+                        st[j] = (w & emask) == ep ? (unsigned)((w >> 32) & 3u) : 0u;
+                        val[j] = (unsigned)w;
+                    }
                 }
-                const unsigned m2 = __ballot_sync(0xffffffffu, st == 2);
-                const unsigned m0 = __ballot_sync(0xffffffffu, st == 0);
-                const int first2 = m2 ? __ffs(m2) - 1 : 31;
-                const unsigned need = first2 == 31 ? 0xffffffffu : ((2u << first2) - 1u);
-                if (m0 & need) {
+                int f2 = kPer, f0 = kPer;           // first inclusive, first unpublished in the lane
+#pragma unroll
+                for (int j = kPer - 1; j >= 0; j--) {
+                    if (st[j] == 2) f2 = j;
+                    if (st[j] == 0) f0 = j;
+                }
+                const unsigned m2 = __ballot_sync(0xffffffffu, f2 < kPer);
+                const unsigned m0 = __ballot_sync(0xffffffffu, f0 < kPer);
+                const int l2 = m2 ? __ffs(m2) - 1 : 32, l0 = m0 ? __ffs(m0) - 1 : 32;
+                const int A = l2 < 32 ? l2 * kPer + __shfl_sync(0xffffffffu, f2, l2 & 31) : 32 * kPer;
+                const int B = l0 < 32 ? l0 * kPer + __shfl_sync(0xffffffffu, f0, l0 & 31) : 32 * kPer;
+                const bool done = A < B;            // an inclusive prefix before any gap
+                const int limit = done ? A + 1 : B; // entries [0, limit) are summed this round
+                unsigned part = 0;
+#pragma unroll
+                for (int j = 0; j < kPer; j++)
+                    if (lane * kPer + j < limit) part += val[j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                excl += part;
+                if (done) break;
+                win_end -= limit;
+                if (limit == 0) {                   // the nearest remaining predecessor is not ready
                     if (++spins > kSpinLimit) {
                         if (lane == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
                         break;
                     }
                     __nanosleep(32);
-                    continue;
                 }
-                unsigned add = lane <= first2 ? val : 0u;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
-                excl += add;
-                if (m2) break;
-                win_end -= 32;
             }
             __threadfence();
             if (lane == 0) atomicExch(J.tile_word + k, ep | (2ull << 32) | (excl + total));
@@ -503,8 +526,36 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
                 if ((long long)excl + total > J.pcap) atomicMax(&ctr->need, excl + total);
             }
         }
+    } else if (img_tma) {
+        // meanwhile the other warps turn the staged image (once its copy has landed) into exact
+        // fixed-point values for the piecewise-smooth ball sums
+        const bool landed = mbar_wait_bounded(&s_bar_img);
+        if (!landed) s_img_fail = 1;
+        if (landed && use_int) {
+            const int nw = (blockDim.x >> 5) - 1;
+            for (int row = (tid >> 5) - 1; row < by * bz; row += nw)
+            for (int lx = tid & 31; lx < bx; lx += 32) {
+                const int ly = row % by, lz = row / by;
+                const int i = row * bx + lx;
+                const int x = sb.ox + lx, y = sb.oy + ly, z = sb.oz + lz;
+                const bool in = x >= 0 && x < J.W && y >= 0 && y < J.H && z >= 0 && z < J.D;
+                long long q = 0;
+                if (in) q = J.dtype == SEG_F32 ? fixed_of_f32(sI[i], J.slot_lo)
+                                               : (long long)((const unsigned short*)sRaw)[i];
+                if (q32) {
+                    if (J.dtype == SEG_F32) sQ32[i] = (int)q;   // same element, same size: in place
+                } else {
+                    sQ[i] = q;
+                }
+            }
+        }
     }
     __syncthreads();
+    if (s_img_fail) {                            // the image copy did not land in time
+        if (tid == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
+        mbar_wait_bounded(&s_bar_img);
+        return;
+    }
     const unsigned base = s_base;
     const bool fits = (long long)base + total <= J.pcap;
 
@@ -514,6 +565,7 @@ __global__ void __launch_bounds__(kBlock) k_extract(Group g)
     for (int q = q0; q < q1; q++, walk_next(wk)) {
         int x, y, z, labs[NN];
         if (wk.rx == 0 && wk.ry == 0 && wk.rz == 0) s_cstart[(wk.lz * b.ccy + wk.ly) * b.ccx + wk.lx] = o - base;
+        if (use_mask && !((busy >> ((q - q0) & 31)) & 1u)) continue;
         if (!walk_pixel(wk, x, y, z)) continue;
         int n = particles_at(x, y, z, labs);
         if (n == 0) continue;
