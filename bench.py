@@ -415,10 +415,10 @@ def run_convergence(args, world, rank, local, pg):
         make, _ = workloads()[name]
         w = make(rank)
         runs = {}
-        for flow in ("l2", "sobolev"):
+        for flow in ("l2", "sobolev", "sobolev_global"):
             ctx = seg.Context(torch.from_numpy(w.image).to(dev), torch.from_numpy(w.labels0).to(dev), model=w.model,
                               connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff, ps_radius=w.ps_radius,
-                              gradient=flow, osc_window=args.osc_window if flow == "sobolev" else 0)
+                              gradient=flow, osc_window=args.osc_window if flow != "l2" else 0)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             switch, accepted, it = None, [], 0
@@ -426,7 +426,7 @@ def run_convergence(args, world, rank, local, pg):
                 st = ctx.step(1)
                 it += 1
                 accepted.append(st["n_accepted"])
-                if flow == "sobolev" and switch is None and st["mode_used"] == seg.SEG_L2:
+                if flow != "l2" and switch is None and st["mode_used"] == seg.SEG_L2:
                     switch = st["iteration"]
                 if st["converged"]:
                     break
@@ -439,14 +439,16 @@ def run_convergence(args, world, rank, local, pg):
                           "energy": _pc_energy(w.image, L, w.lam) if w.model == "pc" else None, "labels": L}
             ctx.close()
         agree = float(np.mean(runs["l2"]["labels"] == runs["sobolev"]["labels"]))
+        agree_g = float(np.mean(runs["sobolev_global"]["labels"] == runs["sobolev"]["labels"]))
         for r in runs.values():
             r.pop("labels")
         out.append({"workload": name, "l2": runs["l2"], "sobolev": runs["sobolev"],
-                    "final_label_agreement": agree})
+                    "sobolev_global": runs["sobolev_global"], "final_label_agreement": agree,
+                    "global_vs_local_agreement": agree_g})
     if rank != 0:
         return
-    tot_p = sum(r[f]["particle_iterations"] for r in out for f in ("l2", "sobolev"))
-    tot_s = sum(r[f]["seconds"] for r in out for f in ("l2", "sobolev"))
+    tot_p = sum(r[f]["particle_iterations"] for r in out for f in ("l2", "sobolev", "sobolev_global"))
+    tot_s = sum(r[f]["seconds"] for r in out for f in ("l2", "sobolev", "sobolev_global"))
     line = {"metric": METRIC, "value": tot_p / tot_s, "unit": UNIT, "n_gpus": world, "steps": None,
             "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",

@@ -52,7 +52,14 @@ extern "C" {
 
 enum { SEG_F32 = 0, SEG_U16 = 1 };                 /* image element type */
 enum { SEG_PC = 0, SEG_PS = 1 };                   /* piecewise constant / piecewise smooth */
-enum { SEG_SOBOLEV = 0, SEG_L2 = 1 };              /* gradient type at start */
+/* gradient type at start. SEG_SOBOLEV_GLOBAL: Eq. 6 with the length scale of the inner
+ * product set to the contour length, E = |Gamma| (Length scale section), |Gamma| read as the
+ * number of connectivity-adjacent pixel pairs with different labels (the length prior's
+ * count) and updated every iteration; the support |d| < E/2 then covers (nearly) every
+ * particle pair, so the interaction is all-pairs, O(N^2) per iteration (the paper leaves this
+ * variant to future work as too costly on its CPU). The cutoff parameter only sizes the cell
+ * list in this mode. */
+enum { SEG_SOBOLEV = 0, SEG_L2 = 1, SEG_SOBOLEV_GLOBAL = 2 };
 enum { SEG_STATS_EXACT = 0 };                      /* region sums exact, rounded once to FP64 */
 
 typedef struct seg_ctx seg_ctx;
@@ -67,7 +74,7 @@ typedef struct {
     double  lambda;        /* length weight (Eq. 10), >= 0 */
     double  cutoff;        /* interaction cutoff E/2 in pixels, > 0; E = 2 * cutoff, eps = 1/24 */
     double  ps_radius;     /* local-mean radius R for SEG_PS, >= 1 */
-    int32_t gradient;      /* SEG_SOBOLEV | SEG_L2 */
+    int32_t gradient;      /* SEG_SOBOLEV | SEG_L2 | SEG_SOBOLEV_GLOBAL */
     int32_t osc_window;    /* switch to L2 once the accepted-move count has not reached a new
                               minimum for this many iterations; 0 = never switch */
     int32_t stats_mode;    /* SEG_STATS_EXACT */
@@ -87,7 +94,7 @@ typedef struct {
     int64_t n_accepted;    /* moves executed */
     int64_t n_osc;         /* particles whose two Eq. 6 terms are non-zero with equal sign (FP32) */
     int64_t n_fixup;       /* particles whose gradient was recomputed in FP64 */
-    int32_t mode_used;     /* SEG_SOBOLEV | SEG_L2 */
+    int32_t mode_used;     /* SEG_SOBOLEV | SEG_L2 | SEG_SOBOLEV_GLOBAL */
     int32_t converged;     /* an L2 iteration accepted no move; later iterations do nothing */
     int32_t mis_rounds;    /* rounds of the parallel ranked selection */
     int32_t error;         /* 0, or a SEG_E* code raised on the device; SEG_ENOMEM: the
@@ -100,7 +107,7 @@ typedef struct {
     int64_t t;             /* iterations done */
     int64_t best_A;        /* smallest accepted-move count so far (-1 before the first iteration) */
     int64_t t_best;        /* iteration at which best_A was first reached */
-    int32_t mode;          /* SEG_SOBOLEV | SEG_L2 */
+    int32_t mode;          /* SEG_SOBOLEV | SEG_L2 | SEG_SOBOLEV_GLOBAL */
     int32_t converged;
 } seg_state;
 

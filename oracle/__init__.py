@@ -24,7 +24,7 @@ _lib = None
 
 F32, U16 = 0, 1
 PC, PS = 0, 1
-SOBOLEV, L2 = 0, 1
+SOBOLEV, L2, SOBOLEV_GLOBAL = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -98,6 +98,8 @@ def lib():
             L.orc_admissible.argtypes = [P(Params), vp, C.c_uint32, C.c_int32, C.c_int32]
             L.orc_select.restype = C.c_int64
             L.orc_select.argtypes = [P(Params), vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_perimeter.restype = C.c_int64
+            L.orc_perimeter.argtypes = [P(Params), vp]
             L.orc_state_init.restype = None
             L.orc_state_init.argtypes = [P(Params), P(State)]
             L.orc_iterate.restype = C.c_int
@@ -127,7 +129,8 @@ def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", 
     p.lam = float(lam)
     p.cutoff = float(cutoff)
     p.ps_radius = float(ps_radius)
-    p.gradient = gradient if isinstance(gradient, int) else {"sobolev": SOBOLEV, "l2": L2}[gradient]
+    p.gradient = gradient if isinstance(gradient, int) else {"sobolev": SOBOLEV, "l2": L2,
+                                                             "sobolev_global": SOBOLEV_GLOBAL}[gradient]
     p.osc_window = int(osc_window)
     p.nlabels = int(nlabels if nlabels is not None else int(labels.max()) + 1)
     return p
@@ -182,6 +185,12 @@ def energy(p: Params, I: np.ndarray, L: np.ndarray, idx, l, c, n=None, S=None, w
 def delta_perimeter(p: Params, L: np.ndarray, x: int, l: int, c: int) -> int:
     L = np.ascontiguousarray(L, dtype=np.int32)
     return lib().orc_delta_perimeter(C.byref(p), _ptr(L), x, l, c)
+
+
+def perimeter(p: Params, L: np.ndarray) -> int:
+    """|Gamma|: connectivity-adjacent pixel pairs with different labels."""
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    return int(lib().orc_perimeter(C.byref(p), _ptr(L)))
 
 
 def sobolev(p: Params, idx, l, c, dE, all_pairs: bool = False):

@@ -287,6 +287,22 @@ int64_t orc_delta_perimeter(const orc_params* p, const int32_t* L, uint32_t xi, 
     return d;
 }
 
+/* Length of the contour |Gamma| in the discrete reading used by the length prior: the
+ * number of connectivity-adjacent pixel pairs with different labels (each pair once). */
+int64_t orc_perimeter(const orc_params* p, const int32_t* L)
+{
+    int64_t P = 0;
+    for (int64_t z = 0; z < p->D; z++)
+        for (int64_t y = 0; y < p->H; y++)
+            for (int64_t x = 0; x < p->W; x++) {
+                int32_t m = L[(z * p->H + y) * p->W + x];
+                if (x + 1 < p->W && L[(z * p->H + y) * p->W + x + 1] != m) P++;
+                if (y + 1 < p->H && L[(z * p->H + y + 1) * p->W + x] != m) P++;
+                if (p->ndim == 3 && z + 1 < p->D && L[((z + 1) * p->H + y) * p->W + x] != m) P++;
+            }
+    return P;
+}
+
 /* Energy difference of moving particle (x: l -> c), data term + lambda * length. */
 void orc_energy(const orc_params* p, const void* I, const int32_t* L,
                 const int64_t* n, const double* S, int64_t N,
@@ -596,7 +612,7 @@ int64_t orc_select(const orc_params* p, const int32_t* L, int64_t N,
 /* ------------------------------------------------------------------ */
 void orc_state_init(const orc_params* p, orc_state* st)
 {
-    st->mode = p->gradient == 0 ? 0 : 1;
+    st->mode = p->gradient;          /* 0 = Sobolev, 1 = L2, 2 = Sobolev with E = |Gamma| */
     st->converged = 0;
     st->t = 0;
     st->best_A = -1;
@@ -628,8 +644,16 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
     double* gs = (double*)malloc(sizeof(double) * NN);
     orc_extract(p, L, idx, l, c, N);
     orc_energy(p, I, L, n, S, N, idx, l, c, dE, dEs);
-    if (st->mode == 0) {
-        orc_sobolev(p, N, idx, l, c, dE, 0, g, A, B, NULL, NULL, dEs, gs);
+    if (st->mode == 0 || st->mode == 2) {
+        if (st->mode == 0) {
+            orc_sobolev(p, N, idx, l, c, dE, 0, g, A, B, NULL, NULL, dEs, gs);
+        } else {
+            /* length scale of the inner product set to the contour length (Length scale
+             * section): E = |Gamma|, support |d| < E/2, every particle pair considered */
+            orc_params q = *p;
+            q.cutoff = 0.5 * (double)orc_perimeter(p, L);
+            orc_sobolev(&q, N, idx, l, c, dE, 1, g, A, B, NULL, NULL, dEs, gs);
+        }
         for (int64_t k = 0; k < N; k++)
             if (A[k] != 0.0 && B[k] != 0.0 && ((A[k] > 0.0) == (B[k] > 0.0))) status->n_osc++;
     } else {
@@ -657,7 +681,7 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
     }
     /* oscillation fallback and convergence */
     if (st->best_A < 0 || na < st->best_A) { st->best_A = na; st->t_best = st->t; }
-    if (st->mode == 0 && p->osc_window > 0 && st->t - st->t_best >= p->osc_window) st->mode = 1;
+    if (st->mode != 1 && p->osc_window > 0 && st->t - st->t_best >= p->osc_window) st->mode = 1;
     if (status->mode_used == 1 && na == 0) st->converged = 1;
     status->converged = st->converged;
     st->t++;

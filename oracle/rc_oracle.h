@@ -27,8 +27,12 @@
  *                         centre's link in the cubical complex (3D).
  *   orc_select          - ranked greedy selection; pinned by an independent
  *                         local-minimum-rounds evaluation and permutation tests.
+ *   orc_perimeter       - |Gamma| as the length prior counts it; pinned by square and
+ *                         cube perimeters and a numpy recount.
  *   orc_iterate         - composition of the above; pinned by the partition and
- *                         connectivity invariants after every iteration.
+ *                         connectivity invariants after every iteration. With E = |Gamma|
+ *                         (gradient 2) the Sobolev step is the all-pairs Eq. 6 at E = the
+ *                         perimeter; pinned by a numpy evaluation of Eq. 6 over all pairs.
  */
 #ifndef RC_ORACLE_H
 #define RC_ORACLE_H
@@ -47,7 +51,7 @@ typedef struct {
     double lambda;       /* length weight (Eq. 10) */
     double cutoff;       /* interaction cutoff E/2 in pixels */
     double ps_radius;    /* local-mean radius R (piecewise smooth) */
-    int32_t gradient;    /* 0 = Sobolev (Eq. 6), 1 = L2 */
+    int32_t gradient;    /* 0 = Sobolev (Eq. 6), 1 = L2, 2 = Sobolev with E = |Gamma| (all pairs) */
     int32_t osc_window;  /* iterations without a new minimum of accepted moves before switching to L2; 0 = never */
     int32_t nlabels;     /* M: labels are 0..M-1 */
     int32_t pad_;
@@ -87,6 +91,9 @@ void    orc_energy(const orc_params* p, const void* I, const int32_t* L,
                    const uint32_t* idx, const int32_t* l, const int32_t* c, double* dE, double* scale);
 
 int64_t orc_delta_perimeter(const orc_params* p, const int32_t* L, uint32_t x, int32_t l, int32_t c);
+
+/* |Gamma|: connectivity-adjacent pixel pairs with different labels */
+int64_t orc_perimeter(const orc_params* p, const int32_t* L);
 
 /* scale (may be NULL): sum_Q K s_q / |Q| + sum_Q' K s_q / |Q'| + |A| + |B| of each g, with s_q
  * the scale of dE_q (dE_scale, or |dE_q| when dE_scale is NULL) */

@@ -340,6 +340,70 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int n
             double gval;
             if (mode == SEG_L2) {
                 gval = lane == 0 ? energy64(J, gi, lp, cp, p) : 0.0;
+            } else if (mode == SEG_SOBOLEV_GLOBAL) {
+                // E = |Gamma|: every particle with d^2 < g_lim, in ascending key order (the pixels
+                // of the support's bounding box in row-major order, particles of a pixel in order)
+                int x, y, z;
+                coords(J, gi, x, y, z);
+                const long long lim = J.ctr->g_lim;
+                long long r = 0;
+                while ((r + 1) * (r + 1) < lim) r++;
+                const long long x0 = max(0LL, x - r), x1 = min((long long)J.W - 1, x + r);
+                const long long y0 = max(0LL, y - r), y1 = min((long long)J.H - 1, y + r);
+                const long long z0 = J.ndim == 3 ? max(0LL, z - r) : 0, z1 = J.ndim == 3 ? min((long long)J.D - 1, z + r) : 0;
+                const long long bw = x1 - x0 + 1, bh = y1 - y0 + 1, nbox = bw * bh * (z1 - z0 + 1);
+                double As = 0.0, Bs = 0.0;
+                long long nA = 0, nB = 0;
+                for (long long base0 = 0; base0 < nbox; base0 += 32) {
+                    const long long i = base0 + lane;
+                    unsigned yi = 0, q0 = 0;
+                    long long d2 = 0;
+                    bool ok = false;
+                    if (i < nbox) {
+                        const long long xx = x0 + i % bw, yy = y0 + (i / bw) % bh, zz = z0 + i / (bw * bh);
+                        d2 = (xx - x) * (xx - x) + (yy - y) * (yy - y) + (zz - z) * (zz - z);
+                        if (d2 < lim) {
+                            yi = (unsigned)((zz * J.H + yy) * J.W + xx);
+                            const unsigned long long e = J.pmap[yi];
+                            ok = (unsigned)(e >> 32) == tag;
+                            q0 = (unsigned)e;
+                        }
+                    }
+                    int nt = 0;
+                    if (ok)
+                        for (unsigned q = q0; q < np && J.p_idx[q] == yi; q++)
+                            nt += (J.p_l[q] == lp || J.p_c[q] == lp) ? 1 : 0;
+                    if (!__any_sync(0xffffffffu, nt > 0)) continue;
+                    int incl = nt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                    int pos = incl - nt;
+                    if (ok && nt) {
+                        const double K = J.gK64[d2];
+                        for (unsigned q = q0; q < np && J.p_idx[q] == yi; q++) {
+                            const int lq = J.p_l[q], cq = J.p_c[q];
+                            if (lq != lp && cq != lp) continue;
+                            s_t[w][pos] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
+                            s_a[w][pos] = lq == lp ? 1 : 0;
+                            pos++;
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        for (int u = 0; u < tot; u++) {
+                            if (s_a[w][u]) { As = __dadd_rn(As, s_t[w][u]); nA++; }
+                            else { Bs = __dadd_rn(Bs, s_t[w][u]); nB++; }
+                        }
+                    }
+                    __syncwarp();
+                }
+                const double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
+                const double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
+                gval = __dsub_rn(A, B);
             } else {
                 int x, y, z;
                 coords(J, gi, x, y, z);
@@ -668,7 +732,7 @@ __global__ void k_scan_inputs(const void* I, int dtype, const int* L, int ndim, 
     const long long npix = (long long)D * H * W;
     int lmin = 0x7fffffff, lmax = -0x7fffffff - 1, slo = 0x7fffffff, shi = -1, bad = 0;
     unsigned mabs = 0;
-    unsigned long long parts = 0;
+    unsigned long long parts = 0, pairs = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
         const int l = L[i];
         lmin = min(lmin, l);
@@ -695,6 +759,8 @@ __global__ void k_scan_inputs(const void* I, int dtype, const int* L, int ndim, 
         if (y + 1 < H) nb[n++] = L[i + W];
         if (ndim == 3 && z > 0) nb[n++] = L[i - (long long)W * H];
         if (ndim == 3 && z + 1 < D) nb[n++] = L[i + (long long)W * H];
+        pairs += (x + 1 < W && L[i + 1] != l) + (y + 1 < H && L[i + W] != l) +
+                 (ndim == 3 && z + 1 < D && L[i + (long long)W * H] != l);
         for (int a = 0; a < n; a++) {
             if (nb[a] == l) continue;
             bool first = true;
@@ -709,6 +775,7 @@ __global__ void k_scan_inputs(const void* I, int dtype, const int* L, int ndim, 
     bad = __reduce_or_sync(0xffffffffu, (unsigned)bad);
     mabs = __reduce_max_sync(0xffffffffu, mabs);
     for (int o = 16; o > 0; o >>= 1) parts += __shfl_down_sync(0xffffffffu, parts, o);
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_down_sync(0xffffffffu, pairs, o);
     if ((threadIdx.x & 31) == 0) {
         atomicMin(&out->lab_min, lmin);
         atomicMax(&out->lab_max, lmax);
@@ -717,6 +784,7 @@ __global__ void k_scan_inputs(const void* I, int dtype, const int* L, int ndim, 
         atomicMax(&out->maxabs, mabs);
         if (bad) atomicOr(&out->bad, 1);
         if (parts) atomicAdd(&out->particles, parts);
+        if (pairs) atomicAdd(&out->pairs, pairs);
     }
 }
 
@@ -830,6 +898,21 @@ __device__ __forceinline__ void commit_move_one(const Job& J, unsigned s)
     const int p = J.c_best[s];
     const unsigned gi = J.c_pix[s];
     const int l = J.p_l[p], c = J.p_c[p];
+    if (J.global_E) {
+        // |Gamma| changes by the move's change of unlike neighbour pairs; accepted moves are
+        // never adjacent, so their changes add up exactly
+        int x, y, z;
+        pix_coords(J, gi, x, y, z);
+        long long dP = 0;
+        const long long HW = (long long)J.W * J.H;
+        if (x > 0) { const int m = J.L[gi - 1]; dP += (m != c) - (m != l); }
+        if (x + 1 < J.W) { const int m = J.L[gi + 1]; dP += (m != c) - (m != l); }
+        if (y > 0) { const int m = J.L[gi - J.W]; dP += (m != c) - (m != l); }
+        if (y + 1 < J.H) { const int m = J.L[gi + J.W]; dP += (m != c) - (m != l); }
+        if (J.ndim == 3 && z > 0) { const int m = J.L[gi - HW]; dP += (m != c) - (m != l); }
+        if (J.ndim == 3 && z + 1 < J.D) { const int m = J.L[gi + HW]; dP += (m != c) - (m != l); }
+        if (dP) atomicAdd((unsigned long long*)&J.ctr->perim, (unsigned long long)dP);
+    }
     J.L[gi] = c;
     J.p_flags[p] |= kFlagAcc;
     stats_move(J, gi, l, -1);
@@ -864,13 +947,13 @@ __device__ void commit_job_status(const Job& J, bool ok, unsigned rounds, int er
     const long long A = c->n_accepted;
     const int used = c->mode;
     if (c->best_A < 0 || A < c->best_A) { c->best_A = A; c->t_best = c->t; }
-    if (c->mode == SEG_SOBOLEV && J.osc_window > 0 && c->t - c->t_best >= J.osc_window) c->mode = SEG_L2;
+    if (c->mode != SEG_L2 && J.osc_window > 0 && c->t - c->t_best >= J.osc_window) c->mode = SEG_L2;
     if (used == SEG_L2 && A == 0) c->converged = 1;
     c->last.iteration = c->t;
     c->last.n_particles = c->n_particles;
     c->last.n_candidates = c->n_cand;
     c->last.n_accepted = A;
-    c->last.n_osc = used == SEG_SOBOLEV ? c->n_osc : 0;
+    c->last.n_osc = used != SEG_L2 ? c->n_osc : 0;
     c->last.n_fixup = c->n_flag;
     c->last.mode_used = used;
     c->last.converged = c->converged;

@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
     const unsigned skip = ld_volatile(&ctr->skip) | ld_volatile(&ctr->need);
     const unsigned pstart = J.tile_start[k], pcount = J.tile_count[k];
     const int mode = ld_volatile(&ctr->mode);
-    if (skip || pcount == 0) return;
+    if (skip || pcount == 0 || mode == SEG_SOBOLEV_GLOBAL) return;   // E = |Gamma|: k_sobolev_global
     if (mode == SEG_L2) {
         for (unsigned i = tid; i < pcount; i += blockDim.x) {
             J.p_g[pstart + i] = J.p_dE[pstart + i];

@@ -183,6 +183,7 @@ struct Stepper {
     cudaGraphExec_t exec = nullptr;
     bool use_graph = true;
     bool dirty = true;
+    bool any_global = false;       // a member uses E = |Gamma| (adds its two launches to the step)
     bool profile = false;
     cudaEvent_t ev[10]{};
     cudaStream_t work = nullptr;   // library stream: graphs are captured and launched here
@@ -213,7 +214,14 @@ int validate(const seg_params* p)
     if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return SEG_EINVAL;
     if (!(p->cutoff > 0.0) || p->cutoff > 32.0) return SEG_EINVAL;
     if (p->model == SEG_PS && (!(p->ps_radius >= 1.0) || p->ps_radius > 64.0)) return SEG_EINVAL;
-    if (p->gradient != SEG_SOBOLEV && p->gradient != SEG_L2) return SEG_EINVAL;
+    if (p->gradient != SEG_SOBOLEV && p->gradient != SEG_L2 && p->gradient != SEG_SOBOLEV_GLOBAL) return SEG_EINVAL;
+    if (p->gradient == SEG_SOBOLEV_GLOBAL) {
+        // the E = |Gamma| kernel table spans every squared distance in the image
+        const long double d2 = (long double)(p->shape[0] - 1) * (p->shape[0] - 1) +
+                               (long double)(p->shape[1] - 1) * (p->shape[1] - 1) +
+                               (long double)(p->shape[2] - 1) * (p->shape[2] - 1);
+        if (d2 >= (long double)(1 << 24)) return SEG_EINVAL;
+    }
     if (p->osc_window < 0) return SEG_EINVAL;
     if (p->stats_mode != SEG_STATS_EXACT) return SEG_EINVAL;
     int need = (int)std::ceil(p->cutoff);
@@ -293,6 +301,10 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     h.E = 2.0 * p->cutoff;
     h.r2max = largest_d2_below(p->cutoff);
     h.M = M;
+    h.global_E = p->gradient == SEG_SOBOLEV_GLOBAL ? 1 : 0;
+    h.gd2max = h.global_E ? (int)((long long)(h.D - 1) * (h.D - 1) + (long long)(h.H - 1) * (h.H - 1) +
+                                  (long long)(h.W - 1) * (h.W - 1))
+                          : 0;
     h.osc_window = p->osc_window;
     h.nbr_stride = h.ndim == 3 ? 26 : 8;
     h.slot_lo = slot_lo;
@@ -363,6 +375,8 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     A.add((double**)&h.klut64, P.klut64.size());
     A.add((int4**)&h.ps_off, std::max<size_t>(1, P.ps_off.size()));
     A.add((int4**)&h.nb_off, P.nb_off.size());
+    A.add(&h.gK32, (size_t)h.gd2max + 1);
+    A.add(&h.gK64, (size_t)h.gd2max + 1);
     A.add(&h.ctr, 1);
 }
 
@@ -545,7 +559,11 @@ int stepper_build(Stepper& s)
     std::vector<Job> jobs(n);
     std::vector<int> ids;
     std::vector<unsigned> prefix;
-    for (int i = 0; i < n; i++) jobs[i] = s.members[i]->h;
+    s.any_global = false;
+    for (int i = 0; i < n; i++) {
+        jobs[i] = s.members[i]->h;
+        s.any_global = s.any_global || jobs[i].global_E;
+    }
     int id_off[2] = {0, 0}, pf_off[2] = {0, 0};
     for (int gidx = 0; gidx < 2; gidx++) {
         const int nd = gidx == 0 ? 2 : 3;
@@ -607,8 +625,12 @@ cudaError_t stepper_enqueue(Stepper& s)
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_extract(s.grp[gidx], gidx + 2, s.smem_x[gidx], s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 1)) != cudaSuccess) return e;
+    if (s.any_global && (e = launch_global_lut(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_sobolev(s.grp[gidx], gidx + 2, s.smem_s[gidx], s.work)) != cudaSuccess) return e;
+    for (int gidx = 0; gidx < 2; gidx++)
+        if (s.any_global && s.grp[gidx].njobs && (e = launch_sobolev_global(s.grp[gidx], gidx + 2, s.work)) != cudaSuccess)
+            return e;
     if ((e = stage_mark(s, 2)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_flag(s.grp[gidx], s.work)) != cudaSuccess) return e;
@@ -979,6 +1001,7 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     hc.iter_tag = 1;
     hc.mode = p->gradient;
     hc.best_A = -1;
+    hc.perim = (long long)scan.pairs;
     memset(c->h_ctr, 0, sizeof(Counters));
     CKF(cudaMemsetAsync(c->h.pmap, 0, npix * 8, stream));
     CKF(cudaMemsetAsync(c->h.tile_word, 0, (size_t)c->h.ntiles * 8, stream));

@@ -56,6 +56,8 @@ struct Counters {
     long long best_A;       // smallest accepted count so far, -1 before the first iteration
     long long t_best;
     long long cum_particles; // particles summed over executed iterations
+    long long perim;        // |Gamma|: adjacent pixel pairs with different labels (current labels)
+    long long g_lim;        // E = |Gamma| mode: interaction partners have d^2 < g_lim
     seg_status last;        // status of the last executed iteration
 };
 
@@ -93,6 +95,10 @@ struct alignas(64) Job {
     const int4* nb_off;
     const float* klut;        // K(sqrt(d2)) rounded to float, d2 = 0..r2max
     const double* klut64;     // K(sqrt(d2)) in FP64, Eq. 5 evaluated in the order written
+    int global_E;             // Eq. 6 with E = |Gamma| (all pairs) while in Sobolev mode
+    int gd2max;               // ... largest squared distance within the image
+    float* gK32;              // ... K(sqrt(d2)) for E = |Gamma| of the iteration, float
+    double* gK64;             // ... and FP64 (Eq. 5 in the order written); 0 outside the support
     int M;                    // number of labels
     int osc_window;           // L2 fallback window (0 = never)
     int nbr_stride;           // neighbour-list slots per candidate: 8 (2D) | 26 (3D)
@@ -239,11 +245,14 @@ struct InputScan {
     unsigned maxabs;               // float32: bits of the largest |I|; uint16: the largest value
     int bad;                       // float32: a NaN or an infinity
     unsigned long long particles;  // particles of the initial labels (pixel, neighbouring label) pairs
+    unsigned long long pairs;      // adjacent pixel pairs with different labels (|Gamma|)
 };
 
 // Launch wrappers (one iteration's stages); defined in the kernel translation units.
 cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t s);
 cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t s);
+cudaError_t launch_global_lut(const Job* jobs, int njobs, int sms, cudaStream_t s);
+cudaError_t launch_sobolev_global(const Group& g, int ndim, cudaStream_t s);
 cudaError_t launch_flag(const Group& g, cudaStream_t s);
 cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s);
 cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cudaStream_t s);

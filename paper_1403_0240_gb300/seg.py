@@ -17,7 +17,7 @@ from . import build as _build
 SEG_OK, SEG_EINVAL, SEG_ENOMEM, SEG_ECUDA, SEG_ETIMEOUT, SEG_ESTATE = 0, -1, -2, -3, -4, -5
 SEG_F32, SEG_U16 = 0, 1
 SEG_PC, SEG_PS = 0, 1
-SEG_SOBOLEV, SEG_L2 = 0, 1
+SEG_SOBOLEV, SEG_L2, SEG_SOBOLEV_GLOBAL = 0, 1, 2
 SEG_STATS_EXACT = 0
 
 
@@ -171,7 +171,8 @@ def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_ra
     p.lam = float(lam)
     p.cutoff = float(cutoff)
     p.ps_radius = float(ps_radius)
-    p.gradient = gradient if isinstance(gradient, int) else {"sobolev": SEG_SOBOLEV, "l2": SEG_L2}[gradient]
+    p.gradient = gradient if isinstance(gradient, int) else {"sobolev": SEG_SOBOLEV, "l2": SEG_L2,
+                                                                  "sobolev_global": SEG_SOBOLEV_GLOBAL}[gradient]
     p.osc_window = int(osc_window)
     p.stats_mode = SEG_STATS_EXACT
     p.validate = int(bool(validate))
