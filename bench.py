@@ -360,12 +360,17 @@ def run_served(args, world, rank, local, pg):
         parts_of[key] = st["particles_total"]
         c.close()
     done_t, lat, parts_plain, busy = 0.0, [], 0, 0.0
+    by_kind = {}
     for r, key in zip(reqs, keys):
         start = max(r.arrival, done_t)
         done_t = start + svc[key]
         busy += svc[key]
         lat.append(done_t - r.arrival)
         parts_plain += parts_of[key]
+        k = by_kind.setdefault(key[0], [0, 0.0, 0])
+        k[0] += 1
+        k[1] += svc[key]
+        k[2] += parts_of[key]
     if rank != 0:
         return
     lat = np.array(lat)
@@ -380,6 +385,8 @@ def run_served(args, world, rank, local, pg):
                        "served_makespan_s": t_served, "server_steps": srv.steps,
                        "server_host_s": {k: round(v, 3) if isinstance(v, float) else v for k, v in srv.timing.items()},
                        "plain_value": parts_plain / busy, "plain_makespan_s": done_t,
+                       "plain_by_kind": {k: {"jobs": v[0], "busy_s": round(v[1], 3), "particle_iterations": v[2]}
+                                         for k, v in by_kind.items()},
                        "plain_p50_s": float(np.percentile(lat, 50)), "plain_p99_s": float(np.percentile(lat, 99)),
                        "served_over_plain": (parts / t_served) / (parts_plain / busy)}}
     print(json.dumps(line), flush=True)
