@@ -148,7 +148,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_setup():
+def dist_setup(backend: str | None = None):
+    """One process per GPU (torchrun): NCCL on GPUs, gloo otherwise. Replicas only: the ranks
+    exchange nothing but the barrier and the two scalar reductions of the timing."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -156,8 +158,11 @@ def dist_setup():
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group(backend="nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
         pg = dist
     return world, rank, local, pg
 
@@ -167,22 +172,28 @@ def barrier(pg):
         pg.barrier()
 
 
-def allmax(pg, x: float) -> float:
-    if pg is None:
-        return x
+def _reduce(pg, x: float, op) -> float:
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=op)
     return float(t.item())
+
+
+def allmax(pg, x: float) -> float:
+    return x if pg is None else _reduce(pg, x, pg.ReduceOp.MAX)
 
 
 def allsum(pg, x: float) -> float:
-    if pg is None:
-        return x
-    import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    pg.all_reduce(t, op=pg.ReduceOp.SUM)
-    return float(t.item())
+    return x if pg is None else _reduce(pg, x, pg.ReduceOp.SUM)
+
+
+def aggregate(pg, units: float, seconds: float) -> tuple[float, float, float]:
+    """Whole-job throughput of replicas: the units of all ranks over the slowest rank's time.
+    Returns (value, total units, max seconds)."""
+    t_max = allmax(pg, seconds)
+    total = allsum(pg, units)
+    return total / t_max, total, t_max
 
 
 def oracle_sample(w, seconds: float = 12.0, max_iters: int = 400):
@@ -588,9 +599,7 @@ def run_ours(args, world, rank, local, pg):
         raise RuntimeError(f"device error {st_last['error']}")
     dev_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
     particles = float(sum(step_parts))
-    t_max = allmax(pg, dev_ms / 1000.0)
-    total_particles = allsum(pg, particles)
-    value = total_particles / t_max
+    value, total_particles, t_max = aggregate(pg, particles, dev_ms / 1000.0)
     ctx.close()
 
     # end to end through the public API: host (pinned) inputs, a status read every step,
