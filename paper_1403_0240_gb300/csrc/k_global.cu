@@ -37,6 +37,7 @@ constexpr float kMargin = 1e-12f;               // the FP64 reference's own roun
 // every squared distance that occurs in the image.
 __global__ void k_global_lut(const Job* jobs, int njobs)
 {
+    pdl_enter();
     for (int j = 0; j < njobs; j++) {
         const Job& J = jobs[j];
         if (!J.global_E) continue;
@@ -60,6 +61,7 @@ __global__ void k_global_lut(const Job* jobs, int njobs)
 template <int NDIM>
 __global__ void __launch_bounds__(kBlock) k_sobolev_global(Group g)
 {
+    pdl_enter();
     __shared__ int s_x[kChunk], s_y[kChunk], s_z[kChunk], s_l[kChunk], s_c[kChunk];
     __shared__ float s_dE[kChunk], s_eE[kChunk];
     __shared__ unsigned s_osc;
@@ -134,16 +136,14 @@ __global__ void __launch_bounds__(kBlock) k_sobolev_global(Group g)
 
 cudaError_t launch_global_lut(const Job* jobs, int njobs, int sms, cudaStream_t s)
 {
-    k_global_lut<<<sms * 2, 256, 0, s>>>(jobs, njobs);
-    return cudaGetLastError();
+    return launch_stage(k_global_lut, sms * 2, 256, 0, s, jobs, njobs);
 }
 
 cudaError_t launch_sobolev_global(const Group& g, int ndim, cudaStream_t s)
 {
     if (g.total_tiles == 0) return cudaSuccess;
-    if (ndim == 2) k_sobolev_global<2><<<g.total_tiles, kBlock, 0, s>>>(g);
-    else k_sobolev_global<3><<<g.total_tiles, kBlock, 0, s>>>(g);
-    return cudaGetLastError();
+    if (ndim == 2) return launch_stage(k_sobolev_global<2>, g.total_tiles, kBlock, 0, s, g);
+    return launch_stage(k_sobolev_global<3>, g.total_tiles, kBlock, 0, s, g);
 }
 
 }  // namespace segk

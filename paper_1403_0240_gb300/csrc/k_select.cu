@@ -140,6 +140,7 @@ __device__ __forceinline__ void coords(const Job& J, unsigned gi, int& x, int& y
 // at Chebyshev distance <= 1 (same pixel included), is not certified by the bounds.
 __global__ void __launch_bounds__(256) k_flag(Group g)
 {
+    pdl_enter();
     const unsigned t = blockIdx.x;
     const int gj = group_job_of_tile(g, t);
     const Job& J = g.jobs[g.job_ids[gj]];
@@ -186,8 +187,7 @@ __global__ void __launch_bounds__(256) k_flag(Group g)
 cudaError_t launch_flag(const Group& g, cudaStream_t s)
 {
     if (g.total_tiles == 0) return cudaSuccess;
-    k_flag<<<g.total_tiles, 256, 0, s>>>(g);
-    return cudaGetLastError();
+    return launch_stage(k_flag, g.total_tiles, 256, 0, s, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,6 +318,7 @@ constexpr int kFixTerms = 32 * 6;
 
 __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int njobs)
 {
+    pdl_enter();
     __shared__ double s_t[kFixWarps][kFixTerms];
     __shared__ unsigned char s_a[kFixWarps][kFixTerms];
     __shared__ unsigned s_pref[kMaxBatchJobs + 1];
@@ -465,8 +466,7 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int n
 cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s)
 {
     if (njobs <= 0) return cudaSuccess;
-    k_fixup<<<sms * 2, kFixWarps * 32, 0, s>>>(jobs, njobs);
-    return cudaGetLastError();
+    return launch_stage(k_fixup, sms * 2, kFixWarps * 32, 0, s, jobs, njobs);
 }
 
 __global__ void k_gather_counters(const Job* jobs, int njobs, Counters* out)
@@ -487,6 +487,7 @@ cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cu
 // key is negative and its move passes the topology tests.
 __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
 {
+    pdl_enter();
     const unsigned t = blockIdx.x;
     if (t == 0 && threadIdx.x == 0) {
         bc->bar_count = 0;
@@ -524,8 +525,7 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
 cudaError_t launch_select(const Group& g, BatchCtl* bc, cudaStream_t s)
 {
     if (g.total_tiles == 0) return cudaSuccess;
-    k_select<<<g.total_tiles, 256, 0, s>>>(g, bc);
-    return cudaGetLastError();
+    return launch_stage(k_select, g.total_tiles, 256, 0, s, g, bc);
 }
 
 // ---------------------------------------------------------------------------
@@ -973,6 +973,7 @@ __device__ void commit_job_status(const Job& J, bool ok, unsigned rounds, int er
 // A, as its own grid, over the flattened candidates of all jobs
 __global__ void __launch_bounds__(256) k_lists(const Job* jobs, int njobs)
 {
+    pdl_enter();
     __shared__ unsigned s_pref[kMaxBatchJobs + 1];
     __shared__ unsigned s_tmp[32];
     const unsigned total = block_job_prefix(jobs, njobs, kCountCand, s_pref, s_tmp);
@@ -986,6 +987,7 @@ __global__ void __launch_bounds__(256) k_lists(const Job* jobs, int njobs)
 // block barriers; otherwise the whole co-resident grid runs them with bounded grid barriers.
 __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, BatchCtl* bc)
 {
+    pdl_enter();
     __shared__ unsigned s_red[32];
     __shared__ unsigned s_flag;
     __shared__ unsigned s_pref[kMaxBatchJobs + 1];
@@ -1060,6 +1062,7 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
 // C, as its own grid: accepted moves; accepted counts aggregated per warp and job
 __global__ void __launch_bounds__(256) k_moves(const Job* jobs, int njobs, const BatchCtl* bc)
 {
+    pdl_enter();
     __shared__ unsigned s_pref[kMaxBatchJobs + 1];
     __shared__ unsigned s_tmp[32];
     if (ld_volatile(&bc->err)) return;
@@ -1086,6 +1089,7 @@ __global__ void __launch_bounds__(256) k_moves(const Job* jobs, int njobs, const
 // D, as its own grid: exact region tables of every label of every job, then per-job status
 __global__ void __launch_bounds__(256) k_finish(const Job* jobs, int njobs, BatchCtl* bc)
 {
+    pdl_enter();
     __shared__ unsigned s_pref[kMaxBatchJobs + 1];
     __shared__ unsigned s_tmp[32];
     const int err = ld_volatile(&bc->err);
@@ -1116,8 +1120,7 @@ cudaError_t commit_occupancy(int block, int* blocks_per_sm)
 
 cudaError_t launch_lists(const Job* jobs, int njobs, int sms, cudaStream_t s)
 {
-    k_lists<<<sms * 4, 256, 0, s>>>(jobs, njobs);
-    return cudaGetLastError();
+    return launch_stage(k_lists, sms * 4, 256, 0, s, jobs, njobs);
 }
 
 // the rounds kernel is cooperative: every block co-resident
@@ -1138,14 +1141,12 @@ cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, in
 
 cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s)
 {
-    k_moves<<<sms * 4, 256, 0, s>>>(jobs, njobs, bc);
-    return cudaGetLastError();
+    return launch_stage(k_moves, sms * 4, 256, 0, s, jobs, njobs, (const BatchCtl*)bc);
 }
 
 cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s)
 {
-    k_finish<<<sms, 256, 0, s>>>(jobs, njobs, bc);
-    return cudaGetLastError();
+    return launch_stage(k_finish, sms, 256, 0, s, jobs, njobs, bc);
 }
 
 }  // namespace segk

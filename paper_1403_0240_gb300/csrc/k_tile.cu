@@ -237,6 +237,7 @@ __device__ __forceinline__ StageBox stage_box(const Job& J, const TileBox& b, in
 template <int NDIM>
 __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
 {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned s_ticket, s_base;
     __shared__ unsigned s_warp[32];
@@ -750,9 +751,8 @@ size_t extract_smem_bytes(const Job& J)
 cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t st)
 {
     if (g.total_tiles == 0) return cudaSuccess;
-    if (ndim == 2) k_extract<2><<<g.total_tiles, kBlock, smem, st>>>(g);
-    else k_extract<3><<<g.total_tiles, kBlock, smem, st>>>(g);
-    return cudaGetLastError();
+    if (ndim == 2) return launch_stage(k_extract<2>, g.total_tiles, kBlock, smem, st, g);
+    return launch_stage(k_extract<3>, g.total_tiles, kBlock, smem, st, g);
 }
 
 // --------------------------------------------------------------------------
@@ -868,6 +868,7 @@ __device__ __forceinline__ void sobolev_sums(const Job& J, int lp, int x, int y,
 template <int NDIM>
 __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned s_warp[32];
     __shared__ float s_klut[256];
@@ -1112,9 +1113,8 @@ size_t sobolev_smem_bytes(const Job& J)
 cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t st)
 {
     if (g.total_tiles == 0) return cudaSuccess;
-    if (ndim == 2) k_sobolev<2><<<g.total_tiles, kBlock, smem, st>>>(g);
-    else k_sobolev<3><<<g.total_tiles, kBlock, smem, st>>>(g);
-    return cudaGetLastError();
+    if (ndim == 2) return launch_stage(k_sobolev<2>, g.total_tiles, kBlock, smem, st, g);
+    return launch_stage(k_sobolev<3>, g.total_tiles, kBlock, smem, st, g);
 }
 
 // Dynamic shared memory limits, set outside any stream capture. The limits only grow (per

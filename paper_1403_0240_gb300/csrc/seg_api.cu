@@ -18,6 +18,10 @@
 
 using namespace segk;
 
+namespace segk {
+thread_local bool g_pdl = false;
+}
+
 namespace {
 
 thread_local std::string g_last_cuda;
@@ -617,7 +621,22 @@ cudaError_t stage_mark(Stepper& s, int k)
     return cudaEventRecord(s.ev[k], s.work);
 }
 
+cudaError_t stepper_enqueue_stages(Stepper& s);
+
+// One iteration's stages; their launches overlap each other's ramp and drain (programmatic
+// dependent launch) unless per-stage events are recorded between them. That pays for
+// latency-bound iterations (tile grids of a few waves); with many waves of tiles the early
+// scheduled blocks only wait, so large grids keep plain stream order.
 cudaError_t stepper_enqueue(Stepper& s)
+{
+    const long long tiles = (long long)s.grp[0].total_tiles + s.grp[1].total_tiles;
+    g_pdl = !s.profile && tiles <= 8LL * s.sms;
+    const cudaError_t e = stepper_enqueue_stages(s);
+    g_pdl = false;
+    return e;
+}
+
+cudaError_t stepper_enqueue_stages(Stepper& s)
 {
     cudaError_t e;
     const int n = (int)s.members.size();

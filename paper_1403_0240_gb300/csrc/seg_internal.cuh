@@ -248,6 +248,38 @@ struct InputScan {
     unsigned long long pairs;      // adjacent pixel pairs with different labels (|Gamma|)
 };
 
+// Programmatic dependent launch: a stage kernel launched with programmatic stream
+// serialization may be scheduled while its predecessor finishes. Every stage kernel starts
+// with pdl_enter(): it waits until the predecessor grid has completed and its memory is
+// visible (a no-op when the kernel was launched without the attribute), then lets its own
+// successor be scheduled.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches of the iteration's stages use programmatic serialization while this is set
+// (the stepper sets it while enqueueing an iteration without per-stage events).
+extern thread_local bool g_pdl;
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_stage(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // Launch wrappers (one iteration's stages); defined in the kernel translation units.
 cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t s);
 cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t s);
