@@ -290,19 +290,18 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 mbar_init(&s_bar_img, 1);
                 mbar_expect_tx(&s_bar_img, (unsigned)(nbox * esz));
             }
-            if (NDIM == 3) {
-                tma_load_3d(sL, J.tmap_L, sb.ox, sb.oy, sb.oz, &s_bar);
-            } else {
-                tma_load_2d(sL, J.tmap_L, sb.ox, sb.oy, &s_bar);
-                if (img_tma) tma_load_2d(sRaw, J.tmap_I, sb.ox, sb.oy, &s_bar_img);
-            }
+            if (NDIM == 3) tma_load_3d(sL, J.tmap_L, sb.ox, sb.oy, sb.oz, &s_bar);
+            else tma_load_2d(sL, J.tmap_L, sb.ox, sb.oy, &s_bar);
         }
         __syncthreads();
         const bool arrived = mbar_wait_bounded(&s_bar);
+        // the image only once the labels are in: every tile's labels (which gate the counts
+        // and so every tile's look-back) do not share the DRAM burst with the images
+        if (tid == 0 && img_tma && arrived) tma_load_2d(sRaw, J.tmap_I, sb.ox, sb.oy, &s_bar_img);
         if (__syncthreads_or(!arrived)) {   // the whole block leaves together
             if (tid == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
             mbar_wait_bounded(&s_bar);       // a second bounded wait for the copies in flight
-            if (img_tma) mbar_wait_bounded(&s_bar_img);
+            if (tid == 0 && img_tma && arrived) mbar_wait_bounded(&s_bar_img);
             return;
         }
         if (outside_box) {

@@ -53,3 +53,41 @@ def test_ellipses_1024_one_iteration_after_20():
 def test_ellipsoids_256_one_iteration_after_5():
     st, t = _one_iteration_parity(synth.ellipsoids(), 5)
     assert st["n_particles"] > 1000000
+
+
+def test_batch512_sampled_jobs_match_oracle():
+    """The 512-image batch (sides 64-512, 1-8 disks) stepped together with the batch-tuned
+    settings, as the batch benchmark runs it; eight jobs spread over the batch are replayed by
+    the oracle and must end with the same labels and statistics."""
+    from paper_1403_0240_gb300 import tune
+    jobs = synth.batch_disks(512, seed0=1000, iterations=8)
+    best, _ = tune.autotune_batch([(w.image, w.labels0, dict(model=w.model, lam=w.lam, cutoff=w.cutoff))
+                                   for w in jobs], iters=2, sample=64)
+    settings = lambda w: {"cell_edge": best["cell_multiple"] * int(np.ceil(w.cutoff)), "tile": best["tile"]}
+    ctxs = [seg.Context(w.image, w.labels0, model=w.model, lam=w.lam, cutoff=w.cutoff, **settings(w)) for w in jobs]
+    batch = seg.Batch()
+    for c in ctxs:
+        batch.add(c)
+    sts = batch.step(8)
+    assert all(s["error"] == 0 for s in sts)
+    for i in np.linspace(0, 511, 8).astype(int):
+        w = jobs[i]
+        p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius)
+        run = oracle.Run(p, w.image, w.labels0)
+        for _ in range(8):
+            run.step()
+        assert np.array_equal(ctxs[i].labels(), run.L), i
+        n, S, Q = ctxs[i].stats()
+        n_ref, S_ref, Q_ref = oracle.stats(p, w.image, run.L)
+        assert np.array_equal(n, n_ref) and np.array_equal(S, S_ref) and np.array_equal(Q, Q_ref), i
+    batch.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_large_2d_image_two_iterations():
+    """A 4096 x 4096 image (16.8 M pixels, about 9000 tiles, a sparse contour): one iteration on
+    the GPU, then one whole iteration compared with the oracle."""
+    w = synth.disks(4096, 4096, seed=41, n_disks=40)
+    st, t = _one_iteration_parity(w, 1)
+    assert st["n_particles"] > 1000
