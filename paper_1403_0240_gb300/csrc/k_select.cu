@@ -18,6 +18,36 @@ struct TopoTables {
     int npos[2];
 };
 __constant__ TopoTables c_topo;
+// Simple-point decisions tabulated for every neighbourhood mask: 2^8 (2D) and 2^26 (3D) bits,
+// computed once per process on the device from simple_mask() below.
+__constant__ const unsigned* c_simple[2];
+
+__device__ __forceinline__ bool simple_mask(unsigned X, int d);
+
+__global__ void k_simple_table(unsigned* out, int d, unsigned nwords)
+{
+    const unsigned w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwords) return;
+    unsigned bits = 0;
+    for (unsigned b = 0; b < 32; b++)
+        if (simple_mask(w * 32u + b, d)) bits |= 1u << b;
+    out[w] = bits;
+}
+
+cudaError_t simple_tables_init()
+{
+    unsigned* t2 = nullptr;
+    unsigned* t3 = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&t2, 8 * sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&t3, (1u << 21) * sizeof(unsigned))) != cudaSuccess) return e;
+    k_simple_table<<<1, 32>>>(t2, 0, 8);
+    k_simple_table<<<(1u << 21) / 256, 256>>>(t3, 1, 1u << 21);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    const unsigned* ptrs[2] = {t2, t3};
+    return cudaMemcpyToSymbol(c_simple, ptrs, sizeof ptrs);
+}
 
 cudaError_t topology_tables_init()
 {
@@ -48,7 +78,9 @@ cudaError_t topology_tables_init()
             }
         }
     }
-    return cudaMemcpyToSymbol(c_topo, &t, sizeof t);
+    cudaError_t e = cudaMemcpyToSymbol(c_topo, &t, sizeof t);
+    if (e != cudaSuccess) return e;
+    return simple_tables_init();
 }
 
 // number of components of set S (adjacency adj) that meet `touch` (all if touch == 0); stops at 2
@@ -81,40 +113,44 @@ __device__ __forceinline__ bool simple_mask(unsigned X, int d)
     return components(~X & c_topo.all[d], aB, 0u) == 1;
 }
 
-__device__ __forceinline__ unsigned label_mask(const Job& J, int x, int y, int z, int lab)
+__device__ __forceinline__ bool simple_table(unsigned X, int d)
 {
-    unsigned m = 0;
-    int k = 0;
-    const int rz = J.ndim == 3 ? 1 : 0;
-    for (int dz = -rz; dz <= rz; dz++)
-        for (int dy = -1; dy <= 1; dy++)
-            for (int dx = -1; dx <= 1; dx++) {
-                if (!dz && !dy && !dx) continue;
-                int xx = x + dx, yy = y + dy, zz = z + dz;
-                if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D &&
-                    J.L[((long long)zz * J.H + yy) * J.W + xx] == lab)
-                    m |= 1u << k;
-                k++;
-            }
-    return m;
+    return (__ldg(c_simple[d] + (X >> 5)) >> (X & 31u)) & 1u;
 }
 
 // Topological control: removal from l (foreground) and addition to c (foreground)
-// must both be simple, so regions neither split, vanish, merge nor change holes.
+// must both be simple, so regions neither split, vanish, merge nor change holes. The
+// neighbourhood is read once for both labels.
 __device__ __forceinline__ bool admissible(const Job& J, unsigned gi, int l, int c)
 {
     int x, y, z;
     pix_coords(J, gi, x, y, z);
-    int d = J.ndim == 3 ? 1 : 0;
-    if (l != 0 && !simple_mask(label_mask(J, x, y, z, l), d)) return false;
-    if (c != 0 && !simple_mask(label_mask(J, x, y, z, c), d)) return false;
+    const int d = J.ndim == 3 ? 1 : 0;
+    const int rz = d;
+    unsigned ml = 0, mc = 0;
+    int k = 0;
+    for (int dz = -rz; dz <= rz; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                if (!dz && !dy && !dx) continue;
+                const int xx = x + dx, yy = y + dy, zz = z + dz;
+                if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D) {
+                    const int v = J.L[((long long)zz * J.H + yy) * J.W + xx];
+                    ml |= (unsigned)(v == l) << k;
+                    mc |= (unsigned)(v == c) << k;
+                }
+                k++;
+            }
+    if (l != 0 && !simple_table(ml, d)) return false;
+    if (c != 0 && !simple_table(mc, d)) return false;
     return true;
 }
 
+// the tabulated decision, as the selection uses it
 __global__ void k_debug_simple(const unsigned* masks, int ndim, int n, unsigned char* out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = simple_mask(masks[i], ndim == 3 ? 1 : 0) ? 1 : 0;
+    if (i < n) out[i] = simple_table(masks[i], ndim == 3 ? 1 : 0) ? 1 : 0;
 }
 
 cudaError_t launch_debug_simple(const unsigned* masks, int ndim, int n, unsigned char* out, cudaStream_t s)

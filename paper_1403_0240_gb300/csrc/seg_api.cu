@@ -116,6 +116,16 @@ void dev_free(void* p, cudaStream_t s)
     }
 }
 
+// Topology tables (adjacency masks and the tabulated simple-point decisions), built once
+// per process, before the first context or simple-point query.
+cudaError_t ensure_topology_tables()
+{
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] { err = topology_tables_init(); });
+    return err;
+}
+
 // Pinned host mirrors of the per-context counters, handed out from slabs that live as long
 // as the process (a pinned allocation per context would cost more than the context).
 std::mutex g_pin_mu;
@@ -1012,9 +1022,7 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     if (e != cudaSuccess) { c->d_self = nullptr; return fail(cuda_fail(e, "job descriptor")); }
     if (!(c->h_ctr = pinned_counters())) return fail(cuda_fail(cudaErrorMemoryAllocation, "pinned counters"));
 
-    static std::once_flag topo_once;
-    static cudaError_t topo_err = cudaSuccess;
-    std::call_once(topo_once, [] { topo_err = topology_tables_init(); });
+    const cudaError_t topo_err = ensure_topology_tables();
     if (topo_err != cudaSuccess) return fail(cuda_fail(topo_err, "topology tables"));
     Counters hc{};
     hc.iter_tag = 1;
@@ -1331,11 +1339,7 @@ int seg_debug_simple(int32_t ndim, const uint32_t* masks, int32_t n, uint8_t* ou
 {
     if ((ndim != 2 && ndim != 3) || n < 0 || (n && (!masks || !out))) return SEG_EINVAL;
     if (!n) return SEG_OK;
-    static bool topo_ready = false;
-    if (!topo_ready) {
-        CK(topology_tables_init());
-        topo_ready = true;
-    }
+    CK(ensure_topology_tables());
     unsigned* dm = nullptr;
     unsigned char* dout = nullptr;
     CK(cudaMalloc(&dm, (size_t)n * 4));
