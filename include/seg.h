@@ -51,7 +51,11 @@ extern "C" {
 #define SEG_ESTATE   -5   /* call not valid in the object's current state */
 
 enum { SEG_F32 = 0, SEG_U16 = 1 };                 /* image element type */
-enum { SEG_PC = 0, SEG_PS = 1 };                   /* piecewise constant / piecewise smooth */
+/* region models: piecewise constant (Gaussian noise, region means); piecewise smooth (local
+ * means over a ball of radius R, Gaussian noise); piecewise smooth with Poisson noise: the
+ * data term of a pixel is mu - I ln mu for its local mean mu (the log(I!) term dropped), the
+ * means floored at 2^-20 max(1, max I); intensities must be >= 0 */
+enum { SEG_PC = 0, SEG_PS = 1, SEG_PS_POISSON = 2 };
 /* gradient type at start. SEG_SOBOLEV_GLOBAL: Eq. 6 with the length scale of the inner
  * product set to the contour length, E = |Gamma| (Length scale section), |Gamma| read as the
  * number of connectivity-adjacent pixel pairs with different labels (the length prior's
@@ -69,11 +73,11 @@ typedef struct {
     int32_t ndim;          /* 2 | 3 */
     int32_t dtype;         /* SEG_F32 | SEG_U16 */
     int64_t shape[3];      /* {D, H, W}; D = 1 in 2D; row-major, x fastest; each >= 1, D*H*W < 2^31 */
-    int32_t model;         /* SEG_PC | SEG_PS */
+    int32_t model;         /* SEG_PC | SEG_PS | SEG_PS_POISSON */
     int32_t connectivity;  /* foreground: 4 (2D) | 6 (3D); background uses 8 | 26 */
     double  lambda;        /* length weight (Eq. 10), >= 0 */
     double  cutoff;        /* interaction cutoff E/2 in pixels, > 0; E = 2 * cutoff, eps = 1/24 */
-    double  ps_radius;     /* local-mean radius R for SEG_PS, >= 1 */
+    double  ps_radius;     /* local-mean radius R for SEG_PS and SEG_PS_POISSON, >= 1 */
     int32_t gradient;      /* SEG_SOBOLEV | SEG_L2 | SEG_SOBOLEV_GLOBAL */
     int32_t osc_window;    /* switch to L2 once the accepted-move count has not reached a new
                               minimum for this many iterations; 0 = never switch */

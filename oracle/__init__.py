@@ -8,6 +8,7 @@ readings of the paper and for which test pins each function).
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -23,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 F32, U16 = 0, 1
-PC, PS = 0, 1
+PC, PS, PSP = 0, 1, 2
 SOBOLEV, L2, SOBOLEV_GLOBAL = 0, 1, 2
 
 
@@ -47,7 +48,7 @@ class Params(C.Structure):
                 ("model", C.c_int32), ("conn", C.c_int32),
                 ("lam", C.c_double), ("cutoff", C.c_double), ("ps_radius", C.c_double),
                 ("gradient", C.c_int32), ("osc_window", C.c_int32),
-                ("nlabels", C.c_int32), ("pad_", C.c_int32)]
+                ("nlabels", C.c_int32), ("pad_", C.c_int32), ("mu_floor", C.c_double)]
 
 
 class State(C.Structure):
@@ -98,6 +99,8 @@ def lib():
             L.orc_admissible.argtypes = [P(Params), vp, C.c_uint32, C.c_int32, C.c_int32]
             L.orc_select.restype = C.c_int64
             L.orc_select.argtypes = [P(Params), vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_log.restype = C.c_double
+            L.orc_log.argtypes = [C.c_double]
             L.orc_perimeter.restype = C.c_int64
             L.orc_perimeter.argtypes = [P(Params), vp]
             L.orc_state_init.restype = None
@@ -124,7 +127,7 @@ def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", 
     p.ndim = image.ndim
     p.dtype = F32 if image.dtype == np.float32 else U16
     p.D, p.H, p.W = D, H, W
-    p.model = model if isinstance(model, int) else {"pc": PC, "ps": PS}[model]
+    p.model = model if isinstance(model, int) else {"pc": PC, "ps": PS, "psp": PSP}[model]
     p.conn = connectivity or (4 if image.ndim == 2 else 6)
     p.lam = float(lam)
     p.cutoff = float(cutoff)
@@ -133,7 +136,13 @@ def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", 
                                                              "sobolev_global": SOBOLEV_GLOBAL}[gradient]
     p.osc_window = int(osc_window)
     p.nlabels = int(nlabels if nlabels is not None else int(labels.max()) + 1)
+    # Poisson model: local means are floored at 2^-20 of the largest intensity (at least 2^-20)
+    p.mu_floor = math.ldexp(max(1.0, float(np.abs(image).max()) if image.size else 1.0), -20)
     return p
+
+
+def log(x: float) -> float:
+    return lib().orc_log(x)
 
 
 def kernel_eq5(r: float, E: float, eps: float = 1.0 / 24.0) -> float:

@@ -43,6 +43,36 @@ double orc_kernel_eq5(double r, double E, double eps)
     return (1.0 / E) * (1.0 + num / (2.0 * eps));
 }
 
+double orc_log(double x)
+{
+    int e = 0;
+    double m = frexp(x, &e);                 /* x = m 2^e, m in [1/2, 1) */
+    if (m < 0.70710678118654752440) { m = 2.0 * m; e = e - 1; }
+    double y = (m - 1.0) / (m + 1.0);
+    double y2 = y * y;
+    double s = 1.0 / 23.0;
+    s = 1.0 / 21.0 + y2 * s;
+    s = 1.0 / 19.0 + y2 * s;
+    s = 1.0 / 17.0 + y2 * s;
+    s = 1.0 / 15.0 + y2 * s;
+    s = 1.0 / 13.0 + y2 * s;
+    s = 1.0 / 11.0 + y2 * s;
+    s = 1.0 / 9.0 + y2 * s;
+    s = 1.0 / 7.0 + y2 * s;
+    s = 1.0 / 5.0 + y2 * s;
+    s = 1.0 / 3.0 + y2 * s;
+    s = 1.0 + y2 * s;
+    return (double)e * 0.69314718055994530942 + 2.0 * (y * s);
+}
+
+/* Poisson negative log-likelihood of intensity v under mean mu (the log(v!) term dropped),
+ * the mean floored at mu_floor */
+static double poisson_f(double v, double mu, double mu_floor)
+{
+    double m = mu > mu_floor ? mu : mu_floor;
+    return m - v * orc_log(m);
+}
+
 /* ------------------------------------------------------------------ */
 static double pix(const orc_params* p, const void* I, int64_t i)
 {
@@ -353,12 +383,24 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
                     }
             double muc = sc / (double)cc;
             double mul = sl / (double)cl;
-            double a = v - muc;
-            double b = v - mul;
-            data = a * a - b * b;
-            if (scale)
-                scale[k] = 2.0 * fabs(a) * (fabs(v) + ac / (double)cc) + 2.0 * fabs(b) * (fabs(v) + al / (double)cl) +
-                           a * a + b * b;
+            if (p->model == 2) {
+                /* Poisson noise: -log p(v | mu) = mu - v ln mu, the local means as the model */
+                double fc = poisson_f(v, muc, p->mu_floor);
+                double fl = poisson_f(v, mul, p->mu_floor);
+                data = fc - fl;
+                if (scale) {
+                    double mc = muc > p->mu_floor ? muc : p->mu_floor;
+                    double ml = mul > p->mu_floor ? mul : p->mu_floor;
+                    scale[k] = mc + fabs(v * orc_log(mc)) + ml + fabs(v * orc_log(ml)) + fabs(v);
+                }
+            } else {
+                double a = v - muc;
+                double b = v - mul;
+                data = a * a - b * b;
+                if (scale)
+                    scale[k] = 2.0 * fabs(a) * (fabs(v) + ac / (double)cc) +
+                               2.0 * fabs(b) * (fabs(v) + al / (double)cl) + a * a + b * b;
+            }
         }
         int64_t dP = orc_delta_perimeter(p, L, xi, lp, cp);
         dE[k] = data + p->lambda * (double)dP;

@@ -19,6 +19,9 @@
  *                         recompute of the total SSE before and after the flip.
  *   orc_energy (PS)     - local-mean difference; pinned by scipy.ndimage
  *                         convolutions and by the R -> infinity limit.
+ *   orc_energy (Poisson)- f(v, mu_c) - f(v, mu_l), f(v, mu) = mu - v ln mu over the same
+ *                         local means; pinned by convolutions and numpy logarithms.
+ *   orc_log             - pinned against the C library logarithm within 4 ulp.
  *   orc_energy (length) - pinned by a brute-force recount of the perimeter.
  *   orc_sobolev         - Eq. 6 with a cell list; pinned by all-pairs brute force,
  *                         the degenerate cutoff, and a hand-computed straight line.
@@ -46,7 +49,8 @@ typedef struct {
     int32_t ndim;        /* 2 | 3 */
     int32_t dtype;       /* 0 = float32 image, 1 = uint16 image */
     int64_t D, H, W;     /* D = 1 in 2D; row-major, x fastest */
-    int32_t model;       /* 0 = piecewise constant, 1 = piecewise smooth */
+    int32_t model;       /* 0 = piecewise constant, 1 = piecewise smooth (Gaussian noise),
+                            2 = piecewise smooth with Poisson noise */
     int32_t conn;        /* foreground connectivity: 4 (2D) | 6 (3D) */
     double lambda;       /* length weight (Eq. 10) */
     double cutoff;       /* interaction cutoff E/2 in pixels */
@@ -55,6 +59,7 @@ typedef struct {
     int32_t osc_window;  /* iterations without a new minimum of accepted moves before switching to L2; 0 = never */
     int32_t nlabels;     /* M: labels are 0..M-1 */
     int32_t pad_;
+    double mu_floor;     /* Poisson model: local means below this are taken as this */
 } orc_params;
 
 typedef struct {
@@ -75,6 +80,11 @@ typedef struct {
 } orc_status;
 
 double  orc_kernel_eq5(double r, double E, double eps);
+
+/* natural logarithm of x > 0 by the atanh series after reduction to [sqrt(1/2), sqrt(2)):
+ * ln x = e ln 2 + 2 (y + y^3/3 + ... + y^23/23), y = (m - 1)/(m + 1); every operation an IEEE
+ * double operation in a fixed order */
+double  orc_log(double x);
 
 int64_t orc_extract(const orc_params* p, const int32_t* L,
                     uint32_t* idx, int32_t* l, int32_t* c, int64_t cap);

@@ -235,6 +235,38 @@ __device__ __forceinline__ double image64(const Job& J, long long i)
     return (double)((const unsigned short*)J.I)[i];
 }
 
+// Natural logarithm by the atanh series after reduction to [sqrt(1/2), sqrt(2)):
+// ln x = e ln 2 + 2 (y + y^3/3 + ... + y^23/23), y = (m - 1)/(m + 1), every operation an IEEE
+// double operation in a fixed order (the FP64 reference evaluates the same series the same way).
+__device__ __forceinline__ double log_series(double x)
+{
+    int e = 0;
+    double m = frexp(x, &e);
+    if (m < 0.70710678118654752440) { m = __dmul_rn(2.0, m); e = e - 1; }
+    const double y = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double y2 = __dmul_rn(y, y);
+    double s = 1.0 / 23.0;
+    s = __dadd_rn(1.0 / 21.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 19.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 17.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 15.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 13.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 11.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 9.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 7.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 5.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 3.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0, __dmul_rn(y2, s));
+    return __dadd_rn(__dmul_rn((double)e, 0.69314718055994530942), __dmul_rn(2.0, __dmul_rn(y, s)));
+}
+
+// Poisson negative log-likelihood of v under the (floored) mean mu, the log(v!) term dropped
+__device__ __forceinline__ double poisson_f64(double v, double mu, double floor)
+{
+    const double m = mu > floor ? mu : floor;
+    return __dsub_rn(m, __dmul_rn(v, log_series(m)));
+}
+
 // q: index of the particle (gi, l -> c) in the current particle arrays; its exact ball
 // sums are reused when they were stored (piecewise smooth with exact FP64 ball sums).
 __device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
@@ -270,9 +302,14 @@ __device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
                 else if (m == l) { sl = __dadd_rn(sl, image64(J, j)); cl++; }
             }
         }
-        double a = __dsub_rn(v, __ddiv_rn(sc, (double)cc));
-        double b = __dsub_rn(v, __ddiv_rn(sl, (double)cl));
-        data = __dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+        if (J.model == SEG_PS_POISSON) {
+            data = __dsub_rn(poisson_f64(v, __ddiv_rn(sc, (double)cc), J.mu_floor64),
+                             poisson_f64(v, __ddiv_rn(sl, (double)cl), J.mu_floor64));
+        } else {
+            double a = __dsub_rn(v, __ddiv_rn(sc, (double)cc));
+            double b = __dsub_rn(v, __ddiv_rn(sl, (double)cl));
+            data = __dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+        }
     }
     int dP = 0;
     const int nbz = J.ndim == 3 ? 1 : 0;
@@ -766,7 +803,7 @@ cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream
 __global__ void k_scan_inputs(const void* I, int dtype, const int* L, int ndim, int D, int H, int W, InputScan* out)
 {
     const long long npix = (long long)D * H * W;
-    int lmin = 0x7fffffff, lmax = -0x7fffffff - 1, slo = 0x7fffffff, shi = -1, bad = 0;
+    int lmin = 0x7fffffff, lmax = -0x7fffffff - 1, slo = 0x7fffffff, shi = -1, bad = 0, neg = 0;
     unsigned mabs = 0;
     unsigned long long parts = 0, pairs = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
@@ -778,6 +815,7 @@ __global__ void k_scan_inputs(const void* I, int dtype, const int* L, int ndim, 
             const int eb = (int)((b >> 23) & 0xffu);
             if (eb == 255) bad = 1;
             else if (b & 0x7fffffffu) {
+                if (b >> 31) neg = 1;
                 const int slot = eb ? eb : 1;
                 slo = min(slo, slot);
                 shi = max(shi, slot);
@@ -809,6 +847,7 @@ __global__ void k_scan_inputs(const void* I, int dtype, const int* L, int ndim, 
     slo = __reduce_min_sync(0xffffffffu, slo);
     shi = __reduce_max_sync(0xffffffffu, shi);
     bad = __reduce_or_sync(0xffffffffu, (unsigned)bad);
+    neg = __reduce_or_sync(0xffffffffu, (unsigned)neg);
     mabs = __reduce_max_sync(0xffffffffu, mabs);
     for (int o = 16; o > 0; o >>= 1) parts += __shfl_down_sync(0xffffffffu, parts, o);
     for (int o = 16; o > 0; o >>= 1) pairs += __shfl_down_sync(0xffffffffu, pairs, o);
@@ -819,6 +858,7 @@ __global__ void k_scan_inputs(const void* I, int dtype, const int* L, int ndim, 
         atomicMax(&out->slot_hi, shi);
         atomicMax(&out->maxabs, mabs);
         if (bad) atomicOr(&out->bad, 1);
+        if (neg) atomicOr(&out->neg, 1);
         if (parts) atomicAdd(&out->particles, parts);
         if (pairs) atomicAdd(&out->pairs, pairs);
     }

@@ -139,6 +139,37 @@ __device__ __forceinline__ void energy_ps_finish_int(const Job& J, float v, int 
     eE = err * 1.001f;
 }
 
+// Poisson data term f(v, mu) = mu - v ln mu (mean floored), from a float32 mean with error
+// bound emu: value and a bound on its distance to the FP64 value. logf is within 1 ulp of the
+// logarithm of its argument (CUDA maths library accuracy); the mean's error adds emu / mu.
+__device__ __forceinline__ void poisson_f32(const Job& J, float v, float mu, float emu, float& f, float& ef)
+{
+    const float m = fmaxf(mu, J.mu_floor32);
+    const float L = logf(m);
+    const float eL = kU * fabsf(L) + 1.0001f * emu / m + 1e-37f;
+    const float p = v * L;
+    const float ep = fabsf(v) * eL + kU * fabsf(p);
+    f = m - p;
+    ef = emu + ep + kU * fabsf(f);
+}
+
+// Poisson piecewise-smooth energy difference from the local means of the c and l parts of the
+// ball, each with its error bound
+__device__ __forceinline__ void energy_psp_finish(const Job& J, float v, int dP, float muc, float emc, float mul,
+                                                  float eml, float& dE, float& eE)
+{
+    float fc, efc, fl, efl;
+    poisson_f32(J, v, muc, emc, fc, efc);
+    poisson_f32(J, v, mul, eml, fl, efl);
+    const float d = fc - fl;
+    const float lp = J.lambda32 * (float)dP;
+    dE = d + lp;
+    const float mag = fmaxf(muc, J.mu_floor32) + fmaxf(mul, J.mu_floor32) + fabsf(v) * (fabsf(logf(fmaxf(muc, J.mu_floor32))) +
+                      fabsf(logf(fmaxf(mul, J.mu_floor32))) + 1.0f);
+    const float err = efc + efl + kU * (fabsf(d) + fabsf(lp) + fabsf(dE)) + kFp64Margin * (mag + fabsf(lp));
+    eE = err * 1.001f;
+}
+
 __device__ __forceinline__ float image_at(const Job& J, long long i)
 {
     if (J.dtype == SEG_F32) return __ldg((const float*)J.I + i);
@@ -602,7 +633,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         J.cell_start[cid] = base + s_cstart[kc];
         J.cell_count[cid] = s_cstart[kc + 1] - s_cstart[kc];
     }
-    if (J.model != SEG_PS || !fits) return;
+    if (J.model == SEG_PC || !fits) return;
 
     // piecewise-smooth energy: one particle per thread over the dense range of this tile's
     // particles, so every thread runs the same ball loop
@@ -660,7 +691,15 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                     const float v = (float)qv * J.unit32;
                     const long long sc = isc - (long long)cc * qv, sl = isl - (long long)cl * qv;
                     float dE, eE;
-                    energy_ps_finish_int(J, v, delta_p(si, own, c), sc, cc, sl, cl, dE, eE);
+                    if (J.model == SEG_PS_POISSON) {
+                        // local means from the exact sums: two float32 roundings each
+                        const float muc = ((float)isc / (float)cc) * J.unit32;
+                        const float mul = ((float)isl / (float)cl) * J.unit32;
+                        energy_psp_finish(J, v, delta_p(si, own, c), muc, 1.0001f * kU * muc, mul, 1.0001f * kU * mul,
+                                          dE, eE);
+                    } else {
+                        energy_ps_finish_int(J, v, delta_p(si, own, c), sc, cc, sl, cl, dE, eE);
+                    }
                     J.p_qc[o2] = isc;
                     J.p_ql[o2] = isl;
                     J.p_nc[o2] = cc;
@@ -715,7 +754,29 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         }
         float dE, eE;
         const int dP = delta_p(si, own, c);
-        if (use_int) {
+        if (J.model == SEG_PS_POISSON) {
+            float muc, emc, mul, eml;
+            if (use_int) {
+                const long long rc = isc + (long long)cc * qv, rl = isl + (long long)cl * qv;
+                muc = ((float)rc / (float)cc) * J.unit32;
+                mul = ((float)rl / (float)cl) * J.unit32;
+                emc = 1.0001f * kU * muc;
+                eml = 1.0001f * kU * mul;
+            } else {
+                // shifted float sums: mu = v + sum(I - v) / n
+                muc = v + fsc / (float)cc;
+                mul = v + fsl / (float)cl;
+                emc = gamma_n(cc + 2) * ac / (float)cc + kU * (fabsf(muc) + fabsf(v));
+                eml = gamma_n(cl + 2) * al / (float)cl + kU * (fabsf(mul) + fabsf(v));
+            }
+            energy_psp_finish(J, v, dP, muc, emc, mul, eml, dE, eE);
+            if (use_int) {
+                J.p_qc[o2] = isc + (long long)cc * qv;
+                J.p_ql[o2] = isl + (long long)cl * qv;
+                J.p_nc[o2] = cc;
+                J.p_nl[o2] = cl;
+            }
+        } else if (use_int) {
             energy_ps_finish_int(J, v, dP, isc, cc, isl, cl, dE, eE);
             // keep the exact ball sums for the FP64 recompute
             J.p_qc[o2] = isc + (long long)cc * qv;

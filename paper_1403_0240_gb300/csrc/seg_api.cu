@@ -223,11 +223,11 @@ int validate(const seg_params* p)
     if (p->ndim == 2 && p->shape[0] != 1) return SEG_EINVAL;
     long double npix = (long double)p->shape[0] * p->shape[1] * p->shape[2];
     if (npix >= 2147483647.0L) return SEG_EINVAL;
-    if (p->model != SEG_PC && p->model != SEG_PS) return SEG_EINVAL;
+    if (p->model != SEG_PC && p->model != SEG_PS && p->model != SEG_PS_POISSON) return SEG_EINVAL;
     if ((p->ndim == 2 && p->connectivity != 4) || (p->ndim == 3 && p->connectivity != 6)) return SEG_EINVAL;
     if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return SEG_EINVAL;
     if (!(p->cutoff > 0.0) || p->cutoff > 32.0) return SEG_EINVAL;
-    if (p->model == SEG_PS && (!(p->ps_radius >= 1.0) || p->ps_radius > 64.0)) return SEG_EINVAL;
+    if (p->model != SEG_PC && (!(p->ps_radius >= 1.0) || p->ps_radius > 64.0)) return SEG_EINVAL;
     if (p->gradient != SEG_SOBOLEV && p->gradient != SEG_L2 && p->gradient != SEG_SOBOLEV_GLOBAL) return SEG_EINVAL;
     if (p->gradient == SEG_SOBOLEV_GLOBAL) {
         // the E = |Gamma| kernel table spans every squared distance in the image
@@ -307,7 +307,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     h.ntz = (h.ncz + h.tcz - 1) / h.tcz;
     h.ntiles = h.ntx * h.nty * h.ntz;
     const int R = (int)std::floor(p->ps_radius);
-    h.ps_staged = (h.model == SEG_PS && h.ndim == 2 && R <= 32) ? 1 : 0;
+    h.ps_staged = (h.model != SEG_PC && h.ndim == 2 && R <= 32) ? 1 : 0;
     h.halo = h.ps_staged ? std::max(1, R) : 1;
     h.lambda64 = p->lambda;
     h.lambda32 = (float)p->lambda;
@@ -331,7 +331,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
         P.klut[d2] = (float)P.klut64[d2];
     }
     const int rz = h.ndim == 3 ? 1 : 0;
-    if (h.model == SEG_PS) {
+    if (h.model != SEG_PC) {
         const double R2 = p->ps_radius * p->ps_radius;
         for (int dz = -R * rz; dz <= R * rz; dz++)
             for (int dy = -R; dy <= R; dy++)
@@ -357,7 +357,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     const int qbits = h.dtype == SEG_F32 ? 23 + nS : 16;
     h.e_min = h.dtype == SEG_F32 ? slot_lo - 150 : 0;
     const bool unit_ok = h.e_min >= -120 && h.e_min <= 100;
-    h.ps_int = (h.model == SEG_PS && unit_ok && qbits + lg + 1 <= 62) ? 1 : 0;
+    h.ps_int = (h.model != SEG_PC && unit_ok && qbits + lg + 1 <= 62) ? 1 : 0;
     h.ps_exact64 = (h.ps_int && qbits + lg <= 53) ? 1 : 0;
     h.ps_q32 = (h.ps_int && h.dtype == SEG_F32 && qbits <= 31) ? 1 : 0;
     h.unit32 = unit_ok ? std::ldexp(1.0f, h.e_min) : 0.0f;
@@ -951,13 +951,14 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     InputScan* dscan = (InputScan*)(c->inputs + ib + lb);
     CKF(cudaMemcpyAsync(dI, image, npix * esz, cudaMemcpyDefault, stream));
     CKF(cudaMemcpyAsync(dL, labels0, npix * 4, cudaMemcpyDefault, stream));
-    InputScan scan{0x7fffffff, -0x7fffffff - 1, 0x7fffffff, -1, 0u, 0, 0ull};
+    InputScan scan{0x7fffffff, -0x7fffffff - 1, 0x7fffffff, -1, 0u, 0, 0, 0ull, 0ull};
     CKF(cudaMemcpyAsync(dscan, &scan, sizeof scan, cudaMemcpyHostToDevice, stream));
     CKF(launch_scan_inputs(dI, p->dtype, dL, p->ndim, (int)p->shape[0], (int)p->shape[1], (int)p->shape[2], dscan,
                            stream));
     CKF(cudaMemcpyAsync(&scan, dscan, sizeof scan, cudaMemcpyDeviceToHost, stream));
     CKF(cudaStreamSynchronize(stream));
     if (scan.lab_min < 0 || scan.lab_max >= (1 << 24) || scan.bad) return fail(SEG_EINVAL);
+    if (p->model == SEG_PS_POISSON && scan.neg) return fail(SEG_EINVAL);   // Poisson counts are >= 0
     const int M = scan.lab_max + 1;
     int slot_lo = 1, slot_hi = 1;
     float maxabs = 0.0f;
@@ -1001,6 +1002,8 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     Plan P;
     make_geometry(p, M, slot_lo, slot_hi - slot_lo + 1, P);
     P.h.maxabs = maxabs;
+    P.h.mu_floor64 = std::ldexp(std::max(1.0, (double)maxabs), -20);
+    P.h.mu_floor32 = (float)P.h.mu_floor64;
     c->h = P.h;
     e = dev_alloc((void**)&c->arena, P.fixed.bytes, stream);
     if (e != cudaSuccess) { cudaGetLastError(); c->arena = nullptr; return fail(SEG_ENOMEM); }

@@ -85,6 +85,8 @@ struct alignas(64) Job {
     float unit32;             // 2^e_min as a float
     double unit64;            // 2^e_min as a double
     float maxabs;             // largest |I| of the image
+    float mu_floor32;         // Poisson model: local means below this are taken as this
+    double mu_floor64;
     float lambda32;
     double lambda64;
     double cutoff, E;         // E = 2 * cutoff (Eq. 5 length scale)
@@ -244,6 +246,7 @@ struct InputScan {
     int slot_lo, slot_hi;          // float32: exponent slots of the non-zero values (slot_hi < slot_lo: none)
     unsigned maxabs;               // float32: bits of the largest |I|; uint16: the largest value
     int bad;                       // float32: a NaN or an infinity
+    int neg;                       // float32: a value below zero
     unsigned long long particles;  // particles of the initial labels (pixel, neighbouring label) pairs
     unsigned long long pairs;      // adjacent pixel pairs with different labels (|Gamma|)
 };

@@ -16,7 +16,7 @@ from . import build as _build
 
 SEG_OK, SEG_EINVAL, SEG_ENOMEM, SEG_ECUDA, SEG_ETIMEOUT, SEG_ESTATE = 0, -1, -2, -3, -4, -5
 SEG_F32, SEG_U16 = 0, 1
-SEG_PC, SEG_PS = 0, 1
+SEG_PC, SEG_PS, SEG_PS_POISSON = 0, 1, 2
 SEG_SOBOLEV, SEG_L2, SEG_SOBOLEV_GLOBAL = 0, 1, 2
 SEG_STATS_EXACT = 0
 
@@ -166,7 +166,7 @@ def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_ra
     p.ndim = len(shape)
     p.dtype = _dtype_code(image)
     p.shape[0], p.shape[1], p.shape[2] = (1,) + shape if len(shape) == 2 else shape
-    p.model = model if isinstance(model, int) else {"pc": SEG_PC, "ps": SEG_PS}[model]
+    p.model = model if isinstance(model, int) else {"pc": SEG_PC, "ps": SEG_PS, "psp": SEG_PS_POISSON}[model]
     p.connectivity = connectivity or (4 if len(shape) == 2 else 6)
     p.lam = float(lam)
     p.cutoff = float(cutoff)
