@@ -953,9 +953,10 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
         }
         return;
     }
-    // the thread's first own particle, fetched while the neighbourhood is staged
-    const unsigned my_gi = (unsigned)tid < pcount ? J.p_idx[pstart + tid] : 0u;
-    const int my_l = (unsigned)tid < pcount ? J.p_l[pstart + tid] : 0;
+    // the first own particle of the thread's lane pair, fetched while the neighbourhood is staged
+    const unsigned my_i = (unsigned)tid >> 1;
+    const unsigned my_gi = my_i < pcount ? J.p_idx[pstart + my_i] : 0u;
+    const int my_l = my_i < pcount ? J.p_l[pstart + my_i] : 0;
     const TileBox b = tile_box(J, k);
     const int r2max = J.r2max;
     const int rr = isqrt_floor(r2max);
@@ -1112,20 +1113,26 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
         __syncthreads();
 
         const int nrows = staged ? s_nrows : 0;
-        for (unsigned i = tid; i < pcount; i += blockDim.x) {
-            const unsigned p = pstart + i;
-            const unsigned gi = i == (unsigned)tid ? my_gi : J.p_idx[p];
+        // a pair of lanes per particle, each taking every other row of the ball; their partial
+        // sums are added at the end (the bound below covers any order of the additions)
+        const int h = tid & 1;
+        const unsigned half = blockDim.x >> 1;
+        for (unsigned i0 = 0; i0 < pcount; i0 += half) {
+            const unsigned i = i0 + my_i;
+            const bool own = i < pcount;
+            const unsigned p = pstart + (own ? i : 0u);
+            const unsigned gi = i == my_i ? my_gi : J.p_idx[p];
             int x, y, z;
             pix_coords(J, gi, x, y, z);
-            if (x < sx0 || x >= sx1) continue;
-            const int lp = i == (unsigned)tid ? my_l : J.p_l[p];
+            const bool act = own && x >= sx0 && x < sx1;
+            const int lp = i == my_i ? my_l : J.p_l[p];
             float As = 0.f, Bs = 0.f, aA = 0.f, aB = 0.f, eAs = 0.f, eBs = 0.f;
             int nA = 0, nB = 0;
-            if (staged) {
+            if (act && staged) {
                 // the particle lies in the slab, so every row of its ball lies in the box
                 const int lx = x - bx0;
                 const int cbase = ((z - bz0) * bny + (y - by0)) * bnx + lx;
-                for (int r = 0; r < nrows; r++) {
+                for (int r = h; r < nrows; r += 2) {
                     const int info = s_rinfo[r];
                     const int rx = info & 255, dyz2 = info >> 8;
                     const int base = cbase + s_rdelta[r];
@@ -1143,9 +1150,18 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
                         }
                     }
                 }
-            } else {
+            } else if (act && h == 0) {
                 sobolev_sums<NDIM>(J, lp, x, y, z, r2max, As, Bs, aA, aB, eAs, eBs, nA, nB);
             }
+            As += __shfl_xor_sync(0xffffffffu, As, 1);
+            Bs += __shfl_xor_sync(0xffffffffu, Bs, 1);
+            aA += __shfl_xor_sync(0xffffffffu, aA, 1);
+            aB += __shfl_xor_sync(0xffffffffu, aB, 1);
+            eAs += __shfl_xor_sync(0xffffffffu, eAs, 1);
+            eBs += __shfl_xor_sync(0xffffffffu, eBs, 1);
+            nA += __shfl_xor_sync(0xffffffffu, nA, 1);
+            nB += __shfl_xor_sync(0xffffffffu, nB, 1);
+            if (!act || h) continue;
             float A = nA ? As / (float)nA : 0.f;
             float B = nB ? Bs / (float)nB : 0.f;
             float eA = nA ? ((eAs + (kU + gamma_n(nA)) * aA) * 1.0001f / (float)nA + kU * fabsf(A)) : 0.f;
