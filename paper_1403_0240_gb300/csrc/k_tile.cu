@@ -953,8 +953,9 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
         }
         return;
     }
-    // the first own particle of the thread's lane pair, fetched while the neighbourhood is staged
-    const unsigned my_i = (unsigned)tid >> 1;
+    // the first own particle of the thread's lane group, fetched while the neighbourhood is staged
+    constexpr int kSplit = 2;                        // lanes per particle (4 measured no faster in 3D)
+    const unsigned my_i = (unsigned)tid / kSplit;
     const unsigned my_gi = my_i < pcount ? J.p_idx[pstart + my_i] : 0u;
     const int my_l = my_i < pcount ? J.p_l[pstart + my_i] : 0;
     const TileBox b = tile_box(J, k);
@@ -1113,10 +1114,10 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
         __syncthreads();
 
         const int nrows = staged ? s_nrows : 0;
-        // a pair of lanes per particle, each taking every other row of the ball; their partial
+        // kSplit lanes per particle, each taking every kSplit-th row of the ball; their partial
         // sums are added at the end (the bound below covers any order of the additions)
-        const int h = tid & 1;
-        const unsigned half = blockDim.x >> 1;
+        const int h = tid % kSplit;
+        const unsigned half = blockDim.x / kSplit;
         for (unsigned i0 = 0; i0 < pcount; i0 += half) {
             const unsigned i = i0 + my_i;
             const bool own = i < pcount;
@@ -1132,7 +1133,7 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
                 // the particle lies in the slab, so every row of its ball lies in the box
                 const int lx = x - bx0;
                 const int cbase = ((z - bz0) * bny + (y - by0)) * bnx + lx;
-                for (int r = h; r < nrows; r += 2) {
+                for (int r = h; r < nrows; r += kSplit) {
                     const int info = s_rinfo[r];
                     const int rx = info & 255, dyz2 = info >> 8;
                     const int base = cbase + s_rdelta[r];
@@ -1153,14 +1154,17 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
             } else if (act && h == 0) {
                 sobolev_sums<NDIM>(J, lp, x, y, z, r2max, As, Bs, aA, aB, eAs, eBs, nA, nB);
             }
-            As += __shfl_xor_sync(0xffffffffu, As, 1);
-            Bs += __shfl_xor_sync(0xffffffffu, Bs, 1);
-            aA += __shfl_xor_sync(0xffffffffu, aA, 1);
-            aB += __shfl_xor_sync(0xffffffffu, aB, 1);
-            eAs += __shfl_xor_sync(0xffffffffu, eAs, 1);
-            eBs += __shfl_xor_sync(0xffffffffu, eBs, 1);
-            nA += __shfl_xor_sync(0xffffffffu, nA, 1);
-            nB += __shfl_xor_sync(0xffffffffu, nB, 1);
+#pragma unroll
+            for (int o = 1; o < kSplit; o <<= 1) {
+                As += __shfl_xor_sync(0xffffffffu, As, o);
+                Bs += __shfl_xor_sync(0xffffffffu, Bs, o);
+                aA += __shfl_xor_sync(0xffffffffu, aA, o);
+                aB += __shfl_xor_sync(0xffffffffu, aB, o);
+                eAs += __shfl_xor_sync(0xffffffffu, eAs, o);
+                eBs += __shfl_xor_sync(0xffffffffu, eBs, o);
+                nA += __shfl_xor_sync(0xffffffffu, nA, o);
+                nB += __shfl_xor_sync(0xffffffffu, nB, o);
+            }
             if (!act || h) continue;
             float A = nA ? As / (float)nA : 0.f;
             float B = nB ? Bs / (float)nB : 0.f;
