@@ -929,7 +929,7 @@ template <int NDIM>
 __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
 {
     pdl_enter();
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned s_warp[32];
     __shared__ float s_klut[256];
     __shared__ int s_rdelta[kMaxRows];           // row offset in the pixel box
