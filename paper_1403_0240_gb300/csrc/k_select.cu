@@ -420,7 +420,9 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int n
                 int x, y, z;
                 coords(J, gi, x, y, z);
                 const long long lim = J.ctr->g_lim;
-                long long r = 0;
+                // largest r with r^2 < lim, from the square root corrected by one step
+                long long r = (long long)sqrt((double)(lim > 0 ? lim - 1 : 0));
+                while (r > 0 && r * r >= lim) r--;
                 while ((r + 1) * (r + 1) < lim) r++;
                 const long long x0 = max(0LL, x - r), x1 = min((long long)J.W - 1, x + r);
                 const long long y0 = max(0LL, y - r), y1 = min((long long)J.H - 1, y + r);
