@@ -339,7 +339,10 @@ def run_served(args, world, rank, local, pg):
     free, _ = torch.cuda.mem_get_info(dev)
     budget = int(0.6 * free)
     # warm-up on a few jobs
-    be = SegBackend(stream=torch.cuda.current_stream(dev), init_stream=torch.cuda.Stream(dev), keep_labels=True)
+    # new jobs are set up on a high-priority stream, so that their few small kernels do not queue
+    # behind the batch step in flight
+    be = SegBackend(stream=torch.cuda.current_stream(dev), init_stream=torch.cuda.Stream(dev, priority=-1),
+                    keep_labels=True)
     srv = Server(be, budget, max_jobs=512, max_iters_per_step=args.iters_per_step)
     for r in reqs[:4]:
         srv.submit(Request(r.job_id, 0.0, r.image, r.labels0, 3, r.params, r.nlabels))
