@@ -250,6 +250,14 @@ int seg_region_stats_noalloc(int32_t dtype, int64_t npix, const void* image, con
  * point (4/8 in 2D, 6/26 in 3D). */
 int seg_debug_simple(int32_t ndim, const uint32_t* masks, int32_t n, uint8_t* out);
 
+/* Test-only fault injection, for checking that bounded device waits report instead of
+ * hanging. SEG_INJECT_UNPUBLISHED_TILE: from the next iteration on, extraction leaves the first
+ * tile's particle count unpublished, so the next tile's bounded wait for it runs out (about two
+ * seconds) and the iteration ends with SEG_ETIMEOUT; the context is then poisoned (destroy it).
+ * SEG_INJECT_NONE clears the injection. No GPU fault is raised. */
+enum { SEG_INJECT_NONE = 0, SEG_INJECT_UNPUBLISHED_TILE = 1 };
+int seg_debug_inject(seg_ctx* c, int32_t what);
+
 const char* seg_strerror(int code);
 /* Text of the last CUDA error this thread saw inside libseg ("" if none). */
 const char* seg_last_cuda_error(void);

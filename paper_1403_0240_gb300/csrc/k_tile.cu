@@ -227,12 +227,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, 
         : "memory");
 }
 
-// wait for phase 0 of bar with a bounded number of polls; false when it gave up
+// wait for phase 0 of bar, bounded in time and polls; false when it gave up
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar)
 {
-    for (unsigned spins = 0; spins < kSpinLimit; spins++)
+    WaitBound wb;
+    while (true) {
         if (mbar_try_wait(bar, 0)) return true;
-    return false;
+        if (wb.expired()) return false;
+    }
 }
 
 __host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
@@ -493,7 +495,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         const unsigned long long ep = (unsigned long long)(tag & 0x3fffffffu) << 34;
         const unsigned long long emask = ~((1ull << 34) - 1);
         unsigned excl = 0;
-        if (lane == 0) atomicExch(J.tile_word + k, ep | ((k == 0 ? 2ull : 1ull) << 32) | total);
+        // (fault injection for tests: the first tile publishes nothing)
+        const bool publish = !(J.inject == SEG_INJECT_UNPUBLISHED_TILE && k == 0);
+        if (lane == 0 && publish) atomicExch(J.tile_word + k, ep | ((k == 0 ? 2ull : 1ull) << 32) | total);
         if (k > 0) {
             // each lane reads 8 consecutive predecessors (lane 0 the nearest), 256 per round
             // trip. The ready run nearest to the tile is consumed up to the first inclusive
@@ -501,7 +505,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
             // round starts there (progress without waiting for the whole window).
             constexpr int kPer = 8;
             long long win_end = (long long)k - 1;
-            unsigned spins = 0;
+            WaitBound wb;
             while (true) {
                 unsigned st[kPer], val[kPer];
 #pragma unroll
@@ -538,7 +542,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 if (done) break;
                 win_end -= limit;
                 if (limit == 0) {                   // the nearest remaining predecessor is not ready
-                    if (++spins > kSpinLimit) {
+                    // lane 0 decides for the warp, so that its lanes leave together
+                    if (__shfl_sync(0xffffffffu, (int)wb.expired(), 0)) {
                         if (lane == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
                         break;
                     }

@@ -1338,6 +1338,20 @@ void seg_batch_destroy(seg_batch* b)
     delete b;
 }
 
+int seg_debug_inject(seg_ctx* c, int32_t what)
+{
+    if (!c || (what != SEG_INJECT_NONE && what != SEG_INJECT_UNPUBLISHED_TILE)) return SEG_EINVAL;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    c->h.inject = what;
+    CK(cudaMemcpyAsync(c->d_self, &c->h, sizeof(Job), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->own->dirty = true;                       // the stepper's job table is rebuilt
+    if (c->batch) c->batch->st.dirty = true;
+    return SEG_OK;
+}
+
 int seg_debug_simple(int32_t ndim, const uint32_t* masks, int32_t n, uint8_t* out)
 {
     if ((ndim != 2 && ndim != 3) || n < 0 || (n && (!masks || !out))) return SEG_EINVAL;

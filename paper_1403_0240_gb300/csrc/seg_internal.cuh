@@ -7,8 +7,32 @@
 
 namespace segk {
 
-// Bounded waits: a spin that exceeds this many polls gives up and raises SEG_ETIMEOUT.
+// Bounded waits: every device-side wait gives up, and raises SEG_ETIMEOUT, after kWaitNs of
+// wall time on the GPU's global timer or kSpinLimit polls, whichever comes first.
 constexpr unsigned kSpinLimit = 1u << 26;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct WaitBound {
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    // called once per failed poll; true once the wait has run out
+    __device__ __forceinline__ bool expired()
+    {
+        if (spins++ == 0) {
+            t0 = global_ns();
+            return false;
+        }
+        if (spins > kSpinLimit) return true;
+        return (spins & 255u) == 0 && global_ns() - t0 > kWaitNs;
+    }
+};
 
 constexpr unsigned char kFlagFixup = 1, kFlagCand = 2, kFlagAcc = 4;
 constexpr int kUndecided = 0, kAccepted = 1, kRejected = 2;
@@ -103,6 +127,7 @@ struct alignas(64) Job {
     double* gK64;             // ... and FP64 (Eq. 5 in the order written); 0 outside the support
     int M;                    // number of labels
     int osc_window;           // L2 fallback window (0 = never)
+    int inject;               // test-only fault injection (SEG_INJECT_*)
     int nbr_stride;           // neighbour-list slots per candidate: 8 (2D) | 26 (3D)
     int slot_lo, nS, nQ;      // exact float32 sums: exponent slots [slot_lo, slot_lo + nS)
     const void* I;
@@ -228,9 +253,9 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl* bc, unsigned nblocks)
             __threadfence();
             atomicAdd(&bc->bar_gen, 1u);
         } else {
-            unsigned spins = 0;
+            WaitBound wb;
             while (ld_volatile(&bc->bar_gen) == gen) {
-                if (++spins > kSpinLimit) { atomicExch(&bc->err, SEG_ETIMEOUT); break; }
+                if (wb.expired()) { atomicExch(&bc->err, SEG_ETIMEOUT); break; }
                 __nanosleep(64);
             }
         }

@@ -19,6 +19,7 @@ SEG_F32, SEG_U16 = 0, 1
 SEG_PC, SEG_PS, SEG_PS_POISSON = 0, 1, 2
 SEG_SOBOLEV, SEG_L2, SEG_SOBOLEV_GLOBAL = 0, 1, 2
 SEG_STATS_EXACT = 0
+SEG_INJECT_NONE, SEG_INJECT_UNPUBLISHED_TILE = 0, 1
 
 
 class Params(C.Structure):
@@ -83,6 +84,7 @@ SIGNATURES = [
     ("seg_batch_destroy", None, [_V]),
     ("seg_region_stats_noalloc", C.c_int, [C.c_int32, C.c_int64, _V, _V, C.c_int32, _V, _V, _V, _V]),
     ("seg_debug_simple", C.c_int, [C.c_int32, _V, C.c_int32, _V]),
+    ("seg_debug_inject", C.c_int, [_V, C.c_int32]),
     ("seg_strerror", C.c_char_p, [C.c_int]),
     ("seg_last_cuda_error", C.c_char_p, []),
 ]
@@ -256,6 +258,10 @@ class Context:
         return st.as_dict()
 
     STAGES = ("extract", "sobolev", "flag", "fixup", "select", "lists", "rounds", "moves", "finish")
+
+    def inject(self, what: int):
+        """Test-only fault injection (seg_debug_inject)."""
+        _check(lib().seg_debug_inject(self.handle, int(what)), "seg_debug_inject")
 
     def profile(self, on: bool = True):
         _check(lib().seg_profile(self.handle, int(bool(on))), "seg_profile")
