@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 F32, U16 = 0, 1
-PC, PS, PSP = 0, 1, 2
+PC, PS, PSP, PCD = 0, 1, 2, 3
 SOBOLEV, L2, SOBOLEV_GLOBAL = 0, 1, 2
 
 
@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("model", C.c_int32), ("conn", C.c_int32),
                 ("lam", C.c_double), ("cutoff", C.c_double), ("ps_radius", C.c_double),
                 ("gradient", C.c_int32), ("osc_window", C.c_int32),
-                ("nlabels", C.c_int32), ("pad_", C.c_int32), ("mu_floor", C.c_double)]
+                ("nlabels", C.c_int32), ("pad_", C.c_int32), ("mu_floor", C.c_double),
+                ("psf_r", C.c_int32), ("pad2_", C.c_int32), ("psf", C.c_void_p)]
 
 
 class State(C.Structure):
@@ -99,6 +100,12 @@ def lib():
             L.orc_admissible.argtypes = [P(Params), vp, C.c_uint32, C.c_int32, C.c_int32]
             L.orc_select.restype = C.c_int64
             L.orc_select.argtypes = [P(Params), vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_psf_correlate.restype = None
+            L.orc_psf_correlate.argtypes = [P(Params), vp, vp]
+            L.orc_deconv_fields.restype = None
+            L.orc_deconv_fields.argtypes = [P(Params), vp, vp, vp, vp, vp, vp, vp]
+            L.orc_psf_norm2.restype = C.c_double
+            L.orc_psf_norm2.argtypes = [P(Params), C.c_int64, C.c_int64, C.c_int64]
             L.orc_log.restype = C.c_double
             L.orc_log.argtypes = [C.c_double]
             L.orc_perimeter.restype = C.c_int64
@@ -117,7 +124,8 @@ def _ptr(a: np.ndarray | None):
 
 def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", connectivity: int | None = None,
                 lam: float = 0.0, cutoff: float = 3.0, ps_radius: float = 0.0,
-                gradient: str | int = "sobolev", osc_window: int = 0, nlabels: int | None = None) -> Params:
+                gradient: str | int = "sobolev", osc_window: int = 0, nlabels: int | None = None,
+                psf: np.ndarray | None = None) -> Params:
     shape = image.shape
     if image.ndim == 2:
         D, H, W = 1, shape[0], shape[1]
@@ -127,7 +135,7 @@ def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", 
     p.ndim = image.ndim
     p.dtype = F32 if image.dtype == np.float32 else U16
     p.D, p.H, p.W = D, H, W
-    p.model = model if isinstance(model, int) else {"pc": PC, "ps": PS, "psp": PSP}[model]
+    p.model = model if isinstance(model, int) else {"pc": PC, "ps": PS, "psp": PSP, "pcd": PCD}[model]
     p.conn = connectivity or (4 if image.ndim == 2 else 6)
     p.lam = float(lam)
     p.cutoff = float(cutoff)
@@ -138,7 +146,45 @@ def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", 
     p.nlabels = int(nlabels if nlabels is not None else int(labels.max()) + 1)
     # Poisson model: local means are floored at 2^-20 of the largest intensity (at least 2^-20)
     p.mu_floor = math.ldexp(max(1.0, float(np.abs(image).max()) if image.size else 1.0), -20)
+    set_psf(p, psf)
     return p
+
+
+def set_psf(p: Params, psf: np.ndarray | None):
+    """Attach the 2r+1 taps of the deconvolving model's PSF profile (kept alive on p)."""
+    if psf is None:
+        p.psf_r, p.psf = 0, None
+        p._psf = None
+        return
+    k = np.ascontiguousarray(psf, dtype=np.float64).reshape(-1)
+    if k.size % 2 != 1:
+        raise ValueError("the PSF profile needs an odd number of taps")
+    p._psf = k
+    p.psf_r = (k.size - 1) // 2
+    p.psf = k.ctypes.data
+
+
+def psf_correlate(p: Params, f: np.ndarray) -> np.ndarray:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros_like(f)
+    lib().orc_psf_correlate(C.byref(p), _ptr(f), _ptr(out))
+    return out
+
+
+def deconv_fields(p: Params, I: np.ndarray, L: np.ndarray, n=None, S=None):
+    """(J, R, G) of the deconvolving model for labels L (theta = region means)."""
+    I = np.ascontiguousarray(I)
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    if n is None:
+        n, S, _ = stats(p, I, L)
+    J, R, G = (np.zeros(L.shape, np.float64) for _ in range(3))
+    lib().orc_deconv_fields(C.byref(p), _ptr(I), _ptr(L), _ptr(np.ascontiguousarray(n, np.int64)),
+                            _ptr(np.ascontiguousarray(S, np.float64)), _ptr(J), _ptr(R), _ptr(G))
+    return J, R, G
+
+
+def psf_norm2(p: Params, z: int, y: int, x: int) -> float:
+    return lib().orc_psf_norm2(C.byref(p), z, y, x)
 
 
 def log(x: float) -> float:

@@ -16,6 +16,9 @@
  *    (theta_i = region mean, Methods "Bayesian image models"); the energy change of
  *    one flip is the exact single-pixel SSE change.
  *  - Piecewise-smooth data term: local means over a ball of radius R.
+ *  - Deconvolving data term (Eq. 8): sum (I - K * s_theta)^2 with theta the region means,
+ *    K a separable symmetric PSF, zero outside the image; a flip is evaluated with theta
+ *    held (the change of s is at the flipped pixel only).
  *  - Length prior: number of connectivity-adjacent pixel pairs with different labels.
  *  - Eq. 6 sets use the strict cutoff d < E/2, are normalised by their counts, and an
  *    empty set contributes 0; every q uses its pre-update energy difference.
@@ -299,6 +302,87 @@ void orc_stats(const orc_params* p, const void* I, const int32_t* L,
 }
 
 /* ------------------------------------------------------------------ */
+/* Deconvolving model (Eq. 8): the expected image is J = s_theta(Gamma) * K, s_theta the
+ * piecewise-constant image-generating function (theta_i the region means, the usual estimate
+ * named with Eq. 7), K the PSF, zero outside the image. The data term is sum_x (I - J)^2. */
+
+/* one axis of the separable correlation: out(x) = sum_u k(u) f(x + u e_axis) */
+static void psf_axis(const orc_params* p, const double* f, double* out, int axis)
+{
+    int r = p->psf_r;
+    int64_t extent[3] = {p->W, p->H, p->D};
+    int64_t stride[3] = {1, p->W, p->W * p->H};
+    int64_t npix = p->D * p->H * p->W;
+    for (int64_t i = 0; i < npix; i++) {
+        int64_t z, y, x;
+        coords(p, i, &z, &y, &x);
+        int64_t t = axis == 0 ? x : (axis == 1 ? y : z);
+        double acc = 0.0;
+        for (int u = -r; u <= r; u++) {
+            if (t + u < 0 || t + u >= extent[axis]) continue;   /* f = 0 outside */
+            acc = fma(p->psf[u + r], f[i + u * stride[axis]], acc);
+        }
+        out[i] = acc;
+    }
+}
+
+void orc_psf_correlate(const orc_params* p, const double* f, double* out)
+{
+    int64_t npix = p->D * p->H * p->W;
+    double* t = (double*)malloc(sizeof(double) * (size_t)(npix > 0 ? npix : 1));
+    psf_axis(p, f, t, 0);
+    if (p->ndim == 3) {
+        double* t2 = (double*)malloc(sizeof(double) * (size_t)(npix > 0 ? npix : 1));
+        psf_axis(p, t, t2, 1);
+        psf_axis(p, t2, out, 2);
+        free(t2);
+    } else {
+        psf_axis(p, t, out, 1);
+    }
+    free(t);
+}
+
+void orc_deconv_fields(const orc_params* p, const void* I, const int32_t* L,
+                       const int64_t* n, const double* S, double* J, double* R, double* G)
+{
+    int64_t npix = p->D * p->H * p->W;
+    size_t nb = sizeof(double) * (size_t)(npix > 0 ? npix : 1);
+    double* s = (double*)malloc(nb);
+    double* j = (double*)malloc(nb);
+    double* r = (double*)malloc(nb);
+    for (int64_t i = 0; i < npix; i++) {
+        int32_t m = L[i];
+        s[i] = n[m] > 0 ? S[m] / (double)n[m] : 0.0;
+    }
+    orc_psf_correlate(p, s, j);
+    for (int64_t i = 0; i < npix; i++) r[i] = pix(p, I, i) - j[i];
+    orc_psf_correlate(p, r, G);
+    if (J) memcpy(J, j, nb);
+    if (R) memcpy(R, r, nb);
+    free(s);
+    free(j);
+    free(r);
+}
+
+static double psf_norm2_axis(const orc_params* p, int64_t t, int64_t extent)
+{
+    int r = p->psf_r;
+    double acc = 0.0;
+    for (int u = -r; u <= r; u++) {
+        if (t + u < 0 || t + u >= extent) continue;
+        acc = fma(p->psf[u + r], p->psf[u + r], acc);
+    }
+    return acc;
+}
+
+double orc_psf_norm2(const orc_params* p, int64_t z, int64_t y, int64_t x)
+{
+    double v = psf_norm2_axis(p, x, p->W) * psf_norm2_axis(p, y, p->H);
+    if (p->ndim == 3) v = v * psf_norm2_axis(p, z, p->D);
+    return v;
+}
+
+/* ------------------------------------------------------------------ */
 /* Length prior: change of the number of connectivity-adjacent pixel pairs with
  * different labels when x goes from l to c (neighbours outside the image absent). */
 int64_t orc_delta_perimeter(const orc_params* p, const int32_t* L, uint32_t xi, int32_t l, int32_t c)
@@ -340,12 +424,30 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
 {
     int Ri = (int)floor(p->ps_radius);
     double R2 = p->ps_radius * p->ps_radius;
+    double* G = NULL;
+    if (p->model == 3) {
+        int64_t npix = p->D * p->H * p->W;
+        G = (double*)malloc(sizeof(double) * (size_t)(npix > 0 ? npix : 1));
+        orc_deconv_fields(p, I, L, n, S, NULL, NULL, G);
+    }
     for (int64_t k = 0; k < N; k++) {
         uint32_t xi = idx[k];
         int32_t lp = l[k], cp = c[k];
         double v = pix(p, I, xi);
         double data;
-        if (p->model == 0) {
+        if (p->model == 3) {
+            /* Deconvolving: with theta held, moving x from l to c adds d K(. - x) to J, so the
+             * data term changes by sum (R - d K_x)^2 - R^2 = d^2 |K_x|^2 - 2 d (K * R)(x). */
+            int64_t z, y, x;
+            coords(p, xi, &z, &y, &x);
+            double thc = n[cp] > 0 ? S[cp] / (double)n[cp] : 0.0;
+            double thl = n[lp] > 0 ? S[lp] / (double)n[lp] : 0.0;
+            double d = thc - thl;
+            double t = d * G[xi];
+            double q = (d * d) * orc_psf_norm2(p, z, y, x);
+            data = q - (t + t);
+            if (scale) scale[k] = 2.0 * fabs(t) + q;
+        } else if (p->model == 0) {
             /* Piecewise constant: exact SSE change of moving v from region l to c. */
             double mc = S[cp] / (double)n[cp];
             double ml = S[lp] / (double)n[lp];
@@ -406,6 +508,7 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
         dE[k] = data + p->lambda * (double)dP;
         if (scale) scale[k] += fabs(p->lambda * (double)dP);
     }
+    free(G);
 }
 
 /* ------------------------------------------------------------------ */

@@ -22,6 +22,12 @@
  *   orc_energy (Poisson)- f(v, mu_c) - f(v, mu_l), f(v, mu) = mu - v ln mu over the same
  *                         local means; pinned by convolutions and numpy logarithms.
  *   orc_log             - pinned against the C library logarithm within 4 ulp.
+ *   orc_energy (deconv) - -2 d G(x) + d^2 |K_x|^2 with d = theta_c - theta_l, G = K * (I - K * s);
+ *                         pinned by a brute-force recompute of sum (I - K * s)^2 before and
+ *                         after the flip (numpy/scipy, theta held), and by K = delta reducing
+ *                         to the fixed-mean single-pixel SSE change.
+ *   orc_psf_correlate   - pinned by scipy.ndimage.correlate with the outer-product kernel
+ *                         and by the impulse response (exactly the outer product).
  *   orc_energy (length) - pinned by a brute-force recount of the perimeter.
  *   orc_sobolev         - Eq. 6 with a cell list; pinned by all-pairs brute force,
  *                         the degenerate cutoff, and a hand-computed straight line.
@@ -50,7 +56,8 @@ typedef struct {
     int32_t dtype;       /* 0 = float32 image, 1 = uint16 image */
     int64_t D, H, W;     /* D = 1 in 2D; row-major, x fastest */
     int32_t model;       /* 0 = piecewise constant, 1 = piecewise smooth (Gaussian noise),
-                            2 = piecewise smooth with Poisson noise */
+                            2 = piecewise smooth with Poisson noise, 3 = deconvolving piecewise
+                            constant (J = s_theta * K, Eq. 8) */
     int32_t conn;        /* foreground connectivity: 4 (2D) | 6 (3D) */
     double lambda;       /* length weight (Eq. 10) */
     double cutoff;       /* interaction cutoff E/2 in pixels */
@@ -60,6 +67,10 @@ typedef struct {
     int32_t nlabels;     /* M: labels are 0..M-1 */
     int32_t pad_;
     double mu_floor;     /* Poisson model: local means below this are taken as this */
+    int32_t psf_r;       /* deconvolving model: PSF profile radius r (psf has 2r + 1 taps) */
+    int32_t pad2_;
+    const double* psf;   /* deconvolving model: symmetric 1D PSF profile k(-r..r), the same on
+                            every axis (K(x) = prod_axes k(x_a)) */
 } orc_params;
 
 typedef struct {
@@ -90,6 +101,19 @@ int64_t orc_extract(const orc_params* p, const int32_t* L,
                     uint32_t* idx, int32_t* l, int32_t* c, int64_t cap);
 
 double  orc_exact_sum_f32(const float* v, int64_t n, int squares);
+
+/* separable correlation with the PSF, zero outside the image: along x, then y, then z, each
+ * output sum_{u=-r..r} k(u) f(. + u) in ascending u, every term added by one fma */
+void    orc_psf_correlate(const orc_params* p, const double* f, double* out);
+
+/* deconvolving model fields for the current labels: J = K * s_theta (s_theta(x) = theta_L(x),
+ * theta_i = S_i / n_i), R = I - J, G = K * R; J and R may be NULL */
+void    orc_deconv_fields(const orc_params* p, const void* I, const int32_t* L,
+                          const int64_t* n, const double* S, double* J, double* R, double* G);
+
+/* sum over in-image x of K(x - p)^2, factorised per axis: nrm_a(t) = sum_u k(u)^2 over the
+ * u with t + u inside (ascending u, fma); returns the product over the axes */
+double  orc_psf_norm2(const orc_params* p, int64_t z, int64_t y, int64_t x);
 
 void    orc_stats(const orc_params* p, const void* I, const int32_t* L,
                   int64_t* n, double* S, double* Q);

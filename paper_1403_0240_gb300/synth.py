@@ -20,6 +20,9 @@ Workloads (the paper's own images are not available, so these stand in for them)
                    10-60 px) with amplitude U[0.5,1.5] times a linear bias field
                    0.5 + x/(W-1), Poisson noise at 20 photons per unit; initial labels
                    are 32x32 squares on a 64 px pitch.
+* ``deconv_scene`` - 2D float32 scene for the deconvolving model (Eq. 8): four objects
+                   over a faint background, blurred by a Gaussian PSF (sigma 15 px, as in
+                   Figure 3), Poisson noise; the PSF profile travels with the workload.
 * ``ellipsoids`` - 3D uint16 scene: random ellipsoids (semi-axes 4-20 vox) at 300
                    over background 100, Gaussian blur sigma 1.5 (radius 6, clamped
                    edges), Poisson noise; initial labels are 16^3 cubes on a 32 pitch.
@@ -141,13 +144,14 @@ class Workload:
     name: str
     image: np.ndarray            # float32 (2D) or uint16 (3D); shape (H, W) or (D, H, W)
     labels0: np.ndarray          # int32, same shape; 0 = background
-    model: str                   # "pc" | "ps"
+    model: str                   # "pc" | "ps" | "psp" | "pcd"
     connectivity: int            # 4 (2D) | 6 (3D)
     lam: float                   # length weight lambda (Eq. 10)
     cutoff: float                # interaction cutoff E/2 in pixels
     ps_radius: float = 0.0       # local-mean radius (piecewise-smooth model)
     iterations: int = 50
     extra: dict = field(default_factory=dict)
+    psf: np.ndarray | None = None  # deconvolving model: 1D PSF profile, 2r+1 taps (float64)
 
     @property
     def ndim(self) -> int:
@@ -265,6 +269,58 @@ def _gauss_blur_axis(x: np.ndarray, axis: int, sigma: float, radius: int) -> np.
         src = np.clip(np.arange(n) + k, 0, n - 1)
         out += wk * np.take(x, src, axis=axis)
     return out
+
+
+def gaussian_psf(sigma: float, radius: int | None = None) -> np.ndarray:
+    """Sampled Gaussian profile exp(-u^2 / (2 sigma^2)), u = -r..r (r = ceil(3 sigma) by
+    default), normalised to unit sum; exactly symmetric."""
+    r = int(math.ceil(3.0 * sigma)) if radius is None else int(radius)
+    u = np.arange(-r, r + 1, dtype=np.float64)
+    w = np.exp(-(u * u) / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def _blur_zero(x: np.ndarray, k: np.ndarray) -> np.ndarray:
+    """Separable blur with profile k on every axis, zero outside the array."""
+    r = (k.size - 1) // 2
+    out = x.astype(np.float64)
+    for axis in range(x.ndim):
+        n = out.shape[axis]
+        pad = [(0, 0)] * x.ndim
+        pad[axis] = (r, r)
+        xp = np.pad(out, pad)
+        acc = np.zeros_like(out)
+        for j, wk in enumerate(k):
+            acc += wk * np.take(xp, np.arange(j, j + n), axis=axis)
+        out = acc
+    return out
+
+
+def deconv_scene(H: int = 512, W: int = 512, seed: int = 11, sigma: float = 15.0, photons: float = 10.0,
+                 lam: float = 0.04, cutoff: float = 5.0, iterations: int = 200) -> Workload:
+    """Deconvolution scene: four objects (two disks, a square, an ellipse) at intensities
+    2-4 over background 0.25, blurred by a Gaussian PSF of width sigma (zero outside the
+    image), Poisson noise at `photons` per unit; initial labels are squares on a grid."""
+    rs = Stream(seed, 4)
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    clean = np.full((H, W), 0.25)
+    amp = rs.uniform_range(2.0, 4.0, 4)
+    jit = rs.uniform_range(-0.05, 0.05, 8).reshape(4, 2)
+    s = min(H, W)
+    cy = np.array([0.28, 0.30, 0.72, 0.70]) * H + jit[:, 0] * s
+    cx = np.array([0.28, 0.72, 0.30, 0.70]) * W + jit[:, 1] * s
+    clean[(yy - cy[0]) ** 2 + (xx - cx[0]) ** 2 <= (0.12 * s) ** 2] = amp[0]
+    clean[(yy - cy[1]) ** 2 + (xx - cx[1]) ** 2 <= (0.08 * s) ** 2] = amp[1]
+    clean[(np.abs(yy - cy[2]) <= 0.10 * s) & (np.abs(xx - cx[2]) <= 0.10 * s)] = amp[2]
+    clean[((yy - cy[3]) / (0.06 * s)) ** 2 + ((xx - cx[3]) / (0.14 * s)) ** 2 <= 1.0] = amp[3]
+    psf = gaussian_psf(sigma)
+    blurred = _blur_zero(clean, psf)
+    counts = rs.poisson(photons * blurred)
+    image = (counts.astype(np.float64) / photons).astype(np.float32)
+    pitch = max(8, s // 4)
+    labels0 = square_grid_labels(H, W, pitch, pitch // 2)
+    return Workload("deconv", image, labels0, "pcd", 4, lam, cutoff, 0.0, iterations,
+                    {"seed": seed, "sigma": sigma, "photons": photons}, psf)
 
 
 def ellipsoids(D: int = 256, H: int = 256, W: int = 256, seed: int = 2, n_ellipsoids: int | None = None,
