@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Sobolev particle-iterations/s"
 UNIT = "particle-iterations/s"
-STAGES = ("extract", "sobolev", "flag", "fixup", "select", "lists", "rounds", "moves", "finish")
+STAGES = ("psf", "extract", "sobolev", "flag", "fixup", "select", "lists", "rounds", "moves", "finish")
 L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic bytes per unit (one particle, or one accepted move) of each stage: the
@@ -55,10 +55,42 @@ def workloads():
         "disks128": (lambda seed: synth.disks(seed=seed) if seed == 0 else synth.disks(128, 128, seed=seed),
                      "2D 128x128 float32 piecewise constant: two disks, Gaussian noise 0.3; centred 64x64 square; "
                      "cutoff 3, lambda 0.04, 50 iterations"),
+        "deconv512": (lambda seed: synth.deconv_scene(seed=11 + seed),
+                      "2D 512x512 float32, deconvolving piecewise-constant model (Eq. 8): four objects over a faint "
+                      "background blurred by a Gaussian PSF sigma 15 px (r = 45, as in Figure 3), Poisson noise (10 "
+                      "photons); 64x64 squares on a 128 px pitch; cutoff 5, lambda 0.04, 200 iterations"),
         "ellipsoids256": (lambda seed: synth.ellipsoids(seed=2 + seed),
                           "3D 256^3 uint16 piecewise constant: 200 ellipsoids, blur 1.5, Poisson noise; 16^3 cubes on a "
                           "32 pitch; cutoff 4, lambda 1600, 100 iterations"),
     }
+
+
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64, nominal
+
+
+def psf_passes(w) -> int:
+    """Field passes the deconvolving model adds to an iteration (2D: 3, 3D: 5)."""
+    if w.model != "pcd":
+        return 0
+    return 3 if w.image.ndim == 2 else 5
+
+
+def psf_pass_flops(w) -> float:
+    """FP64 flops (2 per fused multiply-add) of one iteration's field passes: every pixel of
+    a pass takes the taps whose offset stays inside the image along the pass's axis."""
+    import numpy as np
+    r = (w.psf.size - 1) // 2
+    shape = w.image.shape
+    npix = float(np.prod(shape))
+
+    def taps(n):
+        t = np.arange(n)
+        return float((np.minimum(r, n - 1 - t) + np.minimum(r, t) + 1).sum())
+
+    per_axis = [taps(n) * npix / n for n in shape[::-1]]       # x, y[, z]
+    fmas = per_axis[0] + per_axis[1] + per_axis[0] if len(shape) == 2 else \
+        per_axis[0] + per_axis[1] + per_axis[2] + per_axis[0] + per_axis[1]
+    return 2.0 * fmas
 
 
 def read_peaks():
@@ -199,7 +231,7 @@ def aggregate(pg, units: float, seconds: float) -> tuple[float, float, float]:
 def oracle_sample(w, seconds: float = 12.0, max_iters: int = 400):
     """The CPU oracle as it stands, single-threaded, on the first iterations of the job."""
     import oracle
-    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius)
+    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius, psf=w.psf)
     run = oracle.Run(p, w.image, w.labels0)
     t0 = time.perf_counter()
     parts, its = 0, 0
@@ -486,7 +518,7 @@ def run_reference(args, world, rank):
     make, desc = workloads()[name]
     w = make(0)
     import oracle
-    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius)
+    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius, psf=w.psf)
     run = oracle.Run(p, w.image, w.labels0)
     for _ in range(args.warmup):
         run.step()
@@ -540,7 +572,7 @@ def run_ours(args, world, rank, local, pg):
 
     def new_ctx(profile):
         c = seg.Context(img_d, lab_d, model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
-                        ps_radius=w.ps_radius, osc_window=0, stream=stream, **settings)
+                        ps_radius=w.ps_radius, osc_window=0, stream=stream, psf=w.psf, **settings)
         c.profile(profile)
         return c
 
@@ -631,7 +663,7 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     c2 = seg.Context(img_h, lab_h, model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
-                     ps_radius=w.ps_radius, osc_window=0, stream=stream, **settings)
+                     ps_radius=w.ps_radius, osc_window=0, stream=stream, psf=w.psf, **settings)
     for _ in range(k_e2e):
         s2 = c2.step(1)
     c2.labels(out=out_h)
@@ -640,7 +672,7 @@ def run_ours(args, world, rank, local, pg):
     e2e_parts = allsum(pg, float(s2["particles_total"]))
     e2e_t = allmax(pg, e2e_t)
     c2.close()
-    in_bytes = w.image.nbytes + w.labels0.nbytes
+    in_bytes = w.image.nbytes + w.labels0.nbytes + (w.psf.nbytes if w.psf is not None else 0)
     status_bytes = 200     # the per-step counter record read back by seg_step
     e2e = {"value": e2e_parts / e2e_t, "unit": UNIT,
            "h2d_bytes_per_step": int(math.ceil(in_bytes / k_e2e)),
@@ -653,14 +685,23 @@ def run_ours(args, world, rank, local, pg):
     dom = max(mean_stage, key=mean_stage.get)
     mean_parts = particles / args.steps
     stage_mean_parts = stage_parts / n_stage
-    per_p, per_move = ALG_BYTES[dom]
-    alg_bytes = per_p * stage_mean_parts + per_move * (accepted / args.steps)
-    peak, peak_kind = read_peaks()
-    achieved = alg_bytes / (mean_stage[dom] / 1000.0) / 1e9
-    traffic = traffic_from_profile(dom, name, stage_mean_parts)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": dom, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": mean_stage[dom]}
+    if dom == "psf":
+        # the deconvolving model's FP64 field passes: bound by the FP64 pipe
+        flops = psf_pass_flops(w)
+        achieved = flops / (mean_stage[dom] / 1000.0) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": "psf (k_psf_pass x3)",
+                    "peak_source": "nominal FP64 (no measured FP64 figure)", "algorithmic_flops_per_launch": flops,
+                    "mean_launch_ms": mean_stage[dom]}
+    else:
+        per_p, per_move = ALG_BYTES[dom]
+        alg_bytes = per_p * stage_mean_parts + per_move * (accepted / args.steps)
+        peak, peak_kind = read_peaks()
+        achieved = alg_bytes / (mean_stage[dom] / 1000.0) / 1e9
+        traffic = traffic_from_profile(dom, name, stage_mean_parts)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "kernel": dom, "peak_source": peak_kind,
+                    "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": mean_stage[dom]}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -669,7 +710,8 @@ def run_ours(args, world, rank, local, pg):
                "sample": f"first {its} iterations of the same job ({secs:.1f} s), single-threaded FP64 C oracle"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if w.model == "pcd" else "f32",
+            "data": "synthetic",
             "config": {"workload": name, "description": desc, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed iterations (256 MiB write)",
                        "iterations_per_job": iters_per_job, "mean_particles": mean_parts,
@@ -681,7 +723,7 @@ def run_ours(args, world, rank, local, pg):
                                     "decisions, exact region sums"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             # per step: the nine stage kernels of the iteration graph plus the status gather of poll()
-            "gpu_launches": (len(STAGES) + 1) * args.steps, "clocks": clocks,
+            "gpu_launches": (len(STAGES) + psf_passes(w)) * args.steps, "clocks": clocks,
             "stages_ms": {k: round(v, 5) for k, v in mean_stage.items()},
             "stage_pass": {"steps": n_stage, "ms_per_step": stage_dev_ms / n_stage,
                            "note": "per-stage CUDA events inside the iteration graph (serialises the "

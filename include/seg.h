@@ -55,7 +55,16 @@ enum { SEG_F32 = 0, SEG_U16 = 1 };                 /* image element type */
  * means over a ball of radius R, Gaussian noise); piecewise smooth with Poisson noise: the
  * data term of a pixel is mu - I ln mu for its local mean mu (the log(I!) term dropped), the
  * means floored at 2^-20 max(1, max I); intensities must be >= 0 */
-enum { SEG_PC = 0, SEG_PS = 1, SEG_PS_POISSON = 2 };
+enum { SEG_PC = 0, SEG_PS = 1, SEG_PS_POISSON = 2, SEG_PC_DECONV = 3 };
+/* SEG_PC_DECONV, the deconvolving piecewise-constant model (Methods, Eq. 8: the expected image
+ * is J = s_theta(Gamma) * K, K the microscope's point-spread function): s_theta(x) = theta of
+ * the region of x, theta the region means; K = k(x) k(y) [k(z)], a symmetric 1D profile k
+ * given by seg_set_psf, zero outside the image. Data term sum_x (I(x) - J(x))^2; a move of x
+ * from l to c is evaluated with theta held: dE = d^2 |K_x|^2 - 2 d G(x) + lambda dP with
+ * d = theta_c - theta_l, G = K * (I - J) and |K_x|^2 = sum over in-image y of K(y - x)^2.
+ * J and G are recomputed every iteration in FP64 by separable passes along x, then y, then z,
+ * each output the fused multiply-add chain sum_{u=-r..r} k(u) f(. + u) in ascending u. */
+#define SEG_PSF_MAX_RADIUS 512
 /* gradient type at start. SEG_SOBOLEV_GLOBAL: Eq. 6 with the length scale of the inner
  * product set to the contour length, E = |Gamma| (Length scale section), |Gamma| read as the
  * number of connectivity-adjacent pixel pairs with different labels (the length prior's
@@ -73,7 +82,7 @@ typedef struct {
     int32_t ndim;          /* 2 | 3 */
     int32_t dtype;         /* SEG_F32 | SEG_U16 */
     int64_t shape[3];      /* {D, H, W}; D = 1 in 2D; row-major, x fastest; each >= 1, D*H*W < 2^31 */
-    int32_t model;         /* SEG_PC | SEG_PS | SEG_PS_POISSON */
+    int32_t model;         /* SEG_PC | SEG_PS | SEG_PS_POISSON | SEG_PC_DECONV */
     int32_t connectivity;  /* foreground: 4 (2D) | 6 (3D); background uses 8 | 26 */
     double  lambda;        /* length weight (Eq. 10), >= 0 */
     double  cutoff;        /* interaction cutoff E/2 in pixels, > 0; E = 2 * cutoff, eps = 1/24 */
@@ -165,6 +174,14 @@ int seg_autotune(const seg_params* p, const void* image, const int32_t* labels0,
 int seg_init(const seg_params* p, const void* image, const int32_t* labels0,
              void* cuda_stream, seg_ctx** out);
 
+/* Deconvolving model (SEG_PC_DECONV, Eq. 8): set the PSF profile k(-radius..radius), 2 radius + 1
+ * host doubles, read during the call; finite and symmetric (k(u) == k(-u) exactly);
+ * 0 <= radius <= SEG_PSF_MAX_RADIUS. The PSF is K = k(x) k(y) [k(z)] on every axis. Required
+ * before the first step of such a context (a step without it returns SEG_ESTATE); may be
+ * called again between steps, the next iteration then uses the new PSF. Synchronises the
+ * context's stream. Errors: SEG_EINVAL (arguments), SEG_ESTATE (another model). */
+int seg_set_psf(seg_ctx* c, const double* k, int32_t radius);
+
 /* Run iters iterations (iters >= 0) on the context's stream, replaying one
  * captured CUDA graph per iteration, and wait for them. If out is not NULL it
  * receives the status of the last iteration. Returns the device error code if
@@ -179,9 +196,10 @@ int seg_step_async(seg_ctx* c, int32_t iters);
 int seg_poll(seg_ctx* c, seg_status* out);
 
 /* Stage timing: when on, the captured iteration graph also records CUDA events
- * between its stages (extract, sobolev, flag, fixup, select, lists, rounds, moves,
- * finish); seg_stage_times waits for the stream and writes the milliseconds each stage
- * took in the most recent iteration (n >= 9), returning SEG_ESTATE when timing is off. */
+ * between its stages (psf, extract, sobolev, flag, fixup, select, lists, rounds, moves,
+ * finish; psf is the deconvolving model's field passes, empty for the other models);
+ * seg_stage_times waits for the stream and writes the milliseconds each stage took in the
+ * most recent iteration (n >= 10), returning SEG_ESTATE when timing is off. */
 int seg_profile(seg_ctx* c, int32_t on);
 int seg_stage_times(seg_ctx* c, float* ms, int32_t n);
 

@@ -275,7 +275,9 @@ __device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
     coords(J, gi, x, y, z);
     const double v = image64(J, gi);
     double data;
-    if (J.model == SEG_PC) {
+    if (J.model == SEG_PC_DECONV) {
+        data = deconv_data64(J, J.dc_G[gi], x, y, z, l, c);   // G stored by extraction
+    } else if (J.model == SEG_PC) {
         double a = __dsub_rn(v, J.mu64[c]);
         double b = __dsub_rn(v, J.mu64[l]);
         double t1 = __dmul_rn(J.wp64[c], __dmul_rn(a, a));

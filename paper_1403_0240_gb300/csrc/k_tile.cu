@@ -638,7 +638,25 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         J.cell_start[cid] = base + s_cstart[kc];
         J.cell_count[cid] = s_cstart[kc + 1] - s_cstart[kc];
     }
-    if (J.model == SEG_PC || !fits) return;
+    if (J.model == SEG_PC_DECONV && fits) {
+        // deconvolving model: one particle per thread; G at the pixel (the last separable pass,
+        // FP64), then the FP64 energy difference rounded once: |dE - dE64| <= 2^-24 |dE| + 2^-150
+        for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
+            const unsigned gi = J.p_idx[o2];
+            const int own = J.p_l[o2], c = J.p_c[o2];
+            int x, y, z;
+            pix_coords(J, gi, x, y, z);
+            const double G = deconv_G(J, gi, y, z);
+            J.dc_G[gi] = G;                         // for the FP64 recompute (same value per particle)
+            const double e64 = __dadd_rn(deconv_data64(J, G, x, y, z, own, c),
+                                         __dmul_rn(J.lambda64, (double)delta_p(sidx(x, y, z), own, c)));
+            const float dE = __double2float_rn(e64);
+            J.p_dE[o2] = dE;
+            J.p_eE[o2] = fabsf(dE) * kU + 1.5e-45f;
+        }
+        return;
+    }
+    if (!is_ps(J.model) || !fits) return;
 
     // piecewise-smooth energy: one particle per thread over the dense range of this tile's
     // particles, so every thread runs the same ball loop

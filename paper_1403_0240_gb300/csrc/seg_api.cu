@@ -198,13 +198,14 @@ struct Stepper {
     bool use_graph = true;
     bool dirty = true;
     bool any_global = false;       // a member uses E = |Gamma| (adds its two launches to the step)
+    bool any_deconv = false;       // a member uses the deconvolving model (adds its PSF passes)
     bool profile = false;
-    cudaEvent_t ev[10]{};
+    cudaEvent_t ev[11]{};
     cudaStream_t work = nullptr;   // library stream: graphs are captured and launched here
     cudaEvent_t fence_in = nullptr, fence_out = nullptr;
 };
 
-constexpr int kStages = 9;
+constexpr int kStages = 10;
 
 struct seg_batch {
     Stepper st;
@@ -223,11 +224,12 @@ int validate(const seg_params* p)
     if (p->ndim == 2 && p->shape[0] != 1) return SEG_EINVAL;
     long double npix = (long double)p->shape[0] * p->shape[1] * p->shape[2];
     if (npix >= 2147483647.0L) return SEG_EINVAL;
-    if (p->model != SEG_PC && p->model != SEG_PS && p->model != SEG_PS_POISSON) return SEG_EINVAL;
+    if (p->model != SEG_PC && p->model != SEG_PS && p->model != SEG_PS_POISSON && p->model != SEG_PC_DECONV)
+        return SEG_EINVAL;
     if ((p->ndim == 2 && p->connectivity != 4) || (p->ndim == 3 && p->connectivity != 6)) return SEG_EINVAL;
     if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return SEG_EINVAL;
     if (!(p->cutoff > 0.0) || p->cutoff > 32.0) return SEG_EINVAL;
-    if (p->model != SEG_PC && (!(p->ps_radius >= 1.0) || p->ps_radius > 64.0)) return SEG_EINVAL;
+    if (is_ps(p->model) && (!(p->ps_radius >= 1.0) || p->ps_radius > 64.0)) return SEG_EINVAL;
     if (p->gradient != SEG_SOBOLEV && p->gradient != SEG_L2 && p->gradient != SEG_SOBOLEV_GLOBAL) return SEG_EINVAL;
     if (p->gradient == SEG_SOBOLEV_GLOBAL) {
         // the E = |Gamma| kernel table spans every squared distance in the image
@@ -307,7 +309,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     h.ntz = (h.ncz + h.tcz - 1) / h.tcz;
     h.ntiles = h.ntx * h.nty * h.ntz;
     const int R = (int)std::floor(p->ps_radius);
-    h.ps_staged = (h.model != SEG_PC && h.ndim == 2 && R <= 32) ? 1 : 0;
+    h.ps_staged = (is_ps(h.model) && h.ndim == 2 && R <= 32) ? 1 : 0;
     h.halo = h.ps_staged ? std::max(1, R) : 1;
     h.lambda64 = p->lambda;
     h.lambda32 = (float)p->lambda;
@@ -331,7 +333,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
         P.klut[d2] = (float)P.klut64[d2];
     }
     const int rz = h.ndim == 3 ? 1 : 0;
-    if (h.model != SEG_PC) {
+    if (is_ps(h.model)) {
         const double R2 = p->ps_radius * p->ps_radius;
         for (int dz = -R * rz; dz <= R * rz; dz++)
             for (int dy = -R; dy <= R; dy++)
@@ -357,7 +359,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     const int qbits = h.dtype == SEG_F32 ? 23 + nS : 16;
     h.e_min = h.dtype == SEG_F32 ? slot_lo - 150 : 0;
     const bool unit_ok = h.e_min >= -120 && h.e_min <= 100;
-    h.ps_int = (h.model != SEG_PC && unit_ok && qbits + lg + 1 <= 62) ? 1 : 0;
+    h.ps_int = (is_ps(h.model) && unit_ok && qbits + lg + 1 <= 62) ? 1 : 0;
     h.ps_exact64 = (h.ps_int && qbits + lg <= 53) ? 1 : 0;
     h.ps_q32 = (h.ps_int && h.dtype == SEG_F32 && qbits <= 31) ? 1 : 0;
     h.unit32 = unit_ok ? std::ldexp(1.0f, h.e_min) : 0.0f;
@@ -391,6 +393,15 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     A.add((int4**)&h.nb_off, P.nb_off.size());
     A.add(&h.gK32, (size_t)h.gd2max + 1);
     A.add(&h.gK64, (size_t)h.gd2max + 1);
+    h.psf_r = -1;
+    if (h.model == SEG_PC_DECONV) {
+        A.add(&h.psf, 2 * SEG_PSF_MAX_RADIUS + 1);
+        A.add(&h.psf_n, (size_t)h.W + h.H + h.D);
+        A.add(&h.dc_T, npix);
+        if (h.ndim == 3) A.add(&h.dc_T2, npix);
+        A.add(&h.dc_R, npix);
+        A.add(&h.dc_G, npix);
+    }
     A.add(&h.ctr, 1);
 }
 
@@ -574,9 +585,12 @@ int stepper_build(Stepper& s)
     std::vector<int> ids;
     std::vector<unsigned> prefix;
     s.any_global = false;
+    s.any_deconv = false;
     for (int i = 0; i < n; i++) {
         jobs[i] = s.members[i]->h;
+        if (jobs[i].model == SEG_PC_DECONV && jobs[i].psf_r < 0) return SEG_ESTATE;   // no PSF yet
         s.any_global = s.any_global || jobs[i].global_E;
+        s.any_deconv = s.any_deconv || jobs[i].model == SEG_PC_DECONV;
     }
     int id_off[2] = {0, 0}, pf_off[2] = {0, 0};
     for (int gidx = 0; gidx < 2; gidx++) {
@@ -651,32 +665,38 @@ cudaError_t stepper_enqueue_stages(Stepper& s)
     cudaError_t e;
     const int n = (int)s.members.size();
     if ((e = stage_mark(s, 0)) != cudaSuccess) return e;
+    if (s.any_deconv)                   // the deconvolving model's fields, before extraction reads them
+        for (int i = 0; i < n; i++)
+            if (s.members[i]->h.model == SEG_PC_DECONV &&
+                (e = launch_deconv(s.d_jobs, i, s.members[i]->h, s.sms, s.work)) != cudaSuccess)
+                return e;
+    if ((e = stage_mark(s, 1)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_extract(s.grp[gidx], gidx + 2, s.smem_x[gidx], s.work)) != cudaSuccess) return e;
-    if ((e = stage_mark(s, 1)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 2)) != cudaSuccess) return e;
     if (s.any_global && (e = launch_global_lut(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_sobolev(s.grp[gidx], gidx + 2, s.smem_s[gidx], s.work)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.any_global && s.grp[gidx].njobs && (e = launch_sobolev_global(s.grp[gidx], gidx + 2, s.work)) != cudaSuccess)
             return e;
-    if ((e = stage_mark(s, 2)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 3)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_flag(s.grp[gidx], s.work)) != cudaSuccess) return e;
-    if ((e = stage_mark(s, 3)) != cudaSuccess) return e;
-    if ((e = launch_fixup(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 4)) != cudaSuccess) return e;
+    if ((e = launch_fixup(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 5)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_select(s.grp[gidx], s.d_bc, s.work)) != cudaSuccess) return e;
-    if ((e = stage_mark(s, 5)) != cudaSuccess) return e;
-    if ((e = launch_lists(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 6)) != cudaSuccess) return e;
-    if ((e = launch_rounds(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.work)) != cudaSuccess) return e;
+    if ((e = launch_lists(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 7)) != cudaSuccess) return e;
-    if ((e = launch_moves(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
+    if ((e = launch_rounds(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 8)) != cudaSuccess) return e;
+    if ((e = launch_moves(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 9)) != cudaSuccess) return e;
     if ((e = launch_finish(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
-    return stage_mark(s, 9);
+    return stage_mark(s, 10);
 }
 
 int stepper_set_profile(Stepper& s, bool on)
@@ -1336,6 +1356,26 @@ void seg_batch_destroy(seg_batch* b)
     for (auto* c : b->st.members) c->batch = nullptr;
     stepper_release(b->st);
     delete b;
+}
+
+int seg_set_psf(seg_ctx* c, const double* k, int32_t radius)
+{
+    if (!c || !k || radius < 0 || radius > SEG_PSF_MAX_RADIUS) return SEG_EINVAL;
+    if (c->h.model != SEG_PC_DECONV) return SEG_ESTATE;
+    for (int u = 0; u <= 2 * radius; u++)
+        if (!std::isfinite(k[u]) || k[u] != k[2 * radius - u]) return SEG_EINVAL;
+    int rc = ensure_device(c->device);
+    if (rc) return rc;
+    if (c->batch) CK(cudaStreamSynchronize(c->batch->st.stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->h.psf_r = radius;
+    CK(cudaMemcpyAsync(c->h.psf, k, sizeof(double) * (2 * radius + 1), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_self, &c->h, sizeof(Job), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_psf_norms(c->d_self, c->h, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->own->dirty = true;                       // the steppers' job tables are rebuilt
+    if (c->batch) c->batch->st.dirty = true;
+    return SEG_OK;
 }
 
 int seg_debug_inject(seg_ctx* c, int32_t what)

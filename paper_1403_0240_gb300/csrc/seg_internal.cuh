@@ -34,6 +34,9 @@ struct WaitBound {
     }
 };
 
+// region models whose data term uses local means over a ball (the piecewise-smooth ones)
+__host__ __device__ __forceinline__ bool is_ps(int model) { return model == SEG_PS || model == SEG_PS_POISSON; }
+
 constexpr unsigned char kFlagFixup = 1, kFlagCand = 2, kFlagAcc = 4;
 constexpr int kUndecided = 0, kAccepted = 1, kRejected = 2;
 
@@ -125,6 +128,13 @@ struct alignas(64) Job {
     int gd2max;               // ... largest squared distance within the image
     float* gK32;              // ... K(sqrt(d2)) for E = |Gamma| of the iteration, float
     double* gK64;             // ... and FP64 (Eq. 5 in the order written); 0 outside the support
+    int psf_r;                // deconvolving model: PSF profile radius, -1 until seg_set_psf
+    double* psf;              // ... taps k(-r..r) (room for 2 SEG_PSF_MAX_RADIUS + 1)
+    double* psf_n;            // ... per axis sum of k(u)^2 over the in-image offsets: x [W], y [H], z [D]
+    double* dc_T;             // ... FP64 fields of the separable passes [npix]
+    double* dc_T2;            // ... (3D) [npix]
+    double* dc_R;             // ... R = I - J [npix]
+    double* dc_G;             // ... G = K * R at the particle pixels of the iteration [npix]
     int M;                    // number of labels
     int osc_window;           // L2 fallback window (0 = never)
     int inject;               // test-only fault injection (SEG_INJECT_*)
@@ -265,6 +275,36 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl* bc, unsigned nblocks)
     return ld_volatile(&bc->err) == 0;
 }
 
+// Deconvolving model: the last separable pass of G = K * R at pixel gi (along y in 2D, z in
+// 3D), over the field the other passes left, taps in ascending offset, fused multiply-adds.
+__device__ __forceinline__ double deconv_G(const Job& J, unsigned gi, int y, int z)
+{
+    const int r = J.psf_r;
+    const bool d3 = J.ndim == 3;
+    const int t = d3 ? z : y;
+    const int extent = d3 ? J.D : J.H;
+    const long long stride = d3 ? (long long)J.W * J.H : (long long)J.W;
+    const double* f = d3 ? J.dc_T2 : J.dc_T;
+    const int lo = max(-r, -t), hi = min(r, extent - 1 - t);
+    long long q = (long long)gi + (long long)lo * stride;
+    double acc = 0.0;
+    for (int u = lo; u <= hi; u++, q += stride) acc = __fma_rn(J.psf[u + r], f[q], acc);
+    return acc;
+}
+
+// ... and its data-term change for moving the pixel at (x, y, z) from l to c with theta held:
+// d^2 |K_x|^2 - 2 d G, d = theta_c - theta_l, |K_x|^2 the product of the per-axis tables;
+// every operation rounded separately in the order written.
+__device__ __forceinline__ double deconv_data64(const Job& J, double G, int x, int y, int z, int l, int c)
+{
+    const double d = __dsub_rn(J.mu64[c], J.mu64[l]);
+    const double t = __dmul_rn(d, G);
+    double np = __dmul_rn(J.psf_n[x], J.psf_n[J.W + y]);
+    if (J.ndim == 3) np = __dmul_rn(np, J.psf_n[J.W + J.H + z]);
+    const double q = __dmul_rn(__dmul_rn(d, d), np);
+    return __dsub_rn(q, __dadd_rn(t, t));
+}
+
 // What seg_init needs to know about its inputs, found on the device in one pass.
 struct InputScan {
     int lab_min, lab_max;          // smallest and largest label
@@ -323,6 +363,8 @@ cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, in
 cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s);
+cudaError_t launch_deconv(const Job* jobs, int j, const Job& h, int sms, cudaStream_t s);
+cudaError_t launch_psf_norms(const Job* job, const Job& h, cudaStream_t s);
 cudaError_t launch_scan_inputs(const void* I, int dtype, const int* L, int ndim, int D, int H, int W, InputScan* out,
                                cudaStream_t s);
 cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s);

@@ -16,7 +16,9 @@ from . import build as _build
 
 SEG_OK, SEG_EINVAL, SEG_ENOMEM, SEG_ECUDA, SEG_ETIMEOUT, SEG_ESTATE = 0, -1, -2, -3, -4, -5
 SEG_F32, SEG_U16 = 0, 1
-SEG_PC, SEG_PS, SEG_PS_POISSON = 0, 1, 2
+SEG_PC, SEG_PS, SEG_PS_POISSON, SEG_PC_DECONV = 0, 1, 2, 3
+SEG_PSF_MAX_RADIUS = 512
+MODELS = {"pc": SEG_PC, "ps": SEG_PS, "psp": SEG_PS_POISSON, "pcd": SEG_PC_DECONV}
 SEG_SOBOLEV, SEG_L2, SEG_SOBOLEV_GLOBAL = 0, 1, 2
 SEG_STATS_EXACT = 0
 SEG_INJECT_NONE, SEG_INJECT_UNPUBLISHED_TILE = 0, 1
@@ -62,6 +64,7 @@ SIGNATURES = [
     ("seg_autotune", C.c_int, [_P(Params), _V, _V, C.c_int32, _V, _P(Params), _P(TuneEntry), C.c_int32,
                                _P(C.c_int32)]),
     ("seg_init", C.c_int, [_P(Params), _V, _V, _V, _P(_V)]),
+    ("seg_set_psf", C.c_int, [_V, _P(C.c_double), C.c_int32]),
     ("seg_step", C.c_int, [_V, C.c_int32, _P(Status)]),
     ("seg_step_async", C.c_int, [_V, C.c_int32]),
     ("seg_poll", C.c_int, [_V, _P(Status)]),
@@ -168,7 +171,7 @@ def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_ra
     p.ndim = len(shape)
     p.dtype = _dtype_code(image)
     p.shape[0], p.shape[1], p.shape[2] = (1,) + shape if len(shape) == 2 else shape
-    p.model = model if isinstance(model, int) else {"pc": SEG_PC, "ps": SEG_PS, "psp": SEG_PS_POISSON}[model]
+    p.model = model if isinstance(model, int) else MODELS[model]
     p.connectivity = connectivity or (4 if len(shape) == 2 else 6)
     p.lam = float(lam)
     p.cutoff = float(cutoff)
@@ -215,7 +218,8 @@ class Context:
     """One segmentation job resident on the GPU (seg_init ... seg_destroy)."""
 
     def __init__(self, image, labels0, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_radius=0.0,
-                 gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None, stream=None):
+                 gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None, stream=None,
+                 psf=None):
         self.params = make_params(image, model, connectivity, lam, cutoff, ps_radius, gradient, osc_window,
                                   validate, cell_edge, tile)
         self.shape = tuple(int(s) for s in image.shape)
@@ -230,11 +234,25 @@ class Context:
         lib().seg_info(h, C.byref(nl), None)
         self.nlabels = int(nl.value)
         self.npix = int(np.prod(self.shape))
+        if psf is not None:
+            try:
+                self.set_psf(psf)
+            except Exception:
+                self.close()
+                raise
+
+    def set_psf(self, psf):
+        """Deconvolving model: the symmetric 1D PSF profile, 2r+1 taps (seg_set_psf)."""
+        k = np.ascontiguousarray(psf, dtype=np.float64).reshape(-1)
+        if k.size % 2 != 1:
+            raise ValueError("the PSF profile needs an odd number of taps")
+        _check(lib().seg_set_psf(self.handle, k.ctypes.data_as(C.POINTER(C.c_double)), (k.size - 1) // 2),
+               "seg_set_psf")
 
     @classmethod
     def from_workload(cls, w, **kw) -> "Context":
         args = dict(model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
-                    ps_radius=w.ps_radius)
+                    ps_radius=w.ps_radius, psf=getattr(w, "psf", None))
         args.update(kw)
         return cls(w.image, w.labels0, **args)
 
@@ -257,7 +275,7 @@ class Context:
         _check(lib().seg_poll(self.handle, C.byref(st)), "seg_poll")
         return st.as_dict()
 
-    STAGES = ("extract", "sobolev", "flag", "fixup", "select", "lists", "rounds", "moves", "finish")
+    STAGES = ("psf", "extract", "sobolev", "flag", "fixup", "select", "lists", "rounds", "moves", "finish")
 
     def inject(self, what: int):
         """Test-only fault injection (seg_debug_inject)."""

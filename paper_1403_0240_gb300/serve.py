@@ -27,7 +27,7 @@ class Request:
     image: np.ndarray
     labels0: np.ndarray
     iterations: int
-    params: dict = field(default_factory=dict)   # model, connectivity, lam, cutoff, ps_radius, ...
+    params: dict = field(default_factory=dict)   # model, connectivity, lam, cutoff, ps_radius, psf, ...
     nlabels: int | None = None     # largest initial label + 1 (found from labels0 when None)
 
 
@@ -62,7 +62,7 @@ class SegBackend:
     def estimate(self, req: Request) -> int:
         if req.nlabels is None:
             req.nlabels = int(req.labels0.max()) + 1
-        p = self.seg.make_params(req.image, **_param_kwargs(req))
+        p = self.seg.make_params(req.image, **_param_kwargs(req, with_psf=False))
         return self.seg.estimate_bytes(p, req.nlabels)
 
     def create(self, req: Request):
@@ -89,9 +89,12 @@ class SegBackend:
         self.batch.close()
 
 
-def _param_kwargs(req: Request) -> dict:
+def _param_kwargs(req: Request, with_psf: bool = True) -> dict:
     keys = ("model", "connectivity", "lam", "cutoff", "ps_radius", "gradient", "osc_window", "cell_edge", "tile")
-    return {k: req.params[k] for k in keys if k in req.params}
+    out = {k: req.params[k] for k in keys if k in req.params}
+    if with_psf and req.params.get("psf") is not None:
+        out["psf"] = req.params["psf"]          # deconvolving model: set after seg_init
+    return out
 
 
 class Server:

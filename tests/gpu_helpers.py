@@ -15,10 +15,11 @@ REL_TOL = 1e-5
 def pair(w, gradient="sobolev", osc_window=0, cell_edge=0, lam=None, cutoff=None):
     lam = w.lam if lam is None else lam
     cutoff = w.cutoff if cutoff is None else cutoff
+    psf = getattr(w, "psf", None)
     ctx = seg.Context(w.image, w.labels0, model=w.model, connectivity=w.connectivity, lam=lam, cutoff=cutoff,
-                      ps_radius=w.ps_radius, gradient=gradient, osc_window=osc_window, cell_edge=cell_edge)
+                      ps_radius=w.ps_radius, gradient=gradient, osc_window=osc_window, cell_edge=cell_edge, psf=psf)
     p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, lam, cutoff, w.ps_radius,
-                           gradient=gradient, osc_window=osc_window)
+                           gradient=gradient, osc_window=osc_window, psf=psf)
     return ctx, oracle.Run(p, w.image, w.labels0)
 
 

@@ -18,3 +18,19 @@ def test_pc_energy_two_regions():
     L = np.array([[0, 0, 1, 1]], np.int32)
     # means 2 and 12: SSE = 1 + 1 + 4 + 4; one boundary pair
     assert bench._pc_energy(I, L, 0.5) == 10.0 + 0.5
+
+
+def test_psf_pass_flops_counts_the_in_image_taps():
+    from paper_1403_0240_gb300 import synth
+    for shape, sigma in [((9, 13), 1.5), ((5, 7, 6), 1.0), ((4, 30), 3.0)]:
+        w = synth.disks(8, 8)
+        w.model, w.image, w.psf = "pcd", np.zeros(shape, np.float32), synth.gaussian_psf(sigma)
+        r = (w.psf.size - 1) // 2
+        axes = [len(shape) - 1 - a for a in range(len(shape))]           # numpy axis of x, y[, z]
+        passes = [axes[0], axes[1], axes[0]] if len(shape) == 2 else [axes[0], axes[1], axes[2], axes[0], axes[1]]
+        brute = 0
+        for ax in passes:
+            for pos in np.ndindex(*shape):
+                brute += sum(1 for u in range(-r, r + 1) if 0 <= pos[ax] + u < shape[ax])
+        assert bench.psf_pass_flops(w) == 2.0 * brute
+        assert bench.psf_passes(w) == len(passes)

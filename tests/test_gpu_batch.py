@@ -24,7 +24,8 @@ def _jobs():
     e.labels0 = np.zeros((5, 3), np.int32)
     e.labels0[1:3, 1] = 1
     f = synth.ellipsoids(16, 16, 16, seed=10)
-    return [a, b, c, d, e, f]
+    g = synth.deconv_scene(72, 88, seed=12, sigma=2.5)
+    return [a, b, c, d, e, f, g]
 
 
 def _solo(w, iters):
@@ -111,11 +112,12 @@ def test_batch_rejects_double_membership():
 def test_served_jobs_equal_solo():
     from paper_1403_0240_gb300.serve import Request, SegBackend, Server
     jobs = _jobs()
-    iters = [8, 12, 10, 6, 9, 11]
+    iters = [8, 12, 10, 6, 9, 11, 7]
     refs = [_solo(w, n) for w, n in zip(jobs, iters)]
 
     def params(w):
-        return dict(model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff, ps_radius=w.ps_radius)
+        return dict(model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff, ps_radius=w.ps_radius,
+                    psf=w.psf)
 
     backend = SegBackend()
     reqs = [Request(i, 0.0, w.image, w.labels0, n, params(w)) for i, (w, n) in enumerate(zip(jobs, iters))]
