@@ -333,6 +333,82 @@ def run_batch(args, world, rank, local, pg):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args, world, rank, local, pg):
+    """Region-sum precision study on the 512-image batch (50 iterations): the batch stepped with
+    exact, FP64 and compensated-FP32 region sums. Per mode: throughput, the largest relative
+    error of S, Q and the variance Q/n - mu^2 against the exact sums of the same final labels,
+    and the pixels whose final label differs from the exact-mode run."""
+    import numpy as np
+    import torch
+
+    from paper_1403_0240_gb300 import seg, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    iters = args.steps
+    jobs = synth.batch_disks(args.images, seed0=1000 + 100000 * rank, iterations=iters)
+    dev_jobs = [(torch.from_numpy(w.image).to(dev), torch.from_numpy(w.labels0).to(dev), w) for w in jobs]
+
+    def run(mode, n=None, steps=iters):
+        ctxs = [seg.Context(i, l, model=w.model, lam=w.lam, cutoff=w.cutoff, stream=stream, stats=mode)
+                for i, l, w in dev_jobs[:n]]
+        b = seg.Batch(stream=stream)
+        for c in ctxs:
+            b.add(c)
+        b.poll()
+        torch.cuda.synchronize(dev)
+        barrier(pg)
+        t0 = time.perf_counter()
+        st = b.step(steps)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter() - t0
+        parts = sum(x["particles_total"] for x in st)
+        b.close()
+        return ctxs, parts, t
+
+    for mode in ("exact", "f64", "kahan32"):            # warm-up: graph capture and code paths
+        ctxs, _, _ = run(mode, 8, args.warmup)
+        for c in ctxs:
+            c.close()
+    out, ref_labels = {}, None
+    for mode in ("exact", "f64", "kahan32"):
+        ctxs, parts, t = run(mode)
+        labels = [c.labels() for c in ctxs]
+        err = {"S": 0.0, "Q": 0.0, "var": 0.0}
+        for c, (img, _, w), L in zip(ctxs, dev_jobs, labels):
+            n, S, Q = c.stats()
+            ne, Se, Qe = (x.cpu().numpy() for x in seg.region_stats_noalloc(
+                img, torch.from_numpy(L).to(dev), c.nlabels, stream=stream))
+            assert np.array_equal(n, ne)
+            m = n > 0
+            for key, a, e in (("S", S, Se), ("Q", Q, Qe)):
+                err[key] = max(err[key], float((np.abs(a[m] - e[m]) / np.maximum(np.abs(e[m]), 1e-300)).max()))
+            var = Q[m] / n[m] - (S[m] / n[m]) ** 2
+            var_e = Qe[m] / n[m] - (Se[m] / n[m]) ** 2
+            err["var"] = max(err["var"], float((np.abs(var - var_e) / np.maximum(np.abs(var_e), 1e-300)).max()))
+        for c in ctxs:
+            c.close()
+        if ref_labels is None:
+            ref_labels = labels
+        diff = sum(int((a != b).sum()) for a, b in zip(labels, ref_labels))
+        same = sum(int(np.array_equal(a, b)) for a, b in zip(labels, ref_labels))
+        parts_all, t_all = allsum(pg, float(parts)), allmax(pg, t)
+        out[mode] = {"value": parts_all / t_all, "seconds": t_all, "max_rel_err_S": err["S"],
+                     "max_rel_err_Q": err["Q"], "max_rel_err_variance": err["var"],
+                     "label_pixels_differing_from_exact": diff, "jobs_with_labels_equal_to_exact": same}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": out["exact"]["value"], "unit": UNIT, "n_gpus": world, "steps": iters,
+            "warmup": args.warmup, "ms_per_step": 1000 * out["exact"]["seconds"] / iters, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "precision", "description": f"{args.images} 2D float32 disk images (the batch512 "
+                       "set), one batch stepped together per region-sum mode; errors against the exact sums of "
+                       "each run's final labels", "images": args.images, "modes": out,
+                       "timing": "wall clock around whole-batch steps (synchronised)"}}
+    print(json.dumps(line), flush=True)
+
+
 def _pool_workload(kind, side, cache):
     """Synthetic job images, one per (kind, side rounded to a bucket), reused by arrivals."""
     from paper_1403_0240_gb300 import synth
@@ -738,7 +814,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ellipses1024", choices=sorted(list(workloads().keys()) + ["batch512", "served", "convergence"]))
+    ap.add_argument("--workload", default="ellipses1024", choices=sorted(list(workloads().keys()) + ["batch512", "served", "convergence", "precision"]))
     ap.add_argument("--images", type=int, default=512, help="batch512: images in the batch")
     ap.add_argument("--jobs", type=int, default=2000, help="served: jobs in the arrival stream")
     ap.add_argument("--job-iters", type=int, default=100, help="served: iterations per job")
@@ -767,6 +843,8 @@ def main():
         run_served(args, world, rank, local, pg)
     elif args.workload == "convergence":
         run_convergence(args, world, rank, local, pg)
+    elif args.workload == "precision":
+        run_precision(args, world, rank, local, pg)
     else:
         run_ours(args, world, rank, local, pg)
     if pg is not None:

@@ -73,7 +73,16 @@ enum { SEG_PC = 0, SEG_PS = 1, SEG_PS_POISSON = 2, SEG_PC_DECONV = 3 };
  * variant to future work as too costly on its CPU). The cutoff parameter only sizes the cell
  * list in this mode. */
 enum { SEG_SOBOLEV = 0, SEG_L2 = 1, SEG_SOBOLEV_GLOBAL = 2 };
-enum { SEG_STATS_EXACT = 0 };                      /* region sums exact, rounded once to FP64 */
+/* region sums of I and I^2 (precision study; counts are exact int64 in every mode):
+ * SEG_STATS_EXACT   - exact (int64 fixed point), rounded once to FP64: the means are the FP64
+ *                     definition's bit for bit, results are reproducible (default);
+ * SEG_STATS_F64     - FP64 sums (atomic adds, order not fixed);
+ * SEG_STATS_KAHAN32 - compensated FP32 sums: a (sum, compensation) pair of floats per sum, each
+ *                     addition a Neumaier step applied atomically (order not fixed).
+ * In the two inexact modes the means carry the sums' rounding error: decisions are certified
+ * and recomputed against FP64 evaluations that use those means, and results may vary from run
+ * to run. seg_stats reports the sums each mode keeps. */
+enum { SEG_STATS_EXACT = 0, SEG_STATS_F64 = 1, SEG_STATS_KAHAN32 = 2 };
 
 typedef struct seg_ctx seg_ctx;
 typedef struct seg_batch seg_batch;
@@ -90,7 +99,7 @@ typedef struct {
     int32_t gradient;      /* SEG_SOBOLEV | SEG_L2 | SEG_SOBOLEV_GLOBAL */
     int32_t osc_window;    /* switch to L2 once the accepted-move count has not reached a new
                               minimum for this many iterations; 0 = never switch */
-    int32_t stats_mode;    /* SEG_STATS_EXACT */
+    int32_t stats_mode;    /* SEG_STATS_EXACT | SEG_STATS_F64 | SEG_STATS_KAHAN32 */
     int32_t validate;      /* nonzero: check on the host that every foreground label of labels0
                               is one connected component (else SEG_EINVAL) */
     int32_t cell_edge;     /* cell-list edge in pixels, >= ceil(cutoff); 0 = ceil(cutoff) */

@@ -626,10 +626,59 @@ __device__ __forceinline__ void atomic_add_ll(long long* a, long long v)
     atomicAdd((unsigned long long*)a, (unsigned long long)v);
 }
 
+// Compensated FP32 sums (SEG_STATS_KAHAN32): add a then b to the (sum, compensation) float
+// pair at p, each by one Neumaier step (Neumaier 1974: the rounding error of every addition is
+// accumulated in the compensation), the pair updated atomically by compare-and-swap. Retries
+// happen only when another thread's update landed; they are bounded all the same.
+__device__ __forceinline__ unsigned long long neumaier2(unsigned long long pair, float a, float b)
+{
+    float s = __uint_as_float((unsigned)pair), c = __uint_as_float((unsigned)(pair >> 32));
+    for (int k = 0; k < 2; k++) {
+        const float v = k ? b : a;
+        const float t = __fadd_rn(s, v);
+        const float e = fabsf(s) >= fabsf(v) ? __fadd_rn(__fsub_rn(s, t), v) : __fadd_rn(__fsub_rn(v, t), s);
+        c = __fadd_rn(c, e);
+        s = t;
+    }
+    return (unsigned long long)__float_as_uint(s) | ((unsigned long long)__float_as_uint(c) << 32);
+}
+
+__device__ void kahan_add(unsigned long long* p, float a, float b, Counters* ctr)
+{
+    unsigned long long old = ld_volatile(p);
+    for (unsigned tries = 0; tries < kSpinLimit; tries++) {
+        const unsigned long long got = atomicCAS(p, old, neumaier2(old, a, b));
+        if (got == old) return;
+        old = got;
+    }
+    atomicExch(&ctr->error, SEG_ETIMEOUT);
+}
+
+// the value and its exact square split into float head + tail (two-product by fused multiply-add)
+__device__ __forceinline__ void value_parts(const Job& J, long long i, float& v, float& q, float& qe)
+{
+    v = J.dtype == SEG_U16 ? (float)((const unsigned short*)J.I)[i] : ((const float*)J.I)[i];
+    q = __fmul_rn(v, v);
+    qe = __fmaf_rn(v, v, -q);
+}
+
 // one pixel of value at index i joins (sign +1) or leaves (sign -1) label m
 __device__ __forceinline__ void stats_move(const Job& J, long long i, int m, int sign)
 {
     atomic_add_ll(J.st_n + m, sign);
+    if (J.stats_mode == SEG_STATS_F64) {
+        const double v = J.dtype == SEG_U16 ? (double)((const unsigned short*)J.I)[i] : (double)((const float*)J.I)[i];
+        atomicAdd(J.sf64 + m, sign * v);
+        atomicAdd(J.sf64 + J.M + m, sign * (v * v));       // exact: at most 48 significant bits
+        return;
+    }
+    if (J.stats_mode == SEG_STATS_KAHAN32) {
+        float v, q, qe;
+        value_parts(J, i, v, q, qe);
+        kahan_add(J.sk32 + m, sign * v, 0.0f, J.ctr);
+        kahan_add(J.sk32 + J.M + m, sign * q, sign * qe, J.ctr);
+        return;
+    }
     if (J.dtype == SEG_U16) {
         long long v = ((const unsigned short*)J.I)[i];
         atomic_add_ll(J.st_S + m, sign * v);
@@ -716,12 +765,22 @@ __device__ void finalize_label(const Job& J, int m, bool with_Q)
 {
     long long n = J.st_n[m];
     double S;
-    if (J.dtype == SEG_U16) {
+    if (J.stats_mode == SEG_STATS_EXACT && J.dtype == SEG_U16) {
         S = __ll2double_rn(J.st_S[m]);
         if (with_Q) J.Q64[m] = __ll2double_rn(J.st_Q[m]);
-    } else {
+    } else if (J.stats_mode == SEG_STATS_EXACT) {
         S = round_bins(J.st_S + (long long)m * J.nS, J.nS, J.slot_lo - 150);
         if (with_Q) J.Q64[m] = round_bins(J.st_Q + (long long)m * J.nQ, J.nQ, 2 * (J.slot_lo - 150));
+    } else if (J.stats_mode == SEG_STATS_F64) {
+        S = J.sf64[m];
+        if (with_Q) J.Q64[m] = J.sf64[J.M + m];
+    } else {
+        const unsigned long long ps = J.sk32[m];
+        S = __dadd_rn((double)__uint_as_float((unsigned)ps), (double)__uint_as_float((unsigned)(ps >> 32)));
+        if (with_Q) {
+            const unsigned long long pq = J.sk32[J.M + m];
+            J.Q64[m] = __dadd_rn((double)__uint_as_float((unsigned)pq), (double)__uint_as_float((unsigned)(pq >> 32)));
+        }
     }
     const double dn = (double)n;
     const double mu = n > 0 ? __ddiv_rn(S, dn) : 0.0;
@@ -761,6 +820,37 @@ __global__ void __launch_bounds__(256) k_stats_init(const Job* jobs, int j)
         bool valid = i < n;
         int m = valid ? J.L[i] : 0;
         warp_add((unsigned long long)m, valid, 1, J.st_n + m);
+        if (J.stats_mode != SEG_STATS_EXACT) {
+            // inexact modes: the peers of one label add their values lane by lane (FP64, or
+            // compensated FP32), the group's first lane applies the result
+            const unsigned peers = __match_any_sync(0xffffffffu, valid ? (unsigned)m : 0xffffffffu);
+            float v = 0.0f, q = 0.0f, qe = 0.0f;
+            if (valid) value_parts(J, i, v, q, qe);
+            const int lane = threadIdx.x & 31;
+            if (J.stats_mode == SEG_STATS_F64) {
+                double s = 0.0, s2 = 0.0;
+                for (int k = 0; k < 32; k++) {
+                    const double vk = (double)__shfl_sync(0xffffffffu, v, k);
+                    if ((peers >> k) & 1u) { s = __dadd_rn(s, vk); s2 = __dadd_rn(s2, __dmul_rn(vk, vk)); }
+                }
+                if (valid && lane == __ffs(peers) - 1) {
+                    atomicAdd(J.sf64 + m, s);
+                    atomicAdd(J.sf64 + J.M + m, s2);
+                }
+            } else {
+                unsigned long long ps = 0, pq = 0;
+                for (int k = 0; k < 32; k++) {
+                    const float vk = __shfl_sync(0xffffffffu, v, k);
+                    const float qk = __shfl_sync(0xffffffffu, q, k), ek = __shfl_sync(0xffffffffu, qe, k);
+                    if ((peers >> k) & 1u) { ps = neumaier2(ps, vk, 0.0f); pq = neumaier2(pq, qk, ek); }
+                }
+                if (valid && lane == __ffs(peers) - 1) {
+                    kahan_add(J.sk32 + m, __uint_as_float((unsigned)ps), __uint_as_float((unsigned)(ps >> 32)), J.ctr);
+                    kahan_add(J.sk32 + J.M + m, __uint_as_float((unsigned)pq), __uint_as_float((unsigned)(pq >> 32)), J.ctr);
+                }
+            }
+            continue;
+        }
         if (J.dtype == SEG_U16) {
             long long v = valid ? ((const unsigned short*)J.I)[i] : 0;
             warp_add((unsigned long long)m, valid, v, J.st_S + m);

@@ -239,7 +239,8 @@ int validate(const seg_params* p)
         if (d2 >= (long double)(1 << 24)) return SEG_EINVAL;
     }
     if (p->osc_window < 0) return SEG_EINVAL;
-    if (p->stats_mode != SEG_STATS_EXACT) return SEG_EINVAL;
+    if (p->stats_mode != SEG_STATS_EXACT && p->stats_mode != SEG_STATS_F64 && p->stats_mode != SEG_STATS_KAHAN32)
+        return SEG_EINVAL;
     int need = (int)std::ceil(p->cutoff);
     if (p->cell_edge != 0 && (p->cell_edge < need || p->cell_edge > 256)) return SEG_EINVAL;
     for (int i = 0; i < 3; i++)
@@ -379,6 +380,9 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     A.add(&h.st_n, M);
     A.add(&h.st_S, (size_t)M * (h.dtype == SEG_F32 ? h.nS : 1));
     A.add(&h.st_Q, (size_t)M * (h.dtype == SEG_F32 ? h.nQ : 1));
+    h.stats_mode = p->stats_mode;
+    if (h.stats_mode == SEG_STATS_F64) A.add(&h.sf64, 2 * (size_t)M);
+    if (h.stats_mode == SEG_STATS_KAHAN32) A.add(&h.sk32, 2 * (size_t)M);
     A.add(&h.S64, M);
     A.add(&h.Q64, M);
     A.add(&h.mu64, M);
@@ -1058,6 +1062,8 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     CKF(cudaMemsetAsync(c->h.st_n, 0, (size_t)M * 8, stream));
     CKF(cudaMemsetAsync(c->h.st_S, 0, (size_t)M * (p->dtype == SEG_F32 ? c->h.nS : 1) * 8, stream));
     CKF(cudaMemsetAsync(c->h.st_Q, 0, (size_t)M * (p->dtype == SEG_F32 ? c->h.nQ : 1) * 8, stream));
+    if (c->h.sf64) CKF(cudaMemsetAsync(c->h.sf64, 0, 2 * (size_t)M * 8, stream));
+    if (c->h.sk32) CKF(cudaMemsetAsync(c->h.sk32, 0, 2 * (size_t)M * 8, stream));
     CKF(cudaMemcpyAsync((void*)c->h.klut, P.klut.data(), P.klut.size() * 4, cudaMemcpyHostToDevice, stream));
     CKF(cudaMemcpyAsync((void*)c->h.klut64, P.klut64.data(), P.klut64.size() * 8, cudaMemcpyHostToDevice, stream));
     if (!P.ps_off.empty())

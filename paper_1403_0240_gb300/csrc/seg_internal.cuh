@@ -167,6 +167,9 @@ struct alignas(64) Job {
     long long* st_n;          // [M]
     long long* st_S;          // u16: [M]; f32: [M * nS] mantissa sums per exponent slot
     long long* st_Q;          // u16: [M]; f32: [M * nQ] 24-bit limbs of squared mantissas
+    int stats_mode;           // SEG_STATS_*: the sums of I and I^2 above are kept only when exact
+    double* sf64;             // SEG_STATS_F64: [2M] S then Q per label
+    unsigned long long* sk32; // SEG_STATS_KAHAN32: [2M] (sum | compensation << 32) float pairs, S then Q
     double* S64;
     double* Q64;
     double* mu64;

@@ -20,7 +20,8 @@ SEG_PC, SEG_PS, SEG_PS_POISSON, SEG_PC_DECONV = 0, 1, 2, 3
 SEG_PSF_MAX_RADIUS = 512
 MODELS = {"pc": SEG_PC, "ps": SEG_PS, "psp": SEG_PS_POISSON, "pcd": SEG_PC_DECONV}
 SEG_SOBOLEV, SEG_L2, SEG_SOBOLEV_GLOBAL = 0, 1, 2
-SEG_STATS_EXACT = 0
+SEG_STATS_EXACT, SEG_STATS_F64, SEG_STATS_KAHAN32 = 0, 1, 2
+STATS_MODES = {"exact": SEG_STATS_EXACT, "f64": SEG_STATS_F64, "kahan32": SEG_STATS_KAHAN32}
 SEG_INJECT_NONE, SEG_INJECT_UNPUBLISHED_TILE = 0, 1
 
 
@@ -165,7 +166,7 @@ def _stream_handle(stream):
 
 
 def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_radius=0.0,
-                gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None) -> Params:
+                gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None, stats="exact") -> Params:
     shape = tuple(int(s) for s in image.shape)
     p = Params()
     p.ndim = len(shape)
@@ -179,7 +180,7 @@ def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_ra
     p.gradient = gradient if isinstance(gradient, int) else {"sobolev": SEG_SOBOLEV, "l2": SEG_L2,
                                                                   "sobolev_global": SEG_SOBOLEV_GLOBAL}[gradient]
     p.osc_window = int(osc_window)
-    p.stats_mode = SEG_STATS_EXACT
+    p.stats_mode = stats if isinstance(stats, int) else STATS_MODES[stats]
     p.validate = int(bool(validate))
     p.cell_edge = int(cell_edge)
     if tile is not None:
@@ -219,9 +220,9 @@ class Context:
 
     def __init__(self, image, labels0, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_radius=0.0,
                  gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None, stream=None,
-                 psf=None):
+                 psf=None, stats="exact"):
         self.params = make_params(image, model, connectivity, lam, cutoff, ps_radius, gradient, osc_window,
-                                  validate, cell_edge, tile)
+                                  validate, cell_edge, tile, stats)
         self.shape = tuple(int(s) for s in image.shape)
         ip, ikeep = _ptr(image)
         lp, lkeep = _ptr(labels0 if _is_torch(labels0) else np.asarray(labels0, dtype=np.int32))
