@@ -66,6 +66,9 @@ def workloads():
 
 
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64, nominal
+# kernels of one iteration's graph: extract, sobolev, flag, fixup, select, lists, rounds, moves,
+# finish (plus the deconvolving model's field passes); poll() adds one
+KERNELS_PER_ITERATION = 9
 
 
 def psf_passes(w) -> int:
@@ -798,8 +801,8 @@ def run_ours(args, world, rank, local, pg):
                        "precision": "float32 gradients with certified bounds, FP64 recompute of uncertified "
                                     "decisions, exact region sums"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            # per step: the nine stage kernels of the iteration graph plus the status gather of poll()
-            "gpu_launches": (len(STAGES) + psf_passes(w)) * args.steps, "clocks": clocks,
+            # per step: the kernels of the iteration graph plus the status gather of poll()
+            "gpu_launches": (KERNELS_PER_ITERATION + 1 + psf_passes(w)) * args.steps, "clocks": clocks,
             "stages_ms": {k: round(v, 5) for k, v in mean_stage.items()},
             "stage_pass": {"steps": n_stage, "ms_per_step": stage_dev_ms / n_stage,
                            "note": "per-stage CUDA events inside the iteration graph (serialises the "

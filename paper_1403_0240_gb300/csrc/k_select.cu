@@ -388,37 +388,63 @@ __device__ __forceinline__ int job_of(const unsigned* s_pref, int njobs, unsigne
     return lo;
 }
 
-constexpr int kFixWarps = 8;
-constexpr int kFixTerms = 32 * 6;
+constexpr int kFixThreads = 128;             // one block per queued particle
+constexpr int kFixTerms = 6 * kFixThreads;     // at most 6 particles per pixel
 
-__global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int njobs)
+// Block-wide exclusive prefix of v (kFixThreads threads); the total goes to *total.
+__device__ __forceinline__ int block_excl(int v, int* s_w, int* total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int k = 0; k < kFixThreads / 32; k++) {
+        if (k < w) before += s_w[k];
+        all += s_w[k];
+    }
+    *total = all;
+    return before + x - v;
+}
+
+// FP64 recompute of the queued particles' keys in the order of the definition, one block per
+// particle: every thread takes one interaction offset (row-major, i.e. ascending pixel) and
+// the particles of that pixel in order, so that the dependent loads of all offsets overlap;
+// one thread then sums the terms in ascending key order.
+__global__ void __launch_bounds__(kFixThreads) k_fixup(const Job* jobs, int njobs)
 {
     pdl_enter();
-    __shared__ double s_t[kFixWarps][kFixTerms];
-    __shared__ unsigned char s_a[kFixWarps][kFixTerms];
+    __shared__ double s_t[kFixTerms];
+    __shared__ unsigned char s_a[kFixTerms];
     __shared__ unsigned s_pref[kMaxBatchJobs + 1];
     __shared__ unsigned s_tmp[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned gw = blockIdx.x * kFixWarps + w, nw = gridDim.x * kFixWarps;
+    __shared__ int s_w[kFixThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned total = block_job_prefix(jobs, njobs, kCountFlag, s_pref, s_tmp);
-    {
-        for (unsigned fi = gw; fi < total; fi += nw) {
-            const int j = job_of(s_pref, njobs, fi);
-            const Job& J = jobs[j];
-            Counters* ctr = J.ctr;
-            const unsigned f = fi - s_pref[j];
-            const unsigned tag = ld_volatile(&ctr->iter_tag);
-            const unsigned np = ld_volatile(&ctr->n_particles);
-            const int mode = ld_volatile(&ctr->mode);
-            const unsigned p = J.flag_list[f];
-            const unsigned gi = J.p_idx[p];
-            const int lp = J.p_l[p], cp = J.p_c[p];
-            double gval;
-            if (mode == SEG_L2) {
-                gval = lane == 0 ? energy64(J, gi, lp, cp, p) : 0.0;
-            } else if (mode == SEG_SOBOLEV_GLOBAL) {
+    for (unsigned fi = blockIdx.x; fi < total; fi += gridDim.x) {
+        const int j = job_of(s_pref, njobs, fi);
+        const Job& J = jobs[j];
+        Counters* ctr = J.ctr;
+        const unsigned f = fi - s_pref[j];
+        const unsigned tag = ld_volatile(&ctr->iter_tag);
+        const unsigned np = ld_volatile(&ctr->n_particles);
+        const int mode = ld_volatile(&ctr->mode);
+        const unsigned p = J.flag_list[f];
+        const unsigned gi = J.p_idx[p];
+        const int lp = J.p_l[p], cp = J.p_c[p];
+        if (mode == SEG_L2) {
+            if (tid == 0) J.p_key[p] = energy64(J, gi, lp, cp, p);
+        } else if (mode == SEG_SOBOLEV_GLOBAL) {
+            if (w == 0) {
                 // E = |Gamma|: every particle with d^2 < g_lim, in ascending key order (the pixels
-                // of the support's bounding box in row-major order, particles of a pixel in order)
+                // of the support's bounding box in row-major order, particles of a pixel in order);
+                // one warp walks the box
+                double gval;
                 int x, y, z;
                 coords(J, gi, x, y, z);
                 const long long lim = J.ctr->g_lim;
@@ -465,16 +491,16 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int n
                         for (unsigned q = q0; q < np && J.p_idx[q] == yi; q++) {
                             const int lq = J.p_l[q], cq = J.p_c[q];
                             if (lq != lp && cq != lp) continue;
-                            s_t[w][pos] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
-                            s_a[w][pos] = lq == lp ? 1 : 0;
+                            s_t[pos] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
+                            s_a[pos] = lq == lp ? 1 : 0;
                             pos++;
                         }
                     }
                     __syncwarp();
                     if (lane == 0) {
                         for (int u = 0; u < tot; u++) {
-                            if (s_a[w][u]) { As = __dadd_rn(As, s_t[w][u]); nA++; }
-                            else { Bs = __dadd_rn(Bs, s_t[w][u]); nB++; }
+                            if (s_a[u]) { As = __dadd_rn(As, s_t[u]); nA++; }
+                            else { Bs = __dadd_rn(Bs, s_t[u]); nB++; }
                         }
                     }
                     __syncwarp();
@@ -482,68 +508,66 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* jobs, int n
                 const double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
                 const double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
                 gval = __dsub_rn(A, B);
-            } else {
-                int x, y, z;
-                coords(J, gi, x, y, z);
-                double As = 0.0, Bs = 0.0;
-                long long nA = 0, nB = 0;
-                for (int base = 0; base < J.nb_n; base += 32) {
-                    const int u = base + lane;
-                    double tv[6];
-                    unsigned char ta[6];
-                    int nt = 0;
-                    if (u < J.nb_n) {
-                        int4 d = J.nb_off[u];
-                        int xx = x + d.z, yy = y + d.y, zz = z + d.x;
-                        if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D) {
-                            unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
-                            unsigned long long e = J.pmap[yi];
-                            if ((unsigned)(e >> 32) == tag) {
-                                const double K = J.klut64[d.w];
-                                for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi && nt < 6; q++) {
-                                    int lq = J.p_l[q], cq = J.p_c[q];
-                                    if (lq == lp || cq == lp) {
-                                        tv[nt] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
-                                        ta[nt] = lq == lp ? 1 : 0;
-                                        nt++;
-                                    }
+                if (lane == 0) J.p_key[p] = gval;
+            }
+        } else {
+            int x, y, z;
+            coords(J, gi, x, y, z);
+            double As = 0.0, Bs = 0.0;
+            long long nA = 0, nB = 0;
+            for (int base = 0; base < J.nb_n; base += kFixThreads) {
+                const int u = base + tid;
+                double tv[6];
+                unsigned char ta[6];
+                int nt = 0;
+                if (u < J.nb_n) {
+                    const int4 d = J.nb_off[u];
+                    const int xx = x + d.z, yy = y + d.y, zz = z + d.x;
+                    if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D) {
+                        const unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
+                        const unsigned long long e = J.pmap[yi];
+                        if ((unsigned)(e >> 32) == tag) {
+                            const double K = J.klut64[d.w];
+                            for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi && nt < 6; q++) {
+                                const int lq = J.p_l[q], cq = J.p_c[q];
+                                if (lq == lp || cq == lp) {
+                                    tv[nt] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
+                                    ta[nt] = lq == lp ? 1 : 0;
+                                    nt++;
                                 }
                             }
                         }
                     }
-                    int incl = nt;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        int v = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += v;
-                    }
-                    const int tot = __shfl_sync(0xffffffffu, incl, 31);
-                    for (int i = 0; i < nt; i++) {
-                        s_t[w][incl - nt + i] = tv[i];
-                        s_a[w][incl - nt + i] = ta[i];
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        for (int i = 0; i < tot; i++) {
-                            if (s_a[w][i]) { As = __dadd_rn(As, s_t[w][i]); nA++; }
-                            else { Bs = __dadd_rn(Bs, s_t[w][i]); nB++; }
-                        }
-                    }
-                    __syncwarp();
                 }
-                double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
-                double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
-                gval = __dsub_rn(A, B);
+                int tot;
+                const int pos = block_excl(nt, s_w, &tot);
+                for (int i = 0; i < nt; i++) {
+                    s_t[pos + i] = tv[i];
+                    s_a[pos + i] = ta[i];
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    for (int i = 0; i < tot; i++) {
+                        if (s_a[i]) { As = __dadd_rn(As, s_t[i]); nA++; }
+                        else { Bs = __dadd_rn(Bs, s_t[i]); nB++; }
+                    }
+                }
+                __syncthreads();
             }
-            if (lane == 0) J.p_key[p] = gval;
+            if (tid == 0) {
+                const double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
+                const double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
+                J.p_key[p] = __dsub_rn(A, B);
+            }
         }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s)
 {
     if (njobs <= 0) return cudaSuccess;
-    return launch_stage(k_fixup, sms * 2, kFixWarps * 32, 0, s, jobs, njobs);
+    return launch_stage(k_fixup, sms * 8, kFixThreads, 0, s, jobs, njobs);
 }
 
 __global__ void k_gather_counters(const Job* jobs, int njobs, Counters* out)
