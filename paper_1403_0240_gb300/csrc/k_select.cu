@@ -412,6 +412,162 @@ __device__ __forceinline__ int block_excl(int v, int* s_w, int* total)
     return before + x - v;
 }
 
+// E = |Gamma| mode: the FP64 key of particle (gi, lp) over every particle with d^2 < g_lim, in
+// ascending key order (the pixels of the support's bounding box in row-major order, particles
+// of a pixel in order); one warp walks the box, t_w / a_w hold 192 terms. Lane 0's value counts.
+__device__ double fix_global_warp(const Job& J, unsigned gi, int lp, unsigned tag, unsigned np, double* t_w,
+                                  unsigned char* a_w)
+{
+    const int lane = threadIdx.x & 31;
+    int x, y, z;
+    coords(J, gi, x, y, z);
+    const long long lim = J.ctr->g_lim;
+    // largest r with r^2 < lim, from the square root corrected by one step
+    long long r = (long long)sqrt((double)(lim > 0 ? lim - 1 : 0));
+    while (r > 0 && r * r >= lim) r--;
+    while ((r + 1) * (r + 1) < lim) r++;
+    const long long x0 = max(0LL, x - r), x1 = min((long long)J.W - 1, x + r);
+    const long long y0 = max(0LL, y - r), y1 = min((long long)J.H - 1, y + r);
+    const long long z0 = J.ndim == 3 ? max(0LL, z - r) : 0, z1 = J.ndim == 3 ? min((long long)J.D - 1, z + r) : 0;
+    const long long bw = x1 - x0 + 1, bh = y1 - y0 + 1, nbox = bw * bh * (z1 - z0 + 1);
+    double As = 0.0, Bs = 0.0;
+    long long nA = 0, nB = 0;
+    for (long long base0 = 0; base0 < nbox; base0 += 32) {
+        const long long i = base0 + lane;
+        unsigned yi = 0, q0 = 0;
+        long long d2 = 0;
+        bool ok = false;
+        if (i < nbox) {
+            const long long xx = x0 + i % bw, yy = y0 + (i / bw) % bh, zz = z0 + i / (bw * bh);
+            d2 = (xx - x) * (xx - x) + (yy - y) * (yy - y) + (zz - z) * (zz - z);
+            if (d2 < lim) {
+                yi = (unsigned)((zz * J.H + yy) * J.W + xx);
+                const unsigned long long e = J.pmap[yi];
+                ok = (unsigned)(e >> 32) == tag;
+                q0 = (unsigned)e;
+            }
+        }
+        int nt = 0;
+        if (ok)
+            for (unsigned q = q0; q < np && J.p_idx[q] == yi; q++)
+                nt += (J.p_l[q] == lp || J.p_c[q] == lp) ? 1 : 0;
+        if (!__any_sync(0xffffffffu, nt > 0)) continue;
+        int incl = nt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = incl - nt;
+        if (ok && nt) {
+            const double K = J.gK64[d2];
+            for (unsigned q = q0; q < np && J.p_idx[q] == yi; q++) {
+                const int lq = J.p_l[q], cq = J.p_c[q];
+                if (lq != lp && cq != lp) continue;
+                t_w[pos] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
+                a_w[pos] = lq == lp ? 1 : 0;
+                pos++;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            for (int u = 0; u < tot; u++) {
+                if (a_w[u]) { As = __dadd_rn(As, t_w[u]); nA++; }
+                else { Bs = __dadd_rn(Bs, t_w[u]); nB++; }
+            }
+        }
+        __syncwarp();
+    }
+    const double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
+    const double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
+    return __dsub_rn(A, B);
+}
+
+// The same recompute with one queued particle per warp (many queued particles): lanes take
+// the interaction offsets 32 at a time, lane 0 sums each group's terms in ascending key order.
+__device__ void fixup_warps(const Job* jobs, int njobs, unsigned total, const unsigned* s_pref, double* s_t,
+                            unsigned char* s_a)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int kWarps = kFixThreads / 32, kWarpTerms = kFixTerms / kWarps;
+    double* t_w = s_t + w * kWarpTerms;
+    unsigned char* a_w = s_a + w * kWarpTerms;
+    for (unsigned fi = blockIdx.x * kWarps + w; fi < total; fi += gridDim.x * kWarps) {
+        const int j = job_of(s_pref, njobs, fi);
+        const Job& J = jobs[j];
+        Counters* ctr = J.ctr;
+        const unsigned tag = ld_volatile(&ctr->iter_tag);
+        const unsigned np = ld_volatile(&ctr->n_particles);
+        const int mode = ld_volatile(&ctr->mode);
+        const unsigned p = J.flag_list[fi - s_pref[j]];
+        const unsigned gi = J.p_idx[p];
+        const int lp = J.p_l[p], cp = J.p_c[p];
+        if (mode == SEG_L2) {
+            if (lane == 0) J.p_key[p] = energy64(J, gi, lp, cp, p);
+            continue;
+        }
+        if (mode == SEG_SOBOLEV_GLOBAL) {
+            const double gval = fix_global_warp(J, gi, lp, tag, np, t_w, a_w);
+            if (lane == 0) J.p_key[p] = gval;
+            continue;
+        }
+        int x, y, z;
+        coords(J, gi, x, y, z);
+        double As = 0.0, Bs = 0.0;
+        long long nA = 0, nB = 0;
+        for (int base = 0; base < J.nb_n; base += 32) {
+            const int u = base + lane;
+            double tv[6];
+            unsigned char ta[6];
+            int nt = 0;
+            if (u < J.nb_n) {
+                const int4 d = J.nb_off[u];
+                const int xx = x + d.z, yy = y + d.y, zz = z + d.x;
+                if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D) {
+                    const unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
+                    const unsigned long long e = J.pmap[yi];
+                    if ((unsigned)(e >> 32) == tag) {
+                        const double K = J.klut64[d.w];
+                        for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi && nt < 6; q++) {
+                            const int lq = J.p_l[q], cq = J.p_c[q];
+                            if (lq == lp || cq == lp) {
+                                tv[nt] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
+                                ta[nt] = lq == lp ? 1 : 0;
+                                nt++;
+                            }
+                        }
+                    }
+                }
+            }
+            int incl = nt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            for (int i = 0; i < nt; i++) {
+                t_w[incl - nt + i] = tv[i];
+                a_w[incl - nt + i] = ta[i];
+            }
+            __syncwarp();
+            if (lane == 0) {
+                for (int i = 0; i < tot; i++) {
+                    if (a_w[i]) { As = __dadd_rn(As, t_w[i]); nA++; }
+                    else { Bs = __dadd_rn(Bs, t_w[i]); nB++; }
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            const double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
+            const double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
+            J.p_key[p] = __dsub_rn(A, B);
+        }
+    }
+}
+
 // FP64 recompute of the queued particles' keys in the order of the definition, one block per
 // particle: every thread takes one interaction offset (row-major, i.e. ascending pixel) and
 // the particles of that pixel in order, so that the dependent loads of all offsets overlap;
@@ -426,6 +582,10 @@ __global__ void __launch_bounds__(kFixThreads) k_fixup(const Job* jobs, int njob
     __shared__ int s_w[kFixThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned total = block_job_prefix(jobs, njobs, kCountFlag, s_pref, s_tmp);
+    if (total > gridDim.x) {                   // many queued particles: one per warp
+        fixup_warps(jobs, njobs, total, s_pref, s_t, s_a);
+        return;
+    }
     for (unsigned fi = blockIdx.x; fi < total; fi += gridDim.x) {
         const int j = job_of(s_pref, njobs, fi);
         const Job& J = jobs[j];
@@ -441,73 +601,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fixup(const Job* jobs, int njob
             if (tid == 0) J.p_key[p] = energy64(J, gi, lp, cp, p);
         } else if (mode == SEG_SOBOLEV_GLOBAL) {
             if (w == 0) {
-                // E = |Gamma|: every particle with d^2 < g_lim, in ascending key order (the pixels
-                // of the support's bounding box in row-major order, particles of a pixel in order);
-                // one warp walks the box
-                double gval;
-                int x, y, z;
-                coords(J, gi, x, y, z);
-                const long long lim = J.ctr->g_lim;
-                // largest r with r^2 < lim, from the square root corrected by one step
-                long long r = (long long)sqrt((double)(lim > 0 ? lim - 1 : 0));
-                while (r > 0 && r * r >= lim) r--;
-                while ((r + 1) * (r + 1) < lim) r++;
-                const long long x0 = max(0LL, x - r), x1 = min((long long)J.W - 1, x + r);
-                const long long y0 = max(0LL, y - r), y1 = min((long long)J.H - 1, y + r);
-                const long long z0 = J.ndim == 3 ? max(0LL, z - r) : 0, z1 = J.ndim == 3 ? min((long long)J.D - 1, z + r) : 0;
-                const long long bw = x1 - x0 + 1, bh = y1 - y0 + 1, nbox = bw * bh * (z1 - z0 + 1);
-                double As = 0.0, Bs = 0.0;
-                long long nA = 0, nB = 0;
-                for (long long base0 = 0; base0 < nbox; base0 += 32) {
-                    const long long i = base0 + lane;
-                    unsigned yi = 0, q0 = 0;
-                    long long d2 = 0;
-                    bool ok = false;
-                    if (i < nbox) {
-                        const long long xx = x0 + i % bw, yy = y0 + (i / bw) % bh, zz = z0 + i / (bw * bh);
-                        d2 = (xx - x) * (xx - x) + (yy - y) * (yy - y) + (zz - z) * (zz - z);
-                        if (d2 < lim) {
-                            yi = (unsigned)((zz * J.H + yy) * J.W + xx);
-                            const unsigned long long e = J.pmap[yi];
-                            ok = (unsigned)(e >> 32) == tag;
-                            q0 = (unsigned)e;
-                        }
-                    }
-                    int nt = 0;
-                    if (ok)
-                        for (unsigned q = q0; q < np && J.p_idx[q] == yi; q++)
-                            nt += (J.p_l[q] == lp || J.p_c[q] == lp) ? 1 : 0;
-                    if (!__any_sync(0xffffffffu, nt > 0)) continue;
-                    int incl = nt;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += v;
-                    }
-                    const int tot = __shfl_sync(0xffffffffu, incl, 31);
-                    int pos = incl - nt;
-                    if (ok && nt) {
-                        const double K = J.gK64[d2];
-                        for (unsigned q = q0; q < np && J.p_idx[q] == yi; q++) {
-                            const int lq = J.p_l[q], cq = J.p_c[q];
-                            if (lq != lp && cq != lp) continue;
-                            s_t[pos] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
-                            s_a[pos] = lq == lp ? 1 : 0;
-                            pos++;
-                        }
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        for (int u = 0; u < tot; u++) {
-                            if (s_a[u]) { As = __dadd_rn(As, s_t[u]); nA++; }
-                            else { Bs = __dadd_rn(Bs, s_t[u]); nB++; }
-                        }
-                    }
-                    __syncwarp();
-                }
-                const double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
-                const double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
-                gval = __dsub_rn(A, B);
+                const double gval = fix_global_warp(J, gi, lp, tag, np, s_t, s_a);
                 if (lane == 0) J.p_key[p] = gval;
             }
         } else {

@@ -55,6 +55,13 @@ def test_ellipsoids_256_one_iteration_after_5():
     assert st["n_particles"] > 1000000
 
 
+def test_ellipsoids_256_many_recomputes():
+    # around iteration 25 thousands of particles are queued for the FP64 recompute (more than
+    # the recompute grid's blocks), so it runs one particle per warp instead of per block
+    st, t = _one_iteration_parity(synth.ellipsoids(), 24)
+    assert st["n_fixup"] > 8 * 152
+
+
 def test_batch512_sampled_jobs_match_oracle():
     """The 512-image batch (sides 64-512, 1-8 disks) stepped together with the batch-tuned
     settings, as the batch benchmark runs it; eight jobs spread over the batch are replayed by
