@@ -1124,6 +1124,7 @@ __device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* s_red)
 
 constexpr unsigned kMaxRounds = 1u << 20;
 constexpr unsigned kSmallCandidates = 32768;   // at most this many: one block decides alone
+constexpr size_t kRoundsDyn = 160 * 1024;      // dynamic shared memory of the rounds kernel
 
 // A: neighbour lists of smaller-key candidates; states reset
 __device__ void commit_list_one(const Job& J, unsigned s)
@@ -1280,14 +1281,104 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
     __shared__ unsigned s_flag;
     __shared__ unsigned s_pref[kMaxBatchJobs + 1];
     __shared__ unsigned char s_state[kSmallCandidates];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
     const unsigned total = block_job_prefix(jobs, njobs, kCountCand, s_pref, s_red);
     if (total <= kSmallCandidates) {
         if (blockIdx.x != 0) return;
         volatile unsigned char* st = s_state;
-        for (unsigned i = threadIdx.x; i < total; i += blockDim.x) st[i] = kUndecided;
+        // The candidates' neighbour lists (compressed rows of 16-bit flattened indices) and a
+        // list of the undecided candidates live in shared memory when they fit; each round then
+        // visits only the undecided candidates.
+        __shared__ unsigned s_cnt3[3];
+        const unsigned chunk = (total + blockDim.x - 1) / blockDim.x;
+        const unsigned c0 = min(threadIdx.x * chunk, total), c1 = min(c0 + chunk, total);
+        unsigned* s_off = (unsigned*)s_dyn;                                 // [total + 1]
+        const size_t off_bytes = ((size_t)(total + 1) * 4 + 15) & ~(size_t)15;
+        unsigned short* s_wl0 = (unsigned short*)(s_dyn + off_bytes);      // [total]
+        unsigned short* s_wl1 = s_wl0 + total;                              // [total]
+        const size_t wl_bytes = ((size_t)total * 4 + 15) & ~(size_t)15;
+        unsigned short* s_nb = (unsigned short*)(s_dyn + off_bytes + wl_bytes);
+        // counts (coalesced), offsets by a block scan over contiguous chunks, then the rows;
+        // nothing is written to the dynamic region unless the offsets and both lists fit
+        const bool room = off_bytes + wl_bytes <= kRoundsDyn;
+        if (room)
+            for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
+                const int j = job_of(s_pref, njobs, i);
+                s_wl1[i] = (unsigned short)jobs[j].c_nnbr[i - s_pref[j]];
+            }
+        __syncthreads();
+        unsigned mine = 0;
+        if (room)
+            for (unsigned i = c0; i < c1; i++) mine += s_wl1[i];
+        unsigned all_nb;
+        const unsigned nb0 = block_excl_scan(mine, s_red, all_nb);
+        const bool cache = room && off_bytes + wl_bytes + (size_t)all_nb * 2 <= kRoundsDyn;   // uniform
+        if (cache) {
+            unsigned o = nb0;
+            for (unsigned i = c0; i < c1; i++) {
+                s_off[i] = o;
+                o += s_wl1[i];
+            }
+            if (threadIdx.x == blockDim.x - 1) s_off[total] = all_nb;
+        }
+        __syncthreads();
+        if (cache) {
+            for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
+                const int j = job_of(s_pref, njobs, i);
+                const Job& J = jobs[j];
+                const int* nb = J.c_nbr + (long long)(i - s_pref[j]) * J.nbr_stride;
+                const unsigned n = s_wl1[i], o = s_off[i], b = s_pref[j];
+#pragma unroll 8
+                for (unsigned k = 0; k < n; k++) s_nb[o + k] = (unsigned short)(b + nb[k]);
+            }
+        }
+        for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
+            st[i] = kUndecided;
+            if (cache) s_wl0[i] = (unsigned short)i;
+        }
+        if (threadIdx.x == 0) s_cnt3[0] = 0;
         __syncthreads();
         unsigned rounds = 0;
         bool ok = true;
+        if (cache) {
+            // one barrier per round: round r appends to s_cnt3[r % 3] while thread 0 clears the
+            // counter of round r + 1 (last read before the barrier that ended round r - 1)
+            unsigned n_cur = total;
+            unsigned short* cur = s_wl0;
+            unsigned short* nxt = s_wl1;
+            const unsigned lane = threadIdx.x & 31;
+            for (unsigned r = 0; n_cur > 0; r++) {
+                if (r >= kMaxRounds) { ok = false; break; }
+                unsigned* cnt = &s_cnt3[r % 3];
+                if (threadIdx.x == 0) s_cnt3[(r + 1) % 3] = 0;
+                for (unsigned t = threadIdx.x; t < n_cur; t += blockDim.x) {
+                    const unsigned i = cur[t];
+                    bool all_rej = true, rej = false;
+                    for (unsigned k = s_off[i], e = s_off[i + 1]; k < e; k++) {
+                        const int u = st[s_nb[k]];
+                        if (u == kAccepted) { rej = true; break; }
+                        if (u != kRejected) all_rej = false;
+                    }
+                    const int v = rej ? kRejected : (all_rej ? kAccepted : kUndecided);
+                    if (v != kUndecided) st[i] = (unsigned char)v;
+                    const unsigned act = __activemask();
+                    const unsigned m = __ballot_sync(act, v == kUndecided);
+                    if (m) {
+                        const unsigned leader = __ffs(m) - 1;
+                        unsigned base = 0;
+                        if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
+                        base = __shfl_sync(act, base, leader);
+                        if (v == kUndecided) nxt[base + __popc(m & ((1u << lane) - 1u))] = (unsigned short)i;
+                    }
+                }
+                __syncthreads();
+                n_cur = *(volatile unsigned*)cnt;
+                unsigned short* tmp = cur;
+                cur = nxt;
+                nxt = tmp;
+                rounds = r + 1;
+            }
+        } else {
         for (unsigned r = 0;; r++) {
             unsigned und = 0;
             for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
@@ -1305,6 +1396,7 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
             __syncthreads();
             if (rem == 0) { rounds = r + 1; break; }
             if (r + 1 >= kMaxRounds) { ok = false; break; }
+        }
         }
         for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
             const int j = job_of(s_pref, njobs, i);
@@ -1403,7 +1495,9 @@ __global__ void __launch_bounds__(256) k_finish(const Job* jobs, int njobs, Batc
 
 cudaError_t commit_occupancy(int block, int* blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_rounds, block, 0);
+    cudaError_t e = cudaFuncSetAttribute(k_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRoundsDyn);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_rounds, block, kRoundsDyn);
 }
 
 cudaError_t launch_lists(const Job* jobs, int njobs, int sms, cudaStream_t s)
@@ -1417,7 +1511,7 @@ cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, in
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kRoundsDyn;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

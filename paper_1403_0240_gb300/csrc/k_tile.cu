@@ -40,34 +40,6 @@ __device__ __forceinline__ TileBox tile_box(const Job& J, unsigned k)
     return b;
 }
 
-// --------------------------------------------------------------------------
-// Block-wide exclusive scan of one unsigned per thread.
-__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* s_warp, unsigned& total)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        const int nw = blockDim.x >> 5;
-        unsigned a = lane < nw ? s_warp[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(0xffffffffu, a, o);
-            if (lane >= o) a += y;
-        }
-        if (lane < nw) s_warp[lane] = a;       // inclusive warp totals
-    }
-    __syncthreads();
-    unsigned before = w > 0 ? s_warp[w - 1] : 0u;
-    total = s_warp[(blockDim.x >> 5) - 1];
-    return before + x - v;
-}
 
 // --------------------------------------------------------------------------
 // Energy difference of moving a pixel of value v from label l to c (Methods, Eq. 11),

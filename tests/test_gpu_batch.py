@@ -132,3 +132,27 @@ def test_served_jobs_equal_solo():
         assert r.iterations == iters[r.job_id]
         assert np.array_equal(r.labels, refs[r.job_id]["labels"])
     backend.close()
+
+
+def test_batch_of_large_images_equals_solo():
+    # four 1024^2 images: the batch's candidate count per iteration spans the ranges where the
+    # selection rounds run in one block with and without their shared-memory neighbour rows,
+    # and (above 32768 candidates) on the whole grid
+    jobs = [synth.ellipses(seed=s) for s in range(1, 5)]
+    iters = 8
+    refs = [_solo(w, iters) for w in jobs]
+    batch = seg.Batch()
+    ctxs = [seg.Context.from_workload(w) for w in jobs]
+    for c in ctxs:
+        batch.add(c)
+    cands = []
+    for _ in range(iters):
+        sts = batch.step(1)
+        cands.append(sum(s["n_candidates"] for s in sts))
+    assert max(cands) > 20000
+    for c, r in zip(ctxs, refs):
+        assert np.array_equal(c.labels(), r["labels"])
+        assert c.get_state() == r["state"]
+    batch.close()
+    for c in ctxs:
+        c.close()
