@@ -61,3 +61,25 @@ def test_strerror_and_validation_without_gpu(libseg):
     p.tile[0] = p.tile[1] = p.tile[2] = 0
     p.reserved[3] = 1
     assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL
+
+
+def test_model_and_stats_mode_validation_without_gpu(libseg):
+    import numpy as np
+    out = C.c_size_t(0)
+    p = seg.make_params(np.zeros((64, 48), np.float32), model="pc", cutoff=3.0)
+    assert libseg.seg_estimate_bytes(C.byref(p), 3, C.byref(out)) == seg.SEG_OK
+    pc_bytes = out.value
+    # the deconvolving model needs no local-mean radius; it adds its FP64 fields (T, R, G)
+    # and the PSF tables
+    p.model = seg.SEG_PC_DECONV
+    assert libseg.seg_estimate_bytes(C.byref(p), 3, C.byref(out)) == seg.SEG_OK
+    assert out.value >= pc_bytes + 3 * 64 * 48 * 8
+    p.model = 4
+    assert libseg.seg_estimate_bytes(C.byref(p), 3, C.byref(out)) == seg.SEG_EINVAL
+    p.model = seg.SEG_PS                     # piecewise smooth needs R >= 1
+    assert libseg.seg_estimate_bytes(C.byref(p), 3, C.byref(out)) == seg.SEG_EINVAL
+    p.model = seg.SEG_PC
+    for mode, code in [(seg.SEG_STATS_EXACT, seg.SEG_OK), (seg.SEG_STATS_F64, seg.SEG_OK),
+                       (seg.SEG_STATS_KAHAN32, seg.SEG_OK), (3, seg.SEG_EINVAL), (-1, seg.SEG_EINVAL)]:
+        p.stats_mode = mode
+        assert libseg.seg_estimate_bytes(C.byref(p), 3, C.byref(out)) == code, mode
