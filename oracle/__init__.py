@@ -49,7 +49,7 @@ class Params(C.Structure):
                 ("lam", C.c_double), ("cutoff", C.c_double), ("ps_radius", C.c_double),
                 ("gradient", C.c_int32), ("osc_window", C.c_int32),
                 ("nlabels", C.c_int32), ("pad_", C.c_int32), ("mu_floor", C.c_double),
-                ("psf_r", C.c_int32), ("pad2_", C.c_int32), ("psf", C.c_void_p)]
+                ("psf_r", C.c_int32), ("topology", C.c_int32), ("psf", C.c_void_p)]
 
 
 class State(C.Structure):
@@ -125,7 +125,7 @@ def _ptr(a: np.ndarray | None):
 def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", connectivity: int | None = None,
                 lam: float = 0.0, cutoff: float = 3.0, ps_radius: float = 0.0,
                 gradient: str | int = "sobolev", osc_window: int = 0, nlabels: int | None = None,
-                psf: np.ndarray | None = None) -> Params:
+                psf: np.ndarray | None = None, topology: int = 0) -> Params:
     shape = image.shape
     if image.ndim == 2:
         D, H, W = 1, shape[0], shape[1]
@@ -147,6 +147,7 @@ def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", 
     # Poisson model: local means are floored at 2^-20 of the largest intensity (at least 2^-20)
     p.mu_floor = math.ldexp(max(1.0, float(np.abs(image).max()) if image.size else 1.0), -20)
     set_psf(p, psf)
+    p.topology = int(topology)
     return p
 
 

@@ -685,11 +685,27 @@ static int simple_for_label(const orc_params* p, const int32_t* L, uint32_t xi, 
     return p->ndim == 3 ? orc_simple_3d(nb) : orc_simple_2d(nb);
 }
 
+/* Region vanishing: x is the last pixel of its region exactly when no connectivity neighbour
+ * of x has its label (every foreground label is one connected component). */
+static int last_pixel_of(const orc_params* p, const int32_t* L, uint32_t xi, int32_t lab)
+{
+    int off[6][3];
+    int n = nbr_offsets(p, off);
+    int64_t z, y, x;
+    coords(p, xi, &z, &y, &x);
+    for (int k = 0; k < n; k++) {
+        int64_t zz = z + off[k][0], yy = y + off[k][1], xx = x + off[k][2];
+        if (inside(p, zz, yy, xx) && L[(zz * p->H + yy) * p->W + xx] == lab) return 0;
+    }
+    return 1;
+}
+
 /* Topological control: foreground regions stay connected sets without new or lost
- * holes; removal from l (l != 0) and addition to c (c != 0) must both be simple. */
+ * holes; removal from l (l != 0) and addition to c (c != 0) must both be simple. With
+ * topology 1 a region may vanish: the removal of its last pixel is admissible too. */
 int orc_admissible(const orc_params* p, const int32_t* L, uint32_t xi, int32_t l, int32_t c)
 {
-    if (l != 0 && !simple_for_label(p, L, xi, l)) return 0;
+    if (l != 0 && !simple_for_label(p, L, xi, l) && !(p->topology == 1 && last_pixel_of(p, L, xi, l))) return 0;
     if (c != 0 && !simple_for_label(p, L, xi, c)) return 0;
     return 1;
 }

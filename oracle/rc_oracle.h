@@ -34,6 +34,9 @@
  *   orc_simple_2d/3d    - topological numbers; pinned by Yokoi's formula and global
  *                         component counts (2D), and by contractibility of the
  *                         centre's link in the cubical complex (3D).
+ *   orc_admissible      - with topology 1, the removal of a region's last pixel is admissible;
+ *                         pinned by global pixel counts on random connected label images and
+ *                         by a one-pixel region that vanishes.
  *   orc_select          - ranked greedy selection; pinned by an independent
  *                         local-minimum-rounds evaluation and permutation tests.
  *   orc_perimeter       - |Gamma| as the length prior counts it; pinned by square and
@@ -68,7 +71,8 @@ typedef struct {
     int32_t pad_;
     double mu_floor;     /* Poisson model: local means below this are taken as this */
     int32_t psf_r;       /* deconvolving model: PSF profile radius r (psf has 2r + 1 taps) */
-    int32_t pad2_;
+    int32_t topology;    /* topological control: 0 = every move keeps each region's topology;
+                            1 = a region may also vanish (its last pixel may leave it) */
     const double* psf;   /* deconvolving model: symmetric 1D PSF profile k(-r..r), the same on
                             every axis (K(x) = prod_axes k(x_a)) */
 } orc_params;

@@ -320,3 +320,55 @@ def test_degenerate_sobolev_run_equals_l2_run(orc):
         ra.step()
         rb.step()
         assert np.array_equal(ra.L, rb.L)
+
+
+def _rect_labels(shape, seed, n_rect=12):
+    """Random non-overlapping rectangles (some 1x1) on background 0: every label one component."""
+    rng = np.random.default_rng(seed)
+    L = np.zeros(shape, np.int32)
+    lab = 1
+    for _ in range(200):
+        if lab > n_rect:
+            break
+        h, w = (1, 1) if rng.random() < 0.4 else tuple(rng.integers(1, 5, 2))
+        y, x = rng.integers(0, shape[0] - h + 1), rng.integers(0, shape[1] - w + 1)
+        y0, y1, x0, x1 = max(0, y - 1), min(shape[0], y + h + 1), max(0, x - 1), min(shape[1], x + w + 1)
+        if (L[y0:y1, x0:x1] != 0).any():
+            continue
+        L[y:y + h, x:x + w] = lab
+        lab += 1
+    return L
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_vanishing_admits_exactly_the_last_pixels(orc, seed):
+    L = _rect_labels((24, 26), seed)
+    I = np.zeros(L.shape, np.float32)
+    strict = orc.make_params(I, L, "pc", topology=0)
+    vanish = orc.make_params(I, L, "pc", topology=1)
+    counts = np.bincount(L.ravel())
+    singles = 0
+    for x in range(L.size):
+        l = int(L.flat[x])
+        if l == 0:
+            continue
+        a0 = orc.admissible(strict, L, x, l, 0)
+        a1 = orc.admissible(vanish, L, x, l, 0)
+        if counts[l] == 1:
+            singles += 1
+            assert not a0 and a1          # an isolated region: only vanishing removes it
+        else:
+            assert a0 == a1               # everything else is unchanged
+    assert singles > 0
+
+
+def test_a_one_pixel_region_vanishes_only_when_allowed(orc):
+    I = np.zeros((20, 20), np.float32)
+    L = np.zeros((20, 20), np.int32)
+    L[10, 10] = 1                          # a one-pixel region in a flat background
+    L[2:6, 2:6] = 2
+    for topology, gone in [(0, False), (1, True)]:
+        p = orc.make_params(I, L, "pc", lam=0.5, cutoff=1.0, topology=topology, nlabels=3)
+        run = orc.Run(p, I, L)
+        run.step()
+        assert (int((run.L == 1).sum()) == 0) == gone
