@@ -120,7 +120,9 @@ __device__ __forceinline__ bool simple_table(unsigned X, int d)
 
 // Topological control: removal from l (foreground) and addition to c (foreground)
 // must both be simple, so regions neither split, vanish, merge nor change holes. The
-// neighbourhood is read once for both labels.
+// neighbourhood is read once for both labels. With SEG_TOPO_VANISH the removal of a
+// region's last pixel is admissible too: no 4- (6-) neighbour holds l (every foreground
+// label being one connected component).
 __device__ __forceinline__ bool admissible(const Job& J, unsigned gi, int l, int c)
 {
     int x, y, z;
@@ -141,7 +143,7 @@ __device__ __forceinline__ bool admissible(const Job& J, unsigned gi, int l, int
                 }
                 k++;
             }
-    if (l != 0 && !simple_table(ml, d)) return false;
+    if (l != 0 && !simple_table(ml, d) && !(J.topo_vanish && (ml & c_topo.touch[d]) == 0)) return false;
     if (c != 0 && !simple_table(mc, d)) return false;
     return true;
 }

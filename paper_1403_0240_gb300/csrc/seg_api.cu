@@ -246,7 +246,8 @@ int validate(const seg_params* p)
     for (int i = 0; i < 3; i++)
         if (p->tile[i] < 0 || p->tile[i] > 1024) return SEG_EINVAL;
     if (p->ndim == 2 && p->tile[0] > 1) return SEG_EINVAL;
-    for (int i = 0; i < 4; i++)
+    if (p->topology != SEG_TOPO_STRICT && p->topology != SEG_TOPO_VANISH) return SEG_EINVAL;
+    for (int i = 0; i < 3; i++)
         if (p->reserved[i]) return SEG_EINVAL;
     return SEG_OK;
 }
@@ -323,6 +324,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
                                   (long long)(h.W - 1) * (h.W - 1))
                           : 0;
     h.osc_window = p->osc_window;
+    h.topo_vanish = p->topology == SEG_TOPO_VANISH ? 1 : 0;
     h.nbr_stride = h.ndim == 3 ? 26 : 8;
     h.slot_lo = slot_lo;
     h.nS = nS;

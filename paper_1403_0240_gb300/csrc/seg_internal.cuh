@@ -137,6 +137,7 @@ struct alignas(64) Job {
     double* dc_G;             // ... G = K * R at the particle pixels of the iteration [npix]
     int M;                    // number of labels
     int osc_window;           // L2 fallback window (0 = never)
+    int topo_vanish;          // a region's last pixel may leave it (SEG_TOPO_VANISH)
     int inject;               // test-only fault injection (SEG_INJECT_*)
     int nbr_stride;           // neighbour-list slots per candidate: 8 (2D) | 26 (3D)
     int slot_lo, nS, nQ;      // exact float32 sums: exponent slots [slot_lo, slot_lo + nS)

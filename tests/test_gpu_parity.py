@@ -188,3 +188,27 @@ def test_invalid_inputs_rejected():
         seg.Context(I, L, cutoff=0.0)
     with pytest.raises(seg.SegError):
         seg.Context(I, L, model="ps", ps_radius=0.5)
+
+
+def test_region_vanishing_matches_oracle():
+    # small seed squares (1x1 and 2x2) over a two-disk image: with SEG_TOPO_VANISH the seeds
+    # that lie in the background shrink and vanish, iteration by iteration as in the oracle
+    w = synth.disks(96, 96, seed=41)
+    L = np.zeros((96, 96), np.int32)
+    lab = 1
+    for y in range(4, 92, 11):
+        for x in range(4, 92, 11):
+            s = 1 + (lab % 2)
+            L[y:y + s, x:x + s] = lab
+            lab += 1
+    w.labels0 = L
+    import oracle
+    ctx = seg.Context(w.image, L, model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
+                      topology="vanish")
+    p = oracle.make_params(w.image, L, w.model, w.connectivity, w.lam, w.cutoff, topology=1)
+    run = oracle.Run(p, w.image, L)
+    for it in range(12):
+        compare_step(ctx, run, f"vanish it{it}")
+    counts = np.bincount(ctx.labels().ravel(), minlength=lab)
+    assert (counts[1:] == 0).any()          # some seeds have vanished
+    ctx.close()
