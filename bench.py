@@ -532,10 +532,31 @@ def _pc_energy(I: np.ndarray, L: np.ndarray, lam: float) -> float:
     return float(np.sum((I64 - mu[lab]) ** 2) + lam * _contour_length(L))
 
 
+def _deconv_energy(I: np.ndarray, L: np.ndarray, psf: np.ndarray, lam: float) -> float:
+    """sum (I - K * s)^2 + lam |Gamma| for the deconvolving model (theta = region means, K the
+    separable PSF, zero outside the image), evaluated in FP64 on the host for the report."""
+    Id = I.astype(np.float64)
+    M = int(L.max()) + 1
+    n = np.bincount(L.ravel(), minlength=M)
+    S = np.bincount(L.ravel(), weights=Id.ravel(), minlength=M)
+    theta = np.where(n > 0, S / np.maximum(n, 1), 0.0)
+    J = theta[L]
+    r = (psf.size - 1) // 2
+    for axis in range(L.ndim):
+        pad = [(0, 0)] * L.ndim
+        pad[axis] = (r, r)
+        Jp = np.pad(J, pad)
+        acc = np.zeros_like(J)
+        for u, k in enumerate(psf):
+            acc += k * np.take(Jp, np.arange(u, u + J.shape[axis]), axis=axis)
+        J = acc
+    return float(((Id - J) ** 2).sum()) + lam * _contour_length(L)
+
+
 def run_convergence(args, world, rank, local, pg):
     """Iterations to convergence of the L2 flow and of the Sobolev flow with the oscillation
-    switch live, on the 128^2 and 1024^2 workloads (one job at a time, status read every
-    iteration)."""
+    switch live, on the 128^2 and 1024^2 workloads and the 512^2 deconvolution scene (one job at
+    a time, status read every iteration)."""
     import torch
 
     from paper_1403_0240_gb300 import seg
@@ -543,17 +564,20 @@ def run_convergence(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     out = []
-    for name in ("disks128", "ellipses1024"):
+    for name in ("disks128", "ellipses1024", "deconv512"):
         make, _ = workloads()[name]
         w = make(rank)
         runs = {}
         for flow in ("l2", "sobolev", "sobolev_global"):
             ctx = seg.Context(torch.from_numpy(w.image).to(dev), torch.from_numpy(w.labels0).to(dev), model=w.model,
                               connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff, ps_radius=w.ps_radius,
-                              gradient=flow, osc_window=args.osc_window if flow != "l2" else 0)
+                              gradient=flow, osc_window=args.osc_window if flow != "l2" else 0, psf=w.psf)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             switch, accepted, it = None, [], 0
+            # a flow also stops when its labels repeat with period 2 (the deconvolving model's
+            # re-estimated means can make a few pixels flip back and forth for ever)
+            hist, cycle_at = [], None
             while it < args.max_iters:
                 st = ctx.step(1)
                 it += 1
@@ -562,13 +586,21 @@ def run_convergence(args, world, rank, local, pg):
                     switch = st["iteration"]
                 if st["converged"]:
                     break
+                if w.model == "pcd":
+                    hist = (hist + [ctx.labels().copy()])[-3:]
+                    if len(hist) == 3 and np.array_equal(hist[0], hist[2]):
+                        cycle_at = it
+                        break
             torch.cuda.synchronize(dev)
             secs = time.perf_counter() - t0
             L = ctx.labels().copy()
             runs[flow] = {"iterations": it, "converged": bool(st["converged"]), "switch_to_l2_at": switch,
+                          "period2_at": cycle_at, "moves_last_iteration": accepted[-1] if accepted else 0,
                           "seconds": round(secs, 4), "particle_iterations": int(st["particles_total"]),
                           "moves": int(sum(accepted)), "contour_length": _contour_length(L),
-                          "energy": _pc_energy(w.image, L, w.lam) if w.model == "pc" else None, "labels": L}
+                          "energy": (_pc_energy(w.image, L, w.lam) if w.model == "pc" else
+                                     _deconv_energy(w.image, L, w.psf, w.lam) if w.model == "pcd" else None),
+                          "labels": L}
             ctx.close()
         agree = float(np.mean(runs["l2"]["labels"] == runs["sobolev"]["labels"]))
         agree_g = float(np.mean(runs["sobolev_global"]["labels"] == runs["sobolev"]["labels"]))

@@ -34,3 +34,16 @@ def test_psf_pass_flops_counts_the_in_image_taps():
                 brute += sum(1 for u in range(-r, r + 1) if 0 <= pos[ax] + u < shape[ax])
         assert bench.psf_pass_flops(w) == 2.0 * brute
         assert bench.psf_passes(w) == len(passes)
+
+
+def test_deconv_energy_matches_scipy():
+    from scipy import ndimage
+    from paper_1403_0240_gb300 import synth
+    rng = np.random.default_rng(3)
+    I = rng.uniform(0, 2, (20, 23)).astype(np.float32)
+    L = rng.integers(0, 3, (20, 23)).astype(np.int32)
+    k = synth.gaussian_psf(1.5)
+    theta = np.array([I[L == m].astype(np.float64).mean() for m in range(3)])
+    J = ndimage.correlate(theta[L], np.multiply.outer(k, k), mode="constant", cval=0.0)
+    ref = float(((I.astype(np.float64) - J) ** 2).sum()) + 0.3 * bench._contour_length(L)
+    assert abs(bench._deconv_energy(I, L, k, 0.3) - ref) <= 1e-9 * ref
