@@ -286,11 +286,13 @@ int seg_region_stats_noalloc(int32_t dtype, int64_t npix, const void* image, con
 int seg_debug_simple(int32_t ndim, const uint32_t* masks, int32_t n, uint8_t* out);
 
 /* Test-only fault injection, for checking that bounded device waits report instead of
- * hanging. SEG_INJECT_UNPUBLISHED_TILE: from the next iteration on, extraction leaves the first
- * tile's particle count unpublished, so the next tile's bounded wait for it runs out (about two
- * seconds) and the iteration ends with SEG_ETIMEOUT; the context is then poisoned (destroy it).
+ * hanging. SEG_INJECT_WITHHELD_COPY: from the next iteration on, extraction's first tile
+ * arms its barrier for the label copy but issues no copy (when labels arrive by tensor copies,
+ * i.e. rows of a multiple of 16 bytes), so its bounded wait runs out (about two seconds), and so
+ * do the waits of the tiles after it for its particle count; the iteration ends with
+ * SEG_ETIMEOUT and the context is then poisoned (destroy it).
  * SEG_INJECT_NONE clears the injection. No GPU fault is raised. */
-enum { SEG_INJECT_NONE = 0, SEG_INJECT_UNPUBLISHED_TILE = 1 };
+enum { SEG_INJECT_NONE = 0, SEG_INJECT_WITHHELD_COPY = 1 };
 int seg_debug_inject(seg_ctx* c, int32_t what);
 
 const char* seg_strerror(int code);

@@ -295,16 +295,23 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 mbar_init(&s_bar_img, 1);
                 mbar_expect_tx(&s_bar_img, (unsigned)(nbox * esz));
             }
-            if (NDIM == 3) tma_load_3d(sL, J.tmap_L, sb.ox, sb.oy, sb.oz, &s_bar);
-            else tma_load_2d(sL, J.tmap_L, sb.ox, sb.oy, &s_bar);
+            // (fault injection for tests: the first tile's copy is withheld)
+            const bool withhold = J.inject == SEG_INJECT_WITHHELD_COPY && k == 0;
+            if (NDIM == 3 && !withhold) tma_load_3d(sL, J.tmap_L, sb.ox, sb.oy, sb.oz, &s_bar);
+            else if (!withhold) tma_load_2d(sL, J.tmap_L, sb.ox, sb.oy, &s_bar);
         }
         __syncthreads();
         const bool arrived = mbar_wait_bounded(&s_bar);
         // the image only once the labels are in: every tile's labels (which gate the counts
         // and so every tile's look-back) do not share the DRAM burst with the images
         if (tid == 0 && img_tma && arrived) tma_load_2d(sRaw, J.tmap_I, sb.ox, sb.oy, &s_bar_img);
-        if (__syncthreads_or(!arrived)) {   // the whole block leaves together
-            if (tid == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
+        if (__syncthreads_or(!arrived)) {   // the whole block leaves together, its tile empty
+            if (tid == 0) {
+                atomicExch(&ctr->error, SEG_ETIMEOUT);
+                atomicExch(&ctr->skip, 1);       // the later stages of the iteration do nothing
+                J.tile_start[k] = 0;
+                J.tile_count[k] = 0;
+            }
             mbar_wait_bounded(&s_bar);       // a second bounded wait for the copies in flight
             if (tid == 0 && img_tma && arrived) mbar_wait_bounded(&s_bar_img);
             return;
@@ -467,9 +474,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         const unsigned long long ep = (unsigned long long)(tag & 0x3fffffffu) << 34;
         const unsigned long long emask = ~((1ull << 34) - 1);
         unsigned excl = 0;
-        // (fault injection for tests: the first tile publishes nothing)
-        const bool publish = !(J.inject == SEG_INJECT_UNPUBLISHED_TILE && k == 0);
-        if (lane == 0 && publish) atomicExch(J.tile_word + k, ep | ((k == 0 ? 2ull : 1ull) << 32) | total);
+        if (lane == 0) atomicExch(J.tile_word + k, ep | ((k == 0 ? 2ull : 1ull) << 32) | total);
         if (k > 0) {
             // each lane reads 8 consecutive predecessors (lane 0 the nearest), 256 per round
             // trip. The ready run nearest to the tile is consumed up to the first inclusive
@@ -516,7 +521,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 if (limit == 0) {                   // the nearest remaining predecessor is not ready
                     // lane 0 decides for the warp, so that its lanes leave together
                     if (__shfl_sync(0xffffffffu, (int)wb.expired(), 0)) {
-                        if (lane == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
+                        if (lane == 0) {
+                            atomicExch(&ctr->error, SEG_ETIMEOUT);
+                            atomicExch(&ctr->skip, 1);
+                        }
                         break;
                     }
                     __nanosleep(32);
@@ -560,7 +568,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
     }
     __syncthreads();
     if (s_img_fail) {                            // the image copy did not land in time
-        if (tid == 0) atomicExch(&ctr->error, SEG_ETIMEOUT);
+        if (tid == 0) {
+            atomicExch(&ctr->error, SEG_ETIMEOUT);
+            atomicExch(&ctr->skip, 1);
+            J.tile_count[k] = 0;
+        }
         mbar_wait_bounded(&s_bar_img);
         return;
     }

@@ -1388,7 +1388,7 @@ int seg_set_psf(seg_ctx* c, const double* k, int32_t radius)
 
 int seg_debug_inject(seg_ctx* c, int32_t what)
 {
-    if (!c || (what != SEG_INJECT_NONE && what != SEG_INJECT_UNPUBLISHED_TILE)) return SEG_EINVAL;
+    if (!c || (what != SEG_INJECT_NONE && what != SEG_INJECT_WITHHELD_COPY)) return SEG_EINVAL;
     int rc = ensure_device(c->device);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));

@@ -23,7 +23,7 @@ SEG_SOBOLEV, SEG_L2, SEG_SOBOLEV_GLOBAL = 0, 1, 2
 SEG_STATS_EXACT, SEG_STATS_F64, SEG_STATS_KAHAN32 = 0, 1, 2
 SEG_TOPO_STRICT, SEG_TOPO_VANISH = 0, 1
 STATS_MODES = {"exact": SEG_STATS_EXACT, "f64": SEG_STATS_F64, "kahan32": SEG_STATS_KAHAN32}
-SEG_INJECT_NONE, SEG_INJECT_UNPUBLISHED_TILE = 0, 1
+SEG_INJECT_NONE, SEG_INJECT_WITHHELD_COPY = 0, 1
 
 
 class Params(C.Structure):

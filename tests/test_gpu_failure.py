@@ -1,7 +1,7 @@
-"""Failure detection without a GPU fault: a tile whose particle count is never published (a
-test-only injection; nothing sets the flag that the next tile waits for) makes the bounded
-device wait run out. The iteration reports SEG_ETIMEOUT within seconds, the device stays
-usable, and in a batch only the injected job is affected."""
+"""Failure detection without a GPU fault: a tile whose label copy is never issued (a test-only
+injection; nothing completes the barrier the tile waits on) makes the bounded device wait run
+out. The iteration reports SEG_ETIMEOUT within seconds, the device stays usable, and in a batch
+only the injected job is affected."""
 import time
 
 import numpy as np
@@ -20,7 +20,7 @@ def test_unpublished_tile_times_out_and_reports():
     w = _job()
     ctx = seg.Context.from_workload(w)
     ctx.step(1)
-    ctx.inject(seg.SEG_INJECT_UNPUBLISHED_TILE)
+    ctx.inject(seg.SEG_INJECT_WITHHELD_COPY)
     t0 = time.time()
     with pytest.raises(seg.SegError) as e:
         ctx.step(1)
@@ -48,7 +48,7 @@ def test_injected_job_does_not_disturb_its_batch():
     batch.add(bad)
     batch.add(ok)
     batch.step(2)
-    bad.inject(seg.SEG_INJECT_UNPUBLISHED_TILE)
+    bad.inject(seg.SEG_INJECT_WITHHELD_COPY)
     with pytest.raises(seg.SegError) as e:
         batch.step(2)
     assert e.value.code == seg.SEG_ETIMEOUT
