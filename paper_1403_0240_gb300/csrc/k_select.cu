@@ -1206,8 +1206,29 @@ __device__ __forceinline__ void commit_move_one(const Job& J, unsigned s)
     }
     J.L[gi] = c;
     J.p_flags[p] |= kFlagAcc;
-    stats_move(J, gi, l, -1);
-    stats_move(J, gi, c, +1);
+    if (J.stats_mode != SEG_STATS_EXACT) {    // the exact sums are added per warp by the caller
+        stats_move(J, gi, l, -1);
+        stats_move(J, gi, c, +1);
+    }
+}
+
+// Exact statistic deltas of the warp's moves (one pixel leaving m, sign -1, or joining it,
+// sign +1). Every lane of the warp calls this; `valid` marks the lanes with a move of an
+// exact-statistics job. uint16 images: the lanes that hit the same label are summed first (a
+// 3D move mostly shares its label with other lanes); float32 images: one atomic per lane and
+// exponent slot, as the per-lane sums would spread over many slots.
+__device__ __forceinline__ void stats_move_warp(const Job* jobs, int j, bool valid, unsigned gi, int m, int sign)
+{
+    const bool u16 = valid && jobs[j].dtype == SEG_U16;
+    if (valid && !u16) stats_move(jobs[j], gi, m, sign);
+    if (!__any_sync(0xffffffffu, u16)) return;
+    const Job& J = jobs[u16 ? j : 0];
+    const unsigned long long key = u16 ? (((unsigned long long)j << 32) | (unsigned)m) : 0ull;
+    const long long v = u16 ? ((const unsigned short*)J.I)[gi] : 0;
+    const long long mo = u16 ? m : 0;
+    warp_add(key, u16, sign, J.st_n + mo);
+    warp_add(key, u16, sign * v, J.st_S + mo);
+    warp_add(key, u16, sign * v * v, J.st_Q + mo);
 }
 
 // D: per-job oscillation fallback, status and counters for the next iteration
@@ -1455,14 +1476,24 @@ __global__ void __launch_bounds__(256) k_moves(const Job* jobs, int njobs, const
         const unsigned i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
         int j = -1;
         bool acc = false;
+        unsigned gi = 0;
+        int l = 0, c = 0;
         if (i < total) {
             j = job_of(s_pref, njobs, i);
+            const Job& J = jobs[j];
             const unsigned s = i - s_pref[j];
-            if (jobs[j].c_state[s] == kAccepted) {
-                commit_move_one(jobs[j], s);
+            if (J.c_state[s] == kAccepted) {
+                const int p = J.c_best[s];
+                gi = J.c_pix[s];
+                l = J.p_l[p];
+                c = J.p_c[p];
+                commit_move_one(J, s);
                 acc = true;
             }
         }
+        const bool exact = acc && jobs[j].stats_mode == SEG_STATS_EXACT;
+        stats_move_warp(jobs, j, exact, gi, l, -1);
+        stats_move_warp(jobs, j, exact, gi, c, +1);
         const unsigned peers = __match_any_sync(0xffffffffu, acc ? j : -1);
         if (acc && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&jobs[j].ctr->n_accepted, (unsigned)__popc(peers));
     }
