@@ -172,7 +172,8 @@ int seg_estimate_bytes(const seg_params* p, int32_t nlabels, size_t* bytes);
  * max_entries candidates in the order tried, *n_entries (may be NULL) their number.
  * Returns SEG_OK when at least one candidate ran, else the first candidate's error (for
  * SEG_PC_DECONV, which needs its PSF before a step, every candidate fails with SEG_ESTATE: tune
- * such jobs with the piecewise-constant model on the same image, the tile work is the same). */
+ * such jobs with the piecewise-constant model on the same image: the settings act on the same
+ * extraction and interaction kernels). */
 typedef struct {
     int32_t cell_edge;     /* cell-list edge in pixels */
     int32_t tile[3];       /* tile shape in pixels {z, y, x} */
