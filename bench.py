@@ -55,6 +55,12 @@ def workloads():
         "disks128": (lambda seed: synth.disks(seed=seed) if seed == 0 else synth.disks(128, 128, seed=seed),
                      "2D 128x128 float32 piecewise constant: two disks, Gaussian noise 0.3; centred 64x64 square; "
                      "cutoff 3, lambda 0.04, 50 iterations"),
+        "ellipses4096": (lambda seed: synth.ellipses(4096, 4096, seed=1 + seed),
+                         "2D 4096x4096 float32 piecewise smooth: the ellipses1024 recipe at 16x the area (640 "
+                         "ellipses, same density, bias field and noise); 32x32 squares on a 64 px pitch"),
+        "ellipses8192": (lambda seed: synth.ellipses(8192, 8192, seed=1 + seed),
+                         "2D 8192x8192 float32 piecewise smooth: the ellipses1024 recipe at 64x the area (2560 "
+                         "ellipses); 32x32 squares on a 64 px pitch"),
         "deconv512": (lambda seed: synth.deconv_scene(seed=11 + seed),
                       "2D 512x512 float32, deconvolving piecewise-constant model (Eq. 8): four objects over a faint "
                       "background blurred by a Gaussian PSF sigma 15 px (r = 45, as in Figure 3), Poisson noise (10 "
