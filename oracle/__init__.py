@@ -54,7 +54,7 @@ class Params(C.Structure):
 
 class State(C.Structure):
     _fields_ = [("mode", C.c_int32), ("converged", C.c_int32), ("t", C.c_int64),
-                ("best_A", C.c_int64), ("t_best", C.c_int64)]
+                ("best_A", C.c_int64), ("t_best", C.c_int64), ("nlabels", C.c_int32), ("pad_", C.c_int32)]
 
 
 class Dump(C.Structure):
@@ -98,6 +98,8 @@ def lib():
             L.orc_simple_3d.argtypes = [vp]
             L.orc_admissible.restype = C.c_int
             L.orc_admissible.argtypes = [P(Params), vp, C.c_uint32, C.c_int32, C.c_int32]
+            L.orc_relabel.restype = C.c_int32
+            L.orc_relabel.argtypes = [P(Params), vp, C.c_int32]
             L.orc_select.restype = C.c_int64
             L.orc_select.argtypes = [P(Params), vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
             L.orc_psf_correlate.restype = None
@@ -277,6 +279,13 @@ def admissible(p: Params, L: np.ndarray, x: int, l: int, c: int) -> bool:
     return bool(lib().orc_admissible(C.byref(p), _ptr(L), x, l, c))
 
 
+def relabel(p: Params, L: np.ndarray, nlabels: int):
+    """(labels, count) after giving split components new labels (topology 2)."""
+    L = np.ascontiguousarray(L, dtype=np.int32).copy()
+    n = lib().orc_relabel(C.byref(p), _ptr(L), int(nlabels))
+    return L, int(n)
+
+
 def select(p: Params, L: np.ndarray, idx, l, c, g):
     L = np.ascontiguousarray(L, dtype=np.int32)
     idx = np.ascontiguousarray(idx, np.uint32)
@@ -319,4 +328,4 @@ class Run:
         return s.as_dict(), out
 
     def state(self) -> dict:
-        return {k: int(getattr(self.st, k)) for k, _ in State._fields_}
+        return {k: int(getattr(self.st, k)) for k, _ in State._fields_ if k != "pad_"}

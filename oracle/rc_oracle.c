@@ -700,12 +700,41 @@ static int last_pixel_of(const orc_params* p, const int32_t* L, uint32_t xi, int
     return 1;
 }
 
+/* Foreground topological number of x for label lab: connectivity components of the label's
+ * pixels in the neighbourhood (the 8-neighbourhood in 2D, the 18-neighbourhood in 3D) that
+ * contain a connectivity neighbour of x. */
+static int foreground_number(const orc_params* p, const int32_t* L, uint32_t xi, int32_t lab)
+{
+    int64_t z, y, x;
+    coords(p, xi, &z, &y, &x);
+    int pos[26][3], fg[26], touch[26];
+    int k = 0;
+    int rz = p->ndim == 3 ? 1 : 0;
+    for (int dz = -rz; dz <= rz; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                if (dz == 0 && dy == 0 && dx == 0) continue;
+                int64_t zz = z + dz, yy = y + dy, xx = x + dx;
+                int in = inside(p, zz, yy, xx) && L[(zz * p->H + yy) * p->W + xx] == lab;
+                int l1 = abs(dz) + abs(dy) + abs(dx);
+                pos[k][0] = dz; pos[k][1] = dy; pos[k][2] = dx;
+                fg[k] = in && l1 <= 2;
+                touch[k] = l1 == 1;
+                k++;
+            }
+    return count_components(k, fg, (const int (*)[3])pos, p->ndim == 3 ? 6 : 4, touch);
+}
+
 /* Topological control: foreground regions stay connected sets without new or lost
  * holes; removal from l (l != 0) and addition to c (c != 0) must both be simple. With
- * topology 1 a region may vanish: the removal of its last pixel is admissible too. */
+ * topology bit 1 a region may vanish: the removal of its last pixel is admissible too. With
+ * bit 2 a removal that locally disconnects the region (foreground number >= 2) is admissible:
+ * the region splits, or one of its holes opens to the rest of the image. */
 int orc_admissible(const orc_params* p, const int32_t* L, uint32_t xi, int32_t l, int32_t c)
 {
-    if (l != 0 && !simple_for_label(p, L, xi, l) && !(p->topology == 1 && last_pixel_of(p, L, xi, l))) return 0;
+    if (l != 0 && !simple_for_label(p, L, xi, l) && !((p->topology & 1) && last_pixel_of(p, L, xi, l)) &&
+        !((p->topology & 2) && foreground_number(p, L, xi, l) >= 2))
+        return 0;
     if (c != 0 && !simple_for_label(p, L, xi, c)) return 0;
     return 1;
 }
@@ -771,6 +800,50 @@ int64_t orc_select(const orc_params* p, const int32_t* L, int64_t N,
 }
 
 /* ------------------------------------------------------------------ */
+/* After a split: every foreground label's connectivity components but the one holding its
+ * smallest pixel index get new labels, numbered from nlabels upward in ascending order of the
+ * components' smallest pixel indices. Components are found by breadth-first search from the
+ * pixels in raster order, so each is found at its smallest pixel. Returns the new label count. */
+int32_t orc_relabel(const orc_params* p, int32_t* L, int32_t nlabels)
+{
+    int64_t npix = p->D * p->H * p->W;
+    int32_t* comp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(npix > 0 ? npix : 1));
+    int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)(npix > 0 ? npix : 1));
+    uint8_t* seen_label = (uint8_t*)calloc((size_t)nlabels + 1, 1);
+    int off[6][3];
+    int nn = nbr_offsets(p, off);
+    for (int64_t i = 0; i < npix; i++) comp[i] = 0;
+    int32_t next = nlabels;
+    for (int64_t s0 = 0; s0 < npix; s0++) {
+        int32_t m = L[s0];
+        if (m == 0 || comp[s0]) continue;
+        int32_t target = m;
+        if (m < nlabels && seen_label[m]) target = next++;   /* a further component of m */
+        if (m < nlabels) seen_label[m] = 1;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = s0;
+        comp[s0] = 1;
+        while (head < tail) {
+            int64_t u = queue[head++];
+            int64_t z, y, x;
+            coords(p, u, &z, &y, &x);
+            for (int k = 0; k < nn; k++) {
+                int64_t zz = z + off[k][0], yy = y + off[k][1], xx = x + off[k][2];
+                if (!inside(p, zz, yy, xx)) continue;
+                int64_t v = (zz * p->H + yy) * p->W + xx;
+                if (comp[v] || L[v] != m) continue;
+                comp[v] = 1;
+                queue[tail++] = v;
+            }
+            L[u] = target;
+        }
+    }
+    free(comp);
+    free(queue);
+    free(seen_label);
+    return next;
+}
+
 void orc_state_init(const orc_params* p, orc_state* st)
 {
     st->mode = p->gradient;          /* 0 = Sobolev, 1 = L2, 2 = Sobolev with E = |Gamma| */
@@ -778,6 +851,8 @@ void orc_state_init(const orc_params* p, orc_state* st)
     st->t = 0;
     st->best_A = -1;
     st->t_best = 0;
+    st->nlabels = p->nlabels;
+    st->pad_ = 0;
 }
 
 int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
@@ -786,6 +861,9 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
     memset(status, 0, sizeof *status);
     status->mode_used = st->mode;
     if (st->converged) { status->converged = 1; st->t++; return 0; }
+    orc_params q_cur = *p;
+    q_cur.nlabels = st->nlabels > p->nlabels ? st->nlabels : p->nlabels;   /* labels made by splits */
+    p = &q_cur;
     int M = p->nlabels;
     int64_t npix = p->D * p->H * p->W;
     int64_t* n = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
@@ -825,6 +903,7 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
     int64_t ncand = 0;
     int64_t na = orc_select(p, L, N, idx, l, c, g, acc_idx, acc_c, &ncand);
     for (int64_t t = 0; t < na; t++) L[acc_idx[t]] = acc_c[t];
+    if (p->topology & 2) st->nlabels = orc_relabel(p, L, p->nlabels);
     (void)npix;
     status->n_particles = N;
     status->n_candidates = ncand;

@@ -36,7 +36,10 @@
  *                         centre's link in the cubical complex (3D).
  *   orc_admissible      - with topology 1, the removal of a region's last pixel is admissible;
  *                         pinned by global pixel counts on random connected label images and
- *                         by a one-pixel region that vanishes.
+ *                         by a one-pixel region that vanishes. With topology 2 a removal whose
+ *                         foreground topological number is >= 2 is admissible; pinned by a
+ *                         dumbbell whose neck is removed, and by global component counts.
+ *   relabelling (topology 2) - pinned by scipy.ndimage.label components and the numbering rule.
  *   orc_select          - ranked greedy selection; pinned by an independent
  *                         local-minimum-rounds evaluation and permutation tests.
  *   orc_perimeter       - |Gamma| as the length prior counts it; pinned by square and
@@ -71,8 +74,11 @@ typedef struct {
     int32_t pad_;
     double mu_floor;     /* Poisson model: local means below this are taken as this */
     int32_t psf_r;       /* deconvolving model: PSF profile radius r (psf has 2r + 1 taps) */
-    int32_t topology;    /* topological control: 0 = every move keeps each region's topology;
-                            1 = a region may also vanish (its last pixel may leave it) */
+    int32_t topology;    /* topological control, bits: 0 = every move keeps each region's topology;
+                            1 = a region may vanish (its last pixel may leave it); 2 = a region may
+                            split (a removal that locally disconnects it is admissible; after the
+                            moves, every foreground label's components but the one holding its
+                            smallest pixel index get new labels) */
     const double* psf;   /* deconvolving model: symmetric 1D PSF profile k(-r..r), the same on
                             every axis (K(x) = prod_axes k(x_a)) */
 } orc_params;
@@ -83,6 +89,8 @@ typedef struct {
     int64_t t;           /* iterations done */
     int64_t best_A;      /* smallest accepted-move count so far, -1 before the first iteration */
     int64_t t_best;      /* first iteration at which best_A was reached */
+    int32_t nlabels;     /* labels in use: p->nlabels, grown by splits */
+    int32_t pad_;
 } orc_state;
 
 typedef struct {
@@ -143,6 +151,11 @@ void    orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const i
 int     orc_simple_2d(const uint8_t* nb9);
 int     orc_simple_3d(const uint8_t* nb27);
 int     orc_admissible(const orc_params* p, const int32_t* L, uint32_t x, int32_t l, int32_t c);
+
+/* topology 2: give every foreground label's connectivity components but the one holding its
+ * smallest pixel index new labels nlabels, nlabels + 1, ... in ascending order of the components'
+ * smallest pixel indices; returns the new label count */
+int32_t orc_relabel(const orc_params* p, int32_t* L, int32_t nlabels);
 
 int64_t orc_select(const orc_params* p, const int32_t* L, int64_t N,
                    const uint32_t* idx, const int32_t* l, const int32_t* c, const double* g,

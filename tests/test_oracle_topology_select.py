@@ -372,3 +372,76 @@ def test_a_one_pixel_region_vanishes_only_when_allowed(orc):
         run = orc.Run(p, I, L)
         run.step()
         assert (int((run.L == 1).sum()) == 0) == gone
+
+
+@pytest.mark.parametrize("shape,seed", [((30, 34), 0), ((30, 34), 1), ((9, 10, 11), 2)])
+def test_relabel_matches_connected_components(orc, shape, seed):
+    # random blobs where several labels are split into pieces; the relabelling must leave one
+    # component per label, keep each label on the piece with its smallest pixel index, and number
+    # the other pieces upward in ascending order of their smallest pixel indices
+    rng = np.random.default_rng(seed)
+    L = (rng.random(shape) < 0.45).astype(np.int32) * rng.integers(1, 5, shape).astype(np.int32)
+    st = CROSS2 if L.ndim == 2 else CROSS3
+    p = orc.make_params(np.zeros(shape, np.float32), L, "pc", nlabels=5, topology=2)
+    out, n = orc.relabel(p, L, 5)
+    pieces = []                                     # (smallest index, label, mask) of every piece
+    for m in range(1, 5):
+        lab, k = ndimage.label(L == m, structure=st)
+        for c in range(1, k + 1):
+            mask = lab == c
+            pieces.append((int(np.flatnonzero(mask.ravel())[0]), m, mask))
+    pieces.sort(key=lambda t: t[0])
+    first = {}
+    nxt = 5
+    expect = L.copy()
+    for lo, m, mask in pieces:
+        if m not in first:
+            first[m] = lo
+        else:
+            expect[mask] = nxt
+            nxt += 1
+    assert n == nxt
+    assert np.array_equal(out, expect)
+    assert np.array_equal(out == 0, L == 0)
+
+
+def test_split_admits_the_neck_of_a_dumbbell(orc):
+    L = np.zeros((12, 20), np.int32)
+    L[3:9, 2:8] = 1
+    L[3:9, 12:18] = 1
+    L[6, 8:12] = 1                                  # a one-pixel-wide neck
+    I = np.zeros(L.shape, np.float32)
+    x = 6 * 20 + 10                                  # a neck pixel
+    strict = orc.make_params(I, L, "pc", nlabels=2, topology=0)
+    split = orc.make_params(I, L, "pc", nlabels=2, topology=2)
+    assert not orc.admissible(strict, L, x, 1, 0)
+    assert orc.admissible(split, L, x, 1, 0)
+    corner = 3 * 20 + 2                              # a simple point stays admissible either way
+    assert orc.admissible(strict, L, corner, 1, 0) and orc.admissible(split, L, corner, 1, 0)
+    inner = 5 * 20 + 4                               # removing an interior pixel would make a hole
+    assert not orc.admissible(strict, L, inner, 1, 0) and not orc.admissible(split, L, inner, 1, 0)
+
+
+@pytest.mark.parametrize("topology", [2, 3])
+def test_split_iterations_keep_one_component_per_label(orc, topology):
+    from paper_1403_0240_gb300 import synth
+    # one label over two disks joined by a thin bridge of background intensity: the bridge
+    # pixels leave the region and the region splits into two labels
+    w = synth.disks(96, 128, seed=3)
+    I = np.zeros((96, 128), np.float32)
+    I[20:76, 10:50] = 1.0
+    I[20:76, 78:118] = 1.0
+    L = np.zeros(I.shape, np.int32)
+    L[30:66, 18:110] = 1                             # one rectangle across both blobs
+    p = orc.make_params(I + w.image * 0.1, L, "pc", 4, 0.02, 3.0, topology=topology, nlabels=2)
+    run = orc.Run(p, I + w.image * 0.1, L)
+    total = L.size
+    for _ in range(40):
+        run.step()
+        n = run.state()["nlabels"]
+        counts = np.bincount(run.L.ravel(), minlength=n)
+        assert counts.sum() == total
+        for m in range(1, n):
+            if counts[m]:
+                assert ndimage.label(run.L == m, structure=CROSS2)[1] == 1
+    assert run.state()["nlabels"] >= 3                # the region has split
