@@ -73,10 +73,17 @@ enum { SEG_PC = 0, SEG_PS = 1, SEG_PS_POISSON = 2, SEG_PC_DECONV = 3 };
  * variant to future work as too costly on its CPU). The cutoff parameter only sizes the cell
  * list in this mode. */
 enum { SEG_SOBOLEV = 0, SEG_L2 = 1, SEG_SOBOLEV_GLOBAL = 2 };
-/* topological control (Particle-based image segmentation: foreground regions stay connected;
- * the paper's experiments disallow region fusions). Splitting and fusion events are not
- * provided: the paper defers their rules to a reference that is not available. */
-enum { SEG_TOPO_STRICT = 0, SEG_TOPO_VANISH = 1 };
+/* topological control, bits of seg_params.topology (Particle-based image segmentation: foreground
+ * regions stay connected sets; the paper's experiments disallow region fusions):
+ * SEG_TOPO_VANISH - a region may vanish: the removal of its last pixel is admissible;
+ * SEG_TOPO_SPLIT  - a region may split: a removal whose foreground topological number is >= 2
+ *                   (it locally disconnects the region) is admissible, so the region splits or
+ *                   one of its holes opens; after the moves of the iteration every foreground
+ *                   label's connectivity components but the one holding its smallest pixel
+ *                   index get new labels, numbered upward from the label count in ascending order
+ *                   of the components' smallest pixel indices (seg_info reports the count).
+ * Fusion is not provided: the paper defers its rule to a reference that is not available. */
+enum { SEG_TOPO_STRICT = 0, SEG_TOPO_VANISH = 1, SEG_TOPO_SPLIT = 2 };
 /* region sums of I and I^2 (precision study; counts are exact int64 in every mode):
  * SEG_STATS_EXACT   - exact (int64 fixed point), rounded once to FP64: the means are the FP64
  *                     definition's bit for bit, results are reproducible (default);
@@ -110,11 +117,13 @@ typedef struct {
     int32_t tile[3];       /* tile shape in pixels {z, y, x}, each 0 (default) or 1..1024; a tile
                               is floor(tile / cell_edge) cells (at least one) per axis; z must be
                               0 or 1 in 2D. Default 8 x 32 x 32 / cell (3D), 32 x 64 / cell (2D) */
-    int32_t topology;      /* topological control: SEG_TOPO_STRICT (every move keeps each foreground
-                              region one connected component with its holes) or SEG_TOPO_VANISH
-                              (as strict, and a region may also vanish: the removal of its last
-                              pixel is admissible) */
-    int32_t reserved[3];   /* must be zero */
+    int32_t topology;      /* SEG_TOPO_STRICT (0: every move keeps each foreground region one
+                              connected component with its holes) or an OR of SEG_TOPO_VANISH and
+                              SEG_TOPO_SPLIT */
+    int32_t max_labels;    /* with SEG_TOPO_SPLIT: label capacity (labels 0..max_labels-1), >= the
+                              initial count; 0 = max(2 M, M + 256) for M initial labels. A split
+                              beyond it ends the iteration with SEG_ENOMEM. Ignored otherwise */
+    int32_t reserved[2];   /* must be zero */
 } seg_params;
 
 typedef struct {

@@ -902,8 +902,16 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
     int32_t* acc_c = (int32_t*)malloc(sizeof(int32_t) * NN);
     int64_t ncand = 0;
     int64_t na = orc_select(p, L, N, idx, l, c, g, acc_idx, acc_c, &ncand);
+    /* moves admitted by the split rule (judged on the labels before the moves) */
+    int64_t n_split = 0;
+    if (p->topology & 2)
+        for (int64_t t = 0; t < na; t++) {
+            int32_t l0 = L[acc_idx[t]];
+            if (l0 != 0 && !simple_for_label(p, L, acc_idx[t], l0) && foreground_number(p, L, acc_idx[t], l0) >= 2)
+                n_split++;
+        }
     for (int64_t t = 0; t < na; t++) L[acc_idx[t]] = acc_c[t];
-    if (p->topology & 2) st->nlabels = orc_relabel(p, L, p->nlabels);
+    if (n_split > 0) st->nlabels = orc_relabel(p, L, p->nlabels);
     (void)npix;
     status->n_particles = N;
     status->n_candidates = ncand;

@@ -77,8 +77,9 @@ typedef struct {
     int32_t topology;    /* topological control, bits: 0 = every move keeps each region's topology;
                             1 = a region may vanish (its last pixel may leave it); 2 = a region may
                             split (a removal that locally disconnects it is admissible; after the
-                            moves, every foreground label's components but the one holding its
-                            smallest pixel index get new labels) */
+                            moves of an iteration with such a move, every foreground label's
+                            components but the one holding its smallest pixel index get new
+                            labels) */
     const double* psf;   /* deconvolving model: symmetric 1D PSF profile k(-r..r), the same on
                             every axis (K(x) = prod_axes k(x_a)) */
 } orc_params;

@@ -2,6 +2,8 @@
 // recompute of uncertified gradients, candidate selection with topology control,
 // and the cooperative commit (ranked conflict-free selection, label update, exact
 // region statistics, oscillation fallback).
+#include <algorithm>
+
 #include "seg_internal.cuh"
 
 namespace segk {
@@ -122,8 +124,9 @@ __device__ __forceinline__ bool simple_table(unsigned X, int d)
 // must both be simple, so regions neither split, vanish, merge nor change holes. The
 // neighbourhood is read once for both labels. With SEG_TOPO_VANISH the removal of a
 // region's last pixel is admissible too: no 4- (6-) neighbour holds l (every foreground
-// label being one connected component).
-__device__ __forceinline__ bool admissible(const Job& J, unsigned gi, int l, int c)
+// label being one connected component). With SEG_TOPO_SPLIT a removal whose foreground number is
+// >= 2 is admissible too. Returns 0 (not admissible), 1, or 2 (admissible by the split rule).
+__device__ __forceinline__ int admissible(const Job& J, unsigned gi, int l, int c)
 {
     int x, y, z;
     pix_coords(J, gi, x, y, z);
@@ -143,9 +146,11 @@ __device__ __forceinline__ bool admissible(const Job& J, unsigned gi, int l, int
                 }
                 k++;
             }
-    if (l != 0 && !simple_table(ml, d) && !(J.topo_vanish && (ml & c_topo.touch[d]) == 0)) return false;
-    if (c != 0 && !simple_table(mc, d)) return false;
-    return true;
+    if (c != 0 && !simple_table(mc, d)) return 0;
+    if (l == 0 || simple_table(ml, d)) return 1;
+    if (J.topo_vanish && (ml & c_topo.touch[d]) == 0) return 1;
+    if (J.topo_split && components(ml & c_topo.nF[d], c_topo.adjF[d], c_topo.touch[d]) >= 2) return 2;
+    return 0;
 }
 
 // the tabulated decision, as the selection uses it
@@ -708,12 +713,13 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
             if (kq < bk || (kq == bk && cq < bc_)) { best = q; bk = kq; bc_ = cq; }
         }
         int slot = -1;
-        if (bk < 0.0 && admissible(J, gi, J.p_l[best], bc_)) {
+        const int adm = bk < 0.0 ? admissible(J, gi, J.p_l[best], bc_) : 0;
+        if (adm) {
             slot = (int)atomicAdd(&ctr->n_cand, 1u);
             J.c_best[slot] = (int)best;
             J.c_key[slot] = bk;
             J.c_pix[slot] = gi;
-            J.p_flags[best] |= kFlagCand;
+            J.p_flags[best] |= adm == 2 ? (kFlagCand | kFlagSplit) : kFlagCand;
         }
         J.pix_cand[p] = slot;
     }
@@ -929,9 +935,13 @@ __device__ __forceinline__ void warp_add(unsigned long long key, bool valid, lon
     if (valid && lane == __ffs(peers) - 1 && sum) atomic_add_ll(addr, sum);
 }
 
-__global__ void __launch_bounds__(256) k_stats_init(const Job* jobs, int j)
+__global__ void __launch_bounds__(256) k_stats_init(const Job* jobs, int j, bool after_split)
 {
+    if (after_split) pdl_enter();
     const Job& J = jobs[j];
+    // after the moves: only when regions split (their pieces were relabelled); the tables were
+    // zeroed by k_stats_zero
+    if (after_split && (ld_volatile(&J.ctr->n_split) == 0 || ld_volatile(&J.ctr->skip))) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n = J.npix;
     const long long rounds = (n + stride - 1) / stride;
@@ -998,7 +1008,35 @@ __global__ void k_stats_finalize(const Job* jobs, int njobs)
     }
 }
 
-cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s)
+// zero every statistic table of job j before k_stats_init recomputes them after a split
+__global__ void __launch_bounds__(256) k_stats_zero(const Job* jobs, int j)
+{
+    pdl_enter();
+    const Job& J = jobs[j];
+    if (ld_volatile(&J.ctr->n_split) == 0 || ld_volatile(&J.ctr->skip)) return;
+    const long long M = J.M;
+    const long long nS = J.dtype == SEG_F32 ? J.nS : 1, nQ = J.dtype == SEG_F32 ? J.nQ : 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M * (1 + nS + nQ); i += stride) {
+        if (i < M) J.st_n[i] = 0;
+        else if (i < M * (1 + nS)) J.st_S[i - M] = 0;
+        else J.st_Q[i - M * (1 + nS)] = 0;
+        if (i < 2 * M) {
+            if (J.sf64) J.sf64[i] = 0.0;
+            if (J.sk32) J.sk32[i] = 0ull;
+        }
+    }
+}
+
+cudaError_t launch_stats_zero_after_split(const Job* jobs, int j, const Job& h, cudaStream_t s)
+{
+    const long long nS = h.dtype == SEG_F32 ? h.nS : 1, nQ = h.dtype == SEG_F32 ? h.nQ : 1;
+    const long long n = (long long)h.M * (1 + nS + nQ);
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 1024);
+    return launch_stage(k_stats_zero, grid, 256, 0, s, jobs, j);
+}
+
+cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s, bool after_split)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1006,7 +1044,8 @@ cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream
     long long want = (npix + 255) / 256;
     int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
     if (grid < 1) grid = 1;
-    k_stats_init<<<grid, 256, 0, s>>>(jobs, j);
+    if (after_split) return launch_stage(k_stats_init, grid, 256, 0, s, jobs, j, true);
+    k_stats_init<<<grid, 256, 0, s>>>(jobs, j, false);
     return cudaGetLastError();
 }
 
@@ -1206,6 +1245,7 @@ __device__ __forceinline__ void commit_move_one(const Job& J, unsigned s)
     }
     J.L[gi] = c;
     J.p_flags[p] |= kFlagAcc;
+    if (J.p_flags[p] & kFlagSplit) atomicAdd(&J.ctr->n_split, 1u);   // the iteration relabels
     if (J.stats_mode != SEG_STATS_EXACT) {    // the exact sums are added per warp by the caller
         stats_move(J, gi, l, -1);
         stats_move(J, gi, c, +1);
@@ -1276,6 +1316,8 @@ __device__ void commit_job_status(const Job& J, bool ok, unsigned rounds, int er
     c->t++;
     c->iter_tag++;
     c->n_flag = 0;
+    c->n_split = 0;
+    c->n_newcomp = 0;
     c->n_cand = 0;
     c->n_accepted = 0;
     c->n_osc = 0;

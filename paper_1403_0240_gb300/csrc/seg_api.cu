@@ -199,6 +199,7 @@ struct Stepper {
     bool dirty = true;
     bool any_global = false;       // a member uses E = |Gamma| (adds its two launches to the step)
     bool any_deconv = false;       // a member uses the deconvolving model (adds its PSF passes)
+    bool any_split = false;        // a member may split regions (adds the relabelling passes)
     bool profile = false;
     cudaEvent_t ev[11]{};
     cudaStream_t work = nullptr;   // library stream: graphs are captured and launched here
@@ -246,10 +247,20 @@ int validate(const seg_params* p)
     for (int i = 0; i < 3; i++)
         if (p->tile[i] < 0 || p->tile[i] > 1024) return SEG_EINVAL;
     if (p->ndim == 2 && p->tile[0] > 1) return SEG_EINVAL;
-    if (p->topology != SEG_TOPO_STRICT && p->topology != SEG_TOPO_VANISH) return SEG_EINVAL;
-    for (int i = 0; i < 3; i++)
+    if (p->topology < 0 || p->topology > (SEG_TOPO_VANISH | SEG_TOPO_SPLIT)) return SEG_EINVAL;
+    if (p->max_labels < 0 || p->max_labels > (1 << 24)) return SEG_EINVAL;
+    for (int i = 0; i < 2; i++)
         if (p->reserved[i]) return SEG_EINVAL;
     return SEG_OK;
+}
+
+// Label capacity: the initial count M0, or with SEG_TOPO_SPLIT max_labels (default
+// max(2 M0, M0 + 256)), so that the pieces of split regions can take new labels.
+int label_capacity(const seg_params* p, int M0)
+{
+    if (!(p->topology & SEG_TOPO_SPLIT)) return M0;
+    if (p->max_labels) return std::max(p->max_labels, M0);
+    return (int)std::min<long long>(1LL << 24, std::max<long long>(2LL * M0, (long long)M0 + 256));
 }
 
 // Eq. 5 in FP64, then rounded to float for the interaction table.
@@ -324,7 +335,8 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
                                   (long long)(h.W - 1) * (h.W - 1))
                           : 0;
     h.osc_window = p->osc_window;
-    h.topo_vanish = p->topology == SEG_TOPO_VANISH ? 1 : 0;
+    h.topo_vanish = (p->topology & SEG_TOPO_VANISH) ? 1 : 0;
+    h.topo_split = (p->topology & SEG_TOPO_SPLIT) ? 1 : 0;
     h.nbr_stride = h.ndim == 3 ? 26 : 8;
     h.slot_lo = slot_lo;
     h.nS = nS;
@@ -400,6 +412,12 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     A.add(&h.gK32, (size_t)h.gd2max + 1);
     A.add(&h.gK64, (size_t)h.gd2max + 1);
     h.psf_r = -1;
+    if (h.topo_split) {
+        A.add(&h.cc_parent, npix);
+        A.add(&h.cc_newl, npix);
+        A.add(&h.cc_first, M);
+        A.add(&h.cc_list, M);
+    }
     if (h.model == SEG_PC_DECONV) {
         A.add(&h.psf, 2 * SEG_PSF_MAX_RADIUS + 1);
         A.add(&h.psf_n, (size_t)h.W + h.H + h.D);
@@ -592,11 +610,13 @@ int stepper_build(Stepper& s)
     std::vector<unsigned> prefix;
     s.any_global = false;
     s.any_deconv = false;
+    s.any_split = false;
     for (int i = 0; i < n; i++) {
         jobs[i] = s.members[i]->h;
         if (jobs[i].model == SEG_PC_DECONV && jobs[i].psf_r < 0) return SEG_ESTATE;   // no PSF yet
         s.any_global = s.any_global || jobs[i].global_E;
         s.any_deconv = s.any_deconv || jobs[i].model == SEG_PC_DECONV;
+        s.any_split = s.any_split || jobs[i].topo_split;
     }
     int id_off[2] = {0, 0}, pf_off[2] = {0, 0};
     for (int gidx = 0; gidx < 2; gidx++) {
@@ -700,6 +720,11 @@ cudaError_t stepper_enqueue_stages(Stepper& s)
     if ((e = launch_rounds(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 8)) != cudaSuccess) return e;
     if ((e = launch_moves(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
+    if (s.any_split)                    // split regions: pieces get new labels, statistics rebuilt
+        for (int i = 0; i < n; i++)
+            if (s.members[i]->h.topo_split &&
+                (e = launch_relabel(s.d_jobs, i, s.members[i]->h, s.sms, s.work)) != cudaSuccess)
+                return e;
     if ((e = stage_mark(s, 9)) != cudaSuccess) return e;
     if ((e = launch_finish(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
     return stage_mark(s, 10);
@@ -871,8 +896,9 @@ int seg_estimate_bytes(const seg_params* p, int32_t nlabels, size_t* bytes)
     int rc = validate(p);
     if (rc) return rc;
     if (nlabels < 1 || !bytes) return SEG_EINVAL;
+    if ((p->topology & SEG_TOPO_SPLIT) && p->max_labels && p->max_labels < nlabels) return SEG_EINVAL;
     Plan P;
-    make_geometry(p, nlabels, 1, 254, P);
+    make_geometry(p, label_capacity(p, nlabels), 1, 254, P);
     *bytes = input_bytes(P.h.npix, p->dtype) + P.fixed.bytes +
              particle_bytes(default_pcap(P.h.npix, P.h.ndim), P.h.nbr_stride);
     return SEG_OK;
@@ -985,7 +1011,9 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     CKF(cudaStreamSynchronize(stream));
     if (scan.lab_min < 0 || scan.lab_max >= (1 << 24) || scan.bad) return fail(SEG_EINVAL);
     if (p->model == SEG_PS_POISSON && scan.neg) return fail(SEG_EINVAL);   // Poisson counts are >= 0
-    const int M = scan.lab_max + 1;
+    const int M0 = scan.lab_max + 1;                 // labels in use
+    if ((p->topology & SEG_TOPO_SPLIT) && p->max_labels && p->max_labels < M0) return fail(SEG_EINVAL);
+    const int M = label_capacity(p, M0);             // label tables (room for new labels from splits)
     int slot_lo = 1, slot_hi = 1;
     float maxabs = 0.0f;
     if (p->dtype == SEG_F32) {
@@ -1058,7 +1086,9 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     hc.mode = p->gradient;
     hc.best_A = -1;
     hc.perim = (long long)scan.pairs;
+    hc.n_labels = M0;
     memset(c->h_ctr, 0, sizeof(Counters));
+    c->h_ctr->n_labels = M0;
     CKF(cudaMemsetAsync(c->h.pmap, 0, npix * 8, stream));
     CKF(cudaMemsetAsync(c->h.tile_word, 0, (size_t)c->h.ntiles * 8, stream));
     CKF(cudaMemsetAsync(c->h.st_n, 0, (size_t)M * 8, stream));
@@ -1241,7 +1271,7 @@ int seg_set_state(seg_ctx* c, const seg_state* in)
 int seg_info(seg_ctx* c, int32_t* nlabels, int64_t shape[3])
 {
     if (!c) return SEG_EINVAL;
-    if (nlabels) *nlabels = c->h.M;
+    if (nlabels) *nlabels = c->h_ctr->n_labels;   // grows when regions split
     if (shape) {
         shape[0] = c->h.D;
         shape[1] = c->h.H;

@@ -37,7 +37,7 @@ struct WaitBound {
 // region models whose data term uses local means over a ball (the piecewise-smooth ones)
 __host__ __device__ __forceinline__ bool is_ps(int model) { return model == SEG_PS || model == SEG_PS_POISSON; }
 
-constexpr unsigned char kFlagFixup = 1, kFlagCand = 2, kFlagAcc = 4;
+constexpr unsigned char kFlagFixup = 1, kFlagCand = 2, kFlagAcc = 4, kFlagSplit = 8;
 constexpr int kUndecided = 0, kAccepted = 1, kRejected = 2;
 
 // Division by an invariant 32-bit divisor with one multiply-high (Granlund & Montgomery,
@@ -84,6 +84,9 @@ struct Counters {
     long long t_best;
     long long cum_particles; // particles summed over executed iterations
     long long perim;        // |Gamma|: adjacent pixel pairs with different labels (current labels)
+    int n_labels;           // labels in use (grows when regions split)
+    unsigned n_split;       // accepted moves of the iteration admitted by the split rule
+    unsigned n_newcomp;     // pieces given new labels by the iteration's relabelling
     long long g_lim;        // E = |Gamma| mode: interaction partners have d^2 < g_lim
     seg_status last;        // status of the last executed iteration
 };
@@ -138,6 +141,11 @@ struct alignas(64) Job {
     int M;                    // number of labels
     int osc_window;           // L2 fallback window (0 = never)
     int topo_vanish;          // a region's last pixel may leave it (SEG_TOPO_VANISH)
+    int topo_split;           // a region may split (SEG_TOPO_SPLIT); M is then the label capacity
+    int* cc_parent;           // ... relabelling: union-find parent per pixel [npix]
+    int* cc_newl;             // ... new label of each piece, at the piece's root pixel [npix]
+    int* cc_first;            // ... smallest pixel index of each label [M]
+    int* cc_list;             // ... roots of the pieces that get new labels [M]
     int inject;               // test-only fault injection (SEG_INJECT_*)
     int nbr_stride;           // neighbour-list slots per candidate: 8 (2D) | 26 (3D)
     int slot_lo, nS, nQ;      // exact float32 sums: exponent slots [slot_lo, slot_lo + nS)
@@ -394,7 +402,9 @@ cudaError_t launch_lists(const Job* jobs, int njobs, int sms, cudaStream_t s);
 cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s);
 cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
-cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s);
+cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s, bool after_split = false);
+cudaError_t launch_stats_zero_after_split(const Job* jobs, int j, const Job& h, cudaStream_t s);
+cudaError_t launch_relabel(const Job* jobs, int j, const Job& h, int sms, cudaStream_t s);
 cudaError_t launch_deconv(const Job* jobs, int j, const Job& h, int sms, cudaStream_t s);
 cudaError_t launch_psf_norms(const Job* job, const Job& h, cudaStream_t s);
 cudaError_t launch_scan_inputs(const void* I, int dtype, const int* L, int ndim, int D, int H, int W, InputScan* out,

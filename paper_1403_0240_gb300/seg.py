@@ -21,7 +21,8 @@ SEG_PSF_MAX_RADIUS = 512
 MODELS = {"pc": SEG_PC, "ps": SEG_PS, "psp": SEG_PS_POISSON, "pcd": SEG_PC_DECONV}
 SEG_SOBOLEV, SEG_L2, SEG_SOBOLEV_GLOBAL = 0, 1, 2
 SEG_STATS_EXACT, SEG_STATS_F64, SEG_STATS_KAHAN32 = 0, 1, 2
-SEG_TOPO_STRICT, SEG_TOPO_VANISH = 0, 1
+SEG_TOPO_STRICT, SEG_TOPO_VANISH, SEG_TOPO_SPLIT = 0, 1, 2
+TOPOLOGY = {"strict": 0, "vanish": 1, "split": 2, "vanish+split": 3}
 STATS_MODES = {"exact": SEG_STATS_EXACT, "f64": SEG_STATS_F64, "kahan32": SEG_STATS_KAHAN32}
 SEG_INJECT_NONE, SEG_INJECT_WITHHELD_COPY = 0, 1
 
@@ -32,7 +33,7 @@ class Params(C.Structure):
                 ("lam", C.c_double), ("cutoff", C.c_double), ("ps_radius", C.c_double),
                 ("gradient", C.c_int32), ("osc_window", C.c_int32), ("stats_mode", C.c_int32),
                 ("validate", C.c_int32), ("cell_edge", C.c_int32), ("tile", C.c_int32 * 3),
-                ("topology", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("topology", C.c_int32), ("max_labels", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class TuneEntry(C.Structure):
@@ -168,7 +169,7 @@ def _stream_handle(stream):
 
 def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_radius=0.0,
                 gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None, stats="exact",
-                topology=0) -> Params:
+                topology=0, max_labels=0) -> Params:
     shape = tuple(int(s) for s in image.shape)
     p = Params()
     p.ndim = len(shape)
@@ -183,7 +184,8 @@ def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_ra
                                                                   "sobolev_global": SEG_SOBOLEV_GLOBAL}[gradient]
     p.osc_window = int(osc_window)
     p.stats_mode = stats if isinstance(stats, int) else STATS_MODES[stats]
-    p.topology = topology if isinstance(topology, int) else {"strict": SEG_TOPO_STRICT, "vanish": SEG_TOPO_VANISH}[topology]
+    p.topology = topology if isinstance(topology, int) else TOPOLOGY[topology]
+    p.max_labels = int(max_labels)
     p.validate = int(bool(validate))
     p.cell_edge = int(cell_edge)
     if tile is not None:
@@ -223,9 +225,9 @@ class Context:
 
     def __init__(self, image, labels0, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_radius=0.0,
                  gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None, stream=None,
-                 psf=None, stats="exact", topology=0):
+                 psf=None, stats="exact", topology=0, max_labels=0):
         self.params = make_params(image, model, connectivity, lam, cutoff, ps_radius, gradient, osc_window,
-                                  validate, cell_edge, tile, stats, topology)
+                                  validate, cell_edge, tile, stats, topology, max_labels)
         self.shape = tuple(int(s) for s in image.shape)
         ip, ikeep = _ptr(image)
         lp, lkeep = _ptr(labels0 if _is_torch(labels0) else np.asarray(labels0, dtype=np.int32))
@@ -234,9 +236,6 @@ class Context:
         h = C.c_void_p()
         _check(lib().seg_init(C.byref(self.params), ip, lp, _stream_handle(stream), C.byref(h)), "seg_init")
         self._h = h
-        nl = C.c_int32(0)
-        lib().seg_info(h, C.byref(nl), None)
-        self.nlabels = int(nl.value)
         self.npix = int(np.prod(self.shape))
         if psf is not None:
             try:
@@ -259,6 +258,13 @@ class Context:
                     ps_radius=w.ps_radius, psf=getattr(w, "psf", None))
         args.update(kw)
         return cls(w.image, w.labels0, **args)
+
+    @property
+    def nlabels(self) -> int:
+        """Labels in use (grows when regions split, SEG_TOPO_SPLIT)."""
+        nl = C.c_int32(0)
+        _check(lib().seg_info(self.handle, C.byref(nl), None), "seg_info")
+        return int(nl.value)
 
     @property
     def handle(self):

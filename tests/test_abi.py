@@ -34,7 +34,7 @@ def test_header_symbols_exported(libseg):
 
 
 def test_struct_layouts():
-    # seg_params: 2 x int32, 3 x int64, 2 x int32, 3 x double, 5 x int32, 3 x int32 tile, topology, 3 reserved int32
+    # seg_params: 2 x int32, 3 x int64, 2 x int32, 3 x double, 5 x int32, 3 x int32 tile, topology, max_labels, 2 reserved int32
     assert C.sizeof(seg.Params) == 112
     assert C.sizeof(seg.Status) == 72
     assert C.sizeof(seg.State) == 32
@@ -59,12 +59,24 @@ def test_strerror_and_validation_without_gpu(libseg):
         p.tile[0], p.tile[1], p.tile[2] = tile
         assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == code, tile
     p.tile[0] = p.tile[1] = p.tile[2] = 0
-    p.reserved[2] = 1
+    p.reserved[1] = 1
     assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL
-    p.reserved[2] = 0
-    for topology, code in [(seg.SEG_TOPO_STRICT, seg.SEG_OK), (seg.SEG_TOPO_VANISH, seg.SEG_OK), (2, seg.SEG_EINVAL)]:
+    p.reserved[1] = 0
+    for topology, code in [(seg.SEG_TOPO_STRICT, seg.SEG_OK), (seg.SEG_TOPO_VANISH, seg.SEG_OK),
+                           (seg.SEG_TOPO_SPLIT, seg.SEG_OK), (seg.SEG_TOPO_VANISH | seg.SEG_TOPO_SPLIT, seg.SEG_OK),
+                           (4, seg.SEG_EINVAL), (-1, seg.SEG_EINVAL)]:
         p.topology = topology
         assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == code, topology
+    # with splits the label tables (and the relabelling arrays) grow to the capacity
+    p.topology = seg.SEG_TOPO_STRICT
+    assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_OK
+    strict = out.value
+    p.topology = seg.SEG_TOPO_SPLIT
+    assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_OK and out.value > strict
+    p.max_labels = 1                               # below the initial count
+    assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL
+    p.max_labels = 0
+    p.topology = seg.SEG_TOPO_STRICT
 
 
 def test_model_and_stats_mode_validation_without_gpu(libseg):

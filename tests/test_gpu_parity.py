@@ -212,3 +212,82 @@ def test_region_vanishing_matches_oracle():
     counts = np.bincount(ctx.labels().ravel(), minlength=lab)
     assert (counts[1:] == 0).any()          # some seeds have vanished
     ctx.close()
+
+
+def _two_blobs(shape3d=False):
+    rng = np.random.default_rng(5)
+    if shape3d:
+        I = np.zeros((20, 24, 40), np.float32)
+        I[4:16, 6:18, 3:15] = 1.0
+        I[4:16, 6:18, 25:37] = 1.0
+        L = np.zeros(I.shape, np.int32)
+        L[7:13, 9:15, 6:34] = 1                       # one bar across both cubes
+    else:
+        I = np.zeros((96, 128), np.float32)
+        I[20:76, 10:50] = 1.0
+        I[20:76, 78:118] = 1.0
+        L = np.zeros(I.shape, np.int32)
+        L[30:66, 18:110] = 1                          # one rectangle across both blobs
+    I += rng.normal(0.0, 0.1, I.shape).astype(np.float32)
+    return I, L
+
+
+@pytest.mark.parametrize("topology,three_d", [(2, False), (3, False), (2, True)])
+def test_region_splitting_matches_oracle(topology, three_d):
+    # the region loses the pixels between the blobs, splits, and its pieces get new labels,
+    # iteration by iteration as in the oracle
+    import oracle
+    I, L = _two_blobs(three_d)
+    conn = 6 if three_d else 4
+    lam, cutoff = (0.02, 3.0)
+    ctx = seg.Context(I, L, model="pc", connectivity=conn, lam=lam, cutoff=cutoff, topology=topology)
+    p = oracle.make_params(I, L, "pc", conn, lam, cutoff, topology=topology, nlabels=2)
+    run = oracle.Run(p, I, L)
+    for it in range(40 if not three_d else 25):
+        compare_step(ctx, run, f"split it{it}")
+        assert ctx.nlabels == run.state()["nlabels"]
+    assert ctx.nlabels >= 3
+    n, S, Q = ctx.stats()
+    assert np.array_equal(n, np.bincount(ctx.labels().ravel(), minlength=ctx.nlabels))
+    ctx.close()
+
+
+def test_split_beyond_the_label_capacity_is_reported():
+    I, L = _two_blobs()
+    ctx = seg.Context(I, L, model="pc", lam=0.02, cutoff=3.0, topology="split", max_labels=2)
+    with pytest.raises(seg.SegError) as e:
+        for _ in range(40):
+            ctx.step(1)
+    assert e.value.code == seg.SEG_ENOMEM
+    ctx.close()
+    with pytest.raises(seg.SegError) as e:
+        seg.Context(I, L, model="pc", topology="split", max_labels=1)   # below the initial count
+    assert e.value.code == seg.SEG_EINVAL
+
+
+def test_split_job_in_a_batch_equals_solo():
+    I, L = _two_blobs()
+    w2 = synth.disks(64, 80, seed=9)
+
+    def solo(make):
+        c = make()
+        for _ in range(30):
+            c.step(1)
+        out = (c.labels().copy(), c.nlabels)
+        c.close()
+        return out
+
+    mk1 = lambda: seg.Context(I, L, model="pc", lam=0.02, cutoff=3.0, topology="split")
+    mk2 = lambda: seg.Context.from_workload(w2)
+    r1, r2 = solo(mk1), solo(mk2)
+    a, b = mk1(), mk2()
+    batch = seg.Batch()
+    batch.add(a)
+    batch.add(b)
+    for _ in range(30):
+        batch.step(1)
+    assert np.array_equal(a.labels(), r1[0]) and a.nlabels == r1[1]
+    assert np.array_equal(b.labels(), r2[0])
+    batch.close()
+    a.close()
+    b.close()
