@@ -49,7 +49,8 @@ class Params(C.Structure):
                 ("lam", C.c_double), ("cutoff", C.c_double), ("ps_radius", C.c_double),
                 ("gradient", C.c_int32), ("osc_window", C.c_int32),
                 ("nlabels", C.c_int32), ("pad_", C.c_int32), ("mu_floor", C.c_double),
-                ("psf_r", C.c_int32), ("topology", C.c_int32), ("psf", C.c_void_p)]
+                ("psf_r", C.c_int32), ("topology", C.c_int32), ("psf", C.c_void_p),
+                ("regulariser", C.c_int32), ("pad2_", C.c_int32), ("curv_radius", C.c_double)]
 
 
 class State(C.Structure):
@@ -90,6 +91,10 @@ def lib():
             L.orc_energy.argtypes = [P(Params), vp, vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]
             L.orc_delta_perimeter.restype = C.c_int64
             L.orc_delta_perimeter.argtypes = [P(Params), vp, C.c_uint32, C.c_int32, C.c_int32]
+            L.orc_ball_balance.restype = C.c_int64
+            L.orc_ball_balance.argtypes = [P(Params), vp, C.c_uint32, C.c_int32, C.c_int32]
+            L.orc_curvature_weight.restype = C.c_double
+            L.orc_curvature_weight.argtypes = [P(Params)]
             L.orc_sobolev.restype = None
             L.orc_sobolev.argtypes = [P(Params), C.c_int64, vp, vp, vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
             L.orc_simple_2d.restype = C.c_int
@@ -127,7 +132,7 @@ def _ptr(a: np.ndarray | None):
 def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", connectivity: int | None = None,
                 lam: float = 0.0, cutoff: float = 3.0, ps_radius: float = 0.0,
                 gradient: str | int = "sobolev", osc_window: int = 0, nlabels: int | None = None,
-                psf: np.ndarray | None = None, topology: int = 0) -> Params:
+                psf: np.ndarray | None = None, topology: int = 0, curv_radius: float = 0.0) -> Params:
     shape = image.shape
     if image.ndim == 2:
         D, H, W = 1, shape[0], shape[1]
@@ -150,6 +155,9 @@ def make_params(image: np.ndarray, labels: np.ndarray, model: str | int = "pc", 
     p.mu_floor = math.ldexp(max(1.0, float(np.abs(image).max()) if image.size else 1.0), -20)
     set_psf(p, psf)
     p.topology = int(topology)
+    # curvature regulariser when a ball radius is given, else the length prior
+    p.regulariser = 1 if curv_radius > 0 else 0
+    p.curv_radius = float(curv_radius)
     return p
 
 
@@ -243,6 +251,17 @@ def energy(p: Params, I: np.ndarray, L: np.ndarray, idx, l, c, n=None, S=None, w
 def delta_perimeter(p: Params, L: np.ndarray, x: int, l: int, c: int) -> int:
     L = np.ascontiguousarray(L, dtype=np.int32)
     return lib().orc_delta_perimeter(C.byref(p), _ptr(L), x, l, c)
+
+
+def ball_balance(p: Params, L: np.ndarray, x: int, l: int, c: int) -> int:
+    """Curvature regulariser: pixels of label l minus pixels of label c in the ball of radius
+    p.curv_radius around pixel x."""
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    return lib().orc_ball_balance(C.byref(p), _ptr(L), x, l, c)
+
+
+def curvature_weight(p: Params) -> float:
+    return lib().orc_curvature_weight(C.byref(p))
 
 
 def perimeter(p: Params, L: np.ndarray) -> int:

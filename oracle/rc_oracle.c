@@ -417,7 +417,51 @@ int64_t orc_perimeter(const orc_params* p, const int32_t* L)
     return P;
 }
 
-/* Energy difference of moving particle (x: l -> c), data term + lambda * length. */
+/* ------------------------------------------------------------------ */
+/* Curvature regulariser (reading of the curvature regularisation used with weight lambda in the
+ * experiments; RC estimates curvature by counting pixels in a sphere around x). Integral
+ * invariants (Pottmann et al. 2007): a ball of radius rho centred on the boundary of a region
+ * holds A = (pi/2) rho^2 - (kappa/3) rho^3 + O(rho^4) of it in 2D, and
+ * V = (2 pi/3) rho^3 - (pi/4) H rho^4 + O(rho^5) in 3D, H = (kappa_1 + kappa_2)/2 the mean
+ * curvature. With A_m(x) the ball's pixels of label m this gives kappa_m = 3 ((pi/2) rho^2 - A_m)
+ * / rho^3 and kappa_1 + kappa_2 = 2 H_m = 8 ((2 pi/3) rho^3 - V_m) / (pi rho^4). Moving x from l to
+ * c shrinks l and grows c by one pixel; the first variation of a boundary's length (area) under
+ * a normal displacement of unit area (volume) is its curvature (kappa_1 + kappa_2), and every
+ * interface bounds two regions, so |Gamma| = (1/2) sum_m |boundary of m| changes by half the
+ * difference of the two curvatures. The constant terms cancel, leaving w (A_l - A_c) with
+ * w = lambda * 3 / (2 rho^3) (2D) and lambda * 4 / (pi rho^4) (3D). */
+int64_t orc_ball_balance(const orc_params* p, const int32_t* L, uint32_t xi, int32_t l, int32_t c)
+{
+    int Ri = (int)floor(p->curv_radius);
+    double R2 = p->curv_radius * p->curv_radius;
+    int Rz = p->ndim == 3 ? Ri : 0;
+    int64_t z, y, x;
+    coords(p, xi, &z, &y, &x);
+    int64_t bal = 0;
+    for (int dz = -Rz; dz <= Rz; dz++)
+        for (int dy = -Ri; dy <= Ri; dy++)
+            for (int dx = -Ri; dx <= Ri; dx++) {
+                int64_t d2 = (int64_t)dz * dz + (int64_t)dy * dy + (int64_t)dx * dx;
+                if (!((double)d2 <= R2)) continue;
+                int64_t zz = z + dz, yy = y + dy, xx = x + dx;
+                if (!inside(p, zz, yy, xx)) continue;
+                int32_t m = L[(zz * p->H + yy) * p->W + xx];
+                if (m == l) bal++;
+                else if (m == c) bal--;
+            }
+    return bal;
+}
+
+/* the weight, evaluated as written (products and one quotient, no sum) */
+double orc_curvature_weight(const orc_params* p)
+{
+    double r = p->curv_radius;
+    if (p->ndim == 3) return p->lambda * (4.0 / (3.141592653589793 * (r * r * r * r)));
+    return p->lambda * (3.0 / (2.0 * (r * r * r)));
+}
+
+/* Energy difference of moving particle (x: l -> c), data term + regulariser (lambda * change
+ * of the contour length, or the curvature term above). */
 void orc_energy(const orc_params* p, const void* I, const int32_t* L,
                 const int64_t* n, const double* S, int64_t N,
                 const uint32_t* idx, const int32_t* l, const int32_t* c, double* dE, double* scale)
@@ -504,9 +548,17 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
                                2.0 * fabs(b) * (fabs(v) + al / (double)cl) + a * a + b * b;
             }
         }
-        int64_t dP = orc_delta_perimeter(p, L, xi, lp, cp);
-        dE[k] = data + p->lambda * (double)dP;
-        if (scale) scale[k] += fabs(p->lambda * (double)dP);
+        int64_t dP;
+        double w;
+        if (p->regulariser == 1) {
+            dP = orc_ball_balance(p, L, xi, lp, cp);
+            w = orc_curvature_weight(p);
+        } else {
+            dP = orc_delta_perimeter(p, L, xi, lp, cp);
+            w = p->lambda;
+        }
+        dE[k] = data + w * (double)dP;
+        if (scale) scale[k] += fabs(w * (double)dP);
     }
     free(G);
 }

@@ -82,6 +82,10 @@ typedef struct {
                             labels) */
     const double* psf;   /* deconvolving model: symmetric 1D PSF profile k(-r..r), the same on
                             every axis (K(x) = prod_axes k(x_a)) */
+    int32_t regulariser; /* 0 = length prior lambda * (change of unlike neighbour pairs);
+                            1 = curvature from ball counts, weight from lambda (orc_curvature_weight) */
+    int32_t pad2_;
+    double curv_radius;  /* regulariser 1: ball radius rho >= 1 */
 } orc_params;
 
 typedef struct {
@@ -109,6 +113,12 @@ double  orc_kernel_eq5(double r, double E, double eps);
  * ln x = e ln 2 + 2 (y + y^3/3 + ... + y^23/23), y = (m - 1)/(m + 1); every operation an IEEE
  * double operation in a fixed order */
 double  orc_log(double x);
+
+/* Curvature regulariser: A_l(x) - A_c(x), the pixels of label l minus those of label c in the
+ * ball |y - x|^2 <= rho^2 around x (x counts in its own label; pixels outside the image in
+ * neither), and the weight w with which it enters the energy difference. */
+int64_t orc_ball_balance(const orc_params* p, const int32_t* L, uint32_t xi, int32_t l, int32_t c);
+double  orc_curvature_weight(const orc_params* p);
 
 int64_t orc_extract(const orc_params* p, const int32_t* L,
                     uint32_t* idx, int32_t* l, int32_t* c, int64_t cap);
