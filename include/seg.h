@@ -84,6 +84,18 @@ enum { SEG_SOBOLEV = 0, SEG_L2 = 1, SEG_SOBOLEV_GLOBAL = 2 };
  *                   of the components' smallest pixel indices (seg_info reports the count).
  * Fusion is not provided: the paper defers its rule to a reference that is not available. */
 enum { SEG_TOPO_STRICT = 0, SEG_TOPO_VANISH = 1, SEG_TOPO_SPLIT = 2 };
+/* regulariser of the energy difference (seg_params.regulariser):
+ * SEG_REG_LENGTH    - lambda * dP, dP the change of the number of connectivity-adjacent pixel
+ *                     pairs with different labels (the length prior of Eq. 10);
+ * SEG_REG_CURVATURE - curvature regularisation from the pixel counts of a ball (RC's sphere
+ *                     estimate; integral invariants of Pottmann et al. 2007): moving x from l to
+ *                     c adds w (A_l(x) - A_c(x)), A_m(x) the pixels of label m within distance
+ *                     curv_radius = rho of x (x counted in l, pixels outside the image in
+ *                     neither), w = lambda * (3.0 / (2.0 * (rho*rho*rho))) in 2D and
+ *                     lambda * (4.0 / (pi * (rho*rho*rho*rho))) in 3D, evaluated in FP64 as
+ *                     written: the first variation of |Gamma| with each region's curvature
+ *                     taken from its share of the ball. */
+enum { SEG_REG_LENGTH = 0, SEG_REG_CURVATURE = 1 };
 /* region sums of I and I^2 (precision study; counts are exact int64 in every mode):
  * SEG_STATS_EXACT   - exact (int64 fixed point), rounded once to FP64: the means are the FP64
  *                     definition's bit for bit, results are reproducible (default);
@@ -123,7 +135,10 @@ typedef struct {
     int32_t max_labels;    /* with SEG_TOPO_SPLIT: label capacity (labels 0..max_labels-1), >= the
                               initial count; 0 = max(2 M, M + 256) for M initial labels. A split
                               beyond it ends the iteration with SEG_ENOMEM. Ignored otherwise */
-    int32_t reserved[2];   /* must be zero */
+    int32_t regulariser;   /* SEG_REG_LENGTH (0): lambda * change of the unlike neighbour pairs;
+                              SEG_REG_CURVATURE (1): curvature from ball counts, see below */
+    int32_t reserved;      /* must be zero */
+    double  curv_radius;   /* SEG_REG_CURVATURE: ball radius rho, 1 <= rho <= 16; ignored otherwise */
 } seg_params;
 
 typedef struct {

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libseg.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["k_tile.cu", "k_select.cu", "k_global.cu", "k_deconv.cu", "k_relabel.cu", "seg_api.cu", "seg_noalloc.cu"]
+SOURCES = ["k_tile.cu", "k_select.cu", "k_global.cu", "k_deconv.cu", "k_relabel.cu", "k_curv.cu", "seg_api.cu", "seg_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", f"-I{INCLUDE}"]
 

@@ -320,6 +320,18 @@ __device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
             data = __dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b));
         }
     }
+    if (J.curv) {
+        // curvature regulariser: pixels of l minus pixels of c in the ball, weight w
+        int bal = 0;
+        for (int u = 0; u < J.cv_n; u++) {
+            const int4 d = J.cv_off[u];
+            const int xx = x + d.z, yy = y + d.y, zz = z + d.x;
+            if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
+            const int m = J.L[((long long)zz * J.H + yy) * J.W + xx];
+            bal += (int)(m == l) - (int)(m == c);
+        }
+        return __dadd_rn(data, __dmul_rn(J.curv_w64, (double)bal));
+    }
     int dP = 0;
     const int nbz = J.ndim == 3 ? 1 : 0;
     const int off[6][3] = {{0, 0, -1}, {0, 0, 1}, {0, -1, 0}, {0, 1, 0}, {-1, 0, 0}, {1, 0, 0}};

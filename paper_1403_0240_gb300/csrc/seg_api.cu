@@ -200,6 +200,7 @@ struct Stepper {
     bool any_global = false;       // a member uses E = |Gamma| (adds its two launches to the step)
     bool any_deconv = false;       // a member uses the deconvolving model (adds its PSF passes)
     bool any_split = false;        // a member may split regions (adds the relabelling passes)
+    bool any_curv = false;         // a member uses the curvature regulariser (adds its ball counts)
     bool profile = false;
     cudaEvent_t ev[11]{};
     cudaStream_t work = nullptr;   // library stream: graphs are captured and launched here
@@ -249,8 +250,9 @@ int validate(const seg_params* p)
     if (p->ndim == 2 && p->tile[0] > 1) return SEG_EINVAL;
     if (p->topology < 0 || p->topology > (SEG_TOPO_VANISH | SEG_TOPO_SPLIT)) return SEG_EINVAL;
     if (p->max_labels < 0 || p->max_labels > (1 << 24)) return SEG_EINVAL;
-    for (int i = 0; i < 2; i++)
-        if (p->reserved[i]) return SEG_EINVAL;
+    if (p->regulariser != SEG_REG_LENGTH && p->regulariser != SEG_REG_CURVATURE) return SEG_EINVAL;
+    if (p->regulariser == SEG_REG_CURVATURE && (!(p->curv_radius >= 1.0) || p->curv_radius > 16.0)) return SEG_EINVAL;
+    if (p->reserved) return SEG_EINVAL;
     return SEG_OK;
 }
 
@@ -287,7 +289,7 @@ struct Plan {
     Job h{};
     std::vector<float> klut;
     std::vector<double> klut64;
-    std::vector<int4> ps_off, nb_off;
+    std::vector<int4> ps_off, nb_off, cv_off;
     Arena fixed;
 };
 
@@ -324,8 +326,16 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     const int R = (int)std::floor(p->ps_radius);
     h.ps_staged = (is_ps(h.model) && h.ndim == 2 && R <= 32) ? 1 : 0;
     h.halo = h.ps_staged ? std::max(1, R) : 1;
-    h.lambda64 = p->lambda;
-    h.lambda32 = (float)p->lambda;
+    h.curv = p->regulariser == SEG_REG_CURVATURE ? 1 : 0;
+    // with the curvature regulariser the length term's weight is zero and the ball term's weight w
+    h.lambda64 = h.curv ? 0.0 : p->lambda;
+    h.lambda32 = (float)h.lambda64;
+    if (h.curv) {
+        const double r = p->curv_radius;
+        h.curv_w64 = h.ndim == 3 ? p->lambda * (4.0 / (3.141592653589793 * (r * r * r * r)))
+                                 : p->lambda * (3.0 / (2.0 * (r * r * r)));
+        h.curv_w32 = (float)h.curv_w64;
+    }
     h.cutoff = p->cutoff;
     h.E = 2.0 * p->cutoff;
     h.r2max = largest_d2_below(p->cutoff);
@@ -357,6 +367,17 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
                     if ((double)d2 <= R2) P.ps_off.push_back(make_int4(dz, dy, dx, d2));
                 }
     }
+    if (h.curv) {
+        const int Rc = (int)std::floor(p->curv_radius);
+        const double R2 = p->curv_radius * p->curv_radius;
+        for (int dz = -Rc * rz; dz <= Rc * rz; dz++)
+            for (int dy = -Rc; dy <= Rc; dy++)
+                for (int dx = -Rc; dx <= Rc; dx++) {
+                    int d2 = dz * dz + dy * dy + dx * dx;
+                    if ((double)d2 <= R2) P.cv_off.push_back(make_int4(dz, dy, dx, d2));
+                }
+    }
+    h.cv_n = (int)P.cv_off.size();
     const int rr = (int)std::floor(std::sqrt((double)h.r2max));
     for (int dz = -rr * rz; dz <= rr * rz; dz++)
         for (int dy = -rr; dy <= rr; dy++)
@@ -409,6 +430,7 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     A.add((double**)&h.klut64, P.klut64.size());
     A.add((int4**)&h.ps_off, std::max<size_t>(1, P.ps_off.size()));
     A.add((int4**)&h.nb_off, P.nb_off.size());
+    if (h.curv) A.add((int4**)&h.cv_off, P.cv_off.size());
     A.add(&h.gK32, (size_t)h.gd2max + 1);
     A.add(&h.gK64, (size_t)h.gd2max + 1);
     h.psf_r = -1;
@@ -611,12 +633,14 @@ int stepper_build(Stepper& s)
     s.any_global = false;
     s.any_deconv = false;
     s.any_split = false;
+    s.any_curv = false;
     for (int i = 0; i < n; i++) {
         jobs[i] = s.members[i]->h;
         if (jobs[i].model == SEG_PC_DECONV && jobs[i].psf_r < 0) return SEG_ESTATE;   // no PSF yet
         s.any_global = s.any_global || jobs[i].global_E;
         s.any_deconv = s.any_deconv || jobs[i].model == SEG_PC_DECONV;
         s.any_split = s.any_split || jobs[i].topo_split;
+        s.any_curv = s.any_curv || jobs[i].curv;
     }
     int id_off[2] = {0, 0}, pf_off[2] = {0, 0};
     for (int gidx = 0; gidx < 2; gidx++) {
@@ -699,6 +723,9 @@ cudaError_t stepper_enqueue_stages(Stepper& s)
     if ((e = stage_mark(s, 1)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_extract(s.grp[gidx], gidx + 2, s.smem_x[gidx], s.work)) != cudaSuccess) return e;
+    if (s.any_curv)                     // the curvature term, before the Sobolev sums read dE
+        for (int i = 0; i < n; i++)
+            if (s.members[i]->h.curv && (e = launch_curvature(s.d_jobs, i, s.sms, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 2)) != cudaSuccess) return e;
     if (s.any_global && (e = launch_global_lut(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
@@ -1101,6 +1128,8 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     if (!P.ps_off.empty())
         CKF(cudaMemcpyAsync((void*)c->h.ps_off, P.ps_off.data(), P.ps_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
     CKF(cudaMemcpyAsync((void*)c->h.nb_off, P.nb_off.data(), P.nb_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+    if (!P.cv_off.empty())
+        CKF(cudaMemcpyAsync((void*)c->h.cv_off, P.cv_off.data(), P.cv_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
     CKF(cudaMemcpyAsync(c->d_ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, stream));
     CKF(cudaMemcpyAsync(c->d_self, &c->h, sizeof(Job), cudaMemcpyHostToDevice, stream));
     CKF(launch_stats_init(c->d_self, 0, npix, stream));

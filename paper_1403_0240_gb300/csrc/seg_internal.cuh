@@ -117,8 +117,13 @@ struct alignas(64) Job {
     float maxabs;             // largest |I| of the image
     float mu_floor32;         // Poisson model: local means below this are taken as this
     double mu_floor64;
-    float lambda32;
+    float lambda32;           // length-prior weight (0 with the curvature regulariser)
     double lambda64;
+    int curv;                 // curvature regulariser: dE += w (A_l - A_c) over the ball cv_off
+    int cv_n;
+    const int4* cv_off;       // ... ball offsets (dz, dy, dx, d2), row-major
+    float curv_w32;           // ... w rounded to float
+    double curv_w64;          // ... w
     double cutoff, E;         // E = 2 * cutoff (Eq. 5 length scale)
     int r2max;                // interaction partners: squared distance <= r2max  (< cutoff^2)
     int ps_n;                 // piecewise-smooth ball offsets, row-major (dz, dy, dx, d2)
@@ -405,6 +410,7 @@ cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cud
 cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s, bool after_split = false);
 cudaError_t launch_stats_zero_after_split(const Job* jobs, int j, const Job& h, cudaStream_t s);
 cudaError_t launch_relabel(const Job* jobs, int j, const Job& h, int sms, cudaStream_t s);
+cudaError_t launch_curvature(const Job* jobs, int j, int sms, cudaStream_t s);
 cudaError_t launch_deconv(const Job* jobs, int j, const Job& h, int sms, cudaStream_t s);
 cudaError_t launch_psf_norms(const Job* job, const Job& h, cudaStream_t s);
 cudaError_t launch_scan_inputs(const void* I, int dtype, const int* L, int ndim, int D, int H, int W, InputScan* out,

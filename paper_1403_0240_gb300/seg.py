@@ -23,6 +23,7 @@ SEG_SOBOLEV, SEG_L2, SEG_SOBOLEV_GLOBAL = 0, 1, 2
 SEG_STATS_EXACT, SEG_STATS_F64, SEG_STATS_KAHAN32 = 0, 1, 2
 SEG_TOPO_STRICT, SEG_TOPO_VANISH, SEG_TOPO_SPLIT = 0, 1, 2
 TOPOLOGY = {"strict": 0, "vanish": 1, "split": 2, "vanish+split": 3}
+SEG_REG_LENGTH, SEG_REG_CURVATURE = 0, 1
 STATS_MODES = {"exact": SEG_STATS_EXACT, "f64": SEG_STATS_F64, "kahan32": SEG_STATS_KAHAN32}
 SEG_INJECT_NONE, SEG_INJECT_WITHHELD_COPY = 0, 1
 
@@ -33,7 +34,8 @@ class Params(C.Structure):
                 ("lam", C.c_double), ("cutoff", C.c_double), ("ps_radius", C.c_double),
                 ("gradient", C.c_int32), ("osc_window", C.c_int32), ("stats_mode", C.c_int32),
                 ("validate", C.c_int32), ("cell_edge", C.c_int32), ("tile", C.c_int32 * 3),
-                ("topology", C.c_int32), ("max_labels", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("topology", C.c_int32), ("max_labels", C.c_int32), ("regulariser", C.c_int32),
+                ("reserved", C.c_int32), ("curv_radius", C.c_double)]
 
 
 class TuneEntry(C.Structure):
@@ -169,7 +171,7 @@ def _stream_handle(stream):
 
 def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_radius=0.0,
                 gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None, stats="exact",
-                topology=0, max_labels=0) -> Params:
+                topology=0, max_labels=0, curv_radius=0.0) -> Params:
     shape = tuple(int(s) for s in image.shape)
     p = Params()
     p.ndim = len(shape)
@@ -186,6 +188,9 @@ def make_params(image, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_ra
     p.stats_mode = stats if isinstance(stats, int) else STATS_MODES[stats]
     p.topology = topology if isinstance(topology, int) else TOPOLOGY[topology]
     p.max_labels = int(max_labels)
+    # curvature regulariser (SEG_REG_CURVATURE) when a ball radius is given, else the length prior
+    p.regulariser = SEG_REG_CURVATURE if curv_radius > 0 else SEG_REG_LENGTH
+    p.curv_radius = float(curv_radius)
     p.validate = int(bool(validate))
     p.cell_edge = int(cell_edge)
     if tile is not None:
@@ -225,9 +230,9 @@ class Context:
 
     def __init__(self, image, labels0, model="pc", connectivity=None, lam=0.0, cutoff=3.0, ps_radius=0.0,
                  gradient="sobolev", osc_window=0, validate=False, cell_edge=0, tile=None, stream=None,
-                 psf=None, stats="exact", topology=0, max_labels=0):
+                 psf=None, stats="exact", topology=0, max_labels=0, curv_radius=0.0):
         self.params = make_params(image, model, connectivity, lam, cutoff, ps_radius, gradient, osc_window,
-                                  validate, cell_edge, tile, stats, topology, max_labels)
+                                  validate, cell_edge, tile, stats, topology, max_labels, curv_radius)
         self.shape = tuple(int(s) for s in image.shape)
         ip, ikeep = _ptr(image)
         lp, lkeep = _ptr(labels0 if _is_torch(labels0) else np.asarray(labels0, dtype=np.int32))

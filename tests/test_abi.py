@@ -34,8 +34,9 @@ def test_header_symbols_exported(libseg):
 
 
 def test_struct_layouts():
-    # seg_params: 2 x int32, 3 x int64, 2 x int32, 3 x double, 5 x int32, 3 x int32 tile, topology, max_labels, 2 reserved int32
-    assert C.sizeof(seg.Params) == 112
+    # seg_params: 2 x int32, 3 x int64, 2 x int32, 3 x double, 5 x int32, 3 x int32 tile, topology,
+    # max_labels, regulariser, reserved int32, curv_radius double
+    assert C.sizeof(seg.Params) == 120
     assert C.sizeof(seg.Status) == 72
     assert C.sizeof(seg.State) == 32
     assert C.sizeof(seg.ParticleBuffers) == 9 * C.sizeof(C.c_void_p)
@@ -59,9 +60,16 @@ def test_strerror_and_validation_without_gpu(libseg):
         p.tile[0], p.tile[1], p.tile[2] = tile
         assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == code, tile
     p.tile[0] = p.tile[1] = p.tile[2] = 0
-    p.reserved[1] = 1
+    p.reserved = 1
     assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL
-    p.reserved[1] = 0
+    p.reserved = 0
+    # the curvature regulariser needs a ball radius in [1, 16]
+    for reg, radius, code in [(seg.SEG_REG_CURVATURE, 4.0, seg.SEG_OK), (seg.SEG_REG_CURVATURE, 0.5, seg.SEG_EINVAL),
+                              (seg.SEG_REG_CURVATURE, 17.0, seg.SEG_EINVAL), (seg.SEG_REG_LENGTH, 0.0, seg.SEG_OK),
+                              (2, 4.0, seg.SEG_EINVAL), (-1, 4.0, seg.SEG_EINVAL)]:
+        p.regulariser, p.curv_radius = reg, radius
+        assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == code, (reg, radius)
+    p.regulariser, p.curv_radius = seg.SEG_REG_LENGTH, 0.0
     for topology, code in [(seg.SEG_TOPO_STRICT, seg.SEG_OK), (seg.SEG_TOPO_VANISH, seg.SEG_OK),
                            (seg.SEG_TOPO_SPLIT, seg.SEG_OK), (seg.SEG_TOPO_VANISH | seg.SEG_TOPO_SPLIT, seg.SEG_OK),
                            (4, seg.SEG_EINVAL), (-1, seg.SEG_EINVAL)]:
