@@ -95,6 +95,12 @@ def lib():
             L.orc_ball_balance.argtypes = [P(Params), vp, C.c_uint32, C.c_int32, C.c_int32]
             L.orc_curvature_weight.restype = C.c_double
             L.orc_curvature_weight.argtypes = [P(Params)]
+            L.orc_fuse_pairs.restype = C.c_int64
+            L.orc_fuse_pairs.argtypes = [P(Params), vp, vp, vp, vp, C.c_int64]
+            L.orc_fuse_energy.restype = C.c_double
+            L.orc_fuse_energy.argtypes = [P(Params), vp, vp, C.c_int32, C.c_int32, C.c_int64]
+            L.orc_fuse.restype = C.c_int64
+            L.orc_fuse.argtypes = [P(Params), vp, vp]
             L.orc_sobolev.restype = None
             L.orc_sobolev.argtypes = [P(Params), C.c_int64, vp, vp, vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
             L.orc_simple_2d.restype = C.c_int
@@ -258,6 +264,28 @@ def ball_balance(p: Params, L: np.ndarray, x: int, l: int, c: int) -> int:
     p.curv_radius around pixel x."""
     L = np.ascontiguousarray(L, dtype=np.int32)
     return lib().orc_ball_balance(C.byref(p), _ptr(L), x, l, c)
+
+
+def fuse_pairs(p: Params, L: np.ndarray):
+    """Touching foreground label pairs (a < b) and their shared boundary pair counts B."""
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    n = lib().orc_fuse_pairs(C.byref(p), _ptr(L), None, None, None, 0)
+    a, b, B = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int64)
+    lib().orc_fuse_pairs(C.byref(p), _ptr(L), _ptr(a), _ptr(b), _ptr(B), n)
+    return a, b, B
+
+
+def fuse_energy(p: Params, n, S, a: int, b: int, B: int) -> float:
+    n = np.ascontiguousarray(n, np.int64)
+    S = np.ascontiguousarray(S, np.float64)
+    return lib().orc_fuse_energy(C.byref(p), _ptr(n), _ptr(S), a, b, B)
+
+
+def fuse(p: Params, I: np.ndarray, L: np.ndarray) -> tuple[np.ndarray, int]:
+    """One fusion pass (the label count of p must cover L); returns (new labels, fusions)."""
+    L = np.ascontiguousarray(L, dtype=np.int32).copy()
+    nf = lib().orc_fuse(C.byref(p), _ptr(np.ascontiguousarray(I)), _ptr(L))
+    return L, int(nf)
 
 
 def curvature_weight(p: Params) -> float:

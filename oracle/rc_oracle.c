@@ -896,6 +896,123 @@ int32_t orc_relabel(const orc_params* p, int32_t* L, int32_t nlabels)
     return next;
 }
 
+/* ------------------------------------------------------------------ */
+/* Fusion (topology bit 4, piecewise-constant model; reading of RC's controlled merging, whose
+ * criterion the paper leaves to its reference): after the moves of an iteration and the
+ * relabelling of split pieces, two touching foreground regions a < b fuse when that lowers the
+ * energy. Merging them changes the data term by exactly n_a n_b / (n_a + n_b) (mu_a - mu_b)^2
+ * (the sum of squared deviations about the joint mean) and removes the B_ab connectivity-
+ * adjacent pixel pairs between them from the contour, so
+ *     dE = w * (d * d) - lambda * B_ab,  w = (n_a * n_b) / (n_a + n_b),  d = mu_a - mu_b,
+ * evaluated in that order with the statistics after the moves. The pairs with dE < 0 are taken
+ * in ascending (dE, a, b); a pair is accepted when neither of its labels was accepted before in
+ * the iteration, and then b's pixels take label a. Returns the number of fusions. */
+typedef struct {
+    double dE;
+    int32_t a, b;
+} fuse_pair;
+
+static int cmp_u64(const void* x, const void* y)
+{
+    uint64_t a = *(const uint64_t*)x, b = *(const uint64_t*)y;
+    return (a > b) - (a < b);
+}
+
+static int cmp_fuse(const void* x, const void* y)
+{
+    const fuse_pair* u = (const fuse_pair*)x;
+    const fuse_pair* v = (const fuse_pair*)y;
+    if (u->dE != v->dE) return u->dE < v->dE ? -1 : 1;
+    if (u->a != v->a) return u->a < v->a ? -1 : 1;
+    return (u->b > v->b) - (u->b < v->b);
+}
+
+int64_t orc_fuse_pairs(const orc_params* p, const int32_t* L, int32_t* a_out, int32_t* b_out, int64_t* B_out,
+                       int64_t cap)
+{
+    int64_t npix = p->D * p->H * p->W;
+    uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(3 * npix + 1));
+    int64_t nk = 0;
+    for (int64_t z = 0; z < p->D; z++)
+        for (int64_t y = 0; y < p->H; y++)
+            for (int64_t x = 0; x < p->W; x++) {
+                int64_t i = (z * p->H + y) * p->W + x;
+                int32_t m = L[i];
+                if (m == 0) continue;
+                int64_t nb[3];
+                int k = 0;
+                if (x + 1 < p->W) nb[k++] = i + 1;
+                if (y + 1 < p->H) nb[k++] = i + p->W;
+                if (p->ndim == 3 && z + 1 < p->D) nb[k++] = i + p->W * p->H;
+                for (int u = 0; u < k; u++) {
+                    int32_t m2 = L[nb[u]];
+                    if (m2 == 0 || m2 == m) continue;
+                    uint32_t a = (uint32_t)(m < m2 ? m : m2), b = (uint32_t)(m < m2 ? m2 : m);
+                    keys[nk++] = ((uint64_t)a << 32) | b;
+                }
+            }
+    qsort(keys, (size_t)nk, sizeof(uint64_t), cmp_u64);
+    int64_t np = 0;
+    for (int64_t i = 0; i < nk;) {
+        int64_t j = i;
+        while (j < nk && keys[j] == keys[i]) j++;
+        if (np < cap) {
+            a_out[np] = (int32_t)(keys[i] >> 32);
+            b_out[np] = (int32_t)(keys[i] & 0xffffffffu);
+            B_out[np] = j - i;
+        }
+        np++;
+        i = j;
+    }
+    free(keys);
+    return np;
+}
+
+double orc_fuse_energy(const orc_params* p, const int64_t* n, const double* S, int32_t a, int32_t b, int64_t B)
+{
+    double na = (double)n[a], nb = (double)n[b];
+    double w = (na * nb) / (na + nb);
+    double d = S[a] / na - S[b] / nb;
+    return w * (d * d) - p->lambda * (double)B;
+}
+
+int64_t orc_fuse(const orc_params* p, const void* I, int32_t* L)
+{
+    int M = p->nlabels;
+    int64_t npix = p->D * p->H * p->W;
+    int64_t np = orc_fuse_pairs(p, L, NULL, NULL, NULL, 0);
+    size_t cap = (size_t)(np > 0 ? np : 1);
+    int32_t* a = (int32_t*)malloc(sizeof(int32_t) * cap);
+    int32_t* b = (int32_t*)malloc(sizeof(int32_t) * cap);
+    int64_t* B = (int64_t*)malloc(sizeof(int64_t) * cap);
+    orc_fuse_pairs(p, L, a, b, B, np);
+    int64_t* n = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
+    double* S = (double*)malloc(sizeof(double) * (size_t)M);
+    double* Q = (double*)malloc(sizeof(double) * (size_t)M);
+    orc_stats(p, I, L, n, S, Q);
+    fuse_pair* cand = (fuse_pair*)malloc(sizeof(fuse_pair) * cap);
+    int64_t nc = 0;
+    for (int64_t k = 0; k < np; k++) {
+        double dE = orc_fuse_energy(p, n, S, a[k], b[k], B[k]);
+        if (dE < 0.0) { cand[nc].dE = dE; cand[nc].a = a[k]; cand[nc].b = b[k]; nc++; }
+    }
+    qsort(cand, (size_t)nc, sizeof(fuse_pair), cmp_fuse);
+    char* used = (char*)calloc((size_t)M, 1);
+    int32_t* target = (int32_t*)malloc(sizeof(int32_t) * (size_t)M);
+    for (int m = 0; m < M; m++) target[m] = m;
+    int64_t nf = 0;
+    for (int64_t k = 0; k < nc; k++) {
+        if (used[cand[k].a] || used[cand[k].b]) continue;
+        used[cand[k].a] = used[cand[k].b] = 1;
+        target[cand[k].b] = cand[k].a;
+        nf++;
+    }
+    if (nf)
+        for (int64_t i = 0; i < npix; i++) L[i] = target[L[i]];
+    free(a); free(b); free(B); free(n); free(S); free(Q); free(cand); free(used); free(target);
+    return nf;
+}
+
 void orc_state_init(const orc_params* p, orc_state* st)
 {
     st->mode = p->gradient;          /* 0 = Sobolev, 1 = L2, 2 = Sobolev with E = |Gamma| */
@@ -964,6 +1081,11 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
         }
     for (int64_t t = 0; t < na; t++) L[acc_idx[t]] = acc_c[t];
     if (n_split > 0) st->nlabels = orc_relabel(p, L, p->nlabels);
+    if ((p->topology & 4) && p->model == 0) {
+        orc_params q = *p;
+        q.nlabels = st->nlabels > p->nlabels ? st->nlabels : p->nlabels;
+        orc_fuse(&q, I, L);
+    }
     (void)npix;
     status->n_particles = N;
     status->n_candidates = ncand;

@@ -79,7 +79,8 @@ typedef struct {
                             split (a removal that locally disconnects it is admissible; after the
                             moves of an iteration with such a move, every foreground label's
                             components but the one holding its smallest pixel index get new
-                            labels) */
+                            labels); 4 = touching regions may fuse (piecewise-constant model:
+                            after the moves, pairs whose fusion lowers the energy, see orc_fuse) */
     const double* psf;   /* deconvolving model: symmetric 1D PSF profile k(-r..r), the same on
                             every axis (K(x) = prod_axes k(x_a)) */
     int32_t regulariser; /* 0 = length prior lambda * (change of unlike neighbour pairs);
@@ -167,6 +168,13 @@ int     orc_admissible(const orc_params* p, const int32_t* L, uint32_t x, int32_
  * smallest pixel index new labels nlabels, nlabels + 1, ... in ascending order of the components'
  * smallest pixel indices; returns the new label count */
 int32_t orc_relabel(const orc_params* p, int32_t* L, int32_t nlabels);
+
+/* Fusion: the touching foreground label pairs a < b with their number B of connectivity-adjacent
+ * pixel pairs, ascending (a, b) (returns the count; writes at most cap); the energy change of
+ * fusing a pair from statistics n, S; and one fusion pass over L (returns the fusions made). */
+int64_t orc_fuse_pairs(const orc_params* p, const int32_t* L, int32_t* a, int32_t* b, int64_t* B, int64_t cap);
+double  orc_fuse_energy(const orc_params* p, const int64_t* n, const double* S, int32_t a, int32_t b, int64_t B);
+int64_t orc_fuse(const orc_params* p, const void* I, int32_t* L);
 
 int64_t orc_select(const orc_params* p, const int32_t* L, int64_t N,
                    const uint32_t* idx, const int32_t* l, const int32_t* c, const double* g,
