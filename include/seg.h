@@ -82,8 +82,17 @@ enum { SEG_SOBOLEV = 0, SEG_L2 = 1, SEG_SOBOLEV_GLOBAL = 2 };
  *                   label's connectivity components but the one holding its smallest pixel
  *                   index get new labels, numbered upward from the label count in ascending order
  *                   of the components' smallest pixel indices (seg_info reports the count).
- * Fusion is not provided: the paper defers its rule to a reference that is not available. */
-enum { SEG_TOPO_STRICT = 0, SEG_TOPO_VANISH = 1, SEG_TOPO_SPLIT = 2 };
+ * SEG_TOPO_FUSE   - touching regions may fuse (SEG_PC with SEG_STATS_EXACT only): after the
+ *                   moves (and the relabelling of split pieces), two touching foreground
+ *                   labels a < b fuse when dE = w (d d) - lambda B_ab < 0, w = (n_a n_b) /
+ *                   (n_a + n_b), d = S_a / n_a - S_b / n_b (statistics after the moves, FP64 as
+ *                   written), B_ab their connectivity-adjacent pixel pairs: the exact change of
+ *                   the squared deviations about the joint mean minus the shared contour.
+ *                   Pairs are taken in ascending (dE, a, b), each label at most once per
+ *                   iteration; b's pixels take label a and b stays empty. More touching pairs
+ *                   than the pair table holds (max(4096, 16 M) rounded up to a power of two,
+ *                   at most 2^22) end the iteration with SEG_ENOMEM. */
+enum { SEG_TOPO_STRICT = 0, SEG_TOPO_VANISH = 1, SEG_TOPO_SPLIT = 2, SEG_TOPO_FUSE = 4 };
 /* regulariser of the energy difference (seg_params.regulariser):
  * SEG_REG_LENGTH    - lambda * dP, dP the change of the number of connectivity-adjacent pixel
  *                     pairs with different labels (the length prior of Eq. 10);
@@ -130,8 +139,8 @@ typedef struct {
                               is floor(tile / cell_edge) cells (at least one) per axis; z must be
                               0 or 1 in 2D. Default 8 x 32 x 32 / cell (3D), 32 x 64 / cell (2D) */
     int32_t topology;      /* SEG_TOPO_STRICT (0: every move keeps each foreground region one
-                              connected component with its holes) or an OR of SEG_TOPO_VANISH and
-                              SEG_TOPO_SPLIT */
+                              connected component with its holes) or an OR of SEG_TOPO_VANISH,
+                              SEG_TOPO_SPLIT and SEG_TOPO_FUSE */
     int32_t max_labels;    /* with SEG_TOPO_SPLIT: label capacity (labels 0..max_labels-1), >= the
                               initial count; 0 = max(2 M, M + 256) for M initial labels. A split
                               beyond it ends the iteration with SEG_ENOMEM. Ignored otherwise */

@@ -1618,4 +1618,217 @@ cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cud
     return launch_stage(k_finish, sms, 256, 0, s, jobs, njobs, bc);
 }
 
+
+// ---------------------------------------------------------------------------
+// Fusion (SEG_TOPO_FUSE, piecewise-constant model, exact statistics): after the moves (and the
+// relabelling of split pieces), touching foreground regions a < b fuse when
+//     dE = w (d d) - lambda B_ab,  w = (n_a n_b) / (n_a + n_b),  d = S_a / n_a - S_b / n_b
+// is negative (the exact change of the sum of squared deviations about the joint mean, minus
+// the B_ab adjacent pixel pairs between them that leave the contour), greedily in ascending
+// (dE, a, b), each label at most once per iteration; b's pixels then take label a.
+//
+//  1. k_fuse_pairs: every pixel adds its forward-neighbour pairs of different foreground
+//     labels to a hash table keyed by (a << 32 | b) (warp-aggregated counts, bounded probing;
+//     a full table raises SEG_ENOMEM); new keys are listed.
+//  2. k_fuse_match (one block): dE per listed pair from the exact sums after the moves, the
+//     table cleared; then rounds of the greedy matching: a pair is accepted when it holds the
+//     smallest (dE, a, b) among the undecided pairs of both its labels (the lexicographically
+//     first maximal matching, as the ranked candidate selection); accepted pairs merge their
+//     exact statistics into a.
+//  3. k_fuse_relabel: b -> a over the label image.
+constexpr unsigned long long kFuseEmpty = ~0ull;
+constexpr int kFuseBlock = 1024;
+enum { kFuseOpen = 0, kFuseTaken = 1, kFuseOut = 2 };
+
+__device__ __forceinline__ unsigned long long fuse_order(double v)
+{
+    // IEEE order as unsigned order
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ bool fuse_idle(const Job& J)
+{
+    return !J.topo_fuse || ld_volatile(&J.ctr->skip) != 0 || ld_volatile(&J.ctr->need) != 0 ||
+           ld_volatile(&J.ctr->error) != 0;
+}
+
+__device__ void fuse_insert(const Job& J, unsigned long long key, bool valid)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? key : kFuseEmpty);
+    const int lane = threadIdx.x & 31;
+    if (!valid || lane != __ffs(peers) - 1) return;
+    const unsigned cap = J.fz_cap;
+    unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & (cap - 1);
+    for (unsigned probe = 0; probe < cap; probe++, h = (h + 1) & (cap - 1)) {
+        const unsigned long long prev = atomicCAS(J.fz_key + h, kFuseEmpty, key);
+        if (prev == kFuseEmpty || prev == key) {
+            atomicAdd(J.fz_cnt + h, (unsigned)__popc(peers));
+            if (prev == kFuseEmpty) J.fz_list[atomicAdd(&J.ctr->n_fpairs, 1u)] = h;
+            return;
+        }
+    }
+    atomicExch(&J.ctr->error, SEG_ENOMEM);
+}
+
+__global__ void __launch_bounds__(256) k_fuse_pairs(const Job* jobs, int j)
+{
+    pdl_enter();
+    const Job& J = jobs[j];
+    if (fuse_idle(J)) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n = J.npix;
+    const long long rounds = (n + stride - 1) / stride;
+    for (long long r = 0; r < rounds; r++) {
+        const long long i = r * stride + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        const bool in = i < n;
+        int x = 0, y = 0, z = 0, m = 0;
+        if (in) {
+            pix_coords(J, (unsigned)i, x, y, z);
+            m = J.L[i];
+        }
+        for (int axis = 0; axis < 3; axis++) {
+            bool ok = in && m != 0;
+            long long q = 0;
+            if (axis == 0) { ok = ok && x + 1 < J.W; q = i + 1; }
+            else if (axis == 1) { ok = ok && y + 1 < J.H; q = i + J.W; }
+            else { ok = ok && J.ndim == 3 && z + 1 < J.D; q = i + (long long)J.W * J.H; }
+            const int m2 = ok ? J.L[q] : 0;
+            ok = ok && m2 != 0 && m2 != m;
+            const unsigned a = (unsigned)min(m, m2), b = (unsigned)max(m, m2);
+            fuse_insert(J, ((unsigned long long)a << 32) | b, ok);
+        }
+    }
+}
+
+// the region sum of label m as the finish rounds it (exact statistics)
+__device__ __forceinline__ double fuse_sum64(const Job& J, int m)
+{
+    if (J.dtype == SEG_U16) return __ll2double_rn(J.st_S[m]);
+    return round_bins(J.st_S + (long long)m * J.nS, J.nS, J.slot_lo - 150);
+}
+
+__global__ void __launch_bounds__(kFuseBlock) k_fuse_match(const Job* jobs, int j)
+{
+    pdl_enter();
+    __shared__ int s_open, s_fused;
+    const Job& J = jobs[j];
+    if (fuse_idle(J)) return;
+    Counters* ctr = J.ctr;
+    // labels retired by the previous fusion pass map to themselves again
+    const unsigned prev = ld_volatile(&ctr->n_fused);
+    for (unsigned k = threadIdx.x; k < prev; k += kFuseBlock) J.fz_to[J.fz_done[k]] = -1;
+    const unsigned np = min(ld_volatile(&ctr->n_fpairs), J.fz_cap);
+    for (unsigned k = threadIdx.x; k < np; k += kFuseBlock) {
+        const unsigned h = J.fz_list[k];
+        const unsigned long long key = J.fz_key[h];
+        const int a = (int)(key >> 32), b = (int)(key & 0xffffffffu);
+        const double na = (double)J.st_n[a], nb = (double)J.st_n[b];
+        const double w = __ddiv_rn(__dmul_rn(na, nb), __dadd_rn(na, nb));
+        const double d = __dsub_rn(__ddiv_rn(fuse_sum64(J, a), na), __ddiv_rn(fuse_sum64(J, b), nb));
+        const double dE = __dsub_rn(__dmul_rn(w, __dmul_rn(d, d)), __dmul_rn(J.fz_lam64, (double)J.fz_cnt[h]));
+        J.fz_ab[k] = key;
+        J.fz_u[k] = fuse_order(dE);
+        J.fz_B[k] = J.fz_cnt[h];
+        J.fz_state[k] = dE < 0.0 ? kFuseOpen : kFuseOut;
+        J.fz_key[h] = kFuseEmpty;                   // the table is empty again for the next iteration
+        J.fz_cnt[h] = 0;
+        J.fz_used[a] = 0;
+        J.fz_used[b] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s_fused = 0;
+        ctr->n_fpairs = 0;
+    }
+    __syncthreads();
+    // greedy matching in rounds; every round takes at least the smallest open pair
+    for (unsigned round = 0; round <= np; round++) {
+        if (threadIdx.x == 0) s_open = 0;
+        for (unsigned k = threadIdx.x; k < np; k += kFuseBlock)
+            if (J.fz_state[k] == kFuseOpen) {
+                const int a = (int)(J.fz_ab[k] >> 32), b = (int)(J.fz_ab[k] & 0xffffffffu);
+                J.fz_best_u[a] = J.fz_best_u[b] = kFuseEmpty;
+                J.fz_best_ab[a] = J.fz_best_ab[b] = kFuseEmpty;
+            }
+        __syncthreads();
+        for (unsigned k = threadIdx.x; k < np; k += kFuseBlock)
+            if (J.fz_state[k] == kFuseOpen) {
+                const int a = (int)(J.fz_ab[k] >> 32), b = (int)(J.fz_ab[k] & 0xffffffffu);
+                atomicMin(J.fz_best_u + a, J.fz_u[k]);
+                atomicMin(J.fz_best_u + b, J.fz_u[k]);
+            }
+        __syncthreads();
+        for (unsigned k = threadIdx.x; k < np; k += kFuseBlock)
+            if (J.fz_state[k] == kFuseOpen) {
+                const int a = (int)(J.fz_ab[k] >> 32), b = (int)(J.fz_ab[k] & 0xffffffffu);
+                if (J.fz_best_u[a] == J.fz_u[k]) atomicMin(J.fz_best_ab + a, J.fz_ab[k]);
+                if (J.fz_best_u[b] == J.fz_u[k]) atomicMin(J.fz_best_ab + b, J.fz_ab[k]);
+            }
+        __syncthreads();
+        for (unsigned k = threadIdx.x; k < np; k += kFuseBlock)
+            if (J.fz_state[k] == kFuseOpen) {
+                const unsigned long long ab = J.fz_ab[k];
+                const int a = (int)(ab >> 32), b = (int)(ab & 0xffffffffu);
+                if (J.fz_best_u[a] == J.fz_u[k] && J.fz_best_ab[a] == ab && J.fz_best_u[b] == J.fz_u[k] &&
+                    J.fz_best_ab[b] == ab) {
+                    J.fz_state[k] = kFuseTaken;
+                    J.fz_used[a] = 1;
+                    J.fz_used[b] = 1;
+                }
+            }
+        __syncthreads();
+        for (unsigned k = threadIdx.x; k < np; k += kFuseBlock)
+            if (J.fz_state[k] == kFuseOpen) {
+                const int a = (int)(J.fz_ab[k] >> 32), b = (int)(J.fz_ab[k] & 0xffffffffu);
+                if (J.fz_used[a] || J.fz_used[b]) J.fz_state[k] = kFuseOut;
+                else s_open = 1;
+            }
+        __syncthreads();
+        if (!s_open) break;
+        __syncthreads();
+    }
+    // merge the statistics of each accepted pair into a; b is left empty
+    const long long nS = J.dtype == SEG_F32 ? J.nS : 1, nQ = J.dtype == SEG_F32 ? J.nQ : 1;
+    for (unsigned k = threadIdx.x; k < np; k += kFuseBlock)
+        if (J.fz_state[k] == kFuseTaken) {
+            const int a = (int)(J.fz_ab[k] >> 32), b = (int)(J.fz_ab[k] & 0xffffffffu);
+            J.st_n[a] += J.st_n[b];
+            J.st_n[b] = 0;
+            for (long long s = 0; s < nS; s++) {
+                J.st_S[a * nS + s] += J.st_S[b * nS + s];
+                J.st_S[b * nS + s] = 0;
+            }
+            for (long long s = 0; s < nQ; s++) {
+                J.st_Q[a * nQ + s] += J.st_Q[b * nQ + s];
+                J.st_Q[b * nQ + s] = 0;
+            }
+            J.fz_to[b] = a;
+            J.fz_done[atomicAdd(&s_fused, 1)] = b;
+            atomicAdd((unsigned long long*)&ctr->perim, (unsigned long long)(-(long long)J.fz_B[k]));
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) ctr->n_fused = (unsigned)s_fused;
+}
+
+__global__ void __launch_bounds__(256) k_fuse_relabel(const Job* jobs, int j)
+{
+    pdl_enter();
+    const Job& J = jobs[j];
+    if (fuse_idle(J) || ld_volatile(&J.ctr->n_fused) == 0) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < J.npix; i += stride) {
+        const int m = J.L[i];
+        const int t = J.fz_to[m];
+        if (t >= 0) J.L[i] = t;
+    }
+}
+
+cudaError_t launch_fuse(const Job* jobs, int j, int sms, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = launch_stage(k_fuse_pairs, (unsigned)sms * 8, 256, 0, s, jobs, j)) != cudaSuccess) return e;
+    if ((e = launch_stage(k_fuse_match, 1u, kFuseBlock, 0, s, jobs, j)) != cudaSuccess) return e;
+    return launch_stage(k_fuse_relabel, (unsigned)sms * 8, 256, 0, s, jobs, j);
+}
+
 }  // namespace segk

@@ -201,6 +201,7 @@ struct Stepper {
     bool any_deconv = false;       // a member uses the deconvolving model (adds its PSF passes)
     bool any_split = false;        // a member may split regions (adds the relabelling passes)
     bool any_curv = false;         // a member uses the curvature regulariser (adds its ball counts)
+    bool any_fuse = false;         // a member may fuse regions (adds the fusion passes)
     bool profile = false;
     cudaEvent_t ev[11]{};
     cudaStream_t work = nullptr;   // library stream: graphs are captured and launched here
@@ -248,7 +249,9 @@ int validate(const seg_params* p)
     for (int i = 0; i < 3; i++)
         if (p->tile[i] < 0 || p->tile[i] > 1024) return SEG_EINVAL;
     if (p->ndim == 2 && p->tile[0] > 1) return SEG_EINVAL;
-    if (p->topology < 0 || p->topology > (SEG_TOPO_VANISH | SEG_TOPO_SPLIT)) return SEG_EINVAL;
+    if (p->topology < 0 || p->topology > (SEG_TOPO_VANISH | SEG_TOPO_SPLIT | SEG_TOPO_FUSE)) return SEG_EINVAL;
+    // fusion: the piecewise-constant model with exact statistics
+    if ((p->topology & SEG_TOPO_FUSE) && (p->model != SEG_PC || p->stats_mode != SEG_STATS_EXACT)) return SEG_EINVAL;
     if (p->max_labels < 0 || p->max_labels > (1 << 24)) return SEG_EINVAL;
     if (p->regulariser != SEG_REG_LENGTH && p->regulariser != SEG_REG_CURVATURE) return SEG_EINVAL;
     if (p->regulariser == SEG_REG_CURVATURE && (!(p->curv_radius >= 1.0) || p->curv_radius > 16.0)) return SEG_EINVAL;
@@ -347,6 +350,8 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     h.osc_window = p->osc_window;
     h.topo_vanish = (p->topology & SEG_TOPO_VANISH) ? 1 : 0;
     h.topo_split = (p->topology & SEG_TOPO_SPLIT) ? 1 : 0;
+    h.topo_fuse = (p->topology & SEG_TOPO_FUSE) ? 1 : 0;
+    h.fz_lam64 = p->lambda;
     h.nbr_stride = h.ndim == 3 ? 26 : 8;
     h.slot_lo = slot_lo;
     h.nS = nS;
@@ -434,6 +439,25 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     A.add(&h.gK32, (size_t)h.gd2max + 1);
     A.add(&h.gK64, (size_t)h.gd2max + 1);
     h.psf_r = -1;
+    if (h.topo_fuse) {
+        // touching pairs: a planar label graph has fewer than 3 M edges; 16 M slots (at least
+        // 4096, at most 2^22) keep the table at most a quarter full in 2D
+        unsigned cap = 4096;
+        while (cap < (1u << 22) && (long long)cap < 16LL * M) cap <<= 1;
+        h.fz_cap = cap;
+        A.add(&h.fz_key, cap);
+        A.add(&h.fz_cnt, cap);
+        A.add(&h.fz_list, cap);
+        A.add(&h.fz_ab, cap);
+        A.add(&h.fz_u, cap);
+        A.add(&h.fz_B, cap);
+        A.add(&h.fz_state, cap);
+        A.add(&h.fz_best_u, M);
+        A.add(&h.fz_best_ab, M);
+        A.add(&h.fz_used, M);
+        A.add(&h.fz_to, M);
+        A.add(&h.fz_done, M);
+    }
     if (h.topo_split) {
         A.add(&h.cc_parent, npix);
         A.add(&h.cc_newl, npix);
@@ -634,6 +658,7 @@ int stepper_build(Stepper& s)
     s.any_deconv = false;
     s.any_split = false;
     s.any_curv = false;
+    s.any_fuse = false;
     for (int i = 0; i < n; i++) {
         jobs[i] = s.members[i]->h;
         if (jobs[i].model == SEG_PC_DECONV && jobs[i].psf_r < 0) return SEG_ESTATE;   // no PSF yet
@@ -641,6 +666,7 @@ int stepper_build(Stepper& s)
         s.any_deconv = s.any_deconv || jobs[i].model == SEG_PC_DECONV;
         s.any_split = s.any_split || jobs[i].topo_split;
         s.any_curv = s.any_curv || jobs[i].curv;
+        s.any_fuse = s.any_fuse || jobs[i].topo_fuse;
     }
     int id_off[2] = {0, 0}, pf_off[2] = {0, 0};
     for (int gidx = 0; gidx < 2; gidx++) {
@@ -752,6 +778,9 @@ cudaError_t stepper_enqueue_stages(Stepper& s)
             if (s.members[i]->h.topo_split &&
                 (e = launch_relabel(s.d_jobs, i, s.members[i]->h, s.sms, s.work)) != cudaSuccess)
                 return e;
+    if (s.any_fuse)                     // touching regions whose fusion lowers the energy merge
+        for (int i = 0; i < n; i++)
+            if (s.members[i]->h.topo_fuse && (e = launch_fuse(s.d_jobs, i, s.sms, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 9)) != cudaSuccess) return e;
     if ((e = launch_finish(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
     return stage_mark(s, 10);
@@ -1128,6 +1157,12 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     if (!P.ps_off.empty())
         CKF(cudaMemcpyAsync((void*)c->h.ps_off, P.ps_off.data(), P.ps_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
     CKF(cudaMemcpyAsync((void*)c->h.nb_off, P.nb_off.data(), P.nb_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+    if (c->h.topo_fuse) {
+        CKF(cudaMemsetAsync(c->h.fz_key, 0xff, (size_t)c->h.fz_cap * 8, stream));
+        CKF(cudaMemsetAsync(c->h.fz_cnt, 0, (size_t)c->h.fz_cap * 4, stream));
+        CKF(cudaMemsetAsync(c->h.fz_to, 0xff, (size_t)M * 4, stream));
+        CKF(cudaMemsetAsync(c->h.fz_used, 0, (size_t)M * 4, stream));
+    }
     if (!P.cv_off.empty())
         CKF(cudaMemcpyAsync((void*)c->h.cv_off, P.cv_off.data(), P.cv_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
     CKF(cudaMemcpyAsync(c->d_ctr, &hc, sizeof hc, cudaMemcpyHostToDevice, stream));

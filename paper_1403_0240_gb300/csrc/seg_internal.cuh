@@ -87,6 +87,8 @@ struct Counters {
     int n_labels;           // labels in use (grows when regions split)
     unsigned n_split;       // accepted moves of the iteration admitted by the split rule
     unsigned n_newcomp;     // pieces given new labels by the iteration's relabelling
+    unsigned n_fpairs;      // fusion: touching label pairs listed in the hash table
+    unsigned n_fused;       // fusion: pairs fused by the last fusion pass
     long long g_lim;        // E = |Gamma| mode: interaction partners have d^2 < g_lim
     seg_status last;        // status of the last executed iteration
 };
@@ -151,6 +153,21 @@ struct alignas(64) Job {
     int* cc_newl;             // ... new label of each piece, at the piece's root pixel [npix]
     int* cc_first;            // ... smallest pixel index of each label [M]
     int* cc_list;             // ... roots of the pieces that get new labels [M]
+    int topo_fuse;            // touching regions may fuse (SEG_TOPO_FUSE)
+    double fz_lam64;          // ... length weight of the shared boundary
+    unsigned fz_cap;          // ... hash table slots (power of two)
+    unsigned long long* fz_key;   // ... (a << 32 | b) per slot, ~0 when empty [fz_cap]
+    unsigned* fz_cnt;         // ... adjacent pixel pairs of the slot's labels [fz_cap]
+    unsigned* fz_list;        // ... occupied slots, then per listed pair: [fz_cap]
+    unsigned long long* fz_ab;    // ... key [fz_cap]
+    unsigned long long* fz_u;     // ... dE in unsigned order [fz_cap]
+    unsigned* fz_B;           // ... shared pairs [fz_cap]
+    int* fz_state;            // ... open / taken / out [fz_cap]
+    unsigned long long* fz_best_u;   // ... per label: smallest open dE, then key [M]
+    unsigned long long* fz_best_ab;
+    int* fz_used;             // ... per label: fused in this pass [M]
+    int* fz_to;               // ... per label: the label it fused into, or -1 [M]
+    int* fz_done;             // ... labels fused away by the last pass [M]
     int inject;               // test-only fault injection (SEG_INJECT_*)
     int nbr_stride;           // neighbour-list slots per candidate: 8 (2D) | 26 (3D)
     int slot_lo, nS, nQ;      // exact float32 sums: exponent slots [slot_lo, slot_lo + nS)
@@ -411,6 +428,7 @@ cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream
 cudaError_t launch_stats_zero_after_split(const Job* jobs, int j, const Job& h, cudaStream_t s);
 cudaError_t launch_relabel(const Job* jobs, int j, const Job& h, int sms, cudaStream_t s);
 cudaError_t launch_curvature(const Job* jobs, int j, int sms, cudaStream_t s);
+cudaError_t launch_fuse(const Job* jobs, int j, int sms, cudaStream_t s);
 cudaError_t launch_deconv(const Job* jobs, int j, const Job& h, int sms, cudaStream_t s);
 cudaError_t launch_psf_norms(const Job* job, const Job& h, cudaStream_t s);
 cudaError_t launch_scan_inputs(const void* I, int dtype, const int* L, int ndim, int D, int H, int W, InputScan* out,

@@ -21,8 +21,9 @@ SEG_PSF_MAX_RADIUS = 512
 MODELS = {"pc": SEG_PC, "ps": SEG_PS, "psp": SEG_PS_POISSON, "pcd": SEG_PC_DECONV}
 SEG_SOBOLEV, SEG_L2, SEG_SOBOLEV_GLOBAL = 0, 1, 2
 SEG_STATS_EXACT, SEG_STATS_F64, SEG_STATS_KAHAN32 = 0, 1, 2
-SEG_TOPO_STRICT, SEG_TOPO_VANISH, SEG_TOPO_SPLIT = 0, 1, 2
-TOPOLOGY = {"strict": 0, "vanish": 1, "split": 2, "vanish+split": 3}
+SEG_TOPO_STRICT, SEG_TOPO_VANISH, SEG_TOPO_SPLIT, SEG_TOPO_FUSE = 0, 1, 2, 4
+TOPOLOGY = {"strict": 0, "vanish": 1, "split": 2, "vanish+split": 3, "fuse": 4, "vanish+fuse": 5, "split+fuse": 6,
+            "vanish+split+fuse": 7}
 SEG_REG_LENGTH, SEG_REG_CURVATURE = 0, 1
 STATS_MODES = {"exact": SEG_STATS_EXACT, "f64": SEG_STATS_F64, "kahan32": SEG_STATS_KAHAN32}
 SEG_INJECT_NONE, SEG_INJECT_WITHHELD_COPY = 0, 1

@@ -72,7 +72,8 @@ def test_strerror_and_validation_without_gpu(libseg):
     p.regulariser, p.curv_radius = seg.SEG_REG_LENGTH, 0.0
     for topology, code in [(seg.SEG_TOPO_STRICT, seg.SEG_OK), (seg.SEG_TOPO_VANISH, seg.SEG_OK),
                            (seg.SEG_TOPO_SPLIT, seg.SEG_OK), (seg.SEG_TOPO_VANISH | seg.SEG_TOPO_SPLIT, seg.SEG_OK),
-                           (4, seg.SEG_EINVAL), (-1, seg.SEG_EINVAL)]:
+                           (seg.SEG_TOPO_FUSE, seg.SEG_OK), (7, seg.SEG_OK), (8, seg.SEG_EINVAL),
+                           (-1, seg.SEG_EINVAL)]:
         p.topology = topology
         assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == code, topology
     # with splits the label tables (and the relabelling arrays) grow to the capacity
@@ -84,6 +85,16 @@ def test_strerror_and_validation_without_gpu(libseg):
     p.max_labels = 1                               # below the initial count
     assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_EINVAL
     p.max_labels = 0
+    p.topology = seg.SEG_TOPO_STRICT
+    # fusion: piecewise constant with exact statistics only
+    p.topology = seg.SEG_TOPO_FUSE
+    for model, stats, code in [(seg.MODELS["pc"], seg.STATS_MODES["exact"], seg.SEG_OK),
+                               (seg.MODELS["ps"], seg.STATS_MODES["exact"], seg.SEG_EINVAL),
+                               (seg.MODELS["pc"], seg.STATS_MODES["f64"], seg.SEG_EINVAL)]:
+        model0, stats0, radius0 = p.model, p.stats_mode, p.ps_radius
+        p.model, p.stats_mode, p.ps_radius = model, stats, 4.0
+        assert libseg.seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == code, (model, stats)
+        p.model, p.stats_mode, p.ps_radius = model0, stats0, radius0
     p.topology = seg.SEG_TOPO_STRICT
 
 
