@@ -1180,42 +1180,47 @@ constexpr unsigned kSmallCandidates = 32768;   // at most this many: one block d
 constexpr size_t kRoundsDyn = 160 * 1024;      // dynamic shared memory of the rounds kernel
 
 // A: neighbour lists of smaller-key candidates; states reset
-__device__ void commit_list_one(const Job& J, unsigned s)
+// Neighbour positions by compile-time index (dz, dy, dx ascending, the centre skipped), so
+// that the per-neighbour arrays stay in registers.
+template <int NDIM>
+__device__ __forceinline__ void commit_list_nd(const Job& J, unsigned s)
 {
+    constexpr int K = NDIM == 3 ? 27 : 9;
     const unsigned tag = ld_volatile(&J.ctr->iter_tag);
-    const int rz = J.ndim == 3 ? 1 : 0;
     const unsigned gi = J.c_pix[s];
     const double ks = J.c_key[s];
     int x, y, z;
     coords(J, gi, x, y, z);
     // three dependent levels (pixel map, candidate slot, key), each level's loads for all
     // neighbours issued together
-    int slot[26];
-    int nn = 0;
-    for (int dz = -rz; dz <= rz; dz++)
-        for (int dy = -1; dy <= 1; dy++)
-            for (int dx = -1; dx <= 1; dx++) {
-                if (!dz && !dy && !dx) continue;
-                int xx = x + dx, yy = y + dy, zz = z + dz;
-                bool in = xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D;
-                slot[nn++] = in ? (int)(((long long)zz * J.H + yy) * J.W + xx) : -1;
-            }
-    unsigned long long e[26];
+    unsigned long long e[K];
+    unsigned in = 0;
 #pragma unroll
-    for (int i = 0; i < 26; i++)
-        e[i] = (i < nn && slot[i] >= 0) ? J.pmap[(unsigned)slot[i]] : 0ull;
+    for (int t = 0; t < K; t++) {
+        const int dz = NDIM == 3 ? t / 9 - 1 : 0, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        const int xx = x + dx, yy = y + dy, zz = z + dz;
+        const bool ok = t != K / 2 && xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D;
+        e[t] = ok ? J.pmap[(unsigned)(((long long)zz * J.H + yy) * J.W + xx)] : 0ull;
+        in |= ok ? 1u << t : 0u;
+    }
+    int slot[K];
 #pragma unroll
-    for (int i = 0; i < 26; i++)
-        slot[i] = (i < nn && slot[i] >= 0 && (unsigned)(e[i] >> 32) == tag) ? J.pix_cand[(unsigned)e[i]] : -1;
+    for (int t = 0; t < K; t++)
+        slot[t] = ((in >> t) & 1u) && (unsigned)(e[t] >> 32) == tag ? J.pix_cand[(unsigned)e[t]] : -1;
     int n = 0;
 #pragma unroll
-    for (int i = 0; i < 26; i++) {
-        const int o = slot[i];
-        if (i < nn && o >= 0 && key_less(J.c_key[o], J.c_pix[o], ks, gi))
-            J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
+    for (int t = 0; t < K; t++) {
+        const int o = slot[t];
+        if (o >= 0 && key_less(J.c_key[o], J.c_pix[o], ks, gi)) J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
     }
     J.c_nnbr[s] = n;
     J.c_state[s] = kUndecided;
+}
+
+__device__ __forceinline__ void commit_list_one(const Job& J, unsigned s)
+{
+    if (J.ndim == 3) commit_list_nd<3>(J, s);
+    else commit_list_nd<2>(J, s);
 }
 
 // B: one decision for candidate s of job J on state array st (offset b); returns the new
