@@ -40,6 +40,16 @@
  *                         foreground topological number is >= 2 is admissible; pinned by a
  *                         dumbbell whose neck is removed, and by global component counts.
  *   relabelling (topology 2) - pinned by scipy.ndimage.label components and the numbering rule.
+ *   orc_fuse_pairs      - touching foreground pairs and their shared pixel pairs B_ab; pinned
+ *                         by a perimeter recount (P before minus P after renaming b to a).
+ *   orc_fuse_energy     - n_a n_b/(n_a + n_b) (mu_a - mu_b)^2 - lambda B_ab; pinned by brute-force
+ *                         total energies (squared deviations plus lambda P) before and after.
+ *   orc_fuse            - greedy matching of the negative pairs; pinned by a greedy pass over
+ *                         brute-force energies (a matching, maximal, the energy falls).
+ *   orc_ball_balance,   - curvature regulariser w (A_l - A_c); pinned by the exact count on a
+ *   orc_curvature_weight  straight edge (the ball's central row or plane), the curvature of
+ *                         digital disks (1/R) and spheres (2/R) from the inner and outer
+ *                         particles, and a brute-force count with image borders.
  *   orc_select          - ranked greedy selection; pinned by an independent
  *                         local-minimum-rounds evaluation and permutation tests.
  *   orc_perimeter       - |Gamma| as the length prior counts it; pinned by square and
