@@ -90,7 +90,8 @@ class SegBackend:
 
 
 def _param_kwargs(req: Request, with_psf: bool = True) -> dict:
-    keys = ("model", "connectivity", "lam", "cutoff", "ps_radius", "gradient", "osc_window", "cell_edge", "tile")
+    keys = ("model", "connectivity", "lam", "cutoff", "ps_radius", "gradient", "osc_window", "cell_edge", "tile",
+            "stats", "topology", "max_labels", "curv_radius")
     out = {k: req.params[k] for k in keys if k in req.params}
     if with_psf and req.params.get("psf") is not None:
         out["psf"] = req.params["psf"]          # deconvolving model: set after seg_init

@@ -130,3 +130,24 @@ def test_real_time_replay_and_latency_summary():
     assert len(res) == 20
     s = latency_summary(res)
     assert 0.0 < s["p50_s"] <= s["p99_s"]
+
+
+def test_request_options_reach_the_library_parameters():
+    # every option a request may carry ends up in seg_params (topology events, curvature
+    # regulariser, statistics mode), and the device-memory estimate sees the split capacity
+    import ctypes as C
+    from paper_1403_0240_gb300 import seg
+    from paper_1403_0240_gb300.serve import Request, _param_kwargs
+    img = np.zeros((64, 48), np.float32)
+    req = Request(0, 0.0, img, np.zeros(img.shape, np.int32), 10,
+                  params={"model": "pc", "lam": 0.5, "cutoff": 3.0, "stats": "exact", "topology": "vanish+split+fuse",
+                          "max_labels": 64, "curv_radius": 4.0, "psf": None})
+    p = seg.make_params(img, **_param_kwargs(req, with_psf=False))
+    assert p.topology == 7 and p.max_labels == 64
+    assert p.regulariser == seg.SEG_REG_CURVATURE and p.curv_radius == 4.0
+    assert p.stats_mode == seg.STATS_MODES["exact"]
+    out = C.c_size_t(0)
+    assert seg.lib().seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_OK
+    big = out.value
+    p.topology = 0
+    assert seg.lib().seg_estimate_bytes(C.byref(p), 2, C.byref(out)) == seg.SEG_OK and out.value < big
