@@ -83,3 +83,14 @@ def test_curvature_job_in_a_batch_equals_solo():
     batch.close()
     a.close()
     b.close()
+
+
+def test_curvature_ball_beyond_the_staged_offsets_3d():
+    # rho = 8 in 3D has 2109 ball offsets, more than the 2048 the kernel keeps in shared memory:
+    # the rest come from global memory
+    w = synth.ellipsoids(18, 20, 22, seed=44)
+    w.labels0 = synth.cube_grid_labels(18, 20, 22, 9, 5)
+    ctx, run = _pair(w, 8.0, 30000.0)
+    for it in range(4):
+        compare_step(ctx, run, f"curv rho8 3d it{it}")
+    ctx.close()

@@ -57,3 +57,31 @@ def test_fusion_3d_u16_matches_oracle():
 def test_fusion_with_global_length_scale():
     I, L = _touching_blocks(40, 48, 8, seed=4, levels_of=lambda k: 0.5 * (k // 2 % 2))
     _run(I, L, 4, 0.05, 8, gradient="sobolev_global")
+
+
+def test_fusion_job_in_a_batch_equals_solo():
+    I, L = _touching_blocks(96, 112, 16, seed=1, levels_of=lambda k: 0.6 * (k // 3 % 3))
+    w2 = synth.disks(80, 64, seed=9)
+    mk1 = lambda: seg.Context(I, L, model="pc", lam=0.05, cutoff=3.0, topology="fuse")
+    mk2 = lambda: seg.Context.from_workload(w2)
+
+    def solo(make):
+        c = make()
+        for _ in range(15):
+            c.step(1)
+        out = c.labels().copy()
+        c.close()
+        return out
+
+    r1, r2 = solo(mk1), solo(mk2)
+    assert len(np.unique(r1)) < len(np.unique(L))
+    a, b = mk1(), mk2()
+    batch = seg.Batch()
+    batch.add(a)
+    batch.add(b)
+    for _ in range(15):
+        batch.step(1)
+    assert np.array_equal(a.labels(), r1) and np.array_equal(b.labels(), r2)
+    batch.close()
+    a.close()
+    b.close()
