@@ -75,6 +75,22 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64, nominal
 # kernels of one iteration's graph: extract, sobolev, flag, fixup, select, lists, rounds, moves,
 # finish (plus the deconvolving model's field passes); poll() adds one
 KERNELS_PER_ITERATION = 9
+# opt-in events and regulariser: kernels each adds to an iteration (the connected-component
+# relabelling of splits with its statistics rebuild; the fusion pairs, matching and relabelling;
+# the curvature term)
+TOPOLOGY_BITS = {"vanish": 1, "split": 2, "fuse": 4}
+EXTRA_KERNELS = {"split": 8, "fuse": 3, "curvature": 1}
+
+
+def topology_code(name: str) -> int:
+    """'vanish+split' -> 3; '' -> 0."""
+    return sum(TOPOLOGY_BITS[part] for part in name.split("+")) if name else 0
+
+
+def extra_kernels(args) -> int:
+    t = topology_code(args.topology)
+    return ((EXTRA_KERNELS["split"] if t & 2 else 0) + (EXTRA_KERNELS["fuse"] if t & 4 else 0) +
+            (EXTRA_KERNELS["curvature"] if args.curv_radius > 0 else 0))
 
 
 def psf_passes(w) -> int:
@@ -237,10 +253,11 @@ def aggregate(pg, units: float, seconds: float) -> tuple[float, float, float]:
     return total / t_max, total, t_max
 
 
-def oracle_sample(w, seconds: float = 12.0, max_iters: int = 400):
+def oracle_sample(w, seconds: float = 12.0, max_iters: int = 400, topology: int = 0, curv_radius: float = 0.0):
     """The CPU oracle as it stands, single-threaded, on the first iterations of the job."""
     import oracle
-    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius, psf=w.psf)
+    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius, psf=w.psf,
+                           topology=topology, curv_radius=curv_radius)
     run = oracle.Run(p, w.image, w.labels0)
     t0 = time.perf_counter()
     parts, its = 0, 0
@@ -635,7 +652,8 @@ def run_reference(args, world, rank):
     make, desc = workloads()[name]
     w = make(0)
     import oracle
-    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius, psf=w.psf)
+    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius, psf=w.psf,
+                           topology=topology_code(args.topology), curv_radius=args.curv_radius)
     run = oracle.Run(p, w.image, w.labels0)
     for _ in range(args.warmup):
         run.step()
@@ -686,6 +704,10 @@ def run_ours(args, world, rank, local, pg):
                                         connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
                                         ps_radius=w.ps_radius)
         settings = {"cell_edge": best["cell_edge"], "tile": best["tile"]}
+    if args.topology:
+        settings["topology"] = topology_code(args.topology)
+    if args.curv_radius > 0:
+        settings["curv_radius"] = args.curv_radius
 
     def new_ctx(profile):
         c = seg.Context(img_d, lab_d, model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
@@ -822,7 +844,8 @@ def run_ours(args, world, rank, local, pg):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, its, secs = oracle_sample(w, seconds=args.cpu_seconds)
+        v, its, secs = oracle_sample(w, seconds=args.cpu_seconds, topology=topology_code(args.topology),
+                                     curv_radius=args.curv_radius)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {its} iterations of the same job ({secs:.1f} s), single-threaded FP64 C oracle"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -840,7 +863,8 @@ def run_ours(args, world, rank, local, pg):
                                     "decisions, exact region sums"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             # per step: the kernels of the iteration graph plus the status gather of poll()
-            "gpu_launches": (KERNELS_PER_ITERATION + 1 + psf_passes(w)) * args.steps, "clocks": clocks,
+            "gpu_launches": (KERNELS_PER_ITERATION + 1 + psf_passes(w) + extra_kernels(args)) * args.steps,
+            "clocks": clocks,
             "stages_ms": {k: round(v, 5) for k, v in mean_stage.items()},
             "stage_pass": {"steps": n_stage, "ms_per_step": stage_dev_ms / n_stage,
                            "note": "per-stage CUDA events inside the iteration graph (serialises the "
@@ -865,6 +889,11 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batch512: default cell edge and tile shape")
     ap.add_argument("--tile", default="", help="tile shape in pixels, e.g. 30x64 (2D: y x x) or 8x8x32")
     ap.add_argument("--cell-edge", type=int, default=0)
+    ap.add_argument("--topology", default="", choices=["", "vanish", "split", "fuse", "vanish+split", "vanish+fuse",
+                                                         "split+fuse", "vanish+split+fuse"],
+                    help="opt-in topology events (fusion: piecewise-constant workloads)")
+    ap.add_argument("--curv-radius", type=float, default=0.0,
+                    help="curvature regulariser with this ball radius instead of the length prior")
     ap.add_argument("--autotune", action="store_true", help="time seg_autotune's candidates first and use the fastest")
     ap.add_argument("--osc-window", type=int, default=10, help="convergence: oscillation window of the Sobolev flow")
     ap.add_argument("--max-iters", type=int, default=3000, help="convergence: iteration cap per run")

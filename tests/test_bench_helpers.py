@@ -47,3 +47,17 @@ def test_deconv_energy_matches_scipy():
     J = ndimage.correlate(theta[L], np.multiply.outer(k, k), mode="constant", cval=0.0)
     ref = float(((I.astype(np.float64) - J) ** 2).sum()) + 0.3 * bench._contour_length(L)
     assert abs(bench._deconv_energy(I, L, k, 0.3) - ref) <= 1e-9 * ref
+
+
+def test_topology_options_and_their_kernel_counts():
+    import bench
+
+    class A:
+        topology = ""
+        curv_radius = 0.0
+
+    assert bench.topology_code("") == 0 and bench.topology_code("vanish+split+fuse") == 7
+    assert bench.topology_code("split") == 2 and bench.topology_code("vanish+fuse") == 5
+    assert bench.extra_kernels(A) == 0
+    A.topology, A.curv_radius = "vanish+split", 5.0
+    assert bench.extra_kernels(A) == bench.EXTRA_KERNELS["split"] + bench.EXTRA_KERNELS["curvature"]
