@@ -706,6 +706,11 @@ def run_ours(args, world, rank, local, pg):
         settings = {"cell_edge": best["cell_edge"], "tile": best["tile"]}
     if args.topology:
         settings["topology"] = topology_code(args.topology)
+        if topology_code(args.topology) & 2:
+            # split pieces take new labels: room for the job's iterations (the 1024^2 scene gains
+            # 12-20 labels per iteration at its lambda)
+            m0 = int(w.labels0.max()) + 1
+            settings["max_labels"] = args.max_labels or 4 * m0 + 4096
     if args.curv_radius > 0:
         settings["curv_radius"] = args.curv_radius
 
@@ -892,6 +897,8 @@ def main():
     ap.add_argument("--topology", default="", choices=["", "vanish", "split", "fuse", "vanish+split", "vanish+fuse",
                                                          "split+fuse", "vanish+split+fuse"],
                     help="opt-in topology events (fusion: piecewise-constant workloads)")
+    ap.add_argument("--max-labels", type=int, default=0,
+                    help="label capacity with splits (default 4 M + 4096 for M initial labels)")
     ap.add_argument("--curv-radius", type=float, default=0.0,
                     help="curvature regulariser with this ball radius instead of the length prior")
     ap.add_argument("--autotune", action="store_true", help="time seg_autotune's candidates first and use the fastest")
