@@ -126,10 +126,11 @@ def test_fusion_in_3d(orc):
     assert _energy(I, L1, 0.01, orc, p) < _energy(I, L, 0.01, orc, p)
 
 
-def test_iterations_with_fusion_keep_one_component_per_label(orc):
+@pytest.mark.parametrize("topology", [4, 7])
+def test_iterations_with_fusion_keep_one_component_per_label(orc, topology):
     from scipy import ndimage
     I, L = _blocks(H=64, W=80, seed=6, sigma=0.1, levels=[0.0] + [0.5 * (k // 2) for k in range(40)])
-    p = orc.make_params(I, L, "pc", lam=0.05, cutoff=3.0, topology=4)
+    p = orc.make_params(I, L, "pc", lam=0.05, cutoff=3.0, topology=topology)
     run = orc.Run(p, I, L)
     labels0 = len(np.unique(L))
     for _ in range(10):
