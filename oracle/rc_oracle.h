@@ -10,7 +10,7 @@
  * Parity status of each function (what pins it, in tests/test_oracle_*.py):
  *   orc_kernel_eq5      - Eq. 5; pinned by the closed form at eps = 1/24, the
  *                         Figure 2 axis ticks, the vanishing at r = +-E/2, unit mass.
- *   orc_extract         - particles on both sides of the contour (Fig. 1); pinned
+ *   orc_extract         - particles on either side of the contour (Fig. 1); pinned
  *                         by the 64x64 square count (252 inner + 256 outer) and a
  *                         numpy brute-force neighbour scan.
  *   orc_stats           - exact region sums rounded once; pinned by math.fsum,
