@@ -118,3 +118,23 @@ def test_model_and_stats_mode_validation_without_gpu(libseg):
                        (seg.SEG_STATS_KAHAN32, seg.SEG_OK), (3, seg.SEG_EINVAL), (-1, seg.SEG_EINVAL)]:
         p.stats_mode = mode
         assert libseg.seg_estimate_bytes(C.byref(p), 3, C.byref(out)) == code, mode
+
+
+def test_option_edge_values_without_gpu(libseg):
+    import math
+
+    import numpy as np
+    out = C.c_size_t(0)
+    p = seg.make_params(np.zeros((6, 10, 12), np.uint16), model="pc", cutoff=2.0)
+    # fusion on a 3D uint16 piecewise-constant job with exact sums is allowed
+    p.topology = seg.SEG_TOPO_FUSE
+    assert libseg.seg_estimate_bytes(C.byref(p), 3, C.byref(out)) == seg.SEG_OK
+    p.topology = seg.SEG_TOPO_SPLIT
+    for cap, code in [(3, seg.SEG_OK), (1 << 24, seg.SEG_OK), ((1 << 24) + 1, seg.SEG_EINVAL), (-1, seg.SEG_EINVAL)]:
+        p.max_labels = cap
+        assert libseg.seg_estimate_bytes(C.byref(p), 3, C.byref(out)) == code, cap
+    p.max_labels, p.topology = 0, 0
+    p.regulariser = seg.SEG_REG_CURVATURE
+    for r, code in [(1.0, seg.SEG_OK), (16.0, seg.SEG_OK), (math.nan, seg.SEG_EINVAL), (math.inf, seg.SEG_EINVAL)]:
+        p.curv_radius = r
+        assert libseg.seg_estimate_bytes(C.byref(p), 3, C.byref(out)) == code, r
