@@ -308,7 +308,10 @@ void seg_batch_destroy(seg_batch* b);
  * meaningless sums but stay in bounds.
  * The working accumulators live in one fixed device array of about 6.6 MB that every GPU
  * loading libseg holds until the process exits. The first call on a device looks up that
- * array's device address (once per device), so make it before any stream capture. All calls
+ * array's device address (once per device), so make it before any stream capture. Under CUDA's
+ * lazy module loading that first look-up may also load libseg's device code on that device,
+ * which reserves the array and can synchronise the device: a caller with a strict rule against
+ * allocation or synchronisation should make one warm-up call at start-up. All calls
  * share the array, so calls that overlap on the GPU (other streams, other host threads)
  * race and give wrong results. Work is ordered on cuda_stream (a cudaStream_t, NULL = the
  * legacy default stream); the call returns after it has finished. */

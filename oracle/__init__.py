@@ -59,7 +59,7 @@ class State(C.Structure):
 
 
 class Dump(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("idx", "l", "c", "dE", "g", "dE_scale", "g_scale")]
+    _fields_ = [(n, C.c_void_p) for n in ("idx", "l", "c", "dE", "g", "dE_terms", "g_terms")]
 
 
 class Status(C.Structure):
@@ -102,7 +102,7 @@ def lib():
             L.orc_fuse.restype = C.c_int64
             L.orc_fuse.argtypes = [P(Params), vp, vp]
             L.orc_sobolev.restype = None
-            L.orc_sobolev.argtypes = [P(Params), C.c_int64, vp, vp, vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_sobolev.argtypes = [P(Params), C.c_int64, vp, vp, vp, vp, C.c_int, vp, vp, vp, vp, vp, vp]
             L.orc_simple_2d.restype = C.c_int
             L.orc_simple_2d.argtypes = [vp]
             L.orc_simple_3d.restype = C.c_int
@@ -125,6 +125,8 @@ def lib():
             L.orc_perimeter.argtypes = [P(Params), vp]
             L.orc_state_init.restype = None
             L.orc_state_init.argtypes = [P(Params), P(State)]
+            L.orc_advance_mode.restype = None
+            L.orc_advance_mode.argtypes = [P(Params), P(State), C.c_int32, C.c_int64]
             L.orc_iterate.restype = C.c_int
             L.orc_iterate.argtypes = [P(Params), vp, vp, P(State), P(Status), C.c_int64, P(Dump)]
             _lib = L
@@ -238,7 +240,8 @@ def stats(p: Params, I: np.ndarray, L: np.ndarray):
     return n, S, Q
 
 
-def energy(p: Params, I: np.ndarray, L: np.ndarray, idx, l, c, n=None, S=None, with_scale: bool = False):
+def energy(p: Params, I: np.ndarray, L: np.ndarray, idx, l, c, n=None, S=None, with_terms: bool = False):
+    """dE of every particle; with_terms also returns each dE's sum of term magnitudes."""
     I = np.ascontiguousarray(I)
     L = np.ascontiguousarray(L, dtype=np.int32)
     if n is None:
@@ -251,7 +254,7 @@ def energy(p: Params, I: np.ndarray, L: np.ndarray, idx, l, c, n=None, S=None, w
     lib().orc_energy(C.byref(p), _ptr(I), _ptr(L), _ptr(np.ascontiguousarray(n, np.int64)),
                      _ptr(np.ascontiguousarray(S, np.float64)), idx.size, _ptr(idx), _ptr(l), _ptr(c), _ptr(dE),
                      _ptr(sc))
-    return (dE, sc) if with_scale else dE
+    return (dE, sc) if with_terms else dE
 
 
 def delta_perimeter(p: Params, L: np.ndarray, x: int, l: int, c: int) -> int:
@@ -298,7 +301,8 @@ def perimeter(p: Params, L: np.ndarray) -> int:
     return int(lib().orc_perimeter(C.byref(p), _ptr(L)))
 
 
-def sobolev(p: Params, idx, l, c, dE, all_pairs: bool = False):
+def sobolev(p: Params, idx, l, c, dE, all_pairs: bool = False, with_terms: bool = False):
+    """(g, A, B, |Q|, |Q'|) of Eq. 6; with_terms also returns each g's sum of term magnitudes."""
     idx = np.ascontiguousarray(idx, np.uint32)
     l = np.ascontiguousarray(l, np.int32)
     c = np.ascontiguousarray(c, np.int32)
@@ -306,9 +310,10 @@ def sobolev(p: Params, idx, l, c, dE, all_pairs: bool = False):
     N = idx.size
     g, A, B = (np.zeros(N, np.float64) for _ in range(3))
     nQ, nQp = np.zeros(N, np.int32), np.zeros(N, np.int32)
+    terms = np.zeros(N, np.float64)
     lib().orc_sobolev(C.byref(p), N, _ptr(idx), _ptr(l), _ptr(c), _ptr(dE), int(all_pairs),
-                      _ptr(g), _ptr(A), _ptr(B), _ptr(nQ), _ptr(nQp), None, None)
-    return g, A, B, nQ, nQp
+                      _ptr(g), _ptr(A), _ptr(B), _ptr(nQ), _ptr(nQp), _ptr(terms))
+    return (g, A, B, nQ, nQp, terms) if with_terms else (g, A, B, nQ, nQp)
 
 
 def simple_2d(nb9) -> bool:
@@ -348,6 +353,26 @@ def select(p: Params, L: np.ndarray, idx, l, c, g):
     return acc_idx[:na].copy(), acc_c[:na].copy(), int(ncand.value)
 
 
+def mode_sequence(osc_window: int, accepted, gradient: int = SOBOLEV):
+    """Drive the mode and convergence rule with a given accepted-move count per iteration;
+    returns (mode used, converged after) per iteration."""
+    p = Params()
+    p.gradient = gradient
+    p.osc_window = int(osc_window)
+    st = State()
+    lib().orc_state_init(C.byref(p), C.byref(st))
+    out = []
+    for na in accepted:
+        used = int(st.mode)
+        if st.converged:
+            st.t += 1
+            out.append((used, 1))
+            continue
+        lib().orc_advance_mode(C.byref(p), C.byref(st), used, int(na))
+        out.append((used, int(st.converged)))
+    return out
+
+
 class Run:
     """Iterates the oracle on its own copy of the label image."""
 
@@ -366,7 +391,7 @@ class Run:
         L_before = self.L.copy()
         N = lib().orc_extract(C.byref(self.p), _ptr(L_before), None, None, None, 0)
         out = {"idx": np.zeros(N, np.uint32), "l": np.zeros(N, np.int32), "c": np.zeros(N, np.int32)}
-        for k in ("dE", "g", "dE_scale", "g_scale"):
+        for k in ("dE", "g", "dE_terms", "g_terms"):
             out[k] = np.zeros(N, np.float64)
         d = Dump(**{k: out[k].ctypes.data_as(C.c_void_p) for k in out})
         lib().orc_iterate(C.byref(self.p), _ptr(self.I), _ptr(self.L), C.byref(self.st), C.byref(s), N,

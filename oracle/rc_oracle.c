@@ -490,7 +490,7 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
             double t = d * G[xi];
             double q = (d * d) * orc_psf_norm2(p, z, y, x);
             data = q - (t + t);
-            if (scale) scale[k] = 2.0 * fabs(t) + q;
+            if (scale) scale[k] = fabs(q) + fabs(t + t);
         } else if (p->model == 0) {
             /* Piecewise constant: exact SSE change of moving v from region l to c. */
             double mc = S[cp] / (double)n[cp];
@@ -501,18 +501,12 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
             double t2 = 0.0;
             if (n[lp] > 1) t2 = ((double)n[lp] / ((double)n[lp] - 1.0)) * (b * b);
             data = t1 - t2;
-            /* first-order scale: each deviation a = v - mu perturbed by |v| + |mu|, plus the terms */
-            if (scale) {
-                double wc = (double)n[cp] / ((double)n[cp] + 1.0);
-                double wl = n[lp] > 1 ? (double)n[lp] / ((double)n[lp] - 1.0) : 0.0;
-                scale[k] = 2.0 * wc * fabs(a) * (fabs(v) + fabs(mc)) + 2.0 * wl * fabs(b) * (fabs(v) + fabs(ml)) +
-                           fabs(t1) + fabs(t2);
-            }
+            if (scale) scale[k] = fabs(t1) + fabs(t2);
         } else {
             /* Piecewise smooth: local means over the ball of radius R, row-major order. */
             int64_t z, y, x;
             coords(p, xi, &z, &y, &x);
-            double sc = 0.0, sl = 0.0, ac = 0.0, al = 0.0;
+            double sc = 0.0, sl = 0.0;
             int64_t cc = 0, cl = 0;
             int Rz = p->ndim == 3 ? Ri : 0;
             for (int dz = -Rz; dz <= Rz; dz++)
@@ -524,8 +518,8 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
                         if (!inside(p, zz, yy, xx)) continue;
                         int64_t j = (zz * p->H + yy) * p->W + xx;
                         int32_t m = L[j];
-                        if (m == cp) { sc = sc + pix(p, I, j); ac += fabs(pix(p, I, j)); cc++; }
-                        else if (m == lp) { sl = sl + pix(p, I, j); al += fabs(pix(p, I, j)); cl++; }
+                        if (m == cp) { sc = sc + pix(p, I, j); cc++; }
+                        else if (m == lp) { sl = sl + pix(p, I, j); cl++; }
                     }
             double muc = sc / (double)cc;
             double mul = sl / (double)cl;
@@ -535,17 +529,16 @@ void orc_energy(const orc_params* p, const void* I, const int32_t* L,
                 double fl = poisson_f(v, mul, p->mu_floor);
                 data = fc - fl;
                 if (scale) {
+                    /* the four terms of (m_c - v ln m_c) - (m_l - v ln m_l), means floored */
                     double mc = muc > p->mu_floor ? muc : p->mu_floor;
                     double ml = mul > p->mu_floor ? mul : p->mu_floor;
-                    scale[k] = mc + fabs(v * orc_log(mc)) + ml + fabs(v * orc_log(ml)) + fabs(v);
+                    scale[k] = fabs(mc) + fabs(v * orc_log(mc)) + fabs(ml) + fabs(v * orc_log(ml));
                 }
             } else {
                 double a = v - muc;
                 double b = v - mul;
                 data = a * a - b * b;
-                if (scale)
-                    scale[k] = 2.0 * fabs(a) * (fabs(v) + ac / (double)cc) +
-                               2.0 * fabs(b) * (fabs(v) + al / (double)cl) + a * a + b * b;
+                if (scale) scale[k] = a * a + b * b;
             }
         }
         int64_t dP;
@@ -573,8 +566,7 @@ static int cmp_i64(const void* a, const void* b)
 
 void orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int32_t* l,
                  const int32_t* c, const double* dE, int all_pairs,
-                 double* g, double* A, double* B, int32_t* nQ, int32_t* nQp,
-                 const double* dE_scale, double* scale)
+                 double* g, double* A, double* B, int32_t* nQ, int32_t* nQp, double* scale)
 {
     double rc = p->cutoff;
     double r2 = rc * rc;
@@ -613,7 +605,12 @@ void orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int3
                         int64_t zz = kz + dz, yy = ky + dy, xx = kx + dx;
                         if (zz < 0 || zz >= ncz || yy < 0 || yy >= ncy || xx < 0 || xx >= ncx) continue;
                         int64_t cell = (zz * ncy + yy) * ncx + xx;
-                        for (int64_t j = cstart[cell]; j < cstart[cell + 1]; j++) list[nlist++] = order[j];
+                        for (int64_t j = cstart[cell]; j < cstart[cell + 1]; j++) {
+                            int64_t q = order[j];
+                            int64_t ez = cz[q] - cz[k], ey = cy[q] - cy[k], ex = cx[q] - cx[k];
+                            /* only the particles inside the cutoff take part in the sums */
+                            if ((double)(ez * ez + ey * ey + ex * ex) < r2) list[nlist++] = q;
+                        }
                     }
             qsort(list, (size_t)nlist, sizeof(int64_t), cmp_i64);   /* ascending particle key */
         }
@@ -625,9 +622,8 @@ void orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int3
             int64_t d2 = ddz * ddz + ddy * ddy + ddx * ddx;
             if (!((double)d2 < r2)) continue;
             double K = orc_kernel_eq5(sqrt((double)d2), E, eps);
-            double sq = dE_scale ? dE_scale[q] : fabs(dE[q]);
-            if (l[q] == l[k]) { As = As + K * dE[q]; Aa += fabs(K) * sq; na++; }
-            if (c[q] == l[k]) { Bs = Bs + K * dE[q]; Ba += fabs(K) * sq; nb++; }
+            if (l[q] == l[k]) { As = As + K * dE[q]; Aa += fabs(K * dE[q]); na++; }
+            if (c[q] == l[k]) { Bs = Bs + K * dE[q]; Ba += fabs(K * dE[q]); nb++; }
         }
         double a = na ? As / (double)na : 0.0;
         double b = nb ? Bs / (double)nb : 0.0;
@@ -636,7 +632,7 @@ void orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int3
         if (B) B[k] = b;
         if (nQ) nQ[k] = na;
         if (nQp) nQp[k] = nb;
-        if (scale) scale[k] = (na ? Aa / (double)na : 0.0) + (nb ? Ba / (double)nb : 0.0) + fabs(a) + fabs(b);
+        if (scale) scale[k] = (na ? Aa / (double)na : 0.0) + (nb ? Ba / (double)nb : 0.0);
     }
     free(cz); free(cy); free(cx); free(cstart); free(order); free(fill); free(list);
 }
@@ -1024,6 +1020,19 @@ void orc_state_init(const orc_params* p, orc_state* st)
     st->pad_ = 0;
 }
 
+/* Oscillation fallback and convergence (reading of the Eq. 6 discussion): after an iteration
+ * run in mode `mode_used` that accepted `na` moves, record a new minimum of the accepted-move
+ * count (strictly smaller than every earlier one), switch to L2 for good when the last new
+ * minimum lies osc_window or more iterations back, and mark convergence after an L2 iteration
+ * with no accepted move. */
+void orc_advance_mode(const orc_params* p, orc_state* st, int32_t mode_used, int64_t na)
+{
+    if (st->best_A < 0 || na < st->best_A) { st->best_A = na; st->t_best = st->t; }
+    if (st->mode != 1 && p->osc_window > 0 && st->t - st->t_best >= p->osc_window) st->mode = 1;
+    if (mode_used == 1 && na == 0) st->converged = 1;
+    st->t++;
+}
+
 int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
                 orc_status* status, int64_t cap, const orc_dump* dump)
 {
@@ -1054,13 +1063,13 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
     orc_energy(p, I, L, n, S, N, idx, l, c, dE, dEs);
     if (st->mode == 0 || st->mode == 2) {
         if (st->mode == 0) {
-            orc_sobolev(p, N, idx, l, c, dE, 0, g, A, B, NULL, NULL, dEs, gs);
+            orc_sobolev(p, N, idx, l, c, dE, 0, g, A, B, NULL, NULL, gs);
         } else {
             /* length scale of the inner product set to the contour length (Length scale
              * section): E = |Gamma|, support |d| < E/2, every particle pair considered */
             orc_params q = *p;
             q.cutoff = 0.5 * (double)orc_perimeter(p, L);
-            orc_sobolev(&q, N, idx, l, c, dE, 1, g, A, B, NULL, NULL, dEs, gs);
+            orc_sobolev(&q, N, idx, l, c, dE, 1, g, A, B, NULL, NULL, gs);
         }
         for (int64_t k = 0; k < N; k++)
             if (A[k] != 0.0 && B[k] != 0.0 && ((A[k] > 0.0) == (B[k] > 0.0))) status->n_osc++;
@@ -1097,16 +1106,12 @@ int orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,
             if (dump->c) dump->c[k] = c[k];
             if (dump->dE) dump->dE[k] = dE[k];
             if (dump->g) dump->g[k] = g[k];
-            if (dump->dE_scale) dump->dE_scale[k] = dEs[k];
-            if (dump->g_scale) dump->g_scale[k] = gs[k];
+            if (dump->dE_terms) dump->dE_terms[k] = dEs[k];
+            if (dump->g_terms) dump->g_terms[k] = gs[k];
         }
     }
-    /* oscillation fallback and convergence */
-    if (st->best_A < 0 || na < st->best_A) { st->best_A = na; st->t_best = st->t; }
-    if (st->mode != 1 && p->osc_window > 0 && st->t - st->t_best >= p->osc_window) st->mode = 1;
-    if (status->mode_used == 1 && na == 0) st->converged = 1;
+    orc_advance_mode(p, st, status->mode_used, na);
     status->converged = st->converged;
-    st->t++;
     free(n); free(S); free(Q); free(idx); free(l); free(c); free(dE); free(g); free(A); free(B);
     free(dEs); free(gs);
     free(acc_idx); free(acc_c);

@@ -54,6 +54,10 @@
  *                         local-minimum-rounds evaluation and permutation tests.
  *   orc_perimeter       - |Gamma| as the length prior counts it; pinned by square and
  *                         cube perimeters and a numpy recount.
+ *   orc_advance_mode    - pinned by hand-worked accepted-move sequences with their switch and
+ *                         convergence iterations (tests/golden/osc_switch.txt).
+ *   term sums           - the tolerance scale of dE and g (Sum |terms|); pinned by term-by-term
+ *                         numpy recomputes from the region statistics and the Eq. 6 sets.
  *   orc_iterate         - composition of the above; pinned by the partition and
  *                         connectivity invariants after every iteration. With E = |Gamma|
  *                         (gradient 2) the Sobolev step is the all-pairs Eq. 6 at E = the
@@ -152,8 +156,9 @@ double  orc_psf_norm2(const orc_params* p, int64_t z, int64_t y, int64_t x);
 void    orc_stats(const orc_params* p, const void* I, const int32_t* L,
                   int64_t* n, double* S, double* Q);
 
-/* scale (may be NULL): first-order magnitude scale of each dE: every deviation v - mu
- * weighted by the magnitudes it is formed from (|v| + |mu|), plus its terms */
+/* scale (may be NULL): the sum of the magnitudes of the terms each dE adds up, the scale of
+ * the float tolerance: PC |t1| + |t2|, PS a^2 + b^2, Poisson |m_c| + |v ln m_c| + |m_l| +
+ * |v ln m_l|, deconvolving |d^2 |K_x|^2| + |2 d G|; plus |w dP| of the regulariser */
 void    orc_energy(const orc_params* p, const void* I, const int32_t* L,
                    const int64_t* n, const double* S, int64_t N,
                    const uint32_t* idx, const int32_t* l, const int32_t* c, double* dE, double* scale);
@@ -163,12 +168,10 @@ int64_t orc_delta_perimeter(const orc_params* p, const int32_t* L, uint32_t x, i
 /* |Gamma|: connectivity-adjacent pixel pairs with different labels */
 int64_t orc_perimeter(const orc_params* p, const int32_t* L);
 
-/* scale (may be NULL): sum_Q K s_q / |Q| + sum_Q' K s_q / |Q'| + |A| + |B| of each g, with s_q
- * the scale of dE_q (dE_scale, or |dE_q| when dE_scale is NULL) */
+/* scale (may be NULL): the term-magnitude sum of each g, sum_Q |K dE_q| / |Q| + sum_Q' |K dE_q| / |Q'| */
 void    orc_sobolev(const orc_params* p, int64_t N, const uint32_t* idx, const int32_t* l,
                     const int32_t* c, const double* dE, int all_pairs,
-                    double* g, double* A, double* B, int32_t* nQ, int32_t* nQp,
-                    const double* dE_scale, double* scale);
+                    double* g, double* A, double* B, int32_t* nQ, int32_t* nQp, double* scale);
 
 int     orc_simple_2d(const uint8_t* nb9);
 int     orc_simple_3d(const uint8_t* nb27);
@@ -192,6 +195,9 @@ int64_t orc_select(const orc_params* p, const int32_t* L, int64_t N,
 
 void    orc_state_init(const orc_params* p, orc_state* st);
 
+/* the mode and convergence rule applied after each iteration (see rc_oracle.c) */
+void    orc_advance_mode(const orc_params* p, orc_state* st, int32_t mode_used, int64_t na);
+
 /* per-particle arrays of one iteration, in key order (each pointer may be NULL) */
 typedef struct {
     uint32_t* idx;
@@ -199,8 +205,8 @@ typedef struct {
     int32_t* c;
     double* dE;
     double* g;
-    double* dE_scale;
-    double* g_scale;
+    double* dE_terms;    /* term-magnitude sums (orc_energy's scale) */
+    double* g_terms;     /* term-magnitude sums (orc_sobolev's scale; dE_terms in L2 mode) */
 } orc_dump;
 
 int     orc_iterate(const orc_params* p, const void* I, int32_t* L, orc_state* st,

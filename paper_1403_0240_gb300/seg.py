@@ -418,21 +418,37 @@ def debug_simple(ndim: int, masks) -> np.ndarray:
 def region_stats_noalloc(image, labels, nlabels: int, n=None, S=None, Q=None, stream=None):
     """Exact region statistics through the allocation-free entry point.
 
-    image and labels are CUDA tensors; n, S, Q (int64 / float64 CUDA tensors of nlabels
-    elements) are allocated here by torch when not given, since the library allocates
-    nothing. Returns (n, S, Q)."""
+    image (float32 or uint16) and labels (int32, as many elements as image) are CUDA tensors
+    on one device; n, S, Q (int64 / float64 CUDA tensors of nlabels elements on that device)
+    are allocated here by torch when not given, since the library allocates nothing. The work
+    is ordered on `stream`, by default the current torch stream of the image's device.
+    Returns (n, S, Q)."""
     import torch
+    if not (torch.is_tensor(image) and torch.is_tensor(labels) and image.is_cuda and labels.is_cuda):
+        raise ValueError("image and labels must be CUDA tensors")
     dev = image.device
-    if n is None:
-        n = torch.empty(nlabels, dtype=torch.int64, device=dev)
-    if S is None:
-        S = torch.empty(nlabels, dtype=torch.float64, device=dev)
-    if Q is None:
-        Q = torch.empty(nlabels, dtype=torch.float64, device=dev)
-    ip, _ = _ptr(image)
-    lp, _ = _ptr(labels)
-    _check(lib().seg_region_stats_noalloc(_dtype_code(image), int(image.numel()), ip, lp, int(nlabels),
-                                          C.c_void_p(n.data_ptr()), C.c_void_p(S.data_ptr()),
-                                          C.c_void_p(Q.data_ptr()), _stream_handle(stream)),
-           "seg_region_stats_noalloc")
-    return n, S, Q
+    if labels.device != dev:
+        raise ValueError("image and labels must be on one device")
+    if labels.dtype != torch.int32:
+        raise ValueError(f"labels must be int32, not {labels.dtype}")
+    if labels.numel() != image.numel():
+        raise ValueError(f"labels has {labels.numel()} elements, the image {image.numel()}")
+    _dtype_code(image)
+    want = {"n": torch.int64, "S": torch.float64, "Q": torch.float64}
+    outs = {"n": n, "S": S, "Q": Q}
+    for k, t in outs.items():
+        if t is None:
+            outs[k] = torch.empty(nlabels, dtype=want[k], device=dev)
+        elif not (torch.is_tensor(t) and t.device == dev and t.dtype == want[k] and t.numel() == nlabels
+                  and t.is_contiguous()):
+            raise ValueError(f"{k} must be a contiguous {want[k]} tensor of {nlabels} elements on {dev}")
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    ip, ikeep = _ptr(image)
+    lp, lkeep = _ptr(labels)
+    code = lib().seg_region_stats_noalloc(_dtype_code(image), int(image.numel()), ip, lp, int(nlabels),
+                                          C.c_void_p(outs["n"].data_ptr()), C.c_void_p(outs["S"].data_ptr()),
+                                          C.c_void_p(outs["Q"].data_ptr()), _stream_handle(stream))
+    del ikeep, lkeep                              # the call has returned: the copies may go
+    _check(code, "seg_region_stats_noalloc")
+    return outs["n"], outs["S"], outs["Q"]

@@ -364,17 +364,19 @@ def ellipsoids(D: int = 256, H: int = 256, W: int = 256, seed: int = 2, n_ellips
     return Workload("ellipsoids", counts, labels0, "pc", 6, lam, cutoff, 0.0, iterations, {"seed": seed})
 
 
+def batch_disk(i: int, seed0: int = 1000, lo: int = 64, hi: int = 512, iterations: int = 50) -> Workload:
+    """Image i of the uneven batch: a disk scene with seed seed0 + i, sides U{lo..hi}."""
+    rs = Stream(seed0 + i, 7)
+    H, W = (int(v) for v in rs.integers(lo, hi, 2))
+    w = disks(H, W, seed=seed0 + i, iterations=iterations)
+    w.name = f"batch{i}"
+    return w
+
+
 def batch_disks(n_images: int = 512, seed0: int = 1000, lo: int = 64, hi: int = 512,
                 iterations: int = 50) -> list[Workload]:
     """Many uneven 2D disk scenes (seeds seed0 + i), sides U{lo..hi} drawn independently."""
-    out = []
-    for i in range(n_images):
-        rs = Stream(seed0 + i, 7)
-        H, W = (int(v) for v in rs.integers(lo, hi, 2))
-        w = disks(H, W, seed=seed0 + i, iterations=iterations)
-        w.name = f"batch{i}"
-        out.append(w)
-    return out
+    return [batch_disk(i, seed0, lo, hi, iterations) for i in range(n_images)]
 
 
 @dataclass
@@ -411,6 +413,23 @@ def make_job(a: Arrival, iterations: int = 100) -> Workload:
     if a.kind == "ps2d":
         return ellipses(a.side, a.side, seed=a.seed, iterations=iterations)
     return ellipsoids(a.side, a.side, a.side, seed=a.seed, iterations=iterations)
+
+
+def served_job_key(a: Arrival) -> tuple:
+    """The pooled job an arrival of the served stream runs: its kind, its side rounded to a
+    bucket (32 voxels in 3D within 64..256, 64 pixels in 2D within 128..1024) and one seed per
+    bucket. Arrivals of one bucket run the same image, so that the stream needs only a few
+    dozen distinct images (a 256^3 volume takes seconds to generate)."""
+    if a.kind == "pc3d":
+        side = max(64, min(256, int(round(a.side / 32.0)) * 32))
+    else:
+        side = max(128, min(1024, int(round(a.side / 64.0)) * 64))
+    return (a.kind, side, 7 * side + len(a.kind))
+
+
+def served_job(key: tuple, iterations: int = 100) -> Workload:
+    kind, side, seed = key
+    return make_job(Arrival(0.0, kind, side, seed), iterations=iterations)
 
 
 def config(index: int) -> Workload | list:

@@ -12,6 +12,13 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
 
 
+def pytest_sessionfinish(session, exitstatus):
+    # the GPU parity tests' largest float errors per workload, when SEG_PARITY_REPORT is set
+    helpers = sys.modules.get("gpu_helpers")
+    if helpers is not None:
+        helpers.write_report()
+
+
 @pytest.fixture(scope="session")
 def orc():
     import oracle

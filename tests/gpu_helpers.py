@@ -1,15 +1,28 @@
 """Shared helpers of the GPU parity tests: run the CUDA path and the oracle side by side."""
+import json
+import os
+
 import numpy as np
 
 import oracle
 from paper_1403_0240_gb300 import seg
 
-# Float tolerance of the FP32 path against the FP64 oracle: 1e-5 of each value's first-order
-# magnitude scale from the oracle (dE: every deviation v - mu weighted by the magnitudes it is
-# formed from, plus the data and length terms; g: the Eq. 6 sums of K times those scales,
-# plus |A| + |B|), because both are differences of nearly equal quantities. Each value must
-# also lie within the rigorous bound the library reports for it.
+# Float tolerance of the FP32 path against the FP64 oracle. Both dE and g are sums of terms
+# that can cancel (t1 - t2, A - B), so the contract is |x - x_ref| <= REL_TOL * T, with T the
+# value's sum of term magnitudes computed by the oracle (orc_energy / orc_sobolev). Where the
+# value is not dominated by cancellation, |x_ref| >= PLAIN_FLOOR * T, the plain relative error
+# |x - x_ref| / |x_ref| must also stay within REL_TOL. Below that floor a plain relative bound of
+# 1e-5 would need an absolute error under 1e-5 * PLAIN_FLOOR * T, and one float32 rounding of a
+# single input term already costs up to 2^-24 * T = 6e-8 * T; the plain relative error at
+# |x_ref| >= 1e-3 * T is therefore recorded, not asserted. Each value must also lie within the
+# rigorous bound the library reports for it.
 REL_TOL = 1e-5
+PLAIN_FLOOR = 0.1
+REPORT_FLOORS = (1e-3, 1e-2, PLAIN_FLOOR)
+
+# largest errors seen per test label (written out at the end of the session when
+# SEG_PARITY_REPORT names a file)
+ERRORS: dict = {}
 
 
 def pair(w, gradient="sobolev", osc_window=0, cell_edge=0, lam=None, cutoff=None):
@@ -23,25 +36,62 @@ def pair(w, gradient="sobolev", osc_window=0, cell_edge=0, lam=None, cutoff=None
     return ctx, oracle.Run(p, w.image, w.labels0)
 
 
-def scaled_err(x, ref, scale):
-    """max |x - ref| / scale, the scale being the sum of term magnitudes (0 where scale is 0)."""
+def scaled_err(x, ref, terms):
+    """max |x - ref| / T over the values, T the sum of term magnitudes; a value whose terms are
+    all zero must be exact."""
     ref = np.asarray(ref, np.float64)
     if ref.size == 0:
         return 0.0
     err = np.abs(np.asarray(x, np.float64) - ref)
-    scale = np.asarray(scale, np.float64)
-    assert (err[scale == 0] == 0).all()
-    nz = scale > 0
-    return float((err[nz] / scale[nz]).max()) if nz.any() else 0.0
+    terms = np.asarray(terms, np.float64)
+    assert (err[terms == 0] == 0).all(), "a value with no non-zero term is not exact"
+    nz = terms > 0
+    return float((err[nz] / terms[nz]).max()) if nz.any() else 0.0
 
 
-def plain_rel_err(x, ref, scale):
-    """Plain relative error where |ref| > 1e-3 of its scale (reported, not asserted)."""
+def plain_rel_err(x, ref, terms, floor):
+    """max |x - ref| / |ref| over the values with |ref| >= floor * T."""
     ref = np.asarray(ref, np.float64)
-    m = np.abs(ref) > 1e-3 * np.asarray(scale, np.float64)
+    m = np.abs(ref) >= floor * np.asarray(terms, np.float64)
+    m &= ref != 0
     if not m.any():
         return 0.0
     return float((np.abs(np.asarray(x, np.float64)[m] - ref[m]) / np.abs(ref[m])).max())
+
+
+def float_errors(x, ref, terms, name):
+    """The contract's errors of one float output: scaled, and plain relative at each floor."""
+    out = {f"{name}_scaled": scaled_err(x, ref, terms)}
+    for f in REPORT_FLOORS:
+        out[f"{name}_plain@{f:g}"] = plain_rel_err(x, ref, terms, f)
+    return out
+
+
+def check_floats(got_dE, got_g, dump, where):
+    """Assert the float contract on dE and g against the oracle's dump; returns the errors."""
+    e = float_errors(got_dE, dump["dE"], dump["dE_terms"], "dE")
+    e.update(float_errors(got_g, dump["g"], dump["g_terms"], "g"))
+    for name in ("dE", "g"):
+        assert e[f"{name}_scaled"] <= REL_TOL, (where, name, "outside 1e-5 of its term sum", e)
+        assert e[f"{name}_plain@{PLAIN_FLOOR:g}"] <= REL_TOL, (where, name, "plain relative error", e)
+    return e
+
+
+def record(label, errors):
+    """Keep the largest error of each kind per label (the test's workload)."""
+    cur = ERRORS.setdefault(label, {"values": 0})
+    for k, v in errors.items():
+        if k == "n":
+            cur["values"] += int(v)
+        elif isinstance(v, float):
+            cur[k] = max(cur.get(k, 0.0), v)
+
+
+def write_report():
+    path = os.environ.get("SEG_PARITY_REPORT")
+    if path and ERRORS:
+        with open(path, "w") as f:
+            json.dump(ERRORS, f, indent=1, sort_keys=True)
 
 
 def compare_step(ctx, run, label=""):
@@ -66,10 +116,8 @@ def compare_step(ctx, run, label=""):
     assert (g_err <= g["eg"].astype(np.float64)).all(), (where, "g outside its bound", float(g_err.max()))
     fixed = (g["flags"] & 1) != 0
     assert np.array_equal(g["key"][fixed], dump["g"][fixed]), (where, "FP64 recompute differs from the oracle")
-    stats = {"rel_dE": scaled_err(g["dE"], dump["dE"], dump["dE_scale"]),
-             "rel_g": scaled_err(g["g"], dump["g"], dump["g_scale"]),
-             "plain_rel_g": plain_rel_err(g["g"], dump["g"], dump["g_scale"]),
-             "fixed": int(fixed.sum()), "n": int(g["idx"].size)}
-    assert stats["rel_dE"] <= REL_TOL and stats["rel_g"] <= REL_TOL, (where, stats)
+    stats = check_floats(g["dE"], g["g"], dump, where)
+    stats.update(fixed=int(fixed.sum()), n=int(g["idx"].size))
+    record(label.split(" it")[0], stats)
     assert np.array_equal(ctx.labels(), run.L), (where, "labels differ")
     return st, stats

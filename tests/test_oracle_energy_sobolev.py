@@ -220,3 +220,131 @@ def test_degenerate_cutoff_is_rescaled_l2(orc, cutoff):
     assert (nQ == 1).all() and (nQp == 0).all()
     E = 2 * cutoff
     assert np.allclose(g, (3.0 / E) * dE, rtol=1e-15, atol=0)
+
+
+# ---- the tolerance scale: sums of term magnitudes ----
+
+def _region_sse(v):
+    v = np.asarray(v, np.float64)
+    return float(((v - v.mean()) ** 2).sum()) if v.size else 0.0
+
+
+@pytest.mark.parametrize("dtype,shape,lam", [(np.float32, (11, 13), 0.3), (np.uint16, (10, 12), 40.0),
+                                             (np.float32, (5, 6, 7), 0.2)])
+def test_pc_terms_are_brute_force_region_changes(orc, dtype, shape, lam):
+    # The PC energy difference adds two region terms and the length term: the increase of
+    # region c's squared deviations when v joins it, minus the decrease of region l's when v
+    # leaves it, plus lambda * dP. Each is recomputed here by brute force from the pixels.
+    rng = np.random.default_rng(17)
+    I = (rng.normal(1.0, 0.5, shape).astype(np.float32) if dtype == np.float32
+         else rng.integers(50, 400, shape).astype(np.uint16))
+    L = rng.integers(0, 3, shape).astype(np.int32)
+    p = orc.make_params(I, L, "pc", lam=lam, nlabels=3)
+    idx, l, c = orc.extract(p, L)
+    dE, terms = orc.energy(p, I, L, idx, l, c, with_terms=True)
+    flat_I = I.reshape(-1).astype(np.float64)
+    flat_L = L.reshape(-1)
+    P = _perimeter(L)
+    for k in range(0, idx.size, 2):
+        x, lk, ck = int(idx[k]), int(l[k]), int(c[k])
+        in_c, in_l = flat_I[flat_L == ck], flat_I[flat_L == lk]
+        t1 = _region_sse(np.append(in_c, flat_I[x])) - _region_sse(in_c)
+        rest = flat_I[(flat_L == lk) & (np.arange(flat_L.size) != x)]
+        t2 = _region_sse(in_l) - _region_sse(rest)
+        L2 = flat_L.copy()
+        L2[x] = ck
+        dP = _perimeter(L2.reshape(shape)) - P
+        ref = abs(t1) + abs(t2) + abs(lam * dP)
+        tol = 1e-10 * (float((flat_I ** 2).sum()) + 1.0)
+        assert terms[k] == pytest.approx(ref, abs=tol), (k, terms[k], ref)
+        assert terms[k] >= abs(dE[k]) - tol
+
+
+@pytest.mark.parametrize("model", ["ps", "psp"])
+def test_ps_terms_from_convolved_local_means(orc, model):
+    # PS: (v - m_c)^2 + (v - m_l)^2; Poisson: m_c + |v ln m_c| + m_l + |v ln m_l| (means floored),
+    # with the local means from scipy convolutions of the label indicators; plus lambda |dP|
+    rng = np.random.default_rng(19)
+    shape, R, lam = (18, 21), 3.0, 0.05
+    I = rng.uniform(0.2, 2.0, shape).astype(np.float32)
+    L = rng.integers(0, 3, shape).astype(np.int32)
+    p = orc.make_params(I, L, model, lam=lam, ps_radius=R)
+    idx, l, c = orc.extract(p, L)
+    dE, terms = orc.energy(p, I, L, idx, l, c, with_terms=True)
+    fp = _ball(R, 2)
+    Id = I.astype(np.float64)
+    sums = {m: ndimage.convolve((L == m) * Id, fp, mode="constant").reshape(-1) for m in range(3)}
+    cnts = {m: ndimage.convolve((L == m).astype(np.float64), fp, mode="constant").reshape(-1) for m in range(3)}
+    v = Id.reshape(-1)
+    P = _perimeter(L)
+    for k in range(idx.size):
+        x = int(idx[k])
+        mc = sums[int(c[k])][x] / cnts[int(c[k])][x]
+        ml = sums[int(l[k])][x] / cnts[int(l[k])][x]
+        if model == "ps":
+            data_terms = (v[x] - mc) ** 2 + (v[x] - ml) ** 2
+        else:
+            mc, ml = max(mc, p.mu_floor), max(ml, p.mu_floor)
+            data_terms = mc + abs(v[x] * math.log(mc)) + ml + abs(v[x] * math.log(ml))
+        L2 = L.copy().reshape(-1)
+        L2[x] = c[k]
+        dP = _perimeter(L2.reshape(shape)) - P
+        assert terms[k] == pytest.approx(data_terms + abs(lam * dP), rel=1e-9, abs=1e-12)
+
+
+def test_sobolev_terms_straight_line_golden(orc):
+    # every dE = 1 on the straight contour: no term cancels, so the term sum is A + B of the
+    # hand-worked golden values
+    vals = {}
+    for line in open(os.path.join(GOLD, "sobolev_line.txt")):
+        line = line.split("#")[0].strip()
+        if line:
+            k, val = line.split()
+            vals[k] = float(val)
+    L = np.zeros((12, 40), np.int32)
+    L[:6] = 1
+    p = orc.make_params(np.zeros(L.shape, np.float32), L, cutoff=3.0)
+    idx, l, c = orc.extract(p, L)
+    *_, terms = orc.sobolev(p, idx, l, c, np.ones(idx.size), with_terms=True)
+    k = int(np.nonzero(idx == 5 * 40 + 20)[0][0])
+    assert terms[k] == pytest.approx(vals["A"] + vals["B"], abs=1e-15)
+
+
+def test_sobolev_terms_by_brute_force_sets(orc):
+    # sum over Q of |K dE_q| / |Q| plus the same over Q', the sets and K found here by brute
+    # force over all particle pairs with numpy; signed energy differences so that terms cancel
+    rng = np.random.default_rng(23)
+    L = rng.integers(0, 3, (17, 19)).astype(np.int32)
+    cutoff = 3.5
+    p = orc.make_params(np.zeros(L.shape, np.float32), L, cutoff=cutoff)
+    idx, l, c = orc.extract(p, L)
+    dE = rng.normal(0, 1, idx.size)
+    g, A, B, nQ, nQp, terms = orc.sobolev(p, idx, l, c, dE, with_terms=True)
+    y, x = np.divmod(idx.astype(np.int64), L.shape[1])
+    d2 = (y[:, None] - y[None, :]) ** 2 + (x[:, None] - x[None, :]) ** 2
+    near = d2 < cutoff ** 2
+    E = 2 * cutoff
+    K = (3.0 / E) * (1.0 - 2.0 * np.sqrt(d2) / E) ** 2
+    inQ = near & (l[None, :] == l[:, None])
+    inQp = near & (c[None, :] == l[:, None])
+    w = np.abs(K * dE[None, :])
+    ref = (w * inQ).sum(1) / inQ.sum(1) + np.where(inQp.sum(1) > 0, (w * inQp).sum(1) / np.maximum(inQp.sum(1), 1), 0)
+    assert np.allclose(terms, ref, rtol=1e-12, atol=0)
+    assert (terms >= np.abs(g) * (1 - 1e-12)).all()
+    assert (terms > 2 * np.abs(g)).any(), "the case should contain cancelling terms"
+
+
+def test_oscillation_rule_golden(orc):
+    # hand-worked accepted-move sequences (tests/golden/osc_switch.txt)
+    n = 0
+    for line in open(os.path.join(GOLD, "osc_switch.txt")):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        name, grad, window, acc, modes, conv = line.split()
+        acc = [int(t) for t in acc.split(",")]
+        want = list(zip([int(t) for t in modes.split(",")], [int(t) for t in conv.split(",")]))
+        got = orc.mode_sequence(int(window), acc, gradient=int(grad))
+        assert got == want, (name, got, want)
+        n += 1
+    assert n >= 7

@@ -69,8 +69,24 @@ def test_rejects_what_it_cannot_hold():
         seg.region_stats_noalloc(img, lab, 1025)            # above the fixed maximum of labels
     assert e.value.code == seg.SEG_EINVAL
     n = torch.empty(M, dtype=torch.int64)                   # host output: rejected
-    with pytest.raises(seg.SegError):
+    with pytest.raises(ValueError):
         seg.region_stats_noalloc(img, lab, M, n=n)
+    with pytest.raises(ValueError):                         # int64 labels would be read as pairs of words
+        seg.region_stats_noalloc(img, lab.to(torch.int64), M)
+    with pytest.raises(ValueError):                         # fewer labels than pixels: reads past the end
+        seg.region_stats_noalloc(img, lab.reshape(-1)[:-1].contiguous(), M)
+    with pytest.raises(ValueError):                         # an output of the wrong length
+        seg.region_stats_noalloc(img, lab, M, S=torch.empty(M - 1, dtype=torch.float64, device=img.device))
+    # through the C-ABI itself, a host output buffer is refused with SEG_EINVAL
+    import ctypes
+    n_host = np.zeros(M, np.int64)
+    S_dev = torch.empty(M, dtype=torch.float64, device=img.device)
+    Q_dev = torch.empty(M, dtype=torch.float64, device=img.device)
+    code = seg.lib().seg_region_stats_noalloc(seg.SEG_F32, img.numel(), ctypes.c_void_p(img.data_ptr()),
+                                              ctypes.c_void_p(lab.data_ptr()), M, n_host.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.c_void_p(S_dev.data_ptr()), ctypes.c_void_p(Q_dev.data_ptr()),
+                                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert code == seg.SEG_EINVAL
     # a valid call afterwards still matches
     n2, S2, Q2 = seg.region_stats_noalloc(img, lab, M)
     n_ref, S_ref, Q_ref = _reference(I, L)
