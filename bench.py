@@ -1,16 +1,26 @@
 #!/usr/bin/env python
 """Throughput of the particle region-competition iteration with Sobolev gradients.
 
-One step = one iteration of the whole hot path (extraction, energy differences, Eq. 6
-interaction, certified selection, moves, exact statistics) on one job. The default job
-is the 1024x1024 float32 piecewise-smooth ellipse scene (local-mean radius 8, cutoff 5,
-256 square seeds, 200 iterations per job; a fresh job is started, untimed, every 200
-iterations). The metric counts particles processed per second (particle-iterations/s).
+The metric counts particles processed per second (particle-iterations/s), one iteration of
+the whole hot path (extraction, energy differences, Eq. 6 interaction, certified selection,
+moves, exact statistics) over every particle of a job.
+
+Default workload (served): a Poisson arrival stream of segmentation jobs (200 jobs/s; 80% 2D
+of sides 128-1024, half piecewise-constant disk scenes and half piecewise-smooth ellipse scenes,
+20% 3D uint16 ellipsoid volumes of sides 64-256; 100 iterations each) through the continuous-
+batching server. A step is one server step (up to --iters-per-step iterations of every resident
+job); after the ramp-up, K steps are timed with CUDA events. The same stream is also run one
+job at a time (the plain loop), and the line reports both, with p50/p99 job latency and the
+arrival rate the server sustains.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
-Under torchrun (N > 1) every rank steps its own independent job (replicas: the method
-has no exchange step), and rank 0 prints one JSON line.
+Other workloads step one job per iteration (ellipses1024, ellipsoids256, disks128, ...), a
+512-image batch (batch512), the region-sum precision study (precision) or the L2/Sobolev
+convergence study (convergence).
+
+Under torchrun (N > 1) every rank runs its own independent stream or job (replicas: the
+method has no exchange step), and rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -435,108 +445,315 @@ def run_precision(args, world, rank, local, pg):
     print(json.dumps(line), flush=True)
 
 
-def _pool_workload(kind, side, cache):
-    """Synthetic job images, one per (kind, side rounded to a bucket), reused by arrivals."""
+def _served_jobs(args, rank):
+    """The arrival stream and its pooled job images (generated in worker processes, largest
+    first; spawn, so that no worker inherits a CUDA context)."""
+    import multiprocessing as mp
+
     from paper_1403_0240_gb300 import synth
-    if kind == "pc3d":
-        side = max(64, min(256, int(round(side / 32.0)) * 32))
-    else:
-        side = max(128, min(1024, int(round(side / 64.0)) * 64))
-    key = (kind, side)
-    if key not in cache:
-        cache[key] = synth.make_job(synth.Arrival(0.0, kind, side, seed=7 * side + len(kind)), iterations=100)
-    return key, cache[key]
+    arrivals = synth.arrival_stream(args.jobs, rate=args.rate, seed=42 + rank)
+    keys = [synth.served_job_key(a) for a in arrivals]
+    distinct = sorted(set(keys), key=lambda k: -(k[1] ** (3 if k[0] == "pc3d" else 2)))
+    procs = max(1, min(len(os.sched_getaffinity(0)), len(distinct), 16))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        made = pool.starmap(synth.served_job, [(k, args.job_iters) for k in distinct], chunksize=1)
+    return arrivals, keys, dict(zip(distinct, made))
 
 
-def run_served(args, world, rank, local, pg):
-    """Poisson arrivals (200 jobs/s): continuous batching against one job at a time."""
+def _served_params(w) -> dict:
+    return dict(model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff, ps_radius=w.ps_radius)
+
+
+def _plain_stream(reqs, dev):
+    """One job at a time, first come first served, in real time over the same arrivals: each
+    job is set up from its host buffers, stepped through all its iterations and its labels read
+    back before the next one starts. Returns (results, makespan from the first arrival)."""
     import torch
 
-    from paper_1403_0240_gb300 import seg, synth
-    from paper_1403_0240_gb300.serve import Request, SegBackend, Server, latency_summary
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    arrivals = synth.arrival_stream(args.jobs, seed=42 + rank)
-    cache, pinned = {}, {}
-    reqs, keys = [], []
-    for i, a in enumerate(arrivals):
-        key, w = _pool_workload(a.kind, a.side, cache)
-        if key not in pinned:      # request payloads sit in pinned host memory, as a server's would
-            pinned[key] = (torch.from_numpy(w.image).pin_memory(), torch.from_numpy(w.labels0).pin_memory(),
-                           int(w.labels0.max()) + 1)
-        keys.append(key)
-        img_h, lab_h, nl = pinned[key]
-        reqs.append(Request(i, a.t, img_h, lab_h, args.job_iters,
-                            dict(model=w.model, connectivity=w.connectivity, lam=w.lam, cutoff=w.cutoff,
-                                 ps_radius=w.ps_radius), nlabels=nl))
-    free, _ = torch.cuda.mem_get_info(dev)
-    budget = int(0.6 * free)
-    # warm-up on a few jobs
-    # new jobs are set up on a high-priority stream, so that their few small kernels do not queue
-    # behind the batch step in flight
-    be = SegBackend(stream=torch.cuda.current_stream(dev), init_stream=torch.cuda.Stream(dev, priority=-1),
-                    keep_labels=True)
-    srv = Server(be, budget, max_jobs=512, max_iters_per_step=args.iters_per_step)
-    for r in reqs[:4]:
-        srv.submit(Request(r.job_id, 0.0, r.image, r.labels0, 3, r.params, r.nlabels))
-    while not srv.idle():
-        srv.step()
-    srv = Server(be, budget, max_jobs=512, max_iters_per_step=args.iters_per_step)
-    barrier(pg)
+    from paper_1403_0240_gb300 import seg
+    torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    res = srv.run([Request(r.job_id, r.arrival, r.image, r.labels0, r.iterations, r.params, r.nlabels) for r in reqs],
-                  t0=t0)
-    t_served = max(x.completed for x in res) - t0
-    parts = sum(x.particles for x in res)
-    be.close()
-    served = latency_summary(res)
-    # one job at a time, first come first served, over the same arrival stream. Jobs built
-    # from the same pooled image are identical, so each distinct job is run once alone (set-up,
-    # its iterations and the label read-back, timed) and the queue is replayed on a virtual
-    # clock: start = max(arrival, previous completion), completion = start + service time.
-    svc, parts_of = {}, {}
-    for key in sorted(set(keys)):
-        r = reqs[keys.index(key)]
-        torch.cuda.synchronize(dev)
-        t1 = time.perf_counter()
+    out = []
+    for r in sorted(reqs, key=lambda r: r.arrival):
+        now = time.perf_counter() - t0
+        if now < r.arrival:
+            time.sleep(r.arrival - now)
+        start = time.perf_counter() - t0
         c = seg.Context(r.image, r.labels0, **r.params)
         st = c.step(r.iterations)
         c.labels()
-        torch.cuda.synchronize(dev)
-        svc[key] = time.perf_counter() - t1
-        parts_of[key] = st["particles_total"]
         c.close()
-    done_t, lat, parts_plain, busy = 0.0, [], 0, 0.0
-    by_kind = {}
-    for r, key in zip(reqs, keys):
-        start = max(r.arrival, done_t)
-        done_t = start + svc[key]
-        busy += svc[key]
-        lat.append(done_t - r.arrival)
-        parts_plain += parts_of[key]
-        k = by_kind.setdefault(key[0], [0, 0.0, 0])
-        k[0] += 1
-        k[1] += svc[key]
-        k[2] += parts_of[key]
+        done = time.perf_counter() - t0
+        out.append({"job": r.job_id, "arrival": r.arrival, "start": start, "done": done,
+                    "latency": done - r.arrival, "service": done - start, "particles": st["particles_total"]})
+    return out, max(x["done"] for x in out) - min(x["arrival"] for x in out)
+
+
+def _serve_stream(reqs, dev, budget, iters_per_step, keep_labels=False):
+    """The continuous-batching server over the arrivals in real time; returns (server, results)."""
+    import torch
+
+    from paper_1403_0240_gb300.serve import SegBackend, Server
+    be = SegBackend(stream=torch.cuda.current_stream(dev), init_stream=torch.cuda.Stream(dev, priority=-1),
+                    keep_labels=keep_labels, time_steps=True)
+    srv = Server(be, budget, max_jobs=512, max_iters_per_step=iters_per_step)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, t0=t0)
+    torch.cuda.synchronize(dev)
+    srv.t_start = t0
+    be.close()
+    return srv, res
+
+
+def _requests(arrivals, keys, cache, pinned, iters, scale_rate=1.0):
+    from paper_1403_0240_gb300.serve import Request
+    out = []
+    for i, (a, k) in enumerate(zip(arrivals, keys)):
+        img_h, lab_h, nl = pinned[k]
+        out.append(Request(i, a.t * scale_rate, img_h, lab_h, iters, _served_params(cache[k]), nlabels=nl))
+    return out
+
+
+def _oracle_stream_sample(arrivals, keys, cache, seconds, iters_each=5):
+    """The oracle, single-threaded, on the first iterations of the stream's jobs in arrival
+    order (iters_each per job) until `seconds` have passed; returns (particle-iterations/s,
+    seconds, [(key, seconds of that job)])."""
+    import oracle
+    total, parts, sample = 0.0, 0, []
+    for k in keys:
+        if total >= seconds:
+            break
+        w = cache[k]
+        p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius)
+        run = oracle.Run(p, w.image, w.labels0)
+        t0 = time.perf_counter()
+        for _ in range(iters_each):
+            s, _ = run.step()
+            parts += s["n_particles"]
+        dt = time.perf_counter() - t0
+        total += dt
+        sample.append((k, dt))
+    return parts / total, total, sample
+
+
+def _oracle_worker(keys, iters, iters_each, barrier, out):
+    """One host core: set up the oracle runs of its jobs, wait for the others, run them."""
+    import oracle
+    from paper_1403_0240_gb300 import synth
+    runs = []
+    for k in keys:
+        w = synth.served_job(k, iters)
+        p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius)
+        runs.append(oracle.Run(p, w.image, w.labels0))
+    barrier.wait()
+    parts = 0
+    for r in runs:
+        for _ in range(iters_each):
+            s, _ = r.step()
+            parts += s["n_particles"]
+    out.put(parts)
+
+
+def _oracle_all_cores(sample, iters, iters_each):
+    """The same sample with one single-threaded oracle process per host core: jobs assigned
+    longest first to the least loaded core (by their single-core times), set up before the
+    clock starts; returns (particle-iterations/s, processes, seconds)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    cores = max(1, min(len(os.sched_getaffinity(0)), len(sample)))
+    load = [0.0] * cores
+    share = [[] for _ in range(cores)]
+    for k, dt in sorted(sample, key=lambda x: -x[1]):
+        c = load.index(min(load))
+        share[c].append(k)
+        load[c] += dt
+    barrier = ctx.Barrier(cores + 1)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(share[c], iters, iters_each, barrier, out)) for c in range(cores)]
+    for pr in procs:
+        pr.start()
+    barrier.wait()
+    t0 = time.perf_counter()
+    parts = sum(out.get() for _ in procs)
+    dt = time.perf_counter() - t0
+    for pr in procs:
+        pr.join()
+    return parts / dt, cores, dt
+
+
+def run_served(args, world, rank, local, pg):
+    """Served workload: Poisson arrivals (200 jobs/s; 80% 2D of sides 128-1024, half piecewise
+    constant disks and half piecewise smooth ellipses, 20% 3D ellipsoid volumes of sides
+    64-256; 100 iterations each) through the continuous-batching server, against the same
+    stream run one job at a time."""
+    import torch
+
+    from paper_1403_0240_gb300 import seg
+
+    arrivals, keys, cache = _served_jobs(args, rank)     # worker processes before any CUDA work
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pinned = {}
+    for k, w in cache.items():      # request payloads sit in pinned host memory, as a server's would
+        pinned[k] = (torch.from_numpy(w.image).pin_memory(), torch.from_numpy(w.labels0).pin_memory(),
+                     int(w.labels0.max()) + 1)
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(0.6 * free)
+    iters = args.job_iters
+
+    # warm-up: graph capture and first launches on one job of every kind, then one of each
+    # distinct pooled job through the server (untimed)
+    warm_keys = []
+    for kind in ("pc2d", "ps2d", "pc3d"):
+        ks = [k for k in cache if k[0] == kind]
+        if ks:
+            warm_keys.append(min(ks, key=lambda k: k[1]))
+    from paper_1403_0240_gb300.serve import Request
+    warm = [Request(i, 0.0, pinned[k][0], pinned[k][1], 3, _served_params(cache[k]), pinned[k][2])
+            for i, k in enumerate(warm_keys)]
+    _serve_stream(warm, dev, budget, args.iters_per_step)
+
+    # the served stream (timed): per-step device time from CUDA events on the batch stream
+    reqs = _requests(arrivals, keys, cache, pinned, iters)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(pg)
+    launches0 = seg.kernel_launches()
+    srv, res = _serve_stream(reqs, dev, budget, args.iters_per_step)
+    launches_stream = seg.kernel_launches() - launches0
+    clocks = sampler.stop() if sampler else None
+    log = srv.log
+    # the timed window: K server steps from the first step, at or after the W-th, that found
+    # jobs waiting in the queue (the server saturated); earlier steps are the ramp-up
+    s0 = next((i for i, e in enumerate(log) if i >= args.warmup and e["queued"] > 0), min(args.warmup, len(log) - 1))
+    win = log[s0:s0 + args.steps]
+    win_ms = sum(e["device_ms"] for e in win)
+    win_parts = sum(e["particles"] for e in win)
+    win_wall = win[-1]["t1"] - win[0]["t0"]
+    value, _, t_max = aggregate(pg, float(win_parts), win_ms / 1000.0)
+    # kernels launched inside the window: each step's graph replays plus the set-up of the jobs
+    # admitted meanwhile (counted by the library)
+    win_launches = sum(e["launches"] for e in win)
+    t_first = min(r.arrival for r in res)
+    makespan = max(r.completed for r in res) - t_first
+    stream_parts = sum(r.particles for r in res)
+    served_lat = np.array([r.latency for r in res])
+
+    # the same stream, one job at a time (real run, real time)
+    plain, plain_makespan = _plain_stream(_requests(arrivals, keys, cache, pinned, iters), dev)
+    plain_parts = sum(x["particles"] for x in plain)
+    plain_busy = sum(x["service"] for x in plain)
+    plain_lat = np.array([x["latency"] for x in plain])
+
+    # the arrival rate the server sustains: its throughput under overload over the mean job
+    # size; then a shorter stream at 80% of that rate, whose latencies must stay bounded
+    capacity = stream_parts / makespan
+    mean_job = stream_parts / len(res)
+    rate_star = capacity / mean_job
+    n_sus = min(len(reqs), args.sustain_jobs)
+    sus_reqs = _requests(arrivals[:n_sus], keys[:n_sus], cache, pinned, iters,
+                         scale_rate=args.rate / (0.8 * rate_star))
+    srv2, res2 = _serve_stream(sus_reqs, dev, budget, args.iters_per_step)
+    sus_lat = np.array([r.latency for r in res2])
+    sus_first = min(r.arrival for r in res2)
+    sus_span = max(r.arrival for r in res2) - sus_first
+
+    # stage breakdown of a batch of the stream's first jobs (per-stage events inside the graph)
+    prof_jobs = [cache[k] for k in keys[:args.profile_jobs]]
+    ctxs = [seg.Context(pinned[k][0], pinned[k][1], **_served_params(cache[k])) for k in keys[:args.profile_jobs]]
+    b = seg.Batch(stream=torch.cuda.current_stream(dev))
+    for c in ctxs:
+        b.add(c)
+    b.step(2)
+    b.profile(True)
+    b.step(2)
+    stage_ms = {k: 0.0 for k in STAGES}
+    stage_parts, n_prof = 0.0, 5
+    for _ in range(n_prof):
+        sts = b.step(1)
+        st_ms = b.stage_times()
+        for k in STAGES:
+            stage_ms[k] += st_ms[k] / n_prof
+        stage_parts += sum(x["n_particles"] for x in sts) / n_prof
+    b.close()
+    for c in ctxs:
+        c.close()
+
     if rank != 0:
         return
-    lat = np.array(lat)
-    line = {"metric": METRIC, "value": parts / t_served, "unit": UNIT, "n_gpus": world, "steps": len(res),
-            "warmup": 4, "ms_per_step": 1000 * t_served / max(1, srv.steps), "higher_is_better": True,
+    dom = max(stage_ms, key=stage_ms.get)
+    per_p, _ = ALG_BYTES[dom]
+    alg_bytes = per_p * stage_parts
+    peak, peak_kind = read_peaks()
+    achieved = alg_bytes / (stage_ms[dom] / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_from_profile(dom, "served", stage_parts), "kernel": dom, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": stage_ms[dom],
+                "measured_on": f"a batch of the stream's first {len(prof_jobs)} jobs, per-stage CUDA events"}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v1, secs, sample = _oracle_stream_sample(arrivals, keys, cache, args.cpu_seconds)
+        njobs = len(sample)
+        vN, cores, secsN = _oracle_all_cores(sample, iters, 5)
+        cpu = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"iterations 0-4 of the stream's first {njobs} jobs in arrival order ({secs:.1f} s), "
+                         "single-threaded FP64 C oracle",
+               "all_cores": {"value": vN, "cores": cores, "seconds": secsN,
+                             "sample": "the same jobs and iterations, one single-threaded oracle process per "
+                                       "host core (os.sched_getaffinity), jobs set up before the clock"}}
+    in_bytes = sum(r.image.numel() * r.image.element_size() + r.labels0.numel() * 4 for r in reqs)
+    out_bytes = sum(r.labels0.numel() * 4 for r in reqs)
+    n_steps = max(1, srv.steps)
+    e2e = {"value": stream_parts / makespan, "unit": UNIT, "h2d_bytes_per_step": int(in_bytes / n_steps),
+           "d2h_bytes_per_step": int(out_bytes / n_steps) + 200 * int(np.mean([e["members"] for e in log])),
+           "what": "the whole served stream: request payloads from pinned host memory, set-up, all "
+                   "iterations, labels back to the host; first arrival to last completion"}
+    by_kind = {}
+    for r, k in zip(sorted(res, key=lambda r: r.job_id), keys):
+        d = by_kind.setdefault(k[0], {"jobs": 0, "particle_iterations": 0})
+        d["jobs"] += 1
+        d["particle_iterations"] += r.particles
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(win),
+            "warmup": s0, "ms_per_step": win_ms / len(win), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "served", "jobs": len(res), "arrival_rate_per_s": 200,
-                       "description": "Poisson arrivals, 80% 2D (half piecewise constant disks, half piecewise "
-                                      "smooth ellipses, sides 128-1024), 20% 3D ellipsoids (sides 64-256); "
-                                      f"{args.job_iters} iterations per job; images pooled by size bucket",
-                       "budget_bytes": budget, "served_p50_s": served["p50_s"], "served_p99_s": served["p99_s"],
-                       "served_makespan_s": t_served, "server_steps": srv.steps,
-                       "server_host_s": {k: round(v, 3) if isinstance(v, float) else v for k, v in srv.timing.items()},
-                       "plain_value": parts_plain / busy, "plain_makespan_s": done_t,
-                       "plain_by_kind": {k: {"jobs": v[0], "busy_s": round(v[1], 3), "particle_iterations": v[2]}
-                                         for k, v in by_kind.items()},
-                       "plain_p50_s": float(np.percentile(lat, 50)), "plain_p99_s": float(np.percentile(lat, 99)),
-                       "served_over_plain": (parts / t_served) / (parts_plain / busy)}}
+            "config": {"workload": "served", "jobs": len(res), "arrival_rate_per_s": args.rate,
+                       "description": "Poisson arrivals, 80% 2D (half piecewise-constant disks, half piecewise-"
+                                      "smooth ellipses, sides 128-1024), 20% 3D uint16 ellipsoids (sides 64-256); "
+                                      f"{iters} iterations per job; images pooled by size bucket",
+                       "step": "one server step: up to {0} iterations of every resident job, one graph replay "
+                               "per iteration for all of them".format(args.iters_per_step),
+                       "timed_window": f"server steps {s0}..{s0 + len(win) - 1} of {len(log)} (the first step "
+                                       f"at or after step {args.warmup} with jobs queued), CUDA events on the "
+                                       "batch stream; value = their particle-iterations / their device time",
+                       "window_wall_value": win_parts / win_wall,
+                       "l2": "not flushed: every step walks all resident jobs (the working set exceeds L2)",
+                       "served_value": stream_parts / makespan, "served_makespan_s": makespan,
+                       "served_p50_s": float(np.percentile(served_lat, 50)),
+                       "served_p99_s": float(np.percentile(served_lat, 99)),
+                       "plain_value": plain_parts / plain_makespan, "plain_makespan_s": plain_makespan,
+                       "plain_busy_value": plain_parts / plain_busy,
+                       "plain_p50_s": float(np.percentile(plain_lat, 50)),
+                       "plain_p99_s": float(np.percentile(plain_lat, 99)),
+                       "served_over_plain": (stream_parts / makespan) / (plain_parts / plain_makespan),
+                       "plain": "the same arrivals one job at a time in real time (set-up from host buffers, "
+                                "all iterations, labels back), first come first served",
+                       "offered_particle_iterations_per_s": stream_parts / max(1e-9, arrivals[-1].t - arrivals[0].t),
+                       "sustainable_rate_jobs_per_s": rate_star,
+                       "at_80pct_of_sustainable": {"rate_jobs_per_s": 0.8 * rate_star, "jobs": len(res2),
+                                                   "p50_s": float(np.percentile(sus_lat, 50)),
+                                                   "p99_s": float(np.percentile(sus_lat, 99)),
+                                                   "arrival_span_s": sus_span,
+                                                   "makespan_s": max(r.completed for r in res2) - sus_first},
+                       "budget_bytes": budget, "server_steps": len(log),
+                       "by_kind": by_kind,
+                       "stages_ms": {k: round(v, 5) for k, v in stage_ms.items()},
+                       "stage_particles": stage_parts},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": win_launches, "gpu_launches_stream": launches_stream,
+            "clocks": clocks, "wall_s": makespan}
     print(json.dumps(line), flush=True)
 
 
@@ -645,22 +862,39 @@ def run_convergence(args, world, rank, local, pg):
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the oracle, timed on this host's cores, on the same workload."""
+    """Reference arm: the oracle, timed on this host's cores, on the same workload. For the
+    served workload a step is one oracle iteration of a stream job: iterations 0-4 of each job
+    in arrival order (W warm-up steps, then K timed)."""
     if rank != 0:
         return
-    name = args.workload
-    make, desc = workloads()[name]
-    w = make(0)
     import oracle
-    p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius, psf=w.psf,
-                           topology=topology_code(args.topology), curv_radius=args.curv_radius)
-    run = oracle.Run(p, w.image, w.labels0)
-    for _ in range(args.warmup):
-        run.step()
+    name = args.workload
+    if name == "served":
+        from paper_1403_0240_gb300 import synth
+        arrivals = synth.arrival_stream(args.jobs, rate=args.rate, seed=42)
+        keys = [synth.served_job_key(a) for a in arrivals]
+        n_jobs = (args.warmup + args.steps + 4) // 5
+        runs = []
+        for k in keys[:n_jobs]:
+            w = synth.served_job(k, args.job_iters)
+            p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius)
+            runs.append(oracle.Run(p, w.image, w.labels0))
+        seq = [runs[i // 5] for i in range(args.warmup + args.steps)]
+        desc = (f"the served stream's first {n_jobs} jobs in arrival order, iterations 0-4 of each, one oracle "
+                "iteration per step")
+    else:
+        make, desc = workloads()[name]
+        w = make(0)
+        p = oracle.make_params(w.image, w.labels0, w.model, w.connectivity, w.lam, w.cutoff, w.ps_radius, psf=w.psf,
+                               topology=topology_code(args.topology), curv_radius=args.curv_radius)
+        run = oracle.Run(p, w.image, w.labels0)
+        seq = [run] * (args.warmup + args.steps)
+    for r in seq[:args.warmup]:
+        r.step()
     parts, times = 0, []
-    for _ in range(args.steps):
+    for r in seq[args.warmup:]:
         t0 = time.perf_counter()
-        s, _ = run.step()
+        s, _ = r.step()
         times.append(time.perf_counter() - t0)
         parts += s["n_particles"]
     total = sum(times)
@@ -670,7 +904,7 @@ def run_reference(args, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": name, "description": desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"iterations {args.warmup}..{args.warmup + args.steps - 1} of one job, "
+                             "sample": f"steps {args.warmup}..{args.warmup + args.steps - 1} ({desc}), "
                                        "single-threaded FP64 C oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -881,12 +1115,17 @@ def run_ours(args, world, rank, local, pg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: served 40, per-image 1000)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default: served 5, per-image 20)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ellipses1024", choices=sorted(list(workloads().keys()) + ["batch512", "served", "convergence", "precision"]))
+    ap.add_argument("--workload", default="served", choices=sorted(list(workloads().keys()) + ["batch512", "served", "convergence", "precision"]))
     ap.add_argument("--images", type=int, default=512, help="batch512: images in the batch")
-    ap.add_argument("--jobs", type=int, default=2000, help="served: jobs in the arrival stream")
+    ap.add_argument("--jobs", type=int, default=600, help="served: jobs in the arrival stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
+    ap.add_argument("--sustain-jobs", type=int, default=150,
+                    help="served: jobs of the stream replayed at 80%% of the sustainable rate")
+    ap.add_argument("--profile-jobs", type=int, default=48,
+                    help="served: jobs of the batch whose stages are timed for the roofline")
     ap.add_argument("--job-iters", type=int, default=100, help="served: iterations per job")
     ap.add_argument("--iters-per-step", type=int, default=4, help="served: most iterations per batch step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -907,6 +1146,10 @@ def main():
     ap.add_argument("--iter-log", default="", help="write every warm-up and timed iteration's status here "
                     "(JSON lines), to relate profiler launches to their particle counts")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 40 if args.workload == "served" else 1000
+    if args.warmup is None:
+        args.warmup = 5 if args.workload == "served" else 20
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local, pg = dist_setup() if args.impl == "ours" else (

@@ -291,6 +291,12 @@ int seg_batch_size(seg_batch* b);
  * receives one seg_status per context in the order they were added. */
 int seg_batch_step(seg_batch* b, int32_t iters, seg_status* statuses, int32_t n_statuses);
 int seg_batch_step_async(seg_batch* b, int32_t iters);
+/* Per-stage CUDA events of the batch's iteration, as seg_profile / seg_stage_times for one
+ * context (the events serialise the stage launches, so profiled steps run slower): ms
+ * (n >= 10) receives the milliseconds each of the ten stages took in the batch's most recent
+ * iteration, over all members together. */
+int seg_batch_profile(seg_batch* b, int32_t on);
+int seg_batch_stage_times(seg_batch* b, float* ms, int32_t n);
 int seg_batch_poll(seg_batch* b, seg_status* statuses, int32_t n_statuses);
 void seg_batch_destroy(seg_batch* b);
 
@@ -333,6 +339,11 @@ int seg_debug_simple(int32_t ndim, const uint32_t* masks, int32_t n, uint8_t* ou
  * SEG_INJECT_NONE clears the injection. No GPU fault is raised. */
 enum { SEG_INJECT_NONE = 0, SEG_INJECT_WITHHELD_COPY = 1 };
 int seg_debug_inject(seg_ctx* c, int32_t what);
+
+/* Kernels libseg has launched in this process so far (all devices and threads); each replay
+ * of an iteration graph counts every kernel of the graph. For measuring how many kernels a
+ * piece of work takes: read it before and after. */
+int seg_kernel_launches(uint64_t* out);
 
 const char* seg_strerror(int code);
 /* Text of the last CUDA error this thread saw inside libseg ("" if none). */

@@ -116,6 +116,7 @@ cudaError_t launch_deconv(const Job* jobs, int j, const Job& h, int sms, cudaStr
 cudaError_t launch_psf_norms(const Job* job, const Job& h, cudaStream_t s)
 {
     const int total = h.W + h.H + (h.ndim == 3 ? h.D : 0);
+    count_launch();
     k_psf_norms<<<(total + kBlock - 1) / kBlock, kBlock, 0, s>>>(job);
     return cudaGetLastError();
 }

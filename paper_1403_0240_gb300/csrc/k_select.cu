@@ -43,7 +43,9 @@ cudaError_t simple_tables_init()
     cudaError_t e;
     if ((e = cudaMalloc(&t2, 8 * sizeof(unsigned))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&t3, (1u << 21) * sizeof(unsigned))) != cudaSuccess) return e;
+    count_launch();
     k_simple_table<<<1, 32>>>(t2, 0, 8);
+    count_launch();
     k_simple_table<<<(1u << 21) / 256, 256>>>(t3, 1, 1u << 21);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
@@ -163,6 +165,7 @@ __global__ void k_debug_simple(const unsigned* masks, int ndim, int n, unsigned 
 cudaError_t launch_debug_simple(const unsigned* masks, int ndim, int n, unsigned char* out, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
+    count_launch();
     k_debug_simple<<<(n + 255) / 256, 256, 0, s>>>(masks, ndim, n, out);
     return cudaGetLastError();
 }
@@ -692,6 +695,7 @@ __global__ void k_gather_counters(const Job* jobs, int njobs, Counters* out)
 cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cudaStream_t s)
 {
     if (njobs <= 0) return cudaSuccess;
+    count_launch();
     k_gather_counters<<<(njobs + 127) / 128, 128, 0, s>>>(jobs, njobs, out);
     return cudaGetLastError();
 }
@@ -1057,6 +1061,7 @@ cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream
     int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
     if (grid < 1) grid = 1;
     if (after_split) return launch_stage(k_stats_init, grid, 256, 0, s, jobs, j, true);
+    count_launch();
     k_stats_init<<<grid, 256, 0, s>>>(jobs, j, false);
     return cudaGetLastError();
 }
@@ -1139,12 +1144,14 @@ cudaError_t launch_scan_inputs(const void* I, int dtype, const int* L, int ndim,
     long long want = (npix + 255) / 256;
     int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
     if (grid < 1) grid = 1;
+    count_launch();
     k_scan_inputs<<<grid, 256, 0, s>>>(I, dtype, L, ndim, D, H, W, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s)
 {
+    count_launch();
     k_stats_finalize<<<64, 128, 0, s>>>(jobs, njobs);
     return cudaGetLastError();
 }
@@ -1610,6 +1617,7 @@ cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, in
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    count_launch();
     return cudaLaunchKernelEx(&cfg, k_rounds, jobs, njobs, bc);
 }
 

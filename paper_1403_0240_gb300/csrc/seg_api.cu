@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,6 +21,17 @@ using namespace segk;
 
 namespace segk {
 thread_local bool g_pdl = false;
+
+// launches made while a stepper captures its graph count towards the graph, not the process
+thread_local bool g_count_into_graph = false;
+thread_local unsigned long long g_graph_kernels = 0;
+std::atomic<unsigned long long> g_kernel_launches{0};
+
+void count_launch()
+{
+    if (g_count_into_graph) g_graph_kernels++;
+    else g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+}
 }
 
 namespace {
@@ -203,6 +215,7 @@ struct Stepper {
     bool any_curv = false;         // a member uses the curvature regulariser (adds its ball counts)
     bool any_fuse = false;         // a member may fuse regions (adds the fusion passes)
     bool profile = false;
+    unsigned long long graph_kernels = 0;   // kernels in one replay of the graph
     cudaEvent_t ev[11]{};
     cudaStream_t work = nullptr;   // library stream: graphs are captured and launched here
     cudaEvent_t fence_in = nullptr, fence_out = nullptr;
@@ -841,7 +854,11 @@ int stepper_run(Stepper& s, int iters)
         cudaError_t e = cudaStreamBeginCapture(s.work, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             g_capturing = true;
+            g_count_into_graph = true;
+            g_graph_kernels = 0;
             cudaError_t e2 = stepper_enqueue(s);
+            g_count_into_graph = false;
+            s.graph_kernels = g_graph_kernels;
             g_capturing = false;
             cudaGraph_t g = nullptr;
             e = cudaStreamEndCapture(s.work, &g);
@@ -866,8 +883,12 @@ int stepper_run(Stepper& s, int iters)
     CK(cudaEventRecord(s.fence_in, s.stream));
     CK(cudaStreamWaitEvent(s.work, s.fence_in, 0));
     for (int i = 0; i < iters; i++) {
-        if (s.use_graph) CK(cudaGraphLaunch(s.exec, s.work));
-        else CK(stepper_enqueue(s));
+        if (s.use_graph) {
+            CK(cudaGraphLaunch(s.exec, s.work));
+            g_kernel_launches.fetch_add(s.graph_kernels, std::memory_order_relaxed);
+        } else {
+            CK(stepper_enqueue(s));
+        }
     }
     CK(cudaEventRecord(s.fence_out, s.work));
     CK(cudaStreamWaitEvent(s.stream, s.fence_out, 0));
@@ -1405,6 +1426,29 @@ int seg_batch_remove(seg_batch* b, seg_ctx* c)
 }
 
 int seg_batch_size(seg_batch* b) { return b ? (int)b->st.members.size() : 0; }
+
+int seg_batch_profile(seg_batch* b, int32_t on)
+{
+    if (!b) return SEG_EINVAL;
+    int rc = ensure_device(b->st.device);
+    if (rc) return rc;
+    return stepper_set_profile(b->st, on != 0);
+}
+
+int seg_batch_stage_times(seg_batch* b, float* ms, int32_t n)
+{
+    if (!b) return SEG_EINVAL;
+    int rc = ensure_device(b->st.device);
+    if (rc) return rc;
+    return stepper_stage_times(b->st, ms, n);
+}
+
+int seg_kernel_launches(uint64_t* out)
+{
+    if (!out) return SEG_EINVAL;
+    *out = (uint64_t)g_kernel_launches.load(std::memory_order_relaxed);
+    return SEG_OK;
+}
 
 int seg_batch_step(seg_batch* b, int32_t iters, seg_status* statuses, int32_t n_statuses)
 {

@@ -393,6 +393,11 @@ __device__ __forceinline__ void pdl_enter()
 // (the stepper sets it while enqueueing an iteration without per-stage events).
 extern thread_local bool g_pdl;
 
+// Kernel launch accounting (seg_kernel_launches): every launch site calls count_launch().
+// A launch made while a graph is being captured counts towards that graph; each replay of
+// the graph then counts its kernels.
+void count_launch();
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_stage(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                                 Args... args)
@@ -407,6 +412,7 @@ inline cudaError_t launch_stage(void (*k)(KArgs...), dim3 grid, dim3 block, size
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = g_pdl ? 1 : 0;
+    count_launch();
     return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 

@@ -127,6 +127,7 @@ extern "C" int seg_region_stats_noalloc(int32_t dtype, int64_t npix, const void*
     int hbad = 0;
     cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), stream);
     if (e == cudaSuccess) {
+        count_launch();
         k_check_labels<<<256, 256, 0, stream>>>(labels, npix, M, bad);
         e = cudaGetLastError();
     }

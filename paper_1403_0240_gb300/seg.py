@@ -89,6 +89,9 @@ SIGNATURES = [
     ("seg_batch_size", C.c_int, [_V]),
     ("seg_batch_step", C.c_int, [_V, C.c_int32, _V, C.c_int32]),
     ("seg_batch_step_async", C.c_int, [_V, C.c_int32]),
+    ("seg_batch_profile", C.c_int, [_V, C.c_int32]),
+    ("seg_batch_stage_times", C.c_int, [_V, _P(C.c_float), C.c_int32]),
+    ("seg_kernel_launches", C.c_int, [_P(C.c_uint64)]),
     ("seg_batch_poll", C.c_int, [_V, _V, C.c_int32]),
     ("seg_batch_destroy", None, [_V]),
     ("seg_region_stats_noalloc", C.c_int, [C.c_int32, C.c_int64, _V, _V, C.c_int32, _V, _V, _V, _V]),
@@ -394,6 +397,14 @@ class Batch:
         _check(lib().seg_batch_poll(self._h, C.cast(st, C.c_void_p), n), "seg_batch_poll")
         return [st[i].as_dict() for i in range(n)]
 
+    def profile(self, on: bool = True):
+        _check(lib().seg_batch_profile(self._h, int(bool(on))), "seg_batch_profile")
+
+    def stage_times(self) -> dict:
+        ms = (C.c_float * len(Context.STAGES))()
+        _check(lib().seg_batch_stage_times(self._h, ms, len(Context.STAGES)), "seg_batch_stage_times")
+        return {k: float(ms[i]) for i, k in enumerate(Context.STAGES)}
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             lib().seg_batch_destroy(self._h)
@@ -405,6 +416,13 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def kernel_launches() -> int:
+    """Kernels libseg has launched in this process (graph replays count each of their kernels)."""
+    out = C.c_uint64(0)
+    _check(lib().seg_kernel_launches(C.byref(out)), "seg_kernel_launches")
+    return int(out.value)
 
 
 def debug_simple(ndim: int, masks) -> np.ndarray:

@@ -51,13 +51,21 @@ class SegBackend:
     """libseg on the current CUDA device: contexts in one batch. New contexts are set up on
     their own stream (init_stream) so that this overlaps the batch step in flight."""
 
-    def __init__(self, stream=None, init_stream=None, keep_labels: bool = True):
+    def __init__(self, stream=None, init_stream=None, keep_labels: bool = True, time_steps: bool = False):
         from . import seg
         self.seg = seg
         self.stream = stream
         self.init_stream = init_stream
         self.batch = seg.Batch(stream=stream)
         self.keep_labels = keep_labels
+        # CUDA events around every batch step on the batch stream (device time of the step)
+        self.time_steps = time_steps and stream is not None
+        self._ev = None
+        self.last_step_ms = None
+
+    def launches(self) -> int:
+        """Kernels libseg has launched in this process so far."""
+        return self.seg.kernel_launches()
 
     def estimate(self, req: Request) -> int:
         if req.nlabels is None:
@@ -75,10 +83,20 @@ class SegBackend:
         self.batch.remove(ctx)
 
     def step_async(self, iters: int):
+        if self.time_steps:
+            import torch
+            self._ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            self._ev[0].record(self.stream)
         self.batch.step_async(iters)
+        if self._ev is not None:
+            self._ev[1].record(self.stream)
 
     def poll(self) -> list[dict]:
-        return self.batch.poll()
+        out = self.batch.poll()
+        if self._ev is not None:
+            self.last_step_ms = self._ev[0].elapsed_time(self._ev[1])
+            self._ev = None
+        return out
 
     def finish(self, ctx):
         labels = ctx.labels() if self.keep_labels else None
@@ -115,6 +133,10 @@ class Server:
         # host seconds spent per phase of step(): setting up admitted jobs, waiting for the batch
         # step to finish, retiring finished jobs (label read-back), adding joined jobs
         self.timing = {"admit_s": 0.0, "wait_s": 0.0, "retire_s": 0.0, "join_s": 0.0, "member_steps": 0}
+        # one entry per batch step: start and end (server clock), iterations, members, jobs
+        # waiting in the queue when it started, particle-iterations it processed, and the
+        # device time of the step when the backend measures it
+        self.log: list[dict] = []
 
     def submit(self, req: Request):
         self.queue.append(req)
@@ -146,9 +168,12 @@ class Server:
         the admitted ones join; returns the iterations run (0 when nothing was resident)."""
         members = list(self.order)
         k = self._iters_for(members)
+        queued = len(self.queue)
+        count = getattr(self.backend, "launches", None)
+        l0 = count() if count else None
+        t0 = self.clock()
         if k:
             self.backend.step_async(k)
-        t0 = self.clock()
         joined = self._admit()                    # host work overlaps the step in flight
         t1 = self.clock()
         statuses = self.backend.poll() if k else []
@@ -156,9 +181,11 @@ class Server:
         self.timing["admit_s"] += t1 - t0
         self.timing["wait_s"] += t2 - t1
         self.timing["member_steps"] += len(members)
+        step_particles = 0
         for jid, st in zip(members, statuses):
             r = self.resident[jid]
             r["done"] += k
+            step_particles += int(st["particles_total"]) - r["particles"]
             r["particles"] = int(st["particles_total"])
             r["converged"] = bool(st["converged"])
         now = self.clock()
@@ -181,6 +208,10 @@ class Server:
         self.timing["join_s"] += t4 - t3
         if k:
             self.steps += 1
+            self.log.append({"t0": t0, "t1": t4, "iters": k, "members": len(members), "queued": queued,
+                             "particles": step_particles,
+                             "device_ms": getattr(self.backend, "last_step_ms", None),
+                             "launches": (count() - l0) if count else None})
         return k
 
     def idle(self) -> bool:
