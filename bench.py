@@ -625,9 +625,13 @@ def run_served(args, world, rank, local, pg):
     launches_stream = seg.kernel_launches() - launches0
     clocks = sampler.stop() if sampler else None
     log = srv.log
-    # the timed window: K server steps from the first step, at or after the W-th, that found
-    # jobs waiting in the queue (the server saturated); earlier steps are the ramp-up
-    s0 = next((i for i, e in enumerate(log) if i >= args.warmup and e["queued"] > 0), min(args.warmup, len(log) - 1))
+    # the timed window: K server steps from the first step, at or after the W-th, that starts
+    # once the whole stream has arrived (every remaining job is resident or queued: the server
+    # works on its full backlog); earlier steps are the ramp-up. When fewer than K steps remain
+    # the window ends with the last step.
+    last_arrival = max(r.arrival for r in res)
+    s0 = next((i for i, e in enumerate(log) if i >= args.warmup and e["t0"] >= last_arrival), len(log))
+    s0 = max(min(args.warmup, len(log) - 1), min(s0, len(log) - args.steps))
     win = log[s0:s0 + args.steps]
     win_ms = sum(e["device_ms"] for e in win)
     win_parts = sum(e["particles"] for e in win)
@@ -725,9 +729,11 @@ def run_served(args, world, rank, local, pg):
                                       f"{iters} iterations per job; images pooled by size bucket",
                        "step": "one server step: up to {0} iterations of every resident job, one graph replay "
                                "per iteration for all of them".format(args.iters_per_step),
-                       "timed_window": f"server steps {s0}..{s0 + len(win) - 1} of {len(log)} (the first step "
-                                       f"at or after step {args.warmup} with jobs queued), CUDA events on the "
-                                       "batch stream; value = their particle-iterations / their device time",
+                       "timed_window": f"server steps {s0}..{s0 + len(win) - 1} of {len(log)} (from the first step "
+                                       f"at or after step {args.warmup} that starts after the last arrival), CUDA "
+                                       "events on the batch stream; value = their particle-iterations / their "
+                                       "device time",
+                       "window_mean_jobs": float(np.mean([e["members"] for e in win])),
                        "window_wall_value": win_parts / win_wall,
                        "l2": "not flushed: every step walks all resident jobs (the working set exceeds L2)",
                        "served_value": stream_parts / makespan, "served_makespan_s": makespan,

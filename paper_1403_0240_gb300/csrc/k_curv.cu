@@ -6,8 +6,9 @@
 // counts, with w = lambda 3 / (2 rho^3) in 2D and lambda 4 / (pi rho^4) in 3D (host side).
 //
 // One warp per particle, the lanes over the ball offsets (consecutive dx of a row in
-// consecutive lanes, so the label loads of a row coalesce). The FP32 energy difference and its
-// bound are updated in place; the FP64 recompute evaluates the same count (energy64).
+// consecutive lanes, so the label loads of a row coalesce). The energy difference is completed in
+// FP64 from the data term extraction left and stored as a float pair; the FP64 recompute
+// evaluates the same count (energy64).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,8 +21,6 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kStaged = 2048;                 // offsets kept in shared memory
-constexpr float kU = 1.1920929e-7f;           // 2^-23: twice the float32 unit roundoff
-constexpr float kFp64Margin = 1e-12f;         // covers the FP64 evaluation's own rounding
 
 __global__ void __launch_bounds__(kBlock) k_curvature(const Job* jobs, int j)
 {
@@ -51,14 +50,8 @@ __global__ void __launch_bounds__(kBlock) k_curvature(const Job* jobs, int j)
             bal += (int)(m == l) - (int)(m == c);
         }
         bal = __reduce_add_sync(0xffffffffu, bal);
-        if (lane == 0) {
-            // dE approximates the FP64 data term within eE; r = fl(w32 * bal) is within
-            // 2^-24 |w bal| of fl(w bal) twice over, and the sum adds one rounding
-            const float r = J.curv_w32 * (float)bal;
-            const float dE = J.p_dE[p] + r;
-            J.p_eE[p] = (J.p_eE[p] + 2.0001f * kU * fabsf(r) + kU * fabsf(dE) + kFp64Margin * fabsf(r)) * 1.001f;
-            J.p_dE[p] = dE;
-        }
+        // the FP64 data term from extraction plus w times the count, in the order of the definition
+        if (lane == 0) store_dE(J, p, __dadd_rn(J.p_dE64[p], __dmul_rn(J.curv_w64, (double)bal)));
     }
 }
 

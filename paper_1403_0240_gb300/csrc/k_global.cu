@@ -22,14 +22,6 @@ __device__ __forceinline__ double kernel_eq5_fp64(double r, double E)
     return __dmul_rn(__ddiv_rn(1.0, E), __dadd_rn(1.0, __ddiv_rn(num, 2.0 * eps)));
 }
 
-__device__ __forceinline__ float gamma_f(int n)
-{
-    const float t = (float)n * 5.9604645e-8f;   // n * 2^-24
-    return t / (1.0f - t);
-}
-
-constexpr float kUnit = 1.1920929e-7f;          // 2^-23: twice the float32 unit roundoff
-constexpr float kMargin = 1e-12f;               // the FP64 reference's own rounding
 
 }  // namespace
 
@@ -50,20 +42,22 @@ __global__ void k_global_lut(const Job* jobs, int njobs)
         for (long long d2 = blockIdx.x * (long long)blockDim.x + threadIdx.x; d2 <= J.gd2max;
              d2 += (long long)gridDim.x * blockDim.x) {
             const double K = d2 < lim ? kernel_eq5_fp64(__dsqrt_rn((double)d2), E) : 0.0;
+            const float Kh = __double2float_rn(K);
             J.gK64[d2] = K;
-            J.gK32[d2] = __double2float_rn(K);
+            J.gK32[d2] = Kh;
+            J.gK32l[d2] = __double2float_rn(__dsub_rn(K, (double)Kh));
         }
     }
 }
 
 // One block per tile: the tile's particles against every particle of the job, staged in
-// shared memory kChunk at a time; FP32 sums with the running error bound of the local kernel.
+// shared memory kChunk at a time; compensated sums of exact products as in the local kernel.
 template <int NDIM>
 __global__ void __launch_bounds__(kBlock) k_sobolev_global(Group g)
 {
     pdl_enter();
     __shared__ int s_x[kChunk], s_y[kChunk], s_z[kChunk], s_l[kChunk], s_c[kChunk];
-    __shared__ float s_dE[kChunk], s_eE[kChunk];
+    __shared__ float s_dh[kChunk], s_dl[kChunk];
     __shared__ unsigned s_osc;
     const int tid = threadIdx.x;
     const unsigned t = blockIdx.x;
@@ -86,7 +80,8 @@ __global__ void __launch_bounds__(kBlock) k_sobolev_global(Group g)
         int x = 0, y = 0, z = 0;
         pix_coords(J, J.p_idx[p], x, y, z);
         const int lp = J.p_l[p];
-        float As = 0.f, Bs = 0.f, aA = 0.f, aB = 0.f, eAs = 0.f, eBs = 0.f;
+        DotAcc A, B;
+        float aA = 0.f, aB = 0.f;
         int nA = 0, nB = 0;
         for (unsigned q0 = 0; q0 < np; q0 += kChunk) {
             const unsigned nq = min((unsigned)kChunk, np - q0);
@@ -100,8 +95,8 @@ __global__ void __launch_bounds__(kBlock) k_sobolev_global(Group g)
                 s_z[jj] = qz;
                 s_l[jj] = J.p_l[q];
                 s_c[jj] = J.p_c[q];
-                s_dE[jj] = J.p_dE[q];
-                s_eE[jj] = J.p_eE[q];
+                s_dh[jj] = J.p_dE[q];
+                s_dl[jj] = J.p_dEl[q];
             }
             __syncthreads();
             if (!own) continue;
@@ -111,22 +106,20 @@ __global__ void __launch_bounds__(kBlock) k_sobolev_global(Group g)
                 if (d2 >= lim) continue;
                 const int ql = s_l[jj], qc = s_c[jj];
                 if (ql != lp && qc != lp) continue;
-                const float K = __ldg(J.gK32 + d2);
-                const float w = K * s_dE[jj];
-                if (ql == lp) { As += w; aA += fabsf(w); eAs += K * s_eE[jj]; nA++; }
-                else { Bs += w; aB += fabsf(w); eBs += K * s_eE[jj]; nB++; }
+                const float Kh = __ldg(J.gK32 + d2), Kl = __ldg(J.gK32l + d2);
+                if (ql == lp) { aA += fabsf(A.add(Kh, Kl, s_dh[jj], s_dl[jj])); nA++; }
+                else { aB += fabsf(B.add(Kh, Kl, s_dh[jj], s_dl[jj])); nB++; }
             }
         }
         if (own) {
-            const float A = nA ? As / (float)nA : 0.f;
-            const float B = nB ? Bs / (float)nB : 0.f;
-            const float eA = nA ? ((eAs + (kUnit + gamma_f(nA)) * aA) * 1.0001f / (float)nA + kUnit * fabsf(A)) : 0.f;
-            const float eB = nB ? ((eBs + (kUnit + gamma_f(nB)) * aB) * 1.0001f / (float)nB + kUnit * fabsf(B)) : 0.f;
-            const float gp = A - B;
-            const float margin = kMargin * ((nA ? aA / (float)nA : 0.f) + (nB ? aB / (float)nB : 0.f));
+            float Aq = 0.f, Al = 0.f, Bq = 0.f, Bl = 0.f;
+            if (nA) pair_div(A.s, A.t, nA, Aq, Al);
+            if (nB) pair_div(B.s, B.t, nB, Bq, Bl);
+            const float gp = pair_sub(Aq, Al, Bq, Bl);
             J.p_g[p] = gp;
-            J.p_eg[p] = (eA + eB + kUnit * fabsf(gp) + margin) * 1.001f;
-            osc += (A != 0.f && B != 0.f && ((A > 0.f) == (B > 0.f))) ? 1u : 0u;
+            J.p_eg[p] = pair_bound(gp, nA, nA ? aA / (float)nA : 0.f, nB, nB ? aB / (float)nB : 0.f);
+            const float Af = __fadd_rn(Aq, Al), Bf = __fadd_rn(Bq, Bl);
+            osc += (Af != 0.f && Bf != 0.f && ((Af > 0.f) == (Bf > 0.f))) ? 1u : 0u;
         }
     }
     if (osc) atomicAdd(&s_osc, osc);

@@ -239,44 +239,6 @@ cudaError_t launch_flag(const Group& g, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // FP64 recompute in the order of the definition: every product and sum rounded
 // separately (no fused multiply-add), neighbours in ascending particle key.
-__device__ __forceinline__ double image64(const Job& J, long long i)
-{
-    if (J.dtype == SEG_F32) return (double)((const float*)J.I)[i];
-    return (double)((const unsigned short*)J.I)[i];
-}
-
-// Natural logarithm by the atanh series after reduction to [sqrt(1/2), sqrt(2)):
-// ln x = e ln 2 + 2 (y + y^3/3 + ... + y^23/23), y = (m - 1)/(m + 1), every operation an IEEE
-// double operation in a fixed order (the FP64 reference evaluates the same series the same way).
-__device__ __forceinline__ double log_series(double x)
-{
-    int e = 0;
-    double m = frexp(x, &e);
-    if (m < 0.70710678118654752440) { m = __dmul_rn(2.0, m); e = e - 1; }
-    const double y = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
-    const double y2 = __dmul_rn(y, y);
-    double s = 1.0 / 23.0;
-    s = __dadd_rn(1.0 / 21.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0 / 19.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0 / 17.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0 / 15.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0 / 13.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0 / 11.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0 / 9.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0 / 7.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0 / 5.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0 / 3.0, __dmul_rn(y2, s));
-    s = __dadd_rn(1.0, __dmul_rn(y2, s));
-    return __dadd_rn(__dmul_rn((double)e, 0.69314718055994530942), __dmul_rn(2.0, __dmul_rn(y, s)));
-}
-
-// Poisson negative log-likelihood of v under the (floored) mean mu, the log(v!) term dropped
-__device__ __forceinline__ double poisson_f64(double v, double mu, double floor)
-{
-    const double m = mu > floor ? mu : floor;
-    return __dsub_rn(m, __dmul_rn(v, log_series(m)));
-}
-
 // q: index of the particle (gi, l -> c) in the current particle arrays; its exact ball
 // sums are reused when they were stored (piecewise smooth with exact FP64 ball sums).
 __device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
@@ -288,11 +250,7 @@ __device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
     if (J.model == SEG_PC_DECONV) {
         data = deconv_data64(J, J.dc_G[gi], x, y, z, l, c);   // G stored by extraction
     } else if (J.model == SEG_PC) {
-        double a = __dsub_rn(v, J.mu64[c]);
-        double b = __dsub_rn(v, J.mu64[l]);
-        double t1 = __dmul_rn(J.wp64[c], __dmul_rn(a, a));
-        double t2 = J.st_n[l] > 1 ? __dmul_rn(J.wm64[l], __dmul_rn(b, b)) : 0.0;
-        data = __dsub_rn(t1, t2);
+        data = data_pc64(J, v, l, c);
     } else {
         double sc = 0.0, sl = 0.0;
         long long cc = 0, cl = 0;
@@ -314,14 +272,7 @@ __device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
                 else if (m == l) { sl = __dadd_rn(sl, image64(J, j)); cl++; }
             }
         }
-        if (J.model == SEG_PS_POISSON) {
-            data = __dsub_rn(poisson_f64(v, __ddiv_rn(sc, (double)cc), J.mu_floor64),
-                             poisson_f64(v, __ddiv_rn(sl, (double)cl), J.mu_floor64));
-        } else {
-            double a = __dsub_rn(v, __ddiv_rn(sc, (double)cc));
-            double b = __dsub_rn(v, __ddiv_rn(sl, (double)cl));
-            data = __dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b));
-        }
+        data = data_ps64(J, v, sc, cc, sl, cl);
     }
     if (J.curv) {
         // curvature regulariser: pixels of l minus pixels of c in the ball, weight w
@@ -344,7 +295,7 @@ __device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
         int m = J.L[((long long)zz * J.H + yy) * J.W + xx];
         dP += (int)(m != c) - (int)(m != l);
     }
-    return __dadd_rn(data, __dmul_rn(J.lambda64, (double)dP));
+    return with_length64(J, data, dP);
 }
 
 // ---------------------------------------------------------------------------

@@ -8,14 +8,6 @@
 namespace segk {
 
 constexpr int kBlock = 256;
-constexpr float kU = 1.1920929e-7f;          // 2^-23: twice the float32 unit roundoff
-constexpr float kFp64Margin = 1e-12f;        // covers the FP64 evaluation's own rounding
-
-__device__ __forceinline__ float gamma_n(int n)
-{
-    float t = (float)n * 5.9604645e-8f;      // n * 2^-24
-    return t / (1.0f - t);
-}
 
 struct TileBox {
     int x0, x1, y0, y1, z0, z1;   // pixel box of the tile
@@ -40,107 +32,6 @@ __device__ __forceinline__ TileBox tile_box(const Job& J, unsigned k)
     return b;
 }
 
-
-// --------------------------------------------------------------------------
-// Energy difference of moving a pixel of value v from label l to c (Methods, Eq. 11),
-// piecewise-constant data term: the exact single-pixel change of the sum of squared
-// deviations from the region means, plus lambda * change of unlike neighbour pairs.
-// Returns dE in float and a bound on |dE - dE_fp64|.
-__device__ __forceinline__ void energy_pc(const Job& J, float v, int l, int c, int dP, float& dE, float& eE)
-{
-    // the deviations from the region means in FP64 (exact up to one rounding each),
-    // so that v close to a mean loses no accuracy; everything else in float32
-    float a = __double2float_rn(__dsub_rn((double)v, __ldg(J.mu64 + c)));
-    float b = __double2float_rn(__dsub_rn((double)v, __ldg(J.mu64 + l)));
-    float ea = kU * fabsf(a);
-    float eb = kU * fabsf(b);
-    float aa = a * a, bb = b * b;
-    float eaa = (2.0f * fabsf(a) + ea) * ea + kU * aa;
-    float ebb = (2.0f * fabsf(b) + eb) * eb + kU * bb;
-    float wp = __ldg(J.wp32 + c), wm = __ldg(J.wm32 + l);
-    float t1 = wp * aa, t2 = wm * bb;
-    float et1 = wp * eaa * 1.0001f + kU * t1;
-    float et2 = wm * ebb * 1.0001f + kU * t2;
-    float d = t1 - t2;
-    float lp = J.lambda32 * (float)dP;
-    dE = d + lp;
-    float err = et1 + et2 + kU * (fabsf(d) + fabsf(lp) + fabsf(dE)) + kFp64Margin * (t1 + t2 + fabsf(lp));
-    eE = err * 1.001f;
-}
-
-// Piecewise-smooth data term from local means over the ball of radius R around x,
-// x counted in its own label: (v - mu_c)^2 - (v - mu_l)^2. The ball sums are taken of
-// the shifted values I(y) - v, so a = v - mu_c = -(sum (I - v)) / n_c directly.
-// sc, sl: shifted sums; ac, al: sums of |I(y) - v|.
-__device__ __forceinline__ void energy_ps_finish(const Job& J, float v, int dP, float sc, float ac, int cc,
-                                                 float sl, float al, int cl, float& dE, float& eE)
-{
-    float a = -sc / (float)cc, b = -sl / (float)cl;
-    float ea = gamma_n(cc + 1) * ac / (float)cc + kU * fabsf(a);
-    float eb = gamma_n(cl + 1) * al / (float)cl + kU * fabsf(b);
-    float aa = a * a, bb = b * b;
-    float eaa = (2.0f * fabsf(a) + ea) * ea + kU * aa;
-    float ebb = (2.0f * fabsf(b) + eb) * eb + kU * bb;
-    float d = aa - bb;
-    float lp = J.lambda32 * (float)dP;
-    dE = d + lp;
-    float mac = ac / (float)cc + fabsf(v), mal = al / (float)cl + fabsf(v);
-    float err = eaa + ebb + kU * (fabsf(d) + fabsf(lp) + fabsf(dE)) +
-                kFp64Margin * (aa + bb + fabsf(lp) + mac * mac + mal * mal);
-    eE = err * 1.001f;
-}
-
-// Same with exact fixed-point ball sums: isc = sum over the c-part of the ball of q(I) - q(v)
-// (exact), so a = v - mu_c = -(isc / n_c) * 2^e_min with two float32 roundings.
-// ac, al: sums of |I| over each part (for the FP64 margin only).
-__device__ __forceinline__ void energy_ps_finish_int(const Job& J, float v, int dP, long long isc, int cc,
-                                                     long long isl, int cl, float& dE, float& eE)
-{
-    float a = -((float)isc / (float)cc) * J.unit32;
-    float b = -((float)isl / (float)cl) * J.unit32;
-    float ea = 1.0001f * kU * fabsf(a), eb = 1.0001f * kU * fabsf(b);
-    float aa = a * a, bb = b * b;
-    float eaa = (2.0f * fabsf(a) + ea) * ea + kU * aa;
-    float ebb = (2.0f * fabsf(b) + eb) * eb + kU * bb;
-    float d = aa - bb;
-    float lp = J.lambda32 * (float)dP;
-    dE = d + lp;
-    float mx = J.maxabs + fabsf(v);
-    float err = eaa + ebb + kU * (fabsf(d) + fabsf(lp) + fabsf(dE)) +
-                kFp64Margin * (aa + bb + fabsf(lp) + 2.0f * mx * mx);
-    eE = err * 1.001f;
-}
-
-// Poisson data term f(v, mu) = mu - v ln mu (mean floored), from a float32 mean with error
-// bound emu: value and a bound on its distance to the FP64 value. logf is within 1 ulp of the
-// logarithm of its argument (CUDA maths library accuracy); the mean's error adds emu / mu.
-__device__ __forceinline__ void poisson_f32(const Job& J, float v, float mu, float emu, float& f, float& ef)
-{
-    const float m = fmaxf(mu, J.mu_floor32);
-    const float L = logf(m);
-    const float eL = kU * fabsf(L) + 1.0001f * emu / m + 1e-37f;
-    const float p = v * L;
-    const float ep = fabsf(v) * eL + kU * fabsf(p);
-    f = m - p;
-    ef = emu + ep + kU * fabsf(f);
-}
-
-// Poisson piecewise-smooth energy difference from the local means of the c and l parts of the
-// ball, each with its error bound
-__device__ __forceinline__ void energy_psp_finish(const Job& J, float v, int dP, float muc, float emc, float mul,
-                                                  float eml, float& dE, float& eE)
-{
-    float fc, efc, fl, efl;
-    poisson_f32(J, v, muc, emc, fc, efc);
-    poisson_f32(J, v, mul, eml, fl, efl);
-    const float d = fc - fl;
-    const float lp = J.lambda32 * (float)dP;
-    dE = d + lp;
-    const float mag = fmaxf(muc, J.mu_floor32) + fmaxf(mul, J.mu_floor32) + fabsf(v) * (fabsf(logf(fmaxf(muc, J.mu_floor32))) +
-                      fabsf(logf(fmaxf(mul, J.mu_floor32))) + 1.0f);
-    const float err = efc + efl + kU * (fabsf(d) + fabsf(lp) + fabsf(dE)) + kFp64Margin * (mag + fabsf(lp));
-    eE = err * 1.001f;
-}
 
 __device__ __forceinline__ float image_at(const Job& J, long long i)
 {
@@ -604,10 +495,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 J.p_c[o] = c;
                 J.p_flags[o] = 0;
                 if (J.model == SEG_PC) {
-                    float dE, eE;
-                    energy_pc(J, v, own, c, delta_p(si, own, c), dE, eE);
-                    J.p_dE[o] = dE;
-                    J.p_eE[o] = eE;
+                    // the FP64 energy difference in the order of its definition, kept as a float pair
+                    const double data = data_pc64(J, (double)v, own, c);
+                    if (J.curv) J.p_dE64[o] = data;      // the ball term follows (k_curvature)
+                    store_dE(J, o, with_length64(J, data, delta_p(si, own, c)));
                 }
             }
             o++;
@@ -624,7 +515,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
     }
     if (J.model == SEG_PC_DECONV && fits) {
         // deconvolving model: one particle per thread; G at the pixel (the last separable pass,
-        // FP64), then the FP64 energy difference rounded once: |dE - dE64| <= 2^-24 |dE| + 2^-150
+        // FP64), then the FP64 energy difference
         for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
             const unsigned gi = J.p_idx[o2];
             const int own = J.p_l[o2], c = J.p_c[o2];
@@ -632,11 +523,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
             pix_coords(J, gi, x, y, z);
             const double G = deconv_G(J, gi, y, z);
             J.dc_G[gi] = G;                         // for the FP64 recompute (same value per particle)
-            const double e64 = __dadd_rn(deconv_data64(J, G, x, y, z, own, c),
-                                         __dmul_rn(J.lambda64, (double)delta_p(sidx(x, y, z), own, c)));
-            const float dE = __double2float_rn(e64);
-            J.p_dE[o2] = dE;
-            J.p_eE[o2] = fabsf(dE) * kU + 1.5e-45f;
+            const double data = deconv_data64(J, G, x, y, z, own, c);
+            if (J.curv) J.p_dE64[o2] = data;
+            store_dE(J, o2, with_length64(J, data, delta_p(sidx(x, y, z), own, c)));
         }
         return;
     }
@@ -694,25 +583,28 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                     cl += __shfl_xor_sync(0xffffffffu, cl, w2);
                 }
                 if (act && lane4 == 0) {
-                    const long long qv = Q[si];
-                    const float v = (float)qv * J.unit32;
-                    const long long sc = isc - (long long)cc * qv, sl = isl - (long long)cl * qv;
-                    float dE, eE;
-                    if (J.model == SEG_PS_POISSON) {
-                        // local means from the exact sums: two float32 roundings each
-                        const float muc = ((float)isc / (float)cc) * J.unit32;
-                        const float mul = ((float)isl / (float)cl) * J.unit32;
-                        energy_psp_finish(J, v, delta_p(si, own, c), muc, 1.0001f * kU * muc, mul, 1.0001f * kU * mul,
-                                          dE, eE);
+                    const double v = __dmul_rn((double)Q[si], J.unit64);   // the pixel value, exactly
+                    double sc = 0.0, sl = 0.0;
+                    if (J.ps_exact64) {
+                        // every partial sum of the FP64 ball loop is exact: the integer sums are its sums
+                        sc = __dmul_rn((double)isc, J.unit64);
+                        sl = __dmul_rn((double)isl, J.unit64);
                     } else {
-                        energy_ps_finish_int(J, v, delta_p(si, own, c), sc, cc, sl, cl, dE, eE);
+                        // the FP64 loop over the ball in row-major order
+                        for (int u = 0; u < J.ps_n; u++) {
+                            const int sj = si + s_delta[u];
+                            const int m = sL[sj];
+                            if (m == c) sc = __dadd_rn(sc, __dmul_rn((double)Q[sj], J.unit64));
+                            else if (m == own) sl = __dadd_rn(sl, __dmul_rn((double)Q[sj], J.unit64));
+                        }
                     }
+                    const double data = data_ps64(J, v, sc, cc, sl, cl);
+                    if (J.curv) J.p_dE64[o2] = data;
+                    store_dE(J, o2, with_length64(J, data, delta_p(si, own, c)));
                     J.p_qc[o2] = isc;
                     J.p_ql[o2] = isl;
                     J.p_nc[o2] = cc;
                     J.p_nl[o2] = cl;
-                    J.p_dE[o2] = dE;
-                    J.p_eE[o2] = eE;
                 }
             }
         };
@@ -720,26 +612,27 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         else quad_pass(sQ);
         return;
     }
+    // one particle per thread: exact fixed-point ball sums where they are available (kept for the
+    // FP64 recompute), the FP64 row-major ball loop where they are not exact in FP64
     for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
         const unsigned gi = J.p_idx[o2];
         const int own = J.p_l[o2], c = J.p_c[o2];
         int x, y, z;
         pix_coords(J, gi, x, y, z);
         const int si = sidx(x, y, z);
-        const float v = stage_img && !use_int ? sI[si] : image_at(J, gi);
-        long long qv = 0;
-        if (use_int) qv = stage_img ? sQ[si] : image_q(J, gi);
+        const double v = image64(J, gi);
         long long isc = 0, isl = 0;
-        float fsc = 0.f, fsl = 0.f, ac = 0.f, al = 0.f;
+        double fsc = 0.0, fsl = 0.0;
         int cc = 0, cl = 0;
         for (int u = 0; u < J.ps_n; u++) {
             int m;
-            float f = 0.f;
+            double f = 0.0;
             long long qy = 0;
             if (stage_img) {
-                const int sj = si + s_delta[u];
+                const int sj = si + s_delta[u];     // staged float32 image (no fixed point here)
                 m = sL[sj];
-                f = sI[sj];
+                if (m != c && m != own) continue;
+                f = (double)sI[sj];
             } else {
                 const int4 d = __ldg(J.ps_off + u);
                 const int yx = x + d.z, yy = y + d.y, yz = z + d.x;
@@ -747,54 +640,34 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 const long long gj2 = ((long long)yz * J.H + yy) * J.W + yx;
                 m = __ldg(J.L + gj2);
                 if (m != c && m != own) continue;
-                if (use_int) qy = image_q(J, gj2); else f = image_at(J, gj2);
+                if (use_int) qy = image_q(J, gj2);
+                if (!J.ps_exact64) f = image64(J, gj2);
             }
             if (m == c) {
-                if (use_int) isc += qy - qv;
-                else { float dv = f - v; fsc += dv; ac += fabsf(dv); }
+                isc += qy;
+                fsc = __dadd_rn(fsc, f);
                 cc++;
-            } else if (m == own) {
-                if (use_int) isl += qy - qv;
-                else { float dv = f - v; fsl += dv; al += fabsf(dv); }
+            } else {
+                isl += qy;
+                fsl = __dadd_rn(fsl, f);
                 cl++;
             }
         }
-        float dE, eE;
-        const int dP = delta_p(si, own, c);
-        if (J.model == SEG_PS_POISSON) {
-            float muc, emc, mul, eml;
-            if (use_int) {
-                const long long rc = isc + (long long)cc * qv, rl = isl + (long long)cl * qv;
-                muc = ((float)rc / (float)cc) * J.unit32;
-                mul = ((float)rl / (float)cl) * J.unit32;
-                emc = 1.0001f * kU * muc;
-                eml = 1.0001f * kU * mul;
-            } else {
-                // shifted float sums: mu = v + sum(I - v) / n
-                muc = v + fsc / (float)cc;
-                mul = v + fsl / (float)cl;
-                emc = gamma_n(cc + 2) * ac / (float)cc + kU * (fabsf(muc) + fabsf(v));
-                eml = gamma_n(cl + 2) * al / (float)cl + kU * (fabsf(mul) + fabsf(v));
-            }
-            energy_psp_finish(J, v, dP, muc, emc, mul, eml, dE, eE);
-            if (use_int) {
-                J.p_qc[o2] = isc + (long long)cc * qv;
-                J.p_ql[o2] = isl + (long long)cl * qv;
-                J.p_nc[o2] = cc;
-                J.p_nl[o2] = cl;
-            }
-        } else if (use_int) {
-            energy_ps_finish_int(J, v, dP, isc, cc, isl, cl, dE, eE);
-            // keep the exact ball sums for the FP64 recompute
-            J.p_qc[o2] = isc + (long long)cc * qv;
-            J.p_ql[o2] = isl + (long long)cl * qv;
+        double sc = fsc, sl = fsl;
+        if (J.ps_exact64) {
+            sc = __dmul_rn((double)isc, J.unit64);
+            sl = __dmul_rn((double)isl, J.unit64);
+        }
+        const double data = data_ps64(J, v, sc, cc, sl, cl);
+        if (J.curv) J.p_dE64[o2] = data;
+        store_dE(J, o2, with_length64(J, data, delta_p(si, own, c)));
+        if (use_int) {
+            // the exact ball sums for the FP64 recompute
+            J.p_qc[o2] = isc;
+            J.p_ql[o2] = isl;
             J.p_nc[o2] = cc;
             J.p_nl[o2] = cl;
-        } else {
-            energy_ps_finish(J, v, dP, fsc, ac, cc, fsl, al, cl, dE, eE);
         }
-        J.p_dE[o2] = dE;
-        J.p_eE[o2] = eE;
     }
 }
 
@@ -840,7 +713,7 @@ constexpr int kMaxRows = 256;      // (dy, dz) rows of the interaction ball
 constexpr int kMaxRing = 4096;     // ring cells per tile
 
 struct Rec {
-    float dE, eE;
+    float dh, dl;                  // the energy difference as a float pair
     int l, c;
 };
 
@@ -903,9 +776,11 @@ __device__ __forceinline__ int ring_cell_of(const unsigned* s_eoff, int ne, unsi
     return lo;
 }
 
+// The sums of Eq. 6 for particle (x, y, z; label lp) from global memory (tiles that are not
+// staged): compensated sums of exact products, and sum |K dE| per set for the bound
 template <int NDIM>
-__device__ __forceinline__ void sobolev_sums(const Job& J, int lp, int x, int y, int z, int r2max, float& As, float& Bs,
-                                             float& aA, float& aB, float& eAs, float& eBs, int& nA, int& nB)
+__device__ __forceinline__ void sobolev_sums(const Job& J, int lp, int x, int y, int z, int r2max, DotAcc& A,
+                                             DotAcc& B, float& aA, float& aB, int& nA, int& nB)
 {
     const int pcx = (int)fdiv((unsigned)x, J.fd_cell), pcy = (int)fdiv((unsigned)y, J.fd_cell);
     const int pcz = NDIM == 3 ? (int)fdiv((unsigned)z, J.fd_cell) : z;
@@ -919,14 +794,15 @@ __device__ __forceinline__ void sobolev_sums(const Job& J, int lp, int x, int y,
                     pix_coords(J, J.p_idx[j], qx, qy, qz);
                     const int d2 = (qx - x) * (qx - x) + (qy - y) * (qy - y) + (qz - z) * (qz - z);
                     if (d2 > r2max) continue;
-                    const float K = __ldg(J.klut + d2);
                     const int ql = J.p_l[j], qc = J.p_c[j];
+                    if (ql != lp && qc != lp) continue;
+                    const float Kh = __ldg(J.klut + d2), Kl = __ldg(J.klut_lo + d2);
                     if (ql == lp) {
-                        const float wq = K * J.p_dE[j];
-                        As += wq; aA += fabsf(wq); eAs += K * J.p_eE[j]; nA++;
-                    } else if (qc == lp) {
-                        const float wq = K * J.p_dE[j];
-                        Bs += wq; aB += fabsf(wq); eBs += K * J.p_eE[j]; nB++;
+                        aA += fabsf(A.add(Kh, Kl, J.p_dE[j], J.p_dEl[j]));
+                        nA++;
+                    } else {
+                        aB += fabsf(B.add(Kh, Kl, J.p_dE[j], J.p_dEl[j]));
+                        nB++;
                     }
                 }
             }
@@ -938,7 +814,7 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
     pdl_enter();
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned s_warp[32];
-    __shared__ float s_klut[256];
+    __shared__ float s_klut[256], s_klutl[256];
     __shared__ int s_rdelta[kMaxRows];           // row offset in the pixel box
     __shared__ unsigned short s_rinfo[kMaxRows]; // rx | dy^2 + dz^2 << 8
     __shared__ int s_nrows;
@@ -979,7 +855,10 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
     unsigned* s_eoff = (unsigned*)(smem + lay.eoff);
 
     if (tid == 0) s_osc = 0;
-    for (int d2 = tid; d2 <= r2max && d2 < 256; d2 += blockDim.x) s_klut[d2] = __ldg(J.klut + d2);
+    for (int d2 = tid; d2 <= r2max && d2 < 256; d2 += blockDim.x) {
+        s_klut[d2] = __ldg(J.klut + d2);
+        s_klutl[d2] = __ldg(J.klut_lo + d2);
+    }
 
     // staged pixel box: an x-slab [sx0, sx1) of the tile grown by rr (2D: z is the tile's single
     // plane); the whole tile first, halved while its particles do not fit
@@ -1108,8 +987,8 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
                         }
                         const unsigned pos = s_off[(z * bny + y) * bnx + x] + rank;
                         Rec r;
-                        r.dE = J.p_dE[p];
-                        r.eE = J.p_eE[p];
+                        r.dh = J.p_dE[p];
+                        r.dl = J.p_dEl[p];
                         r.l = J.p_l[p];
                         r.c = J.p_c[p];
                         s_rec[pos] = r;
@@ -1134,7 +1013,8 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
             pix_coords(J, gi, x, y, z);
             const bool act = own && x >= sx0 && x < sx1;
             const int lp = i == my_i ? my_l : J.p_l[p];
-            float As = 0.f, Bs = 0.f, aA = 0.f, aB = 0.f, eAs = 0.f, eBs = 0.f;
+            DotAcc A, B;
+            float aA = 0.f, aB = 0.f;
             int nA = 0, nB = 0;
             if (act && staged) {
                 // the particle lies in the slab, so every row of its ball lies in the box
@@ -1147,42 +1027,42 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
                     const unsigned j1 = s_off[base + rx + 1];
                     for (unsigned j = s_off[base - rx]; j < j1; j++) {
                         const int dx = (int)s_x[j] - lx;
-                        const float K = s_klut[dyz2 + dx * dx];
+                        const int d2 = dyz2 + dx * dx;
                         const Rec q = s_rec[j];
                         if (q.l == lp) {
-                            const float wq = K * q.dE;
-                            As += wq; aA += fabsf(wq); eAs += K * q.eE; nA++;
+                            aA += fabsf(A.add(s_klut[d2], s_klutl[d2], q.dh, q.dl));
+                            nA++;
                         } else if (q.c == lp) {
-                            const float wq = K * q.dE;
-                            Bs += wq; aB += fabsf(wq); eBs += K * q.eE; nB++;
+                            aB += fabsf(B.add(s_klut[d2], s_klutl[d2], q.dh, q.dl));
+                            nB++;
                         }
                     }
                 }
             } else if (act && h == 0) {
-                sobolev_sums<NDIM>(J, lp, x, y, z, r2max, As, Bs, aA, aB, eAs, eBs, nA, nB);
+                sobolev_sums<NDIM>(J, lp, x, y, z, r2max, A, B, aA, aB, nA, nB);
             }
 #pragma unroll
             for (int o = 1; o < kSplit; o <<= 1) {
-                As += __shfl_xor_sync(0xffffffffu, As, o);
-                Bs += __shfl_xor_sync(0xffffffffu, Bs, o);
+                // the partner lanes' compensated sums joined by a two-sum of their leading parts
+                const float As2 = __shfl_xor_sync(0xffffffffu, A.s, o), At2 = __shfl_xor_sync(0xffffffffu, A.t, o);
+                const float Bs2 = __shfl_xor_sync(0xffffffffu, B.s, o), Bt2 = __shfl_xor_sync(0xffffffffu, B.t, o);
+                A.add(1.0f, 0.0f, As2, At2);
+                B.add(1.0f, 0.0f, Bs2, Bt2);
                 aA += __shfl_xor_sync(0xffffffffu, aA, o);
                 aB += __shfl_xor_sync(0xffffffffu, aB, o);
-                eAs += __shfl_xor_sync(0xffffffffu, eAs, o);
-                eBs += __shfl_xor_sync(0xffffffffu, eBs, o);
                 nA += __shfl_xor_sync(0xffffffffu, nA, o);
                 nB += __shfl_xor_sync(0xffffffffu, nB, o);
             }
             if (!act || h) continue;
-            float A = nA ? As / (float)nA : 0.f;
-            float B = nB ? Bs / (float)nB : 0.f;
-            float eA = nA ? ((eAs + (kU + gamma_n(nA)) * aA) * 1.0001f / (float)nA + kU * fabsf(A)) : 0.f;
-            float eB = nB ? ((eBs + (kU + gamma_n(nB)) * aB) * 1.0001f / (float)nB + kU * fabsf(B)) : 0.f;
-            float gp = A - B;
-            float margin = kFp64Margin * ((nA ? aA / (float)nA : 0.f) + (nB ? aB / (float)nB : 0.f));
-            float eg = (eA + eB + kU * fabsf(gp) + margin) * 1.001f;
+            float Aq = 0.f, Al = 0.f, Bq = 0.f, Bl = 0.f;
+            if (nA) pair_div(A.s, A.t, nA, Aq, Al);
+            if (nB) pair_div(B.s, B.t, nB, Bq, Bl);
+            const float gp = pair_sub(Aq, Al, Bq, Bl);
+            const float TA = nA ? aA / (float)nA : 0.f, TB = nB ? aB / (float)nB : 0.f;
             J.p_g[p] = gp;
-            J.p_eg[p] = eg;
-            osc += (A != 0.f && B != 0.f && ((A > 0.f) == (B > 0.f))) ? 1u : 0u;
+            J.p_eg[p] = pair_bound(gp, nA ? nA + kSplit : 0, TA, nB ? nB + kSplit : 0, TB);
+            const float Af = __fadd_rn(Aq, Al), Bf = __fadd_rn(Bq, Bl);
+            osc += (Af != 0.f && Bf != 0.f && ((Af > 0.f) == (Bf > 0.f))) ? 1u : 0u;
         }
         sx0 = sx1;
         __syncthreads();                                 // the next slab reuses shared memory

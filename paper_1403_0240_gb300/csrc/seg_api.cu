@@ -303,7 +303,7 @@ int largest_d2_below(double cutoff)
 // Geometry, tables and the plan of the fixed device allocation.
 struct Plan {
     Job h{};
-    std::vector<float> klut;
+    std::vector<float> klut, klut_lo;
     std::vector<double> klut64;
     std::vector<int4> ps_off, nb_off, cv_off;
     Arena fixed;
@@ -370,10 +370,12 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     h.nS = nS;
     h.nQ = 2 * (nS - 1) + 25;
     P.klut.resize(h.r2max + 1);
+    P.klut_lo.resize(h.r2max + 1);
     P.klut64.resize(h.r2max + 1);
     for (int d2 = 0; d2 <= h.r2max; d2++) {
         P.klut64[d2] = kernel_eq5(std::sqrt((double)d2), h.E);
         P.klut[d2] = (float)P.klut64[d2];
+        P.klut_lo[d2] = (float)(P.klut64[d2] - (double)P.klut[d2]);   // exact difference, rounded once
     }
     const int rz = h.ndim == 3 ? 1 : 0;
     if (is_ps(h.model)) {
@@ -445,11 +447,13 @@ void make_geometry(const seg_params* p, int M, int slot_lo, int nS, Plan& P)
     A.add(&h.wp32, M);
     A.add(&h.wm32, M);
     A.add((float**)&h.klut, P.klut.size());
+    A.add((float**)&h.klut_lo, P.klut_lo.size());
     A.add((double**)&h.klut64, P.klut64.size());
     A.add((int4**)&h.ps_off, std::max<size_t>(1, P.ps_off.size()));
     A.add((int4**)&h.nb_off, P.nb_off.size());
     if (h.curv) A.add((int4**)&h.cv_off, P.cv_off.size());
     A.add(&h.gK32, (size_t)h.gd2max + 1);
+    A.add(&h.gK32l, (size_t)h.gd2max + 1);
     A.add(&h.gK64, (size_t)h.gd2max + 1);
     h.psf_r = -1;
     if (h.topo_fuse) {
@@ -544,7 +548,9 @@ size_t particle_bytes(long long pcap, int stride)
     A.add(&h.p_l, pcap);
     A.add(&h.p_c, pcap);
     A.add(&h.p_dE, pcap);
+    A.add(&h.p_dEl, pcap);
     A.add(&h.p_eE, pcap);
+    A.add(&h.p_dE64, pcap);
     A.add(&h.p_g, pcap);
     A.add(&h.p_eg, pcap);
     A.add(&h.p_key, pcap);
@@ -571,7 +577,9 @@ void assign_particles(Job& h, char* base, long long pcap)
     A.add(&h.p_l, pcap);
     A.add(&h.p_c, pcap);
     A.add(&h.p_dE, pcap);
+    A.add(&h.p_dEl, pcap);
     A.add(&h.p_eE, pcap);
+    A.add(&h.p_dE64, pcap);
     A.add(&h.p_g, pcap);
     A.add(&h.p_eg, pcap);
     A.add(&h.p_key, pcap);
@@ -1174,6 +1182,7 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
     if (c->h.sf64) CKF(cudaMemsetAsync(c->h.sf64, 0, 2 * (size_t)M * 8, stream));
     if (c->h.sk32) CKF(cudaMemsetAsync(c->h.sk32, 0, 2 * (size_t)M * 8, stream));
     CKF(cudaMemcpyAsync((void*)c->h.klut, P.klut.data(), P.klut.size() * 4, cudaMemcpyHostToDevice, stream));
+    CKF(cudaMemcpyAsync((void*)c->h.klut_lo, P.klut_lo.data(), P.klut_lo.size() * 4, cudaMemcpyHostToDevice, stream));
     CKF(cudaMemcpyAsync((void*)c->h.klut64, P.klut64.data(), P.klut64.size() * 8, cudaMemcpyHostToDevice, stream));
     if (!P.ps_off.empty())
         CKF(cudaMemcpyAsync((void*)c->h.ps_off, P.ps_off.data(), P.ps_off.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));

@@ -133,10 +133,12 @@ struct alignas(64) Job {
     int nb_n;                 // offsets with d2 <= r2max, row-major (for the FP64 recompute)
     const int4* nb_off;
     const float* klut;        // K(sqrt(d2)) rounded to float, d2 = 0..r2max
+    const float* klut_lo;     // ... and the rest, K - klut rounded to float (the pair holds 48 bits)
     const double* klut64;     // K(sqrt(d2)) in FP64, Eq. 5 evaluated in the order written
     int global_E;             // Eq. 6 with E = |Gamma| (all pairs) while in Sobolev mode
     int gd2max;               // ... largest squared distance within the image
     float* gK32;              // ... K(sqrt(d2)) for E = |Gamma| of the iteration, float
+    float* gK32l;             // ... and the rest, gK64 - gK32 rounded to float
     double* gK64;             // ... and FP64 (Eq. 5 in the order written); 0 outside the support
     int psf_r;                // deconvolving model: PSF profile radius, -1 until seg_set_psf
     double* psf;              // ... taps k(-r..r) (room for 2 SEG_PSF_MAX_RADIUS + 1)
@@ -178,8 +180,10 @@ struct alignas(64) Job {
     unsigned* p_idx;
     int* p_l;
     int* p_c;
-    float* p_dE;
-    float* p_eE;
+    float* p_dE;              // energy difference: the FP64 value rounded to float ...
+    float* p_dEl;             // ... and the rest of it, rounded to float
+    float* p_eE;              // ... bound on |p_dE - FP64 value|
+    double* p_dE64;           // curvature regulariser: the FP64 data term, before the ball term
     float* p_g;
     float* p_eg;
     double* p_key;
@@ -365,6 +369,145 @@ __device__ __forceinline__ double deconv_data64(const Job& J, double G, int x, i
     if (J.ndim == 3) np = __dmul_rn(np, J.psf_n[J.W + J.H + z]);
     const double q = __dmul_rn(__dmul_rn(d, d), np);
     return __dsub_rn(q, __dadd_rn(t, t));
+}
+
+// ---------------------------------------------------------------------------
+// FP64 evaluation of the energy difference in the order of its definition: every product and
+// sum rounded separately (no fused multiply-add), so that it equals the FP64 reference's value
+// bit for bit.
+__device__ __forceinline__ double image64(const Job& J, long long i)
+{
+    if (J.dtype == SEG_F32) return (double)((const float*)J.I)[i];
+    return (double)((const unsigned short*)J.I)[i];
+}
+
+// Natural logarithm by the atanh series after reduction to [sqrt(1/2), sqrt(2)):
+// ln x = e ln 2 + 2 (y + y^3/3 + ... + y^23/23), y = (m - 1)/(m + 1), every operation an IEEE
+// double operation in a fixed order (the FP64 reference evaluates the same series the same way).
+__device__ __forceinline__ double log_series(double x)
+{
+    int e = 0;
+    double m = frexp(x, &e);
+    if (m < 0.70710678118654752440) { m = __dmul_rn(2.0, m); e = e - 1; }
+    const double y = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double y2 = __dmul_rn(y, y);
+    double s = 1.0 / 23.0;
+    s = __dadd_rn(1.0 / 21.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 19.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 17.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 15.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 13.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 11.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 9.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 7.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 5.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0 / 3.0, __dmul_rn(y2, s));
+    s = __dadd_rn(1.0, __dmul_rn(y2, s));
+    return __dadd_rn(__dmul_rn((double)e, 0.69314718055994530942), __dmul_rn(2.0, __dmul_rn(y, s)));
+}
+
+// Poisson negative log-likelihood of v under the (floored) mean mu, the log(v!) term dropped
+__device__ __forceinline__ double poisson_f64(double v, double mu, double floor)
+{
+    const double m = mu > floor ? mu : floor;
+    return __dsub_rn(m, __dmul_rn(v, log_series(m)));
+}
+
+// Piecewise-constant data term (Eq. 11, the exact single-pixel change of the squared deviations
+// from the region means): n_c/(n_c+1) (v - mu_c)^2 - n_l/(n_l-1) (v - mu_l)^2, where the second
+// weight is 0 for n_l <= 1 (so the term is +0, as the definition's 0)
+__device__ __forceinline__ double data_pc64(const Job& J, double v, int l, int c)
+{
+    const double a = __dsub_rn(v, __ldg(J.mu64 + c));
+    const double b = __dsub_rn(v, __ldg(J.mu64 + l));
+    const double t1 = __dmul_rn(__ldg(J.wp64 + c), __dmul_rn(a, a));
+    const double t2 = __dmul_rn(__ldg(J.wm64 + l), __dmul_rn(b, b));
+    return __dsub_rn(t1, t2);
+}
+
+// Piecewise-smooth data terms from the FP64 sums sc, sl of the c and l parts of the ball and
+// their pixel counts: (v - mu_c)^2 - (v - mu_l)^2, or with Poisson noise f(v, mu_c) - f(v, mu_l)
+__device__ __forceinline__ double data_ps64(const Job& J, double v, double sc, long long cc, double sl, long long cl)
+{
+    const double muc = __ddiv_rn(sc, (double)cc), mul = __ddiv_rn(sl, (double)cl);
+    if (J.model == SEG_PS_POISSON)
+        return __dsub_rn(poisson_f64(v, muc, J.mu_floor64), poisson_f64(v, mul, J.mu_floor64));
+    const double a = __dsub_rn(v, muc);
+    const double b = __dsub_rn(v, mul);
+    return __dsub_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+}
+
+// data term + lambda * (change of unlike neighbour pairs)
+__device__ __forceinline__ double with_length64(const Job& J, double data, int dP)
+{
+    return __dadd_rn(data, __dmul_rn(J.lambda64, (double)dP));
+}
+
+// Keep the FP64 energy difference e of particle o as a pair of floats, hi = fl(e) and
+// lo = fl(e - hi): |hi + lo - e| <= 2^-48 |e| + 2^-149. The bound stored with hi is that of
+// its one rounding, 2^-24 |hi| (+ 2^-149 below the normal range), widened by 2^-50 |hi|.
+__device__ __forceinline__ void store_dE(const Job& J, unsigned o, double e)
+{
+    const float hi = __double2float_rn(e);
+    J.p_dE[o] = hi;
+    J.p_dEl[o] = __double2float_rn(__dsub_rn(e, (double)hi));
+    J.p_eE[o] = 5.96047e-8f * fabsf(hi) + 1.4e-45f;
+}
+
+// Compensated sum of exact products (Ogita, Rump and Oishi, "Accurate sum and dot product",
+// SIAM J. Sci. Comput. 2005: algorithm Dot2, the product's error term taken by a fused
+// multiply-add, here with both factors given as float pairs): after n terms s + t equals the sum
+// of (Kh + Kl)(dh + dl) within u |sum| + (gamma_n^2 + 2^-46) sum |K dE|, u = 2^-24.
+struct DotAcc {
+    float s = 0.0f, t = 0.0f;
+    __device__ __forceinline__ float add(float Kh, float Kl, float dh, float dl)
+    {
+        const float p = __fmul_rn(Kh, dh);
+        float e = __fmaf_rn(Kh, dh, -p);          // the product's rounding error, exactly
+        e = __fmaf_rn(Kh, dl, e);
+        e = __fmaf_rn(Kl, dh, e);
+        const float x = __fadd_rn(s, p);          // two-sum: x + err = s + p exactly
+        const float z = __fsub_rn(x, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(x, z)), __fsub_rn(p, z));
+        s = x;
+        t = __fadd_rn(t, __fadd_rn(err, e));
+        return p;
+    }
+};
+
+// (s + t) / n as a pair (q, ql): q the rounded quotient of s, whose remainder s - q n is exact
+__device__ __forceinline__ void pair_div(float s, float t, int n, float& q, float& ql)
+{
+    const float fn = (float)n;
+    q = __fdiv_rn(s, fn);
+    ql = __fdiv_rn(__fadd_rn(__fmaf_rn(-q, fn, s), t), fn);
+}
+
+// (a + al) - (b + bl) rounded to one float, through a two-sum of the leading parts
+__device__ __forceinline__ float pair_sub(float a, float al, float b, float bl)
+{
+    const float x = __fsub_rn(a, b);
+    const float z = __fsub_rn(x, a);
+    const float err = __fsub_rn(__fsub_rn(a, __fsub_rn(x, z)), __fadd_rn(b, z));
+    return __fadd_rn(x, __fadd_rn(err, __fsub_rn(al, bl)));
+}
+
+// Bound on |g - g_fp64| of a gradient from the compensated Eq. 6 sums of nA and nB terms
+// (partial sums of parallel lanes joined count as terms): the final rounding to float, the
+// second-order terms of the compensated sums (gamma_2n^2), the float pairs of K and dE with the
+// products' rounded cross terms (below 6e-14 of |K dE|), the pair divisions and difference
+// (u^2), and the FP64 reference's own rounding (1e-12), each relative to a set's sum of |K dE|
+// over its size (TA, TB).
+__device__ __forceinline__ float pair_bound(float g, int nA, float TA, int nB, float TB)
+{
+    auto g2 = [](int n) {
+        const float t = (float)(2 * n) * 5.9604645e-8f;
+        const float gm = t / (1.0f - t);
+        return gm * gm;
+    };
+    const float cA = nA ? g2(nA) + 6e-14f + 1e-12f : 0.0f;
+    const float cB = nB ? g2(nB) + 6e-14f + 1e-12f : 0.0f;
+    return (5.9604645e-8f * fabsf(g) + (cA * TA + cB * TB) * 1.01f) * 1.001f + 1.4e-45f;
 }
 
 // What seg_init needs to know about its inputs, found on the device in one pass.
