@@ -7,8 +7,7 @@
 //
 // One warp per particle, the lanes over the ball offsets (consecutive dx of a row in
 // consecutive lanes, so the label loads of a row coalesce). The energy difference is completed in
-// FP64 from the data term extraction left and stored as a float pair; the FP64 recompute
-// evaluates the same count (energy64).
+// FP64 from the data term extraction left, in the order of the definition.
 #include <cuda_runtime.h>
 
 #include <algorithm>

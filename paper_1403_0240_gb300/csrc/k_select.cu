@@ -183,7 +183,19 @@ __device__ __forceinline__ void coords(const Job& J, unsigned gi, int& x, int& y
 
 // Certification: a particle that could be negative (g < eg) is queued for the FP64
 // recompute when its sign, or its order against any other possibly-negative particle
-// at Chebyshev distance <= 1 (same pixel included), is not certified by the bounds.
+// at Chebyshev distance <= 1, is not certified by the bounds. In the Sobolev modes particles
+// of one pixel share their label, hence both sets of Eq. 6 and the gradient, bit for bit on
+// both sides, so their order is that of c and needs no certificate (in L2 mode their
+// gradients are their own energy differences and are compared like the others).
+//
+// The comparisons run in float32: with d = fl(gp - gq) and s = fl(ep + eq), each within one
+// rounding, |gp - gq| <= ep + eq implies |d| <= s (1 + 2^-22), so a pair is queued whenever
+// the exact test could fail.
+__device__ __forceinline__ bool order_uncertain(float gp, float ep, float gq, float eq)
+{
+    return fabsf(__fsub_rn(gp, gq)) <= __fmul_rn(__fadd_rn(ep, eq), 1.00000024f);
+}
+
 __global__ void __launch_bounds__(256) k_flag(Group g)
 {
     pdl_enter();
@@ -196,6 +208,7 @@ __global__ void __launch_bounds__(256) k_flag(Group g)
     const unsigned pstart = J.tile_start[k], pcount = J.tile_count[k];
     const unsigned tag = ld_volatile(&ctr->iter_tag);
     const unsigned np = ld_volatile(&ctr->n_particles);
+    const bool same_g_per_pixel = ld_volatile(&ctr->mode) != SEG_L2;
     const int rz = J.ndim == 3 ? 1 : 0;
     for (unsigned i = threadIdx.x; i < pcount; i += blockDim.x) {
         const unsigned p = pstart + i;
@@ -211,6 +224,8 @@ __global__ void __launch_bounds__(256) k_flag(Group g)
                     for (int dx = -1; dx <= 1 && !flag; dx++) {
                         int xx = x + dx, yy = y + dy, zz = z + dz;
                         if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
+                        const bool own_pixel = dx == 0 && dy == 0 && dz == 0;
+                        if (own_pixel && same_g_per_pixel) continue;
                         unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
                         unsigned long long e = J.pmap[yi];
                         if ((unsigned)(e >> 32) != tag) continue;
@@ -218,7 +233,7 @@ __global__ void __launch_bounds__(256) k_flag(Group g)
                             if (q == p) continue;
                             float gq = J.p_g[q], eq = J.p_eg[q];
                             if (!(gq < eq)) continue;
-                            if (fabs((double)gp - (double)gq) <= (double)ep + (double)eq) { flag = true; break; }
+                            if (order_uncertain(gp, ep, gq, eq)) { flag = true; break; }
                         }
                     }
         }
@@ -237,66 +252,9 @@ cudaError_t launch_flag(const Group& g, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
-// FP64 recompute in the order of the definition: every product and sum rounded
-// separately (no fused multiply-add), neighbours in ascending particle key.
-// q: index of the particle (gi, l -> c) in the current particle arrays; its exact ball
-// sums are reused when they were stored (piecewise smooth with exact FP64 ball sums).
-__device__ double energy64(const Job& J, unsigned gi, int l, int c, unsigned q)
-{
-    int x, y, z;
-    coords(J, gi, x, y, z);
-    const double v = image64(J, gi);
-    double data;
-    if (J.model == SEG_PC_DECONV) {
-        data = deconv_data64(J, J.dc_G[gi], x, y, z, l, c);   // G stored by extraction
-    } else if (J.model == SEG_PC) {
-        data = data_pc64(J, v, l, c);
-    } else {
-        double sc = 0.0, sl = 0.0;
-        long long cc = 0, cl = 0;
-        if (J.ps_exact64) {
-            // every partial sum of the row-major FP64 loop is a multiple of 2^e_min below 2^53
-            // units, so that loop is exact and equals the exact integer sum taken by extraction
-            sc = __dmul_rn((double)J.p_qc[q], J.unit64);
-            sl = __dmul_rn((double)J.p_ql[q], J.unit64);
-            cc = J.p_nc[q];
-            cl = J.p_nl[q];
-        } else {
-            for (int u = 0; u < J.ps_n; u++) {
-                int4 d = J.ps_off[u];
-                int xx = x + d.z, yy = y + d.y, zz = z + d.x;
-                if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
-                long long j = ((long long)zz * J.H + yy) * J.W + xx;
-                int m = J.L[j];
-                if (m == c) { sc = __dadd_rn(sc, image64(J, j)); cc++; }
-                else if (m == l) { sl = __dadd_rn(sl, image64(J, j)); cl++; }
-            }
-        }
-        data = data_ps64(J, v, sc, cc, sl, cl);
-    }
-    if (J.curv) {
-        // curvature regulariser: pixels of l minus pixels of c in the ball, weight w
-        int bal = 0;
-        for (int u = 0; u < J.cv_n; u++) {
-            const int4 d = J.cv_off[u];
-            const int xx = x + d.z, yy = y + d.y, zz = z + d.x;
-            if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
-            const int m = J.L[((long long)zz * J.H + yy) * J.W + xx];
-            bal += (int)(m == l) - (int)(m == c);
-        }
-        return __dadd_rn(data, __dmul_rn(J.curv_w64, (double)bal));
-    }
-    int dP = 0;
-    const int nbz = J.ndim == 3 ? 1 : 0;
-    const int off[6][3] = {{0, 0, -1}, {0, 0, 1}, {0, -1, 0}, {0, 1, 0}, {-1, 0, 0}, {1, 0, 0}};
-    for (int u = 0; u < 4 + 2 * nbz; u++) {
-        int xx = x + off[u][2], yy = y + off[u][1], zz = z + off[u][0];
-        if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
-        int m = J.L[((long long)zz * J.H + yy) * J.W + xx];
-        dP += (int)(m != c) - (int)(m != l);
-    }
-    return with_length64(J, data, dP);
-}
+// FP64 recompute in the order of the definition: every product and sum rounded separately (no
+// fused multiply-add), neighbours in ascending particle key. The partners' FP64 energy
+// differences are those extraction evaluated (the FP64 reference's values, bit for bit).
 
 // ---------------------------------------------------------------------------
 // Batches: per-job counts (flagged particles, candidates, labels) turned into one
@@ -438,7 +396,7 @@ __device__ double fix_global_warp(const Job& J, unsigned gi, int lp, unsigned ta
             for (unsigned q = q0; q < np && J.p_idx[q] == yi; q++) {
                 const int lq = J.p_l[q], cq = J.p_c[q];
                 if (lq != lp && cq != lp) continue;
-                t_w[pos] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
+                t_w[pos] = __dmul_rn(K, J.p_dE64[q]);
                 a_w[pos] = lq == lp ? 1 : 0;
                 pos++;
             }
@@ -477,7 +435,7 @@ __device__ void fixup_warps(const Job* jobs, int njobs, unsigned total, const un
         const unsigned gi = J.p_idx[p];
         const int lp = J.p_l[p], cp = J.p_c[p];
         if (mode == SEG_L2) {
-            if (lane == 0) J.p_key[p] = energy64(J, gi, lp, cp, p);
+            if (lane == 0) J.p_key[p] = J.p_dE64[p];
             continue;
         }
         if (mode == SEG_SOBOLEV_GLOBAL) {
@@ -505,7 +463,7 @@ __device__ void fixup_warps(const Job* jobs, int njobs, unsigned total, const un
                         for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi && nt < 6; q++) {
                             const int lq = J.p_l[q], cq = J.p_c[q];
                             if (lq == lp || cq == lp) {
-                                tv[nt] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
+                                tv[nt] = __dmul_rn(K, J.p_dE64[q]);
                                 ta[nt] = lq == lp ? 1 : 0;
                                 nt++;
                             }
@@ -571,7 +529,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fixup(const Job* jobs, int njob
         const unsigned gi = J.p_idx[p];
         const int lp = J.p_l[p], cp = J.p_c[p];
         if (mode == SEG_L2) {
-            if (tid == 0) J.p_key[p] = energy64(J, gi, lp, cp, p);
+            if (tid == 0) J.p_key[p] = J.p_dE64[p];
         } else if (mode == SEG_SOBOLEV_GLOBAL) {
             if (w == 0) {
                 const double gval = fix_global_warp(J, gi, lp, tag, np, s_t, s_a);
@@ -598,7 +556,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fixup(const Job* jobs, int njob
                             for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi && nt < 6; q++) {
                                 const int lq = J.p_l[q], cq = J.p_c[q];
                                 if (lq == lp || cq == lp) {
-                                    tv[nt] = __dmul_rn(K, energy64(J, yi, lq, cq, q));
+                                    tv[nt] = __dmul_rn(K, J.p_dE64[q]);
                                     ta[nt] = lq == lp ? 1 : 0;
                                     nt++;
                                 }

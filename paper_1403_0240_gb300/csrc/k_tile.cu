@@ -497,7 +497,6 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 if (J.model == SEG_PC) {
                     // the FP64 energy difference in the order of its definition, kept as a float pair
                     const double data = data_pc64(J, (double)v, own, c);
-                    if (J.curv) J.p_dE64[o] = data;      // the ball term follows (k_curvature)
                     store_dE(J, o, with_length64(J, data, delta_p(si, own, c)));
                 }
             }
@@ -524,7 +523,6 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
             const double G = deconv_G(J, gi, y, z);
             J.dc_G[gi] = G;                         // for the FP64 recompute (same value per particle)
             const double data = deconv_data64(J, G, x, y, z, own, c);
-            if (J.curv) J.p_dE64[o2] = data;
             store_dE(J, o2, with_length64(J, data, delta_p(sidx(x, y, z), own, c)));
         }
         return;
@@ -583,37 +581,47 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                     cl += __shfl_xor_sync(0xffffffffu, cl, w2);
                 }
                 if (act && lane4 == 0) {
-                    const double v = __dmul_rn((double)Q[si], J.unit64);   // the pixel value, exactly
-                    double sc = 0.0, sl = 0.0;
-                    if (J.ps_exact64) {
-                        // every partial sum of the FP64 ball loop is exact: the integer sums are its sums
-                        sc = __dmul_rn((double)isc, J.unit64);
-                        sl = __dmul_rn((double)isl, J.unit64);
-                    } else {
-                        // the FP64 loop over the ball in row-major order
-                        for (int u = 0; u < J.ps_n; u++) {
-                            const int sj = si + s_delta[u];
-                            const int m = sL[sj];
-                            if (m == c) sc = __dadd_rn(sc, __dmul_rn((double)Q[sj], J.unit64));
-                            else if (m == own) sl = __dadd_rn(sl, __dmul_rn((double)Q[sj], J.unit64));
-                        }
-                    }
-                    const double data = data_ps64(J, v, sc, cc, sl, cl);
-                    if (J.curv) J.p_dE64[o2] = data;
-                    store_dE(J, o2, with_length64(J, data, delta_p(si, own, c)));
                     J.p_qc[o2] = isc;
                     J.p_ql[o2] = isl;
                     J.p_nc[o2] = cc;
                     J.p_nl[o2] = cl;
                 }
             }
+            // the FP64 energy differences from the exact sums, one particle per thread (the FP64
+            // pipe is occupied per warp instruction, so the quads' single lanes would waste it)
+            __syncthreads();
+            for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
+                const unsigned gi = J.p_idx[o2];
+                const int own = J.p_l[o2], c = J.p_c[o2];
+                int x, y, z;
+                pix_coords(J, gi, x, y, z);
+                const int si = sidx(x, y, z);
+                const double v = __dmul_rn((double)Q[si], J.unit64);   // the pixel value, exactly
+                const int cc = J.p_nc[o2], cl = J.p_nl[o2];
+                double sc = 0.0, sl = 0.0;
+                if (J.ps_exact64) {
+                    // every partial sum of the FP64 ball loop is exact: the integer sums are its sums
+                    sc = __dmul_rn((double)J.p_qc[o2], J.unit64);
+                    sl = __dmul_rn((double)J.p_ql[o2], J.unit64);
+                } else {
+                    // the FP64 loop over the ball in row-major order
+                    for (int u = 0; u < J.ps_n; u++) {
+                        const int sj = si + s_delta[u];
+                        const int m = sL[sj];
+                        if (m == c) sc = __dadd_rn(sc, __dmul_rn((double)Q[sj], J.unit64));
+                        else if (m == own) sl = __dadd_rn(sl, __dmul_rn((double)Q[sj], J.unit64));
+                    }
+                }
+                const double data = data_ps64(J, v, sc, cc, sl, cl);
+                store_dE(J, o2, with_length64(J, data, delta_p(si, own, c)));
+            }
         };
         if (q32) quad_pass(sQ32);
         else quad_pass(sQ);
         return;
     }
-    // one particle per thread: exact fixed-point ball sums where they are available (kept for the
-    // FP64 recompute), the FP64 row-major ball loop where they are not exact in FP64
+    // one particle per thread: exact fixed-point ball sums where they are exact in FP64, the FP64
+    // row-major ball loop where they are not
     for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
         const unsigned gi = J.p_idx[o2];
         const int own = J.p_l[o2], c = J.p_c[o2];
@@ -659,15 +667,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
             sl = __dmul_rn((double)isl, J.unit64);
         }
         const double data = data_ps64(J, v, sc, cc, sl, cl);
-        if (J.curv) J.p_dE64[o2] = data;
         store_dE(J, o2, with_length64(J, data, delta_p(si, own, c)));
-        if (use_int) {
-            // the exact ball sums for the FP64 recompute
-            J.p_qc[o2] = isc;
-            J.p_ql[o2] = isl;
-            J.p_nc[o2] = cc;
-            J.p_nl[o2] = cl;
-        }
     }
 }
 

@@ -183,7 +183,8 @@ struct alignas(64) Job {
     float* p_dE;              // energy difference: the FP64 value rounded to float ...
     float* p_dEl;             // ... and the rest of it, rounded to float
     float* p_eE;              // ... bound on |p_dE - FP64 value|
-    double* p_dE64;           // curvature regulariser: the FP64 data term, before the ball term
+    double* p_dE64;           // ... the FP64 value (with the curvature regulariser: the data term until
+                              //     the ball term is added)
     float* p_g;
     float* p_eg;
     double* p_key;
@@ -443,11 +444,13 @@ __device__ __forceinline__ double with_length64(const Job& J, double data, int d
     return __dadd_rn(data, __dmul_rn(J.lambda64, (double)dP));
 }
 
-// Keep the FP64 energy difference e of particle o as a pair of floats, hi = fl(e) and
-// lo = fl(e - hi): |hi + lo - e| <= 2^-48 |e| + 2^-149. The bound stored with hi is that of
-// its one rounding, 2^-24 |hi| (+ 2^-149 below the normal range), widened by 2^-50 |hi|.
+// Keep the FP64 energy difference e of particle o (for the FP64 recompute) and as a pair of
+// floats, hi = fl(e) and lo = fl(e - hi): |hi + lo - e| <= 2^-48 |e| + 2^-149. The bound stored
+// with hi is that of its one rounding, 2^-24 |hi| (+ 2^-149 below the normal range), widened by
+// 2^-50 |hi|.
 __device__ __forceinline__ void store_dE(const Job& J, unsigned o, double e)
 {
+    J.p_dE64[o] = e;
     const float hi = __double2float_rn(e);
     J.p_dE[o] = hi;
     J.p_dEl[o] = __double2float_rn(__dsub_rn(e, (double)hi));
