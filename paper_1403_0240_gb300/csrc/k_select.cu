@@ -124,14 +124,14 @@ __device__ __forceinline__ bool simple_table(unsigned X, int d)
 
 // Topological control: removal from l (foreground) and addition to c (foreground)
 // must both be simple, so regions neither split, vanish, merge nor change holes. The
-// neighbourhood is read once for both labels. With SEG_TOPO_VANISH the removal of a
-// region's last pixel is admissible too: no 4- (6-) neighbour holds l (every foreground
-// label being one connected component). With SEG_TOPO_SPLIT a removal whose foreground number is
-// >= 2 is admissible too. Returns 0 (not admissible), 1, or 2 (admissible by the split rule).
-__device__ __forceinline__ int admissible(const Job& J, unsigned gi, int l, int c)
+// neighbourhood is read once for both labels (lab(dz, dy, dx): the label at that offset, -1
+// outside the image). With SEG_TOPO_VANISH the removal of a region's last pixel is admissible
+// too: no 4- (6-) neighbour holds l (every foreground label being one connected component).
+// With SEG_TOPO_SPLIT a removal whose foreground number is >= 2 is admissible too. Returns 0
+// (not admissible), 1, or 2 (admissible by the split rule).
+template <typename Lab>
+__device__ __forceinline__ int admissible_nb(const Job& J, int l, int c, Lab lab)
 {
-    int x, y, z;
-    pix_coords(J, gi, x, y, z);
     const int d = J.ndim == 3 ? 1 : 0;
     const int rz = d;
     unsigned ml = 0, mc = 0;
@@ -140,12 +140,9 @@ __device__ __forceinline__ int admissible(const Job& J, unsigned gi, int l, int 
         for (int dy = -1; dy <= 1; dy++)
             for (int dx = -1; dx <= 1; dx++) {
                 if (!dz && !dy && !dx) continue;
-                const int xx = x + dx, yy = y + dy, zz = z + dz;
-                if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D) {
-                    const int v = J.L[((long long)zz * J.H + yy) * J.W + xx];
-                    ml |= (unsigned)(v == l) << k;
-                    mc |= (unsigned)(v == c) << k;
-                }
+                const int v = lab(dz, dy, dx);
+                ml |= (unsigned)(v == l) << k;
+                mc |= (unsigned)(v == c) << k;
                 k++;
             }
     if (c != 0 && !simple_table(mc, d)) return 0;
@@ -153,6 +150,18 @@ __device__ __forceinline__ int admissible(const Job& J, unsigned gi, int l, int 
     if (J.topo_vanish && (ml & c_topo.touch[d]) == 0) return 1;
     if (J.topo_split && components(ml & c_topo.nF[d], c_topo.adjF[d], c_topo.touch[d]) >= 2) return 2;
     return 0;
+}
+
+// ... with the labels read from global memory
+__device__ __forceinline__ int admissible(const Job& J, unsigned gi, int l, int c)
+{
+    int x, y, z;
+    pix_coords(J, gi, x, y, z);
+    return admissible_nb(J, l, c, [&](int dz, int dy, int dx) {
+        const int xx = x + dx, yy = y + dy, zz = z + dz;
+        if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) return -1;
+        return J.L[((long long)zz * J.H + yy) * J.W + xx];
+    });
 }
 
 // the tabulated decision, as the selection uses it
@@ -611,10 +620,13 @@ cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cu
 
 // ---------------------------------------------------------------------------
 // Candidates: per pixel the particle with the smallest (key, c); a candidate if its
-// key is negative and its move passes the topology tests.
+// key is negative and its move passes the topology tests. The tile's labels with a one-pixel
+// rim are staged in shared memory first (coalesced rows), so that the topology tests read
+// their neighbourhoods there.
 __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
 {
     pdl_enter();
+    extern __shared__ int s_lab[];
     const unsigned t = blockIdx.x;
     if (t == 0 && threadIdx.x == 0) {
         bc->bar_count = 0;
@@ -626,6 +638,21 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
     Counters* ctr = J.ctr;
     if (job_idle(ctr)) return;
     const unsigned pstart = J.tile_start[k], pend = pstart + J.tile_count[k];
+    if (pend == pstart) return;
+    const TileBox b = tile_box(J, k);
+    const int rz = J.ndim == 3 ? 1 : 0;
+    const int ox = b.x0 - 1, oy = b.y0 - 1, oz = b.z0 - rz;
+    const int bx = b.x1 - b.x0 + 2, by = b.y1 - b.y0 + 2, bz = b.z1 - b.z0 + 2 * rz;
+    const bool staged = (unsigned)(bx * by * bz) <= g.sel_box;
+    if (staged) {
+        for (int row = threadIdx.x >> 5; row < by * bz; row += blockDim.x >> 5)
+            for (int lx = threadIdx.x & 31; lx < bx; lx += 32) {
+                const int x = ox + lx, y = oy + row % by, z = oz + row / by;
+                const bool in = x >= 0 && x < J.W && y >= 0 && y < J.H && z >= 0 && z < J.D;
+                s_lab[row * bx + lx] = in ? J.L[((long long)z * J.H + y) * J.W + x] : -1;
+            }
+        __syncthreads();
+    }
     for (unsigned p = pstart + threadIdx.x; p < pend; p += blockDim.x) {
         const unsigned gi = J.p_idx[p];
         if (p > pstart && J.p_idx[p - 1] == gi) continue;
@@ -638,7 +665,18 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
             if (kq < bk || (kq == bk && cq < bc_)) { best = q; bk = kq; bc_ = cq; }
         }
         int slot = -1;
-        const int adm = bk < 0.0 ? admissible(J, gi, J.p_l[best], bc_) : 0;
+        int adm = 0;
+        if (bk < 0.0) {
+            if (staged) {
+                int x, y, z;
+                pix_coords(J, gi, x, y, z);
+                const int c0 = ((z - oz) * by + (y - oy)) * bx + (x - ox);
+                adm = admissible_nb(J, J.p_l[best], bc_,
+                                    [&](int dz, int dy, int dx) { return s_lab[c0 + (dz * by + dy) * bx + dx]; });
+            } else {
+                adm = admissible(J, gi, J.p_l[best], bc_);
+            }
+        }
         if (adm) {
             slot = (int)atomicAdd(&ctr->n_cand, 1u);
             J.c_best[slot] = (int)best;
@@ -653,7 +691,17 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
 cudaError_t launch_select(const Group& g, BatchCtl* bc, cudaStream_t s)
 {
     if (g.total_tiles == 0) return cudaSuccess;
-    return launch_stage(k_select, g.total_tiles, 256, 0, s, g, bc);
+    return launch_stage(k_select, g.total_tiles, 256, (size_t)g.sel_box * 4, s, g, bc);
+}
+
+// labels staged by the candidate selection for a full tile of job h (tile + one pixel around),
+// or 0 when they would take more than 48 KB (the tests then read global memory)
+unsigned select_box_elems(const Job& h)
+{
+    const long long bx = (long long)h.tcx * h.cell + 2, by = (long long)h.tcy * h.cell + 2;
+    const long long bz = h.ndim == 3 ? (long long)h.tcz * h.cell + 2 : 1;
+    const long long n = bx * by * bz;
+    return n * 4 <= 48 * 1024 ? (unsigned)n : 0u;
 }
 
 // ---------------------------------------------------------------------------

@@ -9,30 +9,6 @@ namespace segk {
 
 constexpr int kBlock = 256;
 
-struct TileBox {
-    int x0, x1, y0, y1, z0, z1;   // pixel box of the tile
-    int cx0, cy0, cz0;            // first cell
-    int ccx, ccy, ccz;            // cells in the tile
-};
-
-__device__ __forceinline__ TileBox tile_box(const Job& J, unsigned k)
-{
-    TileBox b;
-    int tx = (int)(k % (unsigned)J.ntx);
-    int ty = (int)((k / (unsigned)J.ntx) % (unsigned)J.nty);
-    int tz = (int)(k / ((unsigned)J.ntx * (unsigned)J.nty));
-    int s = J.cell, sz = J.ndim == 3 ? J.cell : 1;
-    b.cx0 = tx * J.tcx; b.cy0 = ty * J.tcy; b.cz0 = tz * J.tcz;
-    b.ccx = min(J.tcx, J.ncx - b.cx0);
-    b.ccy = min(J.tcy, J.ncy - b.cy0);
-    b.ccz = min(J.tcz, J.ncz - b.cz0);
-    b.x0 = b.cx0 * s; b.x1 = min(J.W, (b.cx0 + b.ccx) * s);
-    b.y0 = b.cy0 * s; b.y1 = min(J.H, (b.cy0 + b.ccy) * s);
-    b.z0 = b.cz0 * sz; b.z1 = min(J.D, (b.cz0 + b.ccz) * sz);
-    return b;
-}
-
-
 __device__ __forceinline__ float image_at(const Job& J, long long i)
 {
     if (J.dtype == SEG_F32) return __ldg((const float*)J.I + i);

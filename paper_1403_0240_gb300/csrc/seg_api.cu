@@ -696,6 +696,8 @@ int stepper_build(Stepper& s)
         pf_off[gidx] = (int)prefix.size();
         unsigned acc = 0;
         size_t sx = 0, ss = 0;
+        unsigned sel = 0;
+        bool sel_ok = true;
         int cnt = 0;
         for (int i = 0; i < n; i++) {
             if (jobs[i].ndim != nd) continue;
@@ -704,6 +706,9 @@ int stepper_build(Stepper& s)
             acc += (unsigned)jobs[i].ntiles;
             sx = std::max(sx, extract_smem_bytes(jobs[i]));
             ss = std::max(ss, sobolev_smem_bytes(jobs[i]));
+            const unsigned sb = select_box_elems(jobs[i]);
+            sel_ok = sel_ok && sb > 0;
+            sel = std::max(sel, sb);
             cnt++;
         }
         prefix.push_back(acc);
@@ -712,6 +717,7 @@ int stepper_build(Stepper& s)
         g.njobs = cnt;
         g.total_tiles = cnt ? acc : 0;
         g.ticket = &s.d_bc->ticket[gidx];
+        g.sel_box = sel_ok ? sel : 0u;
         s.smem_x[gidx] = sx;
         s.smem_s[gidx] = ss;
     }

@@ -231,6 +231,8 @@ struct Group {
     int njobs;
     unsigned total_tiles;
     unsigned* ticket;         // extraction tile ticket
+    unsigned sel_box;         // candidate selection: label box (tile + 1 px) staged in shared memory,
+                              // in elements (the launch's dynamic shared memory / 4); 0 = read global
 };
 
 struct BatchCtl {
@@ -304,6 +306,30 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* s_warp
     unsigned before = w > 0 ? s_warp[w - 1] : 0u;
     total = s_warp[(blockDim.x >> 5) - 1];
     return before + x - v;
+}
+
+// Pixel box and cell range of tile k of a job.
+struct TileBox {
+    int x0, x1, y0, y1, z0, z1;   // pixel box of the tile
+    int cx0, cy0, cz0;            // first cell
+    int ccx, ccy, ccz;            // cells in the tile
+};
+
+__device__ __forceinline__ TileBox tile_box(const Job& J, unsigned k)
+{
+    TileBox b;
+    int tx = (int)(k % (unsigned)J.ntx);
+    int ty = (int)((k / (unsigned)J.ntx) % (unsigned)J.nty);
+    int tz = (int)(k / ((unsigned)J.ntx * (unsigned)J.nty));
+    int s = J.cell, sz = J.ndim == 3 ? J.cell : 1;
+    b.cx0 = tx * J.tcx; b.cy0 = ty * J.tcy; b.cz0 = tz * J.tcz;
+    b.ccx = min(J.tcx, J.ncx - b.cx0);
+    b.ccy = min(J.tcy, J.ncy - b.cy0);
+    b.ccz = min(J.tcz, J.ncz - b.cz0);
+    b.x0 = b.cx0 * s; b.x1 = min(J.W, (b.cx0 + b.ccx) * s);
+    b.y0 = b.cy0 * s; b.y1 = min(J.H, (b.cy0 + b.ccy) * s);
+    b.z0 = b.cz0 * sz; b.z1 = min(J.D, (b.cz0 + b.ccz) * sz);
+    return b;
 }
 
 // Which job / tile a tile ticket maps to.
@@ -589,6 +615,7 @@ cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s);
 cudaError_t topology_tables_init();
 cudaError_t commit_occupancy(int block, int* blocks_per_sm);
 size_t extract_smem_bytes(const Job& h);
+unsigned select_box_elems(const Job& h);
 size_t sobolev_smem_bytes(const Job& h);
 cudaError_t launch_debug_simple(const unsigned* masks, int ndim, int n, unsigned char* out, cudaStream_t s);
 
