@@ -650,6 +650,12 @@ def run_served(args, world, rank, local, pg):
     plain_parts = sum(x["particles"] for x in plain)
     plain_busy = sum(x["service"] for x in plain)
     plain_lat = np.array([x["latency"] for x in plain])
+    plain_kind = {}
+    for x in plain:
+        d = plain_kind.setdefault(keys[x["job"]][0], {"jobs": 0, "busy_s": 0.0, "particle_iterations": 0})
+        d["jobs"] += 1
+        d["busy_s"] += x["service"]
+        d["particle_iterations"] += x["particles"]
 
     # the arrival rate the server sustains: its throughput under overload over the mean job
     # size; then a shorter stream at 80% of that rate, whose latencies must stay bounded
@@ -741,6 +747,9 @@ def run_served(args, world, rank, local, pg):
                        "served_p99_s": float(np.percentile(served_lat, 99)),
                        "plain_value": plain_parts / plain_makespan, "plain_makespan_s": plain_makespan,
                        "plain_busy_value": plain_parts / plain_busy,
+                       "plain_by_kind": {k: {"jobs": v["jobs"], "busy_s": round(v["busy_s"], 3),
+                                             "particle_iterations": v["particle_iterations"]}
+                                         for k, v in plain_kind.items()},
                        "plain_p50_s": float(np.percentile(plain_lat, 50)),
                        "plain_p99_s": float(np.percentile(plain_lat, 99)),
                        "served_over_plain": (stream_parts / makespan) / (plain_parts / plain_makespan),

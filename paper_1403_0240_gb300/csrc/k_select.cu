@@ -620,13 +620,11 @@ cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cu
 
 // ---------------------------------------------------------------------------
 // Candidates: per pixel the particle with the smallest (key, c); a candidate if its
-// key is negative and its move passes the topology tests. The tile's labels with a one-pixel
-// rim are staged in shared memory first (coalesced rows), so that the topology tests read
-// their neighbourhoods there.
+// key is negative and its move passes the topology tests (labels read from global memory:
+// only a minority of the tile's pixels are tested, and their neighbourhoods overlap in L1).
 __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
 {
     pdl_enter();
-    extern __shared__ int s_lab[];
     const unsigned t = blockIdx.x;
     if (t == 0 && threadIdx.x == 0) {
         bc->bar_count = 0;
@@ -638,21 +636,6 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
     Counters* ctr = J.ctr;
     if (job_idle(ctr)) return;
     const unsigned pstart = J.tile_start[k], pend = pstart + J.tile_count[k];
-    if (pend == pstart) return;
-    const TileBox b = tile_box(J, k);
-    const int rz = J.ndim == 3 ? 1 : 0;
-    const int ox = b.x0 - 1, oy = b.y0 - 1, oz = b.z0 - rz;
-    const int bx = b.x1 - b.x0 + 2, by = b.y1 - b.y0 + 2, bz = b.z1 - b.z0 + 2 * rz;
-    const bool staged = (unsigned)(bx * by * bz) <= g.sel_box;
-    if (staged) {
-        for (int row = threadIdx.x >> 5; row < by * bz; row += blockDim.x >> 5)
-            for (int lx = threadIdx.x & 31; lx < bx; lx += 32) {
-                const int x = ox + lx, y = oy + row % by, z = oz + row / by;
-                const bool in = x >= 0 && x < J.W && y >= 0 && y < J.H && z >= 0 && z < J.D;
-                s_lab[row * bx + lx] = in ? J.L[((long long)z * J.H + y) * J.W + x] : -1;
-            }
-        __syncthreads();
-    }
     for (unsigned p = pstart + threadIdx.x; p < pend; p += blockDim.x) {
         const unsigned gi = J.p_idx[p];
         if (p > pstart && J.p_idx[p - 1] == gi) continue;
@@ -665,18 +648,7 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
             if (kq < bk || (kq == bk && cq < bc_)) { best = q; bk = kq; bc_ = cq; }
         }
         int slot = -1;
-        int adm = 0;
-        if (bk < 0.0) {
-            if (staged) {
-                int x, y, z;
-                pix_coords(J, gi, x, y, z);
-                const int c0 = ((z - oz) * by + (y - oy)) * bx + (x - ox);
-                adm = admissible_nb(J, J.p_l[best], bc_,
-                                    [&](int dz, int dy, int dx) { return s_lab[c0 + (dz * by + dy) * bx + dx]; });
-            } else {
-                adm = admissible(J, gi, J.p_l[best], bc_);
-            }
-        }
+        const int adm = bk < 0.0 ? admissible(J, gi, J.p_l[best], bc_) : 0;
         if (adm) {
             slot = (int)atomicAdd(&ctr->n_cand, 1u);
             J.c_best[slot] = (int)best;
@@ -691,17 +663,7 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
 cudaError_t launch_select(const Group& g, BatchCtl* bc, cudaStream_t s)
 {
     if (g.total_tiles == 0) return cudaSuccess;
-    return launch_stage(k_select, g.total_tiles, 256, (size_t)g.sel_box * 4, s, g, bc);
-}
-
-// labels staged by the candidate selection for a full tile of job h (tile + one pixel around),
-// or 0 when they would take more than 48 KB (the tests then read global memory)
-unsigned select_box_elems(const Job& h)
-{
-    const long long bx = (long long)h.tcx * h.cell + 2, by = (long long)h.tcy * h.cell + 2;
-    const long long bz = h.ndim == 3 ? (long long)h.tcz * h.cell + 2 : 1;
-    const long long n = bx * by * bz;
-    return n * 4 <= 48 * 1024 ? (unsigned)n : 0u;
+    return launch_stage(k_select, g.total_tiles, 256, 0, s, g, bc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1320,7 +1282,8 @@ __global__ void __launch_bounds__(256) k_lists(const Job* jobs, int njobs)
 
 // B: the rounds. With few candidates one block runs them on shared-memory states with
 // block barriers; otherwise the whole co-resident grid runs them with bounded grid barriers.
-__global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, BatchCtl* bc)
+__global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, BatchCtl* bc, unsigned* work,
+                                                  unsigned wcap)
 {
     pdl_enter();
     __shared__ unsigned s_red[32];
@@ -1455,28 +1418,46 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
         return;
     }
 
+    // The whole grid: round 0 visits every candidate, each later round only those the previous
+    // round left undecided (lists in `work`, appended warp by warp); a bounded grid barrier
+    // ends each round. Round r counts its list in rounds_cnt[r % 3] and clears the counter of
+    // round r + 1 before its barrier (that counter was last read right after the barrier that
+    // ended round r - 2).
     const unsigned nblocks = gridDim.x;
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    const unsigned lane = threadIdx.x & 31;
     unsigned rounds = 0;
+    unsigned n_cur = total;
     for (unsigned r = 0;; r++) {
-        unsigned undecided = 0;
-        for (unsigned i = gtid; i < total; i += gstride) {
-            const int j = job_of(s_pref, njobs, i);
-            const Job& J = jobs[j];
-            const unsigned s = i - s_pref[j];
-            if (ld_volatile(J.c_state + s) != kUndecided) continue;
-            const int v = commit_decide(J, s, (const volatile int*)J.c_state, 0u);
-            if (v == kUndecided) undecided++;
-            else *(volatile int*)(J.c_state + s) = v;
+        const unsigned* cur = (r & 1) ? work : work + wcap;      // round r - 1's list (r > 0)
+        unsigned* nxt = (r & 1) ? work + wcap : work;
+        unsigned* cnt = &bc->rounds_cnt[r % 3];
+        const unsigned span = (n_cur + gstride - 1) / gstride * gstride;   // whole warps stay in
+        for (unsigned t = gtid; t < span; t += gstride) {
+            bool und = false;
+            unsigned i = 0;
+            if (t < n_cur) {
+                i = r == 0 ? t : cur[t];
+                const int j = job_of(s_pref, njobs, i);
+                const Job& J = jobs[j];
+                const unsigned s = i - s_pref[j];
+                const int v = commit_decide(J, s, (const volatile int*)J.c_state, 0u);
+                if (v == kUndecided) und = true;
+                else *(volatile int*)(J.c_state + s) = v;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, und);
+            if (m) {
+                const unsigned leader = __ffs(m) - 1;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (und) nxt[base + __popc(m & ((1u << lane) - 1u))] = i;
+            }
         }
-        unsigned bs = block_sum(undecided, s_red);
-        if (threadIdx.x == 0) {
-            if (bs) atomicAdd(&bc->rounds_cnt[r % 3], bs);
-            if (blockIdx.x == 0) bc->rounds_cnt[(r + 1) % 3] = 0;
-        }
+        if (gtid == 0) bc->rounds_cnt[(r + 1) % 3] = 0;
         if (!grid_barrier(bc, nblocks)) break;
-        unsigned rem = ld_volatile(&bc->rounds_cnt[r % 3]);
-        if (rem == 0) { rounds = r + 1; break; }
+        n_cur = ld_volatile(cnt);
+        if (n_cur == 0) { rounds = r + 1; break; }
         if (r + 1 >= kMaxRounds) {
             if (gtid == 0) atomicExch(&bc->err, SEG_ETIMEOUT);
             break;
@@ -1562,7 +1543,8 @@ cudaError_t launch_lists(const Job* jobs, int njobs, int sms, cudaStream_t s)
 }
 
 // the rounds kernel is cooperative: every block co-resident
-cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s)
+cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, unsigned* work, unsigned wcap,
+                          cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1575,7 +1557,7 @@ cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, k_rounds, jobs, njobs, bc);
+    return cudaLaunchKernelEx(&cfg, k_rounds, jobs, njobs, bc, work, wcap);
 }
 
 cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s)

@@ -790,7 +790,8 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
     pdl_enter();
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned s_warp[32];
-    __shared__ float s_klut[256], s_klutl[256];
+    __shared__ float2 s_klut[256];               // K(sqrt(d2)) as a float pair
+    __shared__ unsigned s_dmax;                  // largest |dE| staged (float bits)
     __shared__ int s_rdelta[kMaxRows];           // row offset in the pixel box
     __shared__ unsigned short s_rinfo[kMaxRows]; // rx | dy^2 + dz^2 << 8
     __shared__ int s_nrows;
@@ -832,8 +833,7 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
 
     if (tid == 0) s_osc = 0;
     for (int d2 = tid; d2 <= r2max && d2 < 256; d2 += blockDim.x) {
-        s_klut[d2] = __ldg(J.klut + d2);
-        s_klutl[d2] = __ldg(J.klut_lo + d2);
+        s_klut[d2] = make_float2(__ldg(J.klut + d2), __ldg(J.klut_lo + d2));
     }
 
     // staged pixel box: an x-slab [sx0, sx1) of the tile grown by rr (2D: z is the tile's single
@@ -928,6 +928,7 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
             }
             if (tid == 0) s_off[nbox] = (unsigned short)min(staged_total, 65535u);
             staged = staged_total <= (unsigned)kRecCap;
+            if (tid == 0) s_dmax = 0u;
             __syncthreads();
             if (staged) {
                 // pass 2: scatter. Particles of one pixel are adjacent in their cell, hence in
@@ -943,6 +944,9 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
                         p = s_cs[e] + within;
                         gi = J.p_idx[p];
                     }
+                    const unsigned dbits = v ? __float_as_uint(fabsf(J.p_dE[p])) : 0u;
+                    const unsigned wmax = __reduce_max_sync(0xffffffffu, dbits);
+                    if (lane == 0 && wmax) atomicMax(&s_dmax, wmax);
                     unsigned prev = __shfl_up_sync(0xffffffffu, gi, 1);
                     if (lane == 0 && v && within > 0) prev = J.p_idx[p - 1];
                     const bool eq = v && within > 0 && prev == gi;
@@ -1003,17 +1007,23 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
                     const unsigned j1 = s_off[base + rx + 1];
                     for (unsigned j = s_off[base - rx]; j < j1; j++) {
                         const int dx = (int)s_x[j] - lx;
-                        const int d2 = dyz2 + dx * dx;
+                        const float2 K = s_klut[dyz2 + dx * dx];
                         const Rec q = s_rec[j];
                         if (q.l == lp) {
-                            aA += fabsf(A.add(s_klut[d2], s_klutl[d2], q.dh, q.dl));
+                            A.add(K.x, K.y, q.dh, q.dl);
                             nA++;
                         } else if (q.c == lp) {
-                            aB += fabsf(B.add(s_klut[d2], s_klutl[d2], q.dh, q.dl));
+                            B.add(K.x, K.y, q.dh, q.dl);
                             nB++;
                         }
                     }
                 }
+                // the bound's sums of |K dE|: every term is at most K(0) times the largest staged
+                // |dE| (K falls with the distance; |dl| <= 2^-24 |dh|)
+                const float t_max = __fmul_rn(__fadd_rn(s_klut[0].x, s_klut[0].y),
+                                              __uint_as_float(s_dmax)) * 1.0001f;
+                aA = (float)nA * t_max;
+                aB = (float)nB * t_max;
             } else if (act && h == 0) {
                 sobolev_sums<NDIM>(J, lp, x, y, z, r2max, A, B, aA, aB, nA, nB);
             }

@@ -231,8 +231,6 @@ struct Group {
     int njobs;
     unsigned total_tiles;
     unsigned* ticket;         // extraction tile ticket
-    unsigned sel_box;         // candidate selection: label box (tile + 1 px) staged in shared memory,
-                              // in elements (the launch's dynamic shared memory / 4); 0 = read global
 };
 
 struct BatchCtl {
@@ -599,7 +597,9 @@ cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cu
 cudaError_t configure_kernels(size_t smem_x2, size_t smem_x3, size_t smem_s2, size_t smem_s3);
 cudaError_t launch_select(const Group& g, BatchCtl* bc, cudaStream_t s);
 cudaError_t launch_lists(const Job* jobs, int njobs, int sms, cudaStream_t s);
-cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s);
+// work: two lists of wcap candidate indices each (wcap >= the candidates of all jobs together)
+cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, unsigned* work, unsigned wcap,
+                          cudaStream_t s);
 cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s, bool after_split = false);
@@ -615,7 +615,6 @@ cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s);
 cudaError_t topology_tables_init();
 cudaError_t commit_occupancy(int block, int* blocks_per_sm);
 size_t extract_smem_bytes(const Job& h);
-unsigned select_box_elems(const Job& h);
 size_t sobolev_smem_bytes(const Job& h);
 cudaError_t launch_debug_simple(const unsigned* masks, int ndim, int n, unsigned char* out, cudaStream_t s);
 

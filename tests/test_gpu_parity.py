@@ -291,3 +291,24 @@ def test_split_job_in_a_batch_equals_solo():
     batch.close()
     a.close()
     b.close()
+
+
+def test_exact_ties_take_the_warp_recompute():
+    # A noise-free volume: a bright cube (300 on 100) around a smaller label cube. The particles
+    # of a flat face have translated neighbourhoods, so their gradients are equal in FP64 as in
+    # float32; every such tie is queued for the FP64 recompute, more than the recompute grid has
+    # blocks, so the one-warp-per-particle recompute runs, and the ties are broken by pixel index
+    # as the oracle breaks them.
+    D = H = W = 72
+    img = np.full((D, H, W), 100, np.uint16)
+    img[12:60, 12:60, 12:60] = 300
+    lab = np.zeros((D, H, W), np.int32)
+    lab[26:46, 26:46, 26:46] = 1
+    w = synth.Workload("ties", img, lab, "pc", 6, 1600.0, 4.0, 0.0, 6)
+    ctx, run = pair(w)
+    most = 0
+    for it in range(6):
+        st, _ = compare_step(ctx, run, f"ties it{it}")
+        most = max(most, st["n_fixup"])
+    assert most > 8 * 152, most
+    ctx.close()
