@@ -1418,45 +1418,61 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
         return;
     }
 
-    // The whole grid: round 0 visits every candidate, each later round only those the previous
-    // round left undecided (lists in `work`, appended warp by warp); a bounded grid barrier
-    // ends each round. Round r counts its list in rounds_cnt[r % 3] and clears the counter of
-    // round r + 1 before its barrier (that counter was last read right after the barrier that
-    // ended round r - 2).
+    // The whole grid, one bounded grid barrier per round. While many candidates are undecided a
+    // round visits every candidate (decided ones are skipped after one load) and the undecided
+    // are counted per block; once fewer than an eighth remain, a round also lists its undecided
+    // candidates (appended warp by warp to `work`), and the next round visits only that list.
+    // Round r counts in rounds_cnt[r % 3] and clears the counter of round r + 1 before its
+    // barrier (that counter was last read right after the barrier that ended round r - 2).
     const unsigned nblocks = gridDim.x;
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
     const unsigned lane = threadIdx.x & 31;
     unsigned rounds = 0;
-    unsigned n_cur = total;
+    unsigned n_cur = total;          // undecided after the previous round
+    bool listed = false;             // the previous round listed them in `work`
     for (unsigned r = 0;; r++) {
-        const unsigned* cur = (r & 1) ? work : work + wcap;      // round r - 1's list (r > 0)
+        const unsigned* cur = (r & 1) ? work : work + wcap;
         unsigned* nxt = (r & 1) ? work + wcap : work;
         unsigned* cnt = &bc->rounds_cnt[r % 3];
-        const unsigned span = (n_cur + gstride - 1) / gstride * gstride;   // whole warps stay in
+        const bool build = n_cur < total / 8;                  // uniform over the grid
+        const unsigned n_visit = listed ? n_cur : total;
+        const unsigned span = (n_visit + gstride - 1) / gstride * gstride;   // whole warps stay in
+        unsigned undecided = 0;
         for (unsigned t = gtid; t < span; t += gstride) {
             bool und = false;
             unsigned i = 0;
-            if (t < n_cur) {
-                i = r == 0 ? t : cur[t];
+            if (t < n_visit) {
+                i = listed ? cur[t] : t;
                 const int j = job_of(s_pref, njobs, i);
                 const Job& J = jobs[j];
                 const unsigned s = i - s_pref[j];
-                const int v = commit_decide(J, s, (const volatile int*)J.c_state, 0u);
-                if (v == kUndecided) und = true;
-                else *(volatile int*)(J.c_state + s) = v;
+                if (listed || ld_volatile(J.c_state + s) == kUndecided) {
+                    const int v = commit_decide(J, s, (const volatile int*)J.c_state, 0u);
+                    if (v == kUndecided) und = true;
+                    else *(volatile int*)(J.c_state + s) = v;
+                }
             }
-            const unsigned m = __ballot_sync(0xffffffffu, und);
-            if (m) {
-                const unsigned leader = __ffs(m) - 1;
-                unsigned base = 0;
-                if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (und) nxt[base + __popc(m & ((1u << lane) - 1u))] = i;
+            if (build) {
+                const unsigned m = __ballot_sync(0xffffffffu, und);
+                if (m) {
+                    const unsigned leader = __ffs(m) - 1;
+                    unsigned base = 0;
+                    if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (und) nxt[base + __popc(m & ((1u << lane) - 1u))] = i;
+                }
+            } else {
+                undecided += und ? 1u : 0u;
             }
+        }
+        if (!build) {
+            const unsigned bs = block_sum(undecided, s_red);
+            if (threadIdx.x == 0 && bs) atomicAdd(cnt, bs);
         }
         if (gtid == 0) bc->rounds_cnt[(r + 1) % 3] = 0;
         if (!grid_barrier(bc, nblocks)) break;
         n_cur = ld_volatile(cnt);
+        listed = build;
         if (n_cur == 0) { rounds = r + 1; break; }
         if (r + 1 >= kMaxRounds) {
             if (gtid == 0) atomicExch(&bc->err, SEG_ETIMEOUT);
