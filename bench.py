@@ -705,11 +705,11 @@ def run_served(args, world, rank, local, pg):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v1, secs, sample = _oracle_stream_sample(arrivals, keys, cache, args.cpu_seconds)
+        v1, secs, sample = _oracle_stream_sample(arrivals, keys, cache, args.cpu_seconds, iters_each=2)
         njobs = len(sample)
-        vN, cores, secsN = _oracle_all_cores(sample, iters, 5)
+        vN, cores, secsN = _oracle_all_cores(sample, iters, 2)
         cpu = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"iterations 0-4 of the stream's first {njobs} jobs in arrival order ({secs:.1f} s), "
+               "sample": f"iterations 0-1 of the stream's first {njobs} jobs in arrival order ({secs:.1f} s), "
                          "single-threaded FP64 C oracle",
                "all_cores": {"value": vN, "cores": cores, "seconds": secsN,
                              "sample": "the same jobs and iterations, one single-threaded oracle process per "

@@ -274,9 +274,14 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         v[2] = sL[si - bx];
         v[3] = sL[si + bx];
         if (NDIM == 3) { v[NDIM == 3 ? 4 : 0] = sL[si - bx * by]; v[NDIM == 3 ? 5 : 1] = sL[si + bx * by]; }
+        // interior pixels (every neighbour holds the own label or lies outside) hold no particle
+        bool any = false;
 #pragma unroll
-        for (int j = 0; j < NN; j++)
+        for (int j = 0; j < NN; j++) {
             if (v[j] < 0 || v[j] == own) v[j] = 0x7fffffff;
+            any |= v[j] != 0x7fffffff;
+        }
+        if (!any) return 0;
 #pragma unroll
         for (int r = 0; r < NN; r++)
 #pragma unroll
