@@ -465,7 +465,6 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         const int si = sidx(x, y, z);
         const int own = sL[si];
         if (fits) J.pmap[gi] = ((unsigned long long)tag << 32) | o;
-        const float v = J.model == SEG_PC ? image_at(J, gi) : 0.0f;
 #pragma unroll
         for (int j = 0; j < NN; j++) {
             if (j >= n) break;
@@ -475,11 +474,6 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 J.p_l[o] = own;
                 J.p_c[o] = c;
                 J.p_flags[o] = 0;
-                if (J.model == SEG_PC) {
-                    // the FP64 energy difference in the order of its definition, kept as a float pair
-                    const double data = data_pc64(J, (double)v, own, c);
-                    store_dE(J, o, with_length64(J, data, delta_p(si, own, c)));
-                }
             }
             o++;
         }
@@ -492,6 +486,20 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         long long cid = ((long long)(b.cz0 + lz) * J.ncy + (b.cy0 + ly)) * J.ncx + (b.cx0 + lx);
         J.cell_start[cid] = base + s_cstart[kc];
         J.cell_count[cid] = s_cstart[kc + 1] - s_cstart[kc];
+    }
+    if (J.model == SEG_PC && fits) {
+        // piecewise constant: the FP64 energy difference in the order of its definition, one
+        // particle per thread over the tile's dense range (the FP64 pipe is occupied per warp
+        // instruction, so the emitting threads' uneven particle counts would waste it)
+        for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
+            const unsigned gi = J.p_idx[o2];
+            const int own = J.p_l[o2], c = J.p_c[o2];
+            int x, y, z;
+            pix_coords(J, gi, x, y, z);
+            const double data = data_pc64(J, (double)image_at(J, gi), own, c);
+            store_dE(J, o2, with_length64(J, data, delta_p(sidx(x, y, z), own, c)));
+        }
+        return;
     }
     if (J.model == SEG_PC_DECONV && fits) {
         // deconvolving model: one particle per thread; G at the pixel (the last separable pass,
