@@ -1022,13 +1022,19 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
                         const int dx = (int)s_x[j] - lx;
                         const float2 K = s_klut[dyz2 + dx * dx];
                         const Rec q = s_rec[j];
-                        if (q.l == lp) {
-                            A.add(K.x, K.y, q.dh, q.dl);
-                            nA++;
-                        } else if (q.c == lp) {
-                            B.add(K.x, K.y, q.dh, q.dl);
-                            nB++;
-                        }
+                        // branch-free: the term goes to A (q in Q), to B (q in Q'; never both, as
+                        // l_q != c_q) or nowhere (a zero term); the lanes of a warp stay together
+                        const bool inA = q.l == lp, inB = q.c == lp;
+                        DotAcc T;
+                        T.s = inA ? A.s : B.s;
+                        T.t = inA ? A.t : B.t;
+                        T.add(K.x, K.y, (inA || inB) ? q.dh : 0.0f, (inA || inB) ? q.dl : 0.0f);
+                        A.s = inA ? T.s : A.s;
+                        A.t = inA ? T.t : A.t;
+                        B.s = inA ? B.s : T.s;
+                        B.t = inA ? B.t : T.t;
+                        nA += inA;
+                        nB += inB;
                     }
                 }
                 // the bound's sums of |K dE|: every term is at most K(0) times the largest staged
