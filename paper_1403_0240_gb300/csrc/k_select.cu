@@ -145,8 +145,12 @@ __device__ __forceinline__ int admissible_nb(const Job& J, int l, int c, Lab lab
                 mc |= (unsigned)(v == c) << k;
                 k++;
             }
-    if (c != 0 && !simple_table(mc, d)) return 0;
-    if (l == 0 || simple_table(ml, d)) return 1;
+    // both table words are loaded before either is tested, so that their latencies overlap
+    const unsigned* tab = c_simple[d];
+    const unsigned wc = c != 0 ? __ldg(tab + (mc >> 5)) : 0xffffffffu;
+    const unsigned wl = l != 0 ? __ldg(tab + (ml >> 5)) : 0xffffffffu;
+    if (!((wc >> (mc & 31u)) & 1u)) return 0;
+    if ((wl >> (ml & 31u)) & 1u) return 1;
     if (J.topo_vanish && (ml & c_topo.touch[d]) == 0) return 1;
     if (J.topo_split && components(ml & c_topo.nF[d], c_topo.adjF[d], c_topo.touch[d]) >= 2) return 2;
     return 0;

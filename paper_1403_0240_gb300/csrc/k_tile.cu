@@ -8,6 +8,7 @@
 namespace segk {
 
 constexpr int kBlock = 256;
+constexpr int kLocalCap = 512;               // particles a piecewise-constant tile keeps in shared memory
 
 __device__ __forceinline__ float image_at(const Job& J, long long i)
 {
@@ -145,6 +146,13 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
     int* sL = (int*)(smem + off_b);
     off_b = align128(off_b + (size_t)nbox * 4);
     unsigned* s_cstart = (unsigned*)(smem + off_b);
+    // piecewise constant: the tile's particles at tile-local positions (kLocalCap at most)
+    const size_t off_loc = align128(off_b + ((size_t)b.ccx * b.ccy * b.ccz + 1) * 4);
+    double* s_le = (double*)(smem + off_loc);
+    unsigned* s_lidx = (unsigned*)(s_le + kLocalCap);
+    int* s_ll = (int*)(s_lidx + kLocalCap);
+    int* s_lc = s_ll + kLocalCap;
+    __shared__ unsigned s_w1;
     __shared__ __align__(8) unsigned long long s_bar, s_bar_img;
     __shared__ int s_img_fail;
     const bool outside_box = sb.ox < 0 || sb.oy < 0 || sb.oz < 0 || sb.ox + bx > J.W || sb.oy + by > J.H ||
@@ -339,6 +347,41 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
     unsigned total;
     unsigned off = block_excl_scan(cnt, s_warp, total);
 
+    // Piecewise-constant tiles of at most kLocalCap particles: the particles are emitted into
+    // shared memory at their tile-local positions and their FP64 energy differences formed there
+    // while warp 0 resolves the tile's offset (the look-back below); warps 1.. do so for their
+    // pixels at once, warp 0 for its own after the look-back. Cell starts are tile-local anyway.
+    const bool local = J.model == SEG_PC && total <= (unsigned)kLocalCap;
+    auto emit_local = [&]() {
+        unsigned ol = off;
+        Walk wl = walk_start(q0);
+        for (int q = q0; q < q1; q++, walk_next(wl)) {
+            int x, y, z, labs[NN];
+            if (wl.rx == 0 && wl.ry == 0 && wl.rz == 0) s_cstart[(wl.lz * b.ccy + wl.ly) * b.ccx + wl.lx] = ol;
+            if (use_mask && !((busy >> ((q - q0) & 31)) & 1u)) continue;
+            if (!walk_pixel(wl, x, y, z)) continue;
+            const int n = particles_at(x, y, z, labs);
+            if (n == 0) continue;
+            const unsigned gi = (unsigned)(((long long)z * J.H + y) * J.W + x);
+            const int own = sL[sidx(x, y, z)];
+#pragma unroll
+            for (int j = 0; j < NN; j++) {
+                if (j >= n) break;
+                s_lidx[ol] = gi;
+                s_ll[ol] = own;
+                s_lc[ol] = labs[j];
+                ol++;
+            }
+        }
+    };
+    auto energy_local = [&](unsigned i) {
+        const unsigned gi = s_lidx[i];
+        const int own = s_ll[i], c = s_lc[i];
+        int x, y, z;
+        pix_coords(J, gi, x, y, z);
+        s_le[i] = with_length64(J, data_pc64(J, (double)image_at(J, gi), own, c), delta_p(sidx(x, y, z), own, c));
+    };
+
     // decoupled look-back over the tiles of this job: warp 0 inspects 32 predecessors per
     // round trip, nearest first, and stops at the first one that knows its inclusive prefix
     if (tid < 32) {
@@ -414,6 +457,12 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 if ((long long)excl + total > J.pcap) atomicMax(&ctr->need, excl + total);
             }
         }
+    } else if (local) {
+        // meanwhile warps 1.. emit their pixels' particles and form their energies locally
+        emit_local();
+        if (tid == 32) s_w1 = off;                 // warp 1's first local position
+        asm volatile("bar.sync 1, %0;" ::"r"((int)blockDim.x - 32) : "memory");
+        for (unsigned i = s_w1 + (tid - 32); i < total; i += blockDim.x - 32) energy_local(i);
     } else if (img_tma) {
         // meanwhile the other warps turn the staged image (once its copy has landed) into exact
         // fixed-point values for the piecewise-smooth ball sums
@@ -451,7 +500,37 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
     const unsigned base = s_base;
     const bool fits = (long long)base + total <= J.pcap;
 
-    // emit particles (with their energy differences for the piecewise-constant model)
+    if (local) {
+        // warp 0's own particles, then every particle to global memory at base + its position
+        if (tid < 32) {
+            emit_local();
+            __syncwarp();
+            const unsigned w1 = blockDim.x > 32 ? s_w1 : total;
+            for (unsigned i = tid; i < w1; i += 32) energy_local(i);
+        }
+        if (tid == 0) s_cstart[ncell] = total;
+        __syncthreads();
+        if (fits) {
+            for (unsigned i = tid; i < total; i += blockDim.x) {
+                const unsigned o2 = base + i, gi = s_lidx[i];
+                if (i == 0 || s_lidx[i - 1] != gi) J.pmap[gi] = ((unsigned long long)tag << 32) | o2;
+                J.p_idx[o2] = gi;
+                J.p_l[o2] = s_ll[i];
+                J.p_c[o2] = s_lc[i];
+                J.p_flags[o2] = 0;
+                store_dE(J, o2, s_le[i]);
+            }
+        }
+        for (int kc = tid; kc < ncell; kc += blockDim.x) {
+            int lx = kc % b.ccx, ly = (kc / b.ccx) % b.ccy, lz = kc / (b.ccx * b.ccy);
+            long long cid = ((long long)(b.cz0 + lz) * J.ncy + (b.cy0 + ly)) * J.ncx + (b.cx0 + lx);
+            J.cell_start[cid] = base + s_cstart[kc];
+            J.cell_count[cid] = s_cstart[kc + 1] - s_cstart[kc];
+        }
+        return;
+    }
+
+    // emit particles
     unsigned o = base + off;
     Walk wk = walk_start(q0);
     for (int q = q0; q < q1; q++, walk_next(wk)) {
@@ -674,6 +753,12 @@ size_t extract_smem_bytes(const Job& J)
     b = align128(b + nbox * 4);
     long long ncell = (long long)J.tcx * J.tcy * J.tcz;
     long long deltas = J.ps_staged ? J.ps_n : 0;
+    size_t local = 0;
+    if (J.model == SEG_PC) {        // the tile-local particles: energy f64, pixel u32, l, c i32
+        b = align128(b + (size_t)(ncell + 1) * 4);
+        local = (size_t)kLocalCap * 20;
+        return b + local + 128;
+    }
     return b + (size_t)((ncell + 1) * 4 + deltas * 4) + 128;
 }
 
