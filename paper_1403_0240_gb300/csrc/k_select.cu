@@ -640,27 +640,44 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
     Counters* ctr = J.ctr;
     if (job_idle(ctr)) return;
     const unsigned pstart = J.tile_start[k], pend = pstart + J.tile_count[k];
-    for (unsigned p = pstart + threadIdx.x; p < pend; p += blockDim.x) {
-        const unsigned gi = J.p_idx[p];
-        if (p > pstart && J.p_idx[p - 1] == gi) continue;
-        unsigned best = p;
-        double bk = J.p_key[p];
-        int bc_ = J.p_c[p];
-        for (unsigned q = p + 1; q < pend && J.p_idx[q] == gi; q++) {
-            double kq = J.p_key[q];
-            int cq = J.p_c[q];
-            if (kq < bk || (kq == bk && cq < bc_)) { best = q; bk = kq; bc_ = cq; }
+    __shared__ unsigned s_scan[32], s_slot0;
+    // the tile's candidates take one contiguous range of slots per pass (a block scan and one
+    // counter update), so that candidate indices follow the tiles: the selection rounds give each
+    // block a contiguous range of indices and so a compact region of the image
+    for (unsigned p0 = pstart; p0 < pend; p0 += blockDim.x) {          // uniform over the block
+        const unsigned p = p0 + threadIdx.x;
+        unsigned best = 0, gi = 0;
+        double bk = 0.0;
+        int bc_ = 0, adm = 0;
+        const bool first = p < pend && (p == pstart || J.p_idx[p - 1] != J.p_idx[p]);
+        if (first) {
+            gi = J.p_idx[p];
+            best = p;
+            bk = J.p_key[p];
+            bc_ = J.p_c[p];
+            for (unsigned q = p + 1; q < pend && J.p_idx[q] == gi; q++) {
+                double kq = J.p_key[q];
+                int cq = J.p_c[q];
+                if (kq < bk || (kq == bk && cq < bc_)) { best = q; bk = kq; bc_ = cq; }
+            }
+            adm = bk < 0.0 ? admissible(J, gi, J.p_l[best], bc_) : 0;
         }
-        int slot = -1;
-        const int adm = bk < 0.0 ? admissible(J, gi, J.p_l[best], bc_) : 0;
-        if (adm) {
-            slot = (int)atomicAdd(&ctr->n_cand, 1u);
-            J.c_best[slot] = (int)best;
-            J.c_key[slot] = bk;
-            J.c_pix[slot] = gi;
-            J.p_flags[best] |= adm == 2 ? (kFlagCand | kFlagSplit) : kFlagCand;
+        unsigned n_adm;
+        const unsigned rank = block_excl_scan(adm ? 1u : 0u, s_scan, n_adm);
+        if (threadIdx.x == 0) s_slot0 = n_adm ? atomicAdd(&ctr->n_cand, n_adm) : 0u;
+        __syncthreads();
+        if (first) {
+            int slot = -1;
+            if (adm) {
+                slot = (int)(s_slot0 + rank);
+                J.c_best[slot] = (int)best;
+                J.c_key[slot] = bk;
+                J.c_pix[slot] = gi;
+                J.p_flags[best] |= adm == 2 ? (kFlagCand | kFlagSplit) : kFlagCand;
+            }
+            J.pix_cand[p] = slot;
         }
-        J.pix_cand[p] = slot;
+        __syncthreads();                       // s_scan and s_slot0 are reused by the next pass
     }
 }
 
@@ -1286,8 +1303,7 @@ __global__ void __launch_bounds__(256) k_lists(const Job* jobs, int njobs)
 
 // B: the rounds. With few candidates one block runs them on shared-memory states with
 // block barriers; otherwise the whole co-resident grid runs them with bounded grid barriers.
-__global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, BatchCtl* bc, unsigned* work,
-                                                  unsigned wcap)
+__global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, BatchCtl* bc)
 {
     pdl_enter();
     __shared__ unsigned s_red[32];
@@ -1422,63 +1438,47 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
         return;
     }
 
-    // The whole grid, one bounded grid barrier per round. While many candidates are undecided a
-    // round visits every candidate (decided ones are skipped after one load) and the undecided
-    // are counted per block; once fewer than an eighth remain, a round also lists its undecided
-    // candidates (appended warp by warp to `work`), and the next round visits only that list.
-    // Round r counts in rounds_cnt[r % 3] and clears the counter of round r + 1 before its
-    // barrier (that counter was last read right after the barrier that ended round r - 2).
+    // The whole grid, one bounded grid barrier per round. Block b owns the candidate indices
+    // [lo, hi); candidates are numbered tile by tile, so that is a compact part of each image.
+    // Within a round a block sweeps its range until a sweep decides nothing more (its chains
+    // resolve without the grid), then all blocks meet; the rounds end when no candidate is
+    // undecided. Decisions are final once made and depend only on smaller-key neighbours, so the
+    // order of the sweeps does not change them. Round r counts the undecided in rounds_cnt[r % 3]
+    // and clears the counter of round r + 1 before its barrier (that counter was last read right
+    // after the barrier that ended round r - 2).
     const unsigned nblocks = gridDim.x;
-    const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
-    const unsigned lane = threadIdx.x & 31;
-    unsigned rounds = 0;
-    unsigned n_cur = total;          // undecided after the previous round
-    bool listed = false;             // the previous round listed them in `work`
+    const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned per = (total + nblocks - 1) / nblocks;
+    const unsigned lo = min(blockIdx.x * per, total), hi = min(lo + per, total);
+    unsigned rounds = 0, sweeps = 0;
     for (unsigned r = 0;; r++) {
-        const unsigned* cur = (r & 1) ? work : work + wcap;
-        unsigned* nxt = (r & 1) ? work + wcap : work;
         unsigned* cnt = &bc->rounds_cnt[r % 3];
-        const bool build = n_cur < total / 8;                  // uniform over the grid
-        const unsigned n_visit = listed ? n_cur : total;
-        const unsigned span = (n_visit + gstride - 1) / gstride * gstride;   // whole warps stay in
-        unsigned undecided = 0;
-        for (unsigned t = gtid; t < span; t += gstride) {
-            bool und = false;
-            unsigned i = 0;
-            if (t < n_visit) {
-                i = listed ? cur[t] : t;
+        unsigned undecided;
+        while (true) {
+            int changed = 0;
+            undecided = 0;
+            for (unsigned i = lo + threadIdx.x; i < hi; i += blockDim.x) {
                 const int j = job_of(s_pref, njobs, i);
                 const Job& J = jobs[j];
                 const unsigned s = i - s_pref[j];
-                if (listed || ld_volatile(J.c_state + s) == kUndecided) {
-                    const int v = commit_decide(J, s, (const volatile int*)J.c_state, 0u);
-                    if (v == kUndecided) und = true;
-                    else *(volatile int*)(J.c_state + s) = v;
+                if (ld_volatile(J.c_state + s) != kUndecided) continue;
+                const int v = commit_decide(J, s, (const volatile int*)J.c_state, 0u);
+                if (v == kUndecided) {
+                    undecided++;
+                } else {
+                    *(volatile int*)(J.c_state + s) = v;
+                    changed = 1;
                 }
             }
-            if (build) {
-                const unsigned m = __ballot_sync(0xffffffffu, und);
-                if (m) {
-                    const unsigned leader = __ffs(m) - 1;
-                    unsigned base = 0;
-                    if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (und) nxt[base + __popc(m & ((1u << lane) - 1u))] = i;
-                }
-            } else {
-                undecided += und ? 1u : 0u;
-            }
+            ++sweeps;
+            if (!__syncthreads_or(changed) || sweeps >= kMaxRounds) break;
         }
-        if (!build) {
-            const unsigned bs = block_sum(undecided, s_red);
-            if (threadIdx.x == 0 && bs) atomicAdd(cnt, bs);
-        }
+        const unsigned bs = block_sum(undecided, s_red);
+        if (threadIdx.x == 0 && bs) atomicAdd(cnt, bs);
         if (gtid == 0) bc->rounds_cnt[(r + 1) % 3] = 0;
         if (!grid_barrier(bc, nblocks)) break;
-        n_cur = ld_volatile(cnt);
-        listed = build;
-        if (n_cur == 0) { rounds = r + 1; break; }
-        if (r + 1 >= kMaxRounds) {
+        if (ld_volatile(cnt) == 0) { rounds = r + 1; break; }
+        if (r + 1 >= kMaxRounds || sweeps >= kMaxRounds) {
             if (gtid == 0) atomicExch(&bc->err, SEG_ETIMEOUT);
             break;
         }
@@ -1563,8 +1563,7 @@ cudaError_t launch_lists(const Job* jobs, int njobs, int sms, cudaStream_t s)
 }
 
 // the rounds kernel is cooperative: every block co-resident
-cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, unsigned* work, unsigned wcap,
-                          cudaStream_t s)
+cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1577,7 +1576,7 @@ cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, k_rounds, jobs, njobs, bc, work, wcap);
+    return cudaLaunchKernelEx(&cfg, k_rounds, jobs, njobs, bc);
 }
 
 cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s)

@@ -199,8 +199,6 @@ struct Stepper {
     unsigned* d_prefix = nullptr;  // group tile prefixes (2D then 3D)
     int cap_ids = 0;
     BatchCtl* d_bc = nullptr;
-    unsigned* d_work = nullptr;    // selection rounds: two lists of undecided candidates
-    long long cap_work = 0;        // ... entries per list (the members' particle capacities summed)
     Counters* d_gather = nullptr;
     Counters* h_gather = nullptr;
     int cap_gather = 0;
@@ -674,16 +672,6 @@ int stepper_build(Stepper& s)
         CK(cudaMallocHost(&s.h_gather, sizeof(Counters) * cap));
         s.cap_jobs = cap;
     }
-    long long want_work = 1;
-    for (int i = 0; i < n; i++) want_work += s.members[i]->h.pcap;
-    if (want_work > 0xffffffffLL) return SEG_EINVAL;
-    if (want_work > s.cap_work) {
-        if (s.d_work) CK(cudaFree(s.d_work));
-        s.d_work = nullptr;
-        s.cap_work = 0;
-        CK(cudaMalloc(&s.d_work, sizeof(unsigned) * 2 * (size_t)want_work));
-        s.cap_work = want_work;
-    }
     std::vector<Job> jobs(n);
     std::vector<int> ids;
     std::vector<unsigned> prefix;
@@ -803,9 +791,7 @@ cudaError_t stepper_enqueue_stages(Stepper& s)
     if ((e = stage_mark(s, 6)) != cudaSuccess) return e;
     if ((e = launch_lists(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 7)) != cudaSuccess) return e;
-    if ((e = launch_rounds(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.d_work, (unsigned)s.cap_work,
-                           s.work)) != cudaSuccess)
-        return e;
+    if ((e = launch_rounds(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 8)) != cudaSuccess) return e;
     if ((e = launch_moves(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
     if (s.any_split)                    // split regions: pieces get new labels, statistics rebuilt
@@ -849,7 +835,6 @@ void stepper_release(Stepper& s)
     if (s.d_ids) cudaFree(s.d_ids);
     if (s.d_prefix) cudaFree(s.d_prefix);
     if (s.d_bc) cudaFree(s.d_bc);
-    if (s.d_work) cudaFree(s.d_work);
     if (s.d_gather) cudaFree(s.d_gather);
     if (s.h_gather) cudaFreeHost(s.h_gather);
     for (int k = 0; k <= kStages; k++)

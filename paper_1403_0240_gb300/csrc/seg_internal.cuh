@@ -597,9 +597,7 @@ cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cu
 cudaError_t configure_kernels(size_t smem_x2, size_t smem_x3, size_t smem_s2, size_t smem_s3);
 cudaError_t launch_select(const Group& g, BatchCtl* bc, cudaStream_t s);
 cudaError_t launch_lists(const Job* jobs, int njobs, int sms, cudaStream_t s);
-// work: two lists of wcap candidate indices each (wcap >= the candidates of all jobs together)
-cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, unsigned* work, unsigned wcap,
-                          cudaStream_t s);
+cudaError_t launch_rounds(const Job* jobs, int njobs, BatchCtl* bc, int grid, int block, cudaStream_t s);
 cudaError_t launch_moves(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_finish(const Job* jobs, int njobs, BatchCtl* bc, int sms, cudaStream_t s);
 cudaError_t launch_stats_init(const Job* jobs, int j, long long npix, cudaStream_t s, bool after_split = false);
