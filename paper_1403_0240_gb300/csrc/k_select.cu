@@ -124,27 +124,16 @@ __device__ __forceinline__ bool simple_table(unsigned X, int d)
 
 // Topological control: removal from l (foreground) and addition to c (foreground)
 // must both be simple, so regions neither split, vanish, merge nor change holes. The
-// neighbourhood is read once for both labels (lab(dz, dy, dx): the label at that offset, -1
-// outside the image). With SEG_TOPO_VANISH the removal of a region's last pixel is admissible
-// too: no 4- (6-) neighbour holds l (every foreground label being one connected component).
-// With SEG_TOPO_SPLIT a removal whose foreground number is >= 2 is admissible too. Returns 0
-// (not admissible), 1, or 2 (admissible by the split rule).
-template <typename Lab>
-__device__ __forceinline__ int admissible_nb(const Job& J, int l, int c, Lab lab)
+// neighbourhood enters as two bit masks, written by extraction while it held the labels: bit k
+// of ml (mc) is set when the k-th neighbour (dz, dy, dx ascending, the centre skipped) holds l
+// (c); a neighbour outside the image holds neither. With SEG_TOPO_VANISH the removal of a
+// region's last pixel is admissible too: no 4- (6-) neighbour holds l (every foreground label
+// being one connected component). With SEG_TOPO_SPLIT a removal whose foreground number is
+// >= 2 is admissible too. Returns 0 (not admissible), 1, or 2 (admissible by the split rule).
+__device__ __forceinline__ int admissible(const Job& J, int l, int c, unsigned long long masks)
 {
     const int d = J.ndim == 3 ? 1 : 0;
-    const int rz = d;
-    unsigned ml = 0, mc = 0;
-    int k = 0;
-    for (int dz = -rz; dz <= rz; dz++)
-        for (int dy = -1; dy <= 1; dy++)
-            for (int dx = -1; dx <= 1; dx++) {
-                if (!dz && !dy && !dx) continue;
-                const int v = lab(dz, dy, dx);
-                ml |= (unsigned)(v == l) << k;
-                mc |= (unsigned)(v == c) << k;
-                k++;
-            }
+    const unsigned ml = (unsigned)masks, mc = (unsigned)(masks >> 32);
     // both table words are loaded before either is tested, so that their latencies overlap
     const unsigned* tab = c_simple[d];
     const unsigned wc = c != 0 ? __ldg(tab + (mc >> 5)) : 0xffffffffu;
@@ -154,18 +143,6 @@ __device__ __forceinline__ int admissible_nb(const Job& J, int l, int c, Lab lab
     if (J.topo_vanish && (ml & c_topo.touch[d]) == 0) return 1;
     if (J.topo_split && components(ml & c_topo.nF[d], c_topo.adjF[d], c_topo.touch[d]) >= 2) return 2;
     return 0;
-}
-
-// ... with the labels read from global memory
-__device__ __forceinline__ int admissible(const Job& J, unsigned gi, int l, int c)
-{
-    int x, y, z;
-    pix_coords(J, gi, x, y, z);
-    return admissible_nb(J, l, c, [&](int dz, int dy, int dx) {
-        const int xx = x + dx, yy = y + dy, zz = z + dz;
-        if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) return -1;
-        return J.L[((long long)zz * J.H + yy) * J.W + xx];
-    });
 }
 
 // the tabulated decision, as the selection uses it
@@ -626,6 +603,15 @@ cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cu
 // Candidates: per pixel the particle with the smallest (key, c); a candidate if its
 // key is negative and its move passes the topology tests (labels read from global memory:
 // only a minority of the tile's pixels are tested, and their neighbourhoods overlap in L1).
+// An integer image of a finite double that keeps its order: the sign bit set for x >= 0, all bits
+// flipped for x < 0 (-0 maps to the image of +0, as the two compare equal)
+__device__ __forceinline__ unsigned long long ordered_key(double k)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(k);
+    if (b == 0x8000000000000000ull) b = 0ull;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
 {
     pdl_enter();
@@ -660,7 +646,7 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
                 int cq = J.p_c[q];
                 if (kq < bk || (kq == bk && cq < bc_)) { best = q; bk = kq; bc_ = cq; }
             }
-            adm = bk < 0.0 ? admissible(J, gi, J.p_l[best], bc_) : 0;
+            adm = bk < 0.0 ? admissible(J, J.p_l[best], bc_, J.p_nbm[best]) : 0;
         }
         unsigned n_adm;
         const unsigned rank = block_excl_scan(adm ? 1u : 0u, s_scan, n_adm);
@@ -671,7 +657,7 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
             if (adm) {
                 slot = (int)(s_slot0 + rank);
                 J.c_best[slot] = (int)best;
-                J.c_key[slot] = bk;
+                J.c_key[slot] = ordered_key(bk);
                 J.c_pix[slot] = gi;
                 J.p_flags[best] |= adm == 2 ? (kFlagCand | kFlagSplit) : kFlagCand;
             }
@@ -1105,7 +1091,9 @@ cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s)
 //     (key, pixel) order, whatever the processing order;
 //  C. accepted moves update labels and the exact region sums;
 //  D. region tables, oscillation fallback, status, counters for the next iteration.
-__device__ __forceinline__ bool key_less(double ka, unsigned pa, double kb, unsigned pb)
+// The order of two (key, pixel) pairs on the keys' order-preserving integer images, so that the
+// neighbour lists compare on the integer pipes (the FP64 pipe is narrow here)
+__device__ __forceinline__ bool key_less(unsigned long long ka, unsigned pa, unsigned long long kb, unsigned pb)
 {
     return ka < kb || (ka == kb && pa < pb);
 }
@@ -1135,7 +1123,7 @@ __device__ __forceinline__ void commit_list_nd(const Job& J, unsigned s)
     constexpr int K = NDIM == 3 ? 27 : 9;
     const unsigned tag = ld_volatile(&J.ctr->iter_tag);
     const unsigned gi = J.c_pix[s];
-    const double ks = J.c_key[s];
+    const unsigned long long ks = J.c_key[s];
     int x, y, z;
     coords(J, gi, x, y, z);
     // three dependent levels (pixel map, candidate slot, key), each level's loads for all
@@ -1446,10 +1434,56 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
     // order of the sweeps does not change them. Round r counts the undecided in rounds_cnt[r % 3]
     // and clears the counter of round r + 1 before its barrier (that counter was last read right
     // after the barrier that ended round r - 2).
+    // When they fit, the range's states and rows sit in shared memory: a row entry is the local
+    // index of a neighbour inside the range, or (top bit set) the job slot of one outside it, read
+    // from global memory. Every decision is also written to global memory as it is made.
     const unsigned nblocks = gridDim.x;
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned per = (total + nblocks - 1) / nblocks;
     const unsigned lo = min(blockIdx.x * per, total), hi = min(lo + per, total);
+    const unsigned n = hi - lo;
+    volatile unsigned char* st = s_state;
+    unsigned* s_roff = (unsigned*)s_dyn;                                     // [n + 1]
+    const size_t roff_bytes = ((size_t)(n + 1) * 4 + 15) & ~(size_t)15;
+    unsigned* s_ent = (unsigned*)(s_dyn + roff_bytes);
+    bool cache = n <= kSmallCandidates && roff_bytes <= kRoundsDyn;          // uniform over the block
+    if (cache) {
+        for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+            const int j = job_of(s_pref, njobs, lo + i);
+            s_roff[i] = (unsigned)jobs[j].c_nnbr[lo + i - s_pref[j]];
+            st[i] = kUndecided;
+        }
+        __syncthreads();
+        const unsigned chunk = (n + blockDim.x - 1) / blockDim.x;
+        const unsigned c0 = min(threadIdx.x * chunk, n), c1 = min(c0 + chunk, n);
+        unsigned mine = 0;
+        for (unsigned i = c0; i < c1; i++) mine += s_roff[i];
+        unsigned all_nb;
+        unsigned o = block_excl_scan(mine, s_red, all_nb);
+        cache = roff_bytes + (size_t)all_nb * 4 <= kRoundsDyn;
+        if (cache) {
+            for (unsigned i = c0; i < c1; i++) {
+                const unsigned c = s_roff[i];
+                s_roff[i] = o;
+                o += c;
+            }
+            if (threadIdx.x == 0) s_roff[n] = all_nb;
+        }
+        __syncthreads();
+        if (cache)
+            for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+                const int j = job_of(s_pref, njobs, lo + i);
+                const Job& J = jobs[j];
+                const int* nb = J.c_nbr + (long long)(lo + i - s_pref[j]) * J.nbr_stride;
+                const unsigned e0 = s_roff[i], e1 = s_roff[i + 1];
+                for (unsigned k = e0; k < e1; k++) {
+                    const unsigned slot = (unsigned)nb[k - e0];
+                    const unsigned loc = s_pref[j] + slot - lo;
+                    s_ent[k] = loc < n ? loc : (slot | 0x80000000u);
+                }
+            }
+        __syncthreads();
+    }
     unsigned rounds = 0, sweeps = 0;
     for (unsigned r = 0;; r++) {
         unsigned* cnt = &bc->rounds_cnt[r % 3];
@@ -1457,16 +1491,35 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
         while (true) {
             int changed = 0;
             undecided = 0;
-            for (unsigned i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const int j = job_of(s_pref, njobs, i);
-                const Job& J = jobs[j];
-                const unsigned s = i - s_pref[j];
-                if (ld_volatile(J.c_state + s) != kUndecided) continue;
-                const int v = commit_decide(J, s, (const volatile int*)J.c_state, 0u);
+            for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+                int v;
+                if (cache) {
+                    if (st[i] != kUndecided) continue;
+                    bool all_rej = true, rej = false;
+                    for (unsigned k = s_roff[i], e = s_roff[i + 1]; k < e; k++) {
+                        const unsigned en = s_ent[k];
+                        int u;
+                        if (en & 0x80000000u) {
+                            const Job& J = jobs[job_of(s_pref, njobs, lo + i)];
+                            u = ld_volatile(J.c_state + (en & 0x7fffffffu));
+                        } else {
+                            u = st[en];
+                        }
+                        if (u == kAccepted) { rej = true; break; }
+                        if (u != kRejected) all_rej = false;
+                    }
+                    v = rej ? kRejected : (all_rej ? kAccepted : kUndecided);
+                    if (v != kUndecided) st[i] = (unsigned char)v;
+                } else {
+                    const int j = job_of(s_pref, njobs, lo + i);
+                    if (ld_volatile(jobs[j].c_state + (lo + i - s_pref[j])) != kUndecided) continue;
+                    v = commit_decide(jobs[j], lo + i - s_pref[j], (const volatile int*)jobs[j].c_state, 0u);
+                }
                 if (v == kUndecided) {
                     undecided++;
                 } else {
-                    *(volatile int*)(J.c_state + s) = v;
+                    const int j = job_of(s_pref, njobs, lo + i);
+                    *(volatile int*)(jobs[j].c_state + (lo + i - s_pref[j])) = v;
                     changed = 1;
                 }
             }

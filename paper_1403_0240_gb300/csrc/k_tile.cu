@@ -317,6 +317,25 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
         }
         return n;
     };
+    // the topology masks of a particle: bit k of the low (high) word is set when the k-th of the
+    // 8 (26) neighbours, (dz, dy, dx) ascending without the centre, holds own (c); -1 outside
+    auto nb_masks = [&](int si, int own, int c) -> unsigned long long {
+        unsigned ml = 0, mc = 0;
+        int kb = 0;
+#pragma unroll
+        for (int dz = -(NDIM == 3 ? 1 : 0); dz <= (NDIM == 3 ? 1 : 0); dz++)
+#pragma unroll
+            for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+                for (int dx = -1; dx <= 1; dx++) {
+                    if (dz == 0 && dy == 0 && dx == 0) continue;
+                    const int v = sL[si + (dz * by + dy) * bx + dx];
+                    ml |= (unsigned)(v == own) << kb;
+                    mc |= (unsigned)(v == c) << kb;
+                    kb++;
+                }
+        return (unsigned long long)ml | ((unsigned long long)mc << 32);
+    };
     // change of the number of unlike neighbour pairs when the pixel goes from own to c
     auto delta_p = [&](int si, int own, int c) -> int {
         int nb[NN];
@@ -519,6 +538,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
                 J.p_c[o2] = s_lc[i];
                 J.p_flags[o2] = 0;
                 store_dE(J, o2, s_le[i]);
+                int x, y, z;
+                pix_coords(J, gi, x, y, z);
+                J.p_nbm[o2] = nb_masks(sidx(x, y, z), s_ll[i], s_lc[i]);
             }
         }
         for (int kc = tid; kc < ncell; kc += blockDim.x) {
@@ -575,11 +597,20 @@ __global__ void __launch_bounds__(kBlock, 5) k_extract(Group g)
             const int own = J.p_l[o2], c = J.p_c[o2];
             int x, y, z;
             pix_coords(J, gi, x, y, z);
+            const int si = sidx(x, y, z);
+            J.p_nbm[o2] = nb_masks(si, own, c);
             const double data = data_pc64(J, (double)image_at(J, gi), own, c);
-            store_dE(J, o2, with_length64(J, data, delta_p(sidx(x, y, z), own, c)));
+            store_dE(J, o2, with_length64(J, data, delta_p(si, own, c)));
         }
         return;
     }
+    // the other models: the topology masks in a pass of their own, one particle per thread
+    if (fits)
+        for (unsigned o2 = base + tid; o2 < base + total; o2 += blockDim.x) {
+            int x, y, z;
+            pix_coords(J, J.p_idx[o2], x, y, z);
+            J.p_nbm[o2] = nb_masks(sidx(x, y, z), J.p_l[o2], J.p_c[o2]);
+        }
     if (J.model == SEG_PC_DECONV && fits) {
         // deconvolving model: one particle per thread; G at the pixel (the last separable pass,
         // FP64), then the FP64 energy difference

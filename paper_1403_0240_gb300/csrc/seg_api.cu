@@ -554,6 +554,7 @@ size_t particle_bytes(long long pcap, int stride)
     A.add(&h.p_g, pcap);
     A.add(&h.p_eg, pcap);
     A.add(&h.p_key, pcap);
+    A.add(&h.p_nbm, pcap);
     A.add(&h.p_flags, pcap);
     A.add(&h.p_qc, pcap);
     A.add(&h.p_ql, pcap);
@@ -583,6 +584,7 @@ void assign_particles(Job& h, char* base, long long pcap)
     A.add(&h.p_g, pcap);
     A.add(&h.p_eg, pcap);
     A.add(&h.p_key, pcap);
+    A.add(&h.p_nbm, pcap);
     A.add(&h.p_flags, pcap);
     A.add(&h.p_qc, pcap);
     A.add(&h.p_ql, pcap);

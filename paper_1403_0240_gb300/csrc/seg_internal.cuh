@@ -188,6 +188,7 @@ struct alignas(64) Job {
     float* p_g;
     float* p_eg;
     double* p_key;
+    unsigned long long* p_nbm;   // topology masks: neighbours holding l (low word) and c (high word)
     unsigned char* p_flags;
     long long* p_qc;          // piecewise smooth with exact sums: sum of q(I) over the c part of the ball
     long long* p_ql;          //   ... over the own-label part
@@ -215,7 +216,7 @@ struct alignas(64) Job {
     float* wp32;
     float* wm32;
     int* c_best;              // candidate -> particle
-    double* c_key;
+    unsigned long long* c_key;    // the candidate's key as an order-preserving integer (ordered_key)
     unsigned* c_pix;
     int* c_state;
     int* c_nbr;               // smaller-key neighbouring candidates, nbr_stride slots per candidate
