@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Sobolev particle-iterations/s"
 UNIT = "particle-iterations/s"
-STAGES = ("psf", "extract", "sobolev", "flag", "fixup", "select", "lists", "rounds", "moves", "finish")
+STAGES = ("psf", "extract", "sobolev", "select", "lists", "fixup", "rounds", "moves", "finish")
 L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic bytes per unit (one particle, or one accepted move) of each stage: the
@@ -50,9 +50,9 @@ L2_FLUSH_BYTES = 256 << 20
 #   extract = particle write (idx, l, c: 12 B) + amortised label-band reads (8 B)
 #           + image value (4 B) + energy difference out (4 B)
 #   sobolev = particle in (idx, l, c, dE: 16 B) + gradient out (4 B)
-#   flag, fixup, select, lists, rounds = 12 B per particle (a particle read per decision stage);
+#   select, lists, fixup, rounds = 12 B per particle (a particle read per decision stage);
 #   moves = 24 B per accepted move (label write and statistics); finish = 12 B per particle
-ALG_BYTES = {"extract": (28, 0), "sobolev": (20, 0), "flag": (12, 0), "fixup": (12, 0),
+ALG_BYTES = {"extract": (28, 0), "sobolev": (20, 0), "fixup": (12, 0),
              "select": (12, 0), "lists": (12, 0), "rounds": (12, 0), "moves": (0, 24), "finish": (12, 0)}
 
 
@@ -82,9 +82,9 @@ def workloads():
 
 
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64, nominal
-# kernels of one iteration's graph: extract, sobolev, flag, fixup, select, lists, rounds, moves,
-# finish (plus the deconvolving model's field passes); poll() adds one
-KERNELS_PER_ITERATION = 9
+# kernels of one iteration's graph: extract, sobolev, select, lists, fixup, rounds, moves, finish
+# (plus the deconvolving model's field passes); poll() adds one
+KERNELS_PER_ITERATION = 8
 # opt-in events and regulariser: kernels each adds to an iteration (the connected-component
 # relabelling of splits with its statistics rebuild; the fusion pairs, matching and relabelling;
 # the curvature term)

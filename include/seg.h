@@ -249,10 +249,12 @@ int seg_step_async(seg_ctx* c, int32_t iters);
 int seg_poll(seg_ctx* c, seg_status* out);
 
 /* Stage timing: when on, the captured iteration graph also records CUDA events
- * between its stages (psf, extract, sobolev, flag, fixup, select, lists, rounds, moves,
- * finish; psf is the deconvolving model's field passes, empty for the other models);
- * seg_stage_times waits for the stream and writes the milliseconds each stage took in the
- * most recent iteration (n >= 10), returning SEG_ESTATE when timing is off. */
+ * between its stages (psf, extract, sobolev, select, lists, fixup, rounds, moves, finish;
+ * psf is the deconvolving model's field passes, empty for the other models; lists includes
+ * the order certificates of neighbouring candidates, fixup the FP64 recompute of the keys
+ * they did not certify); seg_stage_times waits for the stream and writes the milliseconds
+ * each stage took in the most recent iteration (n >= 9), returning SEG_ESTATE when timing
+ * is off. */
 int seg_profile(seg_ctx* c, int32_t on);
 int seg_stage_times(seg_ctx* c, float* ms, int32_t n);
 
@@ -293,7 +295,7 @@ int seg_batch_step(seg_batch* b, int32_t iters, seg_status* statuses, int32_t n_
 int seg_batch_step_async(seg_batch* b, int32_t iters);
 /* Per-stage CUDA events of the batch's iteration, as seg_profile / seg_stage_times for one
  * context (the events serialise the stage launches, so profiled steps run slower): ms
- * (n >= 10) receives the milliseconds each of the ten stages took in the batch's most recent
+ * (n >= 9) receives the milliseconds each of the nine stages took in the batch's most recent
  * iteration, over all members together. */
 int seg_batch_profile(seg_batch* b, int32_t on);
 int seg_batch_stage_times(seg_batch* b, float* ms, int32_t n);

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kBlock) k_sobolev_global(Group g)
             const float gp = pair_sub(Aq, Al, Bq, Bl);
             J.p_g[p] = gp;
             J.p_eg[p] = pair_bound(gp, nA, nA ? aA / (float)nA : 0.f, nB, nB ? aB / (float)nB : 0.f);
+            J.p_key[p] = (double)gp;
             const float Af = __fadd_rn(Aq, Al), Bf = __fadd_rn(Bq, Bl);
             osc += (Af != 0.f && Bf != 0.f && ((Af > 0.f) == (Bf > 0.f))) ? 1u : 0u;
         }

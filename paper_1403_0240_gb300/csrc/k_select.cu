@@ -171,12 +171,18 @@ __device__ __forceinline__ void coords(const Job& J, unsigned gi, int& x, int& y
     pix_coords(J, gi, x, y, z);
 }
 
-// Certification: a particle that could be negative (g < eg) is queued for the FP64
-// recompute when its sign, or its order against any other possibly-negative particle
-// at Chebyshev distance <= 1, is not certified by the bounds. In the Sobolev modes particles
-// of one pixel share their label, hence both sets of Eq. 6 and the gradient, bit for bit on
-// both sides, so their order is that of c and needs no certificate (in L2 mode their
-// gradients are their own energy differences and are compared like the others).
+// Certification. A decision takes the float gradient g in place of the FP64 key wherever the
+// bound eg (|g - key| <= eg) makes that safe:
+//  - candidacy needs key < 0. The best particle of a pixel becomes a candidate when g < eg
+//    (possibly negative); when moreover |g| <= eg its sign is uncertain and it is queued for the
+//    FP64 recompute, after which a key >= 0 drops it (it enters the rounds rejected);
+//  - the rounds need the order of neighbouring candidates. Two candidates whose gradients lie
+//    within the sum of their bounds are both queued (each finds the other while listing its
+//    neighbours), and their lists are rebuilt once every queued key is exact. Any other pair
+//    keeps its order: an exact key stays within its bound of the float it replaces.
+// In the Sobolev modes the particles of one pixel share their label, hence both sets of Eq. 6
+// and the gradient, so the best particle of a pixel is the one of smallest c, without a
+// certificate; in L2 mode the key is the FP64 energy difference itself, exact (bound 0).
 //
 // The comparisons run in float32: with d = fl(gp - gq) and s = fl(ep + eq), each within one
 // rounding, |gp - gq| <= ep + eq implies |d| <= s (1 + 2^-22), so a pair is queued whenever
@@ -186,59 +192,12 @@ __device__ __forceinline__ bool order_uncertain(float gp, float ep, float gq, fl
     return fabsf(__fsub_rn(gp, gq)) <= __fmul_rn(__fadd_rn(ep, eq), 1.00000024f);
 }
 
-__global__ void __launch_bounds__(256) k_flag(Group g)
+// queue candidate slot s of job J for the FP64 recompute
+__device__ __forceinline__ void queue_fixup(const Job& J, unsigned s, unsigned p)
 {
-    pdl_enter();
-    const unsigned t = blockIdx.x;
-    const int gj = group_job_of_tile(g, t);
-    const Job& J = g.jobs[g.job_ids[gj]];
-    const unsigned k = t - g.tile_prefix[gj];
-    Counters* ctr = J.ctr;
-    if (job_idle(ctr)) return;
-    const unsigned pstart = J.tile_start[k], pcount = J.tile_count[k];
-    const unsigned tag = ld_volatile(&ctr->iter_tag);
-    const unsigned np = ld_volatile(&ctr->n_particles);
-    const bool same_g_per_pixel = ld_volatile(&ctr->mode) != SEG_L2;
-    const int rz = J.ndim == 3 ? 1 : 0;
-    for (unsigned i = threadIdx.x; i < pcount; i += blockDim.x) {
-        const unsigned p = pstart + i;
-        const float gp = J.p_g[p], ep = J.p_eg[p];
-        J.p_key[p] = (double)gp;
-        if (!(gp < ep)) continue;
-        bool flag = fabsf(gp) <= ep;
-        if (!flag) {
-            int x, y, z;
-            coords(J, J.p_idx[p], x, y, z);
-            for (int dz = -rz; dz <= rz && !flag; dz++)
-                for (int dy = -1; dy <= 1 && !flag; dy++)
-                    for (int dx = -1; dx <= 1 && !flag; dx++) {
-                        int xx = x + dx, yy = y + dy, zz = z + dz;
-                        if (xx < 0 || xx >= J.W || yy < 0 || yy >= J.H || zz < 0 || zz >= J.D) continue;
-                        const bool own_pixel = dx == 0 && dy == 0 && dz == 0;
-                        if (own_pixel && same_g_per_pixel) continue;
-                        unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
-                        unsigned long long e = J.pmap[yi];
-                        if ((unsigned)(e >> 32) != tag) continue;
-                        for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi; q++) {
-                            if (q == p) continue;
-                            float gq = J.p_g[q], eq = J.p_eg[q];
-                            if (!(gq < eq)) continue;
-                            if (order_uncertain(gp, ep, gq, eq)) { flag = true; break; }
-                        }
-                    }
-        }
-        if (flag) {
-            J.p_flags[p] |= kFlagFixup;
-            unsigned slot = atomicAdd(&ctr->n_flag, 1u);
-            J.flag_list[slot] = p;
-        }
-    }
-}
-
-cudaError_t launch_flag(const Group& g, cudaStream_t s)
-{
-    if (g.total_tiles == 0) return cudaSuccess;
-    return launch_stage(k_flag, g.total_tiles, 256, 0, s, g);
+    J.p_flags[p] |= kFlagFixup;
+    const unsigned f = atomicAdd(&J.ctr->n_flag, 1u);
+    J.flag_list[f] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -333,6 +292,29 @@ __device__ __forceinline__ int block_excl(int v, int* s_w, int* total)
     return before + x - v;
 }
 
+// An integer image of a finite double that keeps its order: the sign bit set for x >= 0, all bits
+// flipped for x < 0 (-0 maps to the image of +0, as the two compare equal)
+__device__ __forceinline__ unsigned long long ordered_key(double k)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(k);
+    if (b == 0x8000000000000000ull) b = 0ull;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// The FP64 key of queued candidate slot s (particle p) replaces its float one: exact from now
+// on (bound 0); a key >= 0 drops the candidate, which then enters the rounds rejected.
+__device__ __forceinline__ void fix_apply(const Job& J, unsigned s, unsigned p, double key)
+{
+    J.p_key[p] = key;
+    J.c_key[s] = ordered_key(key);
+    J.c_ge[s] = make_float2(0.0f, 0.0f);
+    if (!(key < 0.0)) {
+        J.c_state[s] = kRejected;
+        J.p_flags[p] &= (unsigned char)~(kFlagCand | kFlagSplit);
+        atomicAdd(&J.ctr->n_void, 1u);
+    }
+}
+
 // E = |Gamma| mode: the FP64 key of particle (gi, lp) over every particle with d^2 < g_lim, in
 // ascending key order (the pixels of the support's bounding box in row-major order, particles
 // of a pixel in order); one warp walks the box, t_w / a_w hold 192 terms. Lane 0's value counts.
@@ -421,16 +403,17 @@ __device__ void fixup_warps(const Job* jobs, int njobs, unsigned total, const un
         const unsigned tag = ld_volatile(&ctr->iter_tag);
         const unsigned np = ld_volatile(&ctr->n_particles);
         const int mode = ld_volatile(&ctr->mode);
-        const unsigned p = J.flag_list[fi - s_pref[j]];
+        const unsigned sl = J.flag_list[fi - s_pref[j]];
+        const unsigned p = (unsigned)J.c_best[sl];
         const unsigned gi = J.p_idx[p];
         const int lp = J.p_l[p], cp = J.p_c[p];
         if (mode == SEG_L2) {
-            if (lane == 0) J.p_key[p] = J.p_dE64[p];
+            if (lane == 0) fix_apply(J, sl, p, J.p_dE64[p]);
             continue;
         }
         if (mode == SEG_SOBOLEV_GLOBAL) {
             const double gval = fix_global_warp(J, gi, lp, tag, np, t_w, a_w);
-            if (lane == 0) J.p_key[p] = gval;
+            if (lane == 0) fix_apply(J, sl, p, gval);
             continue;
         }
         int x, y, z;
@@ -484,105 +467,9 @@ __device__ void fixup_warps(const Job* jobs, int njobs, unsigned total, const un
         if (lane == 0) {
             const double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
             const double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
-            J.p_key[p] = __dsub_rn(A, B);
+            fix_apply(J, sl, p, __dsub_rn(A, B));
         }
     }
-}
-
-// FP64 recompute of the queued particles' keys in the order of the definition, one block per
-// particle: every thread takes one interaction offset (row-major, i.e. ascending pixel) and
-// the particles of that pixel in order, so that the dependent loads of all offsets overlap;
-// one thread then sums the terms in ascending key order.
-__global__ void __launch_bounds__(kFixThreads) k_fixup(const Job* jobs, int njobs)
-{
-    pdl_enter();
-    __shared__ double s_t[kFixTerms];
-    __shared__ unsigned char s_a[kFixTerms];
-    __shared__ unsigned s_pref[kMaxBatchJobs + 1];
-    __shared__ unsigned s_tmp[32];
-    __shared__ int s_w[kFixThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const unsigned total = block_job_prefix(jobs, njobs, kCountFlag, s_pref, s_tmp);
-    if (total > gridDim.x) {                   // many queued particles: one per warp
-        fixup_warps(jobs, njobs, total, s_pref, s_t, s_a);
-        return;
-    }
-    for (unsigned fi = blockIdx.x; fi < total; fi += gridDim.x) {
-        const int j = job_of(s_pref, njobs, fi);
-        const Job& J = jobs[j];
-        Counters* ctr = J.ctr;
-        const unsigned f = fi - s_pref[j];
-        const unsigned tag = ld_volatile(&ctr->iter_tag);
-        const unsigned np = ld_volatile(&ctr->n_particles);
-        const int mode = ld_volatile(&ctr->mode);
-        const unsigned p = J.flag_list[f];
-        const unsigned gi = J.p_idx[p];
-        const int lp = J.p_l[p], cp = J.p_c[p];
-        if (mode == SEG_L2) {
-            if (tid == 0) J.p_key[p] = J.p_dE64[p];
-        } else if (mode == SEG_SOBOLEV_GLOBAL) {
-            if (w == 0) {
-                const double gval = fix_global_warp(J, gi, lp, tag, np, s_t, s_a);
-                if (lane == 0) J.p_key[p] = gval;
-            }
-        } else {
-            int x, y, z;
-            coords(J, gi, x, y, z);
-            double As = 0.0, Bs = 0.0;
-            long long nA = 0, nB = 0;
-            for (int base = 0; base < J.nb_n; base += kFixThreads) {
-                const int u = base + tid;
-                double tv[6];
-                unsigned char ta[6];
-                int nt = 0;
-                if (u < J.nb_n) {
-                    const int4 d = J.nb_off[u];
-                    const int xx = x + d.z, yy = y + d.y, zz = z + d.x;
-                    if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D) {
-                        const unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
-                        const unsigned long long e = J.pmap[yi];
-                        if ((unsigned)(e >> 32) == tag) {
-                            const double K = J.klut64[d.w];
-                            for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi && nt < 6; q++) {
-                                const int lq = J.p_l[q], cq = J.p_c[q];
-                                if (lq == lp || cq == lp) {
-                                    tv[nt] = __dmul_rn(K, J.p_dE64[q]);
-                                    ta[nt] = lq == lp ? 1 : 0;
-                                    nt++;
-                                }
-                            }
-                        }
-                    }
-                }
-                int tot;
-                const int pos = block_excl(nt, s_w, &tot);
-                for (int i = 0; i < nt; i++) {
-                    s_t[pos + i] = tv[i];
-                    s_a[pos + i] = ta[i];
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    for (int i = 0; i < tot; i++) {
-                        if (s_a[i]) { As = __dadd_rn(As, s_t[i]); nA++; }
-                        else { Bs = __dadd_rn(Bs, s_t[i]); nB++; }
-                    }
-                }
-                __syncthreads();
-            }
-            if (tid == 0) {
-                const double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
-                const double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
-                J.p_key[p] = __dsub_rn(A, B);
-            }
-        }
-        __syncthreads();
-    }
-}
-
-cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s)
-{
-    if (njobs <= 0) return cudaSuccess;
-    return launch_stage(k_fixup, sms * 8, kFixThreads, 0, s, jobs, njobs);
 }
 
 __global__ void k_gather_counters(const Job* jobs, int njobs, Counters* out)
@@ -603,15 +490,6 @@ cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cu
 // Candidates: per pixel the particle with the smallest (key, c); a candidate if its
 // key is negative and its move passes the topology tests (labels read from global memory:
 // only a minority of the tile's pixels are tested, and their neighbourhoods overlap in L1).
-// An integer image of a finite double that keeps its order: the sign bit set for x >= 0, all bits
-// flipped for x < 0 (-0 maps to the image of +0, as the two compare equal)
-__device__ __forceinline__ unsigned long long ordered_key(double k)
-{
-    unsigned long long b = (unsigned long long)__double_as_longlong(k);
-    if (b == 0x8000000000000000ull) b = 0ull;
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-
 __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
 {
     pdl_enter();
@@ -626,6 +504,7 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
     Counters* ctr = J.ctr;
     if (job_idle(ctr)) return;
     const unsigned pstart = J.tile_start[k], pend = pstart + J.tile_count[k];
+    const bool exact_keys = ld_volatile(&ctr->mode) == SEG_L2;
     __shared__ unsigned s_scan[32], s_slot0;
     // the tile's candidates take one contiguous range of slots per pass (a block scan and one
     // counter update), so that candidate indices follow the tiles: the selection rounds give each
@@ -634,6 +513,7 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
         const unsigned p = p0 + threadIdx.x;
         unsigned best = 0, gi = 0;
         double bk = 0.0;
+        float bg = 0.0f, be = 0.0f;
         int bc_ = 0, adm = 0;
         const bool first = p < pend && (p == pstart || J.p_idx[p - 1] != J.p_idx[p]);
         if (first) {
@@ -646,7 +526,11 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
                 int cq = J.p_c[q];
                 if (kq < bk || (kq == bk && cq < bc_)) { best = q; bk = kq; bc_ = cq; }
             }
-            adm = bk < 0.0 ? admissible(J, J.p_l[best], bc_, J.p_nbm[best]) : 0;
+            // the candidate's float gradient and bound (exact keys: bound 0)
+            bg = exact_keys ? 0.0f : J.p_g[best];
+            be = exact_keys ? 0.0f : J.p_eg[best];
+            const bool maybe_neg = exact_keys ? bk < 0.0 : bg < be;
+            adm = maybe_neg ? admissible(J, J.p_l[best], bc_, J.p_nbm[best]) : 0;
         }
         unsigned n_adm;
         const unsigned rank = block_excl_scan(adm ? 1u : 0u, s_scan, n_adm);
@@ -659,7 +543,9 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
                 J.c_best[slot] = (int)best;
                 J.c_key[slot] = ordered_key(bk);
                 J.c_pix[slot] = gi;
+                J.c_ge[slot] = make_float2(bg, be);
                 J.p_flags[best] |= adm == 2 ? (kFlagCand | kFlagSplit) : kFlagCand;
+                if (!exact_keys && fabsf(bg) <= be) queue_fixup(J, (unsigned)slot, best);   // sign uncertain
             }
             J.pix_cand[p] = slot;
         }
@@ -1117,7 +1003,7 @@ constexpr size_t kRoundsDyn = 160 * 1024;      // dynamic shared memory of the r
 // A: neighbour lists of smaller-key candidates; states reset
 // Neighbour positions by compile-time index (dz, dy, dx ascending, the centre skipped), so
 // that the per-neighbour arrays stay in registers.
-template <int NDIM>
+template <int NDIM, bool kCertify>
 __device__ __forceinline__ void commit_list_nd(const Job& J, unsigned s)
 {
     constexpr int K = NDIM == 3 ? 27 : 9;
@@ -1142,20 +1028,38 @@ __device__ __forceinline__ void commit_list_nd(const Job& J, unsigned s)
 #pragma unroll
     for (int t = 0; t < K; t++)
         slot[t] = ((in >> t) & 1u) && (unsigned)(e[t] >> 32) == tag ? J.pix_cand[(unsigned)e[t]] : -1;
+    const float2 gs = kCertify ? J.c_ge[s] : make_float2(0.0f, 0.0f);
+    bool uncertain = false;
     int n = 0;
 #pragma unroll
     for (int t = 0; t < K; t++) {
         const int o = slot[t];
-        if (o >= 0 && key_less(J.c_key[o], J.c_pix[o], ks, gi)) J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
+        if (o < 0) continue;
+        if (key_less(J.c_key[o], J.c_pix[o], ks, gi)) J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
+        if (kCertify && gs.y > 0.0f) {
+            const float2 go = J.c_ge[o];
+            uncertain |= order_uncertain(gs.x, gs.y, go.x, go.y);
+        }
     }
     J.c_nnbr[s] = n;
     J.c_state[s] = kUndecided;
+    if (kCertify && uncertain) {
+        const unsigned p = (unsigned)J.c_best[s];
+        if (!(J.p_flags[p] & kFlagFixup)) queue_fixup(J, s, p);   // not already queued for its sign
+    }
 }
 
 __device__ __forceinline__ void commit_list_one(const Job& J, unsigned s)
 {
-    if (J.ndim == 3) commit_list_nd<3>(J, s);
-    else commit_list_nd<2>(J, s);
+    if (J.ndim == 3) commit_list_nd<3, true>(J, s);
+    else commit_list_nd<2, true>(J, s);
+}
+
+// the list of a candidate whose key the FP64 recompute replaced (no certificate needed)
+__device__ __forceinline__ void relist_one(const Job& J, unsigned s)
+{
+    if (J.ndim == 3) commit_list_nd<3, false>(J, s);
+    else commit_list_nd<2, false>(J, s);
 }
 
 // B: one decision for candidate s of job J on state array st (offset b); returns the new
@@ -1255,7 +1159,7 @@ __device__ void commit_job_status(const Job& J, bool ok, unsigned rounds, int er
     if (used == SEG_L2 && A == 0) c->converged = 1;
     c->last.iteration = c->t;
     c->last.n_particles = c->n_particles;
-    c->last.n_candidates = c->n_cand;
+    c->last.n_candidates = c->n_cand - c->n_void;
     c->last.n_accepted = A;
     c->last.n_osc = used != SEG_L2 ? c->n_osc : 0;
     c->last.n_fixup = c->n_flag;
@@ -1271,9 +1175,106 @@ __device__ void commit_job_status(const Job& J, bool ok, unsigned rounds, int er
     c->n_split = 0;
     c->n_newcomp = 0;
     c->n_cand = 0;
+    c->n_void = 0;
     c->n_accepted = 0;
     c->n_osc = 0;
     c->skip = c->converged;
+}
+
+// FP64 recompute of the queued particles' keys in the order of the definition, one block per
+// particle: every thread takes one interaction offset (row-major, i.e. ascending pixel) and
+// the particles of that pixel in order, so that the dependent loads of all offsets overlap;
+// one thread then sums the terms in ascending key order.
+__global__ void __launch_bounds__(kFixThreads) k_fixup(const Job* jobs, int njobs)
+{
+    pdl_enter();
+    __shared__ double s_t[kFixTerms];
+    __shared__ unsigned char s_a[kFixTerms];
+    __shared__ unsigned s_pref[kMaxBatchJobs + 1];
+    __shared__ unsigned s_tmp[32];
+    __shared__ int s_w[kFixThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned total = block_job_prefix(jobs, njobs, kCountFlag, s_pref, s_tmp);
+    if (total > gridDim.x) {                   // many queued particles: one per warp
+        fixup_warps(jobs, njobs, total, s_pref, s_t, s_a);
+    } else
+    for (unsigned fi = blockIdx.x; fi < total; fi += gridDim.x) {
+        const int j = job_of(s_pref, njobs, fi);
+        const Job& J = jobs[j];
+        Counters* ctr = J.ctr;
+        const unsigned f = fi - s_pref[j];
+        const unsigned tag = ld_volatile(&ctr->iter_tag);
+        const unsigned np = ld_volatile(&ctr->n_particles);
+        const int mode = ld_volatile(&ctr->mode);
+        const unsigned sl = J.flag_list[f];
+        const unsigned p = (unsigned)J.c_best[sl];
+        const unsigned gi = J.p_idx[p];
+        const int lp = J.p_l[p], cp = J.p_c[p];
+        if (mode == SEG_L2) {
+            if (tid == 0) fix_apply(J, sl, p, J.p_dE64[p]);
+        } else if (mode == SEG_SOBOLEV_GLOBAL) {
+            if (w == 0) {
+                const double gval = fix_global_warp(J, gi, lp, tag, np, s_t, s_a);
+                if (lane == 0) fix_apply(J, sl, p, gval);
+            }
+        } else {
+            int x, y, z;
+            coords(J, gi, x, y, z);
+            double As = 0.0, Bs = 0.0;
+            long long nA = 0, nB = 0;
+            for (int base = 0; base < J.nb_n; base += kFixThreads) {
+                const int u = base + tid;
+                double tv[6];
+                unsigned char ta[6];
+                int nt = 0;
+                if (u < J.nb_n) {
+                    const int4 d = J.nb_off[u];
+                    const int xx = x + d.z, yy = y + d.y, zz = z + d.x;
+                    if (xx >= 0 && xx < J.W && yy >= 0 && yy < J.H && zz >= 0 && zz < J.D) {
+                        const unsigned yi = (unsigned)(((long long)zz * J.H + yy) * J.W + xx);
+                        const unsigned long long e = J.pmap[yi];
+                        if ((unsigned)(e >> 32) == tag) {
+                            const double K = J.klut64[d.w];
+                            for (unsigned q = (unsigned)e; q < np && J.p_idx[q] == yi && nt < 6; q++) {
+                                const int lq = J.p_l[q], cq = J.p_c[q];
+                                if (lq == lp || cq == lp) {
+                                    tv[nt] = __dmul_rn(K, J.p_dE64[q]);
+                                    ta[nt] = lq == lp ? 1 : 0;
+                                    nt++;
+                                }
+                            }
+                        }
+                    }
+                }
+                int tot;
+                const int pos = block_excl(nt, s_w, &tot);
+                for (int i = 0; i < nt; i++) {
+                    s_t[pos + i] = tv[i];
+                    s_a[pos + i] = ta[i];
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    for (int i = 0; i < tot; i++) {
+                        if (s_a[i]) { As = __dadd_rn(As, s_t[i]); nA++; }
+                        else { Bs = __dadd_rn(Bs, s_t[i]); nB++; }
+                    }
+                }
+                __syncthreads();
+            }
+            if (tid == 0) {
+                const double A = nA ? __ddiv_rn(As, (double)nA) : 0.0;
+                const double B = nB ? __ddiv_rn(Bs, (double)nB) : 0.0;
+                fix_apply(J, sl, p, __dsub_rn(A, B));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s)
+{
+    if (njobs <= 0) return cudaSuccess;
+    return launch_stage(k_fixup, sms * 8, kFixThreads, 0, s, jobs, njobs);
 }
 
 // A, as its own grid, over the flattened candidates of all jobs
@@ -1300,8 +1301,22 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
     __shared__ unsigned char s_state[kSmallCandidates];
     extern __shared__ __align__(16) unsigned char s_dyn[];
     const unsigned total = block_job_prefix(jobs, njobs, kCountCand, s_pref, s_red);
+    // First the lists of the candidates whose keys the FP64 recompute replaced are rebuilt (every
+    // queued key is exact by now); one that the recompute dropped keeps its list, it never waits.
+    __shared__ unsigned s_fpref[kMaxBatchJobs + 1];
+    const unsigned nfix = block_job_prefix(jobs, njobs, kCountFlag, s_fpref, s_red);
+    auto relist = [&](unsigned f0, unsigned stride) {
+        for (unsigned fi = f0; fi < nfix; fi += stride) {
+            const int j = job_of(s_fpref, njobs, fi);
+            const Job& J = jobs[j];
+            const unsigned sl = J.flag_list[fi - s_fpref[j]];
+            if (ld_volatile(J.c_state + sl) != kRejected) relist_one(J, sl);
+        }
+    };
     if (total <= kSmallCandidates) {
         if (blockIdx.x != 0) return;
+        relist(threadIdx.x, blockDim.x);
+        __syncthreads();
         volatile unsigned char* st = s_state;
         // The candidates' neighbour lists (compressed rows of 16-bit flattened indices) and a
         // list of the undecided candidates live in shared memory when they fit; each round then
@@ -1350,7 +1365,8 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
             }
         }
         for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
-            st[i] = kUndecided;
+            const int j = job_of(s_pref, njobs, i);
+            st[i] = (unsigned char)jobs[j].c_state[i - s_pref[j]];   // undecided, or dropped by the recompute
             if (cache) s_wl0[i] = (unsigned short)i;
         }
         if (threadIdx.x == 0) s_cnt3[0] = 0;
@@ -1370,14 +1386,16 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
                 if (threadIdx.x == 0) s_cnt3[(r + 1) % 3] = 0;
                 for (unsigned t = threadIdx.x; t < n_cur; t += blockDim.x) {
                     const unsigned i = cur[t];
+                    const int v0 = st[i];              // decided already: dropped by the recompute
                     bool all_rej = true, rej = false;
-                    for (unsigned k = s_off[i], e = s_off[i + 1]; k < e; k++) {
-                        const int u = st[s_nb[k]];
-                        if (u == kAccepted) { rej = true; break; }
-                        if (u != kRejected) all_rej = false;
-                    }
-                    const int v = rej ? kRejected : (all_rej ? kAccepted : kUndecided);
-                    if (v != kUndecided) st[i] = (unsigned char)v;
+                    if (v0 == kUndecided)
+                        for (unsigned k = s_off[i], e = s_off[i + 1]; k < e; k++) {
+                            const int u = st[s_nb[k]];
+                            if (u == kAccepted) { rej = true; break; }
+                            if (u != kRejected) all_rej = false;
+                        }
+                    const int v = v0 != kUndecided ? v0 : (rej ? kRejected : (all_rej ? kAccepted : kUndecided));
+                    if (v0 == kUndecided && v != kUndecided) st[i] = (unsigned char)v;
                     const unsigned act = __activemask();
                     const unsigned m = __ballot_sync(act, v == kUndecided);
                     if (m) {
@@ -1439,6 +1457,13 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
     // from global memory. Every decision is also written to global memory as it is made.
     const unsigned nblocks = gridDim.x;
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nfix) {                                                             // uniform
+        relist(gtid, nblocks * blockDim.x);
+        if (!grid_barrier(bc, nblocks)) {
+            if (gtid == 0) bc->rounds_done = 0;
+            return;
+        }
+    }
     const unsigned per = (total + nblocks - 1) / nblocks;
     const unsigned lo = min(blockIdx.x * per, total), hi = min(lo + per, total);
     const unsigned n = hi - lo;
@@ -1451,7 +1476,7 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
         for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
             const int j = job_of(s_pref, njobs, lo + i);
             s_roff[i] = (unsigned)jobs[j].c_nnbr[lo + i - s_pref[j]];
-            st[i] = kUndecided;
+            st[i] = (unsigned char)jobs[j].c_state[lo + i - s_pref[j]];
         }
         __syncthreads();
         const unsigned chunk = (n + blockDim.x - 1) / blockDim.x;

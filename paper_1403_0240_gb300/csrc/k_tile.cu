@@ -939,6 +939,7 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
         for (unsigned i = tid; i < pcount; i += blockDim.x) {
             J.p_g[pstart + i] = J.p_dE[pstart + i];
             J.p_eg[pstart + i] = J.p_eE[pstart + i];
+            J.p_key[pstart + i] = J.p_dE64[pstart + i];   // L2: the key is the FP64 energy difference
         }
         return;
     }
@@ -1182,6 +1183,7 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
             const float TA = nA ? aA / (float)nA : 0.f, TB = nB ? aB / (float)nB : 0.f;
             J.p_g[p] = gp;
             J.p_eg[p] = pair_bound(gp, nA ? nA + kSplit : 0, TA, nB ? nB + kSplit : 0, TB);
+            J.p_key[p] = (double)gp;
             const float Af = __fadd_rn(Aq, Al), Bf = __fadd_rn(Bq, Bl);
             osc += (Af != 0.f && Bf != 0.f && ((Af > 0.f) == (Bf > 0.f))) ? 1u : 0u;
         }

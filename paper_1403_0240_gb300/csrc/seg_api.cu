@@ -221,7 +221,7 @@ struct Stepper {
     cudaEvent_t fence_in = nullptr, fence_out = nullptr;
 };
 
-constexpr int kStages = 10;
+constexpr int kStages = 9;
 
 struct seg_batch {
     Stepper st;
@@ -565,6 +565,7 @@ size_t particle_bytes(long long pcap, int stride)
     A.add(&h.c_best, pcap);
     A.add(&h.c_key, pcap);
     A.add(&h.c_pix, pcap);
+    A.add(&h.c_ge, pcap);
     A.add(&h.c_state, pcap);
     A.add(&h.c_nnbr, pcap);
     A.add(&h.c_nbr, pcap * stride);
@@ -595,6 +596,7 @@ void assign_particles(Job& h, char* base, long long pcap)
     A.add(&h.c_best, pcap);
     A.add(&h.c_key, pcap);
     A.add(&h.c_pix, pcap);
+    A.add(&h.c_ge, pcap);
     A.add(&h.c_state, pcap);
     A.add(&h.c_nnbr, pcap);
     A.add(&h.c_nbr, pcap * h.nbr_stride);
@@ -784,17 +786,14 @@ cudaError_t stepper_enqueue_stages(Stepper& s)
             return e;
     if ((e = stage_mark(s, 3)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
-        if (s.grp[gidx].njobs && (e = launch_flag(s.grp[gidx], s.work)) != cudaSuccess) return e;
-    if ((e = stage_mark(s, 4)) != cudaSuccess) return e;
-    if ((e = launch_fixup(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
-    if ((e = stage_mark(s, 5)) != cudaSuccess) return e;
-    for (int gidx = 0; gidx < 2; gidx++)
         if (s.grp[gidx].njobs && (e = launch_select(s.grp[gidx], s.d_bc, s.work)) != cudaSuccess) return e;
-    if ((e = stage_mark(s, 6)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 4)) != cudaSuccess) return e;
     if ((e = launch_lists(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
-    if ((e = stage_mark(s, 7)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 5)) != cudaSuccess) return e;
+    if ((e = launch_fixup(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 6)) != cudaSuccess) return e;
     if ((e = launch_rounds(s.d_jobs, n, s.d_bc, s.commit_grid, s.commit_block, s.work)) != cudaSuccess) return e;
-    if ((e = stage_mark(s, 8)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 7)) != cudaSuccess) return e;
     if ((e = launch_moves(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
     if (s.any_split)                    // split regions: pieces get new labels, statistics rebuilt
         for (int i = 0; i < n; i++)
@@ -804,9 +803,9 @@ cudaError_t stepper_enqueue_stages(Stepper& s)
     if (s.any_fuse)                     // touching regions whose fusion lowers the energy merge
         for (int i = 0; i < n; i++)
             if (s.members[i]->h.topo_fuse && (e = launch_fuse(s.d_jobs, i, s.sms, s.work)) != cudaSuccess) return e;
-    if ((e = stage_mark(s, 9)) != cudaSuccess) return e;
+    if ((e = stage_mark(s, 8)) != cudaSuccess) return e;
     if ((e = launch_finish(s.d_jobs, n, s.d_bc, s.sms, s.work)) != cudaSuccess) return e;
-    return stage_mark(s, 10);
+    return stage_mark(s, 9);
 }
 
 int stepper_set_profile(Stepper& s, bool on)

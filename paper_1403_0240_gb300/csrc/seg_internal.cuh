@@ -89,6 +89,7 @@ struct Counters {
     unsigned n_newcomp;     // pieces given new labels by the iteration's relabelling
     unsigned n_fpairs;      // fusion: touching label pairs listed in the hash table
     unsigned n_fused;       // fusion: pairs fused by the last fusion pass
+    unsigned n_void;        // candidates whose FP64 key turned out >= 0 (dropped before the rounds)
     long long g_lim;        // E = |Gamma| mode: interaction partners have d^2 < g_lim
     seg_status last;        // status of the last executed iteration
 };
@@ -218,6 +219,7 @@ struct alignas(64) Job {
     int* c_best;              // candidate -> particle
     unsigned long long* c_key;    // the candidate's key as an order-preserving integer (ordered_key)
     unsigned* c_pix;
+    float2* c_ge;             // the candidate's gradient as a float and its bound (0: the key is exact)
     int* c_state;
     int* c_nbr;               // smaller-key neighbouring candidates, nbr_stride slots per candidate
     int* c_nnbr;
@@ -592,7 +594,6 @@ cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t s
 cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t s);
 cudaError_t launch_global_lut(const Job* jobs, int njobs, int sms, cudaStream_t s);
 cudaError_t launch_sobolev_global(const Group& g, int ndim, cudaStream_t s);
-cudaError_t launch_flag(const Group& g, cudaStream_t s);
 cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s);
 cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cudaStream_t s);
 cudaError_t configure_kernels(size_t smem_x2, size_t smem_x3, size_t smem_s2, size_t smem_s3);

@@ -294,7 +294,7 @@ class Context:
         _check(lib().seg_poll(self.handle, C.byref(st)), "seg_poll")
         return st.as_dict()
 
-    STAGES = ("psf", "extract", "sobolev", "flag", "fixup", "select", "lists", "rounds", "moves", "finish")
+    STAGES = ("psf", "extract", "sobolev", "select", "lists", "fixup", "rounds", "moves", "finish")
 
     def inject(self, what: int):
         """Test-only fault injection (seg_debug_inject)."""
