@@ -82,9 +82,9 @@ def workloads():
 
 
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64, nominal
-# kernels of one iteration's graph: extract, sobolev, select, lists, fixup, rounds, moves, finish
-# (plus the deconvolving model's field passes); poll() adds one
-KERNELS_PER_ITERATION = 8
+# kernels of one iteration's graph: extract, sobolev (with the candidate selection), lists, fixup,
+# rounds, moves, finish (plus the deconvolving model's field passes); poll() adds one
+KERNELS_PER_ITERATION = 7
 # opt-in events and regulariser: kernels each adds to an iteration (the connected-component
 # relabelling of splits with its statistics rebuild; the fusion pairs, matching and relabelling;
 # the curvature term)

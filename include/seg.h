@@ -250,9 +250,11 @@ int seg_poll(seg_ctx* c, seg_status* out);
 
 /* Stage timing: when on, the captured iteration graph also records CUDA events
  * between its stages (psf, extract, sobolev, select, lists, fixup, rounds, moves, finish;
- * psf is the deconvolving model's field passes, empty for the other models; lists includes
- * the order certificates of neighbouring candidates, fixup the FP64 recompute of the keys
- * they did not certify); seg_stage_times waits for the stream and writes the milliseconds
+ * psf is the deconvolving model's field passes, empty for the other models; sobolev includes
+ * the candidate selection, and select is the E = |Gamma| mode's own selection, empty
+ * otherwise; lists includes the order certificates of neighbouring candidates, fixup the FP64
+ * recompute of the keys they did not certify); seg_stage_times waits for the stream and writes
+ * the milliseconds
  * each stage took in the most recent iteration (n >= 9), returning SEG_ESTATE when timing
  * is off. */
 int seg_profile(seg_ctx* c, int32_t on);

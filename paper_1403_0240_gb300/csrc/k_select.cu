@@ -23,6 +23,10 @@ __constant__ TopoTables c_topo;
 // Simple-point decisions tabulated for every neighbourhood mask: 2^8 (2D) and 2^26 (3D) bits,
 // computed once per process on the device from simple_mask() below.
 __constant__ const unsigned* c_simple[2];
+// host copies of the same, for the job descriptors
+static const unsigned* g_simple[2];
+static const unsigned* g_topo_adjF[2];
+static unsigned g_topo_touch[2], g_topo_nF[2];
 
 __device__ __forceinline__ bool simple_mask(unsigned X, int d);
 
@@ -50,6 +54,8 @@ cudaError_t simple_tables_init()
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
     const unsigned* ptrs[2] = {t2, t3};
+    g_simple[0] = t2;
+    g_simple[1] = t3;
     return cudaMemcpyToSymbol(c_simple, ptrs, sizeof ptrs);
 }
 
@@ -84,29 +90,26 @@ cudaError_t topology_tables_init()
     }
     cudaError_t e = cudaMemcpyToSymbol(c_topo, &t, sizeof t);
     if (e != cudaSuccess) return e;
+    // the jobs reach the foreground adjacency through a pointer (the selection runs in more
+    // than one translation unit)
+    unsigned* adj = nullptr;
+    if ((e = cudaMalloc(&adj, sizeof t.adjF)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(adj, t.adjF, sizeof t.adjF, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    for (int d = 0; d < 2; d++) {
+        g_topo_adjF[d] = adj + 26 * d;
+        g_topo_touch[d] = t.touch[d];
+        g_topo_nF[d] = t.nF[d];
+    }
     return simple_tables_init();
 }
 
-// number of components of set S (adjacency adj) that meet `touch` (all if touch == 0); stops at 2
-__device__ __forceinline__ int components(unsigned S, const unsigned* adj, unsigned touch)
+void topology_for_job(Job& h)
 {
-    int count = 0;
-    while (S) {
-        unsigned comp = S & (0u - S);
-        unsigned frontier = comp;
-        while (frontier) {
-            int a = __ffs(frontier) - 1;
-            frontier &= frontier - 1;
-            unsigned nb = adj[a] & S & ~comp;
-            comp |= nb;
-            frontier |= nb;
-        }
-        S &= ~comp;
-        if (!touch || (comp & touch)) {
-            if (++count > 1) return count;
-        }
-    }
-    return count;
+    const int d = h.ndim == 3 ? 1 : 0;
+    h.simple_tab = g_simple[d];
+    h.topo_adjF = g_topo_adjF[d];
+    h.topo_touch = g_topo_touch[d];
+    h.topo_nF = g_topo_nF[d];
 }
 
 __device__ __forceinline__ bool simple_mask(unsigned X, int d)
@@ -120,29 +123,6 @@ __device__ __forceinline__ bool simple_mask(unsigned X, int d)
 __device__ __forceinline__ bool simple_table(unsigned X, int d)
 {
     return (__ldg(c_simple[d] + (X >> 5)) >> (X & 31u)) & 1u;
-}
-
-// Topological control: removal from l (foreground) and addition to c (foreground)
-// must both be simple, so regions neither split, vanish, merge nor change holes. The
-// neighbourhood enters as two bit masks, written by extraction while it held the labels: bit k
-// of ml (mc) is set when the k-th neighbour (dz, dy, dx ascending, the centre skipped) holds l
-// (c); a neighbour outside the image holds neither. With SEG_TOPO_VANISH the removal of a
-// region's last pixel is admissible too: no 4- (6-) neighbour holds l (every foreground label
-// being one connected component). With SEG_TOPO_SPLIT a removal whose foreground number is
-// >= 2 is admissible too. Returns 0 (not admissible), 1, or 2 (admissible by the split rule).
-__device__ __forceinline__ int admissible(const Job& J, int l, int c, unsigned long long masks)
-{
-    const int d = J.ndim == 3 ? 1 : 0;
-    const unsigned ml = (unsigned)masks, mc = (unsigned)(masks >> 32);
-    // both table words are loaded before either is tested, so that their latencies overlap
-    const unsigned* tab = c_simple[d];
-    const unsigned wc = c != 0 ? __ldg(tab + (mc >> 5)) : 0xffffffffu;
-    const unsigned wl = l != 0 ? __ldg(tab + (ml >> 5)) : 0xffffffffu;
-    if (!((wc >> (mc & 31u)) & 1u)) return 0;
-    if ((wl >> (ml & 31u)) & 1u) return 1;
-    if (J.topo_vanish && (ml & c_topo.touch[d]) == 0) return 1;
-    if (J.topo_split && components(ml & c_topo.nF[d], c_topo.adjF[d], c_topo.touch[d]) >= 2) return 2;
-    return 0;
 }
 
 // the tabulated decision, as the selection uses it
@@ -192,13 +172,6 @@ __device__ __forceinline__ bool order_uncertain(float gp, float ep, float gq, fl
     return fabsf(__fsub_rn(gp, gq)) <= __fmul_rn(__fadd_rn(ep, eq), 1.00000024f);
 }
 
-// queue candidate slot s of job J for the FP64 recompute
-__device__ __forceinline__ void queue_fixup(const Job& J, unsigned s, unsigned p)
-{
-    J.p_flags[p] |= kFlagFixup;
-    const unsigned f = atomicAdd(&J.ctr->n_flag, 1u);
-    J.flag_list[f] = s;
-}
 
 // ---------------------------------------------------------------------------
 // FP64 recompute in the order of the definition: every product and sum rounded separately (no
@@ -292,14 +265,6 @@ __device__ __forceinline__ int block_excl(int v, int* s_w, int* total)
     return before + x - v;
 }
 
-// An integer image of a finite double that keeps its order: the sign bit set for x >= 0, all bits
-// flipped for x < 0 (-0 maps to the image of +0, as the two compare equal)
-__device__ __forceinline__ unsigned long long ordered_key(double k)
-{
-    unsigned long long b = (unsigned long long)__double_as_longlong(k);
-    if (b == 0x8000000000000000ull) b = 0ull;
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
 
 // The FP64 key of queued candidate slot s (particle p) replaces its float one: exact from now
 // on (bound 0); a key >= 0 drops the candidate, which then enters the rounds rejected.
@@ -502,9 +467,9 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
     const Job& J = g.jobs[g.job_ids[gj]];
     const unsigned k = t - g.tile_prefix[gj];
     Counters* ctr = J.ctr;
-    if (job_idle(ctr)) return;
+    if (job_idle(ctr) || ld_volatile(&ctr->mode) != SEG_SOBOLEV_GLOBAL) return;   // the others: k_sobolev
     const unsigned pstart = J.tile_start[k], pend = pstart + J.tile_count[k];
-    const bool exact_keys = ld_volatile(&ctr->mode) == SEG_L2;
+    const bool exact_keys = false;
     __shared__ unsigned s_scan[32], s_slot0;
     // the tile's candidates take one contiguous range of slots per pass (a block scan and one
     // counter update), so that candidate indices follow the tiles: the selection rounds give each

@@ -914,9 +914,13 @@ __device__ __forceinline__ void sobolev_sums(const Job& J, int lp, int x, int y,
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
+__global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g, BatchCtl* bc)
 {
     pdl_enter();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {       // the rounds' grid barrier and error word
+        bc->bar_count = 0;
+        bc->err = 0;
+    }
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned s_warp[32];
     __shared__ float2 s_klut[256];               // K(sqrt(d2)) as a float pair
@@ -935,11 +939,60 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
     const unsigned pstart = J.tile_start[k], pcount = J.tile_count[k];
     const int mode = ld_volatile(&ctr->mode);
     if (skip || pcount == 0 || mode == SEG_SOBOLEV_GLOBAL) return;   // E = |Gamma|: k_sobolev_global
+    __shared__ unsigned s_slot0;
+    // Candidates (Region Competition's selection): the best particle of a pixel (smallest key,
+    // then c) is a candidate when its key could be negative and the move is admissible. The
+    // pixel's first particle decides for the pixel; the block's candidates of one pass take one
+    // contiguous range of slots (a block scan, one counter update), so that candidate indices
+    // follow the tiles. Every thread of the block calls this once per pass.
+    auto select_append = [&](bool first, int adm, unsigned pfirst, unsigned best, unsigned gi, double bk, float bg,
+                             float be, bool exact) {
+        unsigned n_adm;
+        const unsigned rank = block_excl_scan(adm ? 1u : 0u, s_warp, n_adm);
+        if (tid == 0) s_slot0 = n_adm ? atomicAdd(&ctr->n_cand, n_adm) : 0u;
+        __syncthreads();
+        if (first) {
+            int slot = -1;
+            if (adm) {
+                slot = (int)(s_slot0 + rank);
+                J.c_best[slot] = (int)best;
+                J.c_key[slot] = ordered_key(bk);
+                J.c_pix[slot] = gi;
+                J.c_ge[slot] = make_float2(bg, be);
+                J.p_flags[best] |= adm == 2 ? (kFlagCand | kFlagSplit) : kFlagCand;
+                if (!exact && fabsf(bg) <= be) queue_fixup(J, (unsigned)slot, best);   // sign uncertain
+            }
+            J.pix_cand[pfirst] = slot;
+        }
+        __syncthreads();                       // s_warp and s_slot0 are reused by the next pass
+    };
     if (mode == SEG_L2) {
-        for (unsigned i = tid; i < pcount; i += blockDim.x) {
-            J.p_g[pstart + i] = J.p_dE[pstart + i];
-            J.p_eg[pstart + i] = J.p_eE[pstart + i];
-            J.p_key[pstart + i] = J.p_dE64[pstart + i];   // L2: the key is the FP64 energy difference
+        // L2: the gradient is the energy difference, the key its FP64 value (exact)
+        for (unsigned i0 = 0; i0 < pcount; i0 += blockDim.x) {       // uniform over the block
+            const unsigned i = i0 + tid;
+            const unsigned p = pstart + i;
+            bool first = false;
+            int adm = 0, bc_ = 0;
+            unsigned best = p, gi = 0;
+            double bk = 0.0;
+            if (i < pcount) {
+                J.p_g[p] = J.p_dE[p];
+                J.p_eg[p] = J.p_eE[p];
+                bk = J.p_dE64[p];
+                J.p_key[p] = bk;
+                gi = J.p_idx[p];
+                first = i == 0 || J.p_idx[p - 1] != gi;
+                if (first) {
+                    bc_ = J.p_c[p];
+                    for (unsigned q = p + 1; q < pstart + pcount && J.p_idx[q] == gi; q++) {
+                        const double kq = J.p_dE64[q];
+                        const int cq = J.p_c[q];
+                        if (kq < bk || (kq == bk && cq < bc_)) { best = q; bk = kq; bc_ = cq; }
+                    }
+                    adm = bk < 0.0 ? admissible(J, J.p_l[best], bc_, J.p_nbm[best]) : 0;
+                }
+            }
+            select_append(first, adm, p, best, gi, bk, 0.0f, 0.0f, true);
         }
         return;
     }
@@ -1123,6 +1176,11 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
             pix_coords(J, gi, x, y, z);
             const bool act = own && x >= sx0 && x < sx1;
             const int lp = i == my_i ? my_l : J.p_l[p];
+            // the particles of a pixel share g here, so its first particle (smallest c) is its
+            // best. Whether its move is admissible does not depend on g: the test (and its table
+            // loads) is issued now, so that its latency passes while Eq. 6 is summed.
+            const bool first = act && h == 0 && (i == 0 || J.p_idx[p - 1] != gi);
+            const int adm_pre = first ? admissible(J, lp, J.p_c[p], J.p_nbm[p]) : 0;
             DotAcc A, B;
             float aA = 0.f, aB = 0.f;
             int nA = 0, nB = 0;
@@ -1175,20 +1233,46 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g)
                 nA += __shfl_xor_sync(0xffffffffu, nA, o);
                 nB += __shfl_xor_sync(0xffffffffu, nB, o);
             }
-            if (!act || h) continue;
-            float Aq = 0.f, Al = 0.f, Bq = 0.f, Bl = 0.f;
-            if (nA) pair_div(A.s, A.t, nA, Aq, Al);
-            if (nB) pair_div(B.s, B.t, nB, Bq, Bl);
-            const float gp = pair_sub(Aq, Al, Bq, Bl);
-            const float TA = nA ? aA / (float)nA : 0.f, TB = nB ? aB / (float)nB : 0.f;
-            J.p_g[p] = gp;
-            J.p_eg[p] = pair_bound(gp, nA ? nA + kSplit : 0, TA, nB ? nB + kSplit : 0, TB);
-            J.p_key[p] = (double)gp;
-            const float Af = __fadd_rn(Aq, Al), Bf = __fadd_rn(Bq, Bl);
-            osc += (Af != 0.f && Bf != 0.f && ((Af > 0.f) == (Bf > 0.f))) ? 1u : 0u;
+            if (act && h == 0) {
+                float gp, ep;
+                float Aq = 0.f, Al = 0.f, Bq = 0.f, Bl = 0.f;
+                if (nA) pair_div(A.s, A.t, nA, Aq, Al);
+                if (nB) pair_div(B.s, B.t, nB, Bq, Bl);
+                gp = pair_sub(Aq, Al, Bq, Bl);
+                const float TA = nA ? aA / (float)nA : 0.f, TB = nB ? aB / (float)nB : 0.f;
+                ep = pair_bound(gp, nA ? nA + kSplit : 0, TA, nB ? nB + kSplit : 0, TB);
+                J.p_g[p] = gp;
+                J.p_eg[p] = ep;
+                J.p_key[p] = (double)gp;
+                const float Af = __fadd_rn(Aq, Al), Bf = __fadd_rn(Bq, Bl);
+                osc += (Af != 0.f && Bf != 0.f && ((Af > 0.f) == (Bf > 0.f))) ? 1u : 0u;
+                // possibly negative (g < eg) and admissible makes the pixel's best a candidate;
+                // its slot is taken after the last pass (no block barrier between passes)
+                if (gp < ep && adm_pre) J.p_flags[p] |= adm_pre == 2 ? (kFlagCand | kFlagSplit) : kFlagCand;
+            }
         }
         sx0 = sx1;
         __syncthreads();                                 // the next slab reuses shared memory
+    }
+    // the tile's candidates, marked above at their pixels' first particles, take their slots
+    for (unsigned i0 = 0; i0 < pcount; i0 += blockDim.x) {           // uniform over the block
+        const unsigned i = i0 + tid;
+        const unsigned p = pstart + i;
+        bool first = false;
+        int adm = 0;
+        unsigned gi = 0;
+        float gp = 0.0f, ep = 0.0f;
+        if (i < pcount) {
+            gi = J.p_idx[p];
+            first = i == 0 || J.p_idx[p - 1] != gi;
+            const unsigned char f = first ? J.p_flags[p] : (unsigned char)0;
+            adm = (f & kFlagCand) ? ((f & kFlagSplit) ? 2 : 1) : 0;
+            if (adm) {
+                gp = J.p_g[p];
+                ep = J.p_eg[p];
+            }
+        }
+        select_append(first, adm, p, p, gi, (double)gp, gp, ep, false);
     }
     if (osc) atomicAdd(&s_osc, osc);
     __syncthreads();
@@ -1200,11 +1284,11 @@ size_t sobolev_smem_bytes(const Job& J)
     return sob_layout(J).total;
 }
 
-cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t st)
+cudaError_t launch_sobolev(const Group& g, BatchCtl* bc, int ndim, size_t smem, cudaStream_t st)
 {
     if (g.total_tiles == 0) return cudaSuccess;
-    if (ndim == 2) return launch_stage(k_sobolev<2>, g.total_tiles, kBlock, smem, st, g);
-    return launch_stage(k_sobolev<3>, g.total_tiles, kBlock, smem, st, g);
+    if (ndim == 2) return launch_stage(k_sobolev<2>, g.total_tiles, kBlock, smem, st, g, bc);
+    return launch_stage(k_sobolev<3>, g.total_tiles, kBlock, smem, st, g, bc);
 }
 
 // Dynamic shared memory limits, set outside any stream capture. The limits only grow (per

@@ -780,13 +780,14 @@ cudaError_t stepper_enqueue_stages(Stepper& s)
     if ((e = stage_mark(s, 2)) != cudaSuccess) return e;
     if (s.any_global && (e = launch_global_lut(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
-        if (s.grp[gidx].njobs && (e = launch_sobolev(s.grp[gidx], gidx + 2, s.smem_s[gidx], s.work)) != cudaSuccess) return e;
+        if (s.grp[gidx].njobs && (e = launch_sobolev(s.grp[gidx], s.d_bc, gidx + 2, s.smem_s[gidx], s.work)) != cudaSuccess) return e;
     for (int gidx = 0; gidx < 2; gidx++)
         if (s.any_global && s.grp[gidx].njobs && (e = launch_sobolev_global(s.grp[gidx], gidx + 2, s.work)) != cudaSuccess)
             return e;
     if ((e = stage_mark(s, 3)) != cudaSuccess) return e;
-    for (int gidx = 0; gidx < 2; gidx++)
-        if (s.grp[gidx].njobs && (e = launch_select(s.grp[gidx], s.d_bc, s.work)) != cudaSuccess) return e;
+    if (s.any_global)                   // E = |Gamma|: its candidates (the other modes select in k_sobolev)
+        for (int gidx = 0; gidx < 2; gidx++)
+            if (s.grp[gidx].njobs && (e = launch_select(s.grp[gidx], s.d_bc, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 4)) != cudaSuccess) return e;
     if ((e = launch_lists(s.d_jobs, n, s.sms, s.work)) != cudaSuccess) return e;
     if ((e = stage_mark(s, 5)) != cudaSuccess) return e;
@@ -1167,6 +1168,7 @@ int seg_init(const seg_params* p, const void* image, const int32_t* labels0, voi
 
     const cudaError_t topo_err = ensure_topology_tables();
     if (topo_err != cudaSuccess) return fail(cuda_fail(topo_err, "topology tables"));
+    topology_for_job(c->h);
     Counters hc{};
     hc.iter_tag = 1;
     hc.mode = p->gradient;

@@ -150,6 +150,9 @@ struct alignas(64) Job {
     double* dc_G;             // ... G = K * R at the particle pixels of the iteration [npix]
     int M;                    // number of labels
     int osc_window;           // L2 fallback window (0 = never)
+    const unsigned* simple_tab;   // simple-point decisions, one bit per neighbourhood mask (this job's dimension)
+    const unsigned* topo_adjF;    // foreground adjacency of the neighbour positions (26 masks)
+    unsigned topo_touch, topo_nF; // 4- (6-) neighbours of the centre; the foreground count's neighbourhood
     int topo_vanish;          // a region's last pixel may leave it (SEG_TOPO_VANISH)
     int topo_split;           // a region may split (SEG_TOPO_SPLIT); M is then the label capacity
     int* cc_parent;           // ... relabelling: union-find parent per pixel [npix]
@@ -367,6 +370,72 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl* bc, unsigned nblocks)
     }
     __syncthreads();
     return ld_volatile(&bc->err) == 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// Candidate selection helpers shared by the kernels that select (the interaction kernel for the
+// local modes, the selection kernel for E = |Gamma|).
+
+// number of components of set S (adjacency adj) that meet `touch` (all if touch == 0); stops at 2
+__device__ __forceinline__ int components(unsigned S, const unsigned* adj, unsigned touch)
+{
+    int count = 0;
+    while (S) {
+        unsigned comp = S & (0u - S);
+        unsigned frontier = comp;
+        while (frontier) {
+            int a = __ffs(frontier) - 1;
+            frontier &= frontier - 1;
+            unsigned nb = adj[a] & S & ~comp;
+            comp |= nb;
+            frontier |= nb;
+        }
+        S &= ~comp;
+        if (!touch || (comp & touch)) {
+            if (++count > 1) return count;
+        }
+    }
+    return count;
+}
+
+// Topological control: removal from l (foreground) and addition to c (foreground)
+// must both be simple, so regions neither split, vanish, merge nor change holes. The
+// neighbourhood enters as two bit masks, written by extraction while it held the labels: bit k
+// of ml (mc) is set when the k-th neighbour (dz, dy, dx ascending, the centre skipped) holds l
+// (c); a neighbour outside the image holds neither. With SEG_TOPO_VANISH the removal of a
+// region's last pixel is admissible too: no 4- (6-) neighbour holds l (every foreground label
+// being one connected component). With SEG_TOPO_SPLIT a removal whose foreground number is
+// >= 2 is admissible too. Returns 0 (not admissible), 1, or 2 (admissible by the split rule).
+__device__ __forceinline__ int admissible(const Job& J, int l, int c, unsigned long long masks)
+{
+    const unsigned ml = (unsigned)masks, mc = (unsigned)(masks >> 32);
+    // both table words are loaded before either is tested, so that their latencies overlap
+    const unsigned* tab = J.simple_tab;
+    const unsigned wc = c != 0 ? __ldg(tab + (mc >> 5)) : 0xffffffffu;
+    const unsigned wl = l != 0 ? __ldg(tab + (ml >> 5)) : 0xffffffffu;
+    if (!((wc >> (mc & 31u)) & 1u)) return 0;
+    if ((wl >> (ml & 31u)) & 1u) return 1;
+    if (J.topo_vanish && (ml & J.topo_touch) == 0) return 1;
+    if (J.topo_split && components(ml & J.topo_nF, J.topo_adjF, J.topo_touch) >= 2) return 2;
+    return 0;
+}
+
+// An integer image of a finite double that keeps its order: the sign bit set for x >= 0, all bits
+// flipped for x < 0 (-0 maps to the image of +0, as the two compare equal)
+__device__ __forceinline__ unsigned long long ordered_key(double k)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(k);
+    if (b == 0x8000000000000000ull) b = 0ull;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// queue candidate slot s of job J for the FP64 recompute
+__device__ __forceinline__ void queue_fixup(const Job& J, unsigned s, unsigned p)
+{
+    J.p_flags[p] |= kFlagFixup;
+    const unsigned f = atomicAdd(&J.ctr->n_flag, 1u);
+    J.flag_list[f] = s;
 }
 
 // Deconvolving model: the last separable pass of G = K * R at pixel gi (along y in 2D, z in
@@ -591,7 +660,7 @@ inline cudaError_t launch_stage(void (*k)(KArgs...), dim3 grid, dim3 block, size
 
 // Launch wrappers (one iteration's stages); defined in the kernel translation units.
 cudaError_t launch_extract(const Group& g, int ndim, size_t smem, cudaStream_t s);
-cudaError_t launch_sobolev(const Group& g, int ndim, size_t smem, cudaStream_t s);
+cudaError_t launch_sobolev(const Group& g, BatchCtl* bc, int ndim, size_t smem, cudaStream_t s);
 cudaError_t launch_global_lut(const Job* jobs, int njobs, int sms, cudaStream_t s);
 cudaError_t launch_sobolev_global(const Group& g, int ndim, cudaStream_t s);
 cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s);
@@ -613,6 +682,7 @@ cudaError_t launch_scan_inputs(const void* I, int dtype, const int* L, int ndim,
                                cudaStream_t s);
 cudaError_t launch_stats_finalize(const Job* jobs, int njobs, cudaStream_t s);
 cudaError_t topology_tables_init();
+void topology_for_job(Job& h);   // the job's pointers to the topology tables (after topology_tables_init)
 cudaError_t commit_occupancy(int block, int* blocks_per_sm);
 size_t extract_smem_bytes(const Job& h);
 size_t sobolev_smem_bytes(const Job& h);

@@ -6,10 +6,10 @@ from paper_1403_0240_gb300 import seg, synth
 
 pytestmark = pytest.mark.gpu
 
-# one iteration of a 2D piecewise-constant job: extraction with the energy differences, Eq. 6,
-# candidates, neighbour lists with the order certificates, FP64 recompute, selection rounds,
+# one iteration of a 2D piecewise-constant job: extraction with the energy differences, Eq. 6 with
+# the candidates, neighbour lists with the order certificates, FP64 recompute, selection rounds,
 # moves, finish
-KERNELS_PER_ITERATION = 8
+KERNELS_PER_ITERATION = 7
 
 
 def test_graph_replays_count_every_kernel():
