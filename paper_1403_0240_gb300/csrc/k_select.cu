@@ -968,7 +968,9 @@ constexpr size_t kRoundsDyn = 160 * 1024;      // dynamic shared memory of the r
 // A: neighbour lists of smaller-key candidates; states reset
 // Neighbour positions by compile-time index (dz, dy, dx ascending, the centre skipped), so
 // that the per-neighbour arrays stay in registers.
-template <int NDIM, bool kCertify>
+constexpr int kMarked = (int)0x80000000u;    // a list entry whose order the rounds settle
+
+template <int NDIM>
 __device__ __forceinline__ void commit_list_nd(const Job& J, unsigned s)
 {
     constexpr int K = NDIM == 3 ? 27 : 9;
@@ -993,22 +995,23 @@ __device__ __forceinline__ void commit_list_nd(const Job& J, unsigned s)
 #pragma unroll
     for (int t = 0; t < K; t++)
         slot[t] = ((in >> t) & 1u) && (unsigned)(e[t] >> 32) == tag ? J.pix_cand[(unsigned)e[t]] : -1;
-    const float2 gs = kCertify ? J.c_ge[s] : make_float2(0.0f, 0.0f);
+    const float2 gs = J.c_ge[s];
     bool uncertain = false;
     int n = 0;
 #pragma unroll
     for (int t = 0; t < K; t++) {
         const int o = slot[t];
         if (o < 0) continue;
-        if (key_less(J.c_key[o], J.c_pix[o], ks, gi)) J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
-        if (kCertify && gs.y > 0.0f) {
-            const float2 go = J.c_ge[o];
-            uncertain |= order_uncertain(gs.x, gs.y, go.x, go.y);
-        }
+        // a pair whose gap is not certified enters the list marked, whatever the float order:
+        // both keys are recomputed in FP64, and the rounds compare them then
+        const bool unc = gs.y > 0.0f && order_uncertain(gs.x, gs.y, J.c_ge[o].x, J.c_ge[o].y);
+        uncertain |= unc;
+        if (unc) J.c_nbr[(long long)s * J.nbr_stride + n++] = o | kMarked;
+        else if (key_less(J.c_key[o], J.c_pix[o], ks, gi)) J.c_nbr[(long long)s * J.nbr_stride + n++] = o;
     }
     J.c_nnbr[s] = n;
     J.c_state[s] = kUndecided;
-    if (kCertify && uncertain) {
+    if (uncertain) {
         const unsigned p = (unsigned)J.c_best[s];
         if (!(J.p_flags[p] & kFlagFixup)) queue_fixup(J, s, p);   // not already queued for its sign
     }
@@ -1016,15 +1019,18 @@ __device__ __forceinline__ void commit_list_nd(const Job& J, unsigned s)
 
 __device__ __forceinline__ void commit_list_one(const Job& J, unsigned s)
 {
-    if (J.ndim == 3) commit_list_nd<3, true>(J, s);
-    else commit_list_nd<2, true>(J, s);
+    if (J.ndim == 3) commit_list_nd<3>(J, s);
+    else commit_list_nd<2>(J, s);
 }
 
-// the list of a candidate whose key the FP64 recompute replaced (no certificate needed)
-__device__ __forceinline__ void relist_one(const Job& J, unsigned s)
+// A list entry of candidate s: candidate o when it has the smaller (key, pixel), -1 when it
+// does not. Unmarked entries are smaller by construction; a marked one is compared on the
+// keys, exact by the time the rounds run.
+__device__ __forceinline__ int list_entry(const Job& J, unsigned s, int e)
 {
-    if (J.ndim == 3) commit_list_nd<3, false>(J, s);
-    else commit_list_nd<2, false>(J, s);
+    if (!(e & kMarked)) return e;
+    const int o = e & ~kMarked;
+    return key_less(J.c_key[o], J.c_pix[o], J.c_key[s], J.c_pix[s]) ? o : -1;
 }
 
 // B: one decision for candidate s of job J on state array st (offset b); returns the new
@@ -1036,7 +1042,9 @@ __device__ __forceinline__ int commit_decide(const Job& J, unsigned s, State st,
     const int* nb = J.c_nbr + (long long)s * J.nbr_stride;
     bool all_rej = true;
     for (int i = 0; i < n; i++) {
-        const int v = st[b + nb[i]];
+        const int o = list_entry(J, s, nb[i]);
+        if (o < 0) continue;
+        const int v = st[b + o];
         if (v == kAccepted) return kRejected;
         if (v != kRejected) all_rej = false;
     }
@@ -1263,25 +1271,11 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
     __shared__ unsigned s_red[32];
     __shared__ unsigned s_flag;
     __shared__ unsigned s_pref[kMaxBatchJobs + 1];
-    __shared__ unsigned char s_state[kSmallCandidates];
+    __shared__ unsigned char s_state[kSmallCandidates + 1];   // + a sentinel, always rejected
     extern __shared__ __align__(16) unsigned char s_dyn[];
     const unsigned total = block_job_prefix(jobs, njobs, kCountCand, s_pref, s_red);
-    // First the lists of the candidates whose keys the FP64 recompute replaced are rebuilt (every
-    // queued key is exact by now); one that the recompute dropped keeps its list, it never waits.
-    __shared__ unsigned s_fpref[kMaxBatchJobs + 1];
-    const unsigned nfix = block_job_prefix(jobs, njobs, kCountFlag, s_fpref, s_red);
-    auto relist = [&](unsigned f0, unsigned stride) {
-        for (unsigned fi = f0; fi < nfix; fi += stride) {
-            const int j = job_of(s_fpref, njobs, fi);
-            const Job& J = jobs[j];
-            const unsigned sl = J.flag_list[fi - s_fpref[j]];
-            if (ld_volatile(J.c_state + sl) != kRejected) relist_one(J, sl);
-        }
-    };
     if (total <= kSmallCandidates) {
         if (blockIdx.x != 0) return;
-        relist(threadIdx.x, blockDim.x);
-        __syncthreads();
         volatile unsigned char* st = s_state;
         // The candidates' neighbour lists (compressed rows of 16-bit flattened indices) and a
         // list of the undecided candidates live in shared memory when they fit; each round then
@@ -1326,7 +1320,10 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
                 const int* nb = J.c_nbr + (long long)(i - s_pref[j]) * J.nbr_stride;
                 const unsigned n = s_wl1[i], o = s_off[i], b = s_pref[j];
 #pragma unroll 8
-                for (unsigned k = 0; k < n; k++) s_nb[o + k] = (unsigned short)(b + nb[k]);
+                for (unsigned k = 0; k < n; k++) {
+                    const int e = list_entry(J, i - b, nb[k]);
+                    s_nb[o + k] = (unsigned short)(e >= 0 ? b + (unsigned)e : total);   // total: the sentinel
+                }
             }
         }
         for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
@@ -1334,6 +1331,7 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
             st[i] = (unsigned char)jobs[j].c_state[i - s_pref[j]];   // undecided, or dropped by the recompute
             if (cache) s_wl0[i] = (unsigned short)i;
         }
+        if (threadIdx.x == 0) st[total] = kRejected;               // the sentinel of settled entries
         if (threadIdx.x == 0) s_cnt3[0] = 0;
         __syncthreads();
         unsigned rounds = 0;
@@ -1422,13 +1420,6 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
     // from global memory. Every decision is also written to global memory as it is made.
     const unsigned nblocks = gridDim.x;
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (nfix) {                                                             // uniform
-        relist(gtid, nblocks * blockDim.x);
-        if (!grid_barrier(bc, nblocks)) {
-            if (gtid == 0) bc->rounds_done = 0;
-            return;
-        }
-    }
     const unsigned per = (total + nblocks - 1) / nblocks;
     const unsigned lo = min(blockIdx.x * per, total), hi = min(lo + per, total);
     const unsigned n = hi - lo;
@@ -1443,6 +1434,7 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
             s_roff[i] = (unsigned)jobs[j].c_nnbr[lo + i - s_pref[j]];
             st[i] = (unsigned char)jobs[j].c_state[lo + i - s_pref[j]];
         }
+        if (threadIdx.x == 0) st[n] = kRejected;                   // the sentinel of settled entries
         __syncthreads();
         const unsigned chunk = (n + blockDim.x - 1) / blockDim.x;
         const unsigned c0 = min(threadIdx.x * chunk, n), c1 = min(c0 + chunk, n);
@@ -1467,9 +1459,10 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
                 const int* nb = J.c_nbr + (long long)(lo + i - s_pref[j]) * J.nbr_stride;
                 const unsigned e0 = s_roff[i], e1 = s_roff[i + 1];
                 for (unsigned k = e0; k < e1; k++) {
-                    const unsigned slot = (unsigned)nb[k - e0];
+                    const int e = list_entry(J, lo + i - s_pref[j], nb[k - e0]);
+                    const unsigned slot = (unsigned)e;
                     const unsigned loc = s_pref[j] + slot - lo;
-                    s_ent[k] = loc < n ? loc : (slot | 0x80000000u);
+                    s_ent[k] = e < 0 ? n : (loc < n ? loc : (slot | 0x80000000u));   // n: the sentinel
                 }
             }
         __syncthreads();
