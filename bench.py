@@ -49,10 +49,12 @@ L2_FLUSH_BYTES = 256 << 20
 # method's own traffic, band-only (a full-image rescan is implementation overhead).
 #   extract = particle write (idx, l, c: 12 B) + amortised label-band reads (8 B)
 #           + image value (4 B) + energy difference out (4 B)
-#   sobolev = particle in (idx, l, c, dE: 16 B) + gradient out (4 B)
-#   select, lists, fixup, rounds = 12 B per particle (a particle read per decision stage);
+#   sobolev = particle in (idx, l, c, dE: 16 B) + gradient out (4 B), plus the candidate
+#           selection fused into it (12 B: a particle read per decision stage)
+#   select (E = |Gamma| only), lists, fixup, rounds = 12 B per particle (a particle read per
+#           decision stage);
 #   moves = 24 B per accepted move (label write and statistics); finish = 12 B per particle
-ALG_BYTES = {"extract": (28, 0), "sobolev": (20, 0), "fixup": (12, 0),
+ALG_BYTES = {"extract": (28, 0), "sobolev": (32, 0), "fixup": (12, 0),
              "select": (12, 0), "lists": (12, 0), "rounds": (12, 0), "moves": (0, 24), "finish": (12, 0)}
 
 
