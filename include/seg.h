@@ -159,7 +159,7 @@ typedef struct {
     int64_t n_fixup;       /* particles whose gradient was recomputed in FP64 */
     int32_t mode_used;     /* SEG_SOBOLEV | SEG_L2 | SEG_SOBOLEV_GLOBAL */
     int32_t converged;     /* an L2 iteration accepted no move; later iterations do nothing */
-    int32_t mis_rounds;    /* rounds of the parallel ranked selection */
+    int32_t mis_rounds;    /* rounds of the parallel ranked selection (many candidates: the most sweeps of one block) */
     int32_t error;         /* 0, or a SEG_E* code raised on the device; SEG_ENOMEM: the
                               particle buffers overflowed and the iteration was not run
                               (the next seg_step regrows them and runs it) */

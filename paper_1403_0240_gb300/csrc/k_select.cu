@@ -462,6 +462,7 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
     if (t == 0 && threadIdx.x == 0) {
         bc->bar_count = 0;
         bc->err = 0;
+        bc->rounds_done = 0;
     }
     const int gj = group_job_of_tile(g, t);
     const Job& J = g.jobs[g.job_ids[gj]];
@@ -1419,7 +1420,6 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
     // index of a neighbour inside the range, or (top bit set) the job slot of one outside it, read
     // from global memory. Every decision is also written to global memory as it is made.
     const unsigned nblocks = gridDim.x;
-    const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned per = (total + nblocks - 1) / nblocks;
     const unsigned lo = min(blockIdx.x * per, total), hi = min(lo + per, total);
     const unsigned n = hi - lo;
@@ -1467,59 +1467,64 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
             }
         __syncthreads();
     }
-    unsigned rounds = 0, sweeps = 0;
-    for (unsigned r = 0;; r++) {
-        unsigned* cnt = &bc->rounds_cnt[r % 3];
-        unsigned undecided;
-        while (true) {
-            int changed = 0;
-            undecided = 0;
-            for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-                int v;
-                if (cache) {
-                    if (st[i] != kUndecided) continue;
-                    bool all_rej = true, rej = false;
-                    for (unsigned k = s_roff[i], e = s_roff[i + 1]; k < e; k++) {
-                        const unsigned en = s_ent[k];
-                        int u;
-                        if (en & 0x80000000u) {
-                            const Job& J = jobs[job_of(s_pref, njobs, lo + i)];
-                            u = ld_volatile(J.c_state + (en & 0x7fffffffu));
-                        } else {
-                            u = st[en];
-                        }
-                        if (u == kAccepted) { rej = true; break; }
-                        if (u != kRejected) all_rej = false;
+    // No grid-wide rounds: each block sweeps its range until all of it is decided. A sweep that
+    // decides nothing while some of the range is left waits (bounded) for the other blocks'
+    // decisions, which arrive through global memory; the smallest undecided candidate of the whole
+    // grid can always be decided, so some block always progresses. A block leaves as soon as its
+    // range is done.
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) s_stop = 0;
+    unsigned sweeps = 0;
+    WaitBound wb;
+    while (true) {
+        int changed = 0, left = 0;
+        for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+            int v;
+            if (cache) {
+                if (st[i] != kUndecided) continue;
+                bool all_rej = true, rej = false;
+                for (unsigned k = s_roff[i], e = s_roff[i + 1]; k < e; k++) {
+                    const unsigned en = s_ent[k];
+                    int u;
+                    if (en & 0x80000000u) {
+                        const Job& J = jobs[job_of(s_pref, njobs, lo + i)];
+                        u = ld_volatile(J.c_state + (en & 0x7fffffffu));
+                    } else {
+                        u = st[en];
                     }
-                    v = rej ? kRejected : (all_rej ? kAccepted : kUndecided);
-                    if (v != kUndecided) st[i] = (unsigned char)v;
-                } else {
-                    const int j = job_of(s_pref, njobs, lo + i);
-                    if (ld_volatile(jobs[j].c_state + (lo + i - s_pref[j])) != kUndecided) continue;
-                    v = commit_decide(jobs[j], lo + i - s_pref[j], (const volatile int*)jobs[j].c_state, 0u);
+                    if (u == kAccepted) { rej = true; break; }
+                    if (u != kRejected) all_rej = false;
                 }
-                if (v == kUndecided) {
-                    undecided++;
-                } else {
-                    const int j = job_of(s_pref, njobs, lo + i);
-                    *(volatile int*)(jobs[j].c_state + (lo + i - s_pref[j])) = v;
-                    changed = 1;
-                }
+                v = rej ? kRejected : (all_rej ? kAccepted : kUndecided);
+                if (v != kUndecided) st[i] = (unsigned char)v;
+            } else {
+                const int j = job_of(s_pref, njobs, lo + i);
+                if (ld_volatile(jobs[j].c_state + (lo + i - s_pref[j])) != kUndecided) continue;
+                v = commit_decide(jobs[j], lo + i - s_pref[j], (const volatile int*)jobs[j].c_state, 0u);
             }
-            ++sweeps;
-            if (!__syncthreads_or(changed) || sweeps >= kMaxRounds) break;
+            if (v == kUndecided) {
+                left = 1;
+            } else {
+                const int j = job_of(s_pref, njobs, lo + i);
+                *(volatile int*)(jobs[j].c_state + (lo + i - s_pref[j])) = v;
+                changed = 1;
+            }
         }
-        const unsigned bs = block_sum(undecided, s_red);
-        if (threadIdx.x == 0 && bs) atomicAdd(cnt, bs);
-        if (gtid == 0) bc->rounds_cnt[(r + 1) % 3] = 0;
-        if (!grid_barrier(bc, nblocks)) break;
-        if (ld_volatile(cnt) == 0) { rounds = r + 1; break; }
-        if (r + 1 >= kMaxRounds || sweeps >= kMaxRounds) {
-            if (gtid == 0) atomicExch(&bc->err, SEG_ETIMEOUT);
-            break;
+        ++sweeps;
+        if (!__syncthreads_or(left)) break;
+        if (__syncthreads_or(changed)) {
+            if (threadIdx.x == 0) wb = WaitBound();
+            continue;
         }
+        if (threadIdx.x == 0 && (wb.expired() || sweeps >= kMaxRounds)) {
+            s_stop = 1;
+            atomicExch(&bc->err, SEG_ETIMEOUT);
+        }
+        __syncthreads();
+        if (s_stop) break;
+        __nanosleep(128);
     }
-    if (gtid == 0) bc->rounds_done = rounds;
+    if (threadIdx.x == 0) atomicMax(&bc->rounds_done, sweeps);
 }
 
 // C, as its own grid: accepted moves; accepted counts aggregated per warp and job

@@ -917,9 +917,10 @@ template <int NDIM>
 __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g, BatchCtl* bc)
 {
     pdl_enter();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {       // the rounds' grid barrier and error word
+    if (blockIdx.x == 0 && threadIdx.x == 0) {       // the selection's control words
         bc->bar_count = 0;
         bc->err = 0;
+        bc->rounds_done = 0;
     }
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned s_warp[32];
