@@ -153,6 +153,26 @@ def test_no_particles():
     ctx.close()
 
 
+@pytest.mark.parametrize("three_d", [False, True])
+def test_zero_gradients_drop_every_speculative_candidate(three_d):
+    # A flat image and no length prior: every energy difference, hence every gradient, is exactly
+    # zero, and the oracle has no candidate. On the GPU each admissible pixel is a possible
+    # candidate whose sign the bound cannot certify (|g| <= eg); the FP64 recompute finds 0 and
+    # drops it before the rounds, so that the counts and labels match.
+    shape = (20, 24, 28) if three_d else (48, 56)
+    I = np.full(shape, 5, np.uint16) if three_d else np.full(shape, 5.0, np.float32)
+    idx = np.indices(shape)
+    r2 = sum((idx[k] - shape[k] // 2) ** 2 for k in range(len(shape)))
+    L = np.where(r2 <= 49, 1, 0).astype(np.int32)
+    w = synth.Workload("zero", I, L, "pc", 6 if three_d else 4, 0.0, 3.0)
+    ctx, run = pair(w)
+    for it in range(3):
+        st, _ = compare_step(ctx, run, f"zero{len(shape)}d it{it}")
+        assert st["n_candidates"] == 0 and st["n_accepted"] == 0
+        assert st["n_fixup"] > 0, st                 # the speculative candidates were recomputed
+    ctx.close()
+
+
 def test_checkpoint_resume_repeats_bit_for_bit():
     w = synth.disks(96, 96, seed=81)
     a = seg.Context.from_workload(w, osc_window=4)
