@@ -371,7 +371,7 @@ __device__ void fixup_warps(const Job* jobs, int njobs, unsigned total, const un
         const unsigned sl = J.flag_list[fi - s_pref[j]];
         const unsigned p = (unsigned)J.c_best[sl];
         const unsigned gi = J.p_idx[p];
-        const int lp = J.p_l[p], cp = J.p_c[p];
+        const int lp = J.p_l[p];
         if (mode == SEG_L2) {
             if (lane == 0) fix_apply(J, sl, p, J.p_dE64[p]);
             continue;
@@ -460,7 +460,6 @@ __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
     pdl_enter();
     const unsigned t = blockIdx.x;
     if (t == 0 && threadIdx.x == 0) {
-        bc->bar_count = 0;
         bc->err = 0;
         bc->rounds_done = 0;
     }
@@ -1183,7 +1182,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fixup(const Job* jobs, int njob
         const unsigned sl = J.flag_list[f];
         const unsigned p = (unsigned)J.c_best[sl];
         const unsigned gi = J.p_idx[p];
-        const int lp = J.p_l[p], cp = J.p_c[p];
+        const int lp = J.p_l[p];
         if (mode == SEG_L2) {
             if (tid == 0) fix_apply(J, sl, p, J.p_dE64[p]);
         } else if (mode == SEG_SOBOLEV_GLOBAL) {
@@ -1408,14 +1407,10 @@ __global__ void __launch_bounds__(1024) k_rounds(const Job* jobs, int njobs, Bat
         return;
     }
 
-    // The whole grid, one bounded grid barrier per round. Block b owns the candidate indices
-    // [lo, hi); candidates are numbered tile by tile, so that is a compact part of each image.
-    // Within a round a block sweeps its range until a sweep decides nothing more (its chains
-    // resolve without the grid), then all blocks meet; the rounds end when no candidate is
-    // undecided. Decisions are final once made and depend only on smaller-key neighbours, so the
-    // order of the sweeps does not change them. Round r counts the undecided in rounds_cnt[r % 3]
-    // and clears the counter of round r + 1 before its barrier (that counter was last read right
-    // after the barrier that ended round r - 2).
+    // The whole co-resident grid. Block b owns the candidate indices [lo, hi); candidates are
+    // numbered tile by tile, so that is a compact part of each image. Decisions are final once
+    // made and depend only on smaller-key neighbours, so the order in which blocks and sweeps
+    // make them does not change them.
     // When they fit, the range's states and rows sit in shared memory: a row entry is the local
     // index of a neighbour inside the range, or (top bit set) the job slot of one outside it, read
     // from global memory. Every decision is also written to global memory as it is made.
@@ -1585,9 +1580,6 @@ __global__ void __launch_bounds__(256) k_finish(const Job* jobs, int njobs, Batc
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         bc->ticket[0] = 0;
         bc->ticket[1] = 0;
-        bc->rounds_cnt[0] = 0;
-        bc->rounds_cnt[1] = 0;
-        bc->rounds_cnt[2] = 0;
     }
 }
 

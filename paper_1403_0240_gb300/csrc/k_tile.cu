@@ -918,7 +918,6 @@ __global__ void __launch_bounds__(kBlock, NDIM == 2 ? 4 : 3) k_sobolev(Group g, 
 {
     pdl_enter();
     if (blockIdx.x == 0 && threadIdx.x == 0) {       // the selection's control words
-        bc->bar_count = 0;
         bc->err = 0;
         bc->rounds_done = 0;
     }

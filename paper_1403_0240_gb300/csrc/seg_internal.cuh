@@ -241,9 +241,6 @@ struct Group {
 
 struct BatchCtl {
     unsigned ticket[2];       // per group
-    unsigned bar_count;
-    unsigned bar_gen;
-    unsigned rounds_cnt[3];
     int err;
     unsigned rounds_done;     // selection rounds of the last iteration
     unsigned pad[7];
@@ -346,32 +343,6 @@ __device__ __forceinline__ int group_job_of_tile(const Group& g, unsigned t)
     }
     return lo;
 }
-
-// Bounded grid-wide barrier for a co-resident (cooperative) grid.
-__device__ __forceinline__ bool grid_barrier(BatchCtl* bc, unsigned nblocks)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned gen = ld_volatile(&bc->bar_gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(&bc->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            bc->bar_count = 0;
-            __threadfence();
-            atomicAdd(&bc->bar_gen, 1u);
-        } else {
-            WaitBound wb;
-            while (ld_volatile(&bc->bar_gen) == gen) {
-                if (wb.expired()) { atomicExch(&bc->err, SEG_ETIMEOUT); break; }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ld_volatile(&bc->err) == 0;
-}
-
 
 // ---------------------------------------------------------------------------
 // Candidate selection helpers shared by the kernels that select (the interaction kernel for the
