@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -141,10 +142,16 @@ def read_peaks():
 
 
 def kernel_sources_digest() -> str:
+    """A digest of the profiled kernels' code: the sources without their comments and blank lines, so
+    that a change of wording leaves the committed ncu figures valid and a change of code does not."""
     h = hashlib.sha256()
     for f in ("k_tile.cu", "k_select.cu", "seg_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1403_0240_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1403_0240_gb300", "csrc", f), encoding="utf-8") as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code.strip():
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

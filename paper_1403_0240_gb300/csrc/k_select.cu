@@ -1,7 +1,8 @@
-// Decision kernels of one iteration: certification of float32 decisions, the FP64
-// recompute of uncertified gradients, candidate selection with topology control,
-// and the cooperative commit (ranked conflict-free selection, label update, exact
-// region statistics, oscillation fallback).
+// Decision kernels of one iteration: the neighbour lists of the candidates with the order
+// certificates of their float32 keys, the FP64 recompute of uncertified keys, the candidate
+// selection of the E = |Gamma| mode (the other modes select inside the interaction kernel), and
+// the commit (ranked conflict-free selection, label update, exact region statistics,
+// oscillation fallback).
 #include <algorithm>
 
 #include "seg_internal.cuh"
@@ -452,9 +453,10 @@ cudaError_t launch_gather_counters(const Job* jobs, int njobs, Counters* out, cu
 }
 
 // ---------------------------------------------------------------------------
-// Candidates: per pixel the particle with the smallest (key, c); a candidate if its
-// key is negative and its move passes the topology tests (labels read from global memory:
-// only a minority of the tile's pixels are tested, and their neighbourhoods overlap in L1).
+// Candidates of the E = |Gamma| mode (after the all-pairs interaction kernel): per pixel the
+// particle with the smallest (key, c); a candidate when its key could be negative and its move
+// passes the topology tests on the masks extraction wrote. The other modes select the same way
+// inside the interaction kernel.
 __global__ void __launch_bounds__(256) k_select(Group g, BatchCtl* bc)
 {
     pdl_enter();

@@ -1,5 +1,6 @@
-// Tile kernels of one iteration: particle extraction fused with the energy
-// difference, and the Sobolev interaction of Eq. 6 over a cell tile.
+// Tile kernels of one iteration: particle extraction fused with the energy difference and
+// the topology masks, and the Sobolev interaction of Eq. 6 over a cell tile fused with the
+// candidate selection.
 #include <algorithm>
 #include <mutex>
 
