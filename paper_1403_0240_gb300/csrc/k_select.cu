@@ -1253,7 +1253,7 @@ cudaError_t launch_fixup(const Job* jobs, int njobs, int sms, cudaStream_t s)
 }
 
 // A, as its own grid, over the flattened candidates of all jobs
-__global__ void __launch_bounds__(256) k_lists(const Job* jobs, int njobs)
+__global__ void __launch_bounds__(256, 4) k_lists(const Job* jobs, int njobs)
 {
     pdl_enter();
     __shared__ unsigned s_pref[kMaxBatchJobs + 1];
