@@ -141,18 +141,26 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_sources_digest() -> str:
-    """A digest of the profiled kernels' code: the sources without their comments and blank lines, so
-    that a change of wording leaves the committed ncu figures valid and a change of code does not."""
+def _code_digest(texts) -> str:
+    """sha256 (16 hex digits) of C/CUDA sources without their comments and blank lines."""
     h = hashlib.sha256()
-    for f in ("k_tile.cu", "k_select.cu", "seg_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1403_0240_gb300", "csrc", f), encoding="utf-8") as fh:
-            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+    for src in texts:
+        text = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         for line in text.splitlines():
             code = line.split("//", 1)[0].rstrip()
             if code.strip():
                 h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
+
+
+def kernel_sources_digest() -> str:
+    """A digest of the profiled kernels' code: the sources without their comments and blank lines, so
+    that a change of wording leaves the committed ncu figures valid and a change of code does not."""
+    texts = []
+    for f in ("k_tile.cu", "k_select.cu", "seg_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1403_0240_gb300", "csrc", f), encoding="utf-8") as fh:
+            texts.append(fh.read())
+    return _code_digest(texts)
 
 
 def traffic_from_profile(stage: str, workload: str, units: float):

@@ -61,3 +61,12 @@ def test_topology_options_and_their_kernel_counts():
     assert bench.extra_kernels(A) == 0
     A.topology, A.curv_radius = "vanish+split", 5.0
     assert bench.extra_kernels(A) == bench.EXTRA_KERNELS["split"] + bench.EXTRA_KERNELS["curvature"]
+
+
+def test_profile_digest_covers_code_not_comments():
+    a = ["int f(int x) { return x + 1; }  // adds one\n/* a block\n   comment */\n"]
+    b = ["// another note\nint f(int x) { return x + 1; }\n\n"]
+    c = ["int f(int x) { return x + 2; }\n"]
+    assert bench._code_digest(a) == bench._code_digest(b)
+    assert bench._code_digest(a) != bench._code_digest(c)
+    assert len(bench.kernel_sources_digest()) == 16
