@@ -89,3 +89,45 @@ def test_certified_selection_equals_the_exact_greedy(seed):
     e = np.maximum(e, np.abs(g.astype(np.float64) - keys).astype(np.float32) * np.float32(1.0000002))
     assert (np.abs(g.astype(np.float64) - keys) <= e.astype(np.float64)).all()
     assert _certified(keys, g, e, pix, nbrs) == _exact_greedy(keys, pix, nbrs)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_block_sweeps_in_any_interleaving_reach_the_greedy_set(seed):
+    # The rounds without grid barriers: candidates are split into contiguous ranges (one per
+    # block); in every step one randomly chosen block sweeps its range once, in a random thread
+    # order, reading the states as they are. Decisions depend only on smaller-key neighbours, so
+    # whatever the interleaving the result is the greedy set, and a sweep of some block always
+    # decides something while candidates are left (no block can wait for ever).
+    rng = np.random.default_rng(100 + seed)
+    n = 400
+    pos = rng.permutation(30 * 30)[:n]
+    pix = list(pos)
+    where = {p: i for i, p in enumerate(pix)}
+    nbrs = []
+    for p in pix:
+        y, x = divmod(int(p), 30)
+        nbrs.append([where[(y + dy) * 30 + x + dx] for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                     if (dy or dx) and 0 <= y + dy < 30 and 0 <= x + dx < 30 and (y + dy) * 30 + x + dx in where])
+    keys = -rng.integers(1, 40, n).astype(np.float64)          # many exact ties, broken by pixel
+    order = sorted(range(n), key=lambda i: pix[i])              # candidates numbered in pixel order
+    smaller = [[o for o in nbrs[s] if (keys[o], pix[o]) < (keys[s], pix[s])] for s in range(n)]
+    state = ["undecided"] * n
+    blocks = np.array_split(np.array(order), 7)
+    left = n
+    while left:
+        progress = False
+        for b in rng.permutation(len(blocks)):
+            for s in rng.permutation(blocks[b]):
+                if state[s] != "undecided":
+                    continue
+                st = [state[o] for o in smaller[s]]
+                if "accepted" in st:
+                    state[s] = "rejected"
+                elif all(v == "rejected" for v in st):
+                    state[s] = "accepted"
+                else:
+                    continue
+                left -= 1
+                progress = True
+        assert progress, "no block could decide anything"
+    assert {i for i in range(n) if state[i] == "accepted"} == _exact_greedy(keys, pix, nbrs)
